@@ -1,0 +1,331 @@
+"""Benchmark of the NEP hot path on GB300.
+
+Headline: NVE molecular dynamics with the FP32 NEP force path on the
+125,000-atom diamond workload (25^3 cells, 32-30-1 network, 300 K start,
+dt = 1 fs, 1 A skin), in atom-steps per second.  One bench step is one MD
+step: kick + drift, skin check (and list rebuild when due), site energies
+and partial forces, force/virial assembly with the second kick, heat current
+and FP64 reductions.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this paper
+has: it publishes no code) on the host cores, on bounded samples of the same
+workload.  Under torchrun (N > 1) every rank runs an independent replica
+(the path has no exchange step) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_08119_gb300 import inputs  # noqa: E402
+
+METRIC = "NEP MD atom-step/s at 125k atoms; SNES generation/s (pop 50) vs plain FP32"
+UNIT = "atom-step/s"
+WORKLOAD = "NVE MD, 125,000-atom Si-like diamond (25^3 cells), NEP 32-30-1 FP32, dt 1 fs, skin 1 A"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- flop model
+def flops_per_atom(m_r: float, m_a: float, n_neu: int = 30) -> float:
+    """Algorithmic FP32 flops (FMA = 2) of one atom's site + partial-force pass
+    in the O(M) harmonic form: per radial pair 134 (g_n, g_n' for 8 orders,
+    accumulation, contraction), per angular pair 1500 (g_n, g_n' for 6 orders,
+    24 harmonics and gradients, 144 accumulations, 2 x 144 contractions,
+    r-hat and gradient terms), per atom 288 for q_nl plus 2 x 2 x n_neu x 32
+    for the network and its input gradient and 10 per tanh."""
+    return 134.0 * m_r + 1500.0 * m_a + 288.0 + 4.0 * n_neu * 32 + 10.0 * n_neu
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_oracle_md(seconds: float = 15.0, cells: int = 8, max_steps: int | None = None):
+    """Oracle MD on an 8^3-cell (4,096-atom) block of the same lattice, model,
+    displacements and temperature; atom-steps/s on the host cores."""
+    import oracle
+    pos, vel, box, z = inputs.config2(n_cells=cells)
+    h = oracle.NepHyper()
+    z = np.asarray(z, np.float32).astype(np.float64)
+    n = len(pos)
+    t0 = time.perf_counter()
+    pos, vel, _, _ = oracle.md(h, z, pos, vel, box, inputs.MASS_SI, 1.0, 1)
+    per = time.perf_counter() - t0
+    steps = max(1, int(seconds / max(per, 1e-3)))
+    if max_steps is not None:
+        steps = min(steps, max_steps)
+    t0 = time.perf_counter()
+    oracle.md(h, z, pos, vel, box, inputs.MASS_SI, 1.0, steps)
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} velocity-Verlet steps (+1 startup force call excluded) of the FP64 oracle on a "
+                      f"{n}-atom {cells}^3-cell block of the same workload (same model, sigma, 300 K)"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: W + K MD steps on the 4,096-atom sample."""
+    if rank != 0:
+        return 0
+    import oracle
+    pos, vel, box, z = inputs.config2(n_cells=8)
+    h = oracle.NepHyper()
+    z = np.asarray(z, np.float32).astype(np.float64)
+    n = len(pos)
+    if args.warmup > 0:
+        pos, vel, _, _ = oracle.md(h, z, pos, vel, box, inputs.MASS_SI, 1.0, args.warmup)
+    t0 = time.perf_counter()
+    oracle.md(h, z, pos, vel, box, inputs.MASS_SI, 1.0, args.steps)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{n}-atom 8^3-cell block per step", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: one oracle MD step on a {n}-atom 8^3-cell block of the workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_2107_08119_gb300 import build
+    build.build()
+    from paper_2107_08119_gb300 import nep as N
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+    pos, vel, box, z = inputs.config2()
+    n = len(pos)
+    hyper = N.Hyper()
+    model = N.NEP(np.asarray(z, np.float32), hyper)
+
+    # average neighbour counts within r_c^R and r_c^A of the starting state (flop model)
+    p0 = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
+    model.compute(p0, box)
+    cnt, nbr = model.neighbors(n)
+    j = (nbr & 0xFFFFFF).long()
+    code = (nbr >> 24).long()
+    valid = torch.arange(nbr.shape[0], device="cuda")[:, None] < cnt[None, :]
+    L = torch.tensor(np.diag(box), device="cuda")
+    wrapped = p0 - L[:, None] * torch.floor(p0 / L[:, None])
+    shifts = torch.stack([code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2]).double() * L[:, None, None]
+    jj = j.clamp(max=n - 1)
+    r = wrapped[:, jj] + shifts - wrapped[:, None, :]
+    d = torch.linalg.norm(r, dim=0)
+    m_r = float(((d < hyper.rc_R) & valid).sum()) / n
+    m_a = float(((d < hyper.rc_A) & valid).sum()) / n
+    del j, code, valid, shifts, jj, r, d, nbr, cnt
+
+    md = N.MD(model, n, box, inputs.MASS_SI)
+    p = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
+    v = torch.tensor(vel.T.copy(), dtype=torch.float64, device="cuda")
+    K, W = args.steps, args.warmup
+    thermo = torch.zeros(max(K, W, 1), N.THERMO_COLS, dtype=torch.float64, device="cuda")
+    heat = torch.zeros(max(K, W, 1), 3, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    md.step(p, v, W, 1.0, thermo, heat)
+    md.sync_status()
+    rebuilds0 = md.rebuild_count()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    model.profile_read()
+    model.profile(True)          # events around each force-pass launch, on the launching stream
+    e0.record(stream)
+    md.step(p, v, K, 1.0, thermo, heat)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    model.profile(False)
+    prof = model.profile_read()
+    site_ms = prof["site_ms"] / max(1, prof["site_launches"])
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    md.sync_status()
+    ms = e0.elapsed_time(e1)
+    rebuilds = md.rebuild_count() - rebuilds0
+    th = thermo[:K].cpu().numpy()
+    etot = th[:, 0] + th[:, 1]
+
+    # end to end through the C ABI with host buffers: per step, the state goes
+    # host -> device from pinned memory and comes back with the thermo row
+    hp = torch.empty_like(p, device="cpu").pin_memory()
+    hv = torch.empty_like(v, device="cpu").pin_memory()
+    hth = torch.empty(N.THERMO_COLS, dtype=torch.float64).pin_memory()
+    hp.copy_(p)
+    hv.copy_(v)
+    Ke = max(1, min(K, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        p.copy_(hp, non_blocking=True)
+        v.copy_(hv, non_blocking=True)
+        md.step(p, v, 1, 1.0, thermo, None)
+        hp.copy_(p, non_blocking=True)
+        hv.copy_(v, non_blocking=True)
+        hth.copy_(thermo[0], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    md.sync_status()
+
+    t_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        e = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(e, op=dist.ReduceOp.MAX)
+        e2e_s = float(e.item())
+    value = world * n * K / (t_max / 1e3)
+
+    flops_atom = flops_per_atom(m_r, m_a, hyper.n_neu)
+    achieved = flops_atom * n / (site_ms / 1e3) / 1e12
+    peak = fp32_peak_tflops(2070.0)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "atoms": n, "md_steps_timed": K, "list_rebuilds_timed": rebuilds,
+                       "l2": "inputs larger than L2 (per-step working set: positions, velocities, 96-slot "
+                             "neighbour list, reverse index and partial forces ~340 MB > 129 MB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "mean_neighbors_rcR": m_r, "mean_neighbors_rcA": m_a,
+                       "energy_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / n)},
+            "roofline": {"kernel": "k_site (descriptors + network + partial forces)", "bound": "alu",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None, "flops_per_atom": flops_atom, "kernel_ms": site_ms,
+                         "kernel_share_of_step": prof["site_ms"] / t_max if t_max > 0 else None,
+                         "assemble_ms": prof["assemble_ms"] / max(1, prof["assemble_launches"]),
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (fp32 pipe, derived)"},
+            "clocks": clocks,
+            "e2e": {"value": world * n * Ke / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": int(p.numel() * 8 + v.numel() * 8),
+                    "d2h_bytes_per_step": int(p.numel() * 8 + v.numel() * 8 + N.THERMO_COLS * 8),
+                    "steps": Ke},
+            "gpu_launches": 13 * K,
+            "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_md(seconds=args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    md.close()
+    model.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

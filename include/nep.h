@@ -1,0 +1,256 @@
+/*
+ * nep.h -- C ABI of the GB300 (sm_103a) neuroevolution-potential library.
+ *
+ * The method is the NEP of Fan et al., "Neuroevolution machine learning
+ * potentials" (arXiv 2107.08119).  Equation numbers below are the paper's.
+ *
+ * Conventions for every entry point
+ *   - Return value: NEP_OK (0) or a negative nep_status; never aborts or
+ *     throws across the ABI.  nep_last_error() gives a message for the last
+ *     failing call of the calling thread.
+ *   - "dev" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are ordinary host memory read during the call only.
+ *   - Work is enqueued on the caller's CUDA stream (cudaStream_t passed as
+ *     void*, NULL = legacy default stream) and is asynchronous; errors found
+ *     on the device (neighbour-list overflow, non-finite values) are latched
+ *     in the handle and reported by nep_sync_status().
+ *   - Units: Angstrom, eV, amu, fs.  Positions and velocities are FP64
+ *     structure-of-arrays [3][n] (all x, then all y, then all z).  Per-atom
+ *     forces and virials are FP32; site energies and totals are FP64.
+ *   - Boxes are 9 doubles, rows = lattice vectors a, b, c.  This library
+ *     handles orthorhombic boxes (a, b, c along x, y, z); each edge must be
+ *     at least half the neighbour-list radius.  Other boxes: NEP_ERR_BOX.
+ *   - Handles are not thread-safe: one handle, one host thread at a time.
+ */
+#ifndef NEP_H
+#define NEP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NEP_OK = 0,
+    NEP_ERR_ARG = -1,                /* null pointer, bad size, bad hyperparameter */
+    NEP_ERR_OOM = -2,                /* device allocation failed */
+    NEP_ERR_CUDA = -3,               /* a CUDA runtime call failed */
+    NEP_ERR_NEIGHBOR_OVERFLOW = -4,  /* an atom had more than max_neighbors neighbours */
+    NEP_ERR_NONFINITE = -5,          /* non-finite site energy or force */
+    NEP_ERR_TIMEOUT = -6,            /* a bounded device-side wait gave up */
+    NEP_ERR_BOX = -7,                /* box not orthorhombic, or an edge too short */
+    NEP_ERR_UNSUPPORTED = -8         /* hyperparameters this build has no kernel for */
+} nep_status;
+
+/*
+ * Hyperparameters (Table I of the paper names n_max^R, n_max^A, l_max, N_neu,
+ * r_c^R, r_c^A).  Descriptor size N_des = (n_max_R+1) + (n_max_A+1) l_max
+ * (Eq. 16); parameter count N_par = (N_des+2) N_neu + 1 (Eq. 26).
+ * This build has kernels for n_max_R = 7, n_max_A = 5, l_max = 4 and any
+ * n_neu in [1, 64].
+ */
+typedef struct {
+    int n_max_R;        /* radial Chebyshev orders 0..n_max_R */
+    int n_max_A;        /* radial orders 0..n_max_A inside the angular terms */
+    int l_max;          /* Legendre orders 1..l_max */
+    int n_neu;          /* hidden-layer neurons */
+    double rc_R;        /* radial cutoff r_c^R */
+    double rc_A;        /* angular cutoff r_c^A */
+    double skin;        /* Verlet skin for MD; the list radius is max(rc_R, rc_A) + skin */
+    int max_neighbors;  /* Verlet-list capacity per atom, 1..384 (e.g. 96) */
+} nep_hyper;
+
+typedef struct nep_model nep_model;
+typedef struct nep_md nep_md;
+
+/*
+ * nep_create -- build a model handle.
+ *   hp      host, hyperparameters (copied).
+ *   z       host, n_par floats: the parameter vector of Sec. II.D.3,
+ *           laid out as w1 [n_neu][N_des] row-major, b1 [n_neu], w2 [n_neu], b2,
+ *           with descriptor order q_0..q_{n_max_R}, then q_{nl} with n outer and
+ *           l inner.  Biases enter with a minus sign (Eqs. 21-22).
+ *   out     receives the handle; the handle owns all device scratch.
+ * Errors: NEP_ERR_ARG, NEP_ERR_UNSUPPORTED, NEP_ERR_OOM, NEP_ERR_CUDA.
+ */
+int nep_create(const nep_hyper* hp, const float* z, int n_par, nep_model** out);
+
+/* Replace the parameter vector (host, n_par floats); stream-ordered copy. */
+int nep_set_parameters(nep_model* m, const float* z, int n_par, void* stream);
+
+/* Free the handle and its device scratch (synchronises the device). */
+int nep_destroy(nep_model* m);
+
+/*
+ * nep_compute_efv -- site energies, forces and per-atom virials of one
+ * configuration (Sec. II.A-D):
+ *   U_i (Eq. 22) from the descriptor q^i (Eqs. 12-15) through the network
+ *   (Eqs. 21-22); partial forces dU_i/dr_ij (Eqs. 23-25); forces
+ *   F_i = sum_j (dU_i/dr_ij - dU_j/dr_ji) (Eqs. 4-5); per-atom virials
+ *   W_i^{ab} = sum_j r_ij^a (dU_j/dr_ji)^b (Eq. 6).
+ *   n            number of atoms, 1 <= n < 2^24.
+ *   box9         host, 9 doubles (orthorhombic).
+ *   pos          dev, FP64 [3][n]; not modified (wrapped into the box internally).
+ *   e_total      dev, 1 double, sum_i U_i; or NULL.
+ *   e_atom       dev, n doubles, U_i (the FP32 path carries U_i as a compensated
+ *                hi + lo pair; it is reported without a final FP32 rounding); or NULL.
+ *   force        dev, FP32 [3][n]; or NULL.
+ *   virial_atom  dev, FP32 [9][n], component 3a+b holds W_i^{ab}; or NULL.
+ *   virial_total dev, 9 doubles, sum_i W_i (symmetric); or NULL.
+ *   stream       cudaStream_t.
+ * The neighbour list is rebuilt on every call with radius max(rc_R, rc_A).
+ * Errors: NEP_ERR_ARG, NEP_ERR_BOX, NEP_ERR_OOM, NEP_ERR_CUDA (immediate);
+ * NEP_ERR_NEIGHBOR_OVERFLOW (latched, see nep_sync_status).
+ */
+int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, double* e_total, double* e_atom,
+                    float* force, float* virial_atom, double* virial_total, void* stream);
+
+/*
+ * nep_sync_status -- synchronise `stream`, then return and clear the first
+ * device-side error latched by earlier calls on this handle (NEP_OK if none).
+ */
+int nep_sync_status(nep_model* m, void* stream);
+
+/*
+ * nep_heat_current -- J = sum_i W_i . v_i, J^a = sum_b W_i^{ab} v_i^b
+ * (Eq. 7 summed over atoms), products in FP32 and accumulation in FP64, in a
+ * fixed order (deterministic).
+ *   virial_atom  dev, FP32 [9][n] as written by nep_compute_efv.
+ *   vel          dev, FP64 [3][n] (Angstrom/fs).
+ *   J            dev, 3 doubles (eV Angstrom/fs).
+ */
+int nep_heat_current(nep_model* m, int n, const float* virial_atom, const double* vel, double* J, void* stream);
+
+/*
+ * Molecular dynamics: NVE velocity Verlet with a Verlet neighbour list of
+ * radius max(rc_R, rc_A) + skin, rebuilt on the device whenever an atom has
+ * moved more than skin/2 since the last build.  Per step:
+ *   v += dt/2 F/m; x += dt v; [rebuild]; F, W from x; v += dt/2 F/m;
+ *   then E_pot, E_kin, sum_i W_i and J = sum_i W_i . v_i (Eq. 7) in FP64.
+ * Positions, velocities and the integrator update are FP64; the force path
+ * is FP32.  Positions are wrapped into the box at every list rebuild.
+ *
+ * nep_md_create: n atoms of one species of mass `mass` (amu) in box9 (host).
+ */
+int nep_md_create(nep_model* m, int n, const double* box9, double mass, nep_md** out);
+int nep_md_destroy(nep_md* md);
+
+#define NEP_THERMO_COLS 8 /* E_pot, E_kin, W_xx, W_yy, W_zz, W_xy, W_yz, W_zx (eV) */
+
+/*
+ * nep_md_step -- advance n_steps steps of dt fs.
+ *   pos, vel   dev, FP64 [3][n], updated in place.
+ *   thermo     dev, [n_steps][NEP_THERMO_COLS] doubles, or NULL.
+ *   heat       dev, [n_steps][3] doubles: J after each step, or NULL.
+ * Forces are recomputed at the start of a call when the positions may have
+ * changed outside the library (first call, or nep_md_invalidate()).
+ */
+int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, double* thermo, double* heat,
+                void* stream);
+
+/* Mark positions as changed by the caller: the next step rebuilds the list and forces. */
+int nep_md_invalidate(nep_md* md);
+
+/* Number of neighbour-list builds so far (synchronises `stream`). */
+int nep_md_rebuild_count(nep_md* md, long long* count, void* stream);
+
+/* Per-atom force (FP32 [3][n], dev) of the current MD state, owned by the handle. */
+const float* nep_md_forces(const nep_md* md);
+
+/*
+ * nep_get_neighbors -- copy the neighbour list built by the last
+ * nep_compute_efv call on this handle (radius max(rc_R, rc_A)).
+ *   count  dev, n ints: neighbours of each atom (may exceed max_neighbors
+ *          when the list overflowed).
+ *   nbr    dev, [max_neighbors][n] ints, slot-major: entry (k, i) is
+ *          j | c << 24 for the k-th neighbour j of atom i seen through the
+ *          periodic image (sx, sy, sz) = (c/25 - 2, (c/5)%5 - 2, c%5 - 2),
+ *          i.e. r_ij = r_j + sx a + sy b + sz c - r_i.  Slots beyond count
+ *          are unspecified.  Order: increasing distance (ties keep the cell
+ *          stencil / atom index order).
+ */
+int nep_get_neighbors(nep_model* m, int n, int* count, int* nbr, void* stream);
+
+/*
+ * Training set for the separable natural evolution strategy (Sec. II.D.2):
+ * structures of uneven size evaluated together (Sec. II.E concatenates them
+ * into one "super-structure").  nep_dataset_create copies the structures to
+ * the device and precomputes everything independent of the parameters:
+ * descriptors and, per pair, the derivatives of each atom's descriptor with
+ * respect to its pair vectors (Eqs. 24-25).
+ *   n_struct   number of structures (>= 1); n_atoms host [n_struct].
+ *   boxes      host [n_struct][9] (orthorhombic).
+ *   pos        host [N][3] FP64 (AoS; structures consecutive), N = sum n_atoms.
+ *   e_tar      host [n_struct] target energies (eV, per structure).
+ *   f_tar      host [N][3] target forces (eV/A).
+ *   w_tar      host [n_struct][6] target virials sum_i W_i, order xx yy zz xy yz zx.
+ * The handle keeps a pointer to the model (same hyperparameters).
+ */
+typedef struct nep_dataset nep_dataset;
+int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const double* boxes, const double* pos,
+                       const double* e_tar, const double* f_tar, const double* w_tar, nep_dataset** out);
+int nep_dataset_destroy(nep_dataset* ds);
+/* Atoms, stored pairs and device bytes of a training set; pointers may be NULL. */
+int nep_dataset_info(const nep_dataset* ds, int* n_atoms, long long* n_pairs, long long* device_bytes);
+/* Copy the precomputed descriptors, dev [N][N_des] FP32. */
+int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
+
+#define NEP_PREC_FP32 0 /* network of every member in FP32 (CUDA cores) */
+#define NEP_PREC_BF16 1 /* population GEMMs in BF16 with FP32 accumulation (tensor cores) */
+#define NEP_LOSS_COLS 6 /* L, L_e, L_f, L_v, L_1, L_2 */
+
+/*
+ * snes_evaluate_population -- the loss of Eq. 29 for every member of a
+ * population on a training set: L = l_e L_e + l_f L_f + l_v L_v + l_1 L_1 + l_2 L_2
+ * with the RMSEs of Eqs. 30-32 (energy and virial per atom) and the
+ * regularisers of Eqs. 33-34.
+ *   z_pop      dev [n_pop][n_par] FP32 parameter vectors, 1 <= n_pop <= 64.
+ *   precision  NEP_PREC_FP32 or NEP_PREC_BF16.
+ *   lambdas    host [5] = {l_e, l_f, l_v, l_1, l_2}; NULL = {1, 1, 1, 0.05, 0.05}.
+ *   loss       dev [n_pop][NEP_LOSS_COLS] FP64.
+ * Deterministic: fixed summation order.
+ */
+int snes_evaluate_population(nep_model* m, nep_dataset* ds, const float* z_pop, int n_pop, int precision,
+                             const double* lambdas, double* loss, void* stream);
+
+/*
+ * SNES state (Sec. II.D.2, Eqs. 35-39): mean m and step sizes s (FP32,
+ * n_par each), population size n_pop (2..64), and the seed of the
+ * Philox4x32-10 stream that draws r_k.
+ */
+typedef struct snes_state snes_state;
+int snes_create(nep_model* m, int n_pop, const float* mean0, const float* sigma0, unsigned long long seed,
+                snes_state** out);
+int snes_destroy(snes_state* st);
+/*
+ * snes_step -- one generation: draws r_k (standard normals, Philox4x32-10 with
+ * counter {e/4, 0, generation, 0x4E4550}, Box-Muller) unless r_in (dev
+ * [n_pop][n_par]) is given, forms z_k = m + s (.) r_k (Eq. 35), evaluates the
+ * losses, ranks members by ascending loss (ties: lower index first), and
+ * updates m then s with rank utilities u_k = max(0, ln(n/2+1) - ln k) / sum - 1/n,
+ * eta_m = 1, eta_s = (3 + ln N_par) / (5 sqrt N_par) (Eqs. 36-39).
+ *   loss_out   dev [n_pop][NEP_LOSS_COLS] or NULL.
+ */
+int snes_step(snes_state* st, nep_dataset* ds, int precision, const double* lambdas, const float* r_in,
+              double* loss_out, void* stream);
+/* Copy m, s (dev [n_par]), the last draws r (dev [n_pop][n_par]) and the
+ * member index at each rank (dev int [n_pop]); NULL pointers are skipped. */
+int snes_get_state(snes_state* st, float* mean, float* sigma, float* r_last, int* order, void* stream);
+
+/*
+ * Kernel timing: when enabled, the library records CUDA events on the
+ * launching stream around every launch of its two force passes (site
+ * energies + partial forces; force/virial assembly).  nep_profile_read
+ * synchronises, returns the summed durations (ms) and launch counts since
+ * the last read, and resets them.  Any pointer may be NULL.
+ */
+int nep_profile_enable(nep_model* m, int on);
+int nep_profile_read(nep_model* m, double* site_ms, long long* site_launches, double* assemble_ms,
+                     long long* assemble_launches);
+
+/* Message describing the last failing call on this thread ("" if none). */
+const char* nep_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEP_H */

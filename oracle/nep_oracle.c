@@ -654,6 +654,92 @@ int orc_site(const orc_hyper* h, const double* z, int n, const double* box, cons
     return efv_impl(h, z, n, box, pos, 2, NULL, NULL, NULL, q, G, x);
 }
 
+/*
+ * Energy, force and per-atom virial of selected atoms only (same definitions
+ * as orc_efv).  Site quantities are evaluated for the selected atoms and their
+ * neighbours; F_i and W_i need the neighbours' partial forces towards i,
+ * found as the neighbour's pair with the opposite vector.
+ */
+int orc_efv_sample(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, int n_sample,
+                   const int* idx, double* U, double* F, double* W)
+{
+    int rcode = check_hyper(h);
+    if (rcode) return rcode;
+    nlist L;
+    rcode = nlist_build(n, box, pos, max_cutoff(h), 2, &L);
+    if (rcode) return rcode;
+    int nd = orc_n_des(h), nh = h->n_neu;
+    char* need = (char*)calloc((size_t)n, 1);
+    for (int s = 0; s < n_sample; ++s) {
+        int i = idx[s];
+        if (i < 0 || i >= n) {
+            free(need);
+            nlist_free(&L);
+            return ORC_ERR_ARG;
+        }
+        need[i] = 1;
+        for (int t = L.start[i]; t < L.start[i + 1]; ++t) need[L.j[t]] = 1;
+    }
+    size_t np = (size_t)L.start[n];
+    double* p = (double*)calloc(3 * (np > 0 ? np : 1), sizeof(double));
+    double* Ua = (double*)calloc((size_t)n, sizeof(double));
+#pragma omp parallel
+    {
+        double* q = (double*)malloc(sizeof(double) * nd);
+        double* G = (double*)malloc(sizeof(double) * nd);
+        double* x = (double*)malloc(sizeof(double) * nh);
+        double* Jb = (double*)malloc(sizeof(double) * 3 * nd);
+#pragma omp for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            if (!need[i]) continue;
+            env E;
+            env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i]);
+            descriptor(h, &E, q);
+            Ua[i] = network(h, z, q, x, G);
+            for (int a = 0; a < E.m; ++a) partial_force(h, &E, a, G, Jb, p + 3 * ((size_t)L.start[i] + a));
+            env_free(&E);
+        }
+        free(q);
+        free(G);
+        free(x);
+        free(Jb);
+    }
+    for (int s = 0; s < n_sample; ++s) {
+        int i = idx[s];
+        if (U) U[s] = Ua[i];
+        double f[3] = {0, 0, 0}, w[9] = {0};
+        for (int t = L.start[i]; t < L.start[i + 1]; ++t) {
+            int j = L.j[t];
+            const double* rij = L.r + 3 * (size_t)t;
+            /* the pair of j pointing back to i through the opposite image */
+            int back = -1;
+            for (int u = L.start[j]; u < L.start[j + 1]; ++u) {
+                const double* rji = L.r + 3 * (size_t)u;
+                if (L.j[u] == i && fabs(rji[0] + rij[0]) < 1e-9 && fabs(rji[1] + rij[1]) < 1e-9 &&
+                    fabs(rji[2] + rij[2]) < 1e-9) {
+                    back = u;
+                    break;
+                }
+            }
+            const double* pij = p + 3 * (size_t)t;
+            for (int c = 0; c < 3; ++c) f[c] += pij[c];
+            if (back >= 0) {
+                const double* pji = p + 3 * (size_t)back;
+                for (int c = 0; c < 3; ++c) f[c] -= pji[c];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) w[3 * a + b] += rij[a] * pji[b];
+            }
+        }
+        if (F) memcpy(F + 3 * (size_t)s, f, sizeof(f));
+        if (W) memcpy(W + 9 * (size_t)s, w, sizeof(w));
+    }
+    free(p);
+    free(Ua);
+    free(need);
+    nlist_free(&L);
+    return ORC_OK;
+}
+
 /* Heat current J = sum_i W_i . v_i (Eq. 7), J^a = sum_b W_i^{ab} v_i^b. */
 void orc_heat_current(int n, const double* W, const double* v, double* J)
 {

@@ -39,6 +39,8 @@ int orc_efv(const orc_hyper* h, const double* z, int n, const double* box, const
             double* W);
 int orc_efv_brute(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, double* U,
                   double* F, double* W);
+int orc_efv_sample(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, int n_sample,
+                   const int* idx, double* U, double* F, double* W);
 int orc_site(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, double* q,
              double* G, double* x);
 void orc_heat_current(int n, const double* W, const double* v, double* J);

@@ -80,6 +80,7 @@ def _load():
             "orc_efv": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, _D, _D]),
             "orc_efv_brute": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, _D, _D]),
             "orc_site": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, _D, _D]),
+            "orc_efv_sample": (C.c_int, [_H, _D, C.c_int, _D, _D, C.c_int, _I, _D, _D, _D]),
             "orc_heat_current": (None, [C.c_int, _D, _D, _D]),
             "orc_md": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, _D, _D]),
             "orc_loss": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D]),
@@ -185,6 +186,21 @@ def efv(h: NepHyper, z, pos, box, brute: bool = False):
     W = np.zeros((n, 3, 3))
     fn = _load().orc_efv_brute if brute else _load().orc_efv
     _check(fn(C.byref(h.c()), _d(z), n, _d(box), _d(pos), _d(U), _d(F), _d(W)), "efv")
+    return U, F, W
+
+
+def efv_sample(h: NepHyper, z, pos, box, idx):
+    """U, F, W of the atoms in idx only (same definitions as efv)."""
+    z = _f64(z)
+    pos = _f64(pos, (-1, 3))
+    box = _f64(box, (3, 3))
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    k = idx.size
+    U = np.zeros(k)
+    F = np.zeros((k, 3))
+    W = np.zeros((k, 3, 3))
+    _check(_load().orc_efv_sample(C.byref(h.c()), _d(z), pos.shape[0], _d(box), _d(pos), k, idx.ctypes.data_as(_I),
+                                  _d(U), _d(F), _d(W)), "efv_sample")
     return U, F, W
 
 

@@ -1,0 +1,160 @@
+// nep_force.cu -- the FP32 force path: site energies + partial forces, then
+// force / per-atom virial assembly, and deterministic FP64 reductions.
+//
+// Pass A (k_site): one thread per atom runs the descriptor sums, the network
+// and the partial forces dU_i/dr_ij of all its pairs (nep_site.cuh); the
+// parameter vector sits in shared memory where every lane reads the same
+// word (broadcast).  Partial forces go to pf[k][c][i] (coalesced per slot).
+// Pass B (k_assemble): one thread per atom gathers its own p_ij and the
+// neighbours' p_ji through the reverse-pair index: F_i = sum_j (p_ij - p_ji)
+// and W_i = sum_j r_ij (x) p_ji (Eqs. 4-6).  In MD mode the same pass applies
+// the second velocity-Verlet half kick and accumulates E_kin and the heat
+// current J = sum_i W_i . v_i (Eq. 7) without storing W.
+// Totals are summed per block in FP64 and then by one block in a fixed order,
+// so every result is bitwise reproducible run to run.
+#include <cstdio>
+
+#include "nep_site.cuh"
+
+namespace nep {
+
+namespace {
+
+constexpr int kSiteThreads = 128;
+constexpr int kAsmThreads = 128;
+
+__global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const int* __restrict__ count,
+                                                       const int* __restrict__ nbr, const float* __restrict__ xh,
+                                                       const float* __restrict__ xl, Box box,
+                                                       const float* __restrict__ z, int n_par, SiteParams P,
+                                                       float* __restrict__ pf, double* __restrict__ e_atom,
+                                                       double* __restrict__ e_partials, unsigned* err)
+{
+    extern __shared__ float s_w[];
+    for (int t = threadIdx.x; t < n_par; t += blockDim.x) s_w[t] = z[t];
+    __syncthreads();
+    P.w = s_w;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double e[1] = {0.0};
+    // every lane runs the site function (the warp walks neighbour ranks in
+    // step); lanes past the last atom see no neighbours and store nothing
+    const bool active = i < n;
+    float uh, ul;
+    site_partial_forces(active ? i : 0, active, n, m_cap, count, nbr, xh, xl, box, P, pf, uh, ul);
+    if (active) {
+        e[0] = (double)uh + (double)ul;
+        if (e_atom) e_atom[i] = e[0];
+        if (!isfinite(uh)) atomicOr(err, kErrNonFinite);
+    }
+    block_sum_store<1>(e, e_partials + blockIdx.x);
+}
+
+// Totals per block: [0..8] virial, and in MD mode [9] E_kin, [10..12] J.
+template <bool MD>
+__global__ void __launch_bounds__(kAsmThreads) k_assemble(int n, int m_cap, float rc2max, const int* __restrict__ count,
+                                                          const int* __restrict__ nbr, const int* __restrict__ rev,
+                                                          const float* __restrict__ xh, const float* __restrict__ xl,
+                                                          Box box, const float* __restrict__ pf,
+                                                          float* __restrict__ force, float* __restrict__ virial_atom,
+                                                          double* __restrict__ partials, unsigned* err,
+                                                          double* __restrict__ vel, double hdtm, double kef)
+{
+    constexpr int K = MD ? 13 : 9;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    if (i < n) {
+        float F[3], W[9];
+        assemble_atom(i, n, m_cap, rc2max, count, nbr, rev, xh, xl, box, pf, F, W);
+        if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) atomicOr(err, kErrNonFinite);
+        if (force) {
+            force[i] = F[0];
+            force[(size_t)n + i] = F[1];
+            force[(size_t)2 * n + i] = F[2];
+        }
+        if (virial_atom)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) virial_atom[(size_t)c * n + i] = W[c];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] = (double)W[c];
+        if constexpr (MD) {
+            double v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = vel[(size_t)c * n + i] + hdtm * (double)F[c];
+                vel[(size_t)c * n + i] = v[c];
+            }
+            acc[9] = kef * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            // J^a = sum_b W^{ab} v^b, FP32 products accumulated in FP64
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                acc[10 + a] = (double)(W[3 * a] * (float)v[0]) + (double)(W[3 * a + 1] * (float)v[1]) +
+                              (double)(W[3 * a + 2] * (float)v[2]);
+        }
+    }
+    block_sum_store<K>(acc, partials + (size_t)blockIdx.x * K);
+}
+
+// out[k] = sum_b partials[b * ncomp + k]: one warp per component, each lane
+// summing a fixed stride of blocks, then a fixed shuffle tree (deterministic).
+__global__ void k_reduce(const double* __restrict__ partials, int nblocks, int ncomp, double* __restrict__ out)
+{
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= ncomp) return;
+    double s = 0.0;
+    for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * ncomp + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[k] = s;
+}
+
+inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, double* e_partials,
+                               unsigned* d_err, cudaStream_t st, int& nblocks)
+{
+    SiteParams P;
+    P.w = nullptr;
+    P.n_neu = a.n_neu;
+    P.rcR = a.rcR;
+    P.rcA = a.rcA;
+    P.rcR2 = a.rcR * a.rcR;
+    P.rcA2 = a.rcA * a.rcA;
+    P.inv_rcR = 1.f / a.rcR;
+    P.inv_rcA = 1.f / a.rcA;
+    const int n_par = (kNdes + 2) * a.n_neu + 1;
+    nblocks = blocks_for(n, kSiteThreads);
+    k_site<<<nblocks, kSiteThreads, n_par * sizeof(float), st>>>(n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box,
+                                                                  a.z, n_par, P, nl.pf, e_atom, e_partials, d_err);
+    return cuda_fail(cudaGetLastError(), "site kernel");
+}
+
+int launch_assemble(const AssembleArgs& a, NeighborList& nl, int n, float* force, float* virial_atom,
+                    double* partials, unsigned* d_err, cudaStream_t st, int& nblocks, int& ncomp)
+{
+    nblocks = blocks_for(n, kAsmThreads);
+    const float rc2 = a.rc_max * a.rc_max;
+    if (a.vel) {
+        ncomp = 13;
+        k_assemble<true><<<nblocks, kAsmThreads, 0, st>>>(n, nl.m_cap, rc2, nl.count, nl.nbr, nl.rev, nl.xh, nl.xl,
+                                                          a.box, nl.pf, force, virial_atom, partials, d_err, a.vel,
+                                                          a.half_dt_over_m, a.ke_factor);
+    } else {
+        ncomp = 9;
+        k_assemble<false><<<nblocks, kAsmThreads, 0, st>>>(n, nl.m_cap, rc2, nl.count, nl.nbr, nl.rev, nl.xh, nl.xl,
+                                                           a.box, nl.pf, force, virial_atom, partials, d_err,
+                                                           nullptr, 0.0, 0.0);
+    }
+    return cuda_fail(cudaGetLastError(), "assemble kernel");
+}
+
+int launch_reduce(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st)
+{
+    k_reduce<<<1, 32 * ncomp, 0, st>>>(partials, nblocks, ncomp, out);
+    return cuda_fail(cudaGetLastError(), "reduce kernel");
+}
+
+}  // namespace nep

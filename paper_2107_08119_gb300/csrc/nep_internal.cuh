@@ -1,0 +1,243 @@
+// nep_internal.cuh -- shared definitions of the sm_103a NEP library.
+//
+// Data layout in device memory (n atoms, M = neighbour capacity per atom):
+//   positions        FP64 [3][n] (caller) + FP32 hi/lo split xh, xl [3][n]
+//   neighbour list   int32 nbr[M][n] = j | image_code << 24, count[n]
+//                    int32 rev[M][n] = slot of i in j's list (reverse pair)
+//   partial forces   FP32 pf[M][3][n] = dU_i/dr_ij (Eq. 23), slot-major
+//   forces           FP32 [3][n], per-atom virials FP32 [9][n]
+// Slot-major layouts make the per-atom loops of a warp read consecutive
+// addresses at every slot.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nep.h"
+
+#ifdef __CUDA_ARCH__
+#define NEP_LDG(p) __ldg(p)
+#else
+#define NEP_LDG(p) (*(p))
+#endif
+
+namespace nep {
+
+__host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+
+// ---------------------------------------------------------------- sizes
+constexpr int kNR = 8;               // radial orders n = 0..7
+constexpr int kNA = 6;               // angular radial orders n = 0..5
+constexpr int kLmax = 4;             // Legendre orders l = 1..4
+constexpr int kLM = 24;              // real harmonics with 1 <= l <= 4: 3+5+7+9
+constexpr int kNdes = kNR + kNA * kLmax;  // 32
+constexpr int kMaxNeu = 64;
+constexpr int kMaxAtoms = (1 << 24) - 1;
+constexpr int kImgCenter = 62;       // image code of the zero shift
+
+// device error word bits
+enum : unsigned {
+    kErrOverflow = 1u,
+    kErrNonFinite = 2u,
+    kErrReverse = 4u,
+    kErrTimeout = 8u,
+};
+
+// Orthorhombic periodic box; lengths split into FP32 hi + lo parts so that a
+// pair vector can be formed to FP32 rounding from hi/lo positions.
+struct Box {
+    double L[3];
+    float Lh[3];
+    float Ll[3];
+    int nc[3];      // cells per direction (0 when the brute-force list is used)
+    int img[3];     // largest |image shift| a pair can need per direction
+};
+
+// Image code of shift (sx, sy, sz), each in [-2, 2].
+__host__ __device__ __forceinline__ int image_code(int sx, int sy, int sz)
+{
+    return (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2);
+}
+
+__host__ __device__ __forceinline__ void image_shift(int code, int& sx, int& sy, int& sz)
+{
+    sx = code / 25 - 2;
+    sy = (code / 5) % 5 - 2;
+    sz = code % 5 - 2;
+}
+
+// r = (x_a + s L) - x_b from hi/lo parts.  The box length is combined first
+// with whichever atom sits near the far face (b when s > 0, a when s < 0), so
+// that subtraction is exact (Sterbenz) and only the final small difference
+// rounds; adding L to the atom near the origin would round at ulp(L).
+__host__ __device__ __forceinline__ float diff1(float ah, float al, float bh, float bl, float s, float Lh, float Ll)
+{
+    const float hi = (s > 0.f) ? ah - fmaf(-s, Lh, bh) : fmaf(s, Lh, ah) - bh;
+    const float lo = fmaf(s, Ll, al - bl);
+    return hi + lo;
+}
+
+// Pair vector r_ij = x_j + shift(code) - x_i, evaluated in a canonical
+// orientation so that r_ji == -r_ij bit for bit.  Both atoms' hi/lo
+// coordinates are passed in.
+__host__ __device__ __forceinline__ void pair_vector(int i, int j, int code, const float (&hi)[3], const float (&li)[3],
+                                            const float (&hj)[3], const float (&lj)[3], const Box& b, float& rx,
+                                            float& ry, float& rz)
+{
+    int sx, sy, sz;
+    image_shift(code, sx, sy, sz);
+    const bool fwd = (j > i) || (j == i && code < kImgCenter);
+    const float sg = fwd ? 1.f : -1.f;
+    const float fx = fwd ? (float)sx : (float)(-sx);
+    const float fy = fwd ? (float)sy : (float)(-sy);
+    const float fz = fwd ? (float)sz : (float)(-sz);
+    // a = the atom whose image is shifted, b = the origin atom
+    rx = sg * diff1(fwd ? hj[0] : hi[0], fwd ? lj[0] : li[0], fwd ? hi[0] : hj[0], fwd ? li[0] : lj[0], fx, b.Lh[0],
+                    b.Ll[0]);
+    ry = sg * diff1(fwd ? hj[1] : hi[1], fwd ? lj[1] : li[1], fwd ? hi[1] : hj[1], fwd ? li[1] : lj[1], fy, b.Lh[1],
+                    b.Ll[1]);
+    rz = sg * diff1(fwd ? hj[2] : hi[2], fwd ? lj[2] : li[2], fwd ? hi[2] : hj[2], fwd ? li[2] : lj[2], fz, b.Lh[2],
+                    b.Ll[2]);
+}
+
+__host__ __device__ __forceinline__ void load_pos(const float* __restrict__ xh, const float* __restrict__ xl, int n, int i,
+                                         float (&h)[3], float (&l)[3])
+{
+    h[0] = NEP_LDG(xh + i);
+    h[1] = NEP_LDG(xh + n + i);
+    h[2] = NEP_LDG(xh + 2 * n + i);
+    l[0] = NEP_LDG(xl + i);
+    l[1] = NEP_LDG(xl + n + i);
+    l[2] = NEP_LDG(xl + 2 * n + i);
+}
+
+// Split an FP64 value into FP32 hi + lo.
+__host__ __device__ __forceinline__ void split_hilo(double x, float& h, float& l)
+{
+    h = (float)x;
+    l = (float)(x - (double)h);
+}
+
+// Block-wide sum of K doubles; thread 0 writes out[k].  blockDim.x must be a
+// multiple of 32 and at most 1024.
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double* __restrict__ out)
+{
+    __shared__ double red[32][K];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = lane < nw ? red[lane][k] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) out[k] = s;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- workspace
+struct NeighborList {
+    int n_cap = 0;       // atoms the buffers hold
+    int m_cap = 0;       // neighbour slots per atom
+    int ncell_cap = 0;
+    int* count = nullptr;
+    int* nbr = nullptr;
+    int* rev = nullptr;
+    float* pf = nullptr;
+    float* xh = nullptr;
+    float* xl = nullptr;
+    int* atom_cell = nullptr;
+    int* cell_count = nullptr;
+    int* cell_start = nullptr;
+    int* cell_fill = nullptr;
+    int* cell_atoms = nullptr;
+};
+
+struct Workspace {
+    NeighborList nl;
+    double* partials = nullptr;  // per-block FP64 partial sums
+    int partial_cap = 0;         // doubles
+    float* force = nullptr;      // [3][n] FP32 (MD and internal use)
+    int force_cap = 0;
+};
+
+// host-side helpers (nep_api.cu)
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_partials);
+void free_workspace(Workspace& ws);
+int setup_box(const double* box9, double r_list, Box& b);
+
+// neighbour list (nep_neighbor.cu)
+// mode: build from positions `pos` (FP64 [3][n]); when wrap_in_place is true
+// the wrapped positions are written back to pos and to x_ref (if non-null).
+int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool wrap_in_place, double* x_ref,
+                        float r_list, unsigned* d_err, const unsigned* d_gate, cudaStream_t st);
+
+// force path (nep_force.cu)
+struct ForceArgs {
+    const float* z;          // parameters on the device
+    int n_neu;
+    float rcR, rcA;
+    Box box;
+};
+int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, double* e_partials,
+                               unsigned* d_err, cudaStream_t st, int& nblocks);
+struct AssembleArgs {
+    float rc_max;
+    Box box;
+    // MD extras (used when vel != nullptr)
+    double* vel;
+    double half_dt_over_m;   // dt/2 / (m * unit)
+    double ke_factor;        // 0.5 m * unit
+    bool heat;
+};
+int launch_assemble(const AssembleArgs& a, NeighborList& nl, int n, float* force, float* virial_atom,
+                    double* partials, unsigned* d_err, cudaStream_t st, int& nblocks, int& ncomp);
+int launch_reduce(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st);
+
+}  // namespace nep
+
+namespace nep {
+// CUDA-event pairs around kernel launches (enabled on demand).
+struct Profiler {
+    bool on = false;
+    struct Slot {
+        cudaEvent_t a = nullptr, b = nullptr;
+        int kind = 0;
+    };
+    Slot* slots = nullptr;
+    int cap = 0, used = 0;
+    // returns the slot to bracket a launch of `kind`, or nullptr when off/full
+    Slot* begin(int kind, cudaStream_t st);
+    void end(Slot* s, cudaStream_t st);
+    int read(double* ms, long long* cnt);  // ms[2], cnt[2]; synchronises
+    void release();
+};
+}  // namespace nep
+
+struct nep_model {
+    nep_hyper hp;
+    nep::Profiler prof;
+    int n_des = 0;
+    int n_par = 0;
+    float* d_z = nullptr;
+    unsigned* d_err = nullptr;   // latched device error bits
+    double* d_red = nullptr;     // reduction outputs (32 doubles)
+    nep::Workspace ws;
+};
+
+namespace nep {
+// status from latched device error bits
+int status_from_bits(unsigned bits);
+}

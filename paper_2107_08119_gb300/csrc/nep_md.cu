@@ -1,0 +1,270 @@
+// nep_md.cu -- NVE velocity-Verlet molecular dynamics on the NEP force path.
+//
+// One step is a fixed sequence of kernels on the caller's stream, with no
+// host round trip:
+//   k_kick_drift   v += dt/2 F/m; x += dt v (FP64); FP32 hi/lo split of x;
+//                  largest squared displacement since the last list build
+//   k_decide       gate = (max displacement > skin/2) or a pending rebuild
+//   list build     wrap, bin, Verlet list, reverse index (gated: the kernels
+//                  return at once when the gate is zero)
+//   k_site         site energies and partial forces
+//   k_assemble     forces, second half kick, E_kin, virial and heat current
+//                  J = sum_i W_i . v_i (Eq. 7), per-block FP64 sums
+//   k_reduce       block sums in a fixed order
+//   k_md_finish    thermo row and J of this step
+#include <cmath>
+#include <new>
+
+#include "nep_internal.cuh"
+
+// 1 amu A^2 / fs^2 expressed in eV (CODATA 2018 atomic mass constant and
+// elementary charge).
+static constexpr double kAmuA2Fs2InEv = 1.66053906660e-27 * 1.0e-20 / 1.0e-30 / 1.602176634e-19;
+
+namespace nep {
+namespace {
+
+// control words on the device
+enum { kCtlDisp = 0, kCtlGate = 1, kCtlPending = 2, kCtlStep = 3, kCtlWords = 4 };
+
+__global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__ v, const float* __restrict__ F,
+                             double hdtm, double dt, float* __restrict__ xh, float* __restrict__ xl,
+                             const double* __restrict__ x_ref, unsigned* __restrict__ ctl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float d2 = 0.f;
+    if (i < n) {
+        double dd = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t o = (size_t)c * n + i;
+            const double vc = v[o] + hdtm * (double)F[o];
+            const double xc = x[o] + dt * vc;
+            v[o] = vc;
+            x[o] = xc;
+            float h, l;
+            split_hilo(xc, h, l);
+            xh[o] = h;
+            xl[o] = l;
+            const double d = xc - x_ref[o];
+            dd += d * d;
+        }
+        d2 = (float)dd;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+    // non-negative floats order like their bit patterns
+    if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(ctl + kCtlDisp, __float_as_uint(d2));
+}
+
+__global__ void k_decide(unsigned* __restrict__ ctl, float thresh2, unsigned long long* __restrict__ rebuilds)
+{
+    const bool go = ctl[kCtlPending] != 0u || __uint_as_float(ctl[kCtlDisp]) > thresh2;
+    ctl[kCtlGate] = go ? 1u : 0u;
+    ctl[kCtlDisp] = 0u;
+    ctl[kCtlPending] = 0u;
+    if (go) *rebuilds += 1ull;
+}
+
+__global__ void k_md_finish(const double* __restrict__ red, double* __restrict__ thermo, double* __restrict__ heat,
+                            unsigned* __restrict__ ctl)
+{
+    // red: [0] E_pot, [1..9] W (row-major), [10] E_kin, [11..13] J
+    const unsigned s = ctl[kCtlStep];
+    if (threadIdx.x == 0) {
+        if (thermo) {
+            double* t = thermo + (size_t)s * NEP_THERMO_COLS;
+            t[0] = red[0];
+            t[1] = red[10];
+            t[2] = red[1];  // xx
+            t[3] = red[5];  // yy
+            t[4] = red[9];  // zz
+            t[5] = red[2];  // xy
+            t[6] = red[6];  // yz
+            t[7] = red[7];  // zx
+        }
+        if (heat) {
+            heat[(size_t)s * 3 + 0] = red[11];
+            heat[(size_t)s * 3 + 1] = red[12];
+            heat[(size_t)s * 3 + 2] = red[13];
+        }
+        ctl[kCtlStep] = s + 1u;
+    }
+}
+
+inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+}  // namespace nep
+
+using namespace nep;
+
+struct nep_md {
+    nep_model* m = nullptr;
+    int n = 0;
+    Box box;
+    double mass = 0.0;
+    float r_list = 0.f;
+    float skin = 0.f;
+    Workspace ws;
+    double* x_ref = nullptr;
+    unsigned* ctl = nullptr;
+    unsigned long long* rebuilds = nullptr;
+    double* red = nullptr;
+    bool need_init = true;
+};
+
+extern "C" {
+
+int nep_md_create(nep_model* m, int n, const double* box9, double mass, nep_md** out)
+{
+    if (!m || !out || n < 1 || n > kMaxAtoms || !(mass > 0.0)) {
+        set_error("nep_md_create: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    *out = nullptr;
+    const double rmax = (m->hp.rc_R > m->hp.rc_A ? m->hp.rc_R : m->hp.rc_A) + m->hp.skin;
+    nep_md* md = new (std::nothrow) nep_md();
+    if (!md) {
+        set_error("nep_md_create: host allocation failed");
+        return NEP_ERR_OOM;
+    }
+    int rc = setup_box(box9, rmax, md->box);
+    if (rc) {
+        delete md;
+        return rc;
+    }
+    md->m = m;
+    md->n = n;
+    md->mass = mass;
+    md->r_list = (float)rmax;
+    md->skin = (float)m->hp.skin;
+    const int ncell = md->box.nc[0] * md->box.nc[1] * md->box.nc[2];
+    const int nb = blocks_for(n, 128);
+    if ((rc = ensure_workspace(md->ws, n, m->hp.max_neighbors, ncell, nb))) {
+        nep_md_destroy(md);
+        return rc;
+    }
+    cudaError_t e = cudaMalloc((void**)&md->x_ref, sizeof(double) * 3 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&md->ctl, sizeof(unsigned) * kCtlWords);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&md->rebuilds, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&md->red, sizeof(double) * 32);
+    if (e == cudaSuccess) e = cudaMemset(md->ctl, 0, sizeof(unsigned) * kCtlWords);
+    if (e == cudaSuccess) e = cudaMemset(md->rebuilds, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("nep_md_create: %s", cudaGetErrorString(e));
+        nep_md_destroy(md);
+        return NEP_ERR_OOM;
+    }
+    *out = md;
+    return NEP_OK;
+}
+
+int nep_md_destroy(nep_md* md)
+{
+    if (!md) return NEP_OK;
+    cudaDeviceSynchronize();
+    free_workspace(md->ws);
+    if (md->x_ref) cudaFree(md->x_ref);
+    if (md->ctl) cudaFree(md->ctl);
+    if (md->rebuilds) cudaFree(md->rebuilds);
+    if (md->red) cudaFree(md->red);
+    delete md;
+    return NEP_OK;
+}
+
+int nep_md_invalidate(nep_md* md)
+{
+    if (!md) {
+        set_error("nep_md_invalidate: NULL handle");
+        return NEP_ERR_ARG;
+    }
+    md->need_init = true;
+    return NEP_OK;
+}
+
+int nep_md_rebuild_count(nep_md* md, long long* count, void* stream)
+{
+    if (!md || !count) {
+        set_error("nep_md_rebuild_count: NULL argument");
+        return NEP_ERR_ARG;
+    }
+    int rc = cuda_fail(cudaStreamSynchronize((cudaStream_t)stream), "stream synchronise");
+    if (rc) return rc;
+    unsigned long long c = 0;
+    rc = cuda_fail(cudaMemcpy(&c, md->rebuilds, sizeof(c), cudaMemcpyDeviceToHost), "read rebuild count");
+    *count = (long long)c;
+    return rc;
+}
+
+const float* nep_md_forces(const nep_md* md) { return md ? md->ws.force : nullptr; }
+
+int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, double* thermo, double* heat,
+                void* stream)
+{
+    if (!md || !pos || !vel || n_steps < 0 || !(dt > 0.0)) {
+        set_error("nep_md_step: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    nep_model* m = md->m;
+    const int n = md->n;
+    NeighborList& nl = md->ws.nl;
+    const int nb = blocks_for(n, 128);
+    double* part_e = md->ws.partials;
+    double* part_a = md->ws.partials + ((nb + 7) / 8) * 8;
+    ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, md->box};
+    const double rmax = m->hp.rc_R > m->hp.rc_A ? m->hp.rc_R : m->hp.rc_A;
+    const double conv = kAmuA2Fs2InEv;
+    int rc;
+    const unsigned* gate = md->ctl + kCtlGate;
+
+    if (md->need_init) {
+        // forces of the starting configuration (list built unconditionally)
+        if ((rc = build_neighbor_list(nl, md->box, n, pos, true, md->x_ref, md->r_list, m->d_err, nullptr, st)))
+            return rc;
+        int b1 = 0, b2 = 0, c2 = 0;
+        if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
+        AssembleArgs aa{};
+        aa.rc_max = (float)rmax;
+        aa.box = md->box;
+        aa.vel = nullptr;
+        if ((rc = launch_assemble(aa, nl, n, md->ws.force, nullptr, part_a, m->d_err, st, b2, c2))) return rc;
+        if ((rc = cuda_fail(cudaMemsetAsync(md->ctl, 0, sizeof(unsigned) * kCtlWords, st), "cudaMemsetAsync")))
+            return rc;
+        md->need_init = false;
+    }
+    if ((rc = cuda_fail(cudaMemsetAsync(md->ctl + kCtlStep, 0, sizeof(unsigned), st), "cudaMemsetAsync"))) return rc;
+
+    const double hdtm = 0.5 * dt / (md->mass * conv);
+    const float thresh = 0.5f * md->skin;
+    for (int s = 0; s < n_steps; ++s) {
+        k_kick_drift<<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, md->ws.force, hdtm, dt, nl.xh, nl.xl, md->x_ref,
+                                                         md->ctl);
+        k_decide<<<1, 1, 0, st>>>(md->ctl, thresh * thresh, md->rebuilds);
+        if ((rc = build_neighbor_list(nl, md->box, n, pos, true, md->x_ref, md->r_list, m->d_err, gate, st)))
+            return rc;
+        int b1 = 0, b2 = 0, c2 = 0;
+        Profiler::Slot* ps = m->prof.begin(0, st);
+        if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
+        m->prof.end(ps, st);
+        AssembleArgs aa{};
+        aa.rc_max = (float)rmax;
+        aa.box = md->box;
+        aa.vel = vel;
+        aa.half_dt_over_m = hdtm;
+        aa.ke_factor = 0.5 * md->mass * conv;
+        aa.heat = heat != nullptr;
+        ps = m->prof.begin(1, st);
+        if ((rc = launch_assemble(aa, nl, n, md->ws.force, nullptr, part_a, m->d_err, st, b2, c2))) return rc;
+        m->prof.end(ps, st);
+        if ((rc = launch_reduce(part_e, b1, 1, md->red, st))) return rc;
+        if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
+        k_md_finish<<<1, 32, 0, st>>>(md->red, thermo, heat, md->ctl);
+        if ((rc = cuda_fail(cudaGetLastError(), "md step kernels"))) return rc;
+    }
+    return NEP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,461 @@
+// nep_site.cuh -- per-atom NEP arithmetic of the force path, in FP32.
+//
+// For one atom i with Verlet-list slots k:
+//   radial descriptors   q_n = sum_j g_n(r_ij)                     (Eq. 12)
+//   angular descriptors  q_nl = sum_{j,k} g_n g_n P_l(cos theta)   (Eq. 13)
+//     evaluated exactly through the addition theorem (Eqs. 17-18 with
+//     n = n'): P_l(u.v) = sum_m c_lm Z_lm(u) Z_lm(v) for the real solid
+//     harmonics Z_lm below, so q_nl = sum_m c_lm S_nlm^2 with
+//     S_nlm = sum_j g_n(r_ij) Z_lm(rhat_ij): O(M) instead of O(M^2);
+//   g_n = (T_n(x) + 1)/2 f_c(r), x = 2 (r/r_c - 1)^2 - 1            (Eq. 14)
+//   f_c = (1 + cos(pi r / r_c))/2                                  (Eq. 15)
+//   network  x_mu = tanh(sum_nu w1 q - b1), U = sum_mu w2 x - b2     (Eqs. 21-22)
+//   G_nu = dU/dq_nu = sum_mu w2_mu (1 - x_mu^2) w1_mu,nu
+//   partial force dU_i/dr_ij = sum_nu G_nu dq_nu/dr_ij               (Eqs. 23-25)
+//     radial: G_n g_n'(r) rhat; angular: sum_nlm 2 c_lm G_nl S_nlm grad(g_n Z_lm),
+//     grad(g Z(rhat)) = g' Z rhat + g (grad_u Z - rhat (rhat . grad_u Z)) / r.
+// Chebyshev T_n and U_n come from the recurrences of App. A (Eqs. A1-A3).
+//
+// The functions are __host__ __device__ so the same code can be exercised
+// on the CPU; on the device the weights pointer refers to shared memory.
+#pragma once
+
+#include <math.h>
+
+#include "nep_internal.cuh"
+
+namespace nep {
+
+__host__ __device__ __forceinline__ void sincospi_f(float x, float* s, float* c)
+{
+#ifdef __CUDA_ARCH__
+    sincospif(x, s, c);
+#else
+    *s = (float)sin(3.14159265358979323846 * (double)x);
+    *c = (float)cos(3.14159265358979323846 * (double)x);
+#endif
+}
+
+// d / rc from d * (1/rc) with one Newton correction: the rounded reciprocal
+// of a cutoff such as 5 A is not exact in FP32, and the plain product would
+// bias every radial function the same way.
+__host__ __device__ __forceinline__ float div_rc(float d, float rc, float inv_rc)
+{
+    const float q0 = d * inv_rc;
+    return fmaf(fmaf(-q0, rc, d), inv_rc, q0);
+}
+
+// g_n(d), n = 0..N-1, for d < rc.
+template <int N>
+__host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_rc, float (&g)[N])
+{
+    float s, c;
+    const float dr = div_rc(d, rc, inv_rc);
+    sincospi_f(dr, &s, &c);
+    const float fc = 0.5f * (1.f + c);
+    const float t = dr - 1.f;
+    const float x = fmaf(2.f * t, t, -1.f);
+    float Tm = 1.f, T = x;  // T_{n-1}, T_n
+    const float hfc = 0.5f * fc;
+    g[0] = fc;
+    if (N > 1) g[1] = fmaf(hfc, x, hfc);
+#pragma unroll
+    for (int n = 2; n < N; ++n) {
+        const float Tn = fmaf(2.f * x, T, -Tm);
+        Tm = T;
+        T = Tn;
+        g[n] = fmaf(hfc, Tn, hfc);
+    }
+}
+
+// g_n(d) and dg_n/dd, n = 0..N-1, for d < rc.
+template <int N>
+__host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float inv_rc, float (&g)[N], float (&dg)[N])
+{
+    float s, c;
+    const float dr = div_rc(d, rc, inv_rc);
+    sincospi_f(dr, &s, &c);
+    const float fc = 0.5f * (1.f + c);
+    const float dfc = -0.5f * 3.14159265358979f * inv_rc * s;
+    const float t = dr - 1.f;
+    const float x = fmaf(2.f * t, t, -1.f);
+    const float dxdr = 4.f * t * inv_rc;
+    const float hfc = 0.5f * fc, hdfc = 0.5f * dfc;
+    const float a = hfc * dxdr;  // (1/2) f_c dx/dr
+    float Tm = 1.f, T = x;       // T_{n-1}, T_n
+    float Um = 1.f, U = 2.f * x; // U_{n-2}, U_{n-1} when at order n
+    g[0] = fc;
+    dg[0] = dfc;
+    if (N > 1) {
+        g[1] = fmaf(hfc, x, hfc);
+        dg[1] = fmaf(a, 1.f, fmaf(hdfc, x, hdfc));  // dT_1/dx = 1 * U_0 = 1
+    }
+#pragma unroll
+    for (int n = 2; n < N; ++n) {
+        const float Tn = fmaf(2.f * x, T, -Tm);
+        Tm = T;
+        T = Tn;
+        // dT_n/dx = n U_{n-1}; U at this point holds U_{n-1}
+        g[n] = fmaf(hfc, Tn, hfc);
+        dg[n] = fmaf(a * (float)n, U, fmaf(hdfc, Tn, hdfc));
+        const float Un = fmaf(2.f * x, U, -Um);
+        Um = U;
+        U = Un;
+    }
+}
+
+// The 24 real solid-harmonic polynomials Z_lm(u) with 1 <= l <= 4 (u a unit
+// vector), listed once as T(lm, Z, dZ/dux, dZ/duy, dZ/duz), and the
+// addition-theorem weights c_lm with sum_m c_lm Z_lm(u) Z_lm(v) = P_l(u . v)
+// (Eqs. 17-18: c_lm = 4 pi/(2l+1) times the squared normalisation of the
+// real spherical harmonic).  Every c_lm is a dyadic rational, exact in FP32.
+// The gradient columns are those of the polynomial extension off the sphere;
+// callers project them onto the tangent plane.  Expects the locals of
+// NEP_SH_LOCALS in scope.
+#define NEP_SH_LOCALS(x, y, z)                                                  \
+    const float x2 = x * x, y2 = y * y, z2 = z * z;                             \
+    const float xy = x * y, yz = y * z, xz = x * z;                             \
+    const float x2my2 = x2 - y2;                                                \
+    const float a5 = 5.f * z2 - 1.f, a7 = 7.f * z2 - 1.f, b7 = 7.f * z2 - 3.f; \
+    const float c21 = 21.f * z2 - 3.f;                                          \
+    (void)x2my2; (void)a5; (void)a7; (void)b7; (void)c21;
+
+#define NEP_SH_TABLE(T)                                                                             \
+    /* l = 1 */                                                                                     \
+    T(0, x, 1.f, 0.f, 0.f)                                                                          \
+    T(1, y, 0.f, 1.f, 0.f)                                                                          \
+    T(2, z, 0.f, 0.f, 1.f)                                                                          \
+    /* l = 2 */                                                                                     \
+    T(3, xy, y, x, 0.f)                                                                             \
+    T(4, yz, 0.f, z, y)                                                                             \
+    T(5, xz, z, 0.f, x)                                                                             \
+    T(6, 3.f * z2 - 1.f, 0.f, 0.f, 6.f * z)                                                         \
+    T(7, x2my2, 2.f * x, -2.f * y, 0.f)                                                             \
+    /* l = 3 */                                                                                     \
+    T(8, y * (3.f * x2 - y2), 6.f * xy, 3.f * x2my2, 0.f)                                           \
+    T(9, xy * z, yz, xz, xy)                                                                        \
+    T(10, y * a5, 0.f, a5, 10.f * yz)                                                               \
+    T(11, z * (5.f * z2 - 3.f), 0.f, 0.f, 15.f * z2 - 3.f)                                          \
+    T(12, x * a5, a5, 0.f, 10.f * xz)                                                               \
+    T(13, z * x2my2, 2.f * xz, -2.f * yz, x2my2)                                                    \
+    T(14, x * (x2 - 3.f * y2), 3.f * x2my2, -6.f * xy, 0.f)                                         \
+    /* l = 4 */                                                                                     \
+    T(15, xy * x2my2, y * (3.f * x2 - y2), x * (x2 - 3.f * y2), 0.f)                                \
+    T(16, yz * (3.f * x2 - y2), 6.f * xy * z, 3.f * z * x2my2, y * (3.f * x2 - y2))                  \
+    T(17, xy * a7, y * a7, x * a7, 14.f * xy * z)                                                   \
+    T(18, yz * b7, 0.f, z * b7, y * c21)                                                            \
+    T(19, z2 * (35.f * z2 - 30.f) + 3.f, 0.f, 0.f, z * (140.f * z2 - 60.f))                         \
+    T(20, xz * b7, z * b7, 0.f, x * c21)                                                            \
+    T(21, x2my2 * a7, 2.f * x * a7, -2.f * y * a7, 14.f * z * x2my2)                                \
+    T(22, xz * (x2 - 3.f * y2), 3.f * z * x2my2, -6.f * xy * z, x * (x2 - 3.f * y2))                 \
+    T(23, x2 * (x2 - 3.f * y2) - y2 * (3.f * x2 - y2), 4.f * x * (x2 - 3.f * y2), 4.f * y * (y2 - 3.f * x2), 0.f)
+
+// addition-theorem weights c_lm in the order of NEP_SH_TABLE
+__host__ __device__ __forceinline__ constexpr float sh_c(int lm)
+{
+    constexpr float c[kLM] = {1.f,          1.f,          1.f,                                        // l = 1
+                              3.f,          3.f,          3.f,          0.25f,        0.75f,        // l = 2
+                              0.625f,       15.f,         0.375f,       0.25f,        0.375f,       // l = 3
+                              3.75f,        0.625f,                                                 //
+                              8.75f,        4.375f,       1.25f,        0.625f,       0.015625f,    // l = 4
+                              0.625f,       0.3125f,      4.375f,       0.546875f};                 //
+    return c[lm];
+}
+
+// l of harmonic index lm (0-based l - 1)
+__host__ __device__ __forceinline__ constexpr int sh_l(int lm) { return lm < 3 ? 0 : (lm < 8 ? 1 : (lm < 15 ? 2 : 3)); }
+
+// S[n][lm] += g[n] * Y_lm(u)
+__host__ __device__ __forceinline__ void sh_acc(float (&S)[kNA][kLM], const float (&g)[kNA], int lm, float Y)
+{
+#pragma unroll
+    for (int n = 0; n < kNA; ++n) S[n][lm] = fmaf(g[n], Y, S[n][lm]);
+}
+
+__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float (&g)[kNA],
+                                                  float (&S)[kNA][kLM])
+{
+    NEP_SH_LOCALS(x, y, z)
+#define NEP_T(lm, Yv, gx, gy, gz) sh_acc(S, g, lm, Yv);
+    NEP_SH_TABLE(NEP_T)
+#undef NEP_T
+}
+
+// One harmonic's contribution to the angular partial force:
+//   cg = sum_n A[n][lm] g_n, cd = sum_n A[n][lm] g_n'
+//   B += cd Y, V += cg grad_u Y.
+__host__ __device__ __forceinline__ void sh_term(const float (&A)[kNA][kLM], const float (&g)[kNA],
+                                                 const float (&dg)[kNA], int lm, float Y, float gx, float gy,
+                                                 float gz, float& B, float& Vx, float& Vy, float& Vz)
+{
+    float cg = 0.f, cd = 0.f;
+#pragma unroll
+    for (int n = 0; n < kNA; ++n) {
+        cg = fmaf(A[n][lm], g[n], cg);
+        cd = fmaf(A[n][lm], dg[n], cd);
+    }
+    B = fmaf(cd, Y, B);
+    Vx = fmaf(cg, gx, Vx);
+    Vy = fmaf(cg, gy, Vy);
+    Vz = fmaf(cg, gz, Vz);
+}
+
+__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const float (&A)[kNA][kLM],
+                                                  const float (&g)[kNA], const float (&dg)[kNA], float& B,
+                                                  float& Vx, float& Vy, float& Vz)
+{
+    NEP_SH_LOCALS(x, y, z)
+#define NEP_T(lm, Yv, gx, gy, gz) sh_term(A, g, dg, lm, Yv, gx, gy, gz, B, Vx, Vy, Vz);
+    NEP_SH_TABLE(NEP_T)
+#undef NEP_T
+}
+
+// All 24 harmonics and their (unprojected) gradients.
+__host__ __device__ __forceinline__ void sh_eval(float x, float y, float z, float (&Y)[kLM], float (&dY)[kLM][3])
+{
+    NEP_SH_LOCALS(x, y, z)
+#define NEP_T(lm, Yv, gx, gy, gz) \
+    Y[lm] = Yv;                   \
+    dY[lm][0] = gx;               \
+    dY[lm][1] = gy;               \
+    dY[lm][2] = gz;
+    NEP_SH_TABLE(NEP_T)
+#undef NEP_T
+}
+
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum).
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Network of Eqs. 21-22 and its input gradient.  w points at the parameter
+// vector [w1 (n_neu x 32), b1, w2, b2].  The pre-activations and the output
+// sum are compensated (rounding errors carried along) because the site energy
+// must hold ~1e-7 relative accuracy.  Returns U as hi + lo.
+__host__ __device__ __forceinline__ void network(const float* w, int n_neu, const float (&q)[kNdes],
+                                                 float (&G)[kNdes], float& U_hi, float& U_lo)
+{
+    const float* b1 = w + n_neu * kNdes;
+    const float* w2 = b1 + n_neu;
+    const float b2 = w2[n_neu];
+#pragma unroll
+    for (int v = 0; v < kNdes; ++v) G[v] = 0.f;
+    float s = 0.f, c = 0.f;
+    for (int mu = 0; mu < n_neu; ++mu) {
+        const float* row = w + mu * kNdes;
+        // compensated (Kahan) pre-activation: the rounding of a plain FP32 dot
+        // product feeds straight into U for every unsaturated neuron
+        float a = -b1[mu], ca = 0.f;
+#pragma unroll
+        for (int v = 0; v < kNdes; ++v) {
+            const float y = fmaf(row[v], q[v], -ca);
+            const float t = a + y;
+            ca = (t - a) - y;
+            a = t;
+        }
+        const float xm = tanhf(a - ca);
+        const float p = w2[mu] * xm;
+        const float ep = fmaf(w2[mu], xm, -p);
+        float t, e;
+        two_sum(s, p, t, e);
+        s = t;
+        c += e + ep;
+        const float d = w2[mu] * fmaf(-xm, xm, 1.f);
+#pragma unroll
+        for (int v = 0; v < kNdes; ++v) G[v] = fmaf(d, row[v], G[v]);
+    }
+    float t, e;
+    two_sum(s, -b2, t, e);
+    U_hi = t;
+    U_lo = c + e;
+}
+
+// Everything atom i contributes in the first force pass: site energy and the
+// partial forces of all its list slots (written to pf[k][c][i] for slots
+// within max(rc_R, rc_A); other slots are left untouched).
+struct SiteParams {
+    const float* w;  // parameters (shared memory on the device)
+    int n_neu;
+    float rcR, rcA, rcR2, rcA2, inv_rcR, inv_rcA;
+};
+
+__host__ __device__ __forceinline__ void site_partial_forces(int i, bool active, int n, int m_cap,
+                                                             const int* __restrict__ count,
+                                                             const int* __restrict__ nbr,
+                                                             const float* __restrict__ xh,
+                                                             const float* __restrict__ xl, const Box& box,
+                                                             const SiteParams& P, float* __restrict__ pf,
+                                                             float& U_hi, float& U_lo)
+{
+    float hi[3], li[3];
+    if (active) load_pos(xh, xl, n, i, hi, li);
+    const int cnt = active ? imin(count[i], m_cap) : 0;
+
+    // radial sums are compensated (Kahan): q_0 ~ 4 accumulates ~28 terms and
+    // its plain FP32 rounding dominates the site-energy error budget
+    float qR[kNR], qC[kNR];
+    float S[kNA][kLM];
+#pragma unroll
+    for (int a = 0; a < kNR; ++a) qR[a] = qC[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < kNA; ++a)
+#pragma unroll
+        for (int b = 0; b < kLM; ++b) S[a][b] = 0.f;
+
+    // pass 1: descriptor sums.  Slots are sorted by increasing distance; walk
+    // the ranks downwards so the largest (nearest) terms are added last, with
+    // all lanes of a warp at the same rank (inactive lanes pass count 0).
+#ifdef __CUDA_ARCH__
+    const int kmax = __reduce_max_sync(0xffffffffu, cnt);
+#else
+    const int kmax = cnt;
+#endif
+    for (int k = kmax - 1; k >= 0; --k) {
+        if (k >= cnt) continue;
+        const int v = nbr[(size_t)k * n + i];
+        const int j = v & 0xFFFFFF;
+        float hj[3], lj[3];
+        load_pos(xh, xl, n, j, hj, lj);
+        float rx, ry, rz;
+        pair_vector(i, j, v >> 24, hi, li, hj, lj, box, rx, ry, rz);
+        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        if (d2 < P.rcR2) {
+            const float d = sqrtf(d2);
+            float g[kNR];
+            radial_g<kNR>(d, P.rcR, P.inv_rcR, g);
+#pragma unroll
+            for (int a = 0; a < kNR; ++a) {
+                const float y = g[a] - qC[a];
+                const float t = qR[a] + y;
+                qC[a] = (t - qR[a]) - y;
+                qR[a] = t;
+            }
+        }
+        if (d2 < P.rcA2) {
+            const float d = sqrtf(d2);
+            const float inv = 1.f / d;
+            float g[kNA];
+            radial_g<kNA>(d, P.rcA, P.inv_rcA, g);
+            sh_pass1(rx * inv, ry * inv, rz * inv, g, S);
+        }
+    }
+
+    // descriptor vector: q_nl = sum_m c_lm S_nlm^2 (compensated), n outer, l inner
+    float q[kNdes];
+#pragma unroll
+    for (int a = 0; a < kNR; ++a) q[a] = qR[a] - qC[a];
+#pragma unroll
+    for (int a = 0; a < kNA; ++a) {
+#pragma unroll
+        for (int l = 0; l < kLmax; ++l) q[kNR + a * kLmax + l] = 0.f;
+        float qc[kLmax] = {0.f, 0.f, 0.f, 0.f};  // Kahan compensation per l
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            const int v = kNR + a * kLmax + sh_l(m);
+            const float y = fmaf(sh_c(m) * S[a][m], S[a][m], -qc[sh_l(m)]);
+            const float t = q[v] + y;
+            qc[sh_l(m)] = (t - q[v]) - y;
+            q[v] = t;
+        }
+#pragma unroll
+        for (int l = 0; l < kLmax; ++l) q[kNR + a * kLmax + l] -= qc[l];
+    }
+
+    float G[kNdes];
+    network(P.w, P.n_neu, q, G, U_hi, U_lo);
+
+    // A_nlm = 2 c_lm G_nl S_nlm (reuses S)
+#pragma unroll
+    for (int a = 0; a < kNA; ++a) {
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            S[a][m] *= 2.f * sh_c(m) * G[kNR + a * kLmax + sh_l(m)];
+        }
+    }
+    float GR[kNR];
+#pragma unroll
+    for (int a = 0; a < kNR; ++a) GR[a] = G[a];
+
+    const float rc2max = P.rcR2 > P.rcA2 ? P.rcR2 : P.rcA2;
+    // pass 2: partial forces
+    for (int k = 0; k < cnt; ++k) {
+        const int v = nbr[(size_t)k * n + i];
+        const int j = v & 0xFFFFFF;
+        float hj[3], lj[3];
+        load_pos(xh, xl, n, j, hj, lj);
+        float rx, ry, rz;
+        pair_vector(i, j, v >> 24, hi, li, hj, lj, box, rx, ry, rz);
+        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        if (!(d2 < rc2max)) continue;
+        const float d = sqrtf(d2);
+        const float inv = 1.f / d;
+        const float ux = rx * inv, uy = ry * inv, uz = rz * inv;
+        float radial = 0.f;  // coefficient of rhat
+        float Vx = 0.f, Vy = 0.f, Vz = 0.f;
+        if (d2 < P.rcR2) {
+            float g[kNR], dg[kNR];
+            radial_g_dg<kNR>(d, P.rcR, P.inv_rcR, g, dg);
+#pragma unroll
+            for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], dg[a], radial);
+        }
+        if (d2 < P.rcA2) {
+            float g[kNA], dg[kNA];
+            radial_g_dg<kNA>(d, P.rcA, P.inv_rcA, g, dg);
+            sh_pass2(ux, uy, uz, S, g, dg, radial, Vx, Vy, Vz);
+            // tangential projection of V, divided by r
+            const float uv = fmaf(ux, Vx, fmaf(uy, Vy, uz * Vz));
+            Vx = (Vx - uv * ux) * inv;
+            Vy = (Vy - uv * uy) * inv;
+            Vz = (Vz - uv * uz) * inv;
+        }
+        float* p = pf + (size_t)k * 3 * n + i;
+        p[0] = fmaf(radial, ux, Vx);
+        p[(size_t)n] = fmaf(radial, uy, Vy);
+        p[(size_t)2 * n] = fmaf(radial, uz, Vz);
+    }
+}
+
+// Force and per-atom virial of atom i from the stored partial forces:
+//   F_i = sum_j (p_ij - p_ji),  W_i^{ab} = sum_j r_ij^a p_ji^b   (Eqs. 4-6).
+__host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, float rc2max,
+                                                       const int* __restrict__ count, const int* __restrict__ nbr,
+                                                       const int* __restrict__ rev, const float* __restrict__ xh,
+                                                       const float* __restrict__ xl, const Box& box,
+                                                       const float* __restrict__ pf, float (&F)[3], float (&W)[9])
+{
+    float hi[3], li[3];
+    load_pos(xh, xl, n, i, hi, li);
+    const int cnt = imin(count[i], m_cap);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a] = 0.f;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) W[a] = 0.f;
+    for (int k = 0; k < cnt; ++k) {
+        const int v = nbr[(size_t)k * n + i];
+        const int j = v & 0xFFFFFF;
+        float hj[3], lj[3];
+        load_pos(xh, xl, n, j, hj, lj);
+        float r[3];
+        pair_vector(i, j, v >> 24, hi, li, hj, lj, box, r[0], r[1], r[2]);
+        const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
+        if (!(d2 < rc2max)) continue;
+        const int kr = rev[(size_t)k * n + i];
+        const float* po = pf + (size_t)k * 3 * n + i;
+        const float* pi = pf + (size_t)kr * 3 * n + j;
+        float pji[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pji[c] = pi[(size_t)c * n];
+            F[c] += po[(size_t)c * n] - pji[c];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) W[3 * a + b] = fmaf(r[a], pji[b], W[3 * a + b]);
+    }
+}
+
+}  // namespace nep

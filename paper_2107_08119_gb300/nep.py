@@ -1,0 +1,370 @@
+"""Python binding of libnep.so (the C ABI in include/nep.h).
+
+Argument marshalling only: every step of the NEP path runs in the library's
+CUDA kernels.  PyTorch provides device memory (output tensors) and the
+current CUDA stream.  There is no CPU fallback: importing this module raises
+if the compiled library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnep.so")
+
+NEP_OK = 0
+STATUS = {
+    0: "NEP_OK", -1: "NEP_ERR_ARG", -2: "NEP_ERR_OOM", -3: "NEP_ERR_CUDA", -4: "NEP_ERR_NEIGHBOR_OVERFLOW",
+    -5: "NEP_ERR_NONFINITE", -6: "NEP_ERR_TIMEOUT", -7: "NEP_ERR_BOX", -8: "NEP_ERR_UNSUPPORTED",
+}
+THERMO_COLS = 8
+LOSS_COLS = 6
+PREC_FP32, PREC_BF16 = 0, 1
+
+
+class NepError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Hyper(C.Structure):
+    _fields_ = [("n_max_R", C.c_int), ("n_max_A", C.c_int), ("l_max", C.c_int), ("n_neu", C.c_int),
+                ("rc_R", C.c_double), ("rc_A", C.c_double), ("skin", C.c_double), ("max_neighbors", C.c_int)]
+
+
+_vp = C.c_void_p
+_SIGNATURES = {
+    "nep_create": (C.c_int, [C.POINTER(_Hyper), _vp, C.c_int, C.POINTER(_vp)]),
+    "nep_set_parameters": (C.c_int, [_vp, _vp, C.c_int, _vp]),
+    "nep_destroy": (C.c_int, [_vp]),
+    "nep_compute_efv": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nep_sync_status": (C.c_int, [_vp, _vp]),
+    "nep_heat_current": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "nep_get_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "nep_md_create": (C.c_int, [_vp, C.c_int, _vp, C.c_double, C.POINTER(_vp)]),
+    "nep_md_destroy": (C.c_int, [_vp]),
+    "nep_md_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
+    "nep_md_invalidate": (C.c_int, [_vp]),
+    "nep_md_rebuild_count": (C.c_int, [_vp, C.POINTER(C.c_longlong), _vp]),
+    "nep_md_forces": (_vp, [_vp]),
+    "nep_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "nep_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_longlong)]),
+    "nep_dataset_create": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
+    "nep_dataset_destroy": (C.c_int, [_vp]),
+    "nep_dataset_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "nep_dataset_descriptors": (C.c_int, [_vp, _vp, _vp]),
+    "snes_evaluate_population": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "snes_create": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_ulonglong, C.POINTER(_vp)]),
+    "snes_destroy": (C.c_int, [_vp]),
+    "snes_step": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "snes_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "nep_last_error": (C.c_char_p, []),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libnep.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+def _check(code: int, where: str):
+    if code != NEP_OK:
+        raise NepError(code, where, _lib.nep_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _box9(box):
+    b = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(9))
+    return b, b.ctypes.data_as(_vp)
+
+
+def _soa_f64(t, n=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+            and t.shape[0] == 3 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor of shape (3, n)")
+    if n is not None and t.shape[1] != n:
+        raise ValueError(f"expected {n} atoms, got {t.shape[1]}")
+    return t
+
+
+@dataclass(frozen=True)
+class Hyper:
+    n_max_R: int = 7
+    n_max_A: int = 5
+    l_max: int = 4
+    n_neu: int = 30
+    rc_R: float = 5.0
+    rc_A: float = 4.0
+    skin: float = 1.0
+    max_neighbors: int = 96
+
+    @property
+    def n_des(self) -> int:
+        return (self.n_max_R + 1) + (self.n_max_A + 1) * self.l_max
+
+    @property
+    def n_par(self) -> int:
+        return (self.n_des + 2) * self.n_neu + 1
+
+    def c(self) -> _Hyper:
+        return _Hyper(self.n_max_R, self.n_max_A, self.l_max, self.n_neu, self.rc_R, self.rc_A, self.skin,
+                      self.max_neighbors)
+
+
+class NEP:
+    """A NEP model on the GPU (handle of nep_create)."""
+
+    def __init__(self, z, hyper: Hyper = Hyper()):
+        self.hyper = hyper
+        zf = np.ascontiguousarray(np.asarray(z, dtype=np.float32).reshape(-1))
+        h = hyper.c()
+        out = _vp()
+        _check(_lib.nep_create(C.byref(h), zf.ctypes.data_as(_vp), zf.size, C.byref(out)), "nep_create")
+        self._h = out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_parameters(self, z, stream=None):
+        zf = np.ascontiguousarray(np.asarray(z, dtype=np.float32).reshape(-1))
+        _check(_lib.nep_set_parameters(self._h, zf.ctypes.data_as(_vp), zf.size, _stream(stream)),
+               "nep_set_parameters")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def compute(self, pos, box, *, e_total=True, e_atom=True, force=True, virial_atom=True, virial_total=True,
+                sync=True, stream=None):
+        """pos: CUDA float64 (3, n).  Returns a dict of device tensors."""
+        pos = _soa_f64(pos)
+        n = pos.shape[1]
+        dev = pos.device
+        out = {
+            "e_total": torch.empty(1, dtype=torch.float64, device=dev) if e_total else None,
+            "e_atom": torch.empty(n, dtype=torch.float64, device=dev) if e_atom else None,
+            "force": torch.empty(3, n, dtype=torch.float32, device=dev) if force else None,
+            "virial_atom": torch.empty(9, n, dtype=torch.float32, device=dev) if virial_atom else None,
+            "virial_total": torch.empty(9, dtype=torch.float64, device=dev) if virial_total else None,
+        }
+        b, bp = _box9(box)
+        _check(_lib.nep_compute_efv(self._h, n, bp, _ptr(pos), _ptr(out["e_total"]), _ptr(out["e_atom"]),
+                                    _ptr(out["force"]), _ptr(out["virial_atom"]), _ptr(out["virial_total"]),
+                                    _stream(stream)), "nep_compute_efv")
+        if sync:
+            self.sync_status(stream)
+        return {k: v for k, v in out.items() if v is not None}
+
+    def sync_status(self, stream=None):
+        _check(_lib.nep_sync_status(self._h, _stream(stream)), "nep_sync_status")
+
+    def neighbors(self, n: int, stream=None):
+        """(count[n], nbr[max_neighbors, n]) of the last compute() call."""
+        dev = torch.device("cuda")
+        cnt = torch.empty(n, dtype=torch.int32, device=dev)
+        nbr = torch.empty(self.hyper.max_neighbors, n, dtype=torch.int32, device=dev)
+        _check(_lib.nep_get_neighbors(self._h, n, _ptr(cnt), _ptr(nbr), _stream(stream)), "nep_get_neighbors")
+        return cnt, nbr
+
+    def profile(self, on: bool = True):
+        _check(_lib.nep_profile_enable(self._h, 1 if on else 0), "nep_profile_enable")
+
+    def profile_read(self):
+        """{'site_ms', 'site_launches', 'assemble_ms', 'assemble_launches'} since the last read."""
+        a, b = C.c_double(), C.c_double()
+        ca, cb = C.c_longlong(), C.c_longlong()
+        _check(_lib.nep_profile_read(self._h, C.byref(a), C.byref(ca), C.byref(b), C.byref(cb)), "nep_profile_read")
+        return {"site_ms": a.value, "site_launches": ca.value, "assemble_ms": b.value, "assemble_launches": cb.value}
+
+    def heat_current(self, virial_atom, vel, stream=None):
+        vel = _soa_f64(vel)
+        n = vel.shape[1]
+        if not (virial_atom.is_cuda and virial_atom.dtype == torch.float32 and tuple(virial_atom.shape) == (9, n)
+                and virial_atom.is_contiguous()):
+            raise ValueError("virial_atom must be a contiguous CUDA float32 tensor of shape (9, n)")
+        J = torch.empty(3, dtype=torch.float64, device=vel.device)
+        _check(_lib.nep_heat_current(self._h, n, _ptr(virial_atom), _ptr(vel), _ptr(J), _stream(stream)),
+               "nep_heat_current")
+        return J
+
+
+class MD:
+    """NVE velocity-Verlet integrator on a NEP model (handle of nep_md_create)."""
+
+    def __init__(self, model: NEP, n: int, box, mass: float):
+        self.model = model
+        self.n = n
+        b, bp = _box9(box)
+        out = _vp()
+        _check(_lib.nep_md_create(model._h, n, bp, float(mass), C.byref(out)), "nep_md_create")
+        self._h = out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nep_md_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, pos, vel, n_steps: int, dt: float, thermo=None, heat=None, stream=None):
+        """Advance in place.  thermo: CUDA float64 (n_steps, 8) or None;
+        heat: CUDA float64 (n_steps, 3) or None."""
+        pos = _soa_f64(pos, self.n)
+        vel = _soa_f64(vel, self.n)
+        for t, cols in ((thermo, THERMO_COLS), (heat, 3)):
+            if t is not None and not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                                      and t.numel() >= n_steps * cols):
+                raise ValueError("thermo/heat buffers must be contiguous CUDA float64 with room for every step")
+        _check(_lib.nep_md_step(self._h, _ptr(pos), _ptr(vel), int(n_steps), float(dt), _ptr(thermo), _ptr(heat),
+                                _stream(stream)), "nep_md_step")
+
+    def invalidate(self):
+        _check(_lib.nep_md_invalidate(self._h), "nep_md_invalidate")
+
+    def rebuild_count(self, stream=None) -> int:
+        c = C.c_longlong()
+        _check(_lib.nep_md_rebuild_count(self._h, C.byref(c), _stream(stream)), "nep_md_rebuild_count")
+        return c.value
+
+    def sync_status(self, stream=None):
+        self.model.sync_status(stream)
+
+
+def _host(a, dtype, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Dataset:
+    """A training set on the device (handle of nep_dataset_create).
+    structures: list of {"pos": (n, 3), "box": (3, 3)}; e_tar per structure,
+    f_tar (N, 3) concatenated, w_tar (n_struct, 6) in the order xx yy zz xy yz zx."""
+
+    def __init__(self, model: NEP, structures, e_tar, f_tar, w_tar):
+        self.model = model
+        n_atoms = _host([len(s["pos"]) for s in structures], np.int32)
+        boxes = _host(np.stack([np.asarray(s["box"], np.float64).reshape(3, 3) for s in structures]), np.float64)
+        pos = _host(np.concatenate([np.asarray(s["pos"], np.float64).reshape(-1, 3) for s in structures]),
+                    np.float64)
+        e = _host(e_tar, np.float64)
+        f = _host(f_tar, np.float64, (-1, 3))
+        w = _host(w_tar, np.float64, (-1, 6))
+        out = _vp()
+        _check(_lib.nep_dataset_create(model._h, len(structures), n_atoms.ctypes.data_as(_vp),
+                                       boxes.ctypes.data_as(_vp), pos.ctypes.data_as(_vp), e.ctypes.data_as(_vp),
+                                       f.ctypes.data_as(_vp), w.ctypes.data_as(_vp), C.byref(out)),
+               "nep_dataset_create")
+        self._h = out
+        self.n_struct = len(structures)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.nep_dataset_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        na, npairs, nb = C.c_int(), C.c_longlong(), C.c_longlong()
+        _check(_lib.nep_dataset_info(self._h, C.byref(na), C.byref(npairs), C.byref(nb)), "nep_dataset_info")
+        return {"atoms": na.value, "pairs": npairs.value, "device_bytes": nb.value}
+
+    def descriptors(self, stream=None):
+        n = self.info()["atoms"]
+        q = torch.empty(n, self.model.hyper.n_des, dtype=torch.float32, device="cuda")
+        _check(_lib.nep_dataset_descriptors(self._h, _ptr(q), _stream(stream)), "nep_dataset_descriptors")
+        return q
+
+    def evaluate(self, z_pop, precision=PREC_FP32, lambdas=None, stream=None):
+        """z_pop: CUDA float32 (n_pop, n_par).  Returns CUDA float64 (n_pop, 6)."""
+        if not (z_pop.is_cuda and z_pop.dtype == torch.float32 and z_pop.is_contiguous() and z_pop.dim() == 2):
+            raise ValueError("z_pop must be a contiguous CUDA float32 (n_pop, n_par) tensor")
+        loss = torch.empty(z_pop.shape[0], LOSS_COLS, dtype=torch.float64, device=z_pop.device)
+        lam = None if lambdas is None else _host(lambdas, np.float64, (5,))
+        _check(_lib.snes_evaluate_population(self.model._h, self._h, _ptr(z_pop), z_pop.shape[0], int(precision),
+                                             None if lam is None else lam.ctypes.data_as(_vp), _ptr(loss),
+                                             _stream(stream)), "snes_evaluate_population")
+        return loss
+
+
+class SNES:
+    """Separable natural evolution strategy on the device (handle of snes_create)."""
+
+    def __init__(self, model: NEP, n_pop: int, mean0, sigma0, seed: int):
+        self.model = model
+        self.n_pop = n_pop
+        m0 = _host(mean0, np.float32, (-1,))
+        s0 = _host(sigma0, np.float32, (-1,))
+        out = _vp()
+        _check(_lib.snes_create(model._h, n_pop, m0.ctypes.data_as(_vp), s0.ctypes.data_as(_vp), int(seed),
+                                C.byref(out)), "snes_create")
+        self._h = out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.snes_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, ds: Dataset, precision=PREC_FP32, lambdas=None, r=None, loss=None, stream=None):
+        lam = None if lambdas is None else _host(lambdas, np.float64, (5,))
+        _check(_lib.snes_step(self._h, ds._h, int(precision), None if lam is None else lam.ctypes.data_as(_vp),
+                              _ptr(r), _ptr(loss), _stream(stream)), "snes_step")
+
+    def state(self, stream=None):
+        npar = self.model.hyper.n_par
+        m = torch.empty(npar, dtype=torch.float32, device="cuda")
+        s = torch.empty(npar, dtype=torch.float32, device="cuda")
+        r = torch.empty(self.n_pop, npar, dtype=torch.float32, device="cuda")
+        order = torch.empty(self.n_pop, dtype=torch.int32, device="cuda")
+        _check(_lib.snes_get_state(self._h, _ptr(m), _ptr(s), _ptr(r), _ptr(order), _stream(stream)),
+               "snes_get_state")
+        return m, s, r, order

@@ -1,0 +1,188 @@
+"""Parity of the CUDA force path with the FP64 oracle (per-atom energy
+<= 1e-6 eV, force components <= 1e-4 eV/A, virial components <= 1e-4 eV),
+neighbour lists compared as sets, error statuses, determinism."""
+import numpy as np
+import pytest
+
+from gpu_util import aos, f32_exact, soa, virial_aos
+from paper_2107_08119_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_U, TOL_F, TOL_W = 1e-6, 1e-4, 1e-4
+
+
+@pytest.fixture(scope="module")
+def N():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2107_08119_gb300 import build
+    build.build()
+    from paper_2107_08119_gb300 import nep
+    return nep
+
+
+def _compare(N, orc, pos, box, z, hyper=None):
+    hyper = hyper or N.Hyper()
+    model = N.NEP(z, hyper)
+    out = model.compute(soa(pos), box)
+    oh = orc.NepHyper(hyper.n_max_R, hyper.n_max_A, hyper.l_max, hyper.n_neu, hyper.rc_R, hyper.rc_A)
+    U, F, W = orc.efv(oh, f32_exact(z), pos, box)
+    dU = np.abs(out["e_atom"].cpu().numpy() - U).max()
+    dF = np.abs(aos(out["force"]) - F).max()
+    dW = np.abs(virial_aos(out["virial_atom"]) - W).max()
+    n = len(pos)
+    dE = abs(out["e_total"].item() - U.sum())
+    dWt = np.abs(out["virial_total"].cpu().numpy().reshape(3, 3) - W.sum(axis=0)).max()
+    assert dU <= TOL_U, dU
+    assert dF <= TOL_F, dF
+    assert dW <= TOL_W, dW
+    assert dE <= TOL_U * n and dWt <= TOL_W * n, (dE, dWt)
+    model.close()
+    return dU, dF, dW
+
+
+def test_config1_parity(N, orc):
+    pos, box, z = inputs.config1()
+    _compare(N, orc, pos, box, z)
+
+
+def test_ragged_sizes_and_vacancies(N, orc):
+    """461 atoms (512 sites, 10 % vacancies; 4 blocks with a ragged tail) and
+    a 3 x 3 x 5 cell box (360 atoms) with larger displacements."""
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    assert len(pos) == 461
+    _compare(N, orc, pos, box, z)
+    rng = np.random.default_rng(17)
+    pos, box = inputs.diamond(3, 3, 5)
+    pos = inputs.displace(pos, 0.25, rng)
+    _compare(N, orc, pos, box, inputs.random_z(1021, rng))
+
+
+def test_small_periodic_cells_with_several_images(N, orc):
+    """Training-set cells of 32-256 atoms whose edges are shorter than 2 r_c:
+    the brute-force list with multiple periodic images."""
+    z = inputs.random_z(1021, np.random.default_rng(3))
+    for s in inputs.training_structures(6, seed_stream=9):
+        _compare(N, orc, s["pos"], s["box"], z)
+
+
+def test_degenerate_inputs(N, orc):
+    """One atom with no neighbour, an isolated dimer, and an atom that only
+    sees its own periodic images."""
+    z = inputs.random_z(1021, np.random.default_rng(5))
+    _compare(N, orc, np.array([[3.0, 4.0, 5.0]]), np.eye(3) * 30.0, z)
+    _compare(N, orc, np.array([[10.0, 10.0, 10.0], [12.1, 11.0, 10.3]]), np.eye(3) * 30.0, z)
+    _compare(N, orc, np.array([[1.0, 1.5, 2.0]]), np.diag([3.1, 3.3, 3.6]), z)
+
+
+def test_neighbor_list_matches_oracle(N, orc):
+    """Integer work is exact: the GPU list holds the same (j, image) pairs as
+    the oracle's brute force, away from the cutoff where FP32 and FP64 may
+    legitimately disagree; pairs within 1e-5 A of it must be valid."""
+    for pos, box in (inputs.config1()[:2], (inputs.training_structures(1, 4)[0]["pos"],
+                                           inputs.training_structures(1, 4)[0]["box"])):
+        n = len(pos)
+        h = N.Hyper()
+        model = N.NEP(np.zeros(h.n_par, np.float32), h)
+        model.compute(soa(pos), box)
+        cnt, nbr = model.neighbors(n)
+        cnt = cnt.cpu().numpy()
+        nbr = nbr.cpu().numpy()
+        oc, oj, orr = orc.neighbors(pos, box, 5.0, method=0, cap=256)
+        L = np.diag(box)
+        wrapped = pos - L * np.floor(pos / L)
+        for i in range(n):
+            got = set()
+            for k in range(cnt[i]):
+                v = int(nbr[k, i])
+                j, c = v & 0xFFFFFF, v >> 24
+                s = np.array([c // 25 - 2, (c // 5) % 5 - 2, c % 5 - 2])
+                r = wrapped[j] + s * L - wrapped[i]
+                d = np.linalg.norm(r)
+                assert d < 5.0 + 1e-5
+                if d < 5.0 - 1e-5:
+                    got.add((j, *np.round(r, 6)))
+            want = {(int(j), *np.round(r, 6)) for j, r in zip(oj[i, :oc[i]], orr[i, :oc[i]])
+                    if np.linalg.norm(r) < 5.0 - 1e-5}
+            assert got == want, i
+            assert len(set(int(x) for x in nbr[:cnt[i], i])) == cnt[i]   # no duplicates
+        model.close()
+
+
+def test_error_statuses(N):
+    import torch
+    pos, box, z = inputs.config1()
+    h = N.Hyper(max_neighbors=8)
+    model = N.NEP(z, h)
+    with pytest.raises(N.NepError) as e:
+        model.compute(soa(pos), box)
+    assert e.value.code == -4
+    model.close()
+    model = N.NEP(z)
+    skew = box.copy()
+    skew[1, 0] = 0.5
+    with pytest.raises(N.NepError) as e:
+        model.compute(soa(pos), skew)
+    assert e.value.code == -7
+    with pytest.raises(N.NepError) as e:
+        model.compute(soa(pos[:2]), np.eye(3) * 2.0)
+    assert e.value.code == -7
+    # the handle stays usable after errors
+    out = model.compute(soa(pos), box)
+    assert torch.isfinite(out["force"]).all()
+    model.close()
+
+
+def test_bitwise_deterministic(N):
+    import torch
+    pos, box, z = inputs.config1()
+    model = N.NEP(z)
+    a = model.compute(soa(pos), box)
+    b = model.compute(soa(pos), box)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    model.close()
+
+
+def test_heat_current_contraction(N, orc):
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    model = N.NEP(z)
+    out = model.compute(soa(pos), box)
+    J = model.heat_current(out["virial_atom"], soa(vel)).cpu().numpy()
+    _, _, W = orc.efv(orc.NepHyper(), f32_exact(z), pos, box)
+    Jo = orc.heat_current(W, vel)
+    # |dJ^a| <= sum_i sum_b |dW_i^ab| |v_i^b| <= TOL_W sum_i sum_b |v_i^b|
+    bound = TOL_W * np.abs(vel).sum()
+    assert np.abs(J - Jo).max() <= bound, (J, Jo, bound)
+    model.close()
+
+
+def test_full_size_config2_positions(N, orc):
+    """All 125,000 atoms of the MD workload's starting configuration."""
+    pos, vel, box, z = inputs.config2()
+    dU, dF, dW = _compare(N, orc, pos, box, z)
+    print(f"125k atoms: max |dU| {dU:.2e}, |dF| {dF:.2e}, |dW| {dW:.2e}")
+
+
+def test_full_size_config3_sampled(N, orc):
+    """The 921,600-atom heat-transport box (40 x 40 x 80 cells, 10 % vacancies),
+    evaluated whole on the GPU; 3,000 atoms checked one by one by the oracle:
+    every atom within 0.3 A of a box face (pairs crossing the boundary) plus a
+    seeded random sample."""
+    pos, vel, box, z = inputs.config3()
+    assert len(pos) == 921_600
+    model = N.NEP(z)
+    out = model.compute(soa(pos), box)
+    L = np.diag(box)
+    w = pos - L * np.floor(pos / L)
+    near = np.where(np.minimum(w, L - w).min(axis=1) < 0.3)[0]
+    rng = np.random.default_rng(8)
+    idx = np.unique(np.concatenate([near[:1500], rng.choice(len(pos), 3000 - min(1500, len(near)), replace=False)]))
+    U, F, W = orc.efv_sample(orc.NepHyper(), f32_exact(z), pos, box, idx)
+    dU = np.abs(out["e_atom"].cpu().numpy()[idx] - U).max()
+    dF = np.abs(aos(out["force"])[idx] - F).max()
+    dW = np.abs(virial_aos(out["virial_atom"])[idx] - W).max()
+    print(f"921,600 atoms, {len(idx)} sampled: max |dU| {dU:.2e}, |dF| {dF:.2e}, |dW| {dW:.2e}")
+    assert dU <= TOL_U and dF <= TOL_F and dW <= TOL_W, (dU, dF, dW)
+    model.close()

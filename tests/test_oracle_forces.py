@@ -140,3 +140,15 @@ def test_extensivity_and_brute_force(orc, model):
         assert np.allclose(U8[k * n:(k + 1) * n], U, atol=1e-12)
         assert np.allclose(F8[k * n:(k + 1) * n], F, atol=1e-12)
         assert np.allclose(W8[k * n:(k + 1) * n], W, atol=1e-12)
+
+
+def test_sampled_evaluation_equals_full(orc, model):
+    """The per-atom sampler used for full-size parity gives the full result."""
+    h, z = model
+    for pos, box in (_periodic((3, 3, 3), seed=41), _periodic((1, 2, 2), seed=42)):
+        U, F, W = orc.efv(h, z, pos, box)
+        idx = np.array([0, 5, len(pos) // 2, len(pos) - 1])
+        Us, Fs, Ws = orc.efv_sample(h, z, pos, box, idx)
+        assert np.allclose(Us, U[idx], atol=1e-13)
+        assert np.allclose(Fs, F[idx], atol=1e-12)
+        assert np.allclose(Ws, W[idx], atol=1e-12)
