@@ -247,6 +247,45 @@ int nep_profile_enable(nep_model* m, int on);
 int nep_profile_read(nep_model* m, double* site_ms, long long* site_launches, double* assemble_ms,
                      long long* assemble_launches);
 
+/*
+ * nep_compute_efv_static -- nep_compute_efv without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they need forces -- code that runs while
+ * a memory pool is locked or full by design, plugins whose host application
+ * owns every allocation, or real-time loops that forbid allocator calls.  It
+ * needs no model handle: the caller passes the parameters, inputs and
+ * outputs, all in memory it already owns, and the scratch (neighbour list,
+ * reverse index, partial forces, cells, partial sums) lives in one
+ * file-scope device array of fixed size inside the library.
+ *
+ * Limits (the array holds about 8.3 MB on every GPU that loads the library,
+ * until the process exits): n <= NEP_STATIC_MAX_ATOMS, hp->max_neighbors <=
+ * NEP_STATIC_MAX_NEIGHBORS, and at most NEP_STATIC_MAX_CELLS cells of edge
+ * max(rc_R, rc_A); larger inputs return NEP_ERR_ARG.  The call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one array, which keeps
+ * the previous call's contents (the parts that must start at zero are cleared
+ * by the call itself); calls that overlap on the GPU -- on different streams,
+ * or from host threads without ordering between them -- race on it.
+ *   hp          host, hyperparameters as for nep_create.
+ *   z           dev, n_par FP32 parameters (layout as in nep_create).
+ *   n, box9, pos, e_total, e_atom, force, virial_atom, virial_total, stream:
+ *               as for nep_compute_efv.
+ *   err_out     dev, 1 unsigned or NULL: device-side error bits of this call
+ *               (0 = none; 1 = neighbour overflow, 2 = non-finite value,
+ *               4 = asymmetric list), written by the call's last kernel.
+ */
+#define NEP_STATIC_MAX_ATOMS 4096
+#define NEP_STATIC_MAX_NEIGHBORS 96
+#define NEP_STATIC_MAX_CELLS 32768
+int nep_compute_efv_static(const nep_hyper* hp, const float* z, int n_par, int n, const double* box9,
+                           const double* pos, double* e_total, double* e_atom, float* force, float* virial_atom,
+                           double* virial_total, unsigned* err_out, void* stream);
+
 /* Message describing the last failing call on this thread ("" if none). */
 const char* nep_last_error(void);
 

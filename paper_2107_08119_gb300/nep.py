@@ -65,6 +65,8 @@ _SIGNATURES = {
     "snes_destroy": (C.c_int, [_vp]),
     "snes_step": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
     "snes_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "nep_compute_efv_static": (C.c_int, [C.POINTER(_Hyper), _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         _vp, _vp, _vp]),
     "nep_last_error": (C.c_char_p, []),
 }
 
@@ -219,6 +221,34 @@ class NEP:
         _check(_lib.nep_heat_current(self._h, n, _ptr(virial_atom), _ptr(vel), _ptr(J), _stream(stream)),
                "nep_heat_current")
         return J
+
+
+STATIC_MAX_ATOMS = 4096
+STATIC_MAX_NEIGHBORS = 96
+
+
+def compute_efv_static(z_dev, pos, box, hyper: Hyper = Hyper(max_neighbors=STATIC_MAX_NEIGHBORS), stream=None):
+    """nep_compute_efv_static: the force path without any device allocation
+    inside the call (scratch in a fixed-size array in the library).  z_dev is
+    a CUDA float32 tensor of the n_par parameters.  Output tensors are
+    allocated here by PyTorch, as the caller's memory.  Returns a dict of
+    device tensors including "err" (device-side error bits)."""
+    pos = _soa_f64(pos)
+    n = pos.shape[1]
+    dev = pos.device
+    out = {"e_total": torch.empty(1, dtype=torch.float64, device=dev),
+           "e_atom": torch.empty(n, dtype=torch.float64, device=dev),
+           "force": torch.empty(3, n, dtype=torch.float32, device=dev),
+           "virial_atom": torch.empty(9, n, dtype=torch.float32, device=dev),
+           "virial_total": torch.empty(9, dtype=torch.float64, device=dev),
+           "err": torch.empty(1, dtype=torch.int32, device=dev)}
+    b, bp = _box9(box)
+    h = hyper.c()
+    _check(_lib.nep_compute_efv_static(C.byref(h), _ptr(z_dev), int(z_dev.numel()), n, bp, _ptr(pos),
+                                       _ptr(out["e_total"]), _ptr(out["e_atom"]), _ptr(out["force"]),
+                                       _ptr(out["virial_atom"]), _ptr(out["virial_total"]), _ptr(out["err"]),
+                                       _stream(stream)), "nep_compute_efv_static")
+    return out
 
 
 class MD:
