@@ -225,7 +225,7 @@ def run_gpu(args, rank, world, local):
     torch.cuda.synchronize()
     model.profile(False)
     prof = model.profile_read()
-    site_ms = prof["site_ms"] / max(1, prof["site_launches"])
+    site_ms = prof["site"][0] / max(1, prof["site"][1])
     if dist:
         dist.barrier()
     clocks = sampler.stop()
@@ -234,6 +234,16 @@ def run_gpu(args, rank, world, local):
     rebuilds = md.rebuild_count() - rebuilds0
     th = thermo[:K].cpu().numpy()
     etot = th[:, 0] + th[:, 1]
+
+    if args.only == "md":
+        if rank == 0:
+            print(json.dumps({"md_ms_per_step": ms / K, "phase_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+                              "list_rebuilds_timed": rebuilds, "clocks": clocks}), flush=True)
+        md.close()
+        model.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
 
     # end to end through the C ABI with host buffers: per step, the state goes
     # host -> device from pinned memory and comes back with the thermo row
@@ -285,12 +295,12 @@ def run_gpu(args, rank, world, local):
                              "neighbour list, reverse index and partial forces ~340 MB > 129 MB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "mean_neighbors_rcR": m_r, "mean_neighbors_rcA": m_a,
+                       "phase_ms_per_step": {k: v[0] / K for k, v in prof.items()},
                        "energy_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / n)},
             "roofline": {"kernel": "k_site (descriptors + network + partial forces)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None, "flops_per_atom": flops_atom, "kernel_ms": site_ms,
-                         "kernel_share_of_step": prof["site_ms"] / t_max if t_max > 0 else None,
-                         "assemble_ms": prof["assemble_ms"] / max(1, prof["assemble_launches"]),
+                         "kernel_share_of_step": prof["site"][0] / t_max if t_max > 0 else None,
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (fp32 pipe, derived)"},
             "clocks": clocks,
             "e2e": {"value": world * n * Ke / e2e_s, "unit": UNIT,
@@ -300,6 +310,9 @@ def run_gpu(args, rank, world, local):
             "gpu_launches": 13 * K,
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
+        line["snes"] = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16),
+                        "unit": "generation/s",
+                        "workload": "200 periodic structures of 32-256 atoms, population 50, 32-30-1 NEP"}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_md(seconds=args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -310,6 +323,41 @@ def run_gpu(args, rank, world, local):
     return 0
 
 
+def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
+    """SNES on the 200-structure training workload, population 50: one
+    generation = draws + population evaluation + update, on the device.
+    Labels come from the CUDA force path with the teacher (a timing input)."""
+    import torch
+    structures, teacher, pop = inputs.config4()
+    model = N.NEP(np.asarray(teacher, np.float32))
+    E, F, W = [], [], []
+    for s in structures:
+        out = model.compute(torch.tensor(s["pos"].T.copy(), dtype=torch.float64, device="cuda"), s["box"])
+        wt = out["virial_total"].cpu().numpy().reshape(3, 3)
+        E.append(out["e_total"].item())
+        F.append(out["force"].cpu().numpy().T)
+        W.append([wt[0, 0], wt[1, 1], wt[2, 2], wt[0, 1], wt[1, 2], wt[2, 0]])
+    ds = N.Dataset(model, structures, np.array(E), np.concatenate(F), np.array(W))
+    info = ds.info()
+    snes = N.SNES(model, 50, np.zeros(model.hyper.n_par), np.full(model.hyper.n_par, 0.1), seed=2107081194)
+    for _ in range(warm):
+        snes.step(ds, precision)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(gens):
+        snes.step(ds, precision)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / gens
+    snes.close()
+    ds.close()
+    model.close()
+    return {"generations_per_s": 1e3 / ms, "ms_per_generation": ms, "atoms": info["atoms"], "pairs": info["pairs"],
+            "population": 50, "structures": len(structures), "generations_timed": gens}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,13 +366,28 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default="all", choices=["all", "md", "snes"],
+                    help="md: the timed MD steps alone (no e2e, SNES or CPU legs); snes: the SNES legs alone. "
+                         "Small single-purpose runs for profiler captures.")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.only == "snes":
+        return run_snes_only()
     return run_gpu(args, rank, world, local)
+
+
+def run_snes_only():
+    import torch  # noqa: F401
+    from paper_2107_08119_gb300 import build
+    build.build()
+    from paper_2107_08119_gb300 import nep as N
+    out = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16)}
+    print(json.dumps({"snes": out}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

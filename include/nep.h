@@ -213,6 +213,36 @@ int snes_evaluate_population(nep_model* m, nep_dataset* ds, const float* z_pop, 
                              const double* lambdas, double* loss, void* stream);
 
 /*
+ * nep_force_loss -- the force term of the loss for one parameter vector:
+ * L_f = sqrt( sum_i |F_i - F_tar_i|^2 / (3 N) ) over the N atoms of the
+ * training set (Eq. 30), with F_i from the force path (Eqs. 4-5, 23-25)
+ * evaluated from the structures' positions (descriptors recomputed).
+ *   z        dev [n_par] FP32 parameter vector (layout of nep_create).
+ *   loss_f   dev [1] FP64, or NULL.
+ * The dataset keeps a copy of z, the residuals F_i - F_tar_i and L_f, which
+ * nep_force_loss_backward differentiates; one forward per backward, in
+ * stream order on the same stream.  The paper fits by SNES without gradients
+ * (Sec. II.D); this pair of calls is the differentiable alternative for the
+ * same loss term.  Deterministic (fixed summation order).
+ * Errors: NEP_ERR_ARG (NULL, dataset of another model), NEP_ERR_OOM, NEP_ERR_CUDA;
+ * non-finite forces latch NEP_ERR_NONFINITE (nep_sync_status).
+ */
+int nep_force_loss(nep_model* m, nep_dataset* ds, const float* z, double* loss_f, void* stream);
+
+/*
+ * nep_force_loss_backward -- grad = seed * dL_f/dz at the z of the last
+ * nep_force_loss on ds, by a hand-written adjoint of the force path: per atom
+ * lambda_i = sum_j dq_i/dr_ij . (delta_i - delta_j), delta = (F - F_tar)/(3N L_f),
+ * descriptors and their pair derivatives recomputed from the positions, then
+ * the chain rule through the network of Eqs. 21-22; the sum over atoms is
+ * taken in FP64 in a fixed order.  dL_f/db2 is 0; all of grad is 0 when L_f = 0.
+ *   seed     dev [1] FP64 upstream gradient dOut/dL_f, or NULL for 1.
+ *   grad     dev [n_par] FP64.
+ * Errors: NEP_ERR_ARG (NULL, no nep_force_loss on ds before), NEP_ERR_CUDA.
+ */
+int nep_force_loss_backward(nep_model* m, nep_dataset* ds, const double* seed, double* grad, void* stream);
+
+/*
  * SNES state (Sec. II.D.2, Eqs. 35-39): mean m and step sizes s (FP32,
  * n_par each), population size n_pop (2..64), and the seed of the
  * Philox4x32-10 stream that draws r_k.
@@ -237,15 +267,35 @@ int snes_step(snes_state* st, nep_dataset* ds, int precision, const double* lamb
 int snes_get_state(snes_state* st, float* mean, float* sigma, float* r_last, int* order, void* stream);
 
 /*
- * Kernel timing: when enabled, the library records CUDA events on the
- * launching stream around every launch of its two force passes (site
- * energies + partial forces; force/virial assembly).  nep_profile_read
- * synchronises, returns the summed durations (ms) and launch counts since
- * the last read, and resets them.  Any pointer may be NULL.
+ * nep_tc_selftest -- one 128 x N x 32 BF16 tile through the tcgen05 path used
+ * by NEP_PREC_BF16 (shared-memory operand layout, instruction descriptor,
+ * TMEM accumulation and read-back), for checking it against a plain GEMM.
+ *   A    dev, 128 x 32 BF16, row-major.
+ *   B    dev, N x 32 BF16, row-major (D = A B^T); N a multiple of 16 in [16, 256].
+ *   D    dev, 128 x N FP32, row-major.
+ *   err  dev, 1 unsigned: error bits (8 = a bounded wait gave up), OR-ed in.
  */
+int nep_tc_selftest(const void* A, const void* B, int N, float* D, unsigned* err, void* stream);
+
+/*
+ * Kernel timing: when enabled, the library records CUDA events on the
+ * launching stream around each phase of its force path and integrator:
+ *   NEP_PROFILE_SITE      site energies + partial forces (one kernel)
+ *   NEP_PROFILE_ASSEMBLE  force / per-atom virial assembly (one kernel)
+ *   NEP_PROFILE_NEIGHBOR  neighbour-list build (all its kernels; in MD they
+ *                         return at once on steps without a rebuild)
+ *   NEP_PROFILE_STEP      MD kick/drift, skin gate, reductions, thermo row
+ * nep_profile_read synchronises, writes the summed durations (ms) and
+ * bracket counts since the last read into ms[NEP_PROFILE_KINDS] and
+ * launches[NEP_PROFILE_KINDS] (either may be NULL), and resets them.
+ */
+#define NEP_PROFILE_SITE 0
+#define NEP_PROFILE_ASSEMBLE 1
+#define NEP_PROFILE_NEIGHBOR 2
+#define NEP_PROFILE_STEP 3
+#define NEP_PROFILE_KINDS 4
 int nep_profile_enable(nep_model* m, int on);
-int nep_profile_read(nep_model* m, double* site_ms, long long* site_launches, double* assemble_ms,
-                     long long* assemble_launches);
+int nep_profile_read(nep_model* m, double* ms, long long* launches);
 
 /*
  * nep_compute_efv_static -- nep_compute_efv without any device allocation.

@@ -167,8 +167,8 @@ int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_par
         const size_t N = (size_t)n, M = (size_t)m_cap;
         if ((rc = dev_alloc(&nl.count, N, "neighbour counts")) || (rc = dev_alloc(&nl.nbr, N * M, "neighbour list")) ||
             (rc = dev_alloc(&nl.rev, N * M, "reverse pair index")) ||
-            (rc = dev_alloc(&nl.pf, N * M * 3, "partial forces")) || (rc = dev_alloc(&nl.xh, N * 3, "positions")) ||
-            (rc = dev_alloc(&nl.xl, N * 3, "positions")) || (rc = dev_alloc(&nl.atom_cell, N, "cell index")) ||
+            (rc = dev_alloc(&nl.pf, N * M * 3, "partial forces")) || (rc = dev_alloc(&nl.xh, N * 4, "positions")) ||
+            (rc = dev_alloc(&nl.xl, N * 4, "positions")) || (rc = dev_alloc(&nl.atom_cell, N, "cell index")) ||
             (rc = dev_alloc(&nl.cell_atoms, N, "cell atoms")) || (rc = dev_alloc(&ws.force, N * 3, "forces")))
             return rc;
         nl.n_cap = n;
@@ -252,8 +252,10 @@ void Profiler::end(Slot* s, cudaStream_t st)
 
 int Profiler::read(double* ms, long long* cnt)
 {
-    ms[0] = ms[1] = 0.0;
-    cnt[0] = cnt[1] = 0;
+    for (int k = 0; k < NEP_PROFILE_KINDS; ++k) {
+        ms[k] = 0.0;
+        cnt[k] = 0;
+    }
     for (int k = 0; k < used; ++k) {
         int rc = cuda_fail(cudaEventSynchronize(slots[k].b), "event synchronise");
         if (rc) return rc;
@@ -377,15 +379,17 @@ int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, 
     const int nblocks = (n + 127) / 128;
     if ((rc = ensure_workspace(m->ws, n, m->hp.max_neighbors, ncell, nblocks))) return rc;
     NeighborList& nl = m->ws.nl;
+    Profiler::Slot* pn = m->prof.begin(NEP_PROFILE_NEIGHBOR, st);
     if ((rc = build_neighbor_list(nl, box, n, const_cast<double*>(pos), false, nullptr, (float)rmax, m->d_err,
                                   nullptr, st)))
         return rc;
+    m->prof.end(pn, st);
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, box};
     // partial sums: energies in [0, nblocks), assembly totals after them
     double* part_e = m->ws.partials;
     double* part_v = m->ws.partials + ((nblocks + 7) / 8) * 8;
     int nb1 = 0;
-    Profiler::Slot* ps = m->prof.begin(0, st);
+    Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, st);
     if ((rc = launch_site_partial_forces(fa, nl, n, e_atom, part_e, m->d_err, st, nb1))) return rc;
     m->prof.end(ps, st);
     AssembleArgs aa{};
@@ -393,7 +397,7 @@ int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, 
     aa.box = box;
     aa.vel = nullptr;
     int nb2 = 0, nc2 = 0;
-    ps = m->prof.begin(1, st);
+    ps = m->prof.begin(NEP_PROFILE_ASSEMBLE, st);
     if ((rc = launch_assemble(aa, nl, n, force, virial_atom, part_v, m->d_err, st, nb2, nc2))) return rc;
     m->prof.end(ps, st);
     if (e_total || virial_total) {
@@ -415,21 +419,20 @@ int nep_profile_enable(nep_model* m, int on)
     return NEP_OK;
 }
 
-int nep_profile_read(nep_model* m, double* site_ms, long long* site_launches, double* assemble_ms,
-                     long long* assemble_launches)
+int nep_profile_read(nep_model* m, double* ms, long long* launches)
 {
     if (!m) {
         set_error("nep_profile_read: NULL handle");
         return NEP_ERR_ARG;
     }
-    double ms[2];
-    long long cnt[2];
-    int rc = m->prof.read(ms, cnt);
+    double t[NEP_PROFILE_KINDS];
+    long long c[NEP_PROFILE_KINDS];
+    int rc = m->prof.read(t, c);
     if (rc) return rc;
-    if (site_ms) *site_ms = ms[0];
-    if (site_launches) *site_launches = cnt[0];
-    if (assemble_ms) *assemble_ms = ms[1];
-    if (assemble_launches) *assemble_launches = cnt[1];
+    for (int k = 0; k < NEP_PROFILE_KINDS; ++k) {
+        if (ms) ms[k] = t[k];
+        if (launches) launches[k] = c[k];
+    }
     return NEP_OK;
 }
 

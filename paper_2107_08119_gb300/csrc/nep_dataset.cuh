@@ -1,0 +1,77 @@
+// nep_dataset.cuh -- the device-resident training set shared by the SNES
+// evaluation (nep_train.cu) and the force-loss adjoint (nep_adjoint.cu).
+//
+// Structures of uneven size are concatenated into one set of N atoms, each
+// keeping its own orthorhombic periodic box.  Pairs within max(r_c^R, r_c^A)
+// are stored in CSR form: the pairs of atom i are p in [pstart[i], pstart[i+1]),
+// pj[p] = j | image_code << 24, rev[p] = the slot of the pair (j -> i).
+#pragma once
+
+#include "nep_site.cuh"
+
+namespace nep {
+
+// Jacobian record of one pair, stored at the slot of the OTHER atom (see
+// k_ds_site): the radial part of d q_j / d r_ji.
+struct PairRec {
+    float r[3];   // r_ij of the owning atom i (the vector from i to j)
+    float gd[8];  // g_n'(|r|) / |r|, radial orders n = 0..7 (0 beyond r_c^R)
+    float pad;
+};
+
+// Scratch of the force-loss adjoint.
+struct AdjointScratch {
+    int n_blocks = 0;          // per-atom kernel blocks the partial buffers hold
+    float* pf = nullptr;       // [n_pairs][3] dU_i/dr_ij of the last forward
+    float* res = nullptr;      // [N] float4: F_i - F_tar_i of the last forward
+    float* z = nullptr;        // [n_par] parameters of the last forward
+    double* part = nullptr;    // [n_blocks][n_par] per-block FP64 partial sums
+    double* sums = nullptr;    // [2]: sum |F - F_tar|^2, L_f
+    bool ready = false;        // a forward has run since the scratch was made
+};
+
+}  // namespace nep
+
+struct nep_dataset {
+    nep_model* m = nullptr;
+    int S = 0, N = 0;
+    long long n_pairs = 0, n_ang = 0, bytes = 0;
+    int n_chunks = 0;
+    nep::Box* boxes = nullptr;
+    int* sid = nullptr;
+    int* sstart = nullptr;
+    int* s_natoms = nullptr;
+    int* s_chunk0 = nullptr;
+    int* chunk_begin = nullptr;
+    int* chunk_end = nullptr;
+    float* q = nullptr;
+    float* xh = nullptr;  // FP32 hi/lo wrapped positions (float4 records), kept for the adjoint
+    float* xl = nullptr;
+    float* B = nullptr;
+    long long* pstart = nullptr;
+    int* pj = nullptr;
+    long long* rev = nullptr;   // slot of the reverse pair (j -> i) of each pair
+    long long* aidx = nullptr;
+    nep::PairRec* rec = nullptr;
+    float* ang = nullptr;
+    double* e_tar = nullptr;
+    float* f_tar = nullptr;
+    double* w_tar = nullptr;
+    // evaluation scratch (grown on demand)
+    int pop_cap = 0;
+    float* W1t = nullptr;
+    float* b1t = nullptr;
+    float* w2t = nullptr;
+    float* b2t = nullptr;
+    float* G = nullptr;
+    double* U = nullptr;
+    double* partials = nullptr;
+    unsigned char* packed = nullptr;  // tensor-core operand records
+    // force-loss adjoint scratch (grown on demand, nep_adjoint.cu)
+    nep::AdjointScratch adj;
+};
+
+namespace nep {
+// frees the adjoint scratch of a dataset (nep_adjoint.cu)
+void free_adjoint(AdjointScratch& a);
+}  // namespace nep

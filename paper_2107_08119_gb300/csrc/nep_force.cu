@@ -22,7 +22,30 @@ namespace {
 
 constexpr int kSiteThreads = 128;
 constexpr int kAsmThreads = 128;
+constexpr int kStageSlots = 96;  // slots per atom staged in shared memory
 
+// Copy the block's neighbour slots (slot-major: slot k of the block's atoms is
+// one contiguous run) into shared memory with 4-byte asynchronous copies, all
+// in flight at once; slots past an atom's count are not read.
+__device__ __forceinline__ int stage_slots(const int* __restrict__ nbr, int n, int i, bool active, int cnt,
+                                           int kstage, int* s_nbr)
+{
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int k = 0; k < kstage; ++k) {
+        int* dst = s_nbr + k * T + tid;
+        if (active && k < cnt) {
+            const int* src = nbr + (size_t)k * n + i;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                         "l"(src)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+    return kstage;
+}
+
+// STAGED: the neighbour capacity fits the shared-memory staging (m_cap <= kStageSlots).
+template <bool STAGED>
 __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const int* __restrict__ count,
                                                        const int* __restrict__ nbr, const float* __restrict__ xh,
                                                        const float* __restrict__ xl, Box box,
@@ -32,15 +55,20 @@ __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const i
 {
     extern __shared__ float s_w[];
     for (int t = threadIdx.x; t < n_par; t += blockDim.x) s_w[t] = z[t];
-    __syncthreads();
     P.w = s_w;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double e[1] = {0.0};
     // every lane runs the site function (the warp walks neighbour ranks in
     // step); lanes past the last atom see no neighbours and store nothing
     const bool active = i < n;
+    const int cnt = active ? min(count[i], m_cap) : 0;
+    int* s_nbr = reinterpret_cast<int*>(s_w + ((n_par + 31) / 32) * 32);
+    if (STAGED) stage_slots(nbr, n, i, active, cnt, m_cap, s_nbr);
+    __syncthreads();
+    const SlotTable T = STAGED ? SlotTable{s_nbr, kSiteThreads, (int)threadIdx.x} : SlotTable{nbr, n, i};
     float uh, ul;
-    site_partial_forces(active ? i : 0, active, n, m_cap, count, nbr, xh, xl, box, P, pf, uh, ul);
+    const PfOut out{pf + (active ? i : 0), (size_t)3 * n, (size_t)n};
+    site_partial_forces(active ? i : 0, active, n, cnt, T, xh, xl, box, P, out, uh, ul);
     if (active) {
         e[0] = (double)uh + (double)ul;
         if (e_atom) e_atom[i] = e[0];
@@ -65,8 +93,11 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(int n, int m_cap, floa
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
     if (i < n) {
+        // the list is read straight from global memory: staging it in shared
+        // memory (as the site pass does) cost this pass occupancy and time
+        const SlotTable T{nbr, n, i};
         float F[3], W[9];
-        assemble_atom(i, n, m_cap, rc2max, count, nbr, rev, xh, xl, box, pf, F, W);
+        assemble_atom(i, n, m_cap, rc2max, count, T, rev, xh, xl, box, pf, F, W);
         if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) atomicOr(err, kErrNonFinite);
         if (force) {
             force[i] = F[0];
@@ -127,7 +158,15 @@ int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, doub
     P.inv_rcA = 1.f / a.rcA;
     const int n_par = (kNdes + 2) * a.n_neu + 1;
     nblocks = blocks_for(n, kSiteThreads);
-    k_site<<<nblocks, kSiteThreads, n_par * sizeof(float), st>>>(n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box,
+    const size_t smem = (((size_t)n_par + 31) / 32 * 32 + (size_t)kStageSlots * kSiteThreads) * sizeof(float);
+    const bool staged = a.box.nc[0] >= 0 && nl.m_cap <= kStageSlots;
+    if (staged) {
+        int rc = cuda_fail(cudaFuncSetAttribute(k_site<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                           "site kernel shared memory");
+        if (rc) return rc;
+    }
+    auto kern = staged ? k_site<true> : k_site<false>;
+    kern<<<nblocks, kSiteThreads, staged ? smem : (((size_t)n_par + 31) / 32 * 32) * sizeof(float), st>>>(n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box,
                                                                   a.z, n_par, P, nl.pf, e_atom, e_partials, d_err);
     return cuda_fail(cudaGetLastError(), "site kernel");
 }
@@ -137,17 +176,12 @@ int launch_assemble(const AssembleArgs& a, NeighborList& nl, int n, float* force
 {
     nblocks = blocks_for(n, kAsmThreads);
     const float rc2 = a.rc_max * a.rc_max;
-    if (a.vel) {
-        ncomp = 13;
-        k_assemble<true><<<nblocks, kAsmThreads, 0, st>>>(n, nl.m_cap, rc2, nl.count, nl.nbr, nl.rev, nl.xh, nl.xl,
-                                                          a.box, nl.pf, force, virial_atom, partials, d_err, a.vel,
-                                                          a.half_dt_over_m, a.ke_factor);
-    } else {
-        ncomp = 9;
-        k_assemble<false><<<nblocks, kAsmThreads, 0, st>>>(n, nl.m_cap, rc2, nl.count, nl.nbr, nl.rev, nl.xh, nl.xl,
-                                                           a.box, nl.pf, force, virial_atom, partials, d_err,
-                                                           nullptr, 0.0, 0.0);
-    }
+    const bool md = a.vel != nullptr;
+    ncomp = md ? 13 : 9;
+    auto kern = md ? k_assemble<true> : k_assemble<false>;
+    kern<<<nblocks, kAsmThreads, 0, st>>>(n, nl.m_cap, rc2, nl.count, nl.nbr, nl.rev, nl.xh, nl.xl, a.box, nl.pf,
+                                          force, virial_atom, partials, d_err, md ? a.vel : nullptr,
+                                          md ? a.half_dt_over_m : 0.0, md ? a.ke_factor : 0.0);
     return cuda_fail(cudaGetLastError(), "assemble kernel");
 }
 

@@ -1,7 +1,7 @@
 // nep_internal.cuh -- shared definitions of the sm_103a NEP library.
 //
 // Data layout in device memory (n atoms, M = neighbour capacity per atom):
-//   positions        FP64 [3][n] (caller) + FP32 hi/lo split xh, xl [3][n]
+//   positions        FP64 [3][n] (caller) + FP32 hi/lo split xh, xl [n] float4
 //   neighbour list   int32 nbr[M][n] = j | image_code << 24, count[n]
 //                    int32 rev[M][n] = slot of i in j's list (reverse pair)
 //   partial forces   FP32 pf[M][3][n] = dU_i/dr_ij (Eq. 23), slot-major
@@ -100,22 +100,36 @@ __host__ __device__ __forceinline__ void pair_vector(int i, int j, int code, con
                     b.Ll[2]);
 }
 
+// FP32 hi/lo positions are stored as one float4 record (x, y, z, 0) per atom
+// for each part, so a neighbour's coordinates arrive in two 16-byte loads.
 __host__ __device__ __forceinline__ void load_pos(const float* __restrict__ xh, const float* __restrict__ xl, int n, int i,
                                          float (&h)[3], float (&l)[3])
 {
-    h[0] = NEP_LDG(xh + i);
-    h[1] = NEP_LDG(xh + n + i);
-    h[2] = NEP_LDG(xh + 2 * n + i);
-    l[0] = NEP_LDG(xl + i);
-    l[1] = NEP_LDG(xl + n + i);
-    l[2] = NEP_LDG(xl + 2 * n + i);
+    (void)n;
+    const float4 a = NEP_LDG(reinterpret_cast<const float4*>(xh) + i);
+    const float4 b = NEP_LDG(reinterpret_cast<const float4*>(xl) + i);
+    h[0] = a.x;
+    h[1] = a.y;
+    h[2] = a.z;
+    l[0] = b.x;
+    l[1] = b.y;
+    l[2] = b.z;
 }
+
 
 // Split an FP64 value into FP32 hi + lo.
 __host__ __device__ __forceinline__ void split_hilo(double x, float& h, float& l)
 {
     h = (float)x;
     l = (float)(x - (double)h);
+}
+
+__host__ __device__ __forceinline__ void store_pos(float* __restrict__ xh, float* __restrict__ xl, int i, const double (&x)[3])
+{
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) split_hilo(x[d], h[d], l[d]);
+    reinterpret_cast<float4*>(xh)[i] = make_float4(h[0], h[1], h[2], 0.f);
+    reinterpret_cast<float4*>(xl)[i] = make_float4(l[0], l[1], l[2], 0.f);
 }
 
 // Block-wide sum of K doubles; thread 0 writes out[k].  blockDim.x must be a
@@ -221,9 +235,15 @@ struct Profiler {
     // returns the slot to bracket a launch of `kind`, or nullptr when off/full
     Slot* begin(int kind, cudaStream_t st);
     void end(Slot* s, cudaStream_t st);
-    int read(double* ms, long long* cnt);  // ms[2], cnt[2]; synchronises
+    int read(double* ms, long long* cnt);  // ms[NEP_PROFILE_KINDS], cnt[...]; synchronises
     void release();
 };
+// tensor-core population network (nep_pop_tc.cu)
+size_t pop_tc_packed_bytes(int P);
+int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
+                  const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
+                  cudaStream_t st);
+
 }  // namespace nep
 
 struct nep_model {

@@ -34,7 +34,7 @@ __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float d2 = 0.f;
     if (i < n) {
-        double dd = 0.0;
+        double dd = 0.0, xn[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const size_t o = (size_t)c * n + i;
@@ -42,13 +42,11 @@ __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__
             const double xc = x[o] + dt * vc;
             v[o] = vc;
             x[o] = xc;
-            float h, l;
-            split_hilo(xc, h, l);
-            xh[o] = h;
-            xl[o] = l;
+            xn[c] = xc;
             const double d = xc - x_ref[o];
             dd += d * d;
         }
+        store_pos(xh, xl, i, xn);
         d2 = (float)dd;
     }
 #pragma unroll
@@ -240,13 +238,17 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     const double hdtm = 0.5 * dt / (md->mass * conv);
     const float thresh = 0.5f * md->skin;
     for (int s = 0; s < n_steps; ++s) {
+        Profiler::Slot* pk = m->prof.begin(NEP_PROFILE_STEP, st);
         k_kick_drift<<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, md->ws.force, hdtm, dt, nl.xh, nl.xl, md->x_ref,
                                                          md->ctl);
         k_decide<<<1, 1, 0, st>>>(md->ctl, thresh * thresh, md->rebuilds);
+        m->prof.end(pk, st);
+        pk = m->prof.begin(NEP_PROFILE_NEIGHBOR, st);
         if ((rc = build_neighbor_list(nl, md->box, n, pos, true, md->x_ref, md->r_list, m->d_err, gate, st)))
             return rc;
+        m->prof.end(pk, st);
         int b1 = 0, b2 = 0, c2 = 0;
-        Profiler::Slot* ps = m->prof.begin(0, st);
+        Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, st);
         if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
         m->prof.end(ps, st);
         AssembleArgs aa{};
@@ -256,12 +258,14 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         aa.half_dt_over_m = hdtm;
         aa.ke_factor = 0.5 * md->mass * conv;
         aa.heat = heat != nullptr;
-        ps = m->prof.begin(1, st);
+        ps = m->prof.begin(NEP_PROFILE_ASSEMBLE, st);
         if ((rc = launch_assemble(aa, nl, n, md->ws.force, nullptr, part_a, m->d_err, st, b2, c2))) return rc;
         m->prof.end(ps, st);
+        pk = m->prof.begin(NEP_PROFILE_STEP, st);
         if ((rc = launch_reduce(part_e, b1, 1, md->red, st))) return rc;
         if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
         k_md_finish<<<1, 32, 0, st>>>(md->red, thermo, heat, md->ctl);
+        m->prof.end(pk, st);
         if ((rc = cuda_fail(cudaGetLastError(), "md step kernels"))) return rc;
     }
     return NEP_OK;

@@ -37,6 +37,7 @@ __global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c[3];
+    double wx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double L = b.L[d];
@@ -48,15 +49,13 @@ __global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double
             pos[(size_t)d * n + i] = w;
             if (x_ref) x_ref[(size_t)d * n + i] = w;
         }
-        float h, l;
-        split_hilo(w, h, l);
-        xh[(size_t)d * n + i] = h;
-        xl[(size_t)d * n + i] = l;
+        wx[d] = w;
         if (b.nc[0] > 0) {
             int ci = (int)(w * (double)b.nc[d] / L);
             c[d] = ci < 0 ? 0 : (ci >= b.nc[d] ? b.nc[d] - 1 : ci);
         }
     }
+    store_pos(xh, xl, i, wx);
     if (b.nc[0] > 0) {
         const int cid = (c[0] * b.nc[1] + c[1]) * b.nc[2] + c[2];
         atom_cell[i] = cid;
@@ -154,73 +153,130 @@ __device__ void sort_near_first(int i, int n, int cnt, int* __restrict__ nbr, fl
     }
 }
 
-// One thread per atom.  Each thread keeps its accepted neighbours sorted by
-// distance in its own column of shared memory (entry k of thread t at
-// k * blockDim + t, so the lanes of a warp never share a bank) and writes the
-// sorted list out once.  Ties keep the candidate order (stable insertion).
-__global__ void k_verlet_cells(int n, int m_cap, float rv2, const float* __restrict__ xh,
-                               const float* __restrict__ xl, const int* __restrict__ atom_cell,
-                               const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
-                               int* __restrict__ count, int* __restrict__ nbr, float* __restrict__ key, unsigned* err,
-                               Box b, const unsigned* gate)
+// One warp per atom.  The candidates of the 27 neighbouring cells are
+// numbered consecutively (cell by cell, atom index order inside a cell) and
+// the lanes take them 32 at a time; accepted pairs are compacted in candidate
+// order with a ballot into the warp's shared buffer, which is then sorted by
+// (squared distance, packed index) with a bitonic network and written out.
+// Sorting on the pair of keys makes the order unique, hence deterministic.
+constexpr int kVerletWarps = 4;
+
+__device__ __forceinline__ bool pair_greater(float ka, int va, float kb, int vb)
+{
+    return ka > kb || (ka == kb && va > vb);
+}
+
+__global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m_cap, int lcap, float rv2,
+                                                                   const float* __restrict__ xh,
+                                                                   const float* __restrict__ xl,
+                                                                   const int* __restrict__ atom_cell,
+                                                                   const int* __restrict__ cell_start,
+                                                                   const int* __restrict__ cell_atoms,
+                                                                   int* __restrict__ count, int* __restrict__ nbr,
+                                                                   float* __restrict__ key, unsigned* err, Box b,
+                                                                   const unsigned* gate)
 {
     if (gated_off(gate)) return;
-    extern __shared__ float s_list[];
-    const int T = blockDim.x, tid = threadIdx.x;
-    float* s_key = s_list;
-    int* s_val = reinterpret_cast<int*>(s_list + (size_t)m_cap * T);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    extern __shared__ float s_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // per warp: lcap keys, lcap values, 28 prefix sums, 27 starts, 27 codes
+    float* skey = s_raw + (size_t)warp * (2 * lcap + 96);
+    int* sval = reinterpret_cast<int*>(skey + lcap);
+    int* pre = sval + lcap;
+    int* cst = pre + 32;
+    int* ccode = cst + 32;
+    const int i = blockIdx.x * kVerletWarps + warp;
+    if (i >= n) return;  // whole warp
     float hi[3], li[3];
     load_pos(xh, xl, n, i, hi, li);
     const int cid = atom_cell[i];
     const int cz = cid % b.nc[2];
     const int cy = (cid / b.nc[2]) % b.nc[1];
     const int cx = cid / (b.nc[2] * b.nc[1]);
-    int cnt = 0;
-    for (int ox = -1; ox <= 1; ++ox) {
-        int x2 = cx + ox, sx = 0;
+    // lane c < 27 describes neighbouring cell c (x slowest, z fastest)
+    int ccount = 0;
+    if (lane < 27) {
+        int x2 = cx + lane / 9 - 1, y2 = cy + (lane / 3) % 3 - 1, z2 = cz + lane % 3 - 1;
+        int sx = 0, sy = 0, sz = 0;
         if (x2 < 0) { x2 += b.nc[0]; sx = -1; } else if (x2 >= b.nc[0]) { x2 -= b.nc[0]; sx = 1; }
-        for (int oy = -1; oy <= 1; ++oy) {
-            int y2 = cy + oy, sy = 0;
-            if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
-            for (int oz = -1; oz <= 1; ++oz) {
-                int z2 = cz + oz, sz = 0;
-                if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
-                const int code = image_code(sx, sy, sz);
-                const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
-                const int e = cell_start[c2 + 1];
-                for (int t = cell_start[c2]; t < e; ++t) {
-                    const int j = cell_atoms[t];
-                    if (j == i && code == kImgCenter) continue;
-                    float hj[3], lj[3];
-                    load_pos(xh, xl, n, j, hj, lj);
-                    float rx, ry, rz;
-                    pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
-                    const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    if (d2 < rv2) {
-                        if (cnt < m_cap) {
-                            int q = cnt - 1;
-                            while (q >= 0 && s_key[q * T + tid] > d2) {
-                                s_key[(q + 1) * T + tid] = s_key[q * T + tid];
-                                s_val[(q + 1) * T + tid] = s_val[q * T + tid];
-                                --q;
-                            }
-                            s_key[(q + 1) * T + tid] = d2;
-                            s_val[(q + 1) * T + tid] = j | (code << 24);
-                        }
-                        ++cnt;
-                    }
-                }
+        if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
+        if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
+        const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
+        cst[lane] = cell_start[c2];
+        ccount = cell_start[c2 + 1] - cst[lane];
+        ccode[lane] = image_code(sx, sy, sz);
+    }
+    // exclusive prefix of the cell sizes
+    int incl = ccount;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane < 28) pre[lane] = incl - ccount;
+    __syncwarp();
+    const int total = pre[27];
+    int cnt = 0;
+    for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        bool accept = false;
+        int value = 0;
+        float d2 = 0.f;
+        if (idx < total) {
+            int c = 0;  // last cell whose prefix is <= idx
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (c + step < 27 && pre[c + step] <= idx) c += step;
+            const int j = cell_atoms[cst[c] + idx - pre[c]];
+            const int code = ccode[c];
+            if (!(j == i && code == kImgCenter)) {
+                float hj[3], lj[3];
+                load_pos(xh, xl, n, j, hj, lj);
+                float rx, ry, rz;
+                pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
+                d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                accept = d2 < rv2;
+                value = j | (code << 24);
             }
         }
+        const unsigned mask = __ballot_sync(0xffffffffu, accept);
+        const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+        if (accept && pos < lcap) {
+            skey[pos] = d2;
+            sval[pos] = value;
+        }
+        cnt += __popc(mask);
     }
-    count[i] = cnt;
-    if (cnt > m_cap) atomicOr(err, kErrOverflow);
+    __syncwarp();
+    if (lane == 0) count[i] = cnt;
+    if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
     const int m = cnt < m_cap ? cnt : m_cap;
-    for (int k = 0; k < m; ++k) {
-        nbr[(size_t)k * n + i] = s_val[k * T + tid];
-        key[(size_t)k * n + i] = s_key[k * T + tid];
+    int S = 1;
+    while (S < (cnt < lcap ? cnt : lcap)) S <<= 1;
+    for (int t = (cnt < lcap ? cnt : lcap) + lane; t < S; t += 32) {
+        skey[t] = 3.0e38f;
+        sval[t] = 0x7fffffff;
+    }
+    __syncwarp();
+    for (int size = 2; size <= S; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = lane; t < S / 2; t += 32) {
+                const int lo = 2 * stride * (t / stride) + (t % stride), hi2 = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const float ka = skey[lo], kb = skey[hi2];
+                const int va = sval[lo], vb = sval[hi2];
+                if (pair_greater(ka, va, kb, vb) == asc) {
+                    skey[lo] = kb;
+                    sval[lo] = vb;
+                    skey[hi2] = ka;
+                    sval[hi2] = va;
+                }
+            }
+            __syncwarp();
+        }
+    for (int k = lane; k < m; k += 32) {
+        nbr[(size_t)k * n + i] = sval[k];
+        key[(size_t)k * n + i] = skey[k];
     }
 }
 
@@ -311,18 +367,13 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool
                                                   d_gate);
         k_sort_cells<<<blocks_for(ncell, T), T, 0, st>>>(ncell, nl.cell_start, nl.cell_atoms, nl.cell_count,
                                                          nl.cell_fill, d_gate);
-        // per-thread sorted lists in shared memory: m_cap x 8 bytes per thread
-        const int TV = 64;
-        const size_t smem = (size_t)nl.m_cap * TV * (sizeof(float) + sizeof(int));
-        if (smem > 48 * 1024) {
-            int rc = cuda_fail(cudaFuncSetAttribute(k_verlet_cells, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem),
-                               "neighbour-list shared memory");
-            if (rc) return rc;
-        }
-        k_verlet_cells<<<blocks_for(n, TV), TV, smem, st>>>(n, nl.m_cap, rv2, nl.xh, nl.xl, nl.atom_cell,
-                                                            nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
-                                                            d_err, b, d_gate);
+        // per-warp list buffer: a power of two >= m_cap entries of (key, value)
+        int lcap = 32;
+        while (lcap < nl.m_cap) lcap <<= 1;
+        const size_t smem = (size_t)kVerletWarps * (2 * lcap + 96) * sizeof(float);
+        k_verlet_cells<<<blocks_for(n, kVerletWarps), 32 * kVerletWarps, smem, st>>>(
+            n, nl.m_cap, lcap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
+            d_err, b, d_gate);
     } else {
         k_verlet_brute<<<blocks_for(n, 128), 128, 0, st>>>(n, nl.m_cap, rv2, nl.xh, nl.xl, nl.count, nl.nbr, nl.pf,
                                                            d_err, b, d_gate);

@@ -1,0 +1,345 @@
+// nep_pop_tc.cu -- the SNES population network on the tensor cores (sm_103a).
+//
+// For a population of P parameter vectors z_k and all N training atoms, the
+// network of Eqs. 21-22 and its input gradient are two dense contractions:
+//   H[i, (k, mu)] = sum_nu q_i,nu w1_k,mu,nu            (GEMM 1, K = 32)
+//   x = tanh(H - b1), U_ki = sum_mu w2_k,mu x - b2_k,  D_ki,mu = w2_k,mu (1 - x^2)
+//   G_k[i, nu] = sum_mu D_ki,mu w1_k,mu,nu              (GEMM 2 per member, K = 30 -> 32)
+// One CTA owns 128 atoms.  Members go in groups of 4: GEMM 1 has N = 4 x 30 =
+// 120 (-> 128) columns of TMEM, GEMM 2 writes 4 x 32 columns of a second TMEM
+// region; 256 columns per CTA leave room for two CTAs per SM.  Operands are
+// split BF16 (hi + lo) in shared memory (canonical K-major layout,
+// nep_tc.cuh); accumulation is FP32 in TMEM.  One thread issues the MMAs and commits them
+// to an mbarrier; all waits are bounded (a timeout is latched as an error and
+// the CTA still frees its TMEM).
+#include <cuda_bf16.h>
+
+#include "nep_internal.cuh"
+#include "nep_tc.cuh"
+
+namespace nep {
+namespace {
+
+constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr int kTile = 128;       // atoms per CTA (TMEM lanes)
+constexpr int kPopThreads = 256; // two warps per TMEM lane quarter
+
+__device__ __forceinline__ void put_bf16(unsigned char* base, int row, int k, float v)
+{
+    *reinterpret_cast<__nv_bfloat16*>(base + tc::kmajor_offset(row, k)) = __float2bfloat16_rn(v);
+}
+
+// ----------------------------------------------------------------- self-test
+// D (128 x N, FP32, row-major) = A (128 x 32 BF16 row-major) * B^T (B: N x 32
+// BF16 row-major), one tile, N a multiple of 16 in [16, 256].
+__global__ void __launch_bounds__(128) k_tc_selftest(const __nv_bfloat16* __restrict__ A,
+                                                     const __nv_bfloat16* __restrict__ B, int N,
+                                                     float* __restrict__ D, unsigned* err)
+{
+    __shared__ __align__(1024) unsigned char sA[kTile * 64];
+    __shared__ __align__(1024) unsigned char sB[256 * 64];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int t = threadIdx.x, warp = t >> 5;
+    for (int k = 0; k < 32; ++k)
+        *reinterpret_cast<__nv_bfloat16*>(sA + tc::kmajor_offset(t, k)) = A[t * 32 + k];
+    for (int r = t; r < N; r += blockDim.x)
+        for (int k = 0; k < 32; ++k) *reinterpret_cast<__nv_bfloat16*>(sB + tc::kmajor_offset(r, k)) = B[r * 32 + k];
+    if (t == 0) {
+        tc::mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, 256);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tmem_base;
+    if (t == 0) {
+        const uint32_t idesc = tc::idesc_bf16_f32(kTile, N);
+        for (int ks = 0; ks < 2; ++ks)
+            tc::mma_bf16(tb, tc::smem_desc(tc::smem_u32(sA) + ks * 256, 128, 512),
+                         tc::smem_desc(tc::smem_u32(sB) + ks * 256, 128, 512), idesc, ks > 0);
+        tc::mma_commit(&mbar);
+    }
+    const bool ok = __syncthreads_and(tc::mbar_wait(&mbar, 0, kMaxPolls)) != 0;
+    if (!ok && (t & 31) == 0) atomicOr(err, kErrTimeout);
+    tc::fence_after_sync();
+    if (ok) {
+        for (int c0 = 0; c0 < N; c0 += 8) {
+            uint32_t r[8];
+            tc::tmem_ld8(tb + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) D[(size_t)t * N + c0 + q] = __uint_as_float(r[q]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tb, 256);
+}
+
+// ----------------------------------------------------------------- population
+// Members go in groups of kGroup = 4.  Per group the operands are packed once
+// per evaluation (k_pack_tc) in the exact shared-memory layout, as split BF16
+// pairs hi + lo with hi = bf16(x), lo = bf16(x - hi).  GEMM 1 (which sets the
+// site energies) takes three MMAs, hi*hi + hi*lo + lo*hi, carrying ~16
+// mantissa bits instead of 8; GEMM 2 (forces, whose loss terms average the
+// rounding out) keeps D in BF16 and splits only W1 (two MMAs).  Every MMA is
+// BF16 x BF16 -> FP32.
+constexpr int kTcGroup = 4;
+constexpr int kW1Bytes = kTile * 64;     // GEMM-1 B: 128 rows (member, mu) x 32 nu
+constexpr int kW1tBytes = 32 * 64;       // GEMM-2 B per member: 32 nu x 32 mu
+// packed group record: w1 hi, w1 lo, w1t hi[4], w1t lo[4], b1[4][32], w2[4][32], b2[4]
+constexpr int kGroupBytes = 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes + (2 * kTcGroup * 32 + 4) * 4;
+
+struct PopSmem {
+    unsigned char q_hi[kTile * 64], q_lo[kTile * 64];
+    unsigned char grp[kGroupBytes];                        // the current group's packed record
+    unsigned char d_hi[kTcGroup][kTile * 64];  // GEMM-2 A (hi part only)
+    uint64_t mbar;
+    uint32_t tmem_base;
+};
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ void put_split(unsigned char* hi_base, unsigned char* lo_base, int row, int k, float v)
+{
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    const uint32_t o = tc::kmajor_offset(row, k);
+    *reinterpret_cast<__nv_bfloat16*>(hi_base + o) = h;
+    *reinterpret_cast<__nv_bfloat16*>(lo_base + o) = l;
+}
+
+// One thread per (group, element) of the packed records.
+__global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ W1t, const float* __restrict__ b1t,
+                          const float* __restrict__ w2t, const float* __restrict__ b2t,
+                          unsigned char* __restrict__ packed)
+{
+    const int groups = (P + kTcGroup - 1) / kTcGroup;
+    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32 + 1;  // w1 elems, w1t elems, bias rows, b2
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= groups * per) return;
+    const int g = e / per, r = e % per, k0 = g * kTcGroup;
+    const int mg = min(kTcGroup, P - k0);
+    unsigned char* rec = packed + (size_t)g * kGroupBytes;
+    if (r < kTile * 32) {  // GEMM-1 B row = (member, mu), column nu
+        const int row = r / 32, nu = r % 32, m = row / n_neu, mu = row % n_neu;
+        const bool on = m < mg && row < mg * n_neu;
+        put_split(rec, rec + kW1Bytes, row, nu, on ? W1t[((size_t)mu * kNdes + nu) * P + k0 + m] : 0.f);
+        return;
+    }
+    int t = r - kTile * 32;
+    if (t < kTcGroup * 32 * 32) {  // GEMM-2 B of member m: row nu, column mu
+        const int m = t / 1024, nu = (t / 32) % 32, mu = t % 32;
+        const bool on = m < mg && mu < n_neu;
+        unsigned char* hi = rec + 2 * kW1Bytes + m * kW1tBytes;
+        put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, on ? W1t[((size_t)mu * kNdes + nu) * P + k0 + m] : 0.f);
+        return;
+    }
+    t -= kTcGroup * 32 * 32;
+    float* fb = reinterpret_cast<float*>(rec + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
+    if (t < kTcGroup * 32) {
+        const int m = t / 32, mu = t % 32;
+        const bool on = m < mg && mu < n_neu;
+        fb[m * 32 + mu] = on ? b1t[(size_t)mu * P + k0 + m] : 0.f;
+        fb[kTcGroup * 32 + m * 32 + mu] = on ? w2t[(size_t)mu * P + k0 + m] : 0.f;
+        if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? b2t[k0 + m] : 0.f;
+    }
+}
+
+// Issue the split-BF16 products of one K = 32 tile pair into d_tmem:
+// a_hi b_hi + a_hi b_lo (+ a_lo b_hi when a_lo is given).
+__device__ __forceinline__ void mma_split(uint32_t d_tmem, const unsigned char* a_hi, const unsigned char* a_lo,
+                                          const unsigned char* b_hi, const unsigned char* b_lo, uint32_t idesc)
+{
+    const unsigned char* as[3] = {a_hi, a_hi, a_lo};
+    const unsigned char* bs[3] = {b_hi, b_lo, b_hi};
+    const int np = a_lo ? 3 : 2;
+    for (int p = 0; p < np; ++p)
+        for (int ks = 0; ks < 2; ++ks)
+            tc::mma_bf16(d_tmem, tc::smem_desc(tc::smem_u32(as[p]) + ks * 256, 128, 512),
+                         tc::smem_desc(tc::smem_u32(bs[p]) + ks * 256, 128, 512), idesc, p > 0 || ks > 0);
+}
+
+// One CTA per 128 atoms.  Outputs U [N][P] (FP64) and G [N][32][Pst] (FP32).
+__global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, int n_neu,
+                                                        const float* __restrict__ q,
+                                                        const unsigned char* __restrict__ packed,
+                                                        float* __restrict__ G, double* __restrict__ U, unsigned* err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    PopSmem& S = *reinterpret_cast<PopSmem*>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int quarter = warp & 3;            // TMEM lane quarter of this warp
+    const int half = warp >> 2;              // members {2 half, 2 half + 1} of a group
+    const int row = quarter * 32 + lane;     // tile row = TMEM lane
+    const int i = blockIdx.x * kTile + row;  // atom
+    const bool valid = i < N;
+
+    for (int k = half * 16; k < half * 16 + 16; ++k) put_split(S.q_hi, S.q_lo, row, k, valid ? q[(size_t)i * kNdes + k] : 0.f);
+    if (t == 0) {
+        tc::mbar_init(&S.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&S.tmem_base, 256);
+        tc::tmem_relinquish();
+    }
+    uint32_t phase = 0;
+    bool ok = true;
+    const int groups = (P + kTcGroup - 1) / kTcGroup;
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = S.tmem_base;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    const unsigned char* w1_hi = S.grp;
+    const unsigned char* w1_lo = S.grp + kW1Bytes;
+    const unsigned char* w1t_hi = S.grp + 2 * kW1Bytes;
+    const unsigned char* w1t_lo = w1t_hi + kTcGroup * kW1tBytes;
+    const float* fb = reinterpret_cast<const float*>(S.grp + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
+
+    for (int gi = 0; gi < groups && ok; ++gi) {
+        const int k0 = gi * kTcGroup;
+        const int mg = min(kTcGroup, P - k0);
+        const int n1 = ((mg * n_neu + 15) / 16) * 16;
+        // ---- the group's packed operands (16-byte copies)
+        const uint4* src = reinterpret_cast<const uint4*>(packed + (size_t)gi * kGroupBytes);
+        uint4* dst = reinterpret_cast<uint4*>(S.grp);
+        for (int e = t; e < kGroupBytes / 16; e += blockDim.x) dst[e] = src[e];
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // ---- GEMM 1: H = Q W1^T into TMEM columns [0, n1)
+        if (t == 0) {
+            mma_split(tb, S.q_hi, S.q_lo, w1_hi, w1_lo, tc::idesc_bf16_f32(kTile, n1));
+            tc::mma_commit(&S.mbar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&S.mbar, phase, kMaxPolls)) != 0;
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (!ok) {
+            if (t == 0) atomicOr(err, kErrTimeout);
+            break;
+        }
+        // ---- epilogue 1: members {2 half, 2 half + 1}
+        for (int m = 2 * half; m < min(mg, 2 * half + 2); ++m) {
+            float u = 0.f;
+            const int c_lo = m * n_neu;
+            for (int c0 = (c_lo / 8) * 8; c0 < c_lo + n_neu; c0 += 8) {
+                uint32_t r[8];
+                tc::tmem_ld8(tb + lane_base + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int qd = 0; qd < 8; ++qd) {
+                    const int c = c0 + qd;
+                    if (c < c_lo || c >= c_lo + n_neu) continue;
+                    const int mu = c - c_lo;
+                    const float x = tanhf(__uint_as_float(r[qd]) - fb[m * 32 + mu]);
+                    const float w2 = fb[kTcGroup * 32 + m * 32 + mu];
+                    u = fmaf(w2, x, u);
+                    *reinterpret_cast<__nv_bfloat16*>(S.d_hi[m] + tc::kmajor_offset(row, mu)) =
+                        __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
+                }
+            }
+            for (int mu = n_neu; mu < 32; ++mu)
+                *reinterpret_cast<__nv_bfloat16*>(S.d_hi[m] + tc::kmajor_offset(row, mu)) = __float2bfloat16_rn(0.f);
+            if (valid) U[(size_t)i * P + k0 + m] = (double)u - (double)fb[2 * kTcGroup * 32 + m];
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // ---- GEMM 2: G_m = D_m W1_m into TMEM columns [128 + 32 m, +32)
+        if (t == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(kTile, 32);
+            for (int m = 0; m < mg; ++m)
+                mma_split(tb + 128u + 32u * (uint32_t)m, S.d_hi[m], nullptr, w1t_hi + m * kW1tBytes,
+                          w1t_lo + m * kW1tBytes, idesc);
+            tc::mma_commit(&S.mbar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&S.mbar, phase, kMaxPolls)) != 0;
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (!ok) {
+            if (t == 0) atomicOr(err, kErrTimeout);
+            break;
+        }
+        // ---- epilogue 2: G[i][nu][k0 + m], this warp takes nu in [16 half, 16 half + 16)
+        for (int nc = 2 * half; nc < 2 * half + 2; ++nc) {
+            float g[kTcGroup][8];
+#pragma unroll
+            for (int m = 0; m < kTcGroup; ++m) {
+                if (m < mg) {
+                    uint32_t r[8];
+                    tc::tmem_ld8(tb + lane_base + 128u + 32u * (uint32_t)m + 8u * (uint32_t)nc, r);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int qd = 0; qd < 8; ++qd) g[m][qd] = __uint_as_float(r[qd]);
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int qd = 0; qd < 8; ++qd) {
+                    float* out = G + ((size_t)i * kNdes + nc * 8 + qd) * Pst + k0;
+                    if (mg == kTcGroup)
+                        *reinterpret_cast<float4*>(out) = make_float4(g[0][qd], g[1][qd], g[2][qd], g[3][qd]);
+                    else
+                        for (int m = 0; m < mg; ++m) out[m] = g[m][qd];
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tb, 256);
+}
+
+}  // namespace
+
+size_t pop_tc_packed_bytes(int P) { return (size_t)((P + kTcGroup - 1) / kTcGroup) * kGroupBytes; }
+
+int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
+                  const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
+                  cudaStream_t st)
+{
+    if (n_neu > 32 || Pst % 4 != 0) {
+        set_error("tensor-core population path needs n_neu <= 32 and a member stride that is a multiple of 4");
+        return NEP_ERR_UNSUPPORTED;
+    }
+    const int groups = (P + kTcGroup - 1) / kTcGroup;
+    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32 + 1;
+    k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
+    const size_t smem = sizeof(PopSmem);
+    int rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                       "population kernel shared memory");
+    if (rc) return rc;
+    k_pop_tc<<<(N + kTile - 1) / kTile, kPopThreads, smem, st>>>(N, P, Pst, n_neu, q, packed, G, U, err);
+    return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
+}
+
+}  // namespace nep
+
+extern "C" int nep_tc_selftest(const void* A, const void* B, int N, float* D, unsigned* err, void* stream)
+{
+    if (!A || !B || !D || !err || N < 16 || N > 256 || N % 16 != 0) {
+        nep::set_error("nep_tc_selftest: bad arguments (N a multiple of 16 in [16, 256])");
+        return NEP_ERR_ARG;
+    }
+    nep::k_tc_selftest<<<1, 128, 0, (cudaStream_t)stream>>>(static_cast<const __nv_bfloat16*>(A),
+                                                            static_cast<const __nv_bfloat16*>(B), N, D, err);
+    return nep::cuda_fail(cudaGetLastError(), "tensor-core self-test kernel");
+}

@@ -273,31 +273,60 @@ __host__ __device__ __forceinline__ void network(const float* w, int n_neu, cons
     U_lo = c + e;
 }
 
-// Everything atom i contributes in the first force pass: site energy and the
-// partial forces of all its list slots (written to pf[k][c][i] for slots
-// within max(rc_R, rc_A); other slots are left untouched).
+// One neighbour slot: packed index and the neighbour's hi/lo position.  The
+// loops below fetch slot k+1 (or k-1) before working on slot k so the loads
+// overlap the arithmetic of the current slot.
+struct NbSlot {
+    int v;
+    float h[3], l[3];
+};
+
+// Slot k of the atom is slots[k * stride + idx]: the global list (stride n,
+// idx i) or a block's staged copy in shared memory (stride blockDim, idx tid).
+struct SlotTable {
+    const int* slots;
+    int stride;
+    int idx;
+};
+
+__host__ __device__ __forceinline__ void fetch_slot(const SlotTable& T, const float* __restrict__ xh,
+                                                    const float* __restrict__ xl, int n, int k, int cnt, NbSlot& s)
+{
+    if (k >= 0 && k < cnt) {
+        s.v = T.slots[(size_t)k * T.stride + T.idx];
+        load_pos(xh, xl, n, s.v & 0xFFFFFF, s.h, s.l);
+    }
+}
+
+// Parameters of the per-atom site functions.
 struct SiteParams {
     const float* w;  // parameters (shared memory on the device)
     int n_neu;
     float rcR, rcA, rcR2, rcA2, inv_rcR, inv_rcA;
 };
 
-__host__ __device__ __forceinline__ void site_partial_forces(int i, bool active, int n, int m_cap,
-                                                             const int* __restrict__ count,
-                                                             const int* __restrict__ nbr,
-                                                             const float* __restrict__ xh,
-                                                             const float* __restrict__ xl, const Box& box,
-                                                             const SiteParams& P, float* __restrict__ pf,
-                                                             float& U_hi, float& U_lo)
-{
-    float hi[3], li[3];
-    if (active) load_pos(xh, xl, n, i, hi, li);
-    const int cnt = active ? imin(count[i], m_cap) : 0;
+// Where the partial force of slot k goes: base[k * slot_stride + c * comp_stride].
+// The MD list stores pf[k][c][i] (base = pf + i, strides 3n and n); a
+// training-set CSR list stores pf[p][c] (base = pf + 3 p0, strides 3 and 1).
+struct PfOut {
+    float* base;
+    size_t slot_stride;
+    size_t comp_stride;
+};
 
+// Pass 1 of atom i: the descriptor vector q (Eqs. 12-13 through the harmonic
+// sums) and the harmonic sums S_nlm themselves.  Every lane of a warp must
+// call it (inactive lanes pass cnt = 0): the ranks are walked in step.
+__host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt, const SlotTable& nbr,
+                                                          const float* __restrict__ xh,
+                                                          const float* __restrict__ xl, const Box& box,
+                                                          const SiteParams& P, const float (&hi)[3],
+                                                          const float (&li)[3], float (&q)[kNdes],
+                                                          float (&S)[kNA][kLM])
+{
     // radial sums are compensated (Kahan): q_0 ~ 4 accumulates ~28 terms and
     // its plain FP32 rounding dominates the site-energy error budget
     float qR[kNR], qC[kNR];
-    float S[kNA][kLM];
 #pragma unroll
     for (int a = 0; a < kNR; ++a) qR[a] = qC[a] = 0.f;
 #pragma unroll
@@ -305,22 +334,23 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
 #pragma unroll
         for (int b = 0; b < kLM; ++b) S[a][b] = 0.f;
 
-    // pass 1: descriptor sums.  Slots are sorted by increasing distance; walk
-    // the ranks downwards so the largest (nearest) terms are added last, with
-    // all lanes of a warp at the same rank (inactive lanes pass count 0).
+    // Slots are sorted by increasing distance (MD lists); walk the ranks
+    // downwards so the largest (nearest) terms are added last, with all lanes
+    // of a warp at the same rank.
 #ifdef __CUDA_ARCH__
     const int kmax = __reduce_max_sync(0xffffffffu, cnt);
 #else
     const int kmax = cnt;
 #endif
+    NbSlot nx;
+    fetch_slot(nbr, xh, xl, n, kmax - 1, cnt, nx);
     for (int k = kmax - 1; k >= 0; --k) {
+        const NbSlot cur = nx;
+        fetch_slot(nbr, xh, xl, n, k - 1, cnt, nx);
         if (k >= cnt) continue;
-        const int v = nbr[(size_t)k * n + i];
-        const int j = v & 0xFFFFFF;
-        float hj[3], lj[3];
-        load_pos(xh, xl, n, j, hj, lj);
+        const int j = cur.v & 0xFFFFFF;
         float rx, ry, rz;
-        pair_vector(i, j, v >> 24, hi, li, hj, lj, box, rx, ry, rz);
+        pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, rx, ry, rz);
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         if (d2 < P.rcR2) {
             const float d = sqrtf(d2);
@@ -344,7 +374,6 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
     }
 
     // descriptor vector: q_nl = sum_m c_lm S_nlm^2 (compensated), n outer, l inner
-    float q[kNdes];
 #pragma unroll
     for (int a = 0; a < kNR; ++a) q[a] = qR[a] - qC[a];
 #pragma unroll
@@ -363,6 +392,22 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
 #pragma unroll
         for (int l = 0; l < kLmax; ++l) q[kNR + a * kLmax + l] -= qc[l];
     }
+}
+
+// Everything atom i contributes in the first force pass: site energy and the
+// partial forces dU_i/dr_ij of its first cnt slots (written through `out` for
+// slots within max(rc_R, rc_A); other slots are left untouched).
+__host__ __device__ __forceinline__ void site_partial_forces(int i, bool active, int n, int cnt,
+                                                             const SlotTable& nbr, const float* __restrict__ xh,
+                                                             const float* __restrict__ xl, const Box& box,
+                                                             const SiteParams& P, const PfOut& out, float& U_hi,
+                                                             float& U_lo)
+{
+    float hi[3], li[3];
+    if (active) load_pos(xh, xl, n, i, hi, li);
+    float q[kNdes];
+    float S[kNA][kLM];
+    site_descriptors(i, n, cnt, nbr, xh, xl, box, P, hi, li, q, S);
 
     float G[kNdes];
     network(P.w, P.n_neu, q, G, U_hi, U_lo);
@@ -381,13 +426,14 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
 
     const float rc2max = P.rcR2 > P.rcA2 ? P.rcR2 : P.rcA2;
     // pass 2: partial forces
+    NbSlot nx;
+    fetch_slot(nbr, xh, xl, n, 0, cnt, nx);
     for (int k = 0; k < cnt; ++k) {
-        const int v = nbr[(size_t)k * n + i];
-        const int j = v & 0xFFFFFF;
-        float hj[3], lj[3];
-        load_pos(xh, xl, n, j, hj, lj);
+        const NbSlot cur = nx;
+        fetch_slot(nbr, xh, xl, n, k + 1, cnt, nx);
+        const int j = cur.v & 0xFFFFFF;
         float rx, ry, rz;
-        pair_vector(i, j, v >> 24, hi, li, hj, lj, box, rx, ry, rz);
+        pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, rx, ry, rz);
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         if (!(d2 < rc2max)) continue;
         const float d = sqrtf(d2);
@@ -411,17 +457,17 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
             Vy = (Vy - uv * uy) * inv;
             Vz = (Vz - uv * uz) * inv;
         }
-        float* p = pf + (size_t)k * 3 * n + i;
+        float* p = out.base + (size_t)k * out.slot_stride;
         p[0] = fmaf(radial, ux, Vx);
-        p[(size_t)n] = fmaf(radial, uy, Vy);
-        p[(size_t)2 * n] = fmaf(radial, uz, Vz);
+        p[out.comp_stride] = fmaf(radial, uy, Vy);
+        p[2 * out.comp_stride] = fmaf(radial, uz, Vz);
     }
 }
 
 // Force and per-atom virial of atom i from the stored partial forces:
 //   F_i = sum_j (p_ij - p_ji),  W_i^{ab} = sum_j r_ij^a p_ji^b   (Eqs. 4-6).
 __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, float rc2max,
-                                                       const int* __restrict__ count, const int* __restrict__ nbr,
+                                                       const int* __restrict__ count, const SlotTable& nbr,
                                                        const int* __restrict__ rev, const float* __restrict__ xh,
                                                        const float* __restrict__ xl, const Box& box,
                                                        const float* __restrict__ pf, float (&F)[3], float (&W)[9])
@@ -433,13 +479,14 @@ __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, 
     for (int a = 0; a < 3; ++a) F[a] = 0.f;
 #pragma unroll
     for (int a = 0; a < 9; ++a) W[a] = 0.f;
+    NbSlot nx;
+    fetch_slot(nbr, xh, xl, n, 0, cnt, nx);
     for (int k = 0; k < cnt; ++k) {
-        const int v = nbr[(size_t)k * n + i];
-        const int j = v & 0xFFFFFF;
-        float hj[3], lj[3];
-        load_pos(xh, xl, n, j, hj, lj);
+        const NbSlot cur = nx;
+        fetch_slot(nbr, xh, xl, n, k + 1, cnt, nx);
+        const int j = cur.v & 0xFFFFFF;
         float r[3];
-        pair_vector(i, j, v >> 24, hi, li, hj, lj, box, r[0], r[1], r[2]);
+        pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, r[0], r[1], r[2]);
         const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
         if (!(d2 < rc2max)) continue;
         const int kr = rev[(size_t)k * n + i];

@@ -35,8 +35,8 @@ constexpr size_t kOffNbr = kOffCount + align256(sizeof(int) * kStaticAtoms);
 constexpr size_t kOffRev = kOffNbr + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
 constexpr size_t kOffPf = kOffRev + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
 constexpr size_t kOffXh = kOffPf + align256(sizeof(float) * kStaticAtoms * kStaticSlots * 3);
-constexpr size_t kOffXl = kOffXh + align256(sizeof(float) * kStaticAtoms * 3);
-constexpr size_t kOffAtomCell = kOffXl + align256(sizeof(float) * kStaticAtoms * 3);
+constexpr size_t kOffXl = kOffXh + align256(sizeof(float) * kStaticAtoms * 4);
+constexpr size_t kOffAtomCell = kOffXl + align256(sizeof(float) * kStaticAtoms * 4);
 constexpr size_t kOffCellAtoms = kOffAtomCell + align256(sizeof(int) * kStaticAtoms);
 constexpr size_t kOffCellCount = kOffCellAtoms + align256(sizeof(int) * kStaticAtoms);
 constexpr size_t kOffCellStart = kOffCellCount + align256(sizeof(int) * (kStaticCells + 1));

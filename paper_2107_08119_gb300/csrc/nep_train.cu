@@ -16,7 +16,8 @@
 //   W_ki = sum_j r_ij (x) (G_kj . J_ji)                            (Eq. 6)
 // and the RMSEs of Eqs. 29-34.  Kernels per evaluation:
 //   k_pack      z_pop -> member-innermost weight layout
-//   k_mlp_f32   FP32 network per (atom pair, member): U, G [N][32][P]
+//   k_mlp_f32   FP32 network per (atom pair, member): U [N][P], G [N][32][Pst]
+//   k_pop_tc    the same network as two BF16 tensor-core GEMMs (nep_pop_tc.cu)
 //   k_contract  per (atom, member): F, W, |F - F_tar|^2, summed per chunk
 //   k_loss      per member: per-structure sums in a fixed order, RMSEs
 // SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r), k_snes_update.
@@ -25,7 +26,7 @@
 #include <new>
 #include <vector>
 
-#include "nep_site.cuh"
+#include "nep_dataset.cuh"
 
 namespace nep {
 namespace {
@@ -43,14 +44,16 @@ __global__ void k_ds_split(int N, const double* __restrict__ pos, const int* __r
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const Box b = boxes[sid[i]];
+    double wx[3];
     for (int d = 0; d < 3; ++d) {
         const double L = b.L[d];
         double x = pos[(size_t)d * N + i];
         double w = x - L * floor(x / L);
         if (w >= L) w -= L;
         if (w < 0.0) w = 0.0;
-        split_hilo(w, xh[(size_t)d * N + i], xl[(size_t)d * N + i]);
+        wx[d] = w;
     }
+    store_pos(xh, xl, i, wx);
 }
 
 __global__ void k_ds_list(int N, const int* __restrict__ sid, const int* __restrict__ sstart,
@@ -138,11 +141,6 @@ __global__ void k_ds_reverse(int N, const long long* __restrict__ pstart, const 
 
 // Descriptors of atom i and the Jacobians of its descriptor with respect to
 // each of its pair vectors r_ij, scattered to the reverse slots.
-struct PairRec {
-    float r[3];   // r_ij of the owning atom i (the vector from i to j)
-    float gd[8];  // g_n'(|r|) / |r|, radial orders n = 0..7 (0 beyond r_c^R)
-    float pad;
-};
 
 __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restrict__ boxes,
                           const float* __restrict__ xh, const float* __restrict__ xl,
@@ -281,7 +279,7 @@ __global__ void k_pack(int P, int n_neu, const float* __restrict__ z, float* __r
 
 // FP32 network, two atoms per thread (each weight load feeds two FMAs):
 // thread t -> atom pair a = t / P, member k = t % P.
-__global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int n_neu, const float* __restrict__ q,
+__global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_neu, const float* __restrict__ q,
                                                  const float* __restrict__ W1t, const float* __restrict__ b1t,
                                                  const float* __restrict__ w2t, const float* __restrict__ b2t,
                                                  float* __restrict__ G, double* __restrict__ U)
@@ -333,18 +331,18 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int n_neu, const 
     const double b2 = (double)b2t[k];
     U[i0 * P + k] = (double)s0 + (double)c0 - b2;
 #pragma unroll
-    for (int v = 0; v < kNdes; ++v) G[(i0 * kNdes + v) * P + k] = G0[v];
+    for (int v = 0; v < kNdes; ++v) G[(i0 * kNdes + v) * Pst + k] = G0[v];
     if (two) {
         U[i1 * P + k] = (double)s1 + (double)c1 - b2;
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) G[(i1 * kNdes + v) * P + k] = G1[v];
+        for (int v = 0; v < kNdes; ++v) G[(i1 * kNdes + v) * Pst + k] = G1[v];
     }
 }
 
 // One block per chunk of <= kChunkAtoms atoms of one structure; thread t ->
 // atom begin + t / P, member t % P.  Per chunk and member: sums of U, of
 // |F - F_tar|^2 and of the six virial components, in a fixed order.
-__global__ void __launch_bounds__(1024) k_contract(int N, int P, const int* __restrict__ chunk_begin,
+__global__ void __launch_bounds__(1024) k_contract(int N, int P, int Pst, const int* __restrict__ chunk_begin,
                                                    const int* __restrict__ chunk_end, const float* __restrict__ G,
                                                    const double* __restrict__ U, const float* __restrict__ B,
                                                    const long long* __restrict__ pstart, const int* __restrict__ pj,
@@ -359,12 +357,12 @@ __global__ void __launch_bounds__(1024) k_contract(int N, int P, const int* __re
     const int ia = t / P, k = t % P;
     const int i = begin + ia;
     if (ia < kChunkAtoms && i < end) {
-        const float* Gi = G + (size_t)i * kNdes * P + k;
+        const float* Gi = G + (size_t)i * kNdes * Pst + k;
         float F[3] = {0.f, 0.f, 0.f};
         const float* Bi = B + (size_t)i * kNdes * 3;
 #pragma unroll 8
         for (int v = 0; v < kNdes; ++v) {
-            const float g = Gi[(size_t)v * P];
+            const float g = Gi[(size_t)v * Pst];
             F[0] = fmaf(g, Bi[v * 3 + 0], F[0]);
             F[1] = fmaf(g, Bi[v * 3 + 1], F[1]);
             F[2] = fmaf(g, Bi[v * 3 + 2], F[2]);
@@ -373,10 +371,10 @@ __global__ void __launch_bounds__(1024) k_contract(int N, int P, const int* __re
         for (long long p = pstart[i]; p < pstart[i + 1]; ++p) {
             const int j = pj[p] & 0xFFFFFF;
             const PairRec pr = rec[p];  // describes the pair (j -> i), r = r_ji
-            const float* Gj = G + (size_t)j * kNdes * P + k;
+            const float* Gj = G + (size_t)j * kNdes * Pst + k;
             float cr = 0.f;
 #pragma unroll
-            for (int v = 0; v < kNR; ++v) cr = fmaf(Gj[(size_t)v * P], pr.gd[v], cr);
+            for (int v = 0; v < kNR; ++v) cr = fmaf(Gj[(size_t)v * Pst], pr.gd[v], cr);
             float pv[3] = {cr * pr.r[0], cr * pr.r[1], cr * pr.r[2]};
             const long long ai = aidx[p];
             if (ai >= 0) {
@@ -384,8 +382,8 @@ __global__ void __launch_bounds__(1024) k_contract(int N, int P, const int* __re
 #pragma unroll
                 for (int u = 0; u < kNA * kLmax * 3 / 12; ++u) {  // 4 descriptors (12 floats) per step
                     const float4 a0 = A4[3 * u], a1 = A4[3 * u + 1], a2 = A4[3 * u + 2];
-                    const float g0 = Gj[(size_t)(kNR + 4 * u + 0) * P], g1 = Gj[(size_t)(kNR + 4 * u + 1) * P];
-                    const float g2 = Gj[(size_t)(kNR + 4 * u + 2) * P], g3 = Gj[(size_t)(kNR + 4 * u + 3) * P];
+                    const float g0 = Gj[(size_t)(kNR + 4 * u + 0) * Pst], g1 = Gj[(size_t)(kNR + 4 * u + 1) * Pst];
+                    const float g2 = Gj[(size_t)(kNR + 4 * u + 2) * Pst], g3 = Gj[(size_t)(kNR + 4 * u + 3) * Pst];
                     pv[0] = fmaf(g0, a0.x, pv[0]);
                     pv[1] = fmaf(g0, a0.y, pv[1]);
                     pv[2] = fmaf(g0, a0.z, pv[2]);
@@ -541,12 +539,13 @@ __global__ void k_make_pop(long long count, int n_par, const float* __restrict__
     z[e] = fmaf(s[p], r[e], m[p]);
 }
 
-// One block: rank the members by (loss, index), rank utilities (standard NES
-// rank shaping), natural gradients (Eqs. 36-37) and the update of m with the
-// pre-update s (Eq. 38), then s (Eq. 39).
-__global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss, const float* __restrict__ r,
-                              float* __restrict__ m, float* __restrict__ s, float eta_m, float eta_s,
-                              int* __restrict__ order_out)
+// Rank the members by (loss, index), then the natural gradients (Eqs. 36-37)
+// with the rank utilities `util` and the update of m with the pre-update s
+// (Eq. 38), then s (Eq. 39).  Every block ranks the (few) members itself and
+// updates its own slice of parameters.
+__global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss, const float* __restrict__ util,
+                              const float* __restrict__ r, float* __restrict__ m, float* __restrict__ s, float eta_m,
+                              float eta_s, int* __restrict__ order_out)
 {
     __shared__ int order[kMaxPop];
     __shared__ float u[kMaxPop];
@@ -559,23 +558,21 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
             rank += (lj < lk || (lj == lk && j < t)) ? 1 : 0;
         }
         order[rank] = t;
-        double sum = 0.0;
-        for (int q = 1; q <= P; ++q) sum += fmax(0.0, log(P / 2.0 + 1.0) - log((double)q));
-        u[t] = (float)(fmax(0.0, log(P / 2.0 + 1.0) - log((double)(t + 1))) / sum - 1.0 / P);
+        u[t] = util[t];
     }
     __syncthreads();
-    if (order_out && t < P) order_out[t] = order[t];
-    for (int p = t; p < n_par; p += blockDim.x) {
-        float gm = 0.f, gs = 0.f;
-        for (int q = 0; q < P; ++q) {
-            const float rv = r[(size_t)order[q] * n_par + p];
-            gm = fmaf(u[q], rv, gm);
-            gs = fmaf(u[q], fmaf(rv, rv, -1.f), gs);
-        }
-        const float sp = s[p];
-        m[p] = fmaf(eta_m * sp, gm, m[p]);
-        s[p] = sp * expf(0.5f * eta_s * gs);
+    if (order_out && blockIdx.x == 0 && t < P) order_out[t] = order[t];
+    const int p = blockIdx.x * blockDim.x + t;
+    if (p >= n_par) return;
+    float gm = 0.f, gs = 0.f;
+    for (int q = 0; q < P; ++q) {
+        const float rv = r[(size_t)order[q] * n_par + p];
+        gm = fmaf(u[q], rv, gm);
+        gs = fmaf(u[q], fmaf(rv, rv, -1.f), gs);
     }
+    const float sp = s[p];
+    m[p] = fmaf(eta_m * sp, gm, m[p]);
+    s[p] = sp * expf(0.5f * eta_s * gs);
 }
 
 }  // namespace
@@ -583,38 +580,6 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
 
 using namespace nep;
 
-struct nep_dataset {
-    nep_model* m = nullptr;
-    int S = 0, N = 0;
-    long long n_pairs = 0, n_ang = 0, bytes = 0;
-    int n_chunks = 0;
-    Box* boxes = nullptr;
-    int* sid = nullptr;
-    int* sstart = nullptr;
-    int* s_natoms = nullptr;
-    int* s_chunk0 = nullptr;
-    int* chunk_begin = nullptr;
-    int* chunk_end = nullptr;
-    float* q = nullptr;
-    float* B = nullptr;
-    long long* pstart = nullptr;
-    int* pj = nullptr;
-    long long* aidx = nullptr;
-    PairRec* rec = nullptr;
-    float* ang = nullptr;
-    double* e_tar = nullptr;
-    float* f_tar = nullptr;
-    double* w_tar = nullptr;
-    // evaluation scratch (grown on demand)
-    int pop_cap = 0;
-    float* W1t = nullptr;
-    float* b1t = nullptr;
-    float* w2t = nullptr;
-    float* b2t = nullptr;
-    float* G = nullptr;
-    double* U = nullptr;
-    double* partials = nullptr;
-};
 
 struct snes_state {
     nep_model* m = nullptr;
@@ -627,6 +592,7 @@ struct snes_state {
     float* z = nullptr;
     double* loss = nullptr;
     int* order = nullptr;
+    float* util = nullptr;  // rank utilities u_1..u_P (a constant of P)
 };
 
 namespace {
@@ -653,6 +619,10 @@ void dfree(T*& p)
     p = nullptr;
 }
 
+// member stride of G: a multiple of 4 so that a tensor-core member group
+// (4 members) is one aligned 16-byte store
+inline int member_stride(int P) { return (P + 3) / 4 * 4; }
+
 int ensure_pop(nep_dataset* ds, int P)
 {
     if (P <= ds->pop_cap) return NEP_OK;
@@ -663,14 +633,16 @@ int ensure_pop(nep_dataset* ds, int P)
     dfree(ds->G);
     dfree(ds->U);
     dfree(ds->partials);
+    dfree(ds->packed);
     ds->pop_cap = 0;
     const int nn = ds->m->hp.n_neu;
     int rc;
     if ((rc = dalloc(&ds->W1t, (size_t)nn * kNdes * P, nullptr)) || (rc = dalloc(&ds->b1t, (size_t)nn * P, nullptr)) ||
         (rc = dalloc(&ds->w2t, (size_t)nn * P, nullptr)) || (rc = dalloc(&ds->b2t, (size_t)P, nullptr)) ||
-        (rc = dalloc(&ds->G, (size_t)ds->N * kNdes * P, nullptr)) ||
+        (rc = dalloc(&ds->G, (size_t)ds->N * kNdes * member_stride(P), nullptr)) ||
         (rc = dalloc(&ds->U, (size_t)ds->N * P, nullptr)) ||
-        (rc = dalloc(&ds->partials, (size_t)ds->n_chunks * P * 8, nullptr)))
+        (rc = dalloc(&ds->partials, (size_t)ds->n_chunks * P * 8, nullptr)) ||
+        (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)))
         return rc;
     ds->pop_cap = P;
     return NEP_OK;
@@ -679,18 +651,24 @@ int ensure_pop(nep_dataset* ds, int P)
 int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int precision, const double* lambdas,
              double* loss, cudaStream_t st)
 {
-    if (precision != 0) {
-        set_error("snes_evaluate_population: precision %d not available in this build", precision);
-        return NEP_ERR_UNSUPPORTED;
+    if (precision != NEP_PREC_FP32 && precision != NEP_PREC_BF16) {
+        set_error("snes_evaluate_population: unknown precision %d", precision);
+        return NEP_ERR_ARG;
     }
     int rc = ensure_pop(ds, P);
     if (rc) return rc;
-    const int nn = m->hp.n_neu, n_par = m->n_par;
+    const int nn = m->hp.n_neu, n_par = m->n_par, Pst = member_stride(P);
     k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t, ds->b2t);
-    const long long pairs = (ds->N + 1) / 2;
-    k_mlp_f32<<<blocks_for(pairs * P, 256), 256, 0, st>>>(ds->N, P, nn, ds->q, ds->W1t, ds->b1t, ds->w2t, ds->b2t,
-                                                          ds->G, ds->U);
-    k_contract<<<ds->n_chunks, kChunkAtoms * P, 0, st>>>(ds->N, P, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
+    if (precision == NEP_PREC_BF16) {
+        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
+                                ds->U, m->d_err, st)))
+            return rc;
+    } else {
+        const long long pairs = (ds->N + 1) / 2;
+        k_mlp_f32<<<blocks_for(pairs * P, 256), 256, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
+                                                              ds->b2t, ds->G, ds->U);
+    }
+    k_contract<<<ds->n_chunks, kChunkAtoms * P, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->aidx, ds->ang,
                                                          ds->f_tar, ds->partials);
     const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
@@ -762,18 +740,16 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     ds->n_chunks = (int)hcb.size();
     long long* bytes = &ds->bytes;
     double* dpos = nullptr;
-    float *xh = nullptr, *xl = nullptr;
+    float*& xh = ds->xh;
+    float*& xl = ds->xl;
     int *tmp = nullptr, *cnt = nullptr, *cnta = nullptr;
-    long long* rev = nullptr;
+    long long*& rev = ds->rev;
     int rc = NEP_OK;
     auto fail = [&](int code) {
         dfree(dpos);
-        dfree(xh);
-        dfree(xl);
         dfree(tmp);
         dfree(cnt);
         dfree(cnta);
-        dfree(rev);
         nep_dataset_destroy(ds);
         return code;
     };
@@ -784,7 +760,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
         (rc = dalloc(&ds->B, (size_t)N * kNdes * 3, bytes)) || (rc = dalloc(&ds->pstart, (size_t)N + 1, bytes)) ||
         (rc = dalloc(&ds->e_tar, S, bytes)) || (rc = dalloc(&ds->f_tar, (size_t)3 * N, bytes)) ||
         (rc = dalloc(&ds->w_tar, (size_t)6 * S, bytes)) || (rc = dalloc(&dpos, (size_t)3 * N, nullptr)) ||
-        (rc = dalloc(&xh, (size_t)3 * N, nullptr)) || (rc = dalloc(&xl, (size_t)3 * N, nullptr)) ||
+        (rc = dalloc(&xh, (size_t)4 * N, nullptr)) || (rc = dalloc(&xl, (size_t)4 * N, nullptr)) ||
         (rc = dalloc(&tmp, (size_t)N * kDsCap, nullptr)) || (rc = dalloc(&cnt, N, nullptr)) ||
         (rc = dalloc(&cnta, N, nullptr)))
         return fail(rc);
@@ -832,7 +808,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     if ((rc = dalloc(&ds->pj, (size_t)ds->n_pairs, bytes)) || (rc = dalloc(&ds->aidx, (size_t)ds->n_pairs, bytes)) ||
         (rc = dalloc(&ds->rec, (size_t)ds->n_pairs, bytes)) ||
         (rc = dalloc(&ds->ang, (size_t)ds->n_ang * kNA * kLmax * 3, bytes)) ||
-        (rc = dalloc(&rev, (size_t)ds->n_pairs, nullptr)) || (rc = dalloc(&dastart, (size_t)N + 1, nullptr)))
+        (rc = dalloc(&rev, (size_t)ds->n_pairs, bytes)) || (rc = dalloc(&dastart, (size_t)N + 1, nullptr)))
         return fail(rc);
     up(ds->pstart, hps.data(), sizeof(long long) * (N + 1));
     up(dastart, has.data(), sizeof(long long) * (N + 1));
@@ -856,12 +832,9 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
         return fail(status_from_bits(bits));
     }
     dfree(dpos);
-    dfree(xh);
-    dfree(xl);
     dfree(tmp);
     dfree(cnt);
     dfree(cnta);
-    dfree(rev);
     *out = ds;
     return NEP_OK;
 }
@@ -878,9 +851,12 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->chunk_begin);
     dfree(ds->chunk_end);
     dfree(ds->q);
+    dfree(ds->xh);
+    dfree(ds->xl);
     dfree(ds->B);
     dfree(ds->pstart);
     dfree(ds->pj);
+    dfree(ds->rev);
     dfree(ds->aidx);
     dfree(ds->rec);
     dfree(ds->ang);
@@ -894,6 +870,8 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->G);
     dfree(ds->U);
     dfree(ds->partials);
+    dfree(ds->packed);
+    free_adjoint(ds->adj);
     delete ds;
     return NEP_OK;
 }
@@ -952,12 +930,24 @@ int snes_create(nep_model* m, int n_pop, const float* mean0, const float* sigma0
     int rc;
     if ((rc = dalloc(&st->mean, np, nullptr)) || (rc = dalloc(&st->sigma, np, nullptr)) ||
         (rc = dalloc(&st->r, tot, nullptr)) || (rc = dalloc(&st->z, tot, nullptr)) ||
-        (rc = dalloc(&st->loss, (size_t)n_pop * 6, nullptr)) || (rc = dalloc(&st->order, (size_t)n_pop, nullptr))) {
+        (rc = dalloc(&st->loss, (size_t)n_pop * 6, nullptr)) || (rc = dalloc(&st->order, (size_t)n_pop, nullptr)) ||
+        (rc = dalloc(&st->util, (size_t)n_pop, nullptr))) {
         snes_destroy(st);
         return rc;
     }
+    // rank utilities (standard NES rank shaping, Sec. II.D.2):
+    // u_q = max(0, ln(P/2 + 1) - ln q) / sum_q' max(0, ln(P/2 + 1) - ln q') - 1/P
+    std::vector<float> util(n_pop);
+    {
+        const double top = std::log(n_pop / 2.0 + 1.0);
+        double sum = 0.0;
+        for (int q = 1; q <= n_pop; ++q) sum += std::fmax(0.0, top - std::log((double)q));
+        for (int q = 1; q <= n_pop; ++q)
+            util[q - 1] = (float)(std::fmax(0.0, top - std::log((double)q)) / sum - 1.0 / n_pop);
+    }
     cudaError_t e = cudaMemcpy(st->mean, mean0, sizeof(float) * np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(st->sigma, sigma0, sizeof(float) * np, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(st->util, util.data(), sizeof(float) * n_pop, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         snes_destroy(st);
         return cuda_fail(e, "snes_create upload");
@@ -976,6 +966,7 @@ int snes_destroy(snes_state* st)
     dfree(st->z);
     dfree(st->loss);
     dfree(st->order);
+    dfree(st->util);
     delete st;
     return NEP_OK;
 }
@@ -1000,7 +991,8 @@ int snes_step(snes_state* st, nep_dataset* ds, int precision, const double* lamb
     int rc = evaluate(st->m, ds, st->z, st->P, precision, lambdas, st->loss, cs);
     if (rc) return rc;
     const float eta_s = (float)((3.0 + std::log((double)st->n_par)) / (5.0 * std::sqrt((double)st->n_par)));
-    k_snes_update<<<1, 1024, 0, cs>>>(st->P, st->n_par, st->loss, st->r, st->mean, st->sigma, 1.f, eta_s, st->order);
+    k_snes_update<<<blocks_for(st->n_par, 128), 128, 0, cs>>>(st->P, st->n_par, st->loss, st->util, st->r, st->mean, st->sigma,
+                                                               1.f, eta_s, st->order);
     if (loss_out) {
         rc = cuda_fail(cudaMemcpyAsync(loss_out, st->loss, sizeof(double) * st->P * 6, cudaMemcpyDeviceToDevice, cs),
                        "copy loss");

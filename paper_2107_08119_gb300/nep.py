@@ -54,19 +54,21 @@ _SIGNATURES = {
     "nep_md_rebuild_count": (C.c_int, [_vp, C.POINTER(C.c_longlong), _vp]),
     "nep_md_forces": (_vp, [_vp]),
     "nep_profile_enable": (C.c_int, [_vp, C.c_int]),
-    "nep_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
-                                   C.POINTER(C.c_longlong)]),
+    "nep_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "nep_dataset_create": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     "nep_dataset_destroy": (C.c_int, [_vp]),
     "nep_dataset_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "nep_dataset_descriptors": (C.c_int, [_vp, _vp, _vp]),
     "snes_evaluate_population": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]),
+    "nep_force_loss": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "nep_force_loss_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "snes_create": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_ulonglong, C.POINTER(_vp)]),
     "snes_destroy": (C.c_int, [_vp]),
     "snes_step": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
     "snes_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "nep_compute_efv_static": (C.c_int, [C.POINTER(_Hyper), _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
                                          _vp, _vp, _vp]),
+    "nep_tc_selftest": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
     "nep_last_error": (C.c_char_p, []),
 }
 
@@ -205,11 +207,12 @@ class NEP:
         _check(_lib.nep_profile_enable(self._h, 1 if on else 0), "nep_profile_enable")
 
     def profile_read(self):
-        """{'site_ms', 'site_launches', 'assemble_ms', 'assemble_launches'} since the last read."""
-        a, b = C.c_double(), C.c_double()
-        ca, cb = C.c_longlong(), C.c_longlong()
-        _check(_lib.nep_profile_read(self._h, C.byref(a), C.byref(ca), C.byref(b), C.byref(cb)), "nep_profile_read")
-        return {"site_ms": a.value, "site_launches": ca.value, "assemble_ms": b.value, "assemble_launches": cb.value}
+        """Summed ms and bracket counts per phase since the last read:
+        {"site": (ms, n), "assemble": ..., "neighbor": ..., "step": ...}."""
+        ms = (C.c_double * 4)()
+        cnt = (C.c_longlong * 4)()
+        _check(_lib.nep_profile_read(self._h, ms, cnt), "nep_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(("site", "assemble", "neighbor", "step"))}
 
     def heat_current(self, virial_atom, vel, stream=None):
         vel = _soa_f64(vel)
@@ -221,6 +224,20 @@ class NEP:
         _check(_lib.nep_heat_current(self._h, n, _ptr(virial_atom), _ptr(vel), _ptr(J), _stream(stream)),
                "nep_heat_current")
         return J
+
+
+def tc_selftest(A, B, stream=None):
+    """D = A B^T through the library's tcgen05 BF16 path (A: 128 x 32, B: N x 32,
+    CUDA bfloat16).  Returns (D, error bits)."""
+    if not (A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and A.is_cuda and B.is_cuda
+            and tuple(A.shape) == (128, 32) and B.dim() == 2 and B.shape[1] == 32):
+        raise ValueError("A must be CUDA bf16 (128, 32) and B CUDA bf16 (N, 32)")
+    A = A.contiguous()
+    B = B.contiguous()
+    D = torch.empty(128, B.shape[0], dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(_lib.nep_tc_selftest(_ptr(A), _ptr(B), B.shape[0], _ptr(D), _ptr(err), _stream(stream)), "nep_tc_selftest")
+    return D, err
 
 
 STATIC_MAX_ATOMS = 4096
@@ -358,6 +375,54 @@ class Dataset:
                                              None if lam is None else lam.ctypes.data_as(_vp), _ptr(loss),
                                              _stream(stream)), "snes_evaluate_population")
         return loss
+
+    def force_loss(self, z, stream=None):
+        """L_f of Eq. 30 for one parameter vector (CUDA float32 (n_par,)).
+        Returns a CUDA float64 (1,) tensor; the dataset keeps what
+        force_loss_backward needs."""
+        z = _param_vector(z, self.model.hyper.n_par)
+        out = torch.empty(1, dtype=torch.float64, device=z.device)
+        _check(_lib.nep_force_loss(self.model._h, self._h, _ptr(z), _ptr(out), _stream(stream)), "nep_force_loss")
+        return out
+
+    def force_loss_backward(self, seed=None, stream=None):
+        """seed * dL_f/dz at the z of the last force_loss (CUDA float64 (n_par,));
+        seed: CUDA float64 scalar tensor or None for 1."""
+        grad = torch.empty(self.model.hyper.n_par, dtype=torch.float64, device="cuda")
+        if seed is not None:
+            seed = seed.detach().to(device="cuda", dtype=torch.float64).reshape(1).contiguous()
+        _check(_lib.nep_force_loss_backward(self.model._h, self._h, None if seed is None else _ptr(seed), _ptr(grad),
+                                            _stream(stream)), "nep_force_loss_backward")
+        return grad
+
+
+def _param_vector(z, n_par):
+    if not (z.is_cuda and z.dtype == torch.float32 and z.is_contiguous() and z.numel() == n_par):
+        raise ValueError(f"z must be a contiguous CUDA float32 tensor of {n_par} parameters")
+    return z
+
+
+class ForceLoss(torch.autograd.Function):
+    """Differentiable L_f(z) on a training set: forward = nep_force_loss,
+    backward = nep_force_loss_backward (hand-written adjoint, descriptors
+    recomputed).  Use as ForceLoss.apply(z, dataset); z is CUDA float32.
+    The dataset holds the state of its latest forward, so run each backward
+    before the next forward on the same dataset."""
+
+    @staticmethod
+    def forward(ctx, z, dataset):
+        ctx.dataset = dataset
+        return dataset.force_loss(z.detach().contiguous()).reshape(())
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = ctx.dataset.force_loss_backward(seed=grad_out)
+        return g.to(torch.float32), None
+
+
+def force_loss(z, dataset):
+    """L_f(z) on `dataset` as a differentiable torch scalar (float64)."""
+    return ForceLoss.apply(z, dataset)
 
 
 class SNES:
