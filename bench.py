@@ -310,6 +310,7 @@ def run_gpu(args, rank, world, local):
             "gpu_launches": 13 * K,
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
+        line["force_eval_vs_plain_fp32"] = force_eval_comparison(N, model, p0, box)
         line["snes"] = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16),
                         "unit": "generation/s",
                         "workload": "200 periodic structures of 32-256 atoms, population 50, 32-30-1 NEP"}
@@ -321,6 +322,32 @@ def run_gpu(args, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def force_eval_comparison(N, model, pos, box, reps: int = 10):
+    """One force evaluation (list build, site pass, assembly, reductions) of
+    the 125k-atom state through nep_compute_efv and through the plain FP32
+    comparator nep_compute_efv_plain (literal O(M^2) angular sum, unfused,
+    uncompensated), CUDA events on the current stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, plain in (("optimised", False), ("plain_fp32", True)):
+        for _ in range(2):
+            model.compute(pos, box, plain=plain, sync=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            model.compute(pos, box, plain=plain, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        model.sync_status()
+        out[name] = e0.elapsed_time(e1) / reps
+    n = pos.shape[1]
+    return {"unit": "ms per force evaluation", "atoms": n, "optimised_ms": out["optimised"],
+            "plain_fp32_ms": out["plain_fp32"], "speedup_vs_plain": out["plain_fp32"] / out["optimised"],
+            "evaluations_timed": reps}
 
 
 def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):

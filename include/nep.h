@@ -105,6 +105,20 @@ int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, 
                     float* force, float* virial_atom, double* virial_total, void* stream);
 
 /*
+ * nep_compute_efv_plain -- the same outputs as nep_compute_efv, computed by
+ * the plain FP32 GPU form that the optimised path is measured against: one
+ * thread per atom, three unfused passes (descriptors, network, partial
+ * forces), q_nl by the literal double sum over neighbour pairs of Eq. 13 with
+ * Legendre polynomials (O(M^2) per atom), partial forces by Eqs. 24-25, and
+ * no compensated sums (so site energies carry plain FP32 rounding, ~1e-5 eV).
+ * It shares the neighbour list, assembly and reductions with nep_compute_efv.
+ * At most 96 neighbours within r_c^A per atom (NEP_ERR_NEIGHBOR_OVERFLOW,
+ * latched).  Same arguments and errors as nep_compute_efv.
+ */
+int nep_compute_efv_plain(nep_model* m, int n, const double* box9, const double* pos, double* e_total,
+                          double* e_atom, float* force, float* virial_atom, double* virial_total, void* stream);
+
+/*
  * nep_sync_status -- synchronise `stream`, then return and clear the first
  * device-side error latched by earlier calls on this handle (NEP_OK if none).
  */

@@ -216,8 +216,9 @@ void free_workspace(Workspace& ws)
     dev_free(nl.cell_atoms);
     dev_free(ws.partials);
     dev_free(ws.force);
+    dev_free(ws.plain);
     nl = NeighborList();
-    ws.partial_cap = ws.force_cap = 0;
+    ws.partial_cap = ws.force_cap = ws.plain_cap = 0;
 }
 
 Profiler::Slot* Profiler::begin(int kind, cudaStream_t st)
@@ -363,8 +364,12 @@ int nep_sync_status(nep_model* m, void* stream)
     return status_from_bits(bits);
 }
 
-int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, double* e_total, double* e_atom,
-                    float* force, float* virial_atom, double* virial_total, void* stream)
+}  // extern "C"
+
+namespace {
+
+int compute_efv(nep_model* m, int n, const double* box9, const double* pos, double* e_total, double* e_atom,
+                float* force, float* virial_atom, double* virial_total, void* stream, bool plain)
 {
     if (!m || !pos || n < 1 || n > kMaxAtoms) {
         set_error("nep_compute_efv: bad arguments (handle, positions, 1 <= n < 2^24)");
@@ -390,7 +395,26 @@ int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, 
     double* part_v = m->ws.partials + ((nblocks + 7) / 8) * 8;
     int nb1 = 0;
     Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, st);
-    if ((rc = launch_site_partial_forces(fa, nl, n, e_atom, part_e, m->d_err, st, nb1))) return rc;
+    if (plain) {
+        Workspace& ws = m->ws;
+        if (ws.plain_cap < n) {
+            if (ws.plain) cudaFree(ws.plain);
+            ws.plain = nullptr;
+            ws.plain_cap = 0;
+            cudaError_t e = cudaMalloc((void**)&ws.plain, sizeof(float) * 2 * kNdes * (size_t)n);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_error("nep_compute_efv_plain: scratch allocation failed");
+                return NEP_ERR_OOM;
+            }
+            ws.plain_cap = n;
+        }
+        if ((rc = launch_plain_site(fa, nl, n, ws.plain, ws.plain + (size_t)kNdes * n, e_atom, part_e, m->d_err, st,
+                                    nb1)))
+            return rc;
+    } else if ((rc = launch_site_partial_forces(fa, nl, n, e_atom, part_e, m->d_err, st, nb1))) {
+        return rc;
+    }
     m->prof.end(ps, st);
     AssembleArgs aa{};
     aa.rc_max = (float)rmax;
@@ -407,6 +431,22 @@ int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, 
         if ((rc = cuda_fail(cudaGetLastError(), "finish kernel"))) return rc;
     }
     return NEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nep_compute_efv(nep_model* m, int n, const double* box9, const double* pos, double* e_total, double* e_atom,
+                    float* force, float* virial_atom, double* virial_total, void* stream)
+{
+    return compute_efv(m, n, box9, pos, e_total, e_atom, force, virial_atom, virial_total, stream, false);
+}
+
+int nep_compute_efv_plain(nep_model* m, int n, const double* box9, const double* pos, double* e_total,
+                          double* e_atom, float* force, float* virial_atom, double* virial_total, void* stream)
+{
+    return compute_efv(m, n, box9, pos, e_total, e_atom, force, virial_atom, virial_total, stream, true);
 }
 
 int nep_profile_enable(nep_model* m, int on)

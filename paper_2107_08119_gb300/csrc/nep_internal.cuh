@@ -183,6 +183,8 @@ struct Workspace {
     int partial_cap = 0;         // doubles
     float* force = nullptr;      // [3][n] FP32 (MD and internal use)
     int force_cap = 0;
+    float* plain = nullptr;      // [2][32][n] q and G of the plain comparator (on demand)
+    int plain_cap = 0;
 };
 
 // host-side helpers (nep_api.cu)
@@ -219,6 +221,10 @@ struct AssembleArgs {
 int launch_assemble(const AssembleArgs& a, NeighborList& nl, int n, float* force, float* virial_atom,
                     double* partials, unsigned* d_err, cudaStream_t st, int& nblocks, int& ncomp);
 int launch_reduce(const double* partials, int nblocks, int ncomp, double* out, cudaStream_t st);
+// the plain FP32 comparator (nep_plain.cu): descriptors, network and partial
+// forces by the literal formulas, q and G [32][n] scratch
+int launch_plain_site(const ForceArgs& a, NeighborList& nl, int n, float* q, float* G, double* e_atom,
+                      double* e_partials, unsigned* d_err, cudaStream_t st, int& nblocks);
 
 }  // namespace nep
 
@@ -240,6 +246,7 @@ struct Profiler {
 };
 // tensor-core population network (nep_pop_tc.cu)
 size_t pop_tc_packed_bytes(int P);
+// G [N][32][Pst] FP32, U [N][P] FP64
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
                   const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
                   cudaStream_t st);

@@ -217,35 +217,56 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     __syncwarp();
     const int total = pre[27];
     int cnt = 0;
-    for (int base = 0; base < total; base += 32) {
-        const int idx = base + lane;
-        bool accept = false;
-        int value = 0;
-        float d2 = 0.f;
-        if (idx < total) {
-            int c = 0;  // last cell whose prefix is <= idx
+    // four candidates per lane per round: their index and position loads are
+    // all in flight before the first distance test
+    constexpr int kU = 4;
+    for (int base = 0; base < total; base += 32 * kU) {
+        int value[kU];
+        float d2[kU];
+        bool accept[kU];
+        int jj[kU], code[kU];
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1)
-                if (c + step < 27 && pre[c + step] <= idx) c += step;
-            const int j = cell_atoms[cst[c] + idx - pre[c]];
-            const int code = ccode[c];
-            if (!(j == i && code == kImgCenter)) {
-                float hj[3], lj[3];
-                load_pos(xh, xl, n, j, hj, lj);
-                float rx, ry, rz;
-                pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
-                d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                accept = d2 < rv2;
-                value = j | (code << 24);
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + 32 * u + lane;
+            jj[u] = -1;
+            code[u] = 0;
+            if (idx < total) {
+                int c = 0;  // last cell whose prefix is <= idx
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (c + step < 27 && pre[c + step] <= idx) c += step;
+                jj[u] = cell_atoms[cst[c] + idx - pre[c]];
+                code[u] = ccode[c];
             }
         }
-        const unsigned mask = __ballot_sync(0xffffffffu, accept);
-        const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-        if (accept && pos < lcap) {
-            skey[pos] = d2;
-            sval[pos] = value;
+        float hj[kU][3], lj[kU][3];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (jj[u] >= 0) load_pos(xh, xl, n, jj[u], hj[u], lj[u]);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            accept[u] = false;
+            value[u] = 0;
+            d2[u] = 0.f;
+            const int j = jj[u];
+            if (j >= 0 && !(j == i && code[u] == kImgCenter)) {
+                float rx, ry, rz;
+                pair_vector(i, j, code[u], hi, li, hj[u], lj[u], b, rx, ry, rz);
+                d2[u] = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                accept[u] = d2[u] < rv2;
+                value[u] = j | (code[u] << 24);
+            }
         }
-        cnt += __popc(mask);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const unsigned mask = __ballot_sync(0xffffffffu, accept[u]);
+            const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+            if (accept[u] && pos < lcap) {
+                skey[pos] = d2[u];
+                sval[pos] = value[u];
+            }
+            cnt += __popc(mask);
+        }
     }
     __syncwarp();
     if (lane == 0) count[i] = cnt;

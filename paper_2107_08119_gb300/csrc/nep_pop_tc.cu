@@ -5,13 +5,15 @@
 //   H[i, (k, mu)] = sum_nu q_i,nu w1_k,mu,nu            (GEMM 1, K = 32)
 //   x = tanh(H - b1), U_ki = sum_mu w2_k,mu x - b2_k,  D_ki,mu = w2_k,mu (1 - x^2)
 //   G_k[i, nu] = sum_mu D_ki,mu w1_k,mu,nu              (GEMM 2 per member, K = 30 -> 32)
-// One CTA owns 128 atoms.  Members go in groups of 4: GEMM 1 has N = 4 x 30 =
-// 120 (-> 128) columns of TMEM, GEMM 2 writes 4 x 32 columns of a second TMEM
-// region; 256 columns per CTA leave room for two CTAs per SM.  Operands are
-// split BF16 (hi + lo) in shared memory (canonical K-major layout,
-// nep_tc.cuh); accumulation is FP32 in TMEM.  One thread issues the MMAs and commits them
-// to an mbarrier; all waits are bounded (a timeout is latched as an error and
-// the CTA still frees its TMEM).
+// One CTA owns 128 atoms and one group of 4 members (grid: tiles x groups):
+// GEMM 1 fills 4 x 32 TMEM columns (neurons padded to 32 per member), the
+// epilogue turns them into U and D, and GEMM 2 writes G of the 4 members back
+// into the same 128 columns.  Operands are split BF16 (hi + lo) in shared
+// memory (canonical K-major layout, nep_tc.cuh); accumulation is FP32 in
+// TMEM.  One thread issues the MMAs and commits them to an mbarrier; all
+// waits are bounded (a timeout is latched as an error and the CTA still frees
+// its TMEM).  G is written as [N][32][Pst]: each thread stores its atom's 16
+// descriptors x 4 members as 16-byte pieces.
 #include <cuda_bf16.h>
 
 #include "nep_internal.cuh"
@@ -89,25 +91,43 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const __nv_bfloat16* __rest
 // site energies) takes three MMAs, hi*hi + hi*lo + lo*hi, carrying ~16
 // mantissa bits instead of 8; GEMM 2 (forces, whose loss terms average the
 // rounding out) keeps D in BF16 and splits only W1 (two MMAs).  Every MMA is
-// BF16 x BF16 -> FP32.
+// BF16 x BF16 -> FP32.  GEMM-1 columns are 32 per member (neurons past n_neu
+// have zero weights), so every member starts on an 8-column TMEM boundary.
 constexpr int kTcGroup = 4;
-constexpr int kW1Bytes = kTile * 64;     // GEMM-1 B: 128 rows (member, mu) x 32 nu
+constexpr int kW1Bytes = kTile * 64;     // GEMM-1 B: 128 rows (32 m + mu) x 32 nu
 constexpr int kW1tBytes = 32 * 64;       // GEMM-2 B per member: 32 nu x 32 mu
+constexpr int kTileBytes = kTile * 64;   // one 128 x 32 BF16 operand tile
 // packed group record: w1 hi, w1 lo, w1t hi[4], w1t lo[4], b1[4][32], w2[4][32], b2[4]
 constexpr int kGroupBytes = 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes + (2 * kTcGroup * 32 + 4) * 4;
+constexpr int kTmemCols = 128;
 
+// Shared memory of one CTA (one 128-atom tile, one member group).  Once GEMM 1
+// has completed its operands are dead and the GEMM-2 A tiles (D of the four
+// members, BF16) take their place:
+//   a    q hi | q lo            -> D of members 0 | 1
+//   grp  w1 hi | w1 lo | ...    -> D of members 2 | 3 | (w1t hi, w1t lo, b1, w2, b2 kept)
+// ~50 KB and 128 TMEM columns per CTA: four CTAs fit on one SM.
 struct PopSmem {
-    unsigned char q_hi[kTile * 64], q_lo[kTile * 64];
-    unsigned char grp[kGroupBytes];                        // the current group's packed record
-    unsigned char d_hi[kTcGroup][kTile * 64];  // GEMM-2 A (hi part only)
+    unsigned char a[2 * kTileBytes];
+    unsigned char grp[kGroupBytes];
     uint64_t mbar;
     uint32_t tmem_base;
 };
+
+__device__ __forceinline__ unsigned char* d_tile(PopSmem& S, int m)
+{
+    return m < 2 ? S.a + m * kTileBytes : S.grp + (m - 2) * kTileBytes;
+}
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo)
 {
     hi = __float2bfloat16_rn(x);
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
 __device__ __forceinline__ void put_split(unsigned char* hi_base, unsigned char* lo_base, int row, int k, float v)
@@ -125,15 +145,15 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ W1t, const
                           unsigned char* __restrict__ packed)
 {
     const int groups = (P + kTcGroup - 1) / kTcGroup;
-    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32 + 1;  // w1 elems, w1t elems, bias rows, b2
+    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;  // w1 elems, w1t elems, bias rows
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= groups * per) return;
     const int g = e / per, r = e % per, k0 = g * kTcGroup;
     const int mg = min(kTcGroup, P - k0);
     unsigned char* rec = packed + (size_t)g * kGroupBytes;
-    if (r < kTile * 32) {  // GEMM-1 B row = (member, mu), column nu
-        const int row = r / 32, nu = r % 32, m = row / n_neu, mu = row % n_neu;
-        const bool on = m < mg && row < mg * n_neu;
+    if (r < kTile * 32) {  // GEMM-1 B row = 32 m + mu, column nu
+        const int row = r / 32, nu = r % 32, m = row / 32, mu = row % 32;
+        const bool on = m < mg && mu < n_neu;
         put_split(rec, rec + kW1Bytes, row, nu, on ? W1t[((size_t)mu * kNdes + nu) * P + k0 + m] : 0.f);
         return;
     }
@@ -147,13 +167,11 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ W1t, const
     }
     t -= kTcGroup * 32 * 32;
     float* fb = reinterpret_cast<float*>(rec + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
-    if (t < kTcGroup * 32) {
-        const int m = t / 32, mu = t % 32;
-        const bool on = m < mg && mu < n_neu;
-        fb[m * 32 + mu] = on ? b1t[(size_t)mu * P + k0 + m] : 0.f;
-        fb[kTcGroup * 32 + m * 32 + mu] = on ? w2t[(size_t)mu * P + k0 + m] : 0.f;
-        if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? b2t[k0 + m] : 0.f;
-    }
+    const int m = t / 32, mu = t % 32;
+    const bool on = m < mg && mu < n_neu;
+    fb[m * 32 + mu] = on ? b1t[(size_t)mu * P + k0 + m] : 0.f;
+    fb[kTcGroup * 32 + m * 32 + mu] = on ? w2t[(size_t)mu * P + k0 + m] : 0.f;
+    if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? b2t[k0 + m] : 0.f;
 }
 
 // Issue the split-BF16 products of one K = 32 tile pair into d_tmem:
@@ -170,142 +188,156 @@ __device__ __forceinline__ void mma_split(uint32_t d_tmem, const unsigned char* 
                          tc::smem_desc(tc::smem_u32(bs[p]) + ks * 256, 128, 512), idesc, p > 0 || ks > 0);
 }
 
-// One CTA per 128 atoms.  Outputs U [N][P] (FP64) and G [N][32][Pst] (FP32).
-__global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, int n_neu,
-                                                        const float* __restrict__ q,
+// Barrier that also orders tcgen05 work and async-proxy shared-memory reads
+// around it.
+__device__ __forceinline__ void tc_sync()
+{
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// Grid (member groups of 4, atom tiles of 128), groups fastest so the CTAs
+// that fill one tile's G rows run together.  Outputs U [N][P] (FP64) and
+// G [N][32][Pst] (FP32, member innermost).  Warp w: TMEM lane quarter w & 3 (its 32 atoms),
+// half w >> 2 (members {2h, 2h+1} in epilogue 1, descriptors [16h, 16h+16) in
+// epilogue 2).
+__global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, const float* __restrict__ q,
                                                         const unsigned char* __restrict__ packed,
                                                         float* __restrict__ G, double* __restrict__ U, unsigned* err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PopSmem& S = *reinterpret_cast<PopSmem*>(smem_raw);
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int quarter = warp & 3;            // TMEM lane quarter of this warp
-    const int half = warp >> 2;              // members {2 half, 2 half + 1} of a group
+    const int quarter = warp & 3, half = warp >> 2;
     const int row = quarter * 32 + lane;     // tile row = TMEM lane
-    const int i = blockIdx.x * kTile + row;  // atom
+    const int i = blockIdx.y * kTile + row;  // atom
     const bool valid = i < N;
+    const int gi = blockIdx.x, k0 = gi * kTcGroup;
 
-    for (int k = half * 16; k < half * 16 + 16; ++k) put_split(S.q_hi, S.q_lo, row, k, valid ? q[(size_t)i * kNdes + k] : 0.f);
+    // ---- A of GEMM 1: this thread's 16 descriptors of its atom, split BF16, 16-byte stores
+#pragma unroll
+    for (int c = 2 * half; c < 2 * half + 2; ++c) {
+        float v[8];
+        if (valid) {
+            const float4 a = *reinterpret_cast<const float4*>(q + (size_t)i * kNdes + 8 * c);
+            const float4 b = *reinterpret_cast<const float4*>(q + (size_t)i * kNdes + 8 * c + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        }
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(v[2 * e], h0, l0);
+            split_bf16(v[2 * e + 1], h1, l1);
+            h[e] = pack2(h0, h1);
+            l[e] = pack2(l0, l1);
+        }
+        const uint32_t o = tc::kmajor_offset(row, 8 * c);
+        *reinterpret_cast<uint4*>(S.a + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(S.a + kTileBytes + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    // ---- the group's packed operands (16-byte copies; the records stay in L2)
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(packed + (size_t)gi * kGroupBytes);
+        uint4* dst = reinterpret_cast<uint4*>(S.grp);
+        for (int e = t; e < kGroupBytes / 16; e += blockDim.x) dst[e] = src[e];
+    }
     if (t == 0) {
         tc::mbar_init(&S.mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-        tc::tmem_alloc(&S.tmem_base, 256);
+        tc::tmem_alloc(&S.tmem_base, kTmemCols);
         tc::tmem_relinquish();
     }
-    uint32_t phase = 0;
-    bool ok = true;
-    const int groups = (P + kTcGroup - 1) / kTcGroup;
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
+    tc_sync();
     const uint32_t tb = S.tmem_base;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
-    const unsigned char* w1_hi = S.grp;
-    const unsigned char* w1_lo = S.grp + kW1Bytes;
     const unsigned char* w1t_hi = S.grp + 2 * kW1Bytes;
     const unsigned char* w1t_lo = w1t_hi + kTcGroup * kW1tBytes;
     const float* fb = reinterpret_cast<const float*>(S.grp + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
+    bool ok;
 
-    for (int gi = 0; gi < groups && ok; ++gi) {
-        const int k0 = gi * kTcGroup;
-        const int mg = min(kTcGroup, P - k0);
-        const int n1 = ((mg * n_neu + 15) / 16) * 16;
-        // ---- the group's packed operands (16-byte copies)
-        const uint4* src = reinterpret_cast<const uint4*>(packed + (size_t)gi * kGroupBytes);
-        uint4* dst = reinterpret_cast<uint4*>(S.grp);
-        for (int e = t; e < kGroupBytes / 16; e += blockDim.x) dst[e] = src[e];
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        // ---- GEMM 1: H = Q W1^T into TMEM columns [0, n1)
-        if (t == 0) {
-            mma_split(tb, S.q_hi, S.q_lo, w1_hi, w1_lo, tc::idesc_bf16_f32(kTile, n1));
-            tc::mma_commit(&S.mbar);
-        }
-        ok = __syncthreads_and(tc::mbar_wait(&S.mbar, phase, kMaxPolls)) != 0;
-        phase ^= 1u;
-        tc::fence_after_sync();
-        if (!ok) {
-            if (t == 0) atomicOr(err, kErrTimeout);
-            break;
-        }
-        // ---- epilogue 1: members {2 half, 2 half + 1}
-        for (int m = 2 * half; m < min(mg, 2 * half + 2); ++m) {
-            float u = 0.f;
-            const int c_lo = m * n_neu;
-            for (int c0 = (c_lo / 8) * 8; c0 < c_lo + n_neu; c0 += 8) {
-                uint32_t r[8];
-                tc::tmem_ld8(tb + lane_base + (uint32_t)c0, r);
-                tc::tmem_ld_wait();
+    // ---- GEMM 1: H = Q W1^T into TMEM columns [0, 128), member m at [32 m, 32 m + 32)
+    if (t == 0) {
+        mma_split(tb, S.a, S.a + kTileBytes, S.grp, S.grp + kW1Bytes, tc::idesc_bf16_f32(kTile, kTmemCols));
+        tc::mma_commit(&S.mbar);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&S.mbar, 0, kMaxPolls)) != 0;
+    tc::fence_after_sync();
+    if (ok) {
+        // ---- epilogue 1: x = tanh(H - b1), U, D = w2 (1 - x^2) as BF16 into the GEMM-2 A tiles
+#pragma unroll 1
+        for (int m = 2 * half; m < 2 * half + 2; ++m) {
+            uint32_t r[4][8];
 #pragma unroll
-                for (int qd = 0; qd < 8; ++qd) {
-                    const int c = c0 + qd;
-                    if (c < c_lo || c >= c_lo + n_neu) continue;
-                    const int mu = c - c_lo;
-                    const float x = tanhf(__uint_as_float(r[qd]) - fb[m * 32 + mu]);
-                    const float w2 = fb[kTcGroup * 32 + m * 32 + mu];
-                    u = fmaf(w2, x, u);
-                    *reinterpret_cast<__nv_bfloat16*>(S.d_hi[m] + tc::kmajor_offset(row, mu)) =
-                        __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
+            for (int c = 0; c < 4; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(32 * m + 8 * c), r[c]);
+            tc::tmem_ld_wait();
+            float u = 0.f;
+            unsigned char* D = d_tile(S, m);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t d[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    __nv_bfloat16 dd[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int mu = 8 * c + 2 * e + h;
+                        const float x = tanhf(__uint_as_float(r[c][2 * e + h]) - fb[m * 32 + mu]);
+                        const float w2 = fb[kTcGroup * 32 + m * 32 + mu];
+                        u = fmaf(w2, x, u);
+                        dd[h] = __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
+                    }
+                    d[e] = pack2(dd[0], dd[1]);
                 }
+                *reinterpret_cast<uint4*>(D + tc::kmajor_offset(row, 8 * c)) = make_uint4(d[0], d[1], d[2], d[3]);
             }
-            for (int mu = n_neu; mu < 32; ++mu)
-                *reinterpret_cast<__nv_bfloat16*>(S.d_hi[m] + tc::kmajor_offset(row, mu)) = __float2bfloat16_rn(0.f);
-            if (valid) U[(size_t)i * P + k0 + m] = (double)u - (double)fb[2 * kTcGroup * 32 + m];
+            if (valid && k0 + m < P) U[(size_t)i * P + k0 + m] = (double)u - (double)fb[2 * kTcGroup * 32 + m];
         }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        // ---- GEMM 2: G_m = D_m W1_m into TMEM columns [128 + 32 m, +32)
+    }
+    tc_sync();
+    // ---- GEMM 2: G_m = D_m W1_m into TMEM columns [32 m, 32 m + 32) (epilogue 1 has read them)
+    if (ok) {
         if (t == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(kTile, 32);
-            for (int m = 0; m < mg; ++m)
-                mma_split(tb + 128u + 32u * (uint32_t)m, S.d_hi[m], nullptr, w1t_hi + m * kW1tBytes,
+            for (int m = 0; m < kTcGroup; ++m)
+                mma_split(tb + 32u * (uint32_t)m, d_tile(S, m), nullptr, w1t_hi + m * kW1tBytes,
                           w1t_lo + m * kW1tBytes, idesc);
             tc::mma_commit(&S.mbar);
         }
-        ok = __syncthreads_and(tc::mbar_wait(&S.mbar, phase, kMaxPolls)) != 0;
-        phase ^= 1u;
+        ok = __syncthreads_and(tc::mbar_wait(&S.mbar, 1, kMaxPolls)) != 0;
         tc::fence_after_sync();
-        if (!ok) {
-            if (t == 0) atomicOr(err, kErrTimeout);
-            break;
+    }
+    if (ok) {
+        // ---- epilogue 2: descriptors [16 half, 16 half + 16) of the atom, 4 members per float4
+        uint32_t r[kTcGroup][2][8];
+#pragma unroll
+        for (int m = 0; m < kTcGroup; ++m)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(32 * m + 16 * half + 8 * c), r[m][c]);
+        tc::tmem_ld_wait();
+        if (valid) {
+            float* out = G + ((size_t)i * kNdes + 16 * half) * Pst + k0;
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    *reinterpret_cast<float4*>(out + (size_t)(8 * c + e) * Pst) =
+                        make_float4(__uint_as_float(r[0][c][e]), __uint_as_float(r[1][c][e]),
+                                    __uint_as_float(r[2][c][e]), __uint_as_float(r[3][c][e]));
         }
-        // ---- epilogue 2: G[i][nu][k0 + m], this warp takes nu in [16 half, 16 half + 16)
-        for (int nc = 2 * half; nc < 2 * half + 2; ++nc) {
-            float g[kTcGroup][8];
-#pragma unroll
-            for (int m = 0; m < kTcGroup; ++m) {
-                if (m < mg) {
-                    uint32_t r[8];
-                    tc::tmem_ld8(tb + lane_base + 128u + 32u * (uint32_t)m + 8u * (uint32_t)nc, r);
-                    tc::tmem_ld_wait();
-#pragma unroll
-                    for (int qd = 0; qd < 8; ++qd) g[m][qd] = __uint_as_float(r[qd]);
-                }
-            }
-            if (valid) {
-#pragma unroll
-                for (int qd = 0; qd < 8; ++qd) {
-                    float* out = G + ((size_t)i * kNdes + nc * 8 + qd) * Pst + k0;
-                    if (mg == kTcGroup)
-                        *reinterpret_cast<float4*>(out) = make_float4(g[0][qd], g[1][qd], g[2][qd], g[3][qd]);
-                    else
-                        for (int m = 0; m < mg; ++m) out[m] = g[m][qd];
-                }
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
+    } else if (t == 0) {
+        atomicOr(err, kErrTimeout);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tb, 256);
+    if (warp == 0) tc::tmem_dealloc(tb, kTmemCols);
 }
 
 }  // namespace
@@ -316,18 +348,18 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float*
                   const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
                   cudaStream_t st)
 {
-    if (n_neu > 32 || Pst % 4 != 0) {
+    if (n_neu > 32 || Pst % 4 != 0 || Pst < P) {
         set_error("tensor-core population path needs n_neu <= 32 and a member stride that is a multiple of 4");
         return NEP_ERR_UNSUPPORTED;
     }
     const int groups = (P + kTcGroup - 1) / kTcGroup;
-    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32 + 1;
+    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
     k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
     const size_t smem = sizeof(PopSmem);
     int rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                        "population kernel shared memory");
     if (rc) return rc;
-    k_pop_tc<<<(N + kTile - 1) / kTile, kPopThreads, smem, st>>>(N, P, Pst, n_neu, q, packed, G, U, err);
+    k_pop_tc<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, q, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
 }
 

@@ -231,10 +231,39 @@ __host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, flo
     e = (a - (s - bb)) + (b - bb);
 }
 
+// One neuron's compensated (Kahan) pre-activation a - ca = sum_v row_v q_v - b1:
+// the rounding of a plain FP32 dot product feeds straight into U for every
+// unsaturated neuron.
+__host__ __device__ __forceinline__ void kahan_step(float w, float qv, float& a, float& ca)
+{
+    const float y = fmaf(w, qv, -ca);
+    const float t = a + y;
+    ca = (t - a) - y;
+    a = t;
+}
+
+// Adds neuron mu's output w2 x to the compensated sum (s, c) and its share
+// w2 (1 - x^2) w1_mu of G.
+__host__ __device__ __forceinline__ void neuron_out(float w2, float xm, const float* row, float& s, float& c,
+                                                    float (&G)[kNdes])
+{
+    const float p = w2 * xm;
+    const float ep = fmaf(w2, xm, -p);
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c += e + ep;
+    const float d = w2 * fmaf(-xm, xm, 1.f);
+#pragma unroll
+    for (int v = 0; v < kNdes; ++v) G[v] = fmaf(d, row[v], G[v]);
+}
+
 // Network of Eqs. 21-22 and its input gradient.  w points at the parameter
 // vector [w1 (n_neu x 32), b1, w2, b2].  The pre-activations and the output
 // sum are compensated (rounding errors carried along) because the site energy
-// must hold ~1e-7 relative accuracy.  Returns U as hi + lo.
+// must hold ~1e-7 relative accuracy.  Neurons go two at a time so their
+// pre-activation chains overlap; every sum keeps the neuron order, so the
+// result does not depend on the pairing.  Returns U as hi + lo.
 __host__ __device__ __forceinline__ void network(const float* w, int n_neu, const float (&q)[kNdes],
                                                  float (&G)[kNdes], float& U_hi, float& U_lo)
 {
@@ -244,28 +273,26 @@ __host__ __device__ __forceinline__ void network(const float* w, int n_neu, cons
 #pragma unroll
     for (int v = 0; v < kNdes; ++v) G[v] = 0.f;
     float s = 0.f, c = 0.f;
-    for (int mu = 0; mu < n_neu; ++mu) {
-        const float* row = w + mu * kNdes;
-        // compensated (Kahan) pre-activation: the rounding of a plain FP32 dot
-        // product feeds straight into U for every unsaturated neuron
-        float a = -b1[mu], ca = 0.f;
+    int mu = 0;
+    for (; mu + 1 < n_neu; mu += 2) {
+        const float* r0 = w + mu * kNdes;
+        const float* r1 = r0 + kNdes;
+        float a0 = -b1[mu], c0 = 0.f, a1 = -b1[mu + 1], c1 = 0.f;
 #pragma unroll
         for (int v = 0; v < kNdes; ++v) {
-            const float y = fmaf(row[v], q[v], -ca);
-            const float t = a + y;
-            ca = (t - a) - y;
-            a = t;
+            kahan_step(r0[v], q[v], a0, c0);
+            kahan_step(r1[v], q[v], a1, c1);
         }
-        const float xm = tanhf(a - ca);
-        const float p = w2[mu] * xm;
-        const float ep = fmaf(w2[mu], xm, -p);
-        float t, e;
-        two_sum(s, p, t, e);
-        s = t;
-        c += e + ep;
-        const float d = w2[mu] * fmaf(-xm, xm, 1.f);
+        const float x0 = tanhf(a0 - c0), x1 = tanhf(a1 - c1);
+        neuron_out(w2[mu], x0, r0, s, c, G);
+        neuron_out(w2[mu + 1], x1, r1, s, c, G);
+    }
+    if (mu < n_neu) {
+        const float* r0 = w + mu * kNdes;
+        float a0 = -b1[mu], c0 = 0.f;
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) G[v] = fmaf(d, row[v], G[v]);
+        for (int v = 0; v < kNdes; ++v) kahan_step(r0[v], q[v], a0, c0);
+        neuron_out(w2[mu], tanhf(a0 - c0), r0, s, c, G);
     }
     float t, e;
     two_sum(s, -b2, t, e);

@@ -16,9 +16,11 @@
 //   W_ki = sum_j r_ij (x) (G_kj . J_ji)                            (Eq. 6)
 // and the RMSEs of Eqs. 29-34.  Kernels per evaluation:
 //   k_pack      z_pop -> member-innermost weight layout
-//   k_mlp_f32   FP32 network per (atom pair, member): U [N][P], G [N][32][Pst]
-//   k_pop_tc    the same network as two BF16 tensor-core GEMMs (nep_pop_tc.cu)
-//   k_contract  per (atom, member): F, W, |F - F_tar|^2, summed per chunk
+//   k_mlp_f32   FP32 network per (atom pair, member): U [N][P] and
+//               G [N][32][Pst] (member innermost, Pst = P rounded up to 4)
+//   k_pop_tc    the same network as BF16 tensor-core GEMMs (nep_pop_tc.cu)
+//   k_contract  warp per atom, two members per lane: F, W, |F - F_tar|^2,
+//               summed per chunk of 32 atoms
 //   k_loss      per member: per-structure sums in a fixed order, RMSEs
 // SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r), k_snes_update.
 #include <algorithm>
@@ -32,7 +34,8 @@ namespace nep {
 namespace {
 
 constexpr int kDsCap = 192;      // neighbour capacity per atom while building (within r_c)
-constexpr int kChunkAtoms = 8;   // atoms per contraction block
+constexpr int kChunkAtoms = 32;       // atoms per contraction block (chunks never span structures)
+constexpr int kContractThreads = 128;  // 4 warps, one atom per warp at a time
 constexpr int kMaxPop = 64;
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -339,92 +342,125 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
     }
 }
 
-// One block per chunk of <= kChunkAtoms atoms of one structure; thread t ->
-// atom begin + t / P, member t % P.  Per chunk and member: sums of U, of
-// |F - F_tar|^2 and of the six virial components, in a fixed order.
-__global__ void __launch_bounds__(1024) k_contract(int N, int P, int Pst, const int* __restrict__ chunk_begin,
-                                                   const int* __restrict__ chunk_end, const float* __restrict__ G,
-                                                   const double* __restrict__ U, const float* __restrict__ B,
-                                                   const long long* __restrict__ pstart, const int* __restrict__ pj,
-                                                   const PairRec* __restrict__ rec,
-                                                   const long long* __restrict__ aidx, const float* __restrict__ ang,
-                                                   const float* __restrict__ f_tar, double* __restrict__ partials)
+// One block (4 warps) per chunk of <= kChunkAtoms atoms of one structure; each
+// warp takes every 4th atom of the chunk, one atom at a time, and lane l holds
+// members 2l and 2l + 1.  So every pair record and Jacobian block is one
+// broadcast load for the whole warp, and every G_j row is read as coalesced
+// float2s.  Per chunk and member: sums of U, of |F - F_tar|^2 and of the six
+// virial components, in a fixed order (atoms in order within a warp, then
+// the warps in order).
+__global__ void __launch_bounds__(kContractThreads) k_contract(
+    int N, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
+    const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
+    const long long* __restrict__ pstart, const int* __restrict__ pj, const PairRec* __restrict__ rec,
+    const long long* __restrict__ aidx, const float* __restrict__ ang, const float* __restrict__ f_tar,
+    double* __restrict__ partials)
 {
-    __shared__ double red[kChunkAtoms][kMaxPop][8];
+    constexpr int kWarps = kContractThreads / 32;
+    __shared__ double red[kWarps][kMaxPop][8];
     const int c = blockIdx.x;
-    const int begin = chunk_begin[c], end = chunk_end[c];
-    const int t = threadIdx.x;
-    const int ia = t / P, k = t % P;
-    const int i = begin + ia;
-    if (ia < kChunkAtoms && i < end) {
-        const float* Gi = G + (size_t)i * kNdes * Pst + k;
-        float F[3] = {0.f, 0.f, 0.f};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k0 = 2 * lane;
+    const bool on0 = k0 < P, on1 = k0 + 1 < P;
+    const bool ld = k0 < Pst;  // Pst is even: the float2 at k0 is inside the row
+    // per-lane running sums live in shared memory (this lane's slots only)
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+        if (k0 + m < kMaxPop)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) red[warp][k0 + m][w] = 0.0;
+    const int end = chunk_end[c];
+    for (int i = chunk_begin[c] + warp; i < end; i += kWarps) {
+        float F[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        float W6[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+        // own term G_i . B_i
+        const float* Gi = G + (size_t)i * kNdes * Pst + k0;
         const float* Bi = B + (size_t)i * kNdes * 3;
 #pragma unroll 8
         for (int v = 0; v < kNdes; ++v) {
-            const float g = Gi[(size_t)v * Pst];
-            F[0] = fmaf(g, Bi[v * 3 + 0], F[0]);
-            F[1] = fmaf(g, Bi[v * 3 + 1], F[1]);
-            F[2] = fmaf(g, Bi[v * 3 + 2], F[2]);
+            const float2 g = ld ? *reinterpret_cast<const float2*>(Gi + (size_t)v * Pst) : make_float2(0.f, 0.f);
+            const float b0 = Bi[v * 3], b1 = Bi[v * 3 + 1], b2 = Bi[v * 3 + 2];
+            F[0][0] = fmaf(g.x, b0, F[0][0]);
+            F[0][1] = fmaf(g.x, b1, F[0][1]);
+            F[0][2] = fmaf(g.x, b2, F[0][2]);
+            F[1][0] = fmaf(g.y, b0, F[1][0]);
+            F[1][1] = fmaf(g.y, b1, F[1][1]);
+            F[1][2] = fmaf(g.y, b2, F[1][2]);
         }
-        float W6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        for (long long p = pstart[i]; p < pstart[i + 1]; ++p) {
+        const long long pe = pstart[i + 1];
+        for (long long p = pstart[i]; p < pe; ++p) {
             const int j = pj[p] & 0xFFFFFF;
-            const PairRec pr = rec[p];  // describes the pair (j -> i), r = r_ji
-            const float* Gj = G + (size_t)j * kNdes * Pst + k;
-            float cr = 0.f;
-#pragma unroll
-            for (int v = 0; v < kNR; ++v) cr = fmaf(Gj[(size_t)v * Pst], pr.gd[v], cr);
-            float pv[3] = {cr * pr.r[0], cr * pr.r[1], cr * pr.r[2]};
             const long long ai = aidx[p];
+            const PairRec pr = rec[p];  // describes the pair (j -> i), r = r_ji
+            const float* Gj = G + (size_t)j * kNdes * Pst + k0;
+            float2 gr[kNR];
+#pragma unroll
+            for (int v = 0; v < kNR; ++v)
+                gr[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
+            float cr0 = 0.f, cr1 = 0.f;
+#pragma unroll
+            for (int v = 0; v < kNR; ++v) {
+                cr0 = fmaf(gr[v].x, pr.gd[v], cr0);
+                cr1 = fmaf(gr[v].y, pr.gd[v], cr1);
+            }
+            float pv[2][3] = {{cr0 * pr.r[0], cr0 * pr.r[1], cr0 * pr.r[2]},
+                              {cr1 * pr.r[0], cr1 * pr.r[1], cr1 * pr.r[2]}};
             if (ai >= 0) {
                 const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)ai * (kNA * kLmax * 3));
-#pragma unroll
-                for (int u = 0; u < kNA * kLmax * 3 / 12; ++u) {  // 4 descriptors (12 floats) per step
+#pragma unroll 3
+                for (int u = 0; u < kNA * kLmax / 4; ++u) {  // 4 descriptors (12 floats) per step
                     const float4 a0 = A4[3 * u], a1 = A4[3 * u + 1], a2 = A4[3 * u + 2];
-                    const float g0 = Gj[(size_t)(kNR + 4 * u + 0) * Pst], g1 = Gj[(size_t)(kNR + 4 * u + 1) * Pst];
-                    const float g2 = Gj[(size_t)(kNR + 4 * u + 2) * Pst], g3 = Gj[(size_t)(kNR + 4 * u + 3) * Pst];
-                    pv[0] = fmaf(g0, a0.x, pv[0]);
-                    pv[1] = fmaf(g0, a0.y, pv[1]);
-                    pv[2] = fmaf(g0, a0.z, pv[2]);
-                    pv[0] = fmaf(g1, a0.w, pv[0]);
-                    pv[1] = fmaf(g1, a1.x, pv[1]);
-                    pv[2] = fmaf(g1, a1.y, pv[2]);
-                    pv[0] = fmaf(g2, a1.z, pv[0]);
-                    pv[1] = fmaf(g2, a1.w, pv[1]);
-                    pv[2] = fmaf(g2, a2.x, pv[2]);
-                    pv[0] = fmaf(g3, a2.y, pv[0]);
-                    pv[1] = fmaf(g3, a2.z, pv[1]);
-                    pv[2] = fmaf(g3, a2.w, pv[2]);
+                    const float ja[4][3] = {{a0.x, a0.y, a0.z}, {a0.w, a1.x, a1.y}, {a1.z, a1.w, a2.x},
+                                            {a2.y, a2.z, a2.w}};
+                    float2 g[4];
+#pragma unroll
+                    for (int d = 0; d < 4; ++d)
+                        g[d] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)(kNR + 4 * u + d) * Pst)
+                                  : make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        pv[0][0] = fmaf(g[d].x, ja[d][0], pv[0][0]);
+                        pv[0][1] = fmaf(g[d].x, ja[d][1], pv[0][1]);
+                        pv[0][2] = fmaf(g[d].x, ja[d][2], pv[0][2]);
+                        pv[1][0] = fmaf(g[d].y, ja[d][0], pv[1][0]);
+                        pv[1][1] = fmaf(g[d].y, ja[d][1], pv[1][1]);
+                        pv[1][2] = fmaf(g[d].y, ja[d][2], pv[1][2]);
+                    }
                 }
             }
-            // pv = dU_j/dr_ji for member k
-            F[0] -= pv[0];
-            F[1] -= pv[1];
-            F[2] -= pv[2];
-            // W_i^{ab} += r_ij^a pv^b with r_ij = -r_ji
-            W6[0] = fmaf(-pr.r[0], pv[0], W6[0]);  // xx
-            W6[1] = fmaf(-pr.r[1], pv[1], W6[1]);  // yy
-            W6[2] = fmaf(-pr.r[2], pv[2], W6[2]);  // zz
-            W6[3] = fmaf(-pr.r[0], pv[1], W6[3]);  // xy
-            W6[4] = fmaf(-pr.r[1], pv[2], W6[4]);  // yz
-            W6[5] = fmaf(-pr.r[2], pv[0], W6[5]);  // zx
+            // pv = dU_j/dr_ji per member; W_i^{ab} += r_ij^a pv^b with r_ij = -r_ji
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                F[m][0] -= pv[m][0];
+                F[m][1] -= pv[m][1];
+                F[m][2] -= pv[m][2];
+                W6[m][0] = fmaf(-pr.r[0], pv[m][0], W6[m][0]);  // xx
+                W6[m][1] = fmaf(-pr.r[1], pv[m][1], W6[m][1]);  // yy
+                W6[m][2] = fmaf(-pr.r[2], pv[m][2], W6[m][2]);  // zz
+                W6[m][3] = fmaf(-pr.r[0], pv[m][1], W6[m][3]);  // xy
+                W6[m][4] = fmaf(-pr.r[1], pv[m][2], W6[m][4]);  // yz
+                W6[m][5] = fmaf(-pr.r[2], pv[m][0], W6[m][5]);  // zx
+            }
         }
-        const float dx = F[0] - f_tar[(size_t)i * 3], dy = F[1] - f_tar[(size_t)i * 3 + 1],
-                    dz = F[2] - f_tar[(size_t)i * 3 + 2];
-        red[ia][k][0] = U[(size_t)i * P + k];
-        red[ia][k][1] = (double)dx * dx + (double)dy * dy + (double)dz * dz;
-        for (int w = 0; w < 6; ++w) red[ia][k][2 + w] = (double)W6[w];
-    } else if (ia < kChunkAtoms && k < kMaxPop) {
-        for (int w = 0; w < 8; ++w) red[ia][k][w] = 0.0;
+        const float tx = f_tar[(size_t)i * 3], ty = f_tar[(size_t)i * 3 + 1], tz = f_tar[(size_t)i * 3 + 2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            if (!(m == 0 ? on0 : on1)) continue;
+            const float dx = F[m][0] - tx, dy = F[m][1] - ty, dz = F[m][2] - tz;
+            double* r = red[warp][k0 + m];
+            r[0] += U[(size_t)i * P + k0 + m];
+            r[1] += (double)dx * dx + (double)dy * dy + (double)dz * dz;
+#pragma unroll
+            for (int w = 0; w < 6; ++w) r[2 + w] += (double)W6[m][w];
+        }
     }
     __syncthreads();
-    const int natoms = end - begin;
-    for (int e = t; e < P * 8; e += blockDim.x) {
-        const int kk = e / 8, w = e % 8;
+    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
+        const int k = e / 8, w = e % 8;
         double s = 0.0;
-        for (int a = 0; a < natoms; ++a) s += red[a][kk][w];
-        partials[((size_t)c * P + kk) * 8 + w] = s;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) s += red[q][k][w];
+        partials[((size_t)c * P + k) * 8 + w] = s;
     }
 }
 
@@ -644,6 +680,9 @@ int ensure_pop(nep_dataset* ds, int P)
         (rc = dalloc(&ds->partials, (size_t)ds->n_chunks * P * 8, nullptr)) ||
         (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)))
         return rc;
+    // members past P in the last group of G are never written: keep them zero
+    rc = cuda_fail(cudaMemset(ds->G, 0, sizeof(float) * (size_t)ds->N * kNdes * member_stride(P)), "clear G");
+    if (rc) return rc;
     ds->pop_cap = P;
     return NEP_OK;
 }
@@ -668,9 +707,9 @@ int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int preci
         k_mlp_f32<<<blocks_for(pairs * P, 256), 256, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
                                                               ds->b2t, ds->G, ds->U);
     }
-    k_contract<<<ds->n_chunks, kChunkAtoms * P, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
-                                                         ds->B, ds->pstart, ds->pj, ds->rec, ds->aidx, ds->ang,
-                                                         ds->f_tar, ds->partials);
+    k_contract<<<ds->n_chunks, kContractThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
+                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->aidx, ds->ang,
+                                                          ds->f_tar, ds->partials);
     const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
                            lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
     k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_natoms, ds->partials, ds->e_tar, ds->w_tar,

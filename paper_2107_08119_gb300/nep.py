@@ -44,6 +44,7 @@ _SIGNATURES = {
     "nep_set_parameters": (C.c_int, [_vp, _vp, C.c_int, _vp]),
     "nep_destroy": (C.c_int, [_vp]),
     "nep_compute_efv": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "nep_compute_efv_plain": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "nep_sync_status": (C.c_int, [_vp, _vp]),
     "nep_heat_current": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "nep_get_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
@@ -172,8 +173,9 @@ class NEP:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
 
     def compute(self, pos, box, *, e_total=True, e_atom=True, force=True, virial_atom=True, virial_total=True,
-                sync=True, stream=None):
-        """pos: CUDA float64 (3, n).  Returns a dict of device tensors."""
+                sync=True, stream=None, plain=False):
+        """pos: CUDA float64 (3, n).  Returns a dict of device tensors.
+        plain=True runs nep_compute_efv_plain (the plain FP32 comparator)."""
         pos = _soa_f64(pos)
         n = pos.shape[1]
         dev = pos.device
@@ -185,9 +187,10 @@ class NEP:
             "virial_total": torch.empty(9, dtype=torch.float64, device=dev) if virial_total else None,
         }
         b, bp = _box9(box)
-        _check(_lib.nep_compute_efv(self._h, n, bp, _ptr(pos), _ptr(out["e_total"]), _ptr(out["e_atom"]),
-                                    _ptr(out["force"]), _ptr(out["virial_atom"]), _ptr(out["virial_total"]),
-                                    _stream(stream)), "nep_compute_efv")
+        fn, name = ((_lib.nep_compute_efv_plain, "nep_compute_efv_plain") if plain
+                    else (_lib.nep_compute_efv, "nep_compute_efv"))
+        _check(fn(self._h, n, bp, _ptr(pos), _ptr(out["e_total"]), _ptr(out["e_atom"]), _ptr(out["force"]),
+                  _ptr(out["virial_atom"]), _ptr(out["virial_total"]), _stream(stream)), name)
         if sync:
             self.sync_status(stream)
         return {k: v for k, v in out.items() if v is not None}
