@@ -311,9 +311,12 @@ def run_gpu(args, rank, world, local):
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
         line["force_eval_vs_plain_fp32"] = force_eval_comparison(N, model, p0, box)
+        adj = adjoint_gradients(N)
         line["snes"] = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16),
                         "unit": "generation/s",
                         "workload": "200 periodic structures of 32-256 atoms, population 50, 32-30-1 NEP"}
+        adj["vs_one_fp32_generation"] = adj["ms_per_gradient"] / line["snes"]["fp32"]["ms_per_generation"]
+        line["adjoint"] = adj
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_md(seconds=args.cpu_seconds)
         print(json.dumps(line), flush=True)
@@ -350,10 +353,9 @@ def force_eval_comparison(N, model, pos, box, reps: int = 10):
             "evaluations_timed": reps}
 
 
-def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
-    """SNES on the 200-structure training workload, population 50: one
-    generation = draws + population evaluation + update, on the device.
-    Labels come from the CUDA force path with the teacher (a timing input)."""
+def training_set(N):
+    """The 200-structure training workload on the device, labelled by the CUDA
+    force path with the teacher (a timing input, not a checked value)."""
     import torch
     structures, teacher, pop = inputs.config4()
     model = N.NEP(np.asarray(teacher, np.float32))
@@ -365,6 +367,41 @@ def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
         F.append(out["force"].cpu().numpy().T)
         W.append([wt[0, 0], wt[1, 1], wt[2, 2], wt[0, 1], wt[1, 2], wt[2, 0]])
     ds = N.Dataset(model, structures, np.array(E), np.concatenate(F), np.array(W))
+    return model, ds, structures, pop
+
+
+def adjoint_gradients(N, reps: int = 20, warm: int = 3):
+    """Force-loss gradient of one parameter vector on the same training set:
+    nep_force_loss + nep_force_loss_backward (descriptors recomputed in both),
+    CUDA events on the current stream."""
+    import torch
+    model, ds, structures, pop = training_set(N)
+    z = torch.tensor(np.asarray(pop[0], np.float32), device="cuda")
+    for _ in range(warm):
+        ds.force_loss(z)
+        ds.force_loss_backward()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ds.force_loss(z)
+        ds.force_loss_backward()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    model.sync_status()
+    ms = e0.elapsed_time(e1) / reps
+    ds.close()
+    model.close()
+    return {"ms_per_gradient": ms, "gradients_per_s": 1e3 / ms, "n_par": model.hyper.n_par,
+            "gradients_timed": reps}
+
+
+def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
+    """SNES on the 200-structure training workload, population 50: one
+    generation = draws + population evaluation + update, on the device."""
+    import torch
+    model, ds, structures, pop = training_set(N)
     info = ds.info()
     snes = N.SNES(model, 50, np.zeros(model.hyper.n_par), np.full(model.hyper.n_par, 0.1), seed=2107081194)
     for _ in range(warm):
@@ -413,7 +450,8 @@ def run_snes_only():
     build.build()
     from paper_2107_08119_gb300 import nep as N
     out = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16)}
-    print(json.dumps({"snes": out}), flush=True)
+    adj = adjoint_gradients(N)
+    print(json.dumps({"snes": out, "adjoint": adj}), flush=True)
     return 0
 
 

@@ -167,7 +167,7 @@ int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_par
         const size_t N = (size_t)n, M = (size_t)m_cap;
         if ((rc = dev_alloc(&nl.count, N, "neighbour counts")) || (rc = dev_alloc(&nl.nbr, N * M, "neighbour list")) ||
             (rc = dev_alloc(&nl.rev, N * M, "reverse pair index")) ||
-            (rc = dev_alloc(&nl.pf, N * M * 3, "partial forces")) || (rc = dev_alloc(&nl.xh, N * 4, "positions")) ||
+            (rc = dev_alloc(&nl.pf, N * M * 4, "partial forces")) || (rc = dev_alloc(&nl.xh, N * 4, "positions")) ||
             (rc = dev_alloc(&nl.xl, N * 4, "positions")) || (rc = dev_alloc(&nl.atom_cell, N, "cell index")) ||
             (rc = dev_alloc(&nl.cell_atoms, N, "cell atoms")) || (rc = dev_alloc(&ws.force, N * 3, "forces")))
             return rc;
@@ -381,7 +381,7 @@ int compute_efv(nep_model* m, int n, const double* box9, const double* pos, doub
     int rc = setup_box(box9, rmax, box);
     if (rc) return rc;
     const int ncell = box.nc[0] * box.nc[1] * box.nc[2];
-    const int nblocks = (n + 127) / 128;
+    const int nblocks = site_blocks(n);
     if ((rc = ensure_workspace(m->ws, n, m->hp.max_neighbors, ncell, nblocks))) return rc;
     NeighborList& nl = m->ws.nl;
     Profiler::Slot* pn = m->prof.begin(NEP_PROFILE_NEIGHBOR, st);

@@ -12,7 +12,8 @@
 namespace nep {
 
 // Jacobian record of one pair, stored at the slot of the OTHER atom (see
-// k_ds_site): the radial part of d q_j / d r_ji.
+// k_ds_site): the radial part of d q_j / d r_ji; the angular 24 x 3 block is
+// ang[aidx[slot]].
 struct PairRec {
     float r[3];   // r_ij of the owning atom i (the vector from i to j)
     float gd[8];  // g_n'(|r|) / |r|, radial orders n = 0..7 (0 beyond r_c^R)

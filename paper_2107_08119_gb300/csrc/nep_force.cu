@@ -4,7 +4,8 @@
 // Pass A (k_site): one thread per atom runs the descriptor sums, the network
 // and the partial forces dU_i/dr_ij of all its pairs (nep_site.cuh); the
 // parameter vector sits in shared memory where every lane reads the same
-// word (broadcast).  Partial forces go to pf[k][c][i] (coalesced per slot).
+// word (broadcast).  Partial forces go to pf[k][i] as float4 records
+// (coalesced per slot).
 // Pass B (k_assemble): one thread per atom gathers its own p_ij and the
 // neighbours' p_ji through the reverse-pair index: F_i = sum_j (p_ij - p_ji)
 // and W_i = sum_j r_ij (x) p_ji (Eqs. 4-6).  In MD mode the same pass applies
@@ -20,28 +21,25 @@ namespace nep {
 
 namespace {
 
-constexpr int kSiteThreads = 128;
+constexpr int kSiteThreads = kSiteAtomsPerBlock;  // one thread per atom
 constexpr int kAsmThreads = 128;
 constexpr int kStageSlots = 96;  // slots per atom staged in shared memory
 
 // Copy the block's neighbour slots (slot-major: slot k of the block's atoms is
 // one contiguous run) into shared memory with 4-byte asynchronous copies, all
 // in flight at once; slots past an atom's count are not read.
-__device__ __forceinline__ int stage_slots(const int* __restrict__ nbr, int n, int i, bool active, int cnt,
-                                           int kstage, int* s_nbr)
+__device__ __forceinline__ void stage_slots(const int* __restrict__ nbr, int n, int i, bool active, int cnt,
+                                            int* s_nbr)
 {
-    const int tid = threadIdx.x, T = blockDim.x;
-    for (int k = 0; k < kstage; ++k) {
-        int* dst = s_nbr + k * T + tid;
-        if (active && k < cnt) {
+    if (active)
+        for (int k = 0; k < cnt; ++k) {
+            int* dst = s_nbr + k * kSiteThreads + threadIdx.x;
             const int* src = nbr + (size_t)k * n + i;
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
                          "l"(src)
                          : "memory");
         }
-    }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
-    return kstage;
 }
 
 // STAGED: the neighbour capacity fits the shared-memory staging (m_cap <= kStageSlots).
@@ -63,11 +61,11 @@ __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const i
     const bool active = i < n;
     const int cnt = active ? min(count[i], m_cap) : 0;
     int* s_nbr = reinterpret_cast<int*>(s_w + ((n_par + 31) / 32) * 32);
-    if (STAGED) stage_slots(nbr, n, i, active, cnt, m_cap, s_nbr);
+    if (STAGED) stage_slots(nbr, n, i, active, cnt, s_nbr);
     __syncthreads();
     const SlotTable T = STAGED ? SlotTable{s_nbr, kSiteThreads, (int)threadIdx.x} : SlotTable{nbr, n, i};
     float uh, ul;
-    const PfOut out{pf + (active ? i : 0), (size_t)3 * n, (size_t)n};
+    const PfOut out{pf + 4 * (size_t)(active ? i : 0), (size_t)4 * n, 1};
     site_partial_forces(active ? i : 0, active, n, cnt, T, xh, xl, box, P, out, uh, ul);
     if (active) {
         e[0] = (double)uh + (double)ul;

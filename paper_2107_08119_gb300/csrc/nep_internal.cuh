@@ -4,7 +4,8 @@
 //   positions        FP64 [3][n] (caller) + FP32 hi/lo split xh, xl [n] float4
 //   neighbour list   int32 nbr[M][n] = j | image_code << 24, count[n]
 //                    int32 rev[M][n] = slot of i in j's list (reverse pair)
-//   partial forces   FP32 pf[M][3][n] = dU_i/dr_ij (Eq. 23), slot-major
+//   partial forces   FP32 pf[M][n] float4 (x, y, z, unused) = dU_i/dr_ij
+//                    (Eq. 23), slot-major: one 16-byte gather per reverse pair
 //   forces           FP32 [3][n], per-atom virials FP32 [9][n]
 // Slot-major layouts make the per-atom loops of a warp read consecutive
 // addresses at every slot.
@@ -132,6 +133,37 @@ __host__ __device__ __forceinline__ void store_pos(float* __restrict__ xh, float
     reinterpret_cast<float4*>(xl)[i] = make_float4(l[0], l[1], l[2], 0.f);
 }
 
+// Warp sum of K <= 16 doubles held by every lane.  Each butterfly level keeps
+// half of the remaining components (the lane sends the half its partner keeps),
+// so a lane does 8 + 4 + 2 + 1 + 1 additions instead of 5 K.  On return
+// lanes 2c and 2c + 1 hold the warp total of component warp_comp(lane) (the
+// pattern is fixed, so the sums are deterministic).
+__device__ __forceinline__ int warp_comp(int lane)
+{
+    return ((lane & 16) ? 8 : 0) + ((lane & 8) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 2) ? 1 : 0);
+}
+
+template <int K>
+__device__ __forceinline__ double warp_sum_multi(const double (&v)[K])
+{
+    static_assert(K <= 16, "at most 16 components");
+    const int lane = threadIdx.x & 31;
+    double a[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) a[c] = c < K ? v[c] : 0.0;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int c = 0; c < h; ++c) {
+            const double send = upper ? a[c] : a[c + h];
+            const double keep = upper ? a[c + h] : a[c];
+            a[c] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return a[0] + __shfl_xor_sync(0xffffffffu, a[0], 1);
+}
+
 // Block-wide sum of K doubles; thread 0 writes out[k].  blockDim.x must be a
 // multiple of 32 and at most 1024.
 template <int K>
@@ -139,22 +171,36 @@ __device__ __forceinline__ void block_sum_store(double (&v)[K], double* __restri
 {
     __shared__ double red[32][K];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    if constexpr (K >= 4) {
+        const double s = warp_sum_multi<K>(v);
+        const int c = warp_comp(lane);
+        if ((lane & 1) == 0 && c < K) red[warp][c] = s;
+        __syncthreads();
+        if (warp == 0) {
+            double w[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k)
+            for (int k = 0; k < K; ++k) w[k] = lane < nw ? red[lane][k] : 0.0;
+            const double t = warp_sum_multi<K>(w);
+            if ((lane & 1) == 0 && c < K) out[c] = t;
+        }
+    } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    if (lane == 0)
+        for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[warp][k] = v[k];
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double s = lane < nw ? red[lane][k] : 0.0;
+            for (int k = 0; k < K; ++k) red[warp][k] = v[k];
+        __syncthreads();
+        if (warp == 0) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) out[k] = s;
+            for (int k = 0; k < K; ++k) {
+                double s = lane < nw ? red[lane][k] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) out[k] = s;
+            }
         }
     }
 }
@@ -207,6 +253,11 @@ struct ForceArgs {
     float rcR, rcA;
     Box box;
 };
+// the site pass runs kSiteAtomsPerBlock atoms per block; its per-block
+// energy partials need site_blocks(n) slots, which also bounds the block
+// counts of the assembly and of the plain comparator
+constexpr int kSiteAtomsPerBlock = 128;
+inline int site_blocks(int n) { return (n + kSiteAtomsPerBlock - 1) / kSiteAtomsPerBlock; }
 int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, double* e_partials,
                                unsigned* d_err, cudaStream_t st, int& nblocks);
 struct AssembleArgs {

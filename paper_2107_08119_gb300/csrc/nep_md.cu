@@ -49,10 +49,20 @@ __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__
         store_pos(xh, xl, i, xn);
         d2 = (float)dd;
     }
+    // block maximum, then one atomic per block (one per warp serialised
+    // thousands of atomics on a single word)
+    __shared__ float wmax[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-    // non-negative floats order like their bit patterns
-    if ((threadIdx.x & 31) == 0 && d2 > 0.f) atomicMax(ctl + kCtlDisp, __float_as_uint(d2));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        d2 = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
+        // non-negative floats order like their bit patterns
+        if (threadIdx.x == 0 && d2 > 0.f) atomicMax(ctl + kCtlDisp, __float_as_uint(d2));
+    }
 }
 
 __global__ void k_decide(unsigned* __restrict__ ctl, float thresh2, unsigned long long* __restrict__ rebuilds)
@@ -138,7 +148,7 @@ int nep_md_create(nep_model* m, int n, const double* box9, double mass, nep_md**
     md->r_list = (float)rmax;
     md->skin = (float)m->hp.skin;
     const int ncell = md->box.nc[0] * md->box.nc[1] * md->box.nc[2];
-    const int nb = blocks_for(n, 128);
+    const int nb = site_blocks(n);
     if ((rc = ensure_workspace(md->ws, n, m->hp.max_neighbors, ncell, nb))) {
         nep_md_destroy(md);
         return rc;
@@ -209,7 +219,7 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     nep_model* m = md->m;
     const int n = md->n;
     NeighborList& nl = md->ws.nl;
-    const int nb = blocks_for(n, 128);
+    const int nb = site_blocks(n);
     double* part_e = md->ws.partials;
     double* part_a = md->ws.partials + ((nb + 7) / 8) * 8;
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, md->box};

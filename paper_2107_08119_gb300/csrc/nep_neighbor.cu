@@ -6,16 +6,20 @@
 //      bin atoms into cells of edge >= the list radius;
 //   2. exclusive scan of the cell counts, scatter, then sort each cell by
 //      atom index so the list order (hence every FP32 sum) is deterministic;
-//   3. one thread per atom scans the 27 neighbouring cells and keeps every
+//   3. one warp per atom scans the 27 neighbouring cells and keeps every
 //      (j, image) with |r_ij| below the list radius (full list, both
 //      directions), then orders its slots by increasing distance (the
-//      partial-force buffer is free at this point and holds the sort keys);
-//   4. the reverse-pair index: for slot k of atom i, the slot of i in j's list.
+//      partial-force buffer is free at this point and holds the sort keys,
+//      atom-major: key[i * m_cap + k]);
+//   4. the reverse-pair index: for slot k of atom i, the slot of i in j's
+//      list, by binary search over j's contiguous keys (the list's values
+//      are also copied atom-major, behind the keys, for this search).
 // Boxes with fewer than 3 cells in a direction (small training cells) use a
 // brute-force scan over all atoms and images instead of cells.
 // Every kernel takes an optional device gate word: when it is zero the kernel
 // returns at once, which lets the MD step skip the rebuild without a host
 // round trip.
+#include <algorithm>
 #include <cstdio>
 
 #include "nep_internal.cuh"
@@ -128,7 +132,7 @@ __device__ __forceinline__ void list_push(int i, int n, int m_cap, int& cnt, int
 {
     if (cnt < m_cap) {
         nbr[(size_t)cnt * n + i] = value;
-        key[(size_t)cnt * n + i] = d2;
+        key[(size_t)i * m_cap + cnt] = d2;
     }
     ++cnt;
 }
@@ -137,25 +141,27 @@ __device__ __forceinline__ void list_push(int i, int n, int m_cap, int& cnt, int
 // k then holds roughly the k-th nearest neighbour of every atom, so the lanes
 // of a warp agree on which slots need the (long) angular work, and the force
 // pass can add the nearest (largest) terms last by walking ranks downwards.
-__device__ void sort_near_first(int i, int n, int cnt, int* __restrict__ nbr, float* __restrict__ key)
+__device__ void sort_near_first(int i, int n, int m_cap, int cnt, int* __restrict__ nbr, float* __restrict__ key)
 {
+    float* ki = key + (size_t)i * m_cap;
     for (int a = 1; a < cnt; ++a) {
-        const float kd = key[(size_t)a * n + i];
+        const float kd = ki[a];
         const int kv = nbr[(size_t)a * n + i];
         int b = a - 1;
-        while (b >= 0 && key[(size_t)b * n + i] > kd) {
-            key[(size_t)(b + 1) * n + i] = key[(size_t)b * n + i];
+        while (b >= 0 && ki[b] > kd) {
+            ki[b + 1] = ki[b];
             nbr[(size_t)(b + 1) * n + i] = nbr[(size_t)b * n + i];
             --b;
         }
-        key[(size_t)(b + 1) * n + i] = kd;
+        ki[b + 1] = kd;
         nbr[(size_t)(b + 1) * n + i] = kv;
     }
 }
 
 // One warp per atom.  The candidates of the 27 neighbouring cells are
 // numbered consecutively (cell by cell, atom index order inside a cell) and
-// the lanes take them 32 at a time; accepted pairs are compacted in candidate
+// the lanes take them 32 at a time (a lane finds its cell by stepping from
+// the round's first cell); accepted pairs are compacted in candidate
 // order with a ballot into the warp's shared buffer, which is then sorted by
 // (squared distance, packed index) with a bitonic network and written out.
 // Sorting on the pair of keys makes the order unique, hence deterministic.
@@ -185,8 +191,8 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     int* pre = sval + lcap;
     int* cst = pre + 32;
     int* ccode = cst + 32;
-    const int i = blockIdx.x * kVerletWarps + warp;
-    if (i >= n) return;  // whole warp
+    // a bounded grid strides over the atoms, so a gated-off launch is cheap
+    for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += gridDim.x * kVerletWarps) {
     float hi[3], li[3];
     load_pos(xh, xl, n, i, hi, li);
     const int cid = atom_cell[i];
@@ -217,56 +223,46 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     __syncwarp();
     const int total = pre[27];
     int cnt = 0;
-    // four candidates per lane per round: their index and position loads are
-    // all in flight before the first distance test
-    constexpr int kU = 4;
-    for (int base = 0; base < total; base += 32 * kU) {
-        int value[kU];
-        float d2[kU];
-        bool accept[kU];
-        int jj[kU], code[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int idx = base + 32 * u + lane;
-            jj[u] = -1;
-            code[u] = 0;
-            if (idx < total) {
-                int c = 0;  // last cell whose prefix is <= idx
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (c + step < 27 && pre[c + step] <= idx) c += step;
-                jj[u] = cell_atoms[cst[c] + idx - pre[c]];
-                code[u] = ccode[c];
+    // Quick rejection with the hi parts only: their pair vector is within
+    // 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a pair that
+    // the exact (canonical hi/lo) test below would keep.
+    const float rq = sqrtf(rv2) + 1e-3f, rq2 = rq * rq;
+    int c0 = 0;  // cell of this round's first candidate (warp-uniform)
+    for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        bool accept = false;
+        int value = 0;
+        float d2 = 0.f;
+        int c = c0;
+        if (idx < total) {
+            while (pre[c + 1] <= idx) ++c;  // a cell holds ~12 atoms: 0-3 steps
+            const int j = cell_atoms[cst[c] + idx - pre[c]];
+            const int code = ccode[c];
+            if (!(j == i && code == kImgCenter)) {
+                float hj[3], lj[3];
+                load_pos(xh, xl, n, j, hj, lj);
+                int sx, sy, sz;
+                image_shift(code, sx, sy, sz);
+                const float qx = fmaf((float)sx, b.Lh[0], hj[0] - hi[0]);
+                const float qy = fmaf((float)sy, b.Lh[1], hj[1] - hi[1]);
+                const float qz = fmaf((float)sz, b.Lh[2], hj[2] - hi[2]);
+                if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2) {
+                    float rx, ry, rz;
+                    pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
+                    d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    accept = d2 < rv2;
+                    value = j | (code << 24);
+                }
             }
         }
-        float hj[kU][3], lj[kU][3];
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (jj[u] >= 0) load_pos(xh, xl, n, jj[u], hj[u], lj[u]);
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            accept[u] = false;
-            value[u] = 0;
-            d2[u] = 0.f;
-            const int j = jj[u];
-            if (j >= 0 && !(j == i && code[u] == kImgCenter)) {
-                float rx, ry, rz;
-                pair_vector(i, j, code[u], hi, li, hj[u], lj[u], b, rx, ry, rz);
-                d2[u] = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                accept[u] = d2[u] < rv2;
-                value[u] = j | (code[u] << 24);
-            }
+        c0 = __shfl_sync(0xffffffffu, c, 31);
+        const unsigned mask = __ballot_sync(0xffffffffu, accept);
+        const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+        if (accept && pos < lcap) {
+            skey[pos] = d2;
+            sval[pos] = value;
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const unsigned mask = __ballot_sync(0xffffffffu, accept[u]);
-            const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-            if (accept[u] && pos < lcap) {
-                skey[pos] = d2[u];
-                sval[pos] = value[u];
-            }
-            cnt += __popc(mask);
-        }
+        cnt += __popc(mask);
     }
     __syncwarp();
     if (lane == 0) count[i] = cnt;
@@ -282,7 +278,8 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     for (int size = 2; size <= S; size <<= 1)
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int t = lane; t < S / 2; t += 32) {
-                const int lo = 2 * stride * (t / stride) + (t % stride), hi2 = lo + stride;
+                // stride is a power of two: lo = 2 stride (t / stride) + t % stride
+                const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1)), hi2 = lo + stride;
                 const bool asc = (lo & size) == 0;
                 const float ka = skey[lo], kb = skey[hi2];
                 const int va = sval[lo], vb = sval[hi2];
@@ -295,9 +292,13 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
             }
             __syncwarp();
         }
+    int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
     for (int k = lane; k < m; k += 32) {
         nbr[(size_t)k * n + i] = sval[k];
-        key[(size_t)k * n + i] = skey[k];
+        key[(size_t)i * m_cap + k] = skey[k];
+        vala[(size_t)i * m_cap + k] = sval[k];
+    }
+    __syncwarp();  // the warp's buffers are reused by its next atom
     }
 }
 
@@ -327,37 +328,45 @@ __global__ void k_verlet_brute(int n, int m_cap, float rv2, const float* __restr
     }
     count[i] = cnt;
     if (cnt > m_cap) atomicOr(err, kErrOverflow);
-    sort_near_first(i, n, cnt < m_cap ? cnt : m_cap, nbr, key);
+    const int m = cnt < m_cap ? cnt : m_cap;
+    sort_near_first(i, n, m_cap, m, nbr, key);
+    int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
+    for (int k = 0; k < m; ++k) vala[(size_t)i * m_cap + k] = nbr[(size_t)k * n + i];
 }
 
 // rev[k][i] = slot of (i, -image) in j's list.  The pair vectors are exactly
 // antisymmetric, so both directions carry the same squared distance and j's
 // list (sorted by it) is binary-searched; a miss (only possible after an
-// overflow) is latched as an error.
-__global__ void k_reverse(int n, int m_cap, const int* __restrict__ count, const int* __restrict__ nbr,
-                          const float* __restrict__ key, int* __restrict__ rev, unsigned* err, const unsigned* gate)
+// overflow) is latched as an error.  One warp per atom, a lane per slot; the
+// keys and values are read from their atom-major copies, so every search
+// stays inside one atom's contiguous row.
+__global__ void k_reverse(int n, int m_cap, const int* __restrict__ count, const float* __restrict__ key,
+                          int* __restrict__ rev, unsigned* err, const unsigned* gate)
 {
     if (gated_off(gate)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int* vala = reinterpret_cast<const int*>(key + (size_t)m_cap * n);
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += warps) {
     const int ci = min(count[i], m_cap);
-    for (int k = 0; k < ci; ++k) {
-        const int v = nbr[(size_t)k * n + i];
+    for (int k = lane; k < ci; k += 32) {
+        const int v = vala[(size_t)i * m_cap + k];
         const int j = v & 0xFFFFFF;
         const int target = i | ((124 - (v >> 24)) << 24);
-        const float kd = key[(size_t)k * n + i];
+        const float kd = key[(size_t)i * m_cap + k];
         const int cj = min(count[j], m_cap);
+        const float* kj = key + (size_t)j * m_cap;  // j's keys, contiguous
         int lo = 0, hi = cj;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (key[(size_t)mid * n + j] < kd)
+            if (kj[mid] < kd)
                 lo = mid + 1;
             else
                 hi = mid;
         }
         int found = -1;
-        for (int t = lo; t < cj && key[(size_t)t * n + j] == kd; ++t)
-            if (nbr[(size_t)t * n + j] == target) {
+        for (int t = lo; t < cj && kj[t] == kd; ++t)
+            if (vala[(size_t)j * m_cap + t] == target) {
                 found = t;
                 break;
             }
@@ -367,9 +376,14 @@ __global__ void k_reverse(int n, int m_cap, const int* __restrict__ count, const
         }
         rev[(size_t)k * n + i] = found;
     }
+    }
 }
 
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+// grid of the warp-per-atom list kernels: 152 SMs x 16 blocks of 4 warps
+// keep every SM full, and a launch whose gate is off retires in microseconds
+constexpr int kListGridCap = 152 * 16;
 
 }  // namespace
 
@@ -392,14 +406,15 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool
         int lcap = 32;
         while (lcap < nl.m_cap) lcap <<= 1;
         const size_t smem = (size_t)kVerletWarps * (2 * lcap + 96) * sizeof(float);
-        k_verlet_cells<<<blocks_for(n, kVerletWarps), 32 * kVerletWarps, smem, st>>>(
+        k_verlet_cells<<<std::min(blocks_for(n, kVerletWarps), kListGridCap), 32 * kVerletWarps, smem, st>>>(
             n, nl.m_cap, lcap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
             d_err, b, d_gate);
     } else {
         k_verlet_brute<<<blocks_for(n, 128), 128, 0, st>>>(n, nl.m_cap, rv2, nl.xh, nl.xl, nl.count, nl.nbr, nl.pf,
                                                            d_err, b, d_gate);
     }
-    k_reverse<<<blocks_for(n, 128), 128, 0, st>>>(n, nl.m_cap, nl.count, nl.nbr, nl.pf, nl.rev, d_err, d_gate);
+    k_reverse<<<std::min(blocks_for(n, 4), kListGridCap), 128, 0, st>>>(n, nl.m_cap, nl.count, nl.pf, nl.rev, d_err,
+                                                                         d_gate);
     return cuda_fail(cudaGetLastError(), "neighbour-list kernels");
 }
 

@@ -207,8 +207,8 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_pf(int n, int m_cap, co
             for (int a = 0; a < kNR; ++a) s += Gv[a] * dg[a];
             for (int c = 0; c < 3; ++c) p[c] = s * r[c] / d;
         }
-        float* o = pf + (size_t)k * 3 * n + i;
-        for (int c = 0; c < 3; ++c) o[(size_t)c * n] = p[c];
+        float* o = pf + 4 * ((size_t)k * n + i);  // pf[k][i] float4 record
+        for (int c = 0; c < 3; ++c) o[c] = p[c];
     }
     Gathered A;
     if (!gather_angular(i, n, cnt, nbr, xh, xl, box, rcA, A)) {
@@ -233,8 +233,8 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_pf(int n, int m_cap, co
             for (int cc = 0; cc < 3; ++cc)
                 p[cc] += 2.f * (s1 * A.u[a][cc] + s2 * (A.u[b][cc] - c * A.u[a][cc]) / A.r[a]);
         }
-        float* o = pf + (size_t)A.slot[a] * 3 * n + i;
-        for (int cc = 0; cc < 3; ++cc) o[(size_t)cc * n] += p[cc];
+        float* o = pf + 4 * ((size_t)A.slot[a] * n + i);
+        for (int cc = 0; cc < 3; ++cc) o[cc] += p[cc];
     }
 }
 

@@ -165,15 +165,18 @@ __host__ __device__ __forceinline__ constexpr float sh_c(int lm)
 // l of harmonic index lm (0-based l - 1)
 __host__ __device__ __forceinline__ constexpr int sh_l(int lm) { return lm < 3 ? 0 : (lm < 8 ? 1 : (lm < 15 ? 2 : 3)); }
 
-// S[n][lm] += g[n] * Y_lm(u)
-__host__ __device__ __forceinline__ void sh_acc(float (&S)[kNA][kLM], const float (&g)[kNA], int lm, float Y)
+// S[n][lm] += g[n] * Y_lm(u) for the NN radial orders held (all kNA, or a
+// lane's half of them in the lane-pair form)
+template <int NN>
+__host__ __device__ __forceinline__ void sh_acc(float (&S)[NN][kLM], const float (&g)[NN], int lm, float Y)
 {
 #pragma unroll
-    for (int n = 0; n < kNA; ++n) S[n][lm] = fmaf(g[n], Y, S[n][lm]);
+    for (int n = 0; n < NN; ++n) S[n][lm] = fmaf(g[n], Y, S[n][lm]);
 }
 
-__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float (&g)[kNA],
-                                                  float (&S)[kNA][kLM])
+template <int NN>
+__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float (&g)[NN],
+                                                  float (&S)[NN][kLM])
 {
     NEP_SH_LOCALS(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) sh_acc(S, g, lm, Yv);
@@ -184,13 +187,14 @@ __host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, con
 // One harmonic's contribution to the angular partial force:
 //   cg = sum_n A[n][lm] g_n, cd = sum_n A[n][lm] g_n'
 //   B += cd Y, V += cg grad_u Y.
-__host__ __device__ __forceinline__ void sh_term(const float (&A)[kNA][kLM], const float (&g)[kNA],
-                                                 const float (&dg)[kNA], int lm, float Y, float gx, float gy,
+template <int NN>
+__host__ __device__ __forceinline__ void sh_term(const float (&A)[NN][kLM], const float (&g)[NN],
+                                                 const float (&dg)[NN], int lm, float Y, float gx, float gy,
                                                  float gz, float& B, float& Vx, float& Vy, float& Vz)
 {
     float cg = 0.f, cd = 0.f;
 #pragma unroll
-    for (int n = 0; n < kNA; ++n) {
+    for (int n = 0; n < NN; ++n) {
         cg = fmaf(A[n][lm], g[n], cg);
         cd = fmaf(A[n][lm], dg[n], cd);
     }
@@ -200,8 +204,9 @@ __host__ __device__ __forceinline__ void sh_term(const float (&A)[kNA][kLM], con
     Vz = fmaf(cg, gz, Vz);
 }
 
-__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const float (&A)[kNA][kLM],
-                                                  const float (&g)[kNA], const float (&dg)[kNA], float& B,
+template <int NN>
+__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const float (&A)[NN][kLM],
+                                                  const float (&g)[NN], const float (&dg)[NN], float& B,
                                                   float& Vx, float& Vy, float& Vz)
 {
     NEP_SH_LOCALS(x, y, z)
@@ -261,9 +266,7 @@ __host__ __device__ __forceinline__ void neuron_out(float w2, float xm, const fl
 // Network of Eqs. 21-22 and its input gradient.  w points at the parameter
 // vector [w1 (n_neu x 32), b1, w2, b2].  The pre-activations and the output
 // sum are compensated (rounding errors carried along) because the site energy
-// must hold ~1e-7 relative accuracy.  Neurons go two at a time so their
-// pre-activation chains overlap; every sum keeps the neuron order, so the
-// result does not depend on the pairing.  Returns U as hi + lo.
+// must hold ~1e-7 relative accuracy.  Returns U as hi + lo.
 __host__ __device__ __forceinline__ void network(const float* w, int n_neu, const float (&q)[kNdes],
                                                  float (&G)[kNdes], float& U_hi, float& U_lo)
 {
@@ -273,26 +276,12 @@ __host__ __device__ __forceinline__ void network(const float* w, int n_neu, cons
 #pragma unroll
     for (int v = 0; v < kNdes; ++v) G[v] = 0.f;
     float s = 0.f, c = 0.f;
-    int mu = 0;
-    for (; mu + 1 < n_neu; mu += 2) {
-        const float* r0 = w + mu * kNdes;
-        const float* r1 = r0 + kNdes;
-        float a0 = -b1[mu], c0 = 0.f, a1 = -b1[mu + 1], c1 = 0.f;
+    for (int mu = 0; mu < n_neu; ++mu) {
+        const float* row = w + mu * kNdes;
+        float a = -b1[mu], ca = 0.f;
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) {
-            kahan_step(r0[v], q[v], a0, c0);
-            kahan_step(r1[v], q[v], a1, c1);
-        }
-        const float x0 = tanhf(a0 - c0), x1 = tanhf(a1 - c1);
-        neuron_out(w2[mu], x0, r0, s, c, G);
-        neuron_out(w2[mu + 1], x1, r1, s, c, G);
-    }
-    if (mu < n_neu) {
-        const float* r0 = w + mu * kNdes;
-        float a0 = -b1[mu], c0 = 0.f;
-#pragma unroll
-        for (int v = 0; v < kNdes; ++v) kahan_step(r0[v], q[v], a0, c0);
-        neuron_out(w2[mu], tanhf(a0 - c0), r0, s, c, G);
+        for (int v = 0; v < kNdes; ++v) kahan_step(row[v], q[v], a, ca);
+        neuron_out(w2[mu], tanhf(a - ca), row, s, c, G);
     }
     float t, e;
     two_sum(s, -b2, t, e);
@@ -491,7 +480,8 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
     }
 }
 
-// Force and per-atom virial of atom i from the stored partial forces:
+// Force and per-atom virial of atom i from the stored partial forces
+// (pf[k][i] float4 records, see nep_internal.cuh):
 //   F_i = sum_j (p_ij - p_ji),  W_i^{ab} = sum_j r_ij^a p_ji^b   (Eqs. 4-6).
 __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, float rc2max,
                                                        const int* __restrict__ count, const SlotTable& nbr,
@@ -517,14 +507,13 @@ __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, 
         const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
         if (!(d2 < rc2max)) continue;
         const int kr = rev[(size_t)k * n + i];
-        const float* po = pf + (size_t)k * 3 * n + i;
-        const float* pi = pf + (size_t)kr * 3 * n + j;
-        float pji[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            pji[c] = pi[(size_t)c * n];
-            F[c] += po[(size_t)c * n] - pji[c];
-        }
+        // own p_ij and the neighbour's p_ji: one 16-byte record each
+        const float4 po = NEP_LDG(reinterpret_cast<const float4*>(pf) + (size_t)k * n + i);
+        const float4 pq = NEP_LDG(reinterpret_cast<const float4*>(pf) + (size_t)kr * n + j);
+        const float pji[3] = {pq.x, pq.y, pq.z};
+        F[0] += po.x - pji[0];
+        F[1] += po.y - pji[1];
+        F[2] += po.z - pji[2];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll

@@ -11,7 +11,7 @@
 // inputs and outputs, all in memory it already owns.
 //
 // Limits: at most NEP_STATIC_MAX_ATOMS atoms, NEP_STATIC_MAX_NEIGHBORS slots
-// per atom and NEP_STATIC_MAX_CELLS cells (about 8.3 MB, resident on every
+// per atom and NEP_STATIC_MAX_CELLS cells (about 10.0 MB, resident on every
 // GPU that loads the library until the process exits).  Every call shares
 // the array, which keeps the previous call's contents; calls that overlap on
 // the GPU (different streams, or host threads without ordering) race on it.
@@ -25,7 +25,7 @@ namespace {
 constexpr int kStaticAtoms = NEP_STATIC_MAX_ATOMS;
 constexpr int kStaticSlots = NEP_STATIC_MAX_NEIGHBORS;
 constexpr int kStaticCells = NEP_STATIC_MAX_CELLS;
-constexpr int kStaticBlocks = (kStaticAtoms + 127) / 128;
+constexpr int kStaticBlocks = (kStaticAtoms + kSiteAtomsPerBlock - 1) / kSiteAtomsPerBlock;
 
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -34,7 +34,7 @@ constexpr size_t kOffCount = 0;
 constexpr size_t kOffNbr = kOffCount + align256(sizeof(int) * kStaticAtoms);
 constexpr size_t kOffRev = kOffNbr + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
 constexpr size_t kOffPf = kOffRev + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
-constexpr size_t kOffXh = kOffPf + align256(sizeof(float) * kStaticAtoms * kStaticSlots * 3);
+constexpr size_t kOffXh = kOffPf + align256(sizeof(float) * kStaticAtoms * kStaticSlots * 4);
 constexpr size_t kOffXl = kOffXh + align256(sizeof(float) * kStaticAtoms * 4);
 constexpr size_t kOffAtomCell = kOffXl + align256(sizeof(float) * kStaticAtoms * 4);
 constexpr size_t kOffCellAtoms = kOffAtomCell + align256(sizeof(int) * kStaticAtoms);
@@ -159,7 +159,7 @@ extern "C" int nep_compute_efv_static(const nep_hyper* hp, const float* z, int n
                                   st)))
         return rc;
     ForceArgs fa{z, hp->n_neu, (float)hp->rc_R, (float)hp->rc_A, box};
-    const int nblocks = (n + 127) / 128;
+    const int nblocks = site_blocks(n);
     double* part_e = partials;
     double* part_v = partials + ((nblocks + 7) / 8) * 8;
     int nb1 = 0, nb2 = 0, nc2 = 0;

@@ -226,7 +226,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
                 for (int c = 0; c < 3; ++c) B[a][c] = fmaf(pr.gd[a], r[c], B[a][c]);
             }
         }
-        const long long dst = rev[p];
+        const long long dst = rev[p];  // j's slot for i: where atom j's contraction reads it
         rec[dst] = pr;
         if (d2 < rcA2) {
             float g[kNA], dg[kNA];
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
 // float2s.  Per chunk and member: sums of U, of |F - F_tar|^2 and of the six
 // virial components, in a fixed order (atoms in order within a warp, then
 // the warps in order).
-__global__ void __launch_bounds__(kContractThreads) k_contract(
+__global__ void __launch_bounds__(kContractThreads, 6) k_contract(
     int N, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
     const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
     const long long* __restrict__ pstart, const int* __restrict__ pj, const PairRec* __restrict__ rec,
@@ -812,6 +812,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     up(ds->sstart, hsstart.data(), sizeof(int) * (S + 1));
     up(ds->s_natoms, hnat.data(), sizeof(int) * S);
     up(ds->s_chunk0, hchunk0.data(), sizeof(int) * (S + 1));
+
     up(ds->chunk_begin, hcb.data(), sizeof(int) * hcb.size());
     up(ds->chunk_end, hce.data(), sizeof(int) * hce.size());
     up(dpos, hpos.data(), sizeof(double) * hpos.size());
