@@ -55,6 +55,33 @@ def flops_per_atom(m_r: float, m_a: float, n_neu: int = 30) -> float:
     return 134.0 * m_r + 1500.0 * m_a + 288.0 + 4.0 * n_neu * 32 + 10.0 * n_neu
 
 
+SITE_SOURCES = ("paper_2107_08119_gb300/csrc/nep_site.cuh", "paper_2107_08119_gb300/csrc/nep_force.cu",
+                "paper_2107_08119_gb300/csrc/nep_internal.cuh")
+SITE_PROFILE = os.path.join(ROOT, "profiles", "k_site_md_125k.json")
+
+
+def sources_digest(paths) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def site_dram_traffic():
+    """DRAM bytes (read + write) of one k_site launch on this workload, from
+    the committed ncu summary, or None when the kernel sources changed since
+    those counters were taken."""
+    try:
+        prof = json.load(open(SITE_PROFILE))
+    except (OSError, ValueError):
+        return None
+    if prof.get("sources_sha256") != sources_digest(SITE_SOURCES):
+        return None
+    return prof.get("dram_bytes_per_launch")
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
     """152 SMs x 128 FP32 lanes x 2 flops per FMA x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -182,22 +209,10 @@ def run_gpu(args, rank, world, local):
     hyper = N.Hyper()
     model = N.NEP(np.asarray(z, np.float32), hyper)
 
-    # average neighbour counts within r_c^R and r_c^A of the starting state (flop model)
+    # average neighbour counts within r_c^R and r_c^A (flop model of the site
+    # pass), of the starting state and again of the final state
     p0 = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
-    model.compute(p0, box)
-    cnt, nbr = model.neighbors(n)
-    j = (nbr & 0xFFFFFF).long()
-    code = (nbr >> 24).long()
-    valid = torch.arange(nbr.shape[0], device="cuda")[:, None] < cnt[None, :]
-    L = torch.tensor(np.diag(box), device="cuda")
-    wrapped = p0 - L[:, None] * torch.floor(p0 / L[:, None])
-    shifts = torch.stack([code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2]).double() * L[:, None, None]
-    jj = j.clamp(max=n - 1)
-    r = wrapped[:, jj] + shifts - wrapped[:, None, :]
-    d = torch.linalg.norm(r, dim=0)
-    m_r = float(((d < hyper.rc_R) & valid).sum()) / n
-    m_a = float(((d < hyper.rc_A) & valid).sum()) / n
-    del j, code, valid, shifts, jj, r, d, nbr, cnt
+    m_r0, m_a0 = neighbour_counts(model, p0, box, hyper)
 
     md = N.MD(model, n, box, inputs.MASS_SI)
     p = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
@@ -234,6 +249,8 @@ def run_gpu(args, rank, world, local):
     rebuilds = md.rebuild_count() - rebuilds0
     th = thermo[:K].cpu().numpy()
     etot = th[:, 0] + th[:, 1]
+    m_r1, m_a1 = neighbour_counts(model, p, box, hyper)
+    m_r, m_a = 0.5 * (m_r0 + m_r1), 0.5 * (m_a0 + m_a1)
 
     if args.only == "md":
         if rank == 0:
@@ -295,11 +312,13 @@ def run_gpu(args, rank, world, local):
                              "neighbour list, reverse index and partial forces ~340 MB > 129 MB)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "mean_neighbors_rcR": m_r, "mean_neighbors_rcA": m_a,
+                       "mean_neighbors_start_end": [[m_r0, m_a0], [m_r1, m_a1]],
                        "phase_ms_per_step": {k: v[0] / K for k, v in prof.items()},
                        "energy_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / n)},
             "roofline": {"kernel": "k_site (descriptors + network + partial forces)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None, "flops_per_atom": flops_atom, "kernel_ms": site_ms,
+                         "traffic": site_dram_traffic(), "traffic_unit": "bytes per launch (ncu dram read + write)",
+                         "flops_per_atom": flops_atom, "kernel_ms": site_ms,
                          "kernel_share_of_step": prof["site"][0] / t_max if t_max > 0 else None,
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz (fp32 pipe, derived)"},
             "clocks": clocks,
@@ -311,6 +330,8 @@ def run_gpu(args, rank, world, local):
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
         line["force_eval_vs_plain_fp32"] = force_eval_comparison(N, model, p0, box)
+        v0 = torch.tensor(vel.T.copy(), dtype=torch.float64, device="cuda")
+        line["md_nvt_hnemd"] = md_nvt_hnemd(N, model, p0, v0, box)
         adj = adjoint_gradients(N)
         line["snes"] = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16),
                         "unit": "generation/s",
@@ -325,6 +346,56 @@ def run_gpu(args, rank, world, local):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def md_nvt_hnemd(N, model, pos, vel, box, steps: int = 200, warm: int = 5):
+    """The same 125k-atom state under a Berendsen thermostat (300 K, tau =
+    100 fs) with HNEMD driving F_e = (1e-4, 0, 0) /A, heat current every
+    step: atom-step/s of the heat-transport variant of the MD step."""
+    import torch
+    n = pos.shape[1]
+    md = N.MD(model, n, box, inputs.MASS_SI)
+    md.set_thermostat(300.0, 100.0)
+    md.set_hnemd([1e-4, 0.0, 0.0])
+    p, v = pos.clone(), vel.clone()
+    thermo = torch.zeros(max(steps, warm), N.THERMO_COLS, dtype=torch.float64, device="cuda")
+    heat = torch.zeros(max(steps, warm), 3, dtype=torch.float64, device="cuda")
+    md.step(p, v, warm, 1.0, thermo, heat)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    md.step(p, v, steps, 1.0, thermo, heat)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    md.sync_status()
+    ms = e0.elapsed_time(e1) / steps
+    th = thermo[:steps].cpu().numpy()
+    T = 2 * th[:, 1] / ((3 * n - 3) * inputs.KB_EV)
+    md.close()
+    return {"atom_steps_per_s": n / (ms / 1e3), "ms_per_step": ms, "steps_timed": steps,
+            "temperature_K_last": float(T[-1]), "mean_heat_current_x": float(heat[:steps, 0].mean().item())}
+
+
+def neighbour_counts(model, pos, box, hyper):
+    """Mean number of neighbours within r_c^R and r_c^A per atom of the state
+    `pos` (CUDA (3, n) FP64), from the list the library builds for it."""
+    import torch
+    n = pos.shape[1]
+    model.compute(pos, box)
+    cnt, nbr = model.neighbors(n)
+    j = (nbr & 0xFFFFFF).long()
+    code = (nbr >> 24).long()
+    valid = torch.arange(nbr.shape[0], device="cuda")[:, None] < cnt[None, :]
+    L = torch.tensor(np.diag(box), device="cuda")
+    wrapped = pos - L[:, None] * torch.floor(pos / L[:, None])
+    shifts = torch.stack([code // 25 - 2, (code // 5) % 5 - 2, code % 5 - 2]).double() * L[:, None, None]
+    jj = j.clamp(max=n - 1)
+    r = wrapped[:, jj] + shifts - wrapped[:, None, :]
+    d = torch.linalg.norm(r, dim=0)
+    m_r = float(((d < hyper.rc_R) & valid).sum()) / n
+    m_a = float(((d < hyper.rc_A) & valid).sum()) / n
+    return m_r, m_a
 
 
 def force_eval_comparison(N, model, pos, box, reps: int = 10):

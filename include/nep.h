@@ -164,6 +164,32 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
 /* Mark positions as changed by the caller: the next step rebuilds the list and forces. */
 int nep_md_invalidate(nep_md* md);
 
+/*
+ * nep_md_set_thermostat -- Berendsen velocity rescaling for the following
+ * steps: after the second half kick and the heat current of each step,
+ * v *= lambda with lambda^2 = 1 + (dt/tau)(T0/T - 1) and T = 2 E_kin /
+ * ((3N - 3) k_B); the thermo row then reports E_kin after the rescaling, J
+ * before it.  The paper runs its speed benchmark in the NVT ensemble without
+ * naming a thermostat (Sec. III.C); this is the simplest deterministic one.
+ *   t0   target temperature (K), >= 0.   tau  coupling time (fs); <= 0: off (NVE).
+ * Errors: NEP_ERR_ARG.  nep_md_step needs n >= 2 while it is on.
+ */
+int nep_md_set_thermostat(nep_md* md, double t0, double tau);
+
+/*
+ * nep_md_set_hnemd -- homogeneous non-equilibrium MD driving (Sec. II.B):
+ * every atom feels F_i^ext = F_e . W_i, (F_i^ext)^b = sum_a F_e^a W_i^{ab},
+ * minus its mean over all atoms so that the total momentum is kept; then
+ * <J>/(T V) = kappa F_e gives the thermal conductivity.  With the drive on,
+ * each step assembles F and W_i, sums W, and applies the second half kick
+ * with F + F^ext in a separate kernel; the forces the next step starts from
+ * (and nep_md_forces) include F^ext.
+ *   fe   host [3] driving force parameter (1/A), or NULL / all zero: off.
+ * The next nep_md_step recomputes the starting forces.
+ * Errors: NEP_ERR_ARG, NEP_ERR_OOM.
+ */
+int nep_md_set_hnemd(nep_md* md, const double* fe);
+
 /* Number of neighbour-list builds so far (synchronises `stream`). */
 int nep_md_rebuild_count(nep_md* md, long long* count, void* stream);
 

@@ -797,6 +797,78 @@ int orc_md(const orc_hyper* h, const double* z, int n, const double* box, double
     return rcode;
 }
 
+/*
+ * The same integrator with two optional extensions for heat transport:
+ *   HNEMD driving (Sec. II.B): every atom feels F_i^ext = F_e . W_i, i.e.
+ *     (F_i^ext)^b = sum_a F_e^a W_i^{ab}, minus the mean over all atoms so that
+ *     the total momentum is kept (fe = NULL or zero: off);
+ *   Berendsen thermostat: after the second half kick and the heat current,
+ *     v *= lambda with lambda^2 = 1 + (dt/tau)(T0/T - 1), T = 2 E_kin /
+ *     ((3N - 3) k_B) (tau <= 0: off).
+ * Per step: v += dt/2 F/m; x += dt v; F = F_NEP(x) + F_ext; v += dt/2 F/m;
+ * J = sum_i W_i v_i; thermostat.  thermo (n_steps x 2): potential energy and
+ * kinetic energy after the thermostat.  J (n_steps x 3): before it.
+ * With fe = NULL and tau <= 0 this is orc_md step for step.
+ */
+int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
+               double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
+               double* J)
+{
+    const double conv = amu_a2_fs2_in_ev();
+    const double kb = 8.617333262e-5; /* eV/K, CODATA 2018 */
+    double* U = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double* W = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
+    const int drive = fe && (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
+    int rcode = orc_efv(h, z, n, box, pos, U, F, W);
+    const double acc = dt * 0.5 / (mass * conv);
+    for (int s = -1; s < n_steps && !rcode; ++s) {
+        if (s >= 0) {
+            for (int k = 0; k < 3 * n; ++k) {
+                vel[k] += acc * F[k];
+                pos[k] += dt * vel[k];
+            }
+            rcode = orc_efv(h, z, n, box, pos, U, F, W);
+            if (rcode) break;
+        }
+        if (drive) {
+            double mean[3] = {0.0, 0.0, 0.0};
+            double* fx = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+            for (int i = 0; i < n; ++i)
+                for (int b = 0; b < 3; ++b) {
+                    double f = 0.0;
+                    for (int a = 0; a < 3; ++a) f += fe[a] * W[9 * (size_t)i + 3 * a + b];
+                    fx[3 * (size_t)i + b] = f;
+                    mean[b] += f;
+                }
+            for (int b = 0; b < 3; ++b) mean[b] /= (double)n;
+            for (int i = 0; i < n; ++i)
+                for (int b = 0; b < 3; ++b) F[3 * (size_t)i + b] += fx[3 * (size_t)i + b] - mean[b];
+            free(fx);
+        }
+        if (s < 0) continue; /* forces of the starting configuration */
+        for (int k = 0; k < 3 * n; ++k) vel[k] += acc * F[k];
+        if (J) orc_heat_current(n, W, vel, J + 3 * s);
+        double ep = 0.0, ek = 0.0;
+        for (int i = 0; i < n; ++i) ep += U[i];
+        for (int k = 0; k < 3 * n; ++k) ek += 0.5 * mass * conv * vel[k] * vel[k];
+        if (tau > 0.0 && n > 1 && ek > 0.0) {
+            const double T = 2.0 * ek / ((3.0 * n - 3.0) * kb);
+            const double lam = sqrt(1.0 + dt / tau * (t0 / T - 1.0));
+            for (int k = 0; k < 3 * n; ++k) vel[k] *= lam;
+            ek *= lam * lam;
+        }
+        if (thermo) {
+            thermo[2 * s + 0] = ep;
+            thermo[2 * s + 1] = ek;
+        }
+    }
+    free(U);
+    free(F);
+    free(W);
+    return rcode;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Loss function, Eqs. 29-34.                                                */
 /* ------------------------------------------------------------------------ */

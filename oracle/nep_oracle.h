@@ -46,6 +46,9 @@ int orc_site(const orc_hyper* h, const double* z, int n, const double* box, cons
 void orc_heat_current(int n, const double* W, const double* v, double* J);
 int orc_md(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel, double mass,
            double dt, int n_steps, double* thermo, double* J);
+int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
+               double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
+               double* J);
 int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms, const double* boxes,
              const double* pos, const double* e_tar, const double* f_tar, const double* w_tar,
              const double* lambdas, double* out);

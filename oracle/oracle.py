@@ -83,6 +83,8 @@ def _load():
             "orc_efv_sample": (C.c_int, [_H, _D, C.c_int, _D, _D, C.c_int, _I, _D, _D, _D]),
             "orc_heat_current": (None, [C.c_int, _D, _D, _D]),
             "orc_md": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, _D, _D]),
+            "orc_md_ext": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, C.c_double,
+                                     C.c_double, _D, _D, _D]),
             "orc_loss": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D]),
             "orc_force_loss_grad": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D]),
             "orc_snes_utilities": (None, [C.c_int, _D]),
@@ -235,6 +237,25 @@ def md(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: int):
     J = np.zeros((n_steps, 3))
     _check(_load().orc_md(C.byref(h.c()), _d(z), pos.shape[0], _d(box), _d(pos), _d(vel), float(mass), float(dt),
                           n_steps, _d(thermo), _d(J)), "md")
+    return pos, vel, thermo, J
+
+
+def md_ext(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: int, t0: float = 0.0,
+           tau: float = 0.0, fe=None):
+    """Velocity Verlet with an optional Berendsen thermostat (target t0 K,
+    coupling time tau fs; tau <= 0 off) and HNEMD driving force F_e (1/A;
+    None off).  Returns (pos, vel, thermo[n_steps, 2], J[n_steps, 3]) with
+    E_kin after the thermostat and J before it."""
+    z = _f64(z)
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    box = _f64(box, (3, 3))
+    thermo = np.zeros((n_steps, 2))
+    J = np.zeros((n_steps, 3))
+    fe_arr = None if fe is None else _f64(fe, (3,))
+    _check(_load().orc_md_ext(C.byref(h.c()), _d(z), pos.shape[0], _d(box), _d(pos), _d(vel), float(mass),
+                              float(dt), n_steps, float(t0), float(tau), None if fe_arr is None else _d(fe_arr),
+                              _d(thermo), _d(J)), "md_ext")
     return pos, vel, thermo, J
 
 

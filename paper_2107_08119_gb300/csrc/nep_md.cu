@@ -11,7 +11,15 @@
 //   k_assemble     forces, second half kick, E_kin, virial and heat current
 //                  J = sum_i W_i . v_i (Eq. 7), per-block FP64 sums
 //   k_reduce       block sums in a fixed order
-//   k_md_finish    thermo row and J of this step
+//   k_md_finish    thermo row and J of this step; Berendsen factor
+// Optional extensions (nep_md_set_thermostat, nep_md_set_hnemd):
+//   HNEMD          the assembly writes F and W_i; after the virial sum,
+//                  k_hnemd_kick adds F_i^ext = F_e . W_i - F_e . W / N
+//                  (Sec. II.B; the mean removed so the momentum is kept) and
+//                  does the second half kick, E_kin and J
+//   thermostat     Berendsen: after J, v *= lambda with lambda^2 = 1 +
+//                  (dt/tau)(T0/T - 1), T from E_kin with 3N - 3 degrees of
+//                  freedom (k_scale_v)
 #include <cmath>
 #include <new>
 
@@ -20,6 +28,8 @@
 // 1 amu A^2 / fs^2 expressed in eV (CODATA 2018 atomic mass constant and
 // elementary charge).
 static constexpr double kAmuA2Fs2InEv = 1.66053906660e-27 * 1.0e-20 / 1.0e-30 / 1.602176634e-19;
+// Boltzmann constant in eV/K (CODATA 2018)
+static constexpr double kBoltzmannEv = 8.617333262e-5;
 
 namespace nep {
 namespace {
@@ -74,16 +84,70 @@ __global__ void k_decide(unsigned* __restrict__ ctl, float thresh2, unsigned lon
     if (go) *rebuilds += 1ull;
 }
 
-__global__ void k_md_finish(const double* __restrict__ red, double* __restrict__ thermo, double* __restrict__ heat,
-                            unsigned* __restrict__ ctl)
+// Second half kick with the HNEMD driving force, E_kin and J per block.
+// W is the per-atom virial [9][n]; wtot the total virial (row-major).
+__global__ void k_hnemd_kick(int n, float* __restrict__ F, const float* __restrict__ W, double* __restrict__ vel,
+                             double fe0, double fe1, double fe2, const double* __restrict__ wtot, double inv_n,
+                             double hdtm, double kef, double* __restrict__ partials, unsigned* err)
 {
-    // red: [0] E_pot, [1..9] W (row-major), [10] E_kin, [11..13] J
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+        const double fe[3] = {fe0, fe1, fe2};
+        float w[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) w[c] = W[(size_t)c * n + i];
+        double v[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            double fx = 0.0, fm = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                fx += fe[a] * (double)w[3 * a + b];
+                fm += fe[a] * wtot[3 * a + b];
+            }
+            const float ft = (float)((double)F[(size_t)b * n + i] + fx - fm * inv_n);
+            F[(size_t)b * n + i] = ft;
+            v[b] = vel[(size_t)b * n + i] + hdtm * (double)ft;
+            vel[(size_t)b * n + i] = v[b];
+        }
+        if (!isfinite(v[0] + v[1] + v[2])) atomicOr(err, kErrNonFinite);
+        acc[0] = kef * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            acc[1 + a] = (double)(w[3 * a] * (float)v[0]) + (double)(w[3 * a + 1] * (float)v[1]) +
+                         (double)(w[3 * a + 2] * (float)v[2]);
+    }
+    block_sum_store<4>(acc, partials + (size_t)blockIdx.x * 4);
+}
+
+// v *= lambda (the Berendsen factor k_md_finish left in red[14])
+__global__ void k_scale_v(int n, double* __restrict__ vel, const double* __restrict__ red)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double lam = red[14];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vel[(size_t)c * n + i] *= lam;
+}
+
+__global__ void k_md_finish(double* __restrict__ red, double* __restrict__ thermo, double* __restrict__ heat,
+                            unsigned* __restrict__ ctl, double t0, double tau, double dt, double dof_kb)
+{
+    // red: [0] E_pot, [1..9] W (row-major), [10] E_kin, [11..13] J, [14] lambda
     const unsigned s = ctl[kCtlStep];
     if (threadIdx.x == 0) {
+        double ek = red[10];
+        if (tau > 0.0) {
+            const double T = 2.0 * ek / dof_kb;
+            const double lam = T > 0.0 ? sqrt(1.0 + dt / tau * (t0 / T - 1.0)) : 1.0;
+            red[14] = lam;
+            ek *= lam * lam;
+        }
         if (thermo) {
             double* t = thermo + (size_t)s * NEP_THERMO_COLS;
             t[0] = red[0];
-            t[1] = red[10];
+            t[1] = ek;
             t[2] = red[1];  // xx
             t[3] = red[5];  // yy
             t[4] = red[9];  // zz
@@ -120,6 +184,11 @@ struct nep_md {
     unsigned long long* rebuilds = nullptr;
     double* red = nullptr;
     bool need_init = true;
+    // Berendsen thermostat (tau <= 0: off) and HNEMD driving force
+    double t0 = 0.0, tau = 0.0;
+    double fe[3] = {0.0, 0.0, 0.0};
+    bool drive = false;
+    float* w_atom = nullptr;  // [9][n] per-atom virials (HNEMD only)
 };
 
 extern "C" {
@@ -178,7 +247,41 @@ int nep_md_destroy(nep_md* md)
     if (md->ctl) cudaFree(md->ctl);
     if (md->rebuilds) cudaFree(md->rebuilds);
     if (md->red) cudaFree(md->red);
+    if (md->w_atom) cudaFree(md->w_atom);
     delete md;
+    return NEP_OK;
+}
+
+int nep_md_set_thermostat(nep_md* md, double t0, double tau)
+{
+    if (!md || (tau > 0.0 && !(t0 >= 0.0))) {
+        set_error("nep_md_set_thermostat: NULL handle or negative target temperature");
+        return NEP_ERR_ARG;
+    }
+    md->t0 = t0;
+    md->tau = tau > 0.0 ? tau : 0.0;
+    return NEP_OK;
+}
+
+int nep_md_set_hnemd(nep_md* md, const double* fe)
+{
+    if (!md) {
+        set_error("nep_md_set_hnemd: NULL handle");
+        return NEP_ERR_ARG;
+    }
+    for (int c = 0; c < 3; ++c) md->fe[c] = fe ? fe[c] : 0.0;
+    md->drive = md->fe[0] != 0.0 || md->fe[1] != 0.0 || md->fe[2] != 0.0;
+    if (md->drive && !md->w_atom) {
+        cudaError_t e = cudaMalloc((void**)&md->w_atom, sizeof(float) * 9 * (size_t)md->n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            md->w_atom = nullptr;
+            md->drive = false;
+            set_error("nep_md_set_hnemd: %s", cudaGetErrorString(e));
+            return NEP_ERR_OOM;
+        }
+    }
+    md->need_init = true;  // the next step recomputes the starting forces with (or without) the drive
     return NEP_OK;
 }
 
@@ -222,11 +325,19 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     const int nb = site_blocks(n);
     double* part_e = md->ws.partials;
     double* part_a = md->ws.partials + ((nb + 7) / 8) * 8;
+    double* part_h = part_a + 13 * (size_t)blocks_for(n, 128);  // HNEMD kick partials
+    const bool drive = md->drive;
+    const int nbk = blocks_for(n, 256);
+    const double kef = 0.5 * md->mass * kAmuA2Fs2InEv;
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, md->box};
     const double rmax = m->hp.rc_R > m->hp.rc_A ? m->hp.rc_R : m->hp.rc_A;
     const double conv = kAmuA2Fs2InEv;
     int rc;
     const unsigned* gate = md->ctl + kCtlGate;
+    if (md->tau > 0.0 && n < 2) {
+        set_error("nep_md_step: the thermostat needs at least two atoms");
+        return NEP_ERR_ARG;
+    }
 
     if (md->need_init) {
         // forces of the starting configuration (list built unconditionally)
@@ -238,7 +349,15 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         aa.rc_max = (float)rmax;
         aa.box = md->box;
         aa.vel = nullptr;
-        if ((rc = launch_assemble(aa, nl, n, md->ws.force, nullptr, part_a, m->d_err, st, b2, c2))) return rc;
+        if ((rc = launch_assemble(aa, nl, n, md->ws.force, drive ? md->w_atom : nullptr, part_a, m->d_err, st, b2,
+                                  c2)))
+            return rc;
+        if (drive) {
+            // the starting forces include the driving force (no kick: hdt/m = 0)
+            if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
+            k_hnemd_kick<<<nbk, 256, 0, st>>>(n, md->ws.force, md->w_atom, vel, md->fe[0], md->fe[1], md->fe[2],
+                                              md->red + 1, 1.0 / n, 0.0, kef, part_h, m->d_err);
+        }
         if ((rc = cuda_fail(cudaMemsetAsync(md->ctl, 0, sizeof(unsigned) * kCtlWords, st), "cudaMemsetAsync")))
             return rc;
         md->need_init = false;
@@ -264,17 +383,26 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         AssembleArgs aa{};
         aa.rc_max = (float)rmax;
         aa.box = md->box;
-        aa.vel = vel;
+        aa.vel = drive ? nullptr : vel;  // with HNEMD the kick waits for the total virial
         aa.half_dt_over_m = hdtm;
-        aa.ke_factor = 0.5 * md->mass * conv;
+        aa.ke_factor = kef;
         aa.heat = heat != nullptr;
         ps = m->prof.begin(NEP_PROFILE_ASSEMBLE, st);
-        if ((rc = launch_assemble(aa, nl, n, md->ws.force, nullptr, part_a, m->d_err, st, b2, c2))) return rc;
+        if ((rc = launch_assemble(aa, nl, n, md->ws.force, drive ? md->w_atom : nullptr, part_a, m->d_err, st, b2,
+                                  c2)))
+            return rc;
         m->prof.end(ps, st);
         pk = m->prof.begin(NEP_PROFILE_STEP, st);
         if ((rc = launch_reduce(part_e, b1, 1, md->red, st))) return rc;
         if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
-        k_md_finish<<<1, 32, 0, st>>>(md->red, thermo, heat, md->ctl);
+        if (drive) {
+            k_hnemd_kick<<<nbk, 256, 0, st>>>(n, md->ws.force, md->w_atom, vel, md->fe[0], md->fe[1], md->fe[2],
+                                              md->red + 1, 1.0 / n, hdtm, kef, part_h, m->d_err);
+            if ((rc = launch_reduce(part_h, nbk, 4, md->red + 10, st))) return rc;
+        }
+        k_md_finish<<<1, 32, 0, st>>>(md->red, thermo, heat, md->ctl, md->t0, md->tau, dt,
+                                      (3.0 * n - 3.0) * kBoltzmannEv);
+        if (md->tau > 0.0 && n > 1) k_scale_v<<<nbk, 256, 0, st>>>(n, vel, md->red);
         m->prof.end(pk, st);
         if ((rc = cuda_fail(cudaGetLastError(), "md step kernels"))) return rc;
     }

@@ -193,112 +193,112 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     int* ccode = cst + 32;
     // a bounded grid strides over the atoms, so a gated-off launch is cheap
     for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += gridDim.x * kVerletWarps) {
-    float hi[3], li[3];
-    load_pos(xh, xl, n, i, hi, li);
-    const int cid = atom_cell[i];
-    const int cz = cid % b.nc[2];
-    const int cy = (cid / b.nc[2]) % b.nc[1];
-    const int cx = cid / (b.nc[2] * b.nc[1]);
-    // lane c < 27 describes neighbouring cell c (x slowest, z fastest)
-    int ccount = 0;
-    if (lane < 27) {
-        int x2 = cx + lane / 9 - 1, y2 = cy + (lane / 3) % 3 - 1, z2 = cz + lane % 3 - 1;
-        int sx = 0, sy = 0, sz = 0;
-        if (x2 < 0) { x2 += b.nc[0]; sx = -1; } else if (x2 >= b.nc[0]) { x2 -= b.nc[0]; sx = 1; }
-        if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
-        if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
-        const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
-        cst[lane] = cell_start[c2];
-        ccount = cell_start[c2 + 1] - cst[lane];
-        ccode[lane] = image_code(sx, sy, sz);
-    }
-    // exclusive prefix of the cell sizes
-    int incl = ccount;
+        float hi[3], li[3];
+        load_pos(xh, xl, n, i, hi, li);
+        const int cid = atom_cell[i];
+        const int cz = cid % b.nc[2];
+        const int cy = (cid / b.nc[2]) % b.nc[1];
+        const int cx = cid / (b.nc[2] * b.nc[1]);
+        // lane c < 27 describes neighbouring cell c (x slowest, z fastest)
+        int ccount = 0;
+        if (lane < 27) {
+            int x2 = cx + lane / 9 - 1, y2 = cy + (lane / 3) % 3 - 1, z2 = cz + lane % 3 - 1;
+            int sx = 0, sy = 0, sz = 0;
+            if (x2 < 0) { x2 += b.nc[0]; sx = -1; } else if (x2 >= b.nc[0]) { x2 -= b.nc[0]; sx = 1; }
+            if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
+            if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
+            const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
+            cst[lane] = cell_start[c2];
+            ccount = cell_start[c2 + 1] - cst[lane];
+            ccode[lane] = image_code(sx, sy, sz);
+        }
+        // exclusive prefix of the cell sizes
+        int incl = ccount;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane < 28) pre[lane] = incl - ccount;
-    __syncwarp();
-    const int total = pre[27];
-    int cnt = 0;
-    // Quick rejection with the hi parts only: their pair vector is within
-    // 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a pair that
-    // the exact (canonical hi/lo) test below would keep.
-    const float rq = sqrtf(rv2) + 1e-3f, rq2 = rq * rq;
-    int c0 = 0;  // cell of this round's first candidate (warp-uniform)
-    for (int base = 0; base < total; base += 32) {
-        const int idx = base + lane;
-        bool accept = false;
-        int value = 0;
-        float d2 = 0.f;
-        int c = c0;
-        if (idx < total) {
-            while (pre[c + 1] <= idx) ++c;  // a cell holds ~12 atoms: 0-3 steps
-            const int j = cell_atoms[cst[c] + idx - pre[c]];
-            const int code = ccode[c];
-            if (!(j == i && code == kImgCenter)) {
-                float hj[3], lj[3];
-                load_pos(xh, xl, n, j, hj, lj);
-                int sx, sy, sz;
-                image_shift(code, sx, sy, sz);
-                const float qx = fmaf((float)sx, b.Lh[0], hj[0] - hi[0]);
-                const float qy = fmaf((float)sy, b.Lh[1], hj[1] - hi[1]);
-                const float qz = fmaf((float)sz, b.Lh[2], hj[2] - hi[2]);
-                if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2) {
-                    float rx, ry, rz;
-                    pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
-                    d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    accept = d2 < rv2;
-                    value = j | (code << 24);
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < 28) pre[lane] = incl - ccount;
+        __syncwarp();
+        const int total = pre[27];
+        int cnt = 0;
+        // Quick rejection with the hi parts only: their pair vector is within
+        // 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a pair that
+        // the exact (canonical hi/lo) test below would keep.
+        const float rq = sqrtf(rv2) + 1e-3f, rq2 = rq * rq;
+        int c0 = 0;  // cell of this round's first candidate (warp-uniform)
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            bool accept = false;
+            int value = 0;
+            float d2 = 0.f;
+            int c = c0;
+            if (idx < total) {
+                while (pre[c + 1] <= idx) ++c;  // a cell holds ~12 atoms: 0-3 steps
+                const int j = cell_atoms[cst[c] + idx - pre[c]];
+                const int code = ccode[c];
+                if (!(j == i && code == kImgCenter)) {
+                    float hj[3], lj[3];
+                    load_pos(xh, xl, n, j, hj, lj);
+                    int sx, sy, sz;
+                    image_shift(code, sx, sy, sz);
+                    const float qx = fmaf((float)sx, b.Lh[0], hj[0] - hi[0]);
+                    const float qy = fmaf((float)sy, b.Lh[1], hj[1] - hi[1]);
+                    const float qz = fmaf((float)sz, b.Lh[2], hj[2] - hi[2]);
+                    if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2) {
+                        float rx, ry, rz;
+                        pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
+                        d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        accept = d2 < rv2;
+                        value = j | (code << 24);
+                    }
                 }
             }
-        }
-        c0 = __shfl_sync(0xffffffffu, c, 31);
-        const unsigned mask = __ballot_sync(0xffffffffu, accept);
-        const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-        if (accept && pos < lcap) {
-            skey[pos] = d2;
-            sval[pos] = value;
-        }
-        cnt += __popc(mask);
-    }
-    __syncwarp();
-    if (lane == 0) count[i] = cnt;
-    if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
-    const int m = cnt < m_cap ? cnt : m_cap;
-    int S = 1;
-    while (S < (cnt < lcap ? cnt : lcap)) S <<= 1;
-    for (int t = (cnt < lcap ? cnt : lcap) + lane; t < S; t += 32) {
-        skey[t] = 3.0e38f;
-        sval[t] = 0x7fffffff;
-    }
-    __syncwarp();
-    for (int size = 2; size <= S; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < S / 2; t += 32) {
-                // stride is a power of two: lo = 2 stride (t / stride) + t % stride
-                const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1)), hi2 = lo + stride;
-                const bool asc = (lo & size) == 0;
-                const float ka = skey[lo], kb = skey[hi2];
-                const int va = sval[lo], vb = sval[hi2];
-                if (pair_greater(ka, va, kb, vb) == asc) {
-                    skey[lo] = kb;
-                    sval[lo] = vb;
-                    skey[hi2] = ka;
-                    sval[hi2] = va;
-                }
+            c0 = __shfl_sync(0xffffffffu, c, 31);
+            const unsigned mask = __ballot_sync(0xffffffffu, accept);
+            const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
+            if (accept && pos < lcap) {
+                skey[pos] = d2;
+                sval[pos] = value;
             }
-            __syncwarp();
+            cnt += __popc(mask);
         }
-    int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
-    for (int k = lane; k < m; k += 32) {
-        nbr[(size_t)k * n + i] = sval[k];
-        key[(size_t)i * m_cap + k] = skey[k];
-        vala[(size_t)i * m_cap + k] = sval[k];
-    }
-    __syncwarp();  // the warp's buffers are reused by its next atom
+        __syncwarp();
+        if (lane == 0) count[i] = cnt;
+        if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
+        const int m = cnt < m_cap ? cnt : m_cap;
+        int S = 1;
+        while (S < (cnt < lcap ? cnt : lcap)) S <<= 1;
+        for (int t = (cnt < lcap ? cnt : lcap) + lane; t < S; t += 32) {
+            skey[t] = 3.0e38f;
+            sval[t] = 0x7fffffff;
+        }
+        __syncwarp();
+        for (int size = 2; size <= S; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int t = lane; t < S / 2; t += 32) {
+                    // stride is a power of two: lo = 2 stride (t / stride) + t % stride
+                    const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1)), hi2 = lo + stride;
+                    const bool asc = (lo & size) == 0;
+                    const float ka = skey[lo], kb = skey[hi2];
+                    const int va = sval[lo], vb = sval[hi2];
+                    if (pair_greater(ka, va, kb, vb) == asc) {
+                        skey[lo] = kb;
+                        sval[lo] = vb;
+                        skey[hi2] = ka;
+                        sval[hi2] = va;
+                    }
+                }
+                __syncwarp();
+            }
+        int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
+        for (int k = lane; k < m; k += 32) {
+            nbr[(size_t)k * n + i] = sval[k];
+            key[(size_t)i * m_cap + k] = skey[k];
+            vala[(size_t)i * m_cap + k] = sval[k];
+        }
+        __syncwarp();  // the warp's buffers are reused by its next atom
     }
 }
 
@@ -348,34 +348,34 @@ __global__ void k_reverse(int n, int m_cap, const int* __restrict__ count, const
     const int* vala = reinterpret_cast<const int*>(key + (size_t)m_cap * n);
     const int warps = (int)((gridDim.x * blockDim.x) >> 5);
     for (int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += warps) {
-    const int ci = min(count[i], m_cap);
-    for (int k = lane; k < ci; k += 32) {
-        const int v = vala[(size_t)i * m_cap + k];
-        const int j = v & 0xFFFFFF;
-        const int target = i | ((124 - (v >> 24)) << 24);
-        const float kd = key[(size_t)i * m_cap + k];
-        const int cj = min(count[j], m_cap);
-        const float* kj = key + (size_t)j * m_cap;  // j's keys, contiguous
-        int lo = 0, hi = cj;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (kj[mid] < kd)
-                lo = mid + 1;
-            else
-                hi = mid;
-        }
-        int found = -1;
-        for (int t = lo; t < cj && kj[t] == kd; ++t)
-            if (vala[(size_t)j * m_cap + t] == target) {
-                found = t;
-                break;
+        const int ci = min(count[i], m_cap);
+        for (int k = lane; k < ci; k += 32) {
+            const int v = vala[(size_t)i * m_cap + k];
+            const int j = v & 0xFFFFFF;
+            const int target = i | ((124 - (v >> 24)) << 24);
+            const float kd = key[(size_t)i * m_cap + k];
+            const int cj = min(count[j], m_cap);
+            const float* kj = key + (size_t)j * m_cap;  // j's keys, contiguous
+            int lo = 0, hi = cj;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (kj[mid] < kd)
+                    lo = mid + 1;
+                else
+                    hi = mid;
             }
-        if (found < 0) {
-            atomicOr(err, kErrReverse);
-            found = k;  // keeps later reads in bounds
+            int found = -1;
+            for (int t = lo; t < cj && kj[t] == kd; ++t)
+                if (vala[(size_t)j * m_cap + t] == target) {
+                    found = t;
+                    break;
+                }
+            if (found < 0) {
+                atomicOr(err, kErrReverse);
+                found = k;  // keeps later reads in bounds
+            }
+            rev[(size_t)k * n + i] = found;
         }
-        rev[(size_t)k * n + i] = found;
-    }
     }
 }
 

@@ -52,6 +52,8 @@ _SIGNATURES = {
     "nep_md_destroy": (C.c_int, [_vp]),
     "nep_md_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
     "nep_md_invalidate": (C.c_int, [_vp]),
+    "nep_md_set_thermostat": (C.c_int, [_vp, C.c_double, C.c_double]),
+    "nep_md_set_hnemd": (C.c_int, [_vp, _vp]),
     "nep_md_rebuild_count": (C.c_int, [_vp, C.POINTER(C.c_longlong), _vp]),
     "nep_md_forces": (_vp, [_vp]),
     "nep_profile_enable": (C.c_int, [_vp, C.c_int]),
@@ -272,7 +274,8 @@ def compute_efv_static(z_dev, pos, box, hyper: Hyper = Hyper(max_neighbors=STATI
 
 
 class MD:
-    """NVE velocity-Verlet integrator on a NEP model (handle of nep_md_create)."""
+    """Velocity-Verlet integrator on a NEP model (handle of nep_md_create):
+    NVE, optionally with a Berendsen thermostat and HNEMD driving."""
 
     def __init__(self, model: NEP, n: int, box, mass: float):
         self.model = model
@@ -307,6 +310,16 @@ class MD:
 
     def invalidate(self):
         _check(_lib.nep_md_invalidate(self._h), "nep_md_invalidate")
+
+    def set_thermostat(self, t0: float, tau: float):
+        """Berendsen rescaling towards t0 K with coupling time tau fs (tau <= 0: off)."""
+        _check(_lib.nep_md_set_thermostat(self._h, float(t0), float(tau)), "nep_md_set_thermostat")
+
+    def set_hnemd(self, fe):
+        """HNEMD driving force parameter F_e (1/A, three values), or None: off."""
+        arr = None if fe is None else _host(fe, np.float64, (3,))
+        _check(_lib.nep_md_set_hnemd(self._h, None if arr is None else arr.ctypes.data_as(_vp)),
+               "nep_md_set_hnemd")
 
     def rebuild_count(self, stream=None) -> int:
         c = C.c_longlong()

@@ -91,3 +91,63 @@ def test_md_split_calls_equal_one_call(N):
         md.close()
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
     model.close()
+
+
+def _md_ext_compare(N, orc, steps, t0, tau, fe):
+    import torch
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    n = len(pos)
+    model = N.NEP(z)
+    md = N.MD(model, n, box, inputs.MASS_SI)
+    md.set_thermostat(t0, tau)
+    md.set_hnemd(fe)
+    p, v = soa(pos), soa(vel)
+    thermo = torch.zeros(steps, N.THERMO_COLS, dtype=torch.float64, device="cuda")
+    heat = torch.zeros(steps, 3, dtype=torch.float64, device="cuda")
+    md.step(p, v, steps, 1.0, thermo, heat)
+    md.sync_status()
+    po, vo, th_o, J_o = orc.md_ext(orc.NepHyper(), f32_exact(z), pos, vel, box, inputs.MASS_SI, 1.0, steps,
+                                   t0=t0, tau=tau, fe=fe)
+    th = thermo.cpu().numpy()
+    J = heat.cpu().numpy()
+    assert np.abs(th[:, 0] - th_o[:, 0]).max() <= TOL_U * n
+    assert np.abs(th[:, 1] - th_o[:, 1]).max() <= 1e-6 * n
+    vmax = np.abs(vo).sum() * 1.5
+    assert np.abs(J - J_o).max() <= TOL_W * vmax, np.abs(J - J_o).max()
+    L = np.diag(box)
+    dx = aos(p) - po
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-6
+    assert np.abs(aos(v) - vo).max() < 1e-7
+    md.close()
+    model.close()
+    return th, J, aos(v)
+
+
+def test_md_berendsen_thermostat_matches_oracle(N, orc):
+    """Berendsen rescaling towards 900 K (tau = 20 fs), 40 steps from the
+    461-atom replica: thermo, J and the final state follow the oracle."""
+    _md_ext_compare(N, orc, 40, 900.0, 20.0, None)
+
+
+def test_md_hnemd_matches_oracle_and_keeps_momentum(N, orc):
+    """HNEMD driving F_e = (2e-3, -1e-3, 5e-4) /A with the thermostat on:
+    the state follows the oracle's integrator and the total momentum stays
+    zero (the mean driving force is removed)."""
+    th, J, v = _md_ext_compare(N, orc, 40, 300.0, 50.0, [2e-3, -1e-3, 5e-4])
+    # FP32 forces sum to zero only to rounding (|sum v| ~ 1e-9 A/fs here); an
+    # unremoved mean driving force would add ~1e-4 A/fs per step
+    assert np.abs(v.sum(axis=0)).max() < 1e-6
+
+
+def test_md_thermostat_and_drive_errors(N):
+    pos, box, z = inputs.config1()
+    model = N.NEP(np.asarray(z, np.float32))
+    md = N.MD(model, len(pos), box, inputs.MASS_SI)
+    with pytest.raises(N.NepError):
+        md.set_thermostat(-1.0, 10.0)
+    md.set_thermostat(300.0, 0.0)     # off
+    md.set_hnemd(None)                # off
+    md.set_hnemd([0.0, 0.0, 0.0])     # off
+    md.close()
+    model.close()
