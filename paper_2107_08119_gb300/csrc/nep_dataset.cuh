@@ -11,9 +11,9 @@
 
 namespace nep {
 
-// Jacobian record of one pair, stored at the slot of the OTHER atom (see
-// k_ds_site): the radial part of d q_j / d r_ji; the angular 24 x 3 block is
-// ang[aidx[slot]].
+// Jacobian record of one pair, stored at the owner's slot (slot p of atom i
+// pointing to j): the radial part of d q_i / d r_ij; the angular 24 x 3 block
+// is ang[aidx[p]].
 struct PairRec {
     float r[3];   // r_ij of the owning atom i (the vector from i to j)
     float gd[8];  // g_n'(|r|) / |r|, radial orders n = 0..7 (0 beyond r_c^R)
@@ -68,6 +68,8 @@ struct nep_dataset {
     double* U = nullptr;
     double* partials = nullptr;
     unsigned char* packed = nullptr;  // tensor-core operand records
+    float* pbuf = nullptr;            // [n_pairs][3][Pst] partial forces p_kji at the receiver's slot
+    float* w6 = nullptr;              // [N][6][Pst] virial contributions of each owner
     // force-loss adjoint scratch (grown on demand, nep_adjoint.cu)
     nep::AdjointScratch adj;
 };

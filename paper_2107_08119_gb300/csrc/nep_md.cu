@@ -10,8 +10,8 @@
 //   k_site         site energies and partial forces
 //   k_assemble     forces, second half kick, E_kin, virial and heat current
 //                  J = sum_i W_i . v_i (Eq. 7), per-block FP64 sums
-//   k_reduce       block sums in a fixed order
-//   k_md_finish    thermo row and J of this step; Berendsen factor
+//   k_md_finish    block sums in a fixed order, thermo row and J of this
+//                  step, Berendsen factor
 // Optional extensions (nep_md_set_thermostat, nep_md_set_hnemd):
 //   HNEMD          the assembly writes F and W_i; after the virial sum,
 //                  k_hnemd_kick adds F_i^ext = F_e . W_i - F_e . W / N
@@ -131,10 +131,28 @@ __global__ void k_scale_v(int n, double* __restrict__ vel, const double* __restr
     for (int c = 0; c < 3; ++c) vel[(size_t)c * n + i] *= lam;
 }
 
-__global__ void k_md_finish(double* __restrict__ red, double* __restrict__ thermo, double* __restrict__ heat,
-                            unsigned* __restrict__ ctl, double t0, double tau, double dt, double dof_kb)
+// The step's last kernel: warp 0 sums the site-energy block partials into
+// red[0], warp 1 + c sums component c of the other block partials into
+// red[off_x + c] (fixed order, like k_reduce), then thread 0 writes the thermo
+// row and J and the Berendsen factor.
+__global__ void k_md_finish(const double* __restrict__ part_e, int nb_e, const double* __restrict__ part_x, int nb_x,
+                            int ncomp_x, int off_x, double* __restrict__ red, double* __restrict__ thermo,
+                            double* __restrict__ heat, unsigned* __restrict__ ctl, double t0, double tau, double dt,
+                            double dof_kb)
 {
     // red: [0] E_pot, [1..9] W (row-major), [10] E_kin, [11..13] J, [14] lambda
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w <= ncomp_x) {
+        const double* src = w == 0 ? part_e : part_x + (w - 1);
+        const int nb = w == 0 ? nb_e : nb_x;
+        const int stride = w == 0 ? 1 : ncomp_x;
+        double v = 0.0;
+        for (int b = lane; b < nb; b += 32) v += src[(size_t)b * stride];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[w == 0 ? 0 : off_x + w - 1] = v;
+    }
+    __syncthreads();
     const unsigned s = ctl[kCtlStep];
     if (threadIdx.x == 0) {
         double ek = red[10];
@@ -393,15 +411,18 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
             return rc;
         m->prof.end(ps, st);
         pk = m->prof.begin(NEP_PROFILE_STEP, st);
-        if ((rc = launch_reduce(part_e, b1, 1, md->red, st))) return rc;
-        if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
+        const double dof_kb = (3.0 * n - 3.0) * kBoltzmannEv;
         if (drive) {
+            // the kick needs the total virial first
+            if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
             k_hnemd_kick<<<nbk, 256, 0, st>>>(n, md->ws.force, md->w_atom, vel, md->fe[0], md->fe[1], md->fe[2],
                                               md->red + 1, 1.0 / n, hdtm, kef, part_h, m->d_err);
-            if ((rc = launch_reduce(part_h, nbk, 4, md->red + 10, st))) return rc;
+            k_md_finish<<<1, 32 * 5, 0, st>>>(part_e, b1, part_h, nbk, 4, 10, md->red, thermo, heat, md->ctl, md->t0,
+                                              md->tau, dt, dof_kb);
+        } else {
+            k_md_finish<<<1, 32 * (1 + c2), 0, st>>>(part_e, b1, part_a, b2, c2, 1, md->red, thermo, heat, md->ctl,
+                                                     md->t0, md->tau, dt, dof_kb);
         }
-        k_md_finish<<<1, 32, 0, st>>>(md->red, thermo, heat, md->ctl, md->t0, md->tau, dt,
-                                      (3.0 * n - 3.0) * kBoltzmannEv);
         if (md->tau > 0.0 && n > 1) k_scale_v<<<nbk, 256, 0, st>>>(n, vel, md->red);
         m->prof.end(pk, st);
         if ((rc = cuda_fail(cudaGetLastError(), "md step kernels"))) return rc;

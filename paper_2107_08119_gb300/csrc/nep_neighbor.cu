@@ -163,13 +163,49 @@ __device__ void sort_near_first(int i, int n, int m_cap, int cnt, int* __restric
 // the lanes take them 32 at a time (a lane finds its cell by stepping from
 // the round's first cell); accepted pairs are compacted in candidate
 // order with a ballot into the warp's shared buffer, which is then sorted by
-// (squared distance, packed index) with a bitonic network and written out.
+// (squared distance, packed index) by ranking and written out.
 // Sorting on the pair of keys makes the order unique, hence deterministic.
 constexpr int kVerletWarps = 4;
 
 __device__ __forceinline__ bool pair_greater(float ka, int va, float kb, int vb)
 {
     return ka > kb || (ka == kb && va > vb);
+}
+
+// Sorts the warp's accepted entries by (squared distance, packed index) and
+// writes the first m of them: lane l ranks the entries c0 + l + 32 t against
+// all ns entries (broadcast shared-memory reads) and stores each at its rank,
+// slot-major in nbr and atom-major in key / vala.  The pairs are distinct, so
+// the ranks are a permutation.
+template <int EPL>
+__device__ __forceinline__ void rank_sort_write(int c0, int ns, int m, int lane, const float* skey, const int* sval,
+                                                int i, int n, int m_cap, int* __restrict__ nbr,
+                                                float* __restrict__ key, int* __restrict__ vala)
+{
+    float ke[EPL];
+    int ve[EPL], rk[EPL];
+#pragma unroll
+    for (int t = 0; t < EPL; ++t) {
+        const int e = c0 + lane + 32 * t;
+        ke[t] = e < ns ? skey[e] : 3.0e38f;
+        ve[t] = e < ns ? sval[e] : 0x7fffffff;
+        rk[t] = 0;
+    }
+    for (int f = 0; f < ns; ++f) {
+        const float kf = skey[f];
+        const int vf = sval[f];
+#pragma unroll
+        for (int t = 0; t < EPL; ++t) rk[t] += pair_greater(ke[t], ve[t], kf, vf) ? 1 : 0;
+    }
+#pragma unroll
+    for (int t = 0; t < EPL; ++t) {
+        const int e = c0 + lane + 32 * t;
+        if (e < ns && rk[t] < m) {
+            nbr[(size_t)rk[t] * n + i] = ve[t];
+            key[(size_t)i * m_cap + rk[t]] = ke[t];
+            vala[(size_t)i * m_cap + rk[t]] = ve[t];
+        }
+    }
 }
 
 __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m_cap, int lcap, float rv2,
@@ -268,36 +304,14 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
         if (lane == 0) count[i] = cnt;
         if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
         const int m = cnt < m_cap ? cnt : m_cap;
-        int S = 1;
-        while (S < (cnt < lcap ? cnt : lcap)) S <<= 1;
-        for (int t = (cnt < lcap ? cnt : lcap) + lane; t < S; t += 32) {
-            skey[t] = 3.0e38f;
-            sval[t] = 0x7fffffff;
-        }
-        __syncwarp();
-        for (int size = 2; size <= S; size <<= 1)
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int t = lane; t < S / 2; t += 32) {
-                    // stride is a power of two: lo = 2 stride (t / stride) + t % stride
-                    const int lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1)), hi2 = lo + stride;
-                    const bool asc = (lo & size) == 0;
-                    const float ka = skey[lo], kb = skey[hi2];
-                    const int va = sval[lo], vb = sval[hi2];
-                    if (pair_greater(ka, va, kb, vb) == asc) {
-                        skey[lo] = kb;
-                        sval[lo] = vb;
-                        skey[hi2] = ka;
-                        sval[hi2] = va;
-                    }
-                }
-                __syncwarp();
-            }
+        const int ns = cnt < lcap ? cnt : lcap;
         int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
-        for (int k = lane; k < m; k += 32) {
-            nbr[(size_t)k * n + i] = sval[k];
-            key[(size_t)i * m_cap + k] = skey[k];
-            vala[(size_t)i * m_cap + k] = sval[k];
-        }
+        if (ns <= 32)
+            rank_sort_write<1>(0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
+        else if (ns <= 64)
+            rank_sort_write<2>(0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
+        else
+            for (int c0 = 0; c0 < ns; c0 += 128) rank_sort_write<4>(c0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
         __syncwarp();  // the warp's buffers are reused by its next atom
     }
 }

@@ -5,22 +5,25 @@
 // periodic box.  nep_dataset_create precomputes everything that does not
 // depend on the parameters z (once):
 //   q_i             descriptors [N][32]
-//   J_ji            per pair, the derivatives of atom j's descriptor with
-//                   respect to r_ji (Eqs. 24-25), stored at the slot of atom
-//                   i that points to j: radial part as g_n'(r)/r times the
-//                   vector r_ji (8 floats + vector), angular part 24 x 3
+//   J_ij            per pair, the derivatives of atom i's descriptor with
+//                   respect to r_ij (Eqs. 24-25), stored at i's own slot for
+//                   j: radial part as g_n'(r)/r times the vector r_ij (8
+//                   floats + vector), angular part 24 x 3
 //   B_i             sum over i's own pairs of J_ij ([N][32][3])
 // Per population member k the loss then needs only
 //   U_ki, G_ki = dU/dq  (network, Eqs. 21-22)
-//   F_ki = G_ki . B_i - sum_j G_kj . J_ji                         (Eqs. 4-5, 23)
-//   W_ki = sum_j r_ij (x) (G_kj . J_ji)                            (Eq. 6)
+//   p_kji = G_kj . J_ji = dU_kj / dr_ji                           (Eq. 23)
+//   F_ki = G_ki . B_i - sum_j p_kji                                (Eqs. 4-5)
+//   W_k  = sum_i sum_j r_ij (x) p_kji                              (Eq. 6)
 // and the RMSEs of Eqs. 29-34.  Kernels per evaluation:
 //   k_pack      z_pop -> member-innermost weight layout
 //   k_mlp_f32   FP32 network per (atom pair, member): U [N][P] and
 //               G [N][32][Pst] (member innermost, Pst = P rounded up to 4)
 //   k_pop_tc    the same network as BF16 tensor-core GEMMs (nep_pop_tc.cu)
-//   k_contract  warp per atom, two members per lane: F, W, |F - F_tar|^2,
-//               summed per chunk of 32 atoms
+//   k_contract_owner  warp per atom j, two members per lane: p_kji for j's
+//               pairs from G_j held in registers, stored at the reverse slot
+//   k_contract  warp per atom i: F_i from its slots' p_kji, |F - F_tar|^2,
+//               U and W summed per chunk of 32 atoms
 //   k_loss      per member: per-structure sums in a fixed order, RMSEs
 // SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r), k_snes_update.
 #include <algorithm>
@@ -35,7 +38,8 @@ namespace {
 
 constexpr int kDsCap = 192;      // neighbour capacity per atom while building (within r_c)
 constexpr int kChunkAtoms = 32;       // atoms per contraction block (chunks never span structures)
-constexpr int kContractThreads = 128;  // 4 warps, one atom per warp at a time
+constexpr int kContractThreads = 128;  // owner pass: 4 warps per block, one atom per warp at a time
+constexpr int kReceiverThreads = 256;  // receiver pass: 8 warps per chunk of atoms
 constexpr int kMaxPop = 64;
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -148,7 +152,7 @@ __global__ void k_ds_reverse(int N, const long long* __restrict__ pstart, const 
 __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restrict__ boxes,
                           const float* __restrict__ xh, const float* __restrict__ xl,
                           const long long* __restrict__ pstart, const int* __restrict__ pj,
-                          const long long* __restrict__ rev, const long long* __restrict__ aidx, float rcR2,
+                          const long long* __restrict__ aidx, float rcR2,
                           float rcA2, float rcR, float rcA, float inv_rcR, float inv_rcA, float* __restrict__ q_out,
                           float* __restrict__ B_out, PairRec* __restrict__ rec, float* __restrict__ ang)
 {
@@ -226,8 +230,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
                 for (int c = 0; c < 3; ++c) B[a][c] = fmaf(pr.gd[a], r[c], B[a][c]);
             }
         }
-        const long long dst = rev[p];  // j's slot for i: where atom j's contraction reads it
-        rec[dst] = pr;
+        rec[p] = pr;  // owner order: the contraction's owner pass streams i's records
         if (d2 < rcA2) {
             float g[kNA], dg[kNA];
             radial_g_dg<kNA>(d, rcA, inv_rcA, g, dg);
@@ -247,7 +250,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
                         J[a * kLmax + l][c] = fmaf(two_s, fmaf(dg[a] * Y[m], u[c], g[a] * tg[c]), J[a * kLmax + l][c]);
                 }
             }
-            const long long ai = aidx[dst];
+            const long long ai = aidx[p];
             float* out = ang + (size_t)ai * (kNA * kLmax * 3);
             for (int t = 0; t < kNA * kLmax; ++t)
                 for (int c = 0; c < 3; ++c) {
@@ -342,27 +345,111 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
     }
 }
 
-// One block (4 warps) per chunk of <= kChunkAtoms atoms of one structure; each
-// warp takes every 4th atom of the chunk, one atom at a time, and lane l holds
-// members 2l and 2l + 1.  So every pair record and Jacobian block is one
-// broadcast load for the whole warp, and every G_j row is read as coalesced
-// float2s.  Per chunk and member: sums of U, of |F - F_tar|^2 and of the six
-// virial components, in a fixed order (atoms in order within a warp, then
-// the warps in order).
-__global__ void __launch_bounds__(kContractThreads, 6) k_contract(
+// Contraction, pass 1 (owner side): one warp per atom j, lane l holding
+// members 2l and 2l + 1.  The lane loads its members' G_j once (registers) and
+// walks j's own pair records in order; for each pair (j -> i) it forms
+// p_kji = G_kj . J_ji and stores it at the slot of the reverse pair (i -> j),
+// so that pass 2 finds the partial forces acting on i in i's own slot order.
+// The owner's virial contribution sum_i r_ij (x) p_kji (r_ij = -r_ji) goes to
+// W6[j][w][k].  No atomics: every value has one writer.
+__global__ void __launch_bounds__(kContractThreads) k_contract_owner(
+    int N, int P, int Pst, const float* __restrict__ G, const long long* __restrict__ pstart,
+    const long long* __restrict__ rev, const PairRec* __restrict__ rec, const long long* __restrict__ aidx,
+    const float* __restrict__ ang, float* __restrict__ pbuf, float* __restrict__ w6out)
+{
+    const int lane = threadIdx.x & 31;
+    const int k0 = 2 * lane;
+    const bool ld = k0 < Pst;  // Pst is even: the float2 at k0 is inside the row
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int j = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < N; j += warps) {
+        float2 g[kNdes];
+        const float* Gj = G + (size_t)j * kNdes * Pst + k0;
+#pragma unroll
+        for (int v = 0; v < kNdes; ++v)
+            g[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
+        float w6[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+        // the next pair's angular index and reverse slot are fetched one
+        // iteration ahead, so its Jacobian loads issue as the iteration starts
+        const long long pe = pstart[j + 1];
+        long long q = pstart[j];
+        long long nai = q < pe ? aidx[q] : -1, nrv = q < pe ? rev[q] : 0;
+        for (; q < pe; ++q) {
+            const long long ai = nai, rq = nrv;
+            if (q + 1 < pe) {
+                nai = aidx[q + 1];
+                nrv = rev[q + 1];
+            }
+            const PairRec pr = rec[q];  // d q_j / d r_ji, r = r_ji
+            float cr0 = 0.f, cr1 = 0.f;
+#pragma unroll
+            for (int v = 0; v < kNR; ++v) {
+                cr0 = fmaf(g[v].x, pr.gd[v], cr0);
+                cr1 = fmaf(g[v].y, pr.gd[v], cr1);
+            }
+            float pv[2][3] = {{cr0 * pr.r[0], cr0 * pr.r[1], cr0 * pr.r[2]},
+                              {cr1 * pr.r[0], cr1 * pr.r[1], cr1 * pr.r[2]}};
+            if (ai >= 0) {
+                const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)ai * (kNA * kLmax * 3));
+#pragma unroll
+                for (int u = 0; u < kNA * kLmax / 4; ++u) {  // 4 descriptors (12 floats) per step
+                    const float4 a0 = A4[3 * u], a1 = A4[3 * u + 1], a2 = A4[3 * u + 2];
+                    const float ja[4][3] = {{a0.x, a0.y, a0.z}, {a0.w, a1.x, a1.y}, {a1.z, a1.w, a2.x},
+                                            {a2.y, a2.z, a2.w}};
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const float2 gg = g[kNR + 4 * u + d];
+                        pv[0][0] = fmaf(gg.x, ja[d][0], pv[0][0]);
+                        pv[0][1] = fmaf(gg.x, ja[d][1], pv[0][1]);
+                        pv[0][2] = fmaf(gg.x, ja[d][2], pv[0][2]);
+                        pv[1][0] = fmaf(gg.y, ja[d][0], pv[1][0]);
+                        pv[1][1] = fmaf(gg.y, ja[d][1], pv[1][1]);
+                        pv[1][2] = fmaf(gg.y, ja[d][2], pv[1][2]);
+                    }
+                }
+            }
+            if (ld) {
+                float* o = pbuf + (size_t)rq * 3 * Pst + k0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    *reinterpret_cast<float2*>(o + (size_t)c * Pst) = make_float2(pv[0][c], pv[1][c]);
+            }
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                w6[m][0] = fmaf(-pr.r[0], pv[m][0], w6[m][0]);  // xx
+                w6[m][1] = fmaf(-pr.r[1], pv[m][1], w6[m][1]);  // yy
+                w6[m][2] = fmaf(-pr.r[2], pv[m][2], w6[m][2]);  // zz
+                w6[m][3] = fmaf(-pr.r[0], pv[m][1], w6[m][3]);  // xy
+                w6[m][4] = fmaf(-pr.r[1], pv[m][2], w6[m][4]);  // yz
+                w6[m][5] = fmaf(-pr.r[2], pv[m][0], w6[m][5]);  // zx
+            }
+        }
+        if (ld) {
+            float* o = w6out + (size_t)j * 6 * Pst + k0;
+#pragma unroll
+            for (int w = 0; w < 6; ++w) *reinterpret_cast<float2*>(o + (size_t)w * Pst) = make_float2(w6[0][w], w6[1][w]);
+        }
+    }
+}
+
+// Contraction, pass 2 (receiver side): one block (8 warps) per chunk of <=
+// kChunkAtoms atoms of one structure; each warp takes every 8th atom i, lane l
+// members 2l and 2l + 1: F_i = G_i . B_i - sum over i's slots of the stored
+// p_kji (coalesced float2 rows, in slot order).  Per chunk and member: sums of
+// U, of |F - F_tar|^2 and of the six virial components, in a fixed order
+// (atoms in order within a warp, then the warps in order).
+__global__ void __launch_bounds__(kReceiverThreads) k_contract(
     int N, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
     const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
-    const long long* __restrict__ pstart, const int* __restrict__ pj, const PairRec* __restrict__ rec,
-    const long long* __restrict__ aidx, const float* __restrict__ ang, const float* __restrict__ f_tar,
-    double* __restrict__ partials)
+    const long long* __restrict__ pstart, const float* __restrict__ pbuf, const float* __restrict__ w6in,
+    const float* __restrict__ f_tar, double* __restrict__ partials)
 {
-    constexpr int kWarps = kContractThreads / 32;
+    constexpr int kWarps = kReceiverThreads / 32;
     __shared__ double red[kWarps][kMaxPop][8];
     const int c = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = 2 * lane;
     const bool on0 = k0 < P, on1 = k0 + 1 < P;
-    const bool ld = k0 < Pst;  // Pst is even: the float2 at k0 is inside the row
+    const bool ld = k0 < Pst;
     // per-lane running sums live in shared memory (this lane's slots only)
 #pragma unroll
     for (int m = 0; m < 2; ++m)
@@ -372,7 +459,6 @@ __global__ void __launch_bounds__(kContractThreads, 6) k_contract(
     const int end = chunk_end[c];
     for (int i = chunk_begin[c] + warp; i < end; i += kWarps) {
         float F[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        float W6[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
         // own term G_i . B_i
         const float* Gi = G + (size_t)i * kNdes * Pst + k0;
         const float* Bi = B + (size_t)i * kNdes * 3;
@@ -388,61 +474,19 @@ __global__ void __launch_bounds__(kContractThreads, 6) k_contract(
             F[1][2] = fmaf(g.y, b2, F[1][2]);
         }
         const long long pe = pstart[i + 1];
+#pragma unroll 4
         for (long long p = pstart[i]; p < pe; ++p) {
-            const int j = pj[p] & 0xFFFFFF;
-            const long long ai = aidx[p];
-            const PairRec pr = rec[p];  // describes the pair (j -> i), r = r_ji
-            const float* Gj = G + (size_t)j * kNdes * Pst + k0;
-            float2 gr[kNR];
+            if (!ld) continue;
+            const float* o = pbuf + (size_t)p * 3 * Pst + k0;
 #pragma unroll
-            for (int v = 0; v < kNR; ++v)
-                gr[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
-            float cr0 = 0.f, cr1 = 0.f;
-#pragma unroll
-            for (int v = 0; v < kNR; ++v) {
-                cr0 = fmaf(gr[v].x, pr.gd[v], cr0);
-                cr1 = fmaf(gr[v].y, pr.gd[v], cr1);
-            }
-            float pv[2][3] = {{cr0 * pr.r[0], cr0 * pr.r[1], cr0 * pr.r[2]},
-                              {cr1 * pr.r[0], cr1 * pr.r[1], cr1 * pr.r[2]}};
-            if (ai >= 0) {
-                const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)ai * (kNA * kLmax * 3));
-#pragma unroll 3
-                for (int u = 0; u < kNA * kLmax / 4; ++u) {  // 4 descriptors (12 floats) per step
-                    const float4 a0 = A4[3 * u], a1 = A4[3 * u + 1], a2 = A4[3 * u + 2];
-                    const float ja[4][3] = {{a0.x, a0.y, a0.z}, {a0.w, a1.x, a1.y}, {a1.z, a1.w, a2.x},
-                                            {a2.y, a2.z, a2.w}};
-                    float2 g[4];
-#pragma unroll
-                    for (int d = 0; d < 4; ++d)
-                        g[d] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)(kNR + 4 * u + d) * Pst)
-                                  : make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        pv[0][0] = fmaf(g[d].x, ja[d][0], pv[0][0]);
-                        pv[0][1] = fmaf(g[d].x, ja[d][1], pv[0][1]);
-                        pv[0][2] = fmaf(g[d].x, ja[d][2], pv[0][2]);
-                        pv[1][0] = fmaf(g[d].y, ja[d][0], pv[1][0]);
-                        pv[1][1] = fmaf(g[d].y, ja[d][1], pv[1][1]);
-                        pv[1][2] = fmaf(g[d].y, ja[d][2], pv[1][2]);
-                    }
-                }
-            }
-            // pv = dU_j/dr_ji per member; W_i^{ab} += r_ij^a pv^b with r_ij = -r_ji
-#pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                F[m][0] -= pv[m][0];
-                F[m][1] -= pv[m][1];
-                F[m][2] -= pv[m][2];
-                W6[m][0] = fmaf(-pr.r[0], pv[m][0], W6[m][0]);  // xx
-                W6[m][1] = fmaf(-pr.r[1], pv[m][1], W6[m][1]);  // yy
-                W6[m][2] = fmaf(-pr.r[2], pv[m][2], W6[m][2]);  // zz
-                W6[m][3] = fmaf(-pr.r[0], pv[m][1], W6[m][3]);  // xy
-                W6[m][4] = fmaf(-pr.r[1], pv[m][2], W6[m][4]);  // yz
-                W6[m][5] = fmaf(-pr.r[2], pv[m][0], W6[m][5]);  // zx
+            for (int cc = 0; cc < 3; ++cc) {
+                const float2 x = *reinterpret_cast<const float2*>(o + (size_t)cc * Pst);
+                F[0][cc] -= x.x;
+                F[1][cc] -= x.y;
             }
         }
         const float tx = f_tar[(size_t)i * 3], ty = f_tar[(size_t)i * 3 + 1], tz = f_tar[(size_t)i * 3 + 2];
+        const float* wi = w6in + (size_t)i * 6 * Pst + k0;
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             if (!(m == 0 ? on0 : on1)) continue;
@@ -451,16 +495,16 @@ __global__ void __launch_bounds__(kContractThreads, 6) k_contract(
             r[0] += U[(size_t)i * P + k0 + m];
             r[1] += (double)dx * dx + (double)dy * dy + (double)dz * dz;
 #pragma unroll
-            for (int w = 0; w < 6; ++w) r[2 + w] += (double)W6[m][w];
+            for (int w = 0; w < 6; ++w) r[2 + w] += (double)wi[(size_t)w * Pst + m];
         }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
         const int k = e / 8, w = e % 8;
-        double s = 0.0;
+        double t = 0.0;
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += red[q][k][w];
-        partials[((size_t)c * P + k) * 8 + w] = s;
+        for (int q = 0; q < kWarps; ++q) t += red[q][k][w];
+        partials[((size_t)c * P + k) * 8 + w] = t;
     }
 }
 
@@ -670,6 +714,8 @@ int ensure_pop(nep_dataset* ds, int P)
     dfree(ds->U);
     dfree(ds->partials);
     dfree(ds->packed);
+    dfree(ds->pbuf);
+    dfree(ds->w6);
     ds->pop_cap = 0;
     const int nn = ds->m->hp.n_neu;
     int rc;
@@ -678,7 +724,9 @@ int ensure_pop(nep_dataset* ds, int P)
         (rc = dalloc(&ds->G, (size_t)ds->N * kNdes * member_stride(P), nullptr)) ||
         (rc = dalloc(&ds->U, (size_t)ds->N * P, nullptr)) ||
         (rc = dalloc(&ds->partials, (size_t)ds->n_chunks * P * 8, nullptr)) ||
-        (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)))
+        (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)) ||
+        (rc = dalloc(&ds->pbuf, (size_t)ds->n_pairs * 3 * member_stride(P), nullptr)) ||
+        (rc = dalloc(&ds->w6, (size_t)ds->N * 6 * member_stride(P), nullptr)))
         return rc;
     // members past P in the last group of G are never written: keep them zero
     rc = cuda_fail(cudaMemset(ds->G, 0, sizeof(float) * (size_t)ds->N * kNdes * member_stride(P)), "clear G");
@@ -707,9 +755,11 @@ int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int preci
         k_mlp_f32<<<blocks_for(pairs * P, 256), 256, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
                                                               ds->b2t, ds->G, ds->U);
     }
-    k_contract<<<ds->n_chunks, kContractThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
-                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->aidx, ds->ang,
-                                                          ds->f_tar, ds->partials);
+    k_contract_owner<<<std::min(blocks_for(ds->N, kContractThreads / 32), 152 * 16), kContractThreads, 0, st>>>(
+        ds->N, P, Pst, ds->G, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6);
+    k_contract<<<ds->n_chunks, kReceiverThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
+                                                          ds->B, ds->pstart, ds->pbuf, ds->w6, ds->f_tar,
+                                                          ds->partials);
     const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
                            lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
     k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_natoms, ds->partials, ds->e_tar, ds->w_tar,
@@ -859,7 +909,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     k_ds_compact<<<blocks_for(N, 128), 128>>>(N, tmp, ds->pstart, dastart, ds->sid, ds->boxes, xh, xl, rcA2, ds->pj,
                                               ds->aidx);
     k_ds_reverse<<<blocks_for(N, 128), 128>>>(N, ds->pstart, ds->pj, rev, m->d_err);
-    k_ds_site<<<blocks_for(N, 64), 64>>>(N, ds->sid, ds->boxes, xh, xl, ds->pstart, ds->pj, rev, ds->aidx, rcR2,
+    k_ds_site<<<blocks_for(N, 64), 64>>>(N, ds->sid, ds->boxes, xh, xl, ds->pstart, ds->pj, ds->aidx, rcR2,
                                          rcA2, (float)m->hp.rc_R, (float)m->hp.rc_A, (float)(1.0 / m->hp.rc_R),
                                          (float)(1.0 / m->hp.rc_A), ds->q, ds->B,
                                          ds->rec, ds->ang);
@@ -911,6 +961,8 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->U);
     dfree(ds->partials);
     dfree(ds->packed);
+    dfree(ds->pbuf);
+    dfree(ds->w6);
     free_adjoint(ds->adj);
     delete ds;
     return NEP_OK;
