@@ -349,7 +349,7 @@ int nep_profile_read(nep_model* m, double* ms, long long* launches);
  * reverse index, partial forces, cells, partial sums) lives in one
  * file-scope device array of fixed size inside the library.
  *
- * Limits (the array holds about 10.0 MB on every GPU that loads the library,
+ * Limits (the array holds about 11.6 MB on every GPU that loads the library,
  * until the process exits): n <= NEP_STATIC_MAX_ATOMS, hp->max_neighbors <=
  * NEP_STATIC_MAX_NEIGHBORS, and at most NEP_STATIC_MAX_CELLS cells of edge
  * max(rc_R, rc_A); larger inputs return NEP_ERR_ARG.  The call allocates

@@ -156,6 +156,7 @@ int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_par
         dev_free(nl.count);
         dev_free(nl.nbr);
         dev_free(nl.rev);
+        dev_free(nl.vala);
         dev_free(nl.pf);
         dev_free(nl.xh);
         dev_free(nl.xl);
@@ -167,6 +168,7 @@ int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_par
         const size_t N = (size_t)n, M = (size_t)m_cap;
         if ((rc = dev_alloc(&nl.count, N, "neighbour counts")) || (rc = dev_alloc(&nl.nbr, N * M, "neighbour list")) ||
             (rc = dev_alloc(&nl.rev, N * M, "reverse pair index")) ||
+            (rc = dev_alloc(&nl.vala, N * M, "neighbour list copy")) ||
             (rc = dev_alloc(&nl.pf, N * M * 4, "partial forces")) || (rc = dev_alloc(&nl.xh, N * 4, "positions")) ||
             (rc = dev_alloc(&nl.xl, N * 4, "positions")) || (rc = dev_alloc(&nl.atom_cell, N, "cell index")) ||
             (rc = dev_alloc(&nl.cell_atoms, N, "cell atoms")) || (rc = dev_alloc(&ws.force, N * 3, "forces")))
@@ -206,6 +208,7 @@ void free_workspace(Workspace& ws)
     dev_free(nl.count);
     dev_free(nl.nbr);
     dev_free(nl.rev);
+    dev_free(nl.vala);
     dev_free(nl.pf);
     dev_free(nl.xh);
     dev_free(nl.xl);

@@ -10,10 +10,10 @@
 //      (j, image) with |r_ij| below the list radius (full list, both
 //      directions), then orders its slots by increasing distance (the
 //      partial-force buffer is free at this point and holds the sort keys,
-//      atom-major: key[i * m_cap + k]);
+//      atom-major: key[i * m_cap + k]; the values are also kept atom-major
+//      in vala[i * m_cap + k] for the reverse search and the site pass);
 //   4. the reverse-pair index: for slot k of atom i, the slot of i in j's
-//      list, by binary search over j's contiguous keys (the list's values
-//      are also copied atom-major, behind the keys, for this search).
+//      list, by binary search over j's contiguous keys.
 // Boxes with fewer than 3 cells in a direction (small training cells) use a
 // brute-force scan over all atoms and images instead of cells.
 // Every kernel takes an optional device gate word: when it is zero the kernel
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
                                                                    const int* __restrict__ cell_start,
                                                                    const int* __restrict__ cell_atoms,
                                                                    int* __restrict__ count, int* __restrict__ nbr,
-                                                                   float* __restrict__ key, unsigned* err, Box b,
-                                                                   const unsigned* gate)
+                                                                   float* __restrict__ key, int* __restrict__ vala,
+                                                                   unsigned* err, Box b, const unsigned* gate)
 {
     if (gated_off(gate)) return;
     extern __shared__ float s_raw[];
@@ -305,7 +305,6 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
         if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
         const int m = cnt < m_cap ? cnt : m_cap;
         const int ns = cnt < lcap ? cnt : lcap;
-        int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
         if (ns <= 32)
             rank_sort_write<1>(0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
         else if (ns <= 64)
@@ -318,7 +317,8 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
 
 __global__ void k_verlet_brute(int n, int m_cap, float rv2, const float* __restrict__ xh,
                                const float* __restrict__ xl, int* __restrict__ count, int* __restrict__ nbr,
-                               float* __restrict__ key, unsigned* err, Box b, const unsigned* gate)
+                               float* __restrict__ key, int* __restrict__ vala, unsigned* err, Box b,
+                               const unsigned* gate)
 {
     if (gated_off(gate)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -344,7 +344,6 @@ __global__ void k_verlet_brute(int n, int m_cap, float rv2, const float* __restr
     if (cnt > m_cap) atomicOr(err, kErrOverflow);
     const int m = cnt < m_cap ? cnt : m_cap;
     sort_near_first(i, n, m_cap, m, nbr, key);
-    int* vala = reinterpret_cast<int*>(key + (size_t)m_cap * n);  // atom-major copy of the values
     for (int k = 0; k < m; ++k) vala[(size_t)i * m_cap + k] = nbr[(size_t)k * n + i];
 }
 
@@ -355,11 +354,10 @@ __global__ void k_verlet_brute(int n, int m_cap, float rv2, const float* __restr
 // keys and values are read from their atom-major copies, so every search
 // stays inside one atom's contiguous row.
 __global__ void k_reverse(int n, int m_cap, const int* __restrict__ count, const float* __restrict__ key,
-                          int* __restrict__ rev, unsigned* err, const unsigned* gate)
+                          const int* __restrict__ vala, int* __restrict__ rev, unsigned* err, const unsigned* gate)
 {
     if (gated_off(gate)) return;
     const int lane = threadIdx.x & 31;
-    const int* vala = reinterpret_cast<const int*>(key + (size_t)m_cap * n);
     const int warps = (int)((gridDim.x * blockDim.x) >> 5);
     for (int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += warps) {
         const int ci = min(count[i], m_cap);
@@ -422,13 +420,13 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool
         const size_t smem = (size_t)kVerletWarps * (2 * lcap + 96) * sizeof(float);
         k_verlet_cells<<<std::min(blocks_for(n, kVerletWarps), kListGridCap), 32 * kVerletWarps, smem, st>>>(
             n, nl.m_cap, lcap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
-            d_err, b, d_gate);
+            nl.vala, d_err, b, d_gate);
     } else {
         k_verlet_brute<<<blocks_for(n, 128), 128, 0, st>>>(n, nl.m_cap, rv2, nl.xh, nl.xl, nl.count, nl.nbr, nl.pf,
-                                                           d_err, b, d_gate);
+                                                           nl.vala, d_err, b, d_gate);
     }
-    k_reverse<<<std::min(blocks_for(n, 4), kListGridCap), 128, 0, st>>>(n, nl.m_cap, nl.count, nl.pf, nl.rev, d_err,
-                                                                         d_gate);
+    k_reverse<<<std::min(blocks_for(n, 4), kListGridCap), 128, 0, st>>>(n, nl.m_cap, nl.count, nl.pf, nl.vala, nl.rev,
+                                                                         d_err, d_gate);
     return cuda_fail(cudaGetLastError(), "neighbour-list kernels");
 }
 

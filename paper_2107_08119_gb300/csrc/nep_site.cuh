@@ -410,19 +410,51 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
     }
 }
 
-// Everything atom i contributes in the first force pass: site energy and the
-// partial forces dU_i/dr_ij of its first cnt slots (written through `out` for
-// slots within max(rc_R, rc_A); other slots are left untouched).
-__host__ __device__ __forceinline__ void site_partial_forces(int i, bool active, int n, int cnt,
-                                                             const SlotTable& nbr, const float* __restrict__ xh,
-                                                             const float* __restrict__ xl, const Box& box,
-                                                             const SiteParams& P, const PfOut& out, float& U_hi,
-                                                             float& U_lo)
+// Partial force dU_i/dr_ij of one pair r = r_ij (d2 = |r|^2 < max cutoff^2)
+// from the atom's coefficients A_nlm = 2 c_lm G_nl S_nlm and G_n (Eqs.
+// 23-25): radial G_n g_n' rhat, angular sum_nlm A_nlm grad(g_n Z_lm).
+template <class ArrA, class ArrR>
+__host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, float rz, float d2, const SiteParams& P,
+                                                            const ArrA& A, const ArrR& GR, float& px, float& py,
+                                                            float& pz)
+{
+    const float d = sqrtf(d2);
+    const float inv = 1.f / d;
+    const float ux = rx * inv, uy = ry * inv, uz = rz * inv;
+    float radial = 0.f;  // coefficient of rhat
+    float Vx = 0.f, Vy = 0.f, Vz = 0.f;
+    if (d2 < P.rcR2) {
+        float g[kNR], dg[kNR];
+        radial_g_dg<kNR>(d, P.rcR, P.inv_rcR, g, dg);
+#pragma unroll
+        for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], dg[a], radial);
+    }
+    if (d2 < P.rcA2) {
+        float g[kNA], dg[kNA];
+        radial_g_dg<kNA>(d, P.rcA, P.inv_rcA, g, dg);
+        sh_pass2(ux, uy, uz, A, g, dg, radial, Vx, Vy, Vz);
+        // tangential projection of V, divided by r
+        const float uv = fmaf(ux, Vx, fmaf(uy, Vy, uz * Vz));
+        Vx = (Vx - uv * ux) * inv;
+        Vy = (Vy - uv * uy) * inv;
+        Vz = (Vz - uv * uz) * inv;
+    }
+    px = fmaf(radial, ux, Vx);
+    py = fmaf(radial, uy, Vy);
+    pz = fmaf(radial, uz, Vz);
+}
+
+// Pass 1 and the network of atom i: site energy (hi + lo) and the
+// coefficients A (kNA x kLM, in place of the harmonic sums S) and GR.
+__host__ __device__ __forceinline__ void site_coefficients(int i, bool active, int n, int cnt, const SlotTable& nbr,
+                                                           const float* __restrict__ xh,
+                                                           const float* __restrict__ xl, const Box& box,
+                                                           const SiteParams& P, float (&S)[kNA][kLM],
+                                                           float (&GR)[kNR], float& U_hi, float& U_lo)
 {
     float hi[3], li[3];
     if (active) load_pos(xh, xl, n, i, hi, li);
     float q[kNdes];
-    float S[kNA][kLM];
     site_descriptors(i, n, cnt, nbr, xh, xl, box, P, hi, li, q, S);
 
     float G[kNdes];
@@ -436,9 +468,25 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
             S[a][m] *= 2.f * sh_c(m) * G[kNR + a * kLmax + sh_l(m)];
         }
     }
-    float GR[kNR];
 #pragma unroll
     for (int a = 0; a < kNR; ++a) GR[a] = G[a];
+}
+
+// Everything atom i contributes in the first force pass, in one thread: site
+// energy and the partial forces dU_i/dr_ij of its first cnt slots (written
+// through `out` for slots within max(rc_R, rc_A); other slots are left
+// untouched).
+__host__ __device__ __forceinline__ void site_partial_forces(int i, bool active, int n, int cnt,
+                                                             const SlotTable& nbr, const float* __restrict__ xh,
+                                                             const float* __restrict__ xl, const Box& box,
+                                                             const SiteParams& P, const PfOut& out, float& U_hi,
+                                                             float& U_lo)
+{
+    float S[kNA][kLM];
+    float GR[kNR];
+    site_coefficients(i, active, n, cnt, nbr, xh, xl, box, P, S, GR, U_hi, U_lo);
+    float hi[3], li[3];
+    if (active) load_pos(xh, xl, n, i, hi, li);
 
     const float rc2max = P.rcR2 > P.rcA2 ? P.rcR2 : P.rcA2;
     // pass 2: partial forces
@@ -452,31 +500,12 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
         pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, rx, ry, rz);
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         if (!(d2 < rc2max)) continue;
-        const float d = sqrtf(d2);
-        const float inv = 1.f / d;
-        const float ux = rx * inv, uy = ry * inv, uz = rz * inv;
-        float radial = 0.f;  // coefficient of rhat
-        float Vx = 0.f, Vy = 0.f, Vz = 0.f;
-        if (d2 < P.rcR2) {
-            float g[kNR], dg[kNR];
-            radial_g_dg<kNR>(d, P.rcR, P.inv_rcR, g, dg);
-#pragma unroll
-            for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], dg[a], radial);
-        }
-        if (d2 < P.rcA2) {
-            float g[kNA], dg[kNA];
-            radial_g_dg<kNA>(d, P.rcA, P.inv_rcA, g, dg);
-            sh_pass2(ux, uy, uz, S, g, dg, radial, Vx, Vy, Vz);
-            // tangential projection of V, divided by r
-            const float uv = fmaf(ux, Vx, fmaf(uy, Vy, uz * Vz));
-            Vx = (Vx - uv * ux) * inv;
-            Vy = (Vy - uv * uy) * inv;
-            Vz = (Vz - uv * uz) * inv;
-        }
+        float px, py, pz;
+        pair_partial_force(rx, ry, rz, d2, P, S, GR, px, py, pz);
         float* p = out.base + (size_t)k * out.slot_stride;
-        p[0] = fmaf(radial, ux, Vx);
-        p[out.comp_stride] = fmaf(radial, uy, Vy);
-        p[2 * out.comp_stride] = fmaf(radial, uz, Vz);
+        p[0] = px;
+        p[out.comp_stride] = py;
+        p[2 * out.comp_stride] = pz;
     }
 }
 

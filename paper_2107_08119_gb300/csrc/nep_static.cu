@@ -11,7 +11,7 @@
 // inputs and outputs, all in memory it already owns.
 //
 // Limits: at most NEP_STATIC_MAX_ATOMS atoms, NEP_STATIC_MAX_NEIGHBORS slots
-// per atom and NEP_STATIC_MAX_CELLS cells (about 10.0 MB, resident on every
+// per atom and NEP_STATIC_MAX_CELLS cells (about 11.6 MB, resident on every
 // GPU that loads the library until the process exits).  Every call shares
 // the array, which keeps the previous call's contents; calls that overlap on
 // the GPU (different streams, or host threads without ordering) race on it.
@@ -33,7 +33,8 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kOffCount = 0;
 constexpr size_t kOffNbr = kOffCount + align256(sizeof(int) * kStaticAtoms);
 constexpr size_t kOffRev = kOffNbr + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
-constexpr size_t kOffPf = kOffRev + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
+constexpr size_t kOffVala = kOffRev + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
+constexpr size_t kOffPf = kOffVala + align256(sizeof(int) * kStaticAtoms * kStaticSlots);
 constexpr size_t kOffXh = kOffPf + align256(sizeof(float) * kStaticAtoms * kStaticSlots * 4);
 constexpr size_t kOffXl = kOffXh + align256(sizeof(float) * kStaticAtoms * 4);
 constexpr size_t kOffAtomCell = kOffXl + align256(sizeof(float) * kStaticAtoms * 4);
@@ -137,6 +138,7 @@ extern "C" int nep_compute_efv_static(const nep_hyper* hp, const float* z, int n
     nl.nbr = reinterpret_cast<int*>(base + kOffNbr);
     nl.rev = reinterpret_cast<int*>(base + kOffRev);
     nl.pf = reinterpret_cast<float*>(base + kOffPf);
+    nl.vala = reinterpret_cast<int*>(base + kOffVala);
     nl.xh = reinterpret_cast<float*>(base + kOffXh);
     nl.xl = reinterpret_cast<float*>(base + kOffXl);
     nl.atom_cell = reinterpret_cast<int*>(base + kOffAtomCell);

@@ -346,18 +346,28 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
 }
 
 // Contraction, pass 1 (owner side): one warp per atom j, lane l holding
-// members 2l and 2l + 1.  The lane loads its members' G_j once (registers) and
-// walks j's own pair records in order; for each pair (j -> i) it forms
-// p_kji = G_kj . J_ji and stores it at the slot of the reverse pair (i -> j),
-// so that pass 2 finds the partial forces acting on i in i's own slot order.
-// The owner's virial contribution sum_i r_ij (x) p_kji (r_ij = -r_ji) goes to
-// W6[j][w][k].  No atomics: every value has one writer.
+// members 2l and 2l + 1.  The lane loads its members' G_j once (registers).
+// j's Jacobian records are contiguous (owner order), so the warp stages them
+// into shared memory 32 pairs at a time with coalesced 16-byte loads, all in
+// flight together, and then forms p_kji = G_kj . J_ji pair by pair from
+// shared memory (broadcast reads), storing it at the slot of the reverse pair
+// (i -> j) so that pass 2 finds the partial forces acting on i in i's own
+// slot order.  The owner's virial contribution sum_i r_ij (x) p_kji
+// (r_ij = -r_ji) goes to W6[j][w][k].  No atomics: every value has one writer.
+constexpr int kOwnerChunk = 32;                                     // pairs staged per round
+constexpr int kRecFloats = (int)(sizeof(PairRec) / sizeof(float));  // 12
+constexpr int kAngFloats = kNA * kLmax * 3;                         // 72
+constexpr int kOwnerStage = kOwnerChunk * (kRecFloats + kAngFloats);  // floats per warp
+
 __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
     int N, int P, int Pst, const float* __restrict__ G, const long long* __restrict__ pstart,
     const long long* __restrict__ rev, const PairRec* __restrict__ rec, const long long* __restrict__ aidx,
     const float* __restrict__ ang, float* __restrict__ pbuf, float* __restrict__ w6out)
 {
-    const int lane = threadIdx.x & 31;
+    extern __shared__ float4 s_stage4[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* s_rec = reinterpret_cast<float*>(s_stage4) + (size_t)warp * kOwnerStage;
+    float* s_ang = s_rec + kOwnerChunk * kRecFloats;
     const int k0 = 2 * lane;
     const bool ld = k0 < Pst;  // Pst is even: the float2 at k0 is inside the row
     const int warps = (int)((gridDim.x * blockDim.x) >> 5);
@@ -368,60 +378,67 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
         for (int v = 0; v < kNdes; ++v)
             g[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
         float w6[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
-        // the next pair's angular index and reverse slot are fetched one
-        // iteration ahead, so its Jacobian loads issue as the iteration starts
         const long long pe = pstart[j + 1];
-        long long q = pstart[j];
-        long long nai = q < pe ? aidx[q] : -1, nrv = q < pe ? rev[q] : 0;
-        for (; q < pe; ++q) {
-            const long long ai = nai, rq = nrv;
-            if (q + 1 < pe) {
-                nai = aidx[q + 1];
-                nrv = rev[q + 1];
-            }
-            const PairRec pr = rec[q];  // d q_j / d r_ji, r = r_ji
-            float cr0 = 0.f, cr1 = 0.f;
+        for (long long q0 = pstart[j]; q0 < pe; q0 += kOwnerChunk) {
+            const int nq = (int)min((long long)kOwnerChunk, pe - q0);
+            // this chunk's angular records are the consecutive ones starting at
+            // the first angular pair's index (owner order assigns them in turn)
+            const long long my_ai = lane < nq ? aidx[q0 + lane] : -1;
+            const long long my_rv = lane < nq ? rev[q0 + lane] : 0;
+            const unsigned angmask = __ballot_sync(0xffffffffu, my_ai >= 0);
+            const int na = __popc(angmask);
+            const long long a0 = na ? __shfl_sync(0xffffffffu, my_ai, __ffs(angmask) - 1) : 0;
+            // stage pair records and angular blocks (16-byte pieces, all lanes)
+            const float4* rsrc = reinterpret_cast<const float4*>(rec + q0);
+            for (int t = lane; t < nq * kRecFloats / 4; t += 32)
+                reinterpret_cast<float4*>(s_rec)[t] = rsrc[t];
+            const float4* asrc = reinterpret_cast<const float4*>(ang + (size_t)a0 * kAngFloats);
+            for (int t = lane; t < na * kAngFloats / 4; t += 32)
+                reinterpret_cast<float4*>(s_ang)[t] = asrc[t];
+            __syncwarp();
+            for (int t = 0; t < nq; ++t) {
+                const float* pr = s_rec + t * kRecFloats;  // r_ji [0..2], g_n'/r [3..10]
+                const long long ai = __shfl_sync(0xffffffffu, my_ai, t);
+                const long long rq = __shfl_sync(0xffffffffu, my_rv, t);
+                float cr0 = 0.f, cr1 = 0.f;
 #pragma unroll
-            for (int v = 0; v < kNR; ++v) {
-                cr0 = fmaf(g[v].x, pr.gd[v], cr0);
-                cr1 = fmaf(g[v].y, pr.gd[v], cr1);
-            }
-            float pv[2][3] = {{cr0 * pr.r[0], cr0 * pr.r[1], cr0 * pr.r[2]},
-                              {cr1 * pr.r[0], cr1 * pr.r[1], cr1 * pr.r[2]}};
-            if (ai >= 0) {
-                const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)ai * (kNA * kLmax * 3));
+                for (int v = 0; v < kNR; ++v) {
+                    cr0 = fmaf(g[v].x, pr[3 + v], cr0);
+                    cr1 = fmaf(g[v].y, pr[3 + v], cr1);
+                }
+                const float r0 = pr[0], r1 = pr[1], r2 = pr[2];
+                float pv[2][3] = {{cr0 * r0, cr0 * r1, cr0 * r2}, {cr1 * r0, cr1 * r1, cr1 * r2}};
+                if (ai >= 0) {
+                    const float* A = s_ang + (size_t)(ai - a0) * kAngFloats;
 #pragma unroll
-                for (int u = 0; u < kNA * kLmax / 4; ++u) {  // 4 descriptors (12 floats) per step
-                    const float4 a0 = A4[3 * u], a1 = A4[3 * u + 1], a2 = A4[3 * u + 2];
-                    const float ja[4][3] = {{a0.x, a0.y, a0.z}, {a0.w, a1.x, a1.y}, {a1.z, a1.w, a2.x},
-                                            {a2.y, a2.z, a2.w}};
-#pragma unroll
-                    for (int d = 0; d < 4; ++d) {
-                        const float2 gg = g[kNR + 4 * u + d];
-                        pv[0][0] = fmaf(gg.x, ja[d][0], pv[0][0]);
-                        pv[0][1] = fmaf(gg.x, ja[d][1], pv[0][1]);
-                        pv[0][2] = fmaf(gg.x, ja[d][2], pv[0][2]);
-                        pv[1][0] = fmaf(gg.y, ja[d][0], pv[1][0]);
-                        pv[1][1] = fmaf(gg.y, ja[d][1], pv[1][1]);
-                        pv[1][2] = fmaf(gg.y, ja[d][2], pv[1][2]);
+                    for (int d = 0; d < kNA * kLmax; ++d) {
+                        const float2 gg = g[kNR + d];
+                        const float ja0 = A[3 * d], ja1 = A[3 * d + 1], ja2 = A[3 * d + 2];
+                        pv[0][0] = fmaf(gg.x, ja0, pv[0][0]);
+                        pv[0][1] = fmaf(gg.x, ja1, pv[0][1]);
+                        pv[0][2] = fmaf(gg.x, ja2, pv[0][2]);
+                        pv[1][0] = fmaf(gg.y, ja0, pv[1][0]);
+                        pv[1][1] = fmaf(gg.y, ja1, pv[1][1]);
+                        pv[1][2] = fmaf(gg.y, ja2, pv[1][2]);
                     }
                 }
-            }
-            if (ld) {
-                float* o = pbuf + (size_t)rq * 3 * Pst + k0;
+                if (ld) {
+                    float* o = pbuf + (size_t)rq * 3 * Pst + k0;
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    *reinterpret_cast<float2*>(o + (size_t)c * Pst) = make_float2(pv[0][c], pv[1][c]);
-            }
+                    for (int c = 0; c < 3; ++c)
+                        *reinterpret_cast<float2*>(o + (size_t)c * Pst) = make_float2(pv[0][c], pv[1][c]);
+                }
 #pragma unroll
-            for (int m = 0; m < 2; ++m) {
-                w6[m][0] = fmaf(-pr.r[0], pv[m][0], w6[m][0]);  // xx
-                w6[m][1] = fmaf(-pr.r[1], pv[m][1], w6[m][1]);  // yy
-                w6[m][2] = fmaf(-pr.r[2], pv[m][2], w6[m][2]);  // zz
-                w6[m][3] = fmaf(-pr.r[0], pv[m][1], w6[m][3]);  // xy
-                w6[m][4] = fmaf(-pr.r[1], pv[m][2], w6[m][4]);  // yz
-                w6[m][5] = fmaf(-pr.r[2], pv[m][0], w6[m][5]);  // zx
+                for (int m = 0; m < 2; ++m) {
+                    w6[m][0] = fmaf(-r0, pv[m][0], w6[m][0]);  // xx
+                    w6[m][1] = fmaf(-r1, pv[m][1], w6[m][1]);  // yy
+                    w6[m][2] = fmaf(-r2, pv[m][2], w6[m][2]);  // zz
+                    w6[m][3] = fmaf(-r0, pv[m][1], w6[m][3]);  // xy
+                    w6[m][4] = fmaf(-r1, pv[m][2], w6[m][4]);  // yz
+                    w6[m][5] = fmaf(-r2, pv[m][0], w6[m][5]);  // zx
+                }
             }
+            __syncwarp();  // the stage is refilled by the next chunk
         }
         if (ld) {
             float* o = w6out + (size_t)j * 6 * Pst + k0;
@@ -474,7 +491,7 @@ __global__ void __launch_bounds__(kReceiverThreads) k_contract(
             F[1][2] = fmaf(g.y, b2, F[1][2]);
         }
         const long long pe = pstart[i + 1];
-#pragma unroll 4
+#pragma unroll 8
         for (long long p = pstart[i]; p < pe; ++p) {
             if (!ld) continue;
             const float* o = pbuf + (size_t)p * 3 * Pst + k0;
@@ -755,7 +772,12 @@ int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int preci
         k_mlp_f32<<<blocks_for(pairs * P, 256), 256, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
                                                               ds->b2t, ds->G, ds->U);
     }
-    k_contract_owner<<<std::min(blocks_for(ds->N, kContractThreads / 32), 152 * 16), kContractThreads, 0, st>>>(
+    const size_t ostage = (size_t)(kContractThreads / 32) * kOwnerStage * sizeof(float);
+    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)ostage),
+                        "contraction shared memory")))
+        return rc;
+    k_contract_owner<<<std::min(blocks_for(ds->N, kContractThreads / 32), 152 * 16), kContractThreads, ostage, st>>>(
         ds->N, P, Pst, ds->G, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6);
     k_contract<<<ds->n_chunks, kReceiverThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
                                                           ds->B, ds->pstart, ds->pbuf, ds->w6, ds->f_tar,
