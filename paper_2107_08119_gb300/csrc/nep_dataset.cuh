@@ -70,6 +70,7 @@ struct nep_dataset {
     unsigned char* packed = nullptr;  // tensor-core operand records
     float* pbuf = nullptr;            // [n_pairs][3][Pst] partial forces p_kji at the receiver's slot
     float* w6 = nullptr;              // [N][6][Pst] virial contributions of each owner
+    float* fown = nullptr;            // [N][3][Pst] own force terms G_i . B_i
     // force-loss adjoint scratch (grown on demand, nep_adjoint.cu)
     nep::AdjointScratch adj;
 };

@@ -360,9 +360,10 @@ constexpr int kAngFloats = kNA * kLmax * 3;                         // 72
 constexpr int kOwnerStage = kOwnerChunk * (kRecFloats + kAngFloats);  // floats per warp
 
 __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
-    int N, int P, int Pst, const float* __restrict__ G, const long long* __restrict__ pstart,
-    const long long* __restrict__ rev, const PairRec* __restrict__ rec, const long long* __restrict__ aidx,
-    const float* __restrict__ ang, float* __restrict__ pbuf, float* __restrict__ w6out)
+    int N, int P, int Pst, const float* __restrict__ G, const float* __restrict__ B,
+    const long long* __restrict__ pstart, const long long* __restrict__ rev, const PairRec* __restrict__ rec,
+    const long long* __restrict__ aidx, const float* __restrict__ ang, float* __restrict__ pbuf,
+    float* __restrict__ w6out, float* __restrict__ fown)
 {
     extern __shared__ float4 s_stage4[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -377,6 +378,29 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
 #pragma unroll
         for (int v = 0; v < kNdes; ++v)
             g[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
+        // own term G_j . B_j (B_j = sum of j's own Jacobians), for pass 2
+        {
+            const float4* B4 = reinterpret_cast<const float4*>(B + (size_t)j * kNdes * 3);
+            float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+            for (int u = 0; u < kNdes * 3 / 12; ++u) {  // 4 descriptors (12 floats) per step
+                const float4 b0 = B4[3 * u], b1 = B4[3 * u + 1], b2 = B4[3 * u + 2];
+                const float bb[4][3] = {{b0.x, b0.y, b0.z}, {b0.w, b1.x, b1.y}, {b1.z, b1.w, b2.x},
+                                        {b2.y, b2.z, b2.w}};
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        f[0][c] = fmaf(g[4 * u + d].x, bb[d][c], f[0][c]);
+                        f[1][c] = fmaf(g[4 * u + d].y, bb[d][c], f[1][c]);
+                    }
+            }
+            if (ld) {
+                float* o = fown + (size_t)j * 3 * Pst + k0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * Pst) = make_float2(f[0][c], f[1][c]);
+            }
+        }
         float w6[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
         const long long pe = pstart[j + 1];
         for (long long q0 = pstart[j]; q0 < pe; q0 += kOwnerChunk) {
@@ -450,15 +474,15 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
 
 // Contraction, pass 2 (receiver side): one block (8 warps) per chunk of <=
 // kChunkAtoms atoms of one structure; each warp takes every 8th atom i, lane l
-// members 2l and 2l + 1: F_i = G_i . B_i - sum over i's slots of the stored
-// p_kji (coalesced float2 rows, in slot order).  Per chunk and member: sums of
+// members 2l and 2l + 1: F_i = G_i . B_i (from pass 1) - sum over i's slots of
+// the stored p_kji (coalesced float2 rows, in slot order).  Per chunk and member: sums of
 // U, of |F - F_tar|^2 and of the six virial components, in a fixed order
 // (atoms in order within a warp, then the warps in order).
-__global__ void __launch_bounds__(kReceiverThreads) k_contract(
+__global__ void __launch_bounds__(kReceiverThreads, 3) k_contract(
     int N, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
-    const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
-    const long long* __restrict__ pstart, const float* __restrict__ pbuf, const float* __restrict__ w6in,
-    const float* __restrict__ f_tar, double* __restrict__ partials)
+    const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
+    const float* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
+    double* __restrict__ partials)
 {
     constexpr int kWarps = kReceiverThreads / 32;
     __shared__ double red[kWarps][kMaxPop][8];
@@ -476,22 +500,17 @@ __global__ void __launch_bounds__(kReceiverThreads) k_contract(
     const int end = chunk_end[c];
     for (int i = chunk_begin[c] + warp; i < end; i += kWarps) {
         float F[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        // own term G_i . B_i
-        const float* Gi = G + (size_t)i * kNdes * Pst + k0;
-        const float* Bi = B + (size_t)i * kNdes * 3;
-#pragma unroll 8
-        for (int v = 0; v < kNdes; ++v) {
-            const float2 g = ld ? *reinterpret_cast<const float2*>(Gi + (size_t)v * Pst) : make_float2(0.f, 0.f);
-            const float b0 = Bi[v * 3], b1 = Bi[v * 3 + 1], b2 = Bi[v * 3 + 2];
-            F[0][0] = fmaf(g.x, b0, F[0][0]);
-            F[0][1] = fmaf(g.x, b1, F[0][1]);
-            F[0][2] = fmaf(g.x, b2, F[0][2]);
-            F[1][0] = fmaf(g.y, b0, F[1][0]);
-            F[1][1] = fmaf(g.y, b1, F[1][1]);
-            F[1][2] = fmaf(g.y, b2, F[1][2]);
+        if (ld) {  // own term G_i . B_i from pass 1
+            const float* o = fown + (size_t)i * 3 * Pst + k0;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const float2 x = *reinterpret_cast<const float2*>(o + (size_t)cc * Pst);
+                F[0][cc] = x.x;
+                F[1][cc] = x.y;
+            }
         }
         const long long pe = pstart[i + 1];
-#pragma unroll 8
+#pragma unroll 4
         for (long long p = pstart[i]; p < pe; ++p) {
             if (!ld) continue;
             const float* o = pbuf + (size_t)p * 3 * Pst + k0;
@@ -733,6 +752,7 @@ int ensure_pop(nep_dataset* ds, int P)
     dfree(ds->packed);
     dfree(ds->pbuf);
     dfree(ds->w6);
+    dfree(ds->fown);
     ds->pop_cap = 0;
     const int nn = ds->m->hp.n_neu;
     int rc;
@@ -743,7 +763,8 @@ int ensure_pop(nep_dataset* ds, int P)
         (rc = dalloc(&ds->partials, (size_t)ds->n_chunks * P * 8, nullptr)) ||
         (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)) ||
         (rc = dalloc(&ds->pbuf, (size_t)ds->n_pairs * 3 * member_stride(P), nullptr)) ||
-        (rc = dalloc(&ds->w6, (size_t)ds->N * 6 * member_stride(P), nullptr)))
+        (rc = dalloc(&ds->w6, (size_t)ds->N * 6 * member_stride(P), nullptr)) ||
+        (rc = dalloc(&ds->fown, (size_t)ds->N * 3 * member_stride(P), nullptr)))
         return rc;
     // members past P in the last group of G are never written: keep them zero
     rc = cuda_fail(cudaMemset(ds->G, 0, sizeof(float) * (size_t)ds->N * kNdes * member_stride(P)), "clear G");
@@ -778,9 +799,9 @@ int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int preci
                         "contraction shared memory")))
         return rc;
     k_contract_owner<<<std::min(blocks_for(ds->N, kContractThreads / 32), 152 * 16), kContractThreads, ostage, st>>>(
-        ds->N, P, Pst, ds->G, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6);
-    k_contract<<<ds->n_chunks, kReceiverThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->G, ds->U,
-                                                          ds->B, ds->pstart, ds->pbuf, ds->w6, ds->f_tar,
+        ds->N, P, Pst, ds->G, ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6, ds->fown);
+    k_contract<<<ds->n_chunks, kReceiverThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->U,
+                                                          ds->pstart, ds->fown, ds->pbuf, ds->w6, ds->f_tar,
                                                           ds->partials);
     const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
                            lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
@@ -985,6 +1006,7 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->packed);
     dfree(ds->pbuf);
     dfree(ds->w6);
+    dfree(ds->fown);
     free_adjoint(ds->adj);
     delete ds;
     return NEP_OK;
