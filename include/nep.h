@@ -234,6 +234,38 @@ int nep_dataset_info(const nep_dataset* ds, int* n_atoms, long long* n_pairs, lo
 /* Copy the precomputed descriptors, dev [N][N_des] FP32. */
 int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
 
+/*
+ * Launch shape of the population evaluation of a dataset, host int[5]:
+ *   [0] waves       1..16: the force contraction runs over up to this many
+ *                   consecutive ranges of whole structures with about equal
+ *                   pair counts; the second pass of one range runs on a second
+ *                   stream beside the first pass of the next, reading the
+ *                   range's partial forces back from L2.
+ *   [1] owner warps 4 or 8 warps per block of the first contraction pass.
+ *   [2] discard     0 or 1: the second pass drops from L2 the partial-force
+ *                   lines it has consumed (no write-back of dead data).
+ *   [3] threads     128 or 256 threads per block of the FP32 network.
+ *   [4] unroll      4 or 8 partial-force slots in flight per warp in the
+ *                   second contraction pass.
+ * No shape changes a result bit (every value keeps its writer and its order of
+ * summation).  Default {1, 4, 0, 256, 4}.  Errors: NEP_ERR_ARG (NULL, out of range).
+ */
+int nep_dataset_set_shape(nep_dataset* ds, const int* shape);
+int nep_dataset_get_shape(const nep_dataset* ds, int* shape);
+/*
+ * nep_dataset_tune -- autotuner: times every candidate shape (waves 1, 2, 4
+ * x owner warps 4, 8 x discard 0, 1 when waves > 1 x network threads 128, 256
+ * in FP32 mode x unroll 4, 8) on `reps` evaluations of an n_pop-member population of fixed
+ * stand-in parameters, with CUDA events on `stream` after one warm-up
+ * evaluation each, and keeps the fastest on the dataset.  Synchronises the
+ * stream.  shape_out: host int[5] or NULL; ms_out: host, the best shape's
+ * time per evaluation, or NULL.
+ * Errors: NEP_ERR_ARG (NULL, dataset of another model, n_pop outside 1..64,
+ * reps < 1, unknown precision), NEP_ERR_OOM, NEP_ERR_CUDA.
+ */
+int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, int reps, int* shape_out,
+                     float* ms_out, void* stream);
+
 #define NEP_PREC_FP32 0 /* network of every member in FP32 (CUDA cores) */
 #define NEP_PREC_BF16 1 /* population GEMMs in BF16 with FP32 accumulation (tensor cores) */
 #define NEP_LOSS_COLS 6 /* L, L_e, L_f, L_v, L_1, L_2 */
@@ -302,6 +334,21 @@ int snes_destroy(snes_state* st);
  */
 int snes_step(snes_state* st, nep_dataset* ds, int precision, const double* lambdas, const float* r_in,
               double* loss_out, void* stream);
+/*
+ * snes_run -- n_gen generations of snes_step (drawn r only), replayed from a
+ * CUDA graph of one generation that is captured on the first call and kept
+ * while the dataset, its launch shape, the precision and the lambdas stay the
+ * same.  The generation counter of the draws lives on the device, so every
+ * replay draws the next generation's numbers: the result is bit-identical to
+ * n_gen calls of snes_step with r_in = NULL.
+ *   n_gen      >= 0 generations.
+ *   loss_hist  dev [n_gen][n_pop][NEP_LOSS_COLS] FP64 (row g: the losses of
+ *              generation g of this run, unranked), or NULL.
+ * Errors: NEP_ERR_ARG (NULL, dataset of another model, n_gen < 0, unknown
+ * precision), NEP_ERR_OOM, NEP_ERR_CUDA (capture, instantiation or launch).
+ */
+int snes_run(snes_state* st, nep_dataset* ds, int precision, const double* lambdas, int n_gen, double* loss_hist,
+             void* stream);
 /* Copy m, s (dev [n_par]), the last draws r (dev [n_pop][n_par]) and the
  * member index at each rank (dev int [n_pop]); NULL pointers are skipped. */
 int snes_get_state(snes_state* st, float* mean, float* sigma, float* r_last, int* order, void* stream);

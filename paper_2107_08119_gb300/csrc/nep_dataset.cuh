@@ -7,6 +7,8 @@
 // pj[p] = j | image_code << 24, rev[p] = the slot of the pair (j -> i).
 #pragma once
 
+#include <vector>
+
 #include "nep_site.cuh"
 
 namespace nep {
@@ -29,6 +31,18 @@ struct AdjointScratch {
     double* part = nullptr;    // [n_blocks][n_par] per-block FP64 partial sums
     double* sums = nullptr;    // [2]: sum |F - F_tar|^2, L_f
     bool ready = false;        // a forward has run since the scratch was made
+};
+
+// Launch shapes of the population evaluation.  None of them changes a result
+// bit: every value keeps its single writer and its summation order.
+constexpr int kMaxWaves = 16;
+struct EvalShape {
+    int waves = 1;          // the contraction runs over up to this many consecutive ranges of
+                            // whole structures; pass 2 of range w overlaps pass 1 of range w + 1
+    int owner_warps = 4;    // warps per block of the owner pass (4 or 8)
+    int discard = 0;        // pass 2 drops the partial-force lines it has read from L2
+    int mlp_threads = 256;  // threads per block of the FP32 network (128 or 256)
+    int recv_unroll = 4;    // slots in flight per warp in the receiver pass (4 or 8)
 };
 
 }  // namespace nep
@@ -73,6 +87,16 @@ struct nep_dataset {
     float* fown = nullptr;            // [N][3][Pst] own force terms G_i . B_i
     // force-loss adjoint scratch (grown on demand, nep_adjoint.cu)
     nep::AdjointScratch adj;
+    // launch shape of the evaluation (nep_dataset_set_shape / nep_dataset_tune)
+    nep::EvalShape shape;
+    unsigned long long uid = 0;  // unique per dataset: keys captured generation graphs
+    int epoch = 0;               // bumped whenever the evaluation scratch is reallocated
+    std::vector<int> h_cb, h_ce;         // host copies of the chunk atom ranges
+    std::vector<long long> h_cpairs;     // pairs before each chunk (n_chunks + 1)
+    std::vector<int> h_schunk0;          // first chunk of each structure (S + 1)
+    cudaStream_t aux = nullptr;          // second stream: pass 2 of one range beside pass 1 of the next
+    cudaEvent_t ev_wave[nep::kMaxWaves] = {};
+    cudaEvent_t ev_join = nullptr;
 };
 
 namespace nep {

@@ -27,6 +27,11 @@ namespace nep {
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
+// (x, x), the broadcast operand of the packed f32x2 instructions
+// (__ffma2_rn / __fmul2_rn: two IEEE round-to-nearest operations per
+// instruction, bitwise the same as two scalar fmaf / __fmul_rn calls).
+__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+
 // ---------------------------------------------------------------- sizes
 constexpr int kNR = 8;               // radial orders n = 0..7
 constexpr int kNA = 6;               // angular radial orders n = 0..5
@@ -299,7 +304,9 @@ struct Profiler {
 };
 // tensor-core population network (nep_pop_tc.cu)
 size_t pop_tc_packed_bytes(int P);
-// G [N][32][Pst] FP32, U [N][P] FP64
+// kernel attributes of the tensor-core path; call outside any stream capture
+int prepare_pop_tc();
+// G [N][32][Pst] FP32, U [N][P] FP64 (launches only: capturable)
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
                   const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
                   cudaStream_t st);

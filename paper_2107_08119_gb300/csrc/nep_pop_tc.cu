@@ -344,6 +344,12 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
 
 size_t pop_tc_packed_bytes(int P) { return (size_t)((P + kTcGroup - 1) / kTcGroup) * kGroupBytes; }
 
+int prepare_pop_tc()
+{
+    return cuda_fail(cudaFuncSetAttribute(k_pop_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PopSmem)),
+                     "population kernel shared memory");
+}
+
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
                   const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
                   cudaStream_t st)
@@ -356,9 +362,6 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float*
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
     k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
     const size_t smem = sizeof(PopSmem);
-    int rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                       "population kernel shared memory");
-    if (rc) return rc;
     k_pop_tc<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, q, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
 }

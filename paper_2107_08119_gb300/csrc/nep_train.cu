@@ -27,6 +27,7 @@
 //   k_loss      per member: per-structure sums in a fixed order, RMSEs
 // SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r), k_snes_update.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <new>
 #include <vector>
@@ -38,11 +39,12 @@ namespace {
 
 constexpr int kDsCap = 192;      // neighbour capacity per atom while building (within r_c)
 constexpr int kChunkAtoms = 32;       // atoms per contraction block (chunks never span structures)
-constexpr int kContractThreads = 128;  // owner pass: 4 warps per block, one atom per warp at a time
-constexpr int kReceiverThreads = 256;  // receiver pass: 8 warps per chunk of atoms
+constexpr int kOwnerMaxThreads = 256;  // owner pass: 4 or 8 warps per block, one atom per warp at a time
 constexpr int kMaxPop = 64;
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
+
+std::atomic<unsigned long long> g_dataset_uid{0};
 
 // ------------------------------------------------------------------ build
 __global__ void k_ds_split(int N, const double* __restrict__ pos, const int* __restrict__ sid,
@@ -297,25 +299,21 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
     if (i0 >= N) return;
     const bool two = i0 + 1 < N;
     const long long i1 = two ? i0 + 1 : i0;
-    float q0[kNdes], q1[kNdes], G0[kNdes], G1[kNdes];
+    // the two atoms side by side: (atom i0, atom i1) pairs for the f32x2 FMAs
+    float2 q2[kNdes], G2[kNdes];
 #pragma unroll
     for (int v = 0; v < kNdes; ++v) {
-        q0[v] = q[i0 * kNdes + v];
-        q1[v] = q[i1 * kNdes + v];
-        G0[v] = G1[v] = 0.f;
+        q2[v] = make_float2(q[i0 * kNdes + v], q[i1 * kNdes + v]);
+        G2[v] = make_float2(0.f, 0.f);
     }
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
     for (int mu = 0; mu < n_neu; ++mu) {
         const float* w = W1t + (size_t)mu * kNdes * P + k;
-        float a0 = 0.f, a1 = 0.f;
+        float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) {
-            const float wv = w[(size_t)v * P];
-            a0 = fmaf(wv, q0[v], a0);
-            a1 = fmaf(wv, q1[v], a1);
-        }
+        for (int v = 0; v < kNdes; ++v) a = __ffma2_rn(bcast2(w[(size_t)v * P]), q2[v], a);
         const float bb = b1t[(size_t)mu * P + k], ww = w2t[(size_t)mu * P + k];
-        const float x0 = tanhf(a0 - bb), x1 = tanhf(a1 - bb);
+        const float x0 = tanhf(a.x - bb), x1 = tanhf(a.y - bb);
         float tt, e;
         float p = ww * x0, ep = fmaf(ww, x0, -p);
         two_sum(s0, p, tt, e);
@@ -326,22 +324,18 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
         two_sum(s1, p, tt, e);
         s1 = tt;
         c1 += e + ep;
-        const float d0 = ww * fmaf(-x0, x0, 1.f), d1 = ww * fmaf(-x1, x1, 1.f);
+        const float2 d = make_float2(ww * fmaf(-x0, x0, 1.f), ww * fmaf(-x1, x1, 1.f));
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) {
-            const float wv = w[(size_t)v * P];
-            G0[v] = fmaf(d0, wv, G0[v]);
-            G1[v] = fmaf(d1, wv, G1[v]);
-        }
+        for (int v = 0; v < kNdes; ++v) G2[v] = __ffma2_rn(d, bcast2(w[(size_t)v * P]), G2[v]);
     }
     const double b2 = (double)b2t[k];
     U[i0 * P + k] = (double)s0 + (double)c0 - b2;
 #pragma unroll
-    for (int v = 0; v < kNdes; ++v) G[(i0 * kNdes + v) * Pst + k] = G0[v];
+    for (int v = 0; v < kNdes; ++v) G[(i0 * kNdes + v) * Pst + k] = G2[v].x;
     if (two) {
         U[i1 * P + k] = (double)s1 + (double)c1 - b2;
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) G[(i1 * kNdes + v) * Pst + k] = G1[v];
+        for (int v = 0; v < kNdes; ++v) G[(i1 * kNdes + v) * Pst + k] = G2[v].y;
     }
 }
 
@@ -354,13 +348,14 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
 // (i -> j) so that pass 2 finds the partial forces acting on i in i's own
 // slot order.  The owner's virial contribution sum_i r_ij (x) p_kji
 // (r_ij = -r_ji) goes to W6[j][w][k].  No atomics: every value has one writer.
+// A launch covers the owners j0 <= j < j1 (a range of whole structures).
 constexpr int kOwnerChunk = 32;                                     // pairs staged per round
 constexpr int kRecFloats = (int)(sizeof(PairRec) / sizeof(float));  // 12
 constexpr int kAngFloats = kNA * kLmax * 3;                         // 72
 constexpr int kOwnerStage = kOwnerChunk * (kRecFloats + kAngFloats);  // floats per warp
 
-__global__ void __launch_bounds__(kContractThreads) k_contract_owner(
-    int N, int P, int Pst, const float* __restrict__ G, const float* __restrict__ B,
+__global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
+    int j0, int j1, int P, int Pst, const float* __restrict__ G, const float* __restrict__ B,
     const long long* __restrict__ pstart, const long long* __restrict__ rev, const PairRec* __restrict__ rec,
     const long long* __restrict__ aidx, const float* __restrict__ ang, float* __restrict__ pbuf,
     float* __restrict__ w6out, float* __restrict__ fown)
@@ -372,7 +367,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
     const int k0 = 2 * lane;
     const bool ld = k0 < Pst;  // Pst is even: the float2 at k0 is inside the row
     const int warps = (int)((gridDim.x * blockDim.x) >> 5);
-    for (int j = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < N; j += warps) {
+    for (int j = j0 + (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < j1; j += warps) {
         float2 g[kNdes];
         const float* Gj = G + (size_t)j * kNdes * Pst + k0;
 #pragma unroll
@@ -381,7 +376,7 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
         // own term G_j . B_j (B_j = sum of j's own Jacobians), for pass 2
         {
             const float4* B4 = reinterpret_cast<const float4*>(B + (size_t)j * kNdes * 3);
-            float f[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            float2 f[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
             for (int u = 0; u < kNdes * 3 / 12; ++u) {  // 4 descriptors (12 floats) per step
                 const float4 b0 = B4[3 * u], b1 = B4[3 * u + 1], b2 = B4[3 * u + 2];
@@ -390,18 +385,17 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
 #pragma unroll
                 for (int d = 0; d < 4; ++d)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        f[0][c] = fmaf(g[4 * u + d].x, bb[d][c], f[0][c]);
-                        f[1][c] = fmaf(g[4 * u + d].y, bb[d][c], f[1][c]);
-                    }
+                    for (int c = 0; c < 3; ++c) f[c] = __ffma2_rn(g[4 * u + d], bcast2(bb[d][c]), f[c]);
             }
             if (ld) {
                 float* o = fown + (size_t)j * 3 * Pst + k0;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * Pst) = make_float2(f[0][c], f[1][c]);
+                for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * Pst) = f[c];
             }
         }
-        float w6[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+        float2 w6[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) w6[w] = make_float2(0.f, 0.f);
         const long long pe = pstart[j + 1];
         for (long long q0 = pstart[j]; q0 < pe; q0 += kOwnerChunk) {
             const int nq = (int)min((long long)kOwnerChunk, pe - q0);
@@ -424,50 +418,39 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
                 const float* pr = s_rec + t * kRecFloats;  // r_ji [0..2], g_n'/r [3..10]
                 const long long ai = __shfl_sync(0xffffffffu, my_ai, t);
                 const long long rq = __shfl_sync(0xffffffffu, my_rv, t);
-                float cr0 = 0.f, cr1 = 0.f;
+                // both members of the lane at once (f32x2: two IEEE FMAs per instruction)
+                float2 cr = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int v = 0; v < kNR; ++v) {
-                    cr0 = fmaf(g[v].x, pr[3 + v], cr0);
-                    cr1 = fmaf(g[v].y, pr[3 + v], cr1);
-                }
+                for (int v = 0; v < kNR; ++v) cr = __ffma2_rn(g[v], bcast2(pr[3 + v]), cr);
                 const float r0 = pr[0], r1 = pr[1], r2 = pr[2];
-                float pv[2][3] = {{cr0 * r0, cr0 * r1, cr0 * r2}, {cr1 * r0, cr1 * r1, cr1 * r2}};
+                float2 pv[3] = {__fmul2_rn(cr, bcast2(r0)), __fmul2_rn(cr, bcast2(r1)), __fmul2_rn(cr, bcast2(r2))};
                 if (ai >= 0) {
                     const float* A = s_ang + (size_t)(ai - a0) * kAngFloats;
 #pragma unroll
                     for (int d = 0; d < kNA * kLmax; ++d) {
                         const float2 gg = g[kNR + d];
-                        const float ja0 = A[3 * d], ja1 = A[3 * d + 1], ja2 = A[3 * d + 2];
-                        pv[0][0] = fmaf(gg.x, ja0, pv[0][0]);
-                        pv[0][1] = fmaf(gg.x, ja1, pv[0][1]);
-                        pv[0][2] = fmaf(gg.x, ja2, pv[0][2]);
-                        pv[1][0] = fmaf(gg.y, ja0, pv[1][0]);
-                        pv[1][1] = fmaf(gg.y, ja1, pv[1][1]);
-                        pv[1][2] = fmaf(gg.y, ja2, pv[1][2]);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) pv[c] = __ffma2_rn(gg, bcast2(A[3 * d + c]), pv[c]);
                     }
                 }
                 if (ld) {
                     float* o = pbuf + (size_t)rq * 3 * Pst + k0;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        *reinterpret_cast<float2*>(o + (size_t)c * Pst) = make_float2(pv[0][c], pv[1][c]);
+                    for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * Pst) = pv[c];
                 }
-#pragma unroll
-                for (int m = 0; m < 2; ++m) {
-                    w6[m][0] = fmaf(-r0, pv[m][0], w6[m][0]);  // xx
-                    w6[m][1] = fmaf(-r1, pv[m][1], w6[m][1]);  // yy
-                    w6[m][2] = fmaf(-r2, pv[m][2], w6[m][2]);  // zz
-                    w6[m][3] = fmaf(-r0, pv[m][1], w6[m][3]);  // xy
-                    w6[m][4] = fmaf(-r1, pv[m][2], w6[m][4]);  // yz
-                    w6[m][5] = fmaf(-r2, pv[m][0], w6[m][5]);  // zx
-                }
+                w6[0] = __ffma2_rn(bcast2(-r0), pv[0], w6[0]);  // xx
+                w6[1] = __ffma2_rn(bcast2(-r1), pv[1], w6[1]);  // yy
+                w6[2] = __ffma2_rn(bcast2(-r2), pv[2], w6[2]);  // zz
+                w6[3] = __ffma2_rn(bcast2(-r0), pv[1], w6[3]);  // xy
+                w6[4] = __ffma2_rn(bcast2(-r1), pv[2], w6[4]);  // yz
+                w6[5] = __ffma2_rn(bcast2(-r2), pv[0], w6[5]);  // zx
             }
             __syncwarp();  // the stage is refilled by the next chunk
         }
         if (ld) {
             float* o = w6out + (size_t)j * 6 * Pst + k0;
 #pragma unroll
-            for (int w = 0; w < 6; ++w) *reinterpret_cast<float2*>(o + (size_t)w * Pst) = make_float2(w6[0][w], w6[1][w]);
+            for (int w = 0; w < 6; ++w) *reinterpret_cast<float2*>(o + (size_t)w * Pst) = w6[w];
         }
     }
 }
@@ -475,18 +458,63 @@ __global__ void __launch_bounds__(kContractThreads) k_contract_owner(
 // Contraction, pass 2 (receiver side): one block (8 warps) per chunk of <=
 // kChunkAtoms atoms of one structure; each warp takes every 8th atom i, lane l
 // members 2l and 2l + 1: F_i = G_i . B_i (from pass 1) - sum over i's slots of
-// the stored p_kji (coalesced float2 rows, in slot order).  Per chunk and member: sums of
-// U, of |F - F_tar|^2 and of the six virial components, in a fixed order
-// (atoms in order within a warp, then the warps in order).
-__global__ void __launch_bounds__(kReceiverThreads, 3) k_contract(
-    int N, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
+// the stored p_kji (coalesced float2 rows, in slot order, UNROLL slots in
+// flight).  The per-atom operands (own term, virial terms, U, F_tar, slot
+// range) of the warp's next atom are loaded while the current atom's slots
+// stream in.  Per chunk and member: sums of U, of |F - F_tar|^2 and of the six
+// virial components, in a fixed order (atoms in order within a warp, then the
+// warps in order).  A launch covers the chunks c0 <= c < c0 + gridDim.x.
+// With `discard` set, a warp that has read an atom's slots drops the 128-byte
+// L2 lines lying wholly inside them (discard.global.L2: no write-back of data
+// that is dead until the next evaluation rewrites every slot); lines shared
+// with a neighbouring atom's slots are left alone.
+constexpr int kReceiverThreads = 256;
+
+__device__ __forceinline__ void discard_l2_lines(const float* lo, const float* hi, int lane)
+{
+    const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, b = (uintptr_t)hi & ~(uintptr_t)127;
+    for (uintptr_t l = a + (uintptr_t)lane * 128; l < b; l += 32 * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(l) : "memory");
+}
+
+// Per-atom operands of the receiver pass, loaded one atom ahead.
+struct RecvAtom {
+    float2 fo[3];         // G_i . B_i of the lane's two members
+    float2 w6[6];         // owner virial terms
+    double u0, u1;        // site energies
+    float t[3];           // F_tar
+    long long ps, pe;     // slot range
+};
+
+__device__ __forceinline__ void recv_load(RecvAtom& a, int i, int P, int Pst, int k0, bool ld, bool on0, bool on1,
+                                          const double* __restrict__ U, const long long* __restrict__ pstart,
+                                          const float* __restrict__ fown, const float* __restrict__ w6in,
+                                          const float* __restrict__ f_tar)
+{
+    const float* o = fown + (size_t)i * 3 * Pst + k0;
+    const float* w = w6in + (size_t)i * 6 * Pst + k0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.fo[c] = ld ? *reinterpret_cast<const float2*>(o + (size_t)c * Pst) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a.w6[c] = ld ? *reinterpret_cast<const float2*>(w + (size_t)c * Pst) : make_float2(0.f, 0.f);
+    a.u0 = on0 ? U[(size_t)i * P + k0] : 0.0;
+    a.u1 = on1 ? U[(size_t)i * P + k0 + 1] : 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a.t[c] = f_tar[(size_t)i * 3 + c];
+    a.ps = pstart[i];
+    a.pe = pstart[i + 1];
+}
+
+template <int UNROLL>
+__global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
+    int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
     const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
     const float* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
     double* __restrict__ partials)
 {
     constexpr int kWarps = kReceiverThreads / 32;
     __shared__ double red[kWarps][kMaxPop][8];
-    const int c = blockIdx.x;
+    const int c = c0 + blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = 2 * lane;
     const bool on0 = k0 < P, on1 = k0 + 1 < P;
@@ -498,41 +526,39 @@ __global__ void __launch_bounds__(kReceiverThreads, 3) k_contract(
 #pragma unroll
             for (int w = 0; w < 8; ++w) red[warp][k0 + m][w] = 0.0;
     const int end = chunk_end[c];
-    for (int i = chunk_begin[c] + warp; i < end; i += kWarps) {
-        float F[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        if (ld) {  // own term G_i . B_i from pass 1
-            const float* o = fown + (size_t)i * 3 * Pst + k0;
+    int i = chunk_begin[c] + warp;
+    RecvAtom cur, nxt;
+    if (i < end) recv_load(cur, i, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
+    for (; i < end; i += kWarps) {
+        if (i + kWarps < end) recv_load(nxt, i + kWarps, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
+        float F[2][3] = {{cur.fo[0].x, cur.fo[1].x, cur.fo[2].x}, {cur.fo[0].y, cur.fo[1].y, cur.fo[2].y}};
+        if (ld) {
+#pragma unroll UNROLL
+            for (long long p = cur.ps; p < cur.pe; ++p) {
+                const float* o = pbuf + (size_t)p * 3 * Pst + k0;
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const float2 x = *reinterpret_cast<const float2*>(o + (size_t)cc * Pst);
-                F[0][cc] = x.x;
-                F[1][cc] = x.y;
+                for (int cc = 0; cc < 3; ++cc) {
+                    const float2 x = *reinterpret_cast<const float2*>(o + (size_t)cc * Pst);
+                    F[0][cc] -= x.x;
+                    F[1][cc] -= x.y;
+                }
             }
         }
-        const long long pe = pstart[i + 1];
-#pragma unroll 4
-        for (long long p = pstart[i]; p < pe; ++p) {
-            if (!ld) continue;
-            const float* o = pbuf + (size_t)p * 3 * Pst + k0;
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const float2 x = *reinterpret_cast<const float2*>(o + (size_t)cc * Pst);
-                F[0][cc] -= x.x;
-                F[1][cc] -= x.y;
-            }
+        if (discard) {  // after every lane's loads of i's slots (the barrier orders them)
+            __syncwarp();
+            discard_l2_lines(pbuf + (size_t)cur.ps * 3 * Pst, pbuf + (size_t)cur.pe * 3 * Pst, lane);
         }
-        const float tx = f_tar[(size_t)i * 3], ty = f_tar[(size_t)i * 3 + 1], tz = f_tar[(size_t)i * 3 + 2];
-        const float* wi = w6in + (size_t)i * 6 * Pst + k0;
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             if (!(m == 0 ? on0 : on1)) continue;
-            const float dx = F[m][0] - tx, dy = F[m][1] - ty, dz = F[m][2] - tz;
+            const float dx = F[m][0] - cur.t[0], dy = F[m][1] - cur.t[1], dz = F[m][2] - cur.t[2];
             double* r = red[warp][k0 + m];
-            r[0] += U[(size_t)i * P + k0 + m];
+            r[0] += m == 0 ? cur.u0 : cur.u1;
             r[1] += (double)dx * dx + (double)dy * dy + (double)dz * dz;
 #pragma unroll
-            for (int w = 0; w < 6; ++w) r[2 + w] += (double)wi[(size_t)w * Pst + m];
+            for (int w = 0; w < 6; ++w) r[2 + w] += (double)(m == 0 ? cur.w6[w].x : cur.w6[w].y);
         }
+        cur = nxt;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
@@ -614,12 +640,13 @@ __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
 // e/4 uses counter {e/4, 0, gen, 0x4E4550} and key {seed lo, seed hi};
 // u = (w + 1/2) 2^-32; lanes 0/1 (2/3) are the Box-Muller pair of (u0, u1)
 // ((u2, u3)).  Also writes z = m + s (.) r for a population of n_par-vectors.
-__global__ void k_gauss(long long count, int n_par, unsigned long long seed, unsigned gen,
+__global__ void k_gauss(long long count, int n_par, unsigned long long seed, const unsigned* __restrict__ d_gen,
                         const float* __restrict__ m, const float* __restrict__ s, float* __restrict__ r,
                         float* __restrict__ z)
 {
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (4 * b >= count) return;
+    const unsigned gen = *d_gen;
     uint32_t w[4];
     philox((uint32_t)b, 0u, gen, 0x4E4550u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
     float g[4];
@@ -655,17 +682,42 @@ __global__ void k_make_pop(long long count, int n_par, const float* __restrict__
     z[e] = fmaf(s[p], r[e], m[p]);
 }
 
+// Where a run of generations keeps its loss history: row (generation - base).
+struct SnesCtl {
+    double* hist;   // dev [n_gen][P][6] or NULL
+    unsigned base;  // generation counter at the start of the run
+};
+
+__global__ void k_set_ctl(SnesCtl* ctl, double* hist, unsigned base)
+{
+    ctl->hist = hist;
+    ctl->base = base;
+}
+
 // Rank the members by (loss, index), then the natural gradients (Eqs. 36-37)
 // with the rank utilities `util` and the update of m with the pre-update s
 // (Eq. 38), then s (Eq. 39).  Every block ranks the (few) members itself and
-// updates its own slice of parameters.
+// updates its own slice of parameters.  Block 0 also appends the losses to
+// the run's history (ctl, may be NULL) and advances the device generation
+// counter that the next generation's draws read.
 __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss, const float* __restrict__ util,
                               const float* __restrict__ r, float* __restrict__ m, float* __restrict__ s, float eta_m,
-                              float eta_s, int* __restrict__ order_out)
+                              float eta_s, int* __restrict__ order_out, unsigned* __restrict__ d_gen,
+                              const SnesCtl* __restrict__ ctl)
 {
     __shared__ int order[kMaxPop];
     __shared__ float u[kMaxPop];
     const int t = threadIdx.x;
+    if (blockIdx.x == 0) {
+        const unsigned g = *d_gen;
+        double* hist = ctl ? ctl->hist : nullptr;
+        if (hist) {
+            double* row = hist + (size_t)(g - ctl->base) * P * 6;
+            for (int e = t; e < P * 6; e += blockDim.x) row[e] = loss[e];
+        }
+        __syncthreads();
+        if (t == 0) *d_gen = g + 1;
+    }
     if (t < P) {
         const double lk = loss[(size_t)t * 6];
         int rank = 0;
@@ -691,6 +743,28 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
     s[p] = sp * expf(0.5f * eta_s * gs);
 }
 
+// Deterministic stand-in parameters for timing launch shapes: uniform in
+// [-0.1, 0.1] from an integer hash of the element index (Wellons' lowbias32).
+__global__ void k_tune_pop(long long count, float* __restrict__ z)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    uint32_t x = (uint32_t)e * 2654435761u + 12345u;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    z[e] = 0.1f * (2.f * ((float)(x >> 8) * (1.f / 16777216.f)) - 1.f);
+}
+
+bool valid_shape(const EvalShape& h)
+{
+    return h.waves >= 1 && h.waves <= kMaxWaves && (h.owner_warps == 4 || h.owner_warps == 8) &&
+           (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
+           (h.recv_unroll == 4 || h.recv_unroll == 8);
+}
+
 }  // namespace
 }  // namespace nep
 
@@ -709,6 +783,14 @@ struct snes_state {
     double* loss = nullptr;
     int* order = nullptr;
     float* util = nullptr;  // rank utilities u_1..u_P (a constant of P)
+    unsigned* d_gen = nullptr;  // generation counter read by the draws (device)
+    nep::SnesCtl* d_ctl = nullptr;
+    // one generation captured as a CUDA graph (snes_run), keyed by what it bakes in
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long key_uid = 0;
+    int key_epoch = -1, key_prec = -1;
+    double key_lam[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -773,41 +855,148 @@ int ensure_pop(nep_dataset* ds, int P)
     return NEP_OK;
 }
 
-int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int precision, const double* lambdas,
-             double* loss, cudaStream_t st)
+// Everything an evaluation with P members needs that must not happen inside a
+// stream capture: scratch allocation, kernel attributes, the second stream
+// and its events.
+int prepare_evaluation(nep_dataset* ds, int P)
+{
+    const int cap0 = ds->pop_cap;
+    int rc = ensure_pop(ds, P);
+    if (rc) return rc;
+    if (ds->pop_cap != cap0) ++ds->epoch;
+    if (!ds->aux) {
+        if ((rc = cuda_fail(cudaStreamCreateWithFlags(&ds->aux, cudaStreamNonBlocking), "evaluation stream")))
+            return rc;
+        for (int w = 0; w < kMaxWaves; ++w)
+            if ((rc = cuda_fail(cudaEventCreateWithFlags(&ds->ev_wave[w], cudaEventDisableTiming), "evaluation event")))
+                return rc;
+        if ((rc = cuda_fail(cudaEventCreateWithFlags(&ds->ev_join, cudaEventDisableTiming), "evaluation event")))
+            return rc;
+    }
+    const int ostage = (kOwnerMaxThreads / 32) * kOwnerStage * (int)sizeof(float);
+    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, ostage),
+                        "contraction shared memory")))
+        return rc;
+    return prepare_pop_tc();
+}
+
+// The two contraction passes over the chunk range [c_lo, c_hi) (whole
+// structures): pass 1 on st, pass 2 on `p2`.
+void launch_contraction(const nep_dataset* ds, int P, int Pst, int c_lo, int c_hi, cudaStream_t st,
+                        cudaStream_t p2, bool fork, cudaEvent_t ev)
+{
+    const EvalShape& sh = ds->shape;
+    const int ow = sh.owner_warps == 8 ? 8 : 4;
+    const int a0 = ds->h_cb[c_lo], a1 = ds->h_ce[c_hi - 1];
+    const size_t ostage = (size_t)ow * kOwnerStage * sizeof(float);
+    k_contract_owner<<<std::min(blocks_for(a1 - a0, ow), 152 * 64 / ow), 32 * ow, ostage, st>>>(
+        a0, a1, P, Pst, ds->G, ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6, ds->fown);
+    if (fork) {
+        cudaEventRecord(ev, st);
+        cudaStreamWaitEvent(p2, ev, 0);
+    }
+    auto recv = sh.recv_unroll == 8 ? k_contract<8> : k_contract<4>;
+    recv<<<c_hi - c_lo, kReceiverThreads, 0, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin, ds->chunk_end, ds->U,
+                                                   ds->pstart, ds->fown, ds->pbuf, ds->w6, ds->f_tar, ds->partials);
+}
+
+// Launches of one population evaluation (no allocation, no attribute calls:
+// safe inside a stream capture once prepare_evaluation has run).  With
+// shape.waves = W > 1 the contraction runs over up to W consecutive ranges of
+// whole structures with about equal pair counts; pass 2 of range w (second
+// stream) overlaps pass 1 of range w + 1, and a range's partial forces are
+// read back while they are still in L2.  A range never splits a structure:
+// pass 1 of a structure's owners writes into the slots of all its atoms.
+int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int precision,
+                       const double* lambdas, double* loss, cudaStream_t st)
 {
     if (precision != NEP_PREC_FP32 && precision != NEP_PREC_BF16) {
         set_error("snes_evaluate_population: unknown precision %d", precision);
         return NEP_ERR_ARG;
     }
-    int rc = ensure_pop(ds, P);
-    if (rc) return rc;
     const int nn = m->hp.n_neu, n_par = m->n_par, Pst = member_stride(P);
+    const EvalShape& sh = ds->shape;
     k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t, ds->b2t);
+    int rc;
     if (precision == NEP_PREC_BF16) {
         if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
                                 ds->U, m->d_err, st)))
             return rc;
     } else {
         const long long pairs = (ds->N + 1) / 2;
-        k_mlp_f32<<<blocks_for(pairs * P, 256), 256, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
-                                                              ds->b2t, ds->G, ds->U);
+        const int mt = sh.mlp_threads == 128 ? 128 : 256;
+        k_mlp_f32<<<blocks_for(pairs * P, mt), mt, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
+                                                            ds->b2t, ds->G, ds->U);
     }
-    const size_t ostage = (size_t)(kContractThreads / 32) * kOwnerStage * sizeof(float);
-    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)ostage),
-                        "contraction shared memory")))
-        return rc;
-    k_contract_owner<<<std::min(blocks_for(ds->N, kContractThreads / 32), 152 * 16), kContractThreads, ostage, st>>>(
-        ds->N, P, Pst, ds->G, ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6, ds->fown);
-    k_contract<<<ds->n_chunks, kReceiverThreads, 0, st>>>(ds->N, P, Pst, ds->chunk_begin, ds->chunk_end, ds->U,
-                                                          ds->pstart, ds->fown, ds->pbuf, ds->w6, ds->f_tar,
-                                                          ds->partials);
+    const int C = ds->n_chunks;
+    const int W = std::max(1, std::min(std::min(sh.waves, kMaxWaves), C));
+    // range ends: structure boundaries (the owner pass writes into the slots
+    // of every atom of its structure), near equal shares of the pairs
+    int ends[kMaxWaves];
+    int n_ranges = 0;
+    {
+        const std::vector<int>& s0 = ds->h_schunk0;  // first chunk of each structure, then C
+        const long long tot = ds->h_cpairs[C];
+        int c_lo = 0;
+        for (int w = 1; w <= W && c_lo < C; ++w) {
+            int c_hi = C;
+            if (w < W) {
+                const long long target = tot * w / W;
+                size_t k = 0;
+                while (k < s0.size() && (s0[k] <= c_lo || ds->h_cpairs[s0[k]] < target)) ++k;
+                c_hi = k < s0.size() ? s0[k] : C;
+            }
+            ends[n_ranges++] = c_hi;
+            c_lo = c_hi;
+        }
+    }
+    if (n_ranges == 1) {
+        launch_contraction(ds, P, Pst, 0, C, st, st, false, nullptr);
+    } else {
+        int c_lo = 0;
+        for (int w = 0; w < n_ranges; ++w) {
+            launch_contraction(ds, P, Pst, c_lo, ends[w], st, ds->aux, true, ds->ev_wave[w]);
+            c_lo = ends[w];
+        }
+        cudaEventRecord(ds->ev_join, ds->aux);
+        cudaStreamWaitEvent(st, ds->ev_join, 0);
+    }
     const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
                            lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
     k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_natoms, ds->partials, ds->e_tar, ds->w_tar,
                               z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
     return cuda_fail(cudaGetLastError(), "population evaluation kernels");
+}
+
+int evaluate(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int precision, const double* lambdas,
+             double* loss, cudaStream_t st)
+{
+    int rc = prepare_evaluation(ds, P);
+    if (rc) return rc;
+    return enqueue_evaluation(m, ds, z_pop, P, precision, lambdas, loss, st);
+}
+
+// Launches of one SNES generation: draws (or the given r), z = m + s r, the
+// population evaluation, ranking and update.  Capturable after
+// prepare_evaluation.
+int enqueue_generation(snes_state* st, nep_dataset* ds, int precision, const double* lambdas, const float* r_in,
+                       const SnesCtl* ctl, cudaStream_t cs)
+{
+    const long long tot = (long long)st->P * st->n_par;
+    if (r_in) {
+        int rc = cuda_fail(cudaMemcpyAsync(st->r, r_in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, cs), "copy r");
+        if (rc) return rc;
+        k_make_pop<<<blocks_for(tot, 256), 256, 0, cs>>>(tot, st->n_par, st->mean, st->sigma, st->r, st->z);
+    } else {
+        k_gauss<<<blocks_for((tot + 3) / 4, 256), 256, 0, cs>>>(tot, st->n_par, st->seed, st->d_gen, st->mean,
+                                                                st->sigma, st->r, st->z);
+    }
+    int rc = enqueue_evaluation(st->m, ds, st->z, st->P, precision, lambdas, st->loss, cs);
+    if (rc) return rc;
+    const float eta_s = (float)((3.0 + std::log((double)st->n_par)) / (5.0 * std::sqrt((double)st->n_par)));
+    k_snes_update<<<blocks_for(st->n_par, 128), 128, 0, cs>>>(st->P, st->n_par, st->loss, st->util, st->r, st->mean,
+                                                               st->sigma, 1.f, eta_s, st->order, st->d_gen, ctl);
+    return cuda_fail(cudaGetLastError(), "snes generation kernels");
 }
 
 }  // namespace
@@ -869,6 +1058,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     ds->m = m;
     ds->S = S;
     ds->N = N;
+    ds->uid = ++g_dataset_uid;
     ds->n_chunks = (int)hcb.size();
     long long* bytes = &ds->bytes;
     double* dpos = nullptr;
@@ -937,6 +1127,12 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     }
     ds->n_pairs = hps[N];
     ds->n_ang = has[N];
+    ds->h_cb = hcb;
+    ds->h_ce = hce;
+    ds->h_schunk0 = hchunk0;
+    ds->h_cpairs.resize(hcb.size() + 1);
+    for (size_t c = 0; c < hcb.size(); ++c) ds->h_cpairs[c] = hps[hcb[c]];
+    ds->h_cpairs[hcb.size()] = hps[N];
     long long* dastart = nullptr;
     if ((rc = dalloc(&ds->pj, (size_t)ds->n_pairs, bytes)) || (rc = dalloc(&ds->aidx, (size_t)ds->n_pairs, bytes)) ||
         (rc = dalloc(&ds->rec, (size_t)ds->n_pairs, bytes)) ||
@@ -1008,6 +1204,10 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->w6);
     dfree(ds->fown);
     free_adjoint(ds->adj);
+    for (int w = 0; w < kMaxWaves; ++w)
+        if (ds->ev_wave[w]) cudaEventDestroy(ds->ev_wave[w]);
+    if (ds->ev_join) cudaEventDestroy(ds->ev_join);
+    if (ds->aux) cudaStreamDestroy(ds->aux);
     delete ds;
     return NEP_OK;
 }
@@ -1067,7 +1267,8 @@ int snes_create(nep_model* m, int n_pop, const float* mean0, const float* sigma0
     if ((rc = dalloc(&st->mean, np, nullptr)) || (rc = dalloc(&st->sigma, np, nullptr)) ||
         (rc = dalloc(&st->r, tot, nullptr)) || (rc = dalloc(&st->z, tot, nullptr)) ||
         (rc = dalloc(&st->loss, (size_t)n_pop * 6, nullptr)) || (rc = dalloc(&st->order, (size_t)n_pop, nullptr)) ||
-        (rc = dalloc(&st->util, (size_t)n_pop, nullptr))) {
+        (rc = dalloc(&st->util, (size_t)n_pop, nullptr)) || (rc = dalloc(&st->d_gen, 1, nullptr)) ||
+        (rc = dalloc(&st->d_ctl, 1, nullptr))) {
         snes_destroy(st);
         return rc;
     }
@@ -1084,6 +1285,9 @@ int snes_create(nep_model* m, int n_pop, const float* mean0, const float* sigma0
     cudaError_t e = cudaMemcpy(st->mean, mean0, sizeof(float) * np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(st->sigma, sigma0, sizeof(float) * np, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(st->util, util.data(), sizeof(float) * n_pop, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(st->d_gen, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(st->d_ctl, 0, sizeof(SnesCtl));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         snes_destroy(st);
         return cuda_fail(e, "snes_create upload");
@@ -1103,6 +1307,10 @@ int snes_destroy(snes_state* st)
     dfree(st->loss);
     dfree(st->order);
     dfree(st->util);
+    dfree(st->d_gen);
+    dfree(st->d_ctl);
+    if (st->exec) cudaGraphExecDestroy(st->exec);
+    if (st->cap) cudaStreamDestroy(st->cap);
     delete st;
     return NEP_OK;
 }
@@ -1115,27 +1323,172 @@ int snes_step(snes_state* st, nep_dataset* ds, int precision, const double* lamb
         return NEP_ERR_ARG;
     }
     cudaStream_t cs = (cudaStream_t)stream;
-    const long long tot = (long long)st->P * st->n_par;
-    if (r_in) {
-        int rc = cuda_fail(cudaMemcpyAsync(st->r, r_in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, cs), "copy r");
-        if (rc) return rc;
-        k_make_pop<<<blocks_for(tot, 256), 256, 0, cs>>>(tot, st->n_par, st->mean, st->sigma, st->r, st->z);
-    } else {
-        k_gauss<<<blocks_for((tot + 3) / 4, 256), 256, 0, cs>>>(tot, st->n_par, st->seed, st->gen, st->mean,
-                                                                st->sigma, st->r, st->z);
-    }
-    int rc = evaluate(st->m, ds, st->z, st->P, precision, lambdas, st->loss, cs);
+    int rc = prepare_evaluation(ds, st->P);
     if (rc) return rc;
-    const float eta_s = (float)((3.0 + std::log((double)st->n_par)) / (5.0 * std::sqrt((double)st->n_par)));
-    k_snes_update<<<blocks_for(st->n_par, 128), 128, 0, cs>>>(st->P, st->n_par, st->loss, st->util, st->r, st->mean, st->sigma,
-                                                               1.f, eta_s, st->order);
+    if ((rc = enqueue_generation(st, ds, precision, lambdas, r_in, nullptr, cs))) return rc;
     if (loss_out) {
         rc = cuda_fail(cudaMemcpyAsync(loss_out, st->loss, sizeof(double) * st->P * 6, cudaMemcpyDeviceToDevice, cs),
                        "copy loss");
         if (rc) return rc;
     }
     ++st->gen;
-    return cuda_fail(cudaGetLastError(), "snes step kernels");
+    return NEP_OK;
+}
+
+int snes_run(snes_state* st, nep_dataset* ds, int precision, const double* lambdas, int n_gen, double* loss_hist,
+             void* stream)
+{
+    if (!st || !ds || ds->m != st->m || n_gen < 0) {
+        set_error("snes_run: bad arguments (dataset of this model, n_gen >= 0)");
+        return NEP_ERR_ARG;
+    }
+    if (precision != NEP_PREC_FP32 && precision != NEP_PREC_BF16) {
+        set_error("snes_run: unknown precision %d", precision);
+        return NEP_ERR_ARG;
+    }
+    if (n_gen == 0) return NEP_OK;
+    cudaStream_t cs = (cudaStream_t)stream;
+    int rc = prepare_evaluation(ds, st->P);
+    if (rc) return rc;
+    double lam[5] = {1.0, 1.0, 1.0, 0.05, 0.05};
+    if (lambdas)
+        for (int k = 0; k < 5; ++k) lam[k] = lambdas[k];
+    bool same = st->exec && st->key_uid == ds->uid && st->key_epoch == ds->epoch && st->key_prec == precision;
+    for (int k = 0; same && k < 5; ++k) same = st->key_lam[k] == lam[k];
+    if (!same) {
+        if (st->exec) cudaGraphExecDestroy(st->exec);
+        st->exec = nullptr;
+        cudaGraph_t g = nullptr;
+        if ((rc = cuda_fail(cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal), "begin capture")))
+            return rc;
+        rc = enqueue_generation(st, ds, precision, lam, nullptr, st->d_ctl, st->cap);
+        const cudaError_t e = cudaStreamEndCapture(st->cap, &g);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "end capture");
+        if (!rc) rc = cuda_fail(cudaGraphInstantiate(&st->exec, g, 0), "instantiate generation graph");
+        if (g) cudaGraphDestroy(g);
+        if (rc) {
+            st->exec = nullptr;
+            return rc;
+        }
+        st->key_uid = ds->uid;
+        st->key_epoch = ds->epoch;
+        st->key_prec = precision;
+        for (int k = 0; k < 5; ++k) st->key_lam[k] = lam[k];
+    }
+    k_set_ctl<<<1, 1, 0, cs>>>(st->d_ctl, loss_hist, st->gen);
+    for (int g = 0; g < n_gen; ++g)
+        if ((rc = cuda_fail(cudaGraphLaunch(st->exec, cs), "launch generation graph"))) return rc;
+    k_set_ctl<<<1, 1, 0, cs>>>(st->d_ctl, nullptr, 0u);
+    st->gen += (unsigned)n_gen;
+    return cuda_fail(cudaGetLastError(), "snes_run");
+}
+
+int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
+{
+    if (!ds || !shape) {
+        set_error("nep_dataset_set_shape: NULL argument");
+        return NEP_ERR_ARG;
+    }
+    EvalShape h;
+    h.waves = shape[0];
+    h.owner_warps = shape[1];
+    h.discard = shape[2];
+    h.mlp_threads = shape[3];
+    h.recv_unroll = shape[4];
+    if (!valid_shape(h)) {
+        set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
+                  "receiver unroll 4 or 8",
+                  kMaxWaves);
+        return NEP_ERR_ARG;
+    }
+    ds->shape = h;
+    ++ds->epoch;
+    return NEP_OK;
+}
+
+int nep_dataset_get_shape(const nep_dataset* ds, int* shape)
+{
+    if (!ds || !shape) {
+        set_error("nep_dataset_get_shape: NULL argument");
+        return NEP_ERR_ARG;
+    }
+    shape[0] = ds->shape.waves;
+    shape[1] = ds->shape.owner_warps;
+    shape[2] = ds->shape.discard;
+    shape[3] = ds->shape.mlp_threads;
+    shape[4] = ds->shape.recv_unroll;
+    return NEP_OK;
+}
+
+int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, int reps, int* shape_out,
+                     float* ms_out, void* stream)
+{
+    if (!m || !ds || ds->m != m || n_pop < 1 || n_pop > kMaxPop || reps < 1 ||
+        (precision != NEP_PREC_FP32 && precision != NEP_PREC_BF16)) {
+        set_error("nep_dataset_tune: bad arguments (dataset of this model, 1 <= n_pop <= %d, reps >= 1)", kMaxPop);
+        return NEP_ERR_ARG;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    int rc = prepare_evaluation(ds, n_pop);
+    if (rc) return rc;
+    std::vector<EvalShape> cand;
+    const int wv[] = {1, 2, 4};
+    for (int w : wv)
+        for (int ow = 4; ow <= 8; ow += 4)
+            for (int dc = 0; dc <= (w > 1 ? 1 : 0); ++dc)
+                for (int mt = 128; mt <= 256; mt += 128)
+                    for (int ru = 4; ru <= 8; ru += 4) {
+                        if (precision == NEP_PREC_BF16 && mt == 128) continue;  // the FP32 network is not launched
+                        EvalShape h;
+                        h.waves = w;
+                        h.owner_warps = ow;
+                        h.discard = dc;
+                        h.mlp_threads = mt;
+                        h.recv_unroll = ru;
+                        cand.push_back(h);
+                    }
+    const long long tot = (long long)n_pop * m->n_par;
+    float* z = nullptr;
+    double* loss = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const EvalShape keep = ds->shape;
+    auto cleanup = [&](int code) {
+        dfree(z);
+        dfree(loss);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        return code;
+    };
+    if ((rc = dalloc(&z, (size_t)tot, nullptr)) || (rc = dalloc(&loss, (size_t)n_pop * 6, nullptr))) return cleanup(rc);
+    if ((rc = cuda_fail(cudaEventCreate(&e0), "tune events")) || (rc = cuda_fail(cudaEventCreate(&e1), "tune events")))
+        return cleanup(rc);
+    k_tune_pop<<<blocks_for(tot, 256), 256, 0, cs>>>(tot, z);
+    float best_ms = 0.f;
+    EvalShape best = keep;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        ds->shape = cand[c];
+        rc = enqueue_evaluation(m, ds, z, n_pop, precision, nullptr, loss, cs);  // warm-up
+        if (!rc) rc = cuda_fail(cudaEventRecord(e0, cs), "tune event");
+        for (int r = 0; !rc && r < reps; ++r) rc = enqueue_evaluation(m, ds, z, n_pop, precision, nullptr, loss, cs);
+        if (!rc) rc = cuda_fail(cudaEventRecord(e1, cs), "tune event");
+        if (!rc) rc = cuda_fail(cudaEventSynchronize(e1), "tune timing");
+        float ms = 0.f;
+        if (!rc) rc = cuda_fail(cudaEventElapsedTime(&ms, e0, e1), "tune timing");
+        if (rc) {
+            ds->shape = keep;
+            return cleanup(rc);
+        }
+        ms /= (float)reps;
+        if (c == 0 || ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    ds->shape = best;
+    ++ds->epoch;
+    if (shape_out) nep_dataset_get_shape(ds, shape_out);
+    if (ms_out) *ms_out = best_ms;
+    return cleanup(NEP_OK);
 }
 
 int snes_get_state(snes_state* st, float* mean, float* sigma, float* r_last, int* order, void* stream)

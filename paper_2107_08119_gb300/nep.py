@@ -69,6 +69,10 @@ _SIGNATURES = {
     "snes_destroy": (C.c_int, [_vp]),
     "snes_step": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
     "snes_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "snes_run": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp]),
+    "nep_dataset_set_shape": (C.c_int, [_vp, _vp]),
+    "nep_dataset_get_shape": (C.c_int, [_vp, _vp]),
+    "nep_dataset_tune": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(C.c_float), _vp]),
     "nep_compute_efv_static": (C.c_int, [C.POINTER(_Hyper), _vp, C.c_int, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
                                          _vp, _vp, _vp]),
     "nep_tc_selftest": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp]),
@@ -381,6 +385,26 @@ class Dataset:
         _check(_lib.nep_dataset_descriptors(self._h, _ptr(q), _stream(stream)), "nep_dataset_descriptors")
         return q
 
+    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll")
+
+    def shape(self):
+        """Launch shape of the population evaluation (nep_dataset_get_shape)."""
+        a = np.zeros(5, np.int32)
+        _check(_lib.nep_dataset_get_shape(self._h, a.ctypes.data_as(_vp)), "nep_dataset_get_shape")
+        return dict(zip(self.SHAPE_KEYS, (int(v) for v in a)))
+
+    def set_shape(self, waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4):
+        a = np.asarray([waves, owner_warps, discard, mlp_threads, recv_unroll], np.int32)
+        _check(_lib.nep_dataset_set_shape(self._h, a.ctypes.data_as(_vp)), "nep_dataset_set_shape")
+
+    def tune(self, n_pop, precision=PREC_FP32, reps=5, stream=None):
+        """Autotune the launch shape (nep_dataset_tune); returns (shape, ms per evaluation)."""
+        a = np.zeros(5, np.int32)
+        ms = C.c_float()
+        _check(_lib.nep_dataset_tune(self.model._h, self._h, int(n_pop), int(precision), int(reps),
+                                     a.ctypes.data_as(_vp), C.byref(ms), _stream(stream)), "nep_dataset_tune")
+        return dict(zip(self.SHAPE_KEYS, (int(v) for v in a))), ms.value
+
     def evaluate(self, z_pop, precision=PREC_FP32, lambdas=None, stream=None):
         """z_pop: CUDA float32 (n_pop, n_par).  Returns CUDA float64 (n_pop, 6)."""
         if not (z_pop.is_cuda and z_pop.dtype == torch.float32 and z_pop.is_contiguous() and z_pop.dim() == 2):
@@ -469,6 +493,16 @@ class SNES:
         lam = None if lambdas is None else _host(lambdas, np.float64, (5,))
         _check(_lib.snes_step(self._h, ds._h, int(precision), None if lam is None else lam.ctypes.data_as(_vp),
                               _ptr(r), _ptr(loss), _stream(stream)), "snes_step")
+
+    def run(self, ds: Dataset, n_gen: int, precision=PREC_FP32, lambdas=None, history=False, stream=None):
+        """n_gen generations replayed from a captured CUDA graph (snes_run).
+        Returns the CUDA float64 (n_gen, n_pop, 6) loss history, or None."""
+        lam = None if lambdas is None else _host(lambdas, np.float64, (5,))
+        hist = (torch.empty(max(n_gen, 1), self.n_pop, LOSS_COLS, dtype=torch.float64, device="cuda")
+                if history else None)
+        _check(_lib.snes_run(self._h, ds._h, int(precision), None if lam is None else lam.ctypes.data_as(_vp),
+                             int(n_gen), _ptr(hist), _stream(stream)), "snes_run")
+        return None if hist is None else hist[:n_gen]
 
     def state(self, stream=None):
         npar = self.model.hyper.n_par

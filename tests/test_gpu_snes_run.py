@@ -1,0 +1,136 @@
+"""The graph-replayed SNES loop (snes_run) and the evaluation's launch shapes.
+
+snes_run replays one captured generation; its generation counter lives on the
+device, so n generations of snes_run must equal n calls of snes_step bit for
+bit (draws, losses, m, s).  No launch shape may change a result bit: every
+value keeps its single writer and its summation order, so the losses of
+every shape the autotuner tries must be identical."""
+import numpy as np
+import pytest
+
+from gpu_util import f32_exact
+from paper_2107_08119_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2107_08119_gb300 import build
+    build.build()
+    from paper_2107_08119_gb300 import nep
+    return nep
+
+
+def _gpu_labels(N, model, structures):
+    """Targets from the GPU force path of the model itself (values do not
+    matter here, only that every run sees the same ones)."""
+    import torch
+    E, F, W = [], [], []
+    for st in structures:
+        out = model.compute(torch.tensor(st["pos"].T.copy(), dtype=torch.float64, device="cuda"), st["box"])
+        E.append(out["e_atom"].double().sum().item() + 0.01 * len(st["pos"]))
+        F.append(out["force"].cpu().numpy().T + 0.02)
+        W.append(np.full(6, 0.1))
+    return np.array(E), np.concatenate(F), np.array(W)
+
+
+@pytest.fixture(scope="module")
+def full_set(N):
+    structures, teacher, pop = inputs.config4()
+    rng = np.random.default_rng(5)
+    model = N.NEP(f32_exact(inputs.random_z(1021, rng)).astype(np.float32))
+    E, F, W = _gpu_labels(N, model, structures)
+    ds = N.Dataset(model, structures, E, F, W)
+    yield model, ds, f32_exact(pop)
+    ds.close()
+    model.close()
+
+
+def _all_shapes(precision, N):
+    out = []
+    for w in (1, 2, 4):
+        for ow in (4, 8):
+            for dc in ((0, 1) if w > 1 else (0,)):
+                for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
+                    for ru in (4, 8):
+                        out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru))
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_every_shape_gives_identical_losses(N, full_set, prec):
+    import torch
+    model, ds, pop = full_set
+    zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
+    ds.set_shape()
+    ref = ds.evaluate(zp, prec).cpu().numpy()
+    assert np.isfinite(ref).all()
+    for sh in _all_shapes(prec, N) + [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8)]:
+        ds.set_shape(**sh)
+        assert ds.shape() == sh
+        for _ in range(3):  # repeated: a race between the passes would show as a changed bit
+            got = ds.evaluate(zp, prec).cpu().numpy()
+            assert np.array_equal(got, ref), sh
+    ds.set_shape()
+    model.sync_status()
+
+
+def test_autotuner_picks_a_candidate(N, full_set):
+    import torch
+    model, ds, pop = full_set
+    zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
+    ds.set_shape()
+    ref = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
+    shape, ms = ds.tune(50, N.PREC_BF16, reps=2)
+    assert shape in _all_shapes(N.PREC_BF16, N)
+    assert ds.shape() == shape
+    assert 0.0 < ms < 100.0
+    assert np.array_equal(ds.evaluate(zp, N.PREC_BF16).cpu().numpy(), ref)
+    ds.set_shape()
+
+
+def test_shape_validation(N, full_set):
+    model, ds, pop = full_set
+    for bad in (dict(waves=0), dict(waves=17), dict(owner_warps=6), dict(discard=2), dict(mlp_threads=64),
+                dict(recv_unroll=2)):
+        with pytest.raises(N.NepError) as e:
+            ds.set_shape(**bad)
+        assert e.value.code == -1  # NEP_ERR_ARG
+    assert ds.shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4)
+
+
+@pytest.mark.parametrize("waves", [1, 4])
+def test_run_equals_steps(N, full_set, waves):
+    """Generations from the replayed graph equal eager snes_step calls bit
+    for bit, the loss history included, and the two interleave."""
+    import torch
+    model, ds, pop = full_set
+    ds.set_shape(waves=waves, discard=1 if waves > 1 else 0)
+    m0 = f32_exact(np.random.default_rng(8).uniform(-0.5, 0.5, 1021))
+    a = N.SNES(model, 50, m0, np.full(1021, 0.1), seed=77)
+    b = N.SNES(model, 50, m0, np.full(1021, 0.1), seed=77)
+    steps = []
+    for _ in range(3):
+        loss = torch.empty(50, N.LOSS_COLS, dtype=torch.float64, device="cuda")
+        a.step(ds, N.PREC_BF16, loss=loss)
+        steps.append(loss)
+    hist = b.run(ds, 3, N.PREC_BF16, history=True)
+    assert torch.equal(hist, torch.stack(steps))
+    for x, y in zip(a.state(), b.state()):
+        assert torch.equal(x, y)
+    # interleave: graph, eager, graph (precision switch recaptures)
+    a.run(ds, 2, N.PREC_FP32)
+    b.step(ds, N.PREC_FP32)
+    b.step(ds, N.PREC_FP32)
+    h2 = a.run(ds, 1, N.PREC_BF16, history=True)
+    loss = torch.empty(50, N.LOSS_COLS, dtype=torch.float64, device="cuda")
+    b.step(ds, N.PREC_BF16, loss=loss)
+    assert torch.equal(h2[0], loss)
+    for x, y in zip(a.state(), b.state()):
+        assert torch.equal(x, y)
+    assert a.run(ds, 0) is None
+    a.close()
+    b.close()
+    ds.set_shape()
+    model.sync_status()
