@@ -124,7 +124,7 @@ __global__ void k_adj_loss(int nblocks, int N, const double* __restrict__ part, 
 
 // One harmonic's share of lambda for a pair: with alpha = Z (rhat . d) and
 // beta = grad_u Z . d_t, lambda_nl += A_nlm (g_n' alpha + g_n beta).
-__device__ __forceinline__ void adj_term(const float (&A)[kNA][kLM], const float (&g)[kNA], const float (&dg)[kNA],
+__device__ __forceinline__ void adj_term(const Harm& A, const float (&g)[kNA], const float (&dg)[kNA],
                                          int lm, float Y, float gx, float gy, float gz, float e, float tx, float ty,
                                          float tz, float (&lam)[kNdes])
 {
@@ -132,11 +132,11 @@ __device__ __forceinline__ void adj_term(const float (&A)[kNA][kLM], const float
     const float beta = fmaf(gx, tx, fmaf(gy, ty, gz * tz));
 #pragma unroll
     for (int n = 0; n < kNA; ++n)
-        lam[kNR + n * kLmax + sh_l(lm)] = fmaf(A[n][lm], fmaf(dg[n], alpha, g[n] * beta),
+        lam[kNR + n * kLmax + sh_l(lm)] = fmaf(harm(A, n, lm), fmaf(dg[n], alpha, g[n] * beta),
                                                lam[kNR + n * kLmax + sh_l(lm)]);
 }
 
-__device__ __forceinline__ void adj_pass(float x, float y, float z, const float (&A)[kNA][kLM], const float (&g)[kNA],
+__device__ __forceinline__ void adj_pass(float x, float y, float z, const Harm& A, const float (&g)[kNA],
                                          const float (&dg)[kNA], float e, float tx, float ty, float tz,
                                          float (&lam)[kNdes])
 {
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_lambda(int N, const int* __
     float lam[kNdes];
     {
         float q[kNdes];
-        float S[kNA][kLM];
+        Harm S;
         site_descriptors(ia, N, cnt, T, xh, xl, box, P, hi, li, q, S);
 #pragma unroll
         for (int v = 0; v < kNdes; ++v) row[kNdes + v] = q[v];
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_lambda(int N, const int* __
 #pragma unroll
         for (int a = 0; a < kNA; ++a)
 #pragma unroll
-            for (int m = 0; m < kLM; ++m) S[a][m] *= 2.f * sh_c(m);
+            for (int m = 0; m < kLM; ++m) harm(S, a, m) *= 2.f * sh_c(m);
 #pragma unroll
         for (int v = 0; v < kNdes; ++v) lam[v] = 0.f;
         const float4 ei = res[ia];

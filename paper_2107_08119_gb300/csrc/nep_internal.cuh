@@ -27,10 +27,20 @@ namespace nep {
 
 __host__ __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 
-// (x, x), the broadcast operand of the packed f32x2 instructions
+// Packed FP32 pairs.  On the device these are the f32x2 instructions
 // (__ffma2_rn / __fmul2_rn: two IEEE round-to-nearest operations per
-// instruction, bitwise the same as two scalar fmaf / __fmul_rn calls).
-__device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+// instruction, bitwise the same as two scalar fmaf / products); on the host
+// the two scalar operations.  bcast2(x) = (x, x) is the broadcast operand.
+__host__ __device__ __forceinline__ float2 bcast2(float x) { return make_float2(x, x); }
+
+__host__ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+#ifdef __CUDA_ARCH__
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
 
 // ---------------------------------------------------------------- sizes
 constexpr int kNR = 8;               // radial orders n = 0..7

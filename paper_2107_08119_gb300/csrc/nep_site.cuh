@@ -68,9 +68,9 @@ __host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_r
     }
 }
 
-// g_n(d) and dg_n/dd, n = 0..N-1, for d < rc.
+// (g_n(d), dg_n/dd), n = 0..N-1, for d < rc, as pairs.
 template <int N>
-__host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float inv_rc, float (&g)[N], float (&dg)[N])
+__host__ __device__ __forceinline__ void radial_gd(float d, float rc, float inv_rc, float2 (&gd)[N])
 {
     float s, c;
     const float dr = div_rc(d, rc, inv_rc);
@@ -84,23 +84,31 @@ __host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float in
     const float a = hfc * dxdr;  // (1/2) f_c dx/dr
     float Tm = 1.f, T = x;       // T_{n-1}, T_n
     float Um = 1.f, U = 2.f * x; // U_{n-2}, U_{n-1} when at order n
-    g[0] = fc;
-    dg[0] = dfc;
-    if (N > 1) {
-        g[1] = fmaf(hfc, x, hfc);
-        dg[1] = fmaf(a, 1.f, fmaf(hdfc, x, hdfc));  // dT_1/dx = 1 * U_0 = 1
-    }
+    gd[0] = make_float2(fc, dfc);
+    if (N > 1) gd[1] = make_float2(fmaf(hfc, x, hfc), fmaf(a, 1.f, fmaf(hdfc, x, hdfc)));  // dT_1/dx = U_0 = 1
 #pragma unroll
     for (int n = 2; n < N; ++n) {
         const float Tn = fmaf(2.f * x, T, -Tm);
         Tm = T;
         T = Tn;
         // dT_n/dx = n U_{n-1}; U at this point holds U_{n-1}
-        g[n] = fmaf(hfc, Tn, hfc);
-        dg[n] = fmaf(a * (float)n, U, fmaf(hdfc, Tn, hdfc));
+        gd[n] = make_float2(fmaf(hfc, Tn, hfc), fmaf(a * (float)n, U, fmaf(hdfc, Tn, hdfc)));
         const float Un = fmaf(2.f * x, U, -Um);
         Um = U;
         U = Un;
+    }
+}
+
+// g_n(d) and dg_n/dd, n = 0..N-1, for d < rc, as two arrays.
+template <int N>
+__host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float inv_rc, float (&g)[N], float (&dg)[N])
+{
+    float2 gd[N];
+    radial_gd<N>(d, rc, inv_rc, gd);
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        g[n] = gd[n].x;
+        dg[n] = gd[n].y;
     }
 }
 
@@ -165,18 +173,36 @@ __host__ __device__ __forceinline__ constexpr float sh_c(int lm)
 // l of harmonic index lm (0-based l - 1)
 __host__ __device__ __forceinline__ constexpr int sh_l(int lm) { return lm < 3 ? 0 : (lm < 8 ? 1 : (lm < 15 ? 2 : 3)); }
 
-// S[n][lm] += g[n] * Y_lm(u) for the NN radial orders held (all kNA, or a
-// lane's half of them in the lane-pair form)
-template <int NN>
-__host__ __device__ __forceinline__ void sh_acc(float (&S)[NN][kLM], const float (&g)[NN], int lm, float Y)
+// Harmonic sums S_nlm of one atom (later the coefficients A_nlm), the radial
+// orders in pairs (2p, 2p + 1) so that one packed f32x2 FMA updates two.
+constexpr int kNA2 = kNA / 2;
+static_assert(kNA % 2 == 0, "angular radial orders are paired");
+typedef float2 Harm[kNA2][kLM];
+
+__host__ __device__ __forceinline__ float& harm(Harm& S, int n, int lm)
 {
-#pragma unroll
-    for (int n = 0; n < NN; ++n) S[n][lm] = fmaf(g[n], Y, S[n][lm]);
+    return (n & 1) ? S[n >> 1][lm].y : S[n >> 1][lm].x;
+}
+__host__ __device__ __forceinline__ float harm(const Harm& S, int n, int lm)
+{
+    return (n & 1) ? S[n >> 1][lm].y : S[n >> 1][lm].x;
 }
 
-template <int NN>
-__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float (&g)[NN],
-                                                  float (&S)[NN][kLM])
+// g_n paired as (g_2p, g_2p+1)
+__host__ __device__ __forceinline__ void pair_orders(const float (&g)[kNA], float2 (&g2)[kNA2])
+{
+#pragma unroll
+    for (int p = 0; p < kNA2; ++p) g2[p] = make_float2(g[2 * p], g[2 * p + 1]);
+}
+
+// S[n][lm] += g[n] * Y_lm(u), two radial orders per packed FMA
+__host__ __device__ __forceinline__ void sh_acc(Harm& S, const float2 (&g2)[kNA2], int lm, float Y)
+{
+#pragma unroll
+    for (int p = 0; p < kNA2; ++p) S[p][lm] = ffma2(g2[p], bcast2(Y), S[p][lm]);
+}
+
+__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float2 (&g)[kNA2], Harm& S)
 {
     NEP_SH_LOCALS(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) sh_acc(S, g, lm, Yv);
@@ -185,32 +211,24 @@ __host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, con
 }
 
 // One harmonic's contribution to the angular partial force:
-//   cg = sum_n A[n][lm] g_n, cd = sum_n A[n][lm] g_n'
-//   B += cd Y, V += cg grad_u Y.
-template <int NN>
-__host__ __device__ __forceinline__ void sh_term(const float (&A)[NN][kLM], const float (&g)[NN],
-                                                 const float (&dg)[NN], int lm, float Y, float gx, float gy,
-                                                 float gz, float& B, float& Vx, float& Vy, float& Vz)
+//   (cg, cd) = sum_n A[n][lm] (g_n, g_n')   (one packed FMA per order)
+//   B += cd Y, V += cg grad_u Y             ((Vx, Vy) packed).
+__host__ __device__ __forceinline__ void sh_term(const Harm& A, const float2 (&gd)[kNA], int lm, float Y, float gx,
+                                                 float gy, float gz, float& B, float2& Vxy, float& Vz)
 {
-    float cg = 0.f, cd = 0.f;
+    float2 c = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int n = 0; n < NN; ++n) {
-        cg = fmaf(A[n][lm], g[n], cg);
-        cd = fmaf(A[n][lm], dg[n], cd);
-    }
-    B = fmaf(cd, Y, B);
-    Vx = fmaf(cg, gx, Vx);
-    Vy = fmaf(cg, gy, Vy);
-    Vz = fmaf(cg, gz, Vz);
+    for (int n = 0; n < kNA; ++n) c = ffma2(bcast2(harm(A, n, lm)), gd[n], c);
+    B = fmaf(c.y, Y, B);
+    Vxy = ffma2(bcast2(c.x), make_float2(gx, gy), Vxy);
+    Vz = fmaf(c.x, gz, Vz);
 }
 
-template <int NN>
-__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const float (&A)[NN][kLM],
-                                                  const float (&g)[NN], const float (&dg)[NN], float& B,
-                                                  float& Vx, float& Vy, float& Vz)
+__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const Harm& A, const float2 (&gd)[kNA],
+                                                  float& B, float2& Vxy, float& Vz)
 {
     NEP_SH_LOCALS(x, y, z)
-#define NEP_T(lm, Yv, gx, gy, gz) sh_term(A, g, dg, lm, Yv, gx, gy, gz, B, Vx, Vy, Vz);
+#define NEP_T(lm, Yv, gx, gy, gz) sh_term(A, gd, lm, Yv, gx, gy, gz, B, Vxy, Vz);
     NEP_SH_TABLE(NEP_T)
 #undef NEP_T
 }
@@ -338,7 +356,7 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
                                                           const float* __restrict__ xl, const Box& box,
                                                           const SiteParams& P, const float (&hi)[3],
                                                           const float (&li)[3], float (&q)[kNdes],
-                                                          float (&S)[kNA][kLM])
+                                                          Harm& S)
 {
     // radial sums are compensated (Kahan): q_0 ~ 4 accumulates ~28 terms and
     // its plain FP32 rounding dominates the site-energy error budget
@@ -346,9 +364,9 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
 #pragma unroll
     for (int a = 0; a < kNR; ++a) qR[a] = qC[a] = 0.f;
 #pragma unroll
-    for (int a = 0; a < kNA; ++a)
+    for (int a = 0; a < kNA2; ++a)
 #pragma unroll
-        for (int b = 0; b < kLM; ++b) S[a][b] = 0.f;
+        for (int b = 0; b < kLM; ++b) S[a][b] = make_float2(0.f, 0.f);
 
     // Slots are sorted by increasing distance (MD lists); walk the ranks
     // downwards so the largest (nearest) terms are added last, with all lanes
@@ -385,7 +403,9 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
             const float inv = 1.f / d;
             float g[kNA];
             radial_g<kNA>(d, P.rcA, P.inv_rcA, g);
-            sh_pass1(rx * inv, ry * inv, rz * inv, g, S);
+            float2 g2[kNA2];
+            pair_orders(g, g2);
+            sh_pass1(rx * inv, ry * inv, rz * inv, g2, S);
         }
     }
 
@@ -400,7 +420,7 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
 #pragma unroll
         for (int m = 0; m < kLM; ++m) {
             const int v = kNR + a * kLmax + sh_l(m);
-            const float y = fmaf(sh_c(m) * S[a][m], S[a][m], -qc[sh_l(m)]);
+            const float y = fmaf(sh_c(m) * harm(S, a, m), harm(S, a, m), -qc[sh_l(m)]);
             const float t = q[v] + y;
             qc[sh_l(m)] = (t - q[v]) - y;
             q[v] = t;
@@ -424,19 +444,20 @@ __host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, 
     float radial = 0.f;  // coefficient of rhat
     float Vx = 0.f, Vy = 0.f, Vz = 0.f;
     if (d2 < P.rcR2) {
-        float g[kNR], dg[kNR];
-        radial_g_dg<kNR>(d, P.rcR, P.inv_rcR, g, dg);
+        float2 gd[kNR];
+        radial_gd<kNR>(d, P.rcR, P.inv_rcR, gd);
 #pragma unroll
-        for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], dg[a], radial);
+        for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], gd[a].y, radial);
     }
     if (d2 < P.rcA2) {
-        float g[kNA], dg[kNA];
-        radial_g_dg<kNA>(d, P.rcA, P.inv_rcA, g, dg);
-        sh_pass2(ux, uy, uz, A, g, dg, radial, Vx, Vy, Vz);
+        float2 gd[kNA];
+        radial_gd<kNA>(d, P.rcA, P.inv_rcA, gd);
+        float2 Vxy = make_float2(0.f, 0.f);
+        sh_pass2(ux, uy, uz, A, gd, radial, Vxy, Vz);
         // tangential projection of V, divided by r
-        const float uv = fmaf(ux, Vx, fmaf(uy, Vy, uz * Vz));
-        Vx = (Vx - uv * ux) * inv;
-        Vy = (Vy - uv * uy) * inv;
+        const float uv = fmaf(ux, Vxy.x, fmaf(uy, Vxy.y, uz * Vz));
+        Vx = (Vxy.x - uv * ux) * inv;
+        Vy = (Vxy.y - uv * uy) * inv;
         Vz = (Vz - uv * uz) * inv;
     }
     px = fmaf(radial, ux, Vx);
@@ -449,7 +470,7 @@ __host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, 
 __host__ __device__ __forceinline__ void site_coefficients(int i, bool active, int n, int cnt, const SlotTable& nbr,
                                                            const float* __restrict__ xh,
                                                            const float* __restrict__ xl, const Box& box,
-                                                           const SiteParams& P, float (&S)[kNA][kLM],
+                                                           const SiteParams& P, Harm& S,
                                                            float (&GR)[kNR], float& U_hi, float& U_lo)
 {
     float hi[3], li[3];
@@ -465,7 +486,7 @@ __host__ __device__ __forceinline__ void site_coefficients(int i, bool active, i
     for (int a = 0; a < kNA; ++a) {
 #pragma unroll
         for (int m = 0; m < kLM; ++m) {
-            S[a][m] *= 2.f * sh_c(m) * G[kNR + a * kLmax + sh_l(m)];
+            harm(S, a, m) *= 2.f * sh_c(m) * G[kNR + a * kLmax + sh_l(m)];
         }
     }
 #pragma unroll
@@ -482,7 +503,7 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
                                                              const SiteParams& P, const PfOut& out, float& U_hi,
                                                              float& U_lo)
 {
-    float S[kNA][kLM];
+    Harm S;
     float GR[kNR];
     site_coefficients(i, active, n, cnt, nbr, xh, xl, box, P, S, GR, U_hi, U_lo);
     float hi[3], li[3];

@@ -164,10 +164,10 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
     float hi[3], li[3];
     load_pos(xh, xl, N, i, hi, li);
     float qR[kNR], qC[kNR];
-    float S[kNA][kLM];
+    Harm S;
     for (int a = 0; a < kNR; ++a) qR[a] = qC[a] = 0.f;
-    for (int a = 0; a < kNA; ++a)
-        for (int m = 0; m < kLM; ++m) S[a][m] = 0.f;
+    for (int a = 0; a < kNA2; ++a)
+        for (int m = 0; m < kLM; ++m) S[a][m] = make_float2(0.f, 0.f);
     const long long p0 = pstart[i], p1 = pstart[i + 1];
     for (long long p = p0; p < p1; ++p) {
         const int v = pj[p];
@@ -192,7 +192,9 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
             float g[kNA];
             radial_g<kNA>(d, rcA, inv_rcA, g);
             const float inv = 1.f / d;
-            sh_pass1(rx * inv, ry * inv, rz * inv, g, S);
+            float2 g2[kNA2];
+            pair_orders(g, g2);
+            sh_pass1(rx * inv, ry * inv, rz * inv, g2, S);
         }
     }
     float q[kNdes];
@@ -201,7 +203,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         for (int l = 0; l < kLmax; ++l) {
             float s2 = 0.f;
             for (int m = 0; m < kLM; ++m)
-                if (sh_l(m) == l) s2 = fmaf(sh_c(m) * S[a][m], S[a][m], s2);
+                if (sh_l(m) == l) s2 = fmaf(sh_c(m) * harm(S, a, m), harm(S, a, m), s2);
             q[kNR + a * kLmax + l] = s2;
         }
     for (int v = 0; v < kNdes; ++v) q_out[(size_t)i * kNdes + v] = q[v];
@@ -247,7 +249,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
                 for (int c = 0; c < 3; ++c) tg[c] = (dY[m][c] - ud * u[c]) * inv;
                 const int l = sh_l(m);
                 for (int a = 0; a < kNA; ++a) {
-                    const float two_s = 2.f * sh_c(m) * S[a][m];
+                    const float two_s = 2.f * sh_c(m) * harm(S, a, m);
                     for (int c = 0; c < 3; ++c)
                         J[a * kLmax + l][c] = fmaf(two_s, fmaf(dg[a] * Y[m], u[c], g[a] * tg[c]), J[a * kLmax + l][c]);
                 }
