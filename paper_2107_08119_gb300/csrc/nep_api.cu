@@ -143,6 +143,7 @@ int setup_box(const double* box9, double r_list, Box& b)
         if (b.img[d] > 2) b.img[d] = 2;
     }
     if (!cells) b.nc[0] = b.nc[1] = b.nc[2] = 0;
+    for (int d = 0; d < 3; ++d) b.cpl[d] = b.nc[d] / b.L[d];
     return NEP_OK;
 }
 

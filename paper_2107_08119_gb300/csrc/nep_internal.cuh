@@ -67,6 +67,7 @@ struct Box {
     float Lh[3];
     float Ll[3];
     int nc[3];      // cells per direction (0 when the brute-force list is used)
+    double cpl[3];  // cells per unit length nc / L (binning without a division)
     int img[3];     // largest |image shift| a pair can need per direction
 };
 

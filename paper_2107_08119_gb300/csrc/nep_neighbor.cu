@@ -4,8 +4,9 @@
 // "memory consumption") without describing their construction.  Here:
 //   1. wrap positions into the orthorhombic box, split them into FP32 hi/lo,
 //      bin atoms into cells of edge >= the list radius;
-//   2. exclusive scan of the cell counts, scatter, then sort each cell by
-//      atom index so the list order (hence every FP32 sum) is deterministic;
+//   2. exclusive scan of the cell counts and scatter (the order of atoms
+//      within a cell is whatever the atomics give: the list order below
+//      depends only on the sort keys, so it stays deterministic);
 //   3. one warp per atom scans the 27 neighbouring cells and keeps every
 //      (j, image) with |r_ij| below the list radius (full list, both
 //      directions), then orders its slots by increasing distance (the
@@ -45,8 +46,18 @@ __global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         const double L = b.L[d];
-        double x = pos[(size_t)d * n + i];
-        double w = x - L * floor(x / L);
+        const double x = pos[(size_t)d * n + i];
+        // FP64 division is slow here: atoms within one box length of the box
+        // (all of them between MD rebuilds) wrap by one exact subtraction
+        double w;
+        if (x >= 0.0 && x < L)
+            w = x;
+        else if (x >= L && x < 2.0 * L)
+            w = x - L;
+        else if (x < 0.0 && x >= -L)
+            w = x + L;
+        else
+            w = x - L * floor(x / L);
         if (w >= L) w -= L;
         if (w < 0.0) w = 0.0;
         if (wrap_in_place) {
@@ -55,7 +66,9 @@ __global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double
         }
         wx[d] = w;
         if (b.nc[0] > 0) {
-            int ci = (int)(w * (double)b.nc[d] / L);
+            // any cell within rounding of the true one is valid (cells are at
+            // least the list radius wide); the list order depends only on keys
+            int ci = (int)(w * b.cpl[d]);
             c[d] = ci < 0 ? 0 : (ci >= b.nc[d] ? b.nc[d] - 1 : ci);
         }
     }
@@ -67,31 +80,78 @@ __global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double
     }
 }
 
-// Single-block exclusive scan: cell_start[c] = sum_{c' < c} count[c'].
-__global__ void k_scan(int ncell, const int* __restrict__ count, int* __restrict__ start, const unsigned* gate)
+// Single-block exclusive scan: cell_start[c] = sum_{c' < c} count[c'].  Also
+// clears the per-cell counters for the scatter and the next build.  Rounds
+// of blockDim * kScanPer cells go through shared memory (coalesced global
+// reads and writes; padded so that a thread's run of kScanPer consecutive
+// cells is conflict-free); warp shuffles and the warp totals give the prefix.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanRound = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int scan_pad(int x) { return x + (x >> 5); }
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(int ncell, int* __restrict__ count, int* __restrict__ start,
+                                                       int* __restrict__ fill, const unsigned* gate)
 {
     if (gated_off(gate)) return;
-    __shared__ int part[1024];
-    const int t = threadIdx.x, T = blockDim.x;
-    const int chunk = (ncell + T - 1) / T;
-    const int lo = t * chunk, hi = min(ncell, lo + chunk);
-    int s = 0;
-    for (int c = lo; c < hi; ++c) s += count[c];
-    part[t] = s;
-    __syncthreads();
-    // Hillis-Steele inclusive scan over the chunk sums
-    for (int o = 1; o < T; o <<= 1) {
-        int v = (t >= o) ? part[t - o] : 0;
+    __shared__ int sc[kScanRound + kScanRound / 32];
+    __shared__ int wsum[kScanThreads / 32];
+    __shared__ int carry;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) carry = 0;
+    for (int base = 0; base < ncell; base += kScanRound) {
+#pragma unroll
+        for (int e = 0; e < kScanPer; ++e) {
+            const int x = e * kScanThreads + t;
+            sc[scan_pad(x)] = base + x < ncell ? count[base + x] : 0;
+        }
         __syncthreads();
-        part[t] += v;
+        int v[kScanPer];
+        int s = 0;
+#pragma unroll
+        for (int e = 0; e < kScanPer; ++e) {
+            v[e] = sc[scan_pad(t * kScanPer + e)];
+            s += v[e];
+        }
+        int incl = s;  // inclusive scan of the thread sums within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        int run = carry + (warp > 0 ? wsum[warp - 1] : 0) + incl - s;
+#pragma unroll
+        for (int e = 0; e < kScanPer; ++e) {
+            sc[scan_pad(t * kScanPer + e)] = run;
+            run += v[e];
+        }
+        __syncthreads();  // every thread has read carry and wsum, and sc holds the prefixes
+        if (t == kScanThreads - 1) carry = run;
+#pragma unroll
+        for (int e = 0; e < kScanPer; ++e) {
+            const int x = e * kScanThreads + t;
+            if (base + x < ncell) {
+                start[base + x] = sc[scan_pad(x)];
+                count[base + x] = 0;
+                fill[base + x] = 0;
+            }
+        }
         __syncthreads();
     }
-    int run = part[t] - s;  // exclusive prefix of this chunk
-    for (int c = lo; c < hi; ++c) {
-        start[c] = run;
-        run += count[c];
-    }
-    if (t == T - 1) start[ncell] = part[T - 1];
+    if (t == 0) start[ncell] = carry;
 }
 
 __global__ void k_scatter(int n, const int* __restrict__ atom_cell, const int* __restrict__ cell_start,
@@ -103,28 +163,6 @@ __global__ void k_scatter(int n, const int* __restrict__ atom_cell, const int* _
     const int c = atom_cell[i];
     const int slot = atomicAdd(cell_fill + c, 1);
     cell_atoms[cell_start[c] + slot] = i;
-}
-
-// Sort each cell's atoms by index (insertion sort; cells hold ~10 atoms),
-// and reset the per-cell counters for the next build.
-__global__ void k_sort_cells(int ncell, const int* __restrict__ cell_start, int* __restrict__ cell_atoms,
-                             int* __restrict__ cell_count, int* __restrict__ cell_fill, const unsigned* gate)
-{
-    if (gated_off(gate)) return;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ncell) return;
-    const int lo = cell_start[c], hi = cell_start[c + 1];
-    for (int a = lo + 1; a < hi; ++a) {
-        const int key = cell_atoms[a];
-        int b = a - 1;
-        while (b >= lo && cell_atoms[b] > key) {
-            cell_atoms[b + 1] = cell_atoms[b];
-            --b;
-        }
-        cell_atoms[b + 1] = key;
-    }
-    cell_count[c] = 0;
-    cell_fill[c] = 0;
 }
 
 __device__ __forceinline__ void list_push(int i, int n, int m_cap, int& cnt, int value, float d2, int* __restrict__ nbr,
@@ -166,6 +204,7 @@ __device__ void sort_near_first(int i, int n, int m_cap, int cnt, int* __restric
 // (squared distance, packed index) by ranking and written out.
 // Sorting on the pair of keys makes the order unique, hence deterministic.
 constexpr int kVerletWarps = 4;
+constexpr int kVerletCellWords = 192;  // per-warp cell tables: prefix, start, code, 3 shifts (32 words each)
 
 __device__ __forceinline__ bool pair_greater(float ka, int va, float kb, int vb)
 {
@@ -221,12 +260,14 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     if (gated_off(gate)) return;
     extern __shared__ float s_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per warp: lcap keys, lcap values, 28 prefix sums, 27 starts, 27 codes
-    float* skey = s_raw + (size_t)warp * (2 * lcap + 96);
+    // per warp: lcap keys, lcap values, 28 prefix sums, 27 starts, 27 codes,
+    // 27 image shifts (x, y, z)
+    float* skey = s_raw + (size_t)warp * (2 * lcap + kVerletCellWords);
     int* sval = reinterpret_cast<int*>(skey + lcap);
     int* pre = sval + lcap;
     int* cst = pre + 32;
     int* ccode = cst + 32;
+    float* csh = reinterpret_cast<float*>(ccode + 32);
     // a bounded grid strides over the atoms, so a gated-off launch is cheap
     for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += gridDim.x * kVerletWarps) {
         float hi[3], li[3];
@@ -247,6 +288,9 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
             cst[lane] = cell_start[c2];
             ccount = cell_start[c2 + 1] - cst[lane];
             ccode[lane] = image_code(sx, sy, sz);
+            csh[lane] = (float)sx * b.Lh[0];  // exact: s in {-1, 0, 1}
+            csh[32 + lane] = (float)sy * b.Lh[1];
+            csh[64 + lane] = (float)sz * b.Lh[2];
         }
         // exclusive prefix of the cell sizes
         int incl = ccount;
@@ -277,11 +321,9 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
                 if (!(j == i && code == kImgCenter)) {
                     float hj[3], lj[3];
                     load_pos(xh, xl, n, j, hj, lj);
-                    int sx, sy, sz;
-                    image_shift(code, sx, sy, sz);
-                    const float qx = fmaf((float)sx, b.Lh[0], hj[0] - hi[0]);
-                    const float qy = fmaf((float)sy, b.Lh[1], hj[1] - hi[1]);
-                    const float qz = fmaf((float)sz, b.Lh[2], hj[2] - hi[2]);
+                    const float qx = (hj[0] - hi[0]) + csh[c];
+                    const float qy = (hj[1] - hi[1]) + csh[32 + c];
+                    const float qz = (hj[2] - hi[2]) + csh[64 + c];
                     if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2) {
                         float rx, ry, rz;
                         pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
@@ -409,15 +451,13 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool
     k_bin<<<blocks_for(n, T), T, 0, st>>>(n, pos, wrap_in_place ? 1 : 0, x_ref, nl.xh, nl.xl, nl.atom_cell,
                                           nl.cell_count, b, d_gate);
     if (cells) {
-        k_scan<<<1, 1024, 0, st>>>(ncell, nl.cell_count, nl.cell_start, d_gate);
+        k_scan<<<1, kScanThreads, 0, st>>>(ncell, nl.cell_count, nl.cell_start, nl.cell_fill, d_gate);
         k_scatter<<<blocks_for(n, T), T, 0, st>>>(n, nl.atom_cell, nl.cell_start, nl.cell_fill, nl.cell_atoms,
                                                   d_gate);
-        k_sort_cells<<<blocks_for(ncell, T), T, 0, st>>>(ncell, nl.cell_start, nl.cell_atoms, nl.cell_count,
-                                                         nl.cell_fill, d_gate);
         // per-warp list buffer: a power of two >= m_cap entries of (key, value)
         int lcap = 32;
         while (lcap < nl.m_cap) lcap <<= 1;
-        const size_t smem = (size_t)kVerletWarps * (2 * lcap + 96) * sizeof(float);
+        const size_t smem = (size_t)kVerletWarps * (2 * lcap + kVerletCellWords) * sizeof(float);
         k_verlet_cells<<<std::min(blocks_for(n, kVerletWarps), kListGridCap), 32 * kVerletWarps, smem, st>>>(
             n, nl.m_cap, lcap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
             nl.vala, d_err, b, d_gate);
