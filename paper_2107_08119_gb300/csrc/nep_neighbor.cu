@@ -206,43 +206,44 @@ __device__ void sort_near_first(int i, int n, int m_cap, int cnt, int* __restric
 constexpr int kVerletWarps = 4;
 constexpr int kVerletCellWords = 192;  // per-warp cell tables: prefix, start, code, 3 shifts (32 words each)
 
-__device__ __forceinline__ bool pair_greater(float ka, int va, float kb, int vb)
+// (squared distance, packed index) as one unsigned 64-bit sort key: d2 >= 0,
+// so its IEEE bits order like its value, and the packed index is below 2^31.
+__device__ __forceinline__ unsigned long long sort_key(float d2, int v)
 {
-    return ka > kb || (ka == kb && va > vb);
+    return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)v;
 }
 
-// Sorts the warp's accepted entries by (squared distance, packed index) and
-// writes the first m of them: lane l ranks the entries c0 + l + 32 t against
-// all ns entries (broadcast shared-memory reads) and stores each at its rank,
-// slot-major in nbr and atom-major in key / vala.  The pairs are distinct, so
-// the ranks are a permutation.
+// Sorts the warp's accepted entries by their keys and writes the first m of
+// them: lane l ranks the entries c0 + l + 32 t against all ns entries
+// (broadcast shared-memory reads, one 64-bit compare each) and stores each
+// at its rank, slot-major in nbr and atom-major in key / vala.  The pairs are
+// distinct, so the ranks are a permutation.
 template <int EPL>
-__device__ __forceinline__ void rank_sort_write(int c0, int ns, int m, int lane, const float* skey, const int* sval,
-                                                int i, int n, int m_cap, int* __restrict__ nbr,
-                                                float* __restrict__ key, int* __restrict__ vala)
+__device__ __forceinline__ void rank_sort_write(int c0, int ns, int m, int lane, const unsigned long long* sk, int i,
+                                                int n, int m_cap, int* __restrict__ nbr, float* __restrict__ key,
+                                                int* __restrict__ vala)
 {
-    float ke[EPL];
-    int ve[EPL], rk[EPL];
+    unsigned long long ke[EPL];
+    int rk[EPL];
 #pragma unroll
     for (int t = 0; t < EPL; ++t) {
         const int e = c0 + lane + 32 * t;
-        ke[t] = e < ns ? skey[e] : 3.0e38f;
-        ve[t] = e < ns ? sval[e] : 0x7fffffff;
+        ke[t] = e < ns ? sk[e] : ~0ull;
         rk[t] = 0;
     }
     for (int f = 0; f < ns; ++f) {
-        const float kf = skey[f];
-        const int vf = sval[f];
+        const unsigned long long kf = sk[f];
 #pragma unroll
-        for (int t = 0; t < EPL; ++t) rk[t] += pair_greater(ke[t], ve[t], kf, vf) ? 1 : 0;
+        for (int t = 0; t < EPL; ++t) rk[t] += ke[t] > kf ? 1 : 0;
     }
 #pragma unroll
     for (int t = 0; t < EPL; ++t) {
         const int e = c0 + lane + 32 * t;
         if (e < ns && rk[t] < m) {
-            nbr[(size_t)rk[t] * n + i] = ve[t];
-            key[(size_t)i * m_cap + rk[t]] = ke[t];
-            vala[(size_t)i * m_cap + rk[t]] = ve[t];
+            const int v = (int)(unsigned)ke[t];
+            nbr[(size_t)rk[t] * n + i] = v;
+            key[(size_t)i * m_cap + rk[t]] = __uint_as_float((unsigned)(ke[t] >> 32));
+            vala[(size_t)i * m_cap + rk[t]] = v;
         }
     }
 }
@@ -262,9 +263,8 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // per warp: lcap keys, lcap values, 28 prefix sums, 27 starts, 27 codes,
     // 27 image shifts (x, y, z)
-    float* skey = s_raw + (size_t)warp * (2 * lcap + kVerletCellWords);
-    int* sval = reinterpret_cast<int*>(skey + lcap);
-    int* pre = sval + lcap;
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(s_raw + (size_t)warp * (2 * lcap + kVerletCellWords));
+    int* pre = reinterpret_cast<int*>(sk + lcap);
     int* cst = pre + 32;
     int* ccode = cst + 32;
     float* csh = reinterpret_cast<float*>(ccode + 32);
@@ -285,8 +285,9 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
             if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
             if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
             const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
-            cst[lane] = cell_start[c2];
-            ccount = cell_start[c2 + 1] - cst[lane];
+            const int c2s = cell_start[c2];
+            ccount = cell_start[c2 + 1] - c2s;
+            cst[lane] = c2s;
             ccode[lane] = image_code(sx, sy, sz);
             csh[lane] = (float)sx * b.Lh[0];  // exact: s in {-1, 0, 1}
             csh[32 + lane] = (float)sy * b.Lh[1];
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
             if (lane >= o) incl += t;
         }
         if (lane < 28) pre[lane] = incl - ccount;
+        if (lane < 27) cst[lane] -= incl - ccount;  // candidate idx of cell c sits at cell_atoms[cst[c] + idx]
         __syncwarp();
         const int total = pre[27];
         int cnt = 0;
@@ -316,15 +318,17 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
             int c = c0;
             if (idx < total) {
                 while (pre[c + 1] <= idx) ++c;  // a cell holds ~12 atoms: 0-3 steps
-                const int j = cell_atoms[cst[c] + idx - pre[c]];
+                const int j = cell_atoms[cst[c] + idx];
                 const int code = ccode[c];
                 if (!(j == i && code == kImgCenter)) {
-                    float hj[3], lj[3];
-                    load_pos(xh, xl, n, j, hj, lj);
-                    const float qx = (hj[0] - hi[0]) + csh[c];
-                    const float qy = (hj[1] - hi[1]) + csh[32 + c];
-                    const float qz = (hj[2] - hi[2]) + csh[64 + c];
+                    // hi parts first; the lo parts only for pairs that pass the quick test
+                    const float4 a = NEP_LDG(reinterpret_cast<const float4*>(xh) + j);
+                    const float qx = (a.x - hi[0]) + csh[c];
+                    const float qy = (a.y - hi[1]) + csh[32 + c];
+                    const float qz = (a.z - hi[2]) + csh[64 + c];
                     if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2) {
+                        const float4 bl = NEP_LDG(reinterpret_cast<const float4*>(xl) + j);
+                        const float hj[3] = {a.x, a.y, a.z}, lj[3] = {bl.x, bl.y, bl.z};
                         float rx, ry, rz;
                         pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
                         d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
@@ -337,8 +341,7 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
             const unsigned mask = __ballot_sync(0xffffffffu, accept);
             const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
             if (accept && pos < lcap) {
-                skey[pos] = d2;
-                sval[pos] = value;
+                sk[pos] = sort_key(d2, value);
             }
             cnt += __popc(mask);
         }
@@ -348,11 +351,11 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
         const int m = cnt < m_cap ? cnt : m_cap;
         const int ns = cnt < lcap ? cnt : lcap;
         if (ns <= 32)
-            rank_sort_write<1>(0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
+            rank_sort_write<1>(0, ns, m, lane, sk, i, n, m_cap, nbr, key, vala);
         else if (ns <= 64)
-            rank_sort_write<2>(0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
+            rank_sort_write<2>(0, ns, m, lane, sk, i, n, m_cap, nbr, key, vala);
         else
-            for (int c0 = 0; c0 < ns; c0 += 128) rank_sort_write<4>(c0, ns, m, lane, skey, sval, i, n, m_cap, nbr, key, vala);
+            for (int c0 = 0; c0 < ns; c0 += 128) rank_sort_write<4>(c0, ns, m, lane, sk, i, n, m_cap, nbr, key, vala);
         __syncwarp();  // the warp's buffers are reused by its next atom
     }
 }
