@@ -197,11 +197,11 @@ __device__ void sort_near_first(int i, int n, int m_cap, int cnt, int* __restric
 }
 
 // One warp per atom.  The candidates of the 27 neighbouring cells are
-// numbered consecutively (cell by cell, atom index order inside a cell) and
-// the lanes take them 32 at a time (a lane finds its cell by stepping from
-// the round's first cell); accepted pairs are compacted in candidate
-// order with a ballot into the warp's shared buffer, which is then sorted by
-// (squared distance, packed index) by ranking and written out.
+// numbered consecutively (cell by cell) and the lanes take them 32 at a time
+// (a lane finds its cell by stepping from the round's first cell); a quick
+// test on the hi parts compacts the survivors with a ballot, the exact test
+// then runs on them with every lane busy, and the accepted pairs are sorted
+// by (squared distance, packed index) by ranking and written out.
 // Sorting on the pair of keys makes the order unique, hence deterministic.
 constexpr int kVerletWarps = 4;
 constexpr int kVerletCellWords = 192;  // per-warp cell tables: prefix, start, code, 3 shifts (32 words each)
@@ -261,10 +261,11 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
     if (gated_off(gate)) return;
     extern __shared__ float s_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per warp: lcap keys, lcap values, 28 prefix sums, 27 starts, 27 codes,
-    // 27 image shifts (x, y, z)
-    unsigned long long* sk = reinterpret_cast<unsigned long long*>(s_raw + (size_t)warp * (2 * lcap + kVerletCellWords));
-    int* pre = reinterpret_cast<int*>(sk + lcap);
+    // per warp: lcap sort keys, lcap quick-test survivors, 28 prefix sums,
+    // 27 starts, 27 codes, 27 image shifts (x, y, z)
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(s_raw + (size_t)warp * (3 * lcap + kVerletCellWords));
+    int* sq = reinterpret_cast<int*>(sk + lcap);
+    int* pre = sq + lcap;
     int* cst = pre + 32;
     int* ccode = cst + 32;
     float* csh = reinterpret_cast<float*>(ccode + 32);
@@ -304,45 +305,60 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m
         if (lane < 27) cst[lane] -= incl - ccount;  // candidate idx of cell c sits at cell_atoms[cst[c] + idx]
         __syncwarp();
         const int total = pre[27];
-        int cnt = 0;
-        // Quick rejection with the hi parts only: their pair vector is within
-        // 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a pair that
-        // the exact (canonical hi/lo) test below would keep.
+        // Pass 1, quick rejection with the hi parts only: their pair vector is
+        // within 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a
+        // pair that the exact test keeps.  Survivors are compacted into sq.
         const float rq = sqrtf(rv2) + 1e-3f, rq2 = rq * rq;
+        int nq = 0;
         int c0 = 0;  // cell of this round's first candidate (warp-uniform)
         for (int base = 0; base < total; base += 32) {
             const int idx = base + lane;
-            bool accept = false;
+            bool pass = false;
             int value = 0;
-            float d2 = 0.f;
             int c = c0;
             if (idx < total) {
                 while (pre[c + 1] <= idx) ++c;  // a cell holds ~12 atoms: 0-3 steps
                 const int j = cell_atoms[cst[c] + idx];
                 const int code = ccode[c];
                 if (!(j == i && code == kImgCenter)) {
-                    // hi parts first; the lo parts only for pairs that pass the quick test
                     const float4 a = NEP_LDG(reinterpret_cast<const float4*>(xh) + j);
                     const float qx = (a.x - hi[0]) + csh[c];
                     const float qy = (a.y - hi[1]) + csh[32 + c];
                     const float qz = (a.z - hi[2]) + csh[64 + c];
-                    if (fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2) {
-                        const float4 bl = NEP_LDG(reinterpret_cast<const float4*>(xl) + j);
-                        const float hj[3] = {a.x, a.y, a.z}, lj[3] = {bl.x, bl.y, bl.z};
-                        float rx, ry, rz;
-                        pair_vector(i, j, code, hi, li, hj, lj, b, rx, ry, rz);
-                        d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        accept = d2 < rv2;
-                        value = j | (code << 24);
-                    }
+                    pass = fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2;
+                    value = j | (code << 24);
                 }
             }
             c0 = __shfl_sync(0xffffffffu, c, 31);
+            const unsigned mask = __ballot_sync(0xffffffffu, pass);
+            const int pos = nq + __popc(mask & ((1u << lane) - 1u));
+            if (pass && pos < lcap) sq[pos] = value;
+            nq += __popc(mask);
+        }
+        __syncwarp();
+        if (nq > lcap && lane == 0) atomicOr(err, kErrOverflow);
+        // Pass 2, the exact (canonical hi/lo) test on the survivors, every
+        // lane busy; accepted pairs are compacted into sk as sort keys.
+        const int nqs = nq < lcap ? nq : lcap;
+        int cnt = 0;
+        for (int base = 0; base < nqs; base += 32) {
+            const int e = base + lane;
+            bool accept = false;
+            int value = 0;
+            float d2 = 0.f;
+            if (e < nqs) {
+                value = sq[e];
+                const int j = value & 0xFFFFFF;
+                float hj[3], lj[3];
+                load_pos(xh, xl, n, j, hj, lj);
+                float rx, ry, rz;
+                pair_vector(i, j, value >> 24, hi, li, hj, lj, b, rx, ry, rz);
+                d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                accept = d2 < rv2;
+            }
             const unsigned mask = __ballot_sync(0xffffffffu, accept);
             const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-            if (accept && pos < lcap) {
-                sk[pos] = sort_key(d2, value);
-            }
+            if (accept) sk[pos] = sort_key(d2, value);  // pos < nqs <= lcap
             cnt += __popc(mask);
         }
         __syncwarp();
@@ -460,7 +476,7 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool
         // per-warp list buffer: a power of two >= m_cap entries of (key, value)
         int lcap = 32;
         while (lcap < nl.m_cap) lcap <<= 1;
-        const size_t smem = (size_t)kVerletWarps * (2 * lcap + kVerletCellWords) * sizeof(float);
+        const size_t smem = (size_t)kVerletWarps * (3 * lcap + kVerletCellWords) * sizeof(float);
         k_verlet_cells<<<std::min(blocks_for(n, kVerletWarps), kListGridCap), 32 * kVerletWarps, smem, st>>>(
             n, nl.m_cap, lcap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
             nl.vala, d_err, b, d_gate);
