@@ -814,6 +814,18 @@ int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, do
                double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
                double* J)
 {
+    return orc_md_record(h, z, n, box, pos, vel, mass, dt, n_steps, t0, tau, fe, thermo, J, NULL, NULL);
+}
+
+/*
+ * orc_md_ext that also records, for every step s, the per-atom virials W_i
+ * (n x 9) and velocities v_i (n x 3) from which J(s) is taken (after the
+ * second half kick, before the thermostat): W_hist[s], v_hist[s].
+ */
+int orc_md_record(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
+                  double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
+                  double* J, double* W_hist, double* v_hist)
+{
     const double conv = amu_a2_fs2_in_ev();
     const double kb = 8.617333262e-5; /* eV/K, CODATA 2018 */
     double* U = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -849,6 +861,8 @@ int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, do
         if (s < 0) continue; /* forces of the starting configuration */
         for (int k = 0; k < 3 * n; ++k) vel[k] += acc * F[k];
         if (J) orc_heat_current(n, W, vel, J + 3 * s);
+        if (W_hist) memcpy(W_hist + (size_t)s * 9 * n, W, sizeof(double) * 9 * (size_t)n);
+        if (v_hist) memcpy(v_hist + (size_t)s * 3 * n, vel, sizeof(double) * 3 * (size_t)n);
         double ep = 0.0, ek = 0.0;
         for (int i = 0; i < n; ++i) ep += U[i];
         for (int k = 0; k < 3 * n; ++k) ek += 0.5 * mass * conv * vel[k] * vel[k];
@@ -867,6 +881,59 @@ int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, do
     free(F);
     free(W);
     return rcode;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Spectral heat current (Sec. II.B).                                        */
+/* ------------------------------------------------------------------------ */
+/*
+ * Virial-velocity correlation K(t) = sum_i < W_i(0) . v_i(t) >, with
+ * (W . v)^a = sum_b W^{ab} v^b (the contraction of the heat current, Eq. 7).
+ * Given the per-atom virials and velocities of n_samples samples taken dt_s
+ * apart (W_hist[s] n x 9, v_hist[s] n x 3), K_sum[tau][a] is the sum over all
+ * time origins s0 with s0 + tau < n_samples of sum_i (W_i(s0) . v_i(s0 + tau))^a,
+ * for 0 <= tau < n_lags; the average is K_sum[tau] / (n_samples - tau).
+ */
+void orc_shc(int n, int n_samples, int n_lags, const double* W_hist, const double* v_hist, double* K_sum)
+{
+    for (int t = 0; t < n_lags; ++t)
+        for (int a = 0; a < 3; ++a) K_sum[3 * t + a] = 0.0;
+    for (int s = 0; s < n_samples; ++s) {          /* the later time s0 + tau */
+        const double* v = v_hist + (size_t)s * 3 * n;
+        for (int t = 0; t < n_lags && t <= s; ++t) {  /* lag tau: origin s - tau */
+            const double* W = W_hist + (size_t)(s - t) * 9 * n;
+            for (int i = 0; i < n; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    double k = 0.0;
+                    for (int b = 0; b < 3; ++b) k += W[9 * (size_t)i + 3 * a + b] * v[3 * (size_t)i + b];
+                    K_sum[3 * t + a] += k;
+                }
+        }
+    }
+}
+
+/*
+ * The transform of Sec. II.B: (2 / (T V)) int K(t) e^{i w t} dt =
+ * sum_nu kappa_{mu nu}(w) F_e^nu.  K is known at t = tau dt_s for
+ * 0 <= tau < n_lags and taken as even in t (steady state), so the integral is
+ * 2 int_0^T K(t) cos(w t) dt with T = (n_lags - 1) dt_s, evaluated by the
+ * trapezoid rule; window = 1 multiplies K by the Hann window
+ * (1 + cos(pi tau / (n_lags - 1))) / 2 first.  out[k][a] = scale * integral
+ * for omega[k] (rad per unit of dt_s); scale = 2 / (T V F_e) gives kappa(w).
+ */
+void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, const double* omega, double scale,
+                      int window, double* out)
+{
+    for (int k = 0; k < n_omega; ++k)
+        for (int a = 0; a < 3; ++a) {
+            double sum = 0.0;
+            for (int t = 0; t < n_lags; ++t) {
+                double w = (t == 0 || t == n_lags - 1) ? 0.5 : 1.0; /* trapezoid weights */
+                if (window && n_lags > 1) w *= 0.5 * (1.0 + cos(ORC_PI * t / (n_lags - 1)));
+                sum += w * K[3 * t + a] * cos(omega[k] * t * dt_s);
+            }
+            out[3 * k + a] = scale * 2.0 * dt_s * sum;
+        }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -49,6 +49,12 @@ int orc_md(const orc_hyper* h, const double* z, int n, const double* box, double
 int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
                double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
                double* J);
+int orc_md_record(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
+                  double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
+                  double* J, double* W_hist, double* v_hist);
+void orc_shc(int n, int n_samples, int n_lags, const double* W_hist, const double* v_hist, double* K_sum);
+void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, const double* omega, double scale,
+                      int window, double* out);
 int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms, const double* boxes,
              const double* pos, const double* e_tar, const double* f_tar, const double* w_tar,
              const double* lambdas, double* out);

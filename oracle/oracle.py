@@ -85,6 +85,10 @@ def _load():
             "orc_md": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, _D, _D]),
             "orc_md_ext": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, C.c_double,
                                      C.c_double, _D, _D, _D]),
+            "orc_md_record": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int,
+                                        C.c_double, C.c_double, _D, _D, _D, _D, _D]),
+            "orc_shc": (None, [C.c_int, C.c_int, C.c_int, _D, _D, _D]),
+            "orc_shc_spectrum": (None, [C.c_int, _D, C.c_double, C.c_int, _D, C.c_double, C.c_int, _D]),
             "orc_loss": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D]),
             "orc_force_loss_grad": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D]),
             "orc_snes_utilities": (None, [C.c_int, _D]),
@@ -257,6 +261,49 @@ def md_ext(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: int, 
                               float(dt), n_steps, float(t0), float(tau), None if fe_arr is None else _d(fe_arr),
                               _d(thermo), _d(J)), "md_ext")
     return pos, vel, thermo, J
+
+
+def md_record(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: int, t0: float = 0.0,
+              tau: float = 0.0, fe=None):
+    """md_ext that also returns, per step, the per-atom virials W_i
+    (n_steps, n, 3, 3) and velocities (n_steps, n, 3) from which J is taken."""
+    z = _f64(z)
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    box = _f64(box, (3, 3))
+    n = pos.shape[0]
+    thermo = np.zeros((n_steps, 2))
+    J = np.zeros((n_steps, 3))
+    Wh = np.zeros((n_steps, n, 9))
+    vh = np.zeros((n_steps, n, 3))
+    fe_arr = None if fe is None else _f64(fe, (3,))
+    _check(_load().orc_md_record(C.byref(h.c()), _d(z), n, _d(box), _d(pos), _d(vel), float(mass), float(dt),
+                                 n_steps, float(t0), float(tau), None if fe_arr is None else _d(fe_arr), _d(thermo),
+                                 _d(J), _d(Wh), _d(vh)), "md_record")
+    return pos, vel, thermo, J, Wh.reshape(n_steps, n, 3, 3), vh
+
+
+def shc(W_hist, v_hist, n_lags: int):
+    """Sums over time origins of the virial-velocity correlation,
+    K_sum[tau] = sum_{s0} sum_i W_i(s0) . v_i(s0 + tau), for the samples given
+    (W_hist (S, n, 3, 3), v_hist (S, n, 3)); the average is K_sum[tau] / (S - tau)."""
+    W = _f64(W_hist)
+    v = _f64(v_hist)
+    S, n = v.shape[0], v.shape[1]
+    K = np.zeros((n_lags, 3))
+    _load().orc_shc(n, S, n_lags, _d(W), _d(v), _d(K))
+    return K
+
+
+def shc_spectrum(K, dt_s: float, omega, scale: float = 1.0, window: bool = False):
+    """scale * 2 int_0^T K(t) cos(w t) dt (trapezoid, K even in t) for each
+    omega; K (n_lags, 3) at lags t = tau dt_s."""
+    K = _f64(K, (-1, 3))
+    om = _f64(omega, (-1,))
+    out = np.zeros((om.shape[0], 3))
+    _load().orc_shc_spectrum(K.shape[0], _d(K), float(dt_s), om.shape[0], _d(om), float(scale), 1 if window else 0,
+                             _d(out))
+    return out
 
 
 def _dataset_arrays(structures):

@@ -575,30 +575,42 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
 // One block per member: per structure, the chunk sums (fixed order), then the
 // RMSEs of Eqs. 30-32 with energy and virial per atom, and L1, L2 (Eqs. 33-34).
 __global__ void k_loss(int P, int S, int n_par, int N, const int* __restrict__ s_chunk0,
-                       const int* __restrict__ s_natoms, const double* __restrict__ partials,
+                       const double* __restrict__ s_inv_na, const double* __restrict__ partials,
                        const double* __restrict__ e_tar, const double* __restrict__ w_tar,
                        const float* __restrict__ z, double l_e, double l_f, double l_v, double l_1, double l_2,
                        double* __restrict__ loss)
 {
+    constexpr int kBatch = 8;  // chunks whose loads are issued together (summed in order)
     const int k = blockIdx.x;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // se, sf, sv, l1, l2
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
-        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int c = s_chunk0[s]; c < s_chunk0[s + 1]; ++c)
-            for (int w = 0; w < 8; ++w) v[w] += partials[((size_t)c * P + k) * 8 + w];
-        const double na = (double)s_natoms[s];
-        const double de = (v[0] - e_tar[s]) / na;
-        acc[0] += de * de;
-        acc[1] += v[1];
-        for (int w = 0; w < 6; ++w) {
-            const double dv = (v[2 + w] - w_tar[(size_t)s * 6 + w]) / na;
-            acc[2] += dv * dv;
-        }
-    }
     for (int p = threadIdx.x; p < n_par; p += blockDim.x) {
         const double zz = (double)z[(size_t)k * n_par + p];
         acc[3] += fabs(zz);
         acc[4] += zz * zz;
+    }
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int c1 = s_chunk0[s + 1];
+        for (int c0 = s_chunk0[s]; c0 < c1; c0 += kBatch) {
+            double b[kBatch][8];
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q)
+#pragma unroll
+                for (int w = 0; w < 8; ++w) b[q][w] = c0 + q < c1 ? partials[((size_t)(c0 + q) * P + k) * 8 + w] : 0.0;
+#pragma unroll
+            for (int q = 0; q < kBatch; ++q)
+                if (c0 + q < c1)
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) v[w] += b[q][w];
+        }
+        const double inv = s_inv_na[s];  // per-atom energies and virials (FP64 division is slow here)
+        const double de = (v[0] - e_tar[s]) * inv;
+        acc[0] += de * de;
+        acc[1] += v[1];
+        for (int w = 0; w < 6; ++w) {
+            const double dv = (v[2 + w] - w_tar[(size_t)s * 6 + w]) * inv;
+            acc[2] += dv * dv;
+        }
     }
     __shared__ double tot[5];
     block_sum_store<5>(acc, tot);
@@ -653,14 +665,18 @@ __global__ void k_gauss(long long count, int n_par, unsigned long long seed, con
     philox((uint32_t)b, 0u, gen, 0x4E4550u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
     float g[4];
     for (int pr = 0; pr < 2; ++pr) {
+        // u = (w + 1/2) 2^-32 and 1 - u are exact in FP64; Box-Muller in FP32
+        // (FP64 transcendentals are slow on this part) with ln u taken as
+        // log1p(-(1 - u)) when u is near 1, so that the radius keeps full
+        // relative precision where ln u is tiny
         const double u0 = ((double)w[2 * pr] + 0.5) * (1.0 / 4294967296.0);
         const double u1 = ((double)w[2 * pr + 1] + 0.5) * (1.0 / 4294967296.0);
-        // Box-Muller in FP64 (a few operations per draw), rounded once to FP32
-        const double rad = sqrt(-2.0 * log(u0));
-        double sn, cs;
-        sincospi(2.0 * u1, &sn, &cs);
-        g[2 * pr] = (float)(rad * cs);
-        g[2 * pr + 1] = (float)(rad * sn);
+        const float lu = u0 < 0.5 ? logf((float)u0) : log1pf(-(float)(1.0 - u0));
+        const float rad = sqrtf(-2.f * lu);
+        float sn, cs;
+        sincospif(2.f * (float)u1, &sn, &cs);
+        g[2 * pr] = rad * cs;
+        g[2 * pr + 1] = rad * sn;
     }
     for (int l = 0; l < 4; ++l) {
         const long long e = 4 * b + l;
@@ -735,10 +751,17 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
     const int p = blockIdx.x * blockDim.x + t;
     if (p >= n_par) return;
     float gm = 0.f, gs = 0.f;
-    for (int q = 0; q < P; ++q) {
-        const float rv = r[(size_t)order[q] * n_par + p];
-        gm = fmaf(u[q], rv, gm);
-        gs = fmaf(u[q], fmaf(rv, rv, -1.f), gs);
+    constexpr int kBatch = 10;  // draws loaded together, then summed in rank order
+    for (int q0 = 0; q0 < P; q0 += kBatch) {
+        float rv[kBatch];
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) rv[b] = q0 + b < P ? r[(size_t)order[q0 + b] * n_par + p] : 0.f;
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b)
+            if (q0 + b < P) {
+                gm = fmaf(u[q0 + b], rv[b], gm);
+                gs = fmaf(u[q0 + b], fmaf(rv[b], rv[b], -1.f), gs);
+            }
     }
     const float sp = s[p];
     m[p] = fmaf(eta_m * sp, gm, m[p]);
@@ -965,7 +988,7 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
     }
     const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
                            lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
-    k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_natoms, ds->partials, ds->e_tar, ds->w_tar,
+    k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
                               z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
     return cuda_fail(cudaGetLastError(), "population evaluation kernels");
 }
@@ -1079,6 +1102,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     };
     if ((rc = dalloc(&ds->boxes, S, bytes)) || (rc = dalloc(&ds->sid, N, bytes)) ||
         (rc = dalloc(&ds->sstart, S + 1, bytes)) || (rc = dalloc(&ds->s_natoms, S, bytes)) ||
+        (rc = dalloc(&ds->s_inv_na, S, bytes)) ||
         (rc = dalloc(&ds->s_chunk0, S + 1, bytes)) || (rc = dalloc(&ds->chunk_begin, ds->n_chunks, bytes)) ||
         (rc = dalloc(&ds->chunk_end, ds->n_chunks, bytes)) || (rc = dalloc(&ds->q, (size_t)N * kNdes, bytes)) ||
         (rc = dalloc(&ds->B, (size_t)N * kNdes * 3, bytes)) || (rc = dalloc(&ds->pstart, (size_t)N + 1, bytes)) ||
@@ -1096,6 +1120,9 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     up(ds->sid, hsid.data(), sizeof(int) * N);
     up(ds->sstart, hsstart.data(), sizeof(int) * (S + 1));
     up(ds->s_natoms, hnat.data(), sizeof(int) * S);
+    std::vector<double> hinv(S);
+    for (int t = 0; t < S; ++t) hinv[t] = 1.0 / hnat[t];
+    up(ds->s_inv_na, hinv.data(), sizeof(double) * S);
     up(ds->s_chunk0, hchunk0.data(), sizeof(int) * (S + 1));
 
     up(ds->chunk_begin, hcb.data(), sizeof(int) * hcb.size());
@@ -1178,6 +1205,7 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->sid);
     dfree(ds->sstart);
     dfree(ds->s_natoms);
+    dfree(ds->s_inv_na);
     dfree(ds->s_chunk0);
     dfree(ds->chunk_begin);
     dfree(ds->chunk_end);
