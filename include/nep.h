@@ -190,6 +190,41 @@ int nep_md_set_thermostat(nep_md* md, double t0, double tau);
  */
 int nep_md_set_hnemd(nep_md* md, const double* fe);
 
+/*
+ * nep_md_set_shc -- spectral heat current (Sec. II.B): accumulate the
+ * virial-velocity correlation K(t) = sum_i < W_i(0) . v_i(t) >, with
+ * (W . v)^a = sum_b W^{ab} v^b as in Eq. 7, during nep_md_step.  Every
+ * `every`-th step (counted from this call, across nep_md_step calls) is a
+ * sample s: W_i of that step goes into a ring of n_lags samples and, with
+ * v_i(s) taken where J is (after the second half kick, before a thermostat),
+ * sum_i W_i(s - tau) . v_i(s) is added to K[tau] for 0 <= tau < min(s + 1,
+ * n_lags), in FP64 and a fixed order.  Memory: 36 n n_lags bytes of ring.
+ *   n_lags  0 (off: frees the buffers) or 1..100000; every >= 1.
+ * Resets the sums.  Errors: NEP_ERR_ARG, NEP_ERR_OOM.
+ */
+int nep_md_set_shc(nep_md* md, int n_lags, int every);
+/*
+ * nep_md_get_shc -- K[tau] (dev [n_lags][3] FP64, or NULL) = the sum for lag
+ * tau over the samples so far divided by its number of time origins
+ * (n_samples - tau; 0 where there is none), and the number of samples
+ * (host, or NULL).  Stream-ordered after the steps on `stream`.
+ * Errors: NEP_ERR_ARG (NULL handle, correlation off), NEP_ERR_CUDA.
+ */
+int nep_md_get_shc(nep_md* md, double* K, long long* n_samples, void* stream);
+/*
+ * nep_shc_spectrum -- the transform of Sec. II.B, (2/(T V)) int K(t) e^{iwt} dt
+ * = sum_nu kappa_{mu nu}(w) F_e^nu, for K known at t = tau dt_lag,
+ * 0 <= tau < n_lags, and even in t: out[k][a] = scale * 2 * (trapezoid of
+ * K[tau][a] cos(omega_k tau dt_lag) over the lags), with K first multiplied by
+ * the Hann window (1 + cos(pi tau / (n_lags - 1))) / 2 when window != 0.
+ * scale = 2 / (T V F_e) gives kappa(w) in the units of K dt / (T V F_e).
+ *   K dev [n_lags][3]; omega dev [n_omega] (rad per unit of dt_lag);
+ *   out dev [n_omega][3].  All FP64.
+ * Errors: NEP_ERR_ARG, NEP_ERR_CUDA.
+ */
+int nep_shc_spectrum(const double* K, int n_lags, double dt_lag, int n_omega, const double* omega, double scale,
+                     int window, double* out, void* stream);
+
 /* Number of neighbour-list builds so far (synchronises `stream`). */
 int nep_md_rebuild_count(nep_md* md, long long* count, void* stream);
 

@@ -20,6 +20,11 @@
 //   thermostat     Berendsen: after J, v *= lambda with lambda^2 = 1 +
 //                  (dt/tau)(T0/T - 1), T from E_kin with 3N - 3 degrees of
 //                  freedom (k_scale_v)
+//   spectral heat current (nep_md_set_shc): on every `every`-th step the
+//                  assembly writes W_i into a ring of n_lags samples and,
+//                  next to J, k_shc_corr / k_shc_reduce add
+//                  sum_i W_i(s - tau) . v_i(s) to K[tau] for every lag tau
+//                  already in the ring (Sec. II.B)
 #include <cmath>
 #include <new>
 
@@ -121,6 +126,82 @@ __global__ void k_hnemd_kick(int n, float* __restrict__ F, const float* __restri
     block_sum_store<4>(acc, partials + (size_t)blockIdx.x * 4);
 }
 
+// Virial-velocity correlation of one sample s (the ring holds W of the last
+// `avail` samples, sample s in slot `slot0`): warp w of block (bx, by) takes
+// lag tau = 8 bx + w and the atoms of chunk by, and writes
+// sum_i (W_i(s - tau) . v_i(s))^a for its chunk, in a fixed order (lane
+// strides, then a butterfly), to part[by][tau][a].  The products are FP32
+// and the sums FP64, as in the heat current of the assembly.
+constexpr int kShcChunk = 4096;
+constexpr int kShcLagsPerBlock = 8;
+
+__global__ void __launch_bounds__(32 * kShcLagsPerBlock) k_shc_corr(int n, int n_lags, int avail, int slot0,
+                                                                      const float* __restrict__ ring,
+                                                                      const double* __restrict__ vel,
+                                                                      double* __restrict__ part)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tau = blockIdx.x * kShcLagsPerBlock + warp;
+    if (tau >= avail) return;  // warp-uniform
+    const int slot = (slot0 - tau + n_lags) % n_lags;
+    const float* W = ring + (size_t)slot * 9 * n;
+    const int c0 = blockIdx.y * kShcChunk, c1 = min(n, c0 + kShcChunk);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int i = c0 + lane; i < c1; i += 32) {
+        const float v0 = (float)vel[i], v1 = (float)vel[(size_t)n + i], v2 = (float)vel[2 * (size_t)n + i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            acc[a] += (double)(W[(size_t)(3 * a) * n + i] * v0) + (double)(W[(size_t)(3 * a + 1) * n + i] * v1) +
+                      (double)(W[(size_t)(3 * a + 2) * n + i] * v2);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    if (lane == 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) part[((size_t)blockIdx.y * n_lags + tau) * 3 + a] = acc[a];
+}
+
+// sum[tau][a] += the chunk partials of this sample, chunks in order
+__global__ void k_shc_reduce(int n_lags, int avail, int n_chunks, const double* __restrict__ part,
+                             double* __restrict__ sum)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= avail * 3) return;
+    const int tau = e / 3, a = e % 3;
+    double t = 0.0;
+    for (int c = 0; c < n_chunks; ++c) t += part[((size_t)c * n_lags + tau) * 3 + a];
+    sum[(size_t)tau * 3 + a] += t;
+}
+
+// K[tau] = sum[tau] / (number of origins), 0 without any
+__global__ void k_shc_average(int n_lags, long long n_samples, const double* __restrict__ sum, double* __restrict__ K)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_lags * 3) return;
+    const long long origins = n_samples - e / 3;
+    K[e] = origins > 0 ? sum[e] / (double)origins : 0.0;
+}
+
+// out[k][a] = scale * 2 * trapezoid of K[tau][a] cos(omega_k tau dt) over the
+// lags (K even in t), optionally Hann-windowed (Sec. II.B transform)
+__global__ void k_shc_spectrum(int n_lags, const double* __restrict__ K, double dt, int n_omega,
+                               const double* __restrict__ omega, double scale, int window, double* __restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_omega * 3) return;
+    const int k = e / 3, a = e % 3;
+    const double w0 = omega[k];
+    double s = 0.0;
+    for (int t = 0; t < n_lags; ++t) {
+        double w = (t == 0 || t == n_lags - 1) ? 0.5 : 1.0;
+        if (window && n_lags > 1) w *= 0.5 * (1.0 + cospi((double)t / (n_lags - 1)));
+        s += w * K[(size_t)t * 3 + a] * cos(w0 * t * dt);
+    }
+    out[e] = scale * 2.0 * dt * s;
+}
+
 // v *= lambda (the Berendsen factor k_md_finish left in red[14])
 __global__ void k_scale_v(int n, double* __restrict__ vel, const double* __restrict__ red)
 {
@@ -207,7 +288,27 @@ struct nep_md {
     double fe[3] = {0.0, 0.0, 0.0};
     bool drive = false;
     float* w_atom = nullptr;  // [9][n] per-atom virials (HNEMD only)
+    // spectral heat current: ring of per-atom virials, lag sums, chunk partials
+    int shc_lags = 0, shc_every = 1;
+    long long shc_step = 0, shc_samples = 0;
+    float* shc_ring = nullptr;   // [n_lags][9][n]
+    double* shc_sum = nullptr;   // [n_lags][3]
+    double* shc_part = nullptr;  // [chunks][n_lags][3]
 };
+
+namespace {
+void free_shc(nep_md* md)
+{
+    if (md->shc_ring) cudaFree(md->shc_ring);
+    if (md->shc_sum) cudaFree(md->shc_sum);
+    if (md->shc_part) cudaFree(md->shc_part);
+    md->shc_ring = nullptr;
+    md->shc_sum = nullptr;
+    md->shc_part = nullptr;
+    md->shc_lags = 0;
+    md->shc_step = md->shc_samples = 0;
+}
+}  // namespace
 
 extern "C" {
 
@@ -266,6 +367,7 @@ int nep_md_destroy(nep_md* md)
     if (md->rebuilds) cudaFree(md->rebuilds);
     if (md->red) cudaFree(md->red);
     if (md->w_atom) cudaFree(md->w_atom);
+    free_shc(md);
     delete md;
     return NEP_OK;
 }
@@ -301,6 +403,60 @@ int nep_md_set_hnemd(nep_md* md, const double* fe)
     }
     md->need_init = true;  // the next step recomputes the starting forces with (or without) the drive
     return NEP_OK;
+}
+
+int nep_md_set_shc(nep_md* md, int n_lags, int every)
+{
+    if (!md || n_lags < 0 || n_lags > 100000 || (n_lags > 0 && every < 1)) {
+        set_error("nep_md_set_shc: bad arguments (0 <= n_lags <= 100000, every >= 1)");
+        return NEP_ERR_ARG;
+    }
+    cudaDeviceSynchronize();
+    free_shc(md);
+    if (n_lags == 0) return NEP_OK;
+    const int chunks = (md->n + kShcChunk - 1) / kShcChunk;
+    cudaError_t e = cudaMalloc((void**)&md->shc_ring, sizeof(float) * 9 * (size_t)md->n * n_lags);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&md->shc_sum, sizeof(double) * 3 * (size_t)n_lags);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&md->shc_part, sizeof(double) * 3 * (size_t)n_lags * chunks);
+    if (e == cudaSuccess) e = cudaMemset(md->shc_sum, 0, sizeof(double) * 3 * (size_t)n_lags);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_shc(md);
+        set_error("nep_md_set_shc: %s", cudaGetErrorString(e));
+        return NEP_ERR_OOM;
+    }
+    md->shc_lags = n_lags;
+    md->shc_every = every;
+    return NEP_OK;
+}
+
+int nep_md_get_shc(nep_md* md, double* K, long long* n_samples, void* stream)
+{
+    if (!md || md->shc_lags == 0) {
+        set_error("nep_md_get_shc: NULL handle or no correlation switched on (nep_md_set_shc)");
+        return NEP_ERR_ARG;
+    }
+    if (n_samples) *n_samples = md->shc_samples;
+    if (K) {
+        const int e = md->shc_lags * 3;
+        k_shc_average<<<(e + 255) / 256, 256, 0, (cudaStream_t)stream>>>(md->shc_lags, md->shc_samples, md->shc_sum,
+                                                                        K);
+        return cuda_fail(cudaGetLastError(), "nep_md_get_shc");
+    }
+    return NEP_OK;
+}
+
+int nep_shc_spectrum(const double* K, int n_lags, double dt_lag, int n_omega, const double* omega, double scale,
+                     int window, double* out, void* stream)
+{
+    if (!K || !omega || !out || n_lags < 1 || n_omega < 1 || !(dt_lag > 0.0)) {
+        set_error("nep_shc_spectrum: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    const int e = n_omega * 3;
+    k_shc_spectrum<<<(e + 127) / 128, 128, 0, (cudaStream_t)stream>>>(n_lags, K, dt_lag, n_omega, omega, scale,
+                                                                      window ? 1 : 0, out);
+    return cuda_fail(cudaGetLastError(), "nep_shc_spectrum");
 }
 
 int nep_md_invalidate(nep_md* md)
@@ -395,6 +551,10 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
             return rc;
         m->prof.end(pk, st);
         int b1 = 0, b2 = 0, c2 = 0;
+        // spectral heat current: this step's W_i goes to the ring when sampled
+        const bool sample = md->shc_lags > 0 && md->shc_step % md->shc_every == 0;
+        const int slot = sample ? (int)(md->shc_samples % md->shc_lags) : 0;
+        float* w_out = sample ? md->shc_ring + (size_t)slot * 9 * n : (drive ? md->w_atom : nullptr);
         Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, st);
         if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
         m->prof.end(ps, st);
@@ -406,16 +566,14 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         aa.ke_factor = kef;
         aa.heat = heat != nullptr;
         ps = m->prof.begin(NEP_PROFILE_ASSEMBLE, st);
-        if ((rc = launch_assemble(aa, nl, n, md->ws.force, drive ? md->w_atom : nullptr, part_a, m->d_err, st, b2,
-                                  c2)))
-            return rc;
+        if ((rc = launch_assemble(aa, nl, n, md->ws.force, w_out, part_a, m->d_err, st, b2, c2))) return rc;
         m->prof.end(ps, st);
         pk = m->prof.begin(NEP_PROFILE_STEP, st);
         const double dof_kb = (3.0 * n - 3.0) * kBoltzmannEv;
         if (drive) {
             // the kick needs the total virial first
             if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
-            k_hnemd_kick<<<nbk, 256, 0, st>>>(n, md->ws.force, md->w_atom, vel, md->fe[0], md->fe[1], md->fe[2],
+            k_hnemd_kick<<<nbk, 256, 0, st>>>(n, md->ws.force, w_out, vel, md->fe[0], md->fe[1], md->fe[2],
                                               md->red + 1, 1.0 / n, hdtm, kef, part_h, m->d_err);
             k_md_finish<<<1, 32 * 5, 0, st>>>(part_e, b1, part_h, nbk, 4, 10, md->red, thermo, heat, md->ctl, md->t0,
                                               md->tau, dt, dof_kb);
@@ -423,6 +581,16 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
             k_md_finish<<<1, 32 * (1 + c2), 0, st>>>(part_e, b1, part_a, b2, c2, 1, md->red, thermo, heat, md->ctl,
                                                      md->t0, md->tau, dt, dof_kb);
         }
+        if (sample) {  // v is that of J: after the second half kick, before the thermostat
+            const int avail = (int)(md->shc_samples + 1 < md->shc_lags ? md->shc_samples + 1 : md->shc_lags);
+            const int chunks = (n + kShcChunk - 1) / kShcChunk;
+            k_shc_corr<<<dim3((avail + kShcLagsPerBlock - 1) / kShcLagsPerBlock, chunks), 32 * kShcLagsPerBlock, 0,
+                         st>>>(n, md->shc_lags, avail, slot, md->shc_ring, vel, md->shc_part);
+            k_shc_reduce<<<(avail * 3 + 127) / 128, 128, 0, st>>>(md->shc_lags, avail, chunks, md->shc_part,
+                                                                   md->shc_sum);
+            ++md->shc_samples;
+        }
+        if (md->shc_lags > 0) ++md->shc_step;
         if (md->tau > 0.0 && n > 1) k_scale_v<<<nbk, 256, 0, st>>>(n, vel, md->red);
         m->prof.end(pk, st);
         if ((rc = cuda_fail(cudaGetLastError(), "md step kernels"))) return rc;

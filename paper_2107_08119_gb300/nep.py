@@ -70,6 +70,9 @@ _SIGNATURES = {
     "snes_step": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, _vp]),
     "snes_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "snes_run": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp]),
+    "nep_md_set_shc": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "nep_md_get_shc": (C.c_int, [_vp, _vp, C.POINTER(C.c_longlong), _vp]),
+    "nep_shc_spectrum": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, C.c_double, C.c_int, _vp, _vp]),
     "nep_dataset_set_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_get_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_tune": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(C.c_float), _vp]),
@@ -288,6 +291,7 @@ class MD:
         out = _vp()
         _check(_lib.nep_md_create(model._h, n, bp, float(mass), C.byref(out)), "nep_md_create")
         self._h = out
+        self._shc_lags = 0
 
     def close(self):
         if getattr(self, "_h", None):
@@ -324,6 +328,20 @@ class MD:
         arr = None if fe is None else _host(fe, np.float64, (3,))
         _check(_lib.nep_md_set_hnemd(self._h, None if arr is None else arr.ctypes.data_as(_vp)),
                "nep_md_set_hnemd")
+
+    def set_shc(self, n_lags: int, every: int = 1):
+        """Accumulate the virial-velocity correlation K(t) over n_lags lags,
+        sampling every `every` steps (0 lags: off).  Resets the sums."""
+        _check(_lib.nep_md_set_shc(self._h, int(n_lags), int(every)), "nep_md_set_shc")
+        self._shc_lags = int(n_lags)
+
+    def shc(self, stream=None):
+        """(K, n_samples): K a CUDA float64 (n_lags, 3) tensor, the correlation
+        averaged over its time origins (eV A/fs)."""
+        K = torch.empty(self._shc_lags, 3, dtype=torch.float64, device="cuda")
+        ns = C.c_longlong()
+        _check(_lib.nep_md_get_shc(self._h, _ptr(K), C.byref(ns), _stream(stream)), "nep_md_get_shc")
+        return K, ns.value
 
     def rebuild_count(self, stream=None) -> int:
         c = C.c_longlong()
@@ -463,6 +481,31 @@ class ForceLoss(torch.autograd.Function):
 def force_loss(z, dataset):
     """L_f(z) on `dataset` as a differentiable torch scalar (float64)."""
     return ForceLoss.apply(z, dataset)
+
+
+def shc_spectrum(K, dt_lag: float, omega, scale: float = 1.0, window: bool = False, stream=None):
+    """The transform of Sec. II.B on the device: scale * 2 * trapezoid of
+    K(t) cos(w t) over the lags (K even in t).  K: CUDA float64 (n_lags, 3);
+    omega: CUDA float64 (n_omega,) in rad per unit of dt_lag."""
+    if not (K.is_cuda and K.dtype == torch.float64 and K.is_contiguous() and omega.is_cuda
+            and omega.dtype == torch.float64 and omega.is_contiguous()):
+        raise ValueError("K and omega must be contiguous CUDA float64 tensors")
+    out = torch.empty(omega.numel(), 3, dtype=torch.float64, device="cuda")
+    _check(_lib.nep_shc_spectrum(_ptr(K), K.shape[0], float(dt_lag), omega.numel(), _ptr(omega), float(scale),
+                                 1 if window else 0, _ptr(out), _stream(stream)), "nep_shc_spectrum")
+    return out
+
+
+def kappa_spectrum(K, dt_lag_fs: float, nu_thz, temperature: float, volume: float, fe: float, window: bool = True):
+    """Spectral thermal conductivity kappa(nu) in W / (m K THz) at frequencies
+    nu (THz, CUDA float64) from K in eV A/fs at lags dt_lag_fs apart, for a
+    driving force fe (1/A) along the direction of interest, temperature (K)
+    and volume (A^3): kappa(w) = (2 / (T V F_e)) int K e^{iwt} dt, with
+    int_0^inf kappa(w) dw / (2 pi) the HNEMD conductivity."""
+    omega = 2.0 * np.pi * nu_thz * 1e-3  # rad/fs
+    # eV / (A fs K) -> W / (m K) is 1.602176634e6; per THz of nu = w / (2 pi): times 1e-3 (fs -> ps)
+    scale = 2.0 / (temperature * volume * fe) * 1.602176634e6 * 1e-3
+    return shc_spectrum(K, dt_lag_fs, omega, scale, window)
 
 
 class SNES:

@@ -1,0 +1,98 @@
+"""The spectral heat current on the GPU (nep_md_set_shc / nep_md_get_shc /
+nep_shc_spectrum) against the oracle: the same HNEMD trajectory of the
+461-atom replica, its sampled per-atom virials and velocities correlated by
+the oracle (orc_shc, pinned in test_oracle_shc.py).
+
+Tolerance: K[tau] is an average of J-like sums W_i . v_i; the heat current
+itself matches the oracle within TOL_W times 1.5 sum |v| (test_gpu_md.py),
+so K gets the same bound."""
+import numpy as np
+import pytest
+
+from gpu_util import f32_exact, soa
+from paper_2107_08119_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+TOL_W = 1e-4
+FE = [2e-3, -1e-3, 5e-4]
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2107_08119_gb300 import build
+    build.build()
+    from paper_2107_08119_gb300 import nep
+    return nep
+
+
+def _run(N, steps, n_lags, every, split=None):
+    import torch
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    model = N.NEP(z)
+    md = N.MD(model, len(pos), box, inputs.MASS_SI)
+    md.set_hnemd(FE)
+    md.set_shc(n_lags, every)
+    p, v = soa(pos), soa(vel)
+    heat = torch.zeros(steps, 3, dtype=torch.float64, device="cuda")
+    for a, b in (split or [(0, steps)]):
+        md.step(p, v, b - a, 1.0, None, heat[a:b])
+    K, ns = md.shc()
+    md.sync_status()
+    out = (K.cpu().numpy(), ns, heat.cpu().numpy())
+    md.close()
+    model.close()
+    return out
+
+
+@pytest.mark.parametrize("every,n_lags", [(1, 8), (3, 5)])
+def test_shc_matches_oracle(N, orc, every, n_lags):
+    steps = 30
+    K, ns, J = _run(N, steps, n_lags, every)
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    _, vo, _, J_o, W_h, v_h = orc.md_record(orc.NepHyper(), f32_exact(z), pos, vel, box, inputs.MASS_SI, 1.0,
+                                           steps, fe=FE)
+    sel = np.arange(0, steps, every)
+    assert ns == len(sel)
+    Ko = orc.shc(W_h[sel], v_h[sel], n_lags) / (len(sel) - np.arange(n_lags))[:, None]
+    vmax = np.abs(vo).sum() * 1.5
+    assert np.abs(K - Ko).max() <= TOL_W * vmax, (np.abs(K - Ko).max(), TOL_W * vmax)
+    # lag 0 is the mean heat current of the sampled steps (the same FP32 terms)
+    assert np.allclose(K[0], J[sel].mean(axis=0), rtol=1e-9, atol=1e-12 * vmax)
+
+
+def test_shc_split_calls_and_fewer_samples_than_lags(N):
+    K1, n1, _ = _run(N, 12, 20, 2)
+    K2, n2, _ = _run(N, 12, 20, 2, split=[(0, 5), (5, 12)])
+    assert n1 == n2 == 6
+    assert np.array_equal(K1, K2)
+    assert np.all(K1[6:] == 0.0) and np.any(K1[5] != 0.0)
+
+
+def test_spectrum_matches_oracle(N, orc):
+    import torch
+    rng = np.random.default_rng(11)
+    K = rng.normal(size=(40, 3))
+    om = np.linspace(0.0, 0.3, 17)
+    for window in (False, True):
+        out = N.shc_spectrum(torch.tensor(K, device="cuda"), 2.0, torch.tensor(om, device="cuda"), 0.5,
+                             window).cpu().numpy()
+        want = orc.shc_spectrum(K, 2.0, om, 0.5, window)
+        assert np.allclose(out, want, rtol=1e-12, atol=1e-12)
+
+
+def test_shc_errors(N):
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    model = N.NEP(z)
+    md = N.MD(model, len(pos), box, inputs.MASS_SI)
+    with pytest.raises(N.NepError):
+        md.shc()                      # not switched on
+    for bad in ((-1, 1), (4, 0)):
+        with pytest.raises(N.NepError) as e:
+            md.set_shc(*bad)
+        assert e.value.code == -1
+    md.set_shc(4, 1)
+    md.set_shc(0)                     # off again
+    with pytest.raises(N.NepError):
+        md.shc()
+    md.close()
+    model.close()
