@@ -394,13 +394,21 @@ typedef struct {
     double* dgA;
 } env;
 
-static void env_fill(const orc_hyper* h, env* E)
+/*
+ * Multicomponent weighting (Sec. II.A, "Multicomponent systems"): the cutoff
+ * function of pair (i, j) becomes f_c(r_ij) sqrt(Z_i Z_j); since g_n and g_n'
+ * are linear in f_c, both are multiplied by w_ij = sqrt(Z_i Z_j).  Zat holds
+ * the Z of every atom of the call (NULL: one species, w = 1); jlist the
+ * neighbours of atom i.
+ */
+static void env_fill(const orc_hyper* h, env* E, const double* Zat, int i, const int* jlist)
 {
     int nR = h->n_max_R + 1, nA = h->n_max_A + 1;
     for (int a = 0; a < E->m; ++a) {
         const double* v = E->r + 3 * a;
         double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         E->rn[a] = r;
+        const double w = Zat ? sqrt(Zat[i] * Zat[jlist[a]]) : 1.0;
         if (r < h->rc_R)
             orc_radial(r, h->rc_R, h->n_max_R, E->gR + a * nR, E->dgR + a * nR);
         else
@@ -409,10 +417,19 @@ static void env_fill(const orc_hyper* h, env* E)
             orc_radial(r, h->rc_A, h->n_max_A, E->gA + a * nA, E->dgA + a * nA);
         else
             for (int n = 0; n < nA; ++n) E->gA[a * nA + n] = E->dgA[a * nA + n] = 0.0;
+        for (int n = 0; n < nR; ++n) {
+            E->gR[a * nR + n] *= w;
+            E->dgR[a * nR + n] *= w;
+        }
+        for (int n = 0; n < nA; ++n) {
+            E->gA[a * nA + n] *= w;
+            E->dgA[a * nA + n] *= w;
+        }
     }
 }
 
-static void env_alloc(const orc_hyper* h, env* E, int m, const double* r)
+static void env_alloc(const orc_hyper* h, env* E, int m, const double* r, const double* Zat, int i,
+                      const int* jlist)
 {
     int nR = h->n_max_R + 1, nA = h->n_max_A + 1;
     int mm = m > 0 ? m : 1;
@@ -423,7 +440,7 @@ static void env_alloc(const orc_hyper* h, env* E, int m, const double* r)
     E->dgR = (double*)malloc(sizeof(double) * mm * nR);
     E->gA = (double*)malloc(sizeof(double) * mm * nA);
     E->dgA = (double*)malloc(sizeof(double) * mm * nA);
-    env_fill(h, E);
+    env_fill(h, E, Zat, i, jlist);
 }
 
 static void env_free(env* E)
@@ -550,6 +567,12 @@ static int check_hyper(const orc_hyper* h)
 
 int orc_descriptors(const orc_hyper* h, int n, const double* box, const double* pos, double* q)
 {
+    return orc_descriptors_z(h, n, box, pos, NULL, q);
+}
+
+/* orc_descriptors with per-atom atomic numbers Zat (n), the multicomponent weighting */
+int orc_descriptors_z(const orc_hyper* h, int n, const double* box, const double* pos, const double* Zat, double* q)
+{
     int rcode = check_hyper(h);
     if (rcode) return rcode;
     nlist L;
@@ -559,7 +582,7 @@ int orc_descriptors(const orc_hyper* h, int n, const double* box, const double* 
 #pragma omp parallel for schedule(dynamic, 16)
     for (int i = 0; i < n; ++i) {
         env E;
-        env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i]);
+        env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i], Zat, i, L.j + L.start[i]);
         descriptor(h, &E, q + (size_t)i * nd);
         env_free(&E);
     }
@@ -576,8 +599,8 @@ int orc_descriptors(const orc_hyper* h, int n, const double* box, const double* 
  * x (n x n_neu) are optional intermediate outputs.
  */
 static int efv_impl(const orc_hyper* h, const double* z, int n, const double* box, const double* pos,
-                    int nlist_method, double* U, double* F, double* W, double* q_out, double* G_out,
-                    double* x_out)
+                    int nlist_method, const double* Zat, double* U, double* F, double* W, double* q_out,
+                    double* G_out, double* x_out)
 {
     int rcode = check_hyper(h);
     if (rcode) return rcode;
@@ -597,7 +620,7 @@ static int efv_impl(const orc_hyper* h, const double* z, int n, const double* bo
 #pragma omp for schedule(dynamic, 16)
         for (int i = 0; i < n; ++i) {
             env E;
-            env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i]);
+            env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i], Zat, i, L.j + L.start[i]);
             descriptor(h, &E, q);
             double Ui = network(h, z, q, x, G);
             if (U) U[i] = Ui;
@@ -639,19 +662,26 @@ static int efv_impl(const orc_hyper* h, const double* z, int n, const double* bo
 int orc_efv(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, double* U, double* F,
             double* W)
 {
-    return efv_impl(h, z, n, box, pos, 2, U, F, W, NULL, NULL, NULL);
+    return efv_impl(h, z, n, box, pos, 2, NULL, U, F, W, NULL, NULL, NULL);
+}
+
+/* orc_efv with per-atom atomic numbers Zat (n), the multicomponent weighting */
+int orc_efv_z(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, const double* Zat,
+              double* U, double* F, double* W)
+{
+    return efv_impl(h, z, n, box, pos, 2, Zat, U, F, W, NULL, NULL, NULL);
 }
 
 int orc_efv_brute(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, double* U,
                   double* F, double* W)
 {
-    return efv_impl(h, z, n, box, pos, 0, U, F, W, NULL, NULL, NULL);
+    return efv_impl(h, z, n, box, pos, 0, NULL, U, F, W, NULL, NULL, NULL);
 }
 
 int orc_site(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, double* q,
              double* G, double* x)
 {
-    return efv_impl(h, z, n, box, pos, 2, NULL, NULL, NULL, q, G, x);
+    return efv_impl(h, z, n, box, pos, 2, NULL, NULL, NULL, NULL, q, G, x);
 }
 
 /*
@@ -663,6 +693,7 @@ int orc_site(const orc_hyper* h, const double* z, int n, const double* box, cons
 int orc_efv_sample(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, int n_sample,
                    const int* idx, double* U, double* F, double* W)
 {
+    const double* Zat = NULL; /* one species */
     int rcode = check_hyper(h);
     if (rcode) return rcode;
     nlist L;
@@ -693,7 +724,7 @@ int orc_efv_sample(const orc_hyper* h, const double* z, int n, const double* box
         for (int i = 0; i < n; ++i) {
             if (!need[i]) continue;
             env E;
-            env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i]);
+            env_alloc(h, &E, L.start[i + 1] - L.start[i], L.r + 3 * (size_t)L.start[i], Zat, i, L.j + L.start[i]);
             descriptor(h, &E, q);
             Ua[i] = network(h, z, q, x, G);
             for (int a = 0; a < E.m; ++a) partial_force(h, &E, a, G, Jb, p + 3 * ((size_t)L.start[i] + a));
@@ -814,17 +845,18 @@ int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, do
                double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
                double* J)
 {
-    return orc_md_record(h, z, n, box, pos, vel, mass, dt, n_steps, t0, tau, fe, thermo, J, NULL, NULL);
+    return orc_md_record(h, z, n, box, pos, vel, mass, dt, n_steps, t0, tau, fe, NULL, thermo, J, NULL, NULL);
 }
 
 /*
  * orc_md_ext that also records, for every step s, the per-atom virials W_i
  * (n x 9) and velocities v_i (n x 3) from which J(s) is taken (after the
- * second half kick, before the thermostat): W_hist[s], v_hist[s].
+ * second half kick, before the thermostat): W_hist[s], v_hist[s].  Zat: the
+ * atomic number of every atom (multicomponent weighting), or NULL.
  */
 int orc_md_record(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
-                  double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
-                  double* J, double* W_hist, double* v_hist)
+                  double mass, double dt, int n_steps, double t0, double tau, const double* fe, const double* Zat,
+                  double* thermo, double* J, double* W_hist, double* v_hist)
 {
     const double conv = amu_a2_fs2_in_ev();
     const double kb = 8.617333262e-5; /* eV/K, CODATA 2018 */
@@ -832,7 +864,7 @@ int orc_md_record(const orc_hyper* h, const double* z, int n, const double* box,
     double* F = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     double* W = (double*)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
     const int drive = fe && (fe[0] != 0.0 || fe[1] != 0.0 || fe[2] != 0.0);
-    int rcode = orc_efv(h, z, n, box, pos, U, F, W);
+    int rcode = orc_efv_z(h, z, n, box, pos, Zat, U, F, W);
     const double acc = dt * 0.5 / (mass * conv);
     for (int s = -1; s < n_steps && !rcode; ++s) {
         if (s >= 0) {
@@ -840,7 +872,7 @@ int orc_md_record(const orc_hyper* h, const double* z, int n, const double* box,
                 vel[k] += acc * F[k];
                 pos[k] += dt * vel[k];
             }
-            rcode = orc_efv(h, z, n, box, pos, U, F, W);
+            rcode = orc_efv_z(h, z, n, box, pos, Zat, U, F, W);
             if (rcode) break;
         }
         if (drive) {
@@ -954,6 +986,14 @@ int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_ato
              const double* pos, const double* e_tar, const double* f_tar, const double* w_tar,
              const double* lambdas, double* out)
 {
+    return orc_loss_z(h, z, n_struct, n_atoms, boxes, pos, NULL, e_tar, f_tar, w_tar, lambdas, out);
+}
+
+/* orc_loss with the atomic number of every atom of the set (Zat, concatenated like pos) */
+int orc_loss_z(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms, const double* boxes,
+               const double* pos, const double* Zat, const double* e_tar, const double* f_tar,
+               const double* w_tar, const double* lambdas, double* out)
+{
     int npar = orc_n_par(h);
     double se = 0.0, sf = 0.0, sv = 0.0;
     long ntot = 0;
@@ -964,7 +1004,7 @@ int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_ato
         double* U = (double*)malloc(sizeof(double) * na);
         double* F = (double*)malloc(sizeof(double) * 3 * na);
         double* W = (double*)malloc(sizeof(double) * 9 * na);
-        rcode = orc_efv(h, z, na, boxes + 9 * s, pos + 3 * off, U, F, W);
+        rcode = orc_efv_z(h, z, na, boxes + 9 * s, pos + 3 * off, Zat ? Zat + off : NULL, U, F, W);
         if (!rcode) {
             double E = 0.0, Wt[9] = {0};
             for (int i = 0; i < na; ++i) {
@@ -1020,6 +1060,14 @@ int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_ato
 int orc_force_loss_grad(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms,
                         const double* boxes, const double* pos, const double* f_tar, double* grad, double* lf)
 {
+    return orc_force_loss_grad_z(h, z, n_struct, n_atoms, boxes, pos, NULL, f_tar, grad, lf);
+}
+
+/* orc_force_loss_grad with the atomic number of every atom (Zat, concatenated like pos) */
+int orc_force_loss_grad_z(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms,
+                          const double* boxes, const double* pos, const double* Zat, const double* f_tar,
+                          double* grad, double* lf)
+{
     int rcode = check_hyper(h);
     if (rcode) return rcode;
     int nd = orc_n_des(h), nh = h->n_neu, npar = orc_n_par(h);
@@ -1032,7 +1080,8 @@ int orc_force_loss_grad(const orc_hyper* h, const double* z, int n_struct, const
     double* Fall = (double*)malloc(sizeof(double) * 3 * (size_t)(ntot > 0 ? ntot : 1));
     size_t off = 0;
     for (int s = 0; s < n_struct; ++s) {
-        rcode = orc_efv(h, z, n_atoms[s], boxes + 9 * s, pos + 3 * off, NULL, Fall + 3 * off, NULL);
+        rcode = orc_efv_z(h, z, n_atoms[s], boxes + 9 * s, pos + 3 * off, Zat ? Zat + off : NULL, NULL,
+                          Fall + 3 * off, NULL);
         if (rcode) {
             free(Fall);
             return rcode;
@@ -1067,7 +1116,8 @@ int orc_force_loss_grad(const orc_hyper* h, const double* z, int n_struct, const
 #pragma omp for schedule(dynamic, 8)
             for (int i = 0; i < na; ++i) {
                 env E;
-                env_alloc(h, &E, Lst.start[i + 1] - Lst.start[i], Lst.r + 3 * (size_t)Lst.start[i]);
+                env_alloc(h, &E, Lst.start[i + 1] - Lst.start[i], Lst.r + 3 * (size_t)Lst.start[i],
+                          Zat ? Zat + off : NULL, i, Lst.j + Lst.start[i]);
                 descriptor(h, &E, q);
                 network(h, z, q, x, NULL);
                 for (int v = 0; v < nd; ++v) lam[v] = 0.0;

@@ -50,8 +50,18 @@ int orc_md_ext(const orc_hyper* h, const double* z, int n, const double* box, do
                double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
                double* J);
 int orc_md_record(const orc_hyper* h, const double* z, int n, const double* box, double* pos, double* vel,
-                  double mass, double dt, int n_steps, double t0, double tau, const double* fe, double* thermo,
-                  double* J, double* W_hist, double* v_hist);
+                  double mass, double dt, int n_steps, double t0, double tau, const double* fe, const double* Zat,
+                  double* thermo, double* J, double* W_hist, double* v_hist);
+/* multicomponent weighting: Zat = atomic number of every atom (NULL: one species) */
+int orc_descriptors_z(const orc_hyper* h, int n, const double* box, const double* pos, const double* Zat, double* q);
+int orc_efv_z(const orc_hyper* h, const double* z, int n, const double* box, const double* pos, const double* Zat,
+              double* U, double* F, double* W);
+int orc_loss_z(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms, const double* boxes,
+               const double* pos, const double* Zat, const double* e_tar, const double* f_tar,
+               const double* w_tar, const double* lambdas, double* out);
+int orc_force_loss_grad_z(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms,
+                          const double* boxes, const double* pos, const double* Zat, const double* f_tar,
+                          double* grad, double* lf);
 void orc_shc(int n, int n_samples, int n_lags, const double* W_hist, const double* v_hist, double* K_sum);
 void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, const double* omega, double scale,
                       int window, double* out);

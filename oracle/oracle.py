@@ -86,7 +86,11 @@ def _load():
             "orc_md_ext": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int, C.c_double,
                                      C.c_double, _D, _D, _D]),
             "orc_md_record": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, C.c_double, C.c_double, C.c_int,
-                                        C.c_double, C.c_double, _D, _D, _D, _D, _D]),
+                                        C.c_double, C.c_double, _D, _D, _D, _D, _D, _D]),
+            "orc_descriptors_z": (C.c_int, [_H, C.c_int, _D, _D, _D, _D]),
+            "orc_efv_z": (C.c_int, [_H, _D, C.c_int, _D, _D, _D, _D, _D, _D]),
+            "orc_loss_z": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D, _D]),
+            "orc_force_loss_grad_z": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D]),
             "orc_shc": (None, [C.c_int, C.c_int, C.c_int, _D, _D, _D]),
             "orc_shc_spectrum": (None, [C.c_int, _D, C.c_double, C.c_int, _D, C.c_double, C.c_int, _D]),
             "orc_loss": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D]),
@@ -172,16 +176,25 @@ def neighbors(pos, box, rc: float, method: int = 2, cap: int = 512):
     return cnt, js, rs
 
 
-def descriptors(h: NepHyper, pos, box):
+def _zat(Z, n):
+    """Per-atom atomic numbers (multicomponent weighting), or None."""
+    return None if Z is None else _f64(Z, (n,))
+
+
+def descriptors(h: NepHyper, pos, box, Z=None):
+    """q (n, N_des); Z: the atomic number of every atom (multicomponent
+    weighting f_c -> f_c sqrt(Z_i Z_j)) or None for one species."""
     pos = _f64(pos, (-1, 3))
     box = _f64(box, (3, 3))
     q = np.zeros((pos.shape[0], n_des(h)))
-    _check(_load().orc_descriptors(C.byref(h.c()), pos.shape[0], _d(box), _d(pos), _d(q)), "descriptors")
+    Za = _zat(Z, pos.shape[0])
+    _check(_load().orc_descriptors_z(C.byref(h.c()), pos.shape[0], _d(box), _d(pos), _d(Za), _d(q)), "descriptors")
     return q
 
 
-def efv(h: NepHyper, z, pos, box, brute: bool = False):
-    """Site energies U (n), forces F (n, 3), per-atom virials W (n, 3, 3)."""
+def efv(h: NepHyper, z, pos, box, brute: bool = False, Z=None):
+    """Site energies U (n), forces F (n, 3), per-atom virials W (n, 3, 3);
+    Z: per-atom atomic numbers (multicomponent weighting) or None."""
     z = _f64(z)
     assert z.size == n_par(h)
     pos = _f64(pos, (-1, 3))
@@ -190,6 +203,11 @@ def efv(h: NepHyper, z, pos, box, brute: bool = False):
     U = np.zeros(n)
     F = np.zeros((n, 3))
     W = np.zeros((n, 3, 3))
+    if Z is not None:
+        assert not brute
+        Za = _zat(Z, n)
+        _check(_load().orc_efv_z(C.byref(h.c()), _d(z), n, _d(box), _d(pos), _d(Za), _d(U), _d(F), _d(W)), "efv")
+        return U, F, W
     fn = _load().orc_efv_brute if brute else _load().orc_efv
     _check(fn(C.byref(h.c()), _d(z), n, _d(box), _d(pos), _d(U), _d(F), _d(W)), "efv")
     return U, F, W
@@ -264,7 +282,7 @@ def md_ext(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: int, 
 
 
 def md_record(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: int, t0: float = 0.0,
-              tau: float = 0.0, fe=None):
+              tau: float = 0.0, fe=None, Z=None):
     """md_ext that also returns, per step, the per-atom virials W_i
     (n_steps, n, 3, 3) and velocities (n_steps, n, 3) from which J is taken."""
     z = _f64(z)
@@ -278,8 +296,8 @@ def md_record(h: NepHyper, z, pos, vel, box, mass: float, dt: float, n_steps: in
     vh = np.zeros((n_steps, n, 3))
     fe_arr = None if fe is None else _f64(fe, (3,))
     _check(_load().orc_md_record(C.byref(h.c()), _d(z), n, _d(box), _d(pos), _d(vel), float(mass), float(dt),
-                                 n_steps, float(t0), float(tau), None if fe_arr is None else _d(fe_arr), _d(thermo),
-                                 _d(J), _d(Wh), _d(vh)), "md_record")
+                                 n_steps, float(t0), float(tau), None if fe_arr is None else _d(fe_arr),
+                                 _d(_zat(Z, n)), _d(thermo), _d(J), _d(Wh), _d(vh)), "md_record")
     return pos, vel, thermo, J, Wh.reshape(n_steps, n, 3, 3), vh
 
 
@@ -313,7 +331,7 @@ def _dataset_arrays(structures):
     return n_atoms, boxes, pos
 
 
-def loss(h: NepHyper, z, structures, e_tar, f_tar, w_tar, lambdas=(1.0, 1.0, 1.0, 0.05, 0.05)):
+def loss(h: NepHyper, z, structures, e_tar, f_tar, w_tar, lambdas=(1.0, 1.0, 1.0, 0.05, 0.05), Z=None):
     """(L, L_e, L_f, L_v, L_1, L_2) of Eqs. 29-34 over a list of structures
     (dicts with "pos" (n, 3) and "box" (3, 3)); e_tar per structure, f_tar
     concatenated (N, 3), w_tar (n_struct, 6) in the order xx yy zz xy yz zx."""
@@ -324,20 +342,23 @@ def loss(h: NepHyper, z, structures, e_tar, f_tar, w_tar, lambdas=(1.0, 1.0, 1.0
     w_tar = _f64(w_tar, (-1, 6))
     lam = _f64(lambdas)
     out = np.zeros(6)
-    _check(_load().orc_loss(C.byref(h.c()), _d(z), len(structures), n_atoms.ctypes.data_as(_I), _d(boxes), _d(pos),
-                            _d(e_tar), _d(f_tar), _d(w_tar), _d(lam), _d(out)), "loss")
+    Za = _zat(Z, pos.shape[0])
+    _check(_load().orc_loss_z(C.byref(h.c()), _d(z), len(structures), n_atoms.ctypes.data_as(_I), _d(boxes),
+                              _d(pos), _d(Za), _d(e_tar), _d(f_tar), _d(w_tar), _d(lam), _d(out)), "loss")
     return out
 
 
-def force_loss_grad(h: NepHyper, z, structures, f_tar):
+def force_loss_grad(h: NepHyper, z, structures, f_tar, Z=None):
     """(dL_f/dz, L_f) by the analytic chain rule through the partial forces."""
     z = _f64(z)
     n_atoms, boxes, pos = _dataset_arrays(structures)
     f_tar = _f64(f_tar, (-1, 3))
     grad = np.zeros(z.size)
     lf = C.c_double()
-    _check(_load().orc_force_loss_grad(C.byref(h.c()), _d(z), len(structures), n_atoms.ctypes.data_as(_I), _d(boxes),
-                                       _d(pos), _d(f_tar), _d(grad), C.byref(lf)), "force_loss_grad")
+    Za = _zat(Z, pos.shape[0])
+    _check(_load().orc_force_loss_grad_z(C.byref(h.c()), _d(z), len(structures), n_atoms.ctypes.data_as(_I),
+                                         _d(boxes), _d(pos), _d(Za), _d(f_tar), _d(grad), C.byref(lf)),
+           "force_loss_grad")
     return grad, lf.value
 
 
