@@ -177,6 +177,20 @@ int nep_md_invalidate(nep_md* md);
 int nep_md_set_thermostat(nep_md* md, double t0, double tau);
 
 /*
+ * nep_set_species -- multicomponent systems (Sec. II.A): the cutoff function
+ * of pair (i, j) becomes f_c(r_ij) sqrt(Z_i Z_j), so every g_n and g_n' of
+ * the pair is multiplied by sqrt(Z_i Z_j) (one species: weight 1, the default).
+ *   n       atoms of the configurations that follow (0: back to one species).
+ *   z_atom  host [n] species numbers (atomic numbers, > 0).
+ * Later nep_compute_efv calls and MD handles created afterwards for n atoms
+ * use them (a call for another atom count fails with NEP_ERR_ARG); the plain
+ * comparator (nep_compute_efv_plain) and nep_compute_efv_static stay one
+ * species.  Synchronises the device.
+ * Errors: NEP_ERR_ARG (NULL, non-positive Z), NEP_ERR_OOM, NEP_ERR_CUDA.
+ */
+int nep_set_species(nep_model* m, int n, const double* z_atom);
+
+/*
  * nep_md_set_hnemd -- homogeneous non-equilibrium MD driving (Sec. II.B):
  * every atom feels F_i^ext = F_e . W_i, (F_i^ext)^b = sum_a F_e^a W_i^{ab},
  * minus its mean over all atoms so that the total momentum is kept; then
@@ -263,6 +277,11 @@ int nep_get_neighbors(nep_model* m, int n, int* count, int* nbr, void* stream);
 typedef struct nep_dataset nep_dataset;
 int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const double* boxes, const double* pos,
                        const double* e_tar, const double* f_tar, const double* w_tar, nep_dataset** out);
+/* nep_dataset_create for a multicomponent set: z_atom host [N] species
+ * numbers (atomic numbers, > 0; NULL = one species), see nep_set_species. */
+int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, const double* boxes,
+                               const double* pos, const double* z_atom, const double* e_tar, const double* f_tar,
+                               const double* w_tar, nep_dataset** out);
 int nep_dataset_destroy(nep_dataset* ds);
 /* Atoms, stored pairs and device bytes of a training set; pointers may be NULL. */
 int nep_dataset_info(const nep_dataset* ds, int* n_atoms, long long* n_pairs, long long* device_bytes);

@@ -178,11 +178,12 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_lambda(int N, const int* __
 
     float hi[3], li[3];
     load_pos(xh, xl, N, ia, hi, li);
+    const float zi = load_z(xh, ia);
     float lam[kNdes];
     {
         float q[kNdes];
         Harm S;
-        site_descriptors(ia, N, cnt, T, xh, xl, box, P, hi, li, q, S);
+        site_descriptors(ia, N, cnt, T, xh, xl, box, P, hi, li, zi, q, S);
 #pragma unroll
         for (int v = 0; v < kNdes; ++v) row[kNdes + v] = q[v];
         // A_nlm = 2 c_lm S_nlm
@@ -208,15 +209,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_lambda(int N, const int* __
             const float inv = 1.f / d;
             const float u[3] = {r[0] * inv, r[1] * inv, r[2] * inv};
             const float e = fmaf(u[0], dd[0], fmaf(u[1], dd[1], u[2] * dd[2]));
+            const float wz = pair_weight(P, zi, load_z(xh, j));
             if (d2 < P.rcR2) {
                 float g[kNR], dg[kNR];
-                radial_g_dg<kNR>(d, P.rcR, P.inv_rcR, g, dg);
+                radial_g_dg<kNR>(d, P.rcR, P.inv_rcR, g, dg, wz);
 #pragma unroll
                 for (int a = 0; a < kNR; ++a) lam[a] = fmaf(dg[a], e, lam[a]);
             }
             if (d2 < P.rcA2) {
                 float g[kNA], dg[kNA];
-                radial_g_dg<kNA>(d, P.rcA, P.inv_rcA, g, dg);
+                radial_g_dg<kNA>(d, P.rcA, P.inv_rcA, g, dg, wz);
                 const float tx = fmaf(-e, u[0], dd[0]) * inv, ty = fmaf(-e, u[1], dd[1]) * inv,
                             tz = fmaf(-e, u[2], dd[2]) * inv;
                 adj_pass(u[0], u[1], u[2], S, g, dg, e, tx, ty, tz, lam);
@@ -317,9 +319,10 @@ int ensure_adjoint(nep_model* m, nep_dataset* ds)
     return NEP_OK;
 }
 
-SiteParams site_params(const nep_model* m)
+SiteParams site_params(const nep_model* m, int typed)
 {
     SiteParams P;
+    P.typed = typed;
     P.w = nullptr;
     P.n_neu = m->hp.n_neu;
     P.rcR = (float)m->hp.rc_R;
@@ -365,7 +368,7 @@ int nep_force_loss(nep_model* m, nep_dataset* ds, const float* z, double* loss_f
     if (rc) return rc;
     const size_t smem = (size_t)pad32(n_par) * sizeof(float);
     k_adj_site<<<nb, kAdjThreads, smem, st>>>(N, ds->sid, ds->boxes, ds->xh, ds->xl, ds->pstart, ds->pj, a.z, n_par,
-                                              site_params(m), a.pf, m->d_err);
+                                              site_params(m, ds->typed), a.pf, m->d_err);
     k_adj_force<<<nb, kAdjThreads, 0, st>>>(N, ds->pstart, ds->rev, a.pf, ds->f_tar, reinterpret_cast<float4*>(a.res),
                                             a.part, m->d_err);
     k_adj_loss<<<1, 256, 0, st>>>(nb, N, a.part, a.sums, loss_f);
@@ -394,7 +397,7 @@ int nep_force_loss_backward(nep_model* m, nep_dataset* ds, const double* seed, d
     if (rc) return rc;
     k_adj_lambda<<<nb, kAdjThreads, smem, st>>>(N, ds->sid, ds->boxes, ds->xh, ds->xl, ds->pstart, ds->pj,
                                                 reinterpret_cast<const float4*>(a.res), a.sums, a.z, n_par,
-                                                site_params(m), a.part);
+                                                site_params(m, ds->typed), a.part);
     k_adj_grad<<<blocks_for(n_par, 256), 256, 0, st>>>(nb, n_par, a.part, seed, grad);
     return cuda_fail(cudaGetLastError(), "force-loss adjoint kernels");
 }

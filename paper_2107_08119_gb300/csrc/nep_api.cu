@@ -1,6 +1,7 @@
 // nep_api.cu -- the C ABI of include/nep.h: argument checks, handles,
 // device scratch, and the single-configuration entry points.
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -349,7 +350,37 @@ int nep_destroy(nep_model* m)
     dev_free(m->d_z);
     dev_free(m->d_err);
     dev_free(m->d_red);
+    dev_free(m->zatom);
     delete m;
+    return NEP_OK;
+}
+
+int nep_set_species(nep_model* m, int n, const double* z_atom)
+{
+    if (!m || n < 0 || n > kMaxAtoms || (n > 0 && !z_atom)) {
+        set_error("nep_set_species: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    std::vector<float> zf((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (!(z_atom[i] > 0.0) || !std::isfinite(z_atom[i])) {
+            set_error("nep_set_species: the species number of atom %d is not positive", i);
+            return NEP_ERR_ARG;
+        }
+        zf[(size_t)i] = (float)z_atom[i];
+    }
+    cudaDeviceSynchronize();
+    dev_free(m->zatom);
+    m->zatom_n = 0;
+    if (n == 0) return NEP_OK;
+    int rc = dev_alloc(&m->zatom, (size_t)n, "species numbers");
+    if (rc) return rc;
+    if ((rc = cuda_fail(cudaMemcpy(m->zatom, zf.data(), sizeof(float) * (size_t)n, cudaMemcpyHostToDevice),
+                        "species upload"))) {
+        dev_free(m->zatom);
+        return rc;
+    }
+    m->zatom_n = n;
     return NEP_OK;
 }
 
@@ -379,6 +410,14 @@ int compute_efv(nep_model* m, int n, const double* box9, const double* pos, doub
         set_error("nep_compute_efv: bad arguments (handle, positions, 1 <= n < 2^24)");
         return NEP_ERR_ARG;
     }
+    if (m->zatom && n != m->zatom_n) {
+        set_error("nep_compute_efv: species were set for %d atoms, not %d (nep_set_species)", m->zatom_n, n);
+        return NEP_ERR_ARG;
+    }
+    if (m->zatom && plain) {
+        set_error("nep_compute_efv_plain: the plain comparator has one species only");
+        return NEP_ERR_UNSUPPORTED;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const double rmax = m->hp.rc_R > m->hp.rc_A ? m->hp.rc_R : m->hp.rc_A;
     Box box;
@@ -389,11 +428,12 @@ int compute_efv(nep_model* m, int n, const double* box9, const double* pos, doub
     if ((rc = ensure_workspace(m->ws, n, m->hp.max_neighbors, ncell, nblocks))) return rc;
     NeighborList& nl = m->ws.nl;
     Profiler::Slot* pn = m->prof.begin(NEP_PROFILE_NEIGHBOR, st);
-    if ((rc = build_neighbor_list(nl, box, n, const_cast<double*>(pos), false, nullptr, (float)rmax, m->d_err,
-                                  nullptr, st)))
+    if ((rc = build_neighbor_list(nl, box, n, const_cast<double*>(pos), m->zatom, false, nullptr, (float)rmax,
+                                  m->d_err, nullptr, st)))
         return rc;
     m->prof.end(pn, st);
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, box};
+    fa.typed = m->zatom != nullptr;
     // partial sums: energies in [0, nblocks), assembly totals after them
     double* part_e = m->ws.partials;
     double* part_v = m->ws.partials + ((nblocks + 7) / 8) * 8;

@@ -57,6 +57,7 @@ struct nep_dataset {
     int* sstart = nullptr;
     int* s_natoms = nullptr;
     double* s_inv_na = nullptr;  // 1 / atoms of each structure
+    int typed = 0;               // species numbers given (multicomponent weighting)
     int* s_chunk0 = nullptr;
     int* chunk_begin = nullptr;
     int* chunk_end = nullptr;

@@ -154,6 +154,7 @@ int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, doub
     P.rcA2 = a.rcA * a.rcA;
     P.inv_rcR = 1.f / a.rcR;
     P.inv_rcA = 1.f / a.rcA;
+    P.typed = a.typed;
     const int n_par = (kNdes + 2) * a.n_neu + 1;
     nblocks = blocks_for(n, kSiteThreads);
     const size_t smem = (((size_t)n_par + 31) / 32 * 32 + (size_t)kStageSlots * kSiteThreads) * sizeof(float);

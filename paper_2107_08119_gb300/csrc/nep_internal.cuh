@@ -142,12 +142,20 @@ __host__ __device__ __forceinline__ void split_hilo(double x, float& h, float& l
     l = (float)(x - (double)h);
 }
 
-__host__ __device__ __forceinline__ void store_pos(float* __restrict__ xh, float* __restrict__ xl, int i, const double (&x)[3])
+// The hi record's fourth word carries the atom's species number Z (1 for a
+// single species): the multicomponent weighting f_c -> f_c sqrt(Z_i Z_j).
+__host__ __device__ __forceinline__ void store_pos(float* __restrict__ xh, float* __restrict__ xl, int i, const double (&x)[3],
+                                                  float zi = 1.f)
 {
     float h[3], l[3];
     for (int d = 0; d < 3; ++d) split_hilo(x[d], h[d], l[d]);
-    reinterpret_cast<float4*>(xh)[i] = make_float4(h[0], h[1], h[2], 0.f);
+    reinterpret_cast<float4*>(xh)[i] = make_float4(h[0], h[1], h[2], zi);
     reinterpret_cast<float4*>(xl)[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+__host__ __device__ __forceinline__ float load_z(const float* __restrict__ xh, int i)
+{
+    return reinterpret_cast<const float4*>(xh)[i].w;
 }
 
 // Warp sum of K <= 16 doubles held by every lane.  Each butterfly level keeps
@@ -261,7 +269,9 @@ int setup_box(const double* box9, double r_list, Box& b);
 // neighbour list (nep_neighbor.cu)
 // mode: build from positions `pos` (FP64 [3][n]); when wrap_in_place is true
 // the wrapped positions are written back to pos and to x_ref (if non-null).
-int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool wrap_in_place, double* x_ref,
+// zatom: species number of every atom (dev [n]) or NULL (all 1)
+int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, const float* zatom, bool wrap_in_place,
+                        double* x_ref,
                         float r_list, unsigned* d_err, const unsigned* d_gate, cudaStream_t st);
 
 // force path (nep_force.cu)
@@ -270,6 +280,7 @@ struct ForceArgs {
     int n_neu;
     float rcR, rcA;
     Box box;
+    int typed = 0;           // species numbers in the position records are used (multicomponent)
 };
 // the site pass runs kSiteAtomsPerBlock atoms per block; its per-block
 // energy partials need site_blocks(n) slots, which also bounds the block
@@ -333,6 +344,8 @@ struct nep_model {
     unsigned* d_err = nullptr;   // latched device error bits
     double* d_red = nullptr;     // reduction outputs (32 doubles)
     nep::Workspace ws;
+    float* zatom = nullptr;      // species numbers of the atoms (nep_set_species), or NULL
+    int zatom_n = 0;
 };
 
 namespace nep {

@@ -61,7 +61,7 @@ __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__
             const double d = xc - x_ref[o];
             dd += d * d;
         }
-        store_pos(xh, xl, i, xn);
+        store_pos(xh, xl, i, xn, load_z(xh, i));  // the species number stays
         d2 = (float)dd;
     }
     // block maximum, then one atomic per block (one per warp serialised
@@ -297,6 +297,12 @@ struct nep_md {
 };
 
 namespace {
+// the model's species numbers when they were set for this many atoms
+const float* md_zatom(const nep_md* md)
+{
+    return md->m->zatom && md->m->zatom_n == md->n ? md->m->zatom : nullptr;
+}
+
 void free_shc(nep_md* md)
 {
     if (md->shc_ring) cudaFree(md->shc_ring);
@@ -504,6 +510,11 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     const int nbk = blocks_for(n, 256);
     const double kef = 0.5 * md->mass * kAmuA2Fs2InEv;
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, md->box};
+    fa.typed = md_zatom(md) != nullptr;
+    if (m->zatom && !fa.typed) {
+        set_error("nep_md_step: species were set for %d atoms, not %d", m->zatom_n, n);
+        return NEP_ERR_ARG;
+    }
     const double rmax = m->hp.rc_R > m->hp.rc_A ? m->hp.rc_R : m->hp.rc_A;
     const double conv = kAmuA2Fs2InEv;
     int rc;
@@ -515,7 +526,7 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
 
     if (md->need_init) {
         // forces of the starting configuration (list built unconditionally)
-        if ((rc = build_neighbor_list(nl, md->box, n, pos, true, md->x_ref, md->r_list, m->d_err, nullptr, st)))
+        if ((rc = build_neighbor_list(nl, md->box, n, pos, md_zatom(md), true, md->x_ref, md->r_list, m->d_err, nullptr, st)))
             return rc;
         int b1 = 0, b2 = 0, c2 = 0;
         if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
@@ -547,7 +558,7 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         k_decide<<<1, 1, 0, st>>>(md->ctl, thresh * thresh, md->rebuilds);
         m->prof.end(pk, st);
         pk = m->prof.begin(NEP_PROFILE_NEIGHBOR, st);
-        if ((rc = build_neighbor_list(nl, md->box, n, pos, true, md->x_ref, md->r_list, m->d_err, gate, st)))
+        if ((rc = build_neighbor_list(nl, md->box, n, pos, md_zatom(md), true, md->x_ref, md->r_list, m->d_err, gate, st)))
             return rc;
         m->prof.end(pk, st);
         int b1 = 0, b2 = 0, c2 = 0;

@@ -34,9 +34,9 @@ __device__ __forceinline__ bool gated_off(const unsigned* gate)
     return gate != nullptr && *((volatile const unsigned*)gate) == 0u;
 }
 
-__global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double* __restrict__ x_ref,
-                      float* __restrict__ xh, float* __restrict__ xl, int* __restrict__ atom_cell,
-                      int* __restrict__ cell_count, Box b, const unsigned* gate)
+__global__ void k_bin(int n, double* __restrict__ pos, const float* __restrict__ zatom, int wrap_in_place,
+                      double* __restrict__ x_ref, float* __restrict__ xh, float* __restrict__ xl,
+                      int* __restrict__ atom_cell, int* __restrict__ cell_count, Box b, const unsigned* gate)
 {
     if (gated_off(gate)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,7 +72,7 @@ __global__ void k_bin(int n, double* __restrict__ pos, int wrap_in_place, double
             c[d] = ci < 0 ? 0 : (ci >= b.nc[d] ? b.nc[d] - 1 : ci);
         }
     }
-    store_pos(xh, xl, i, wx);
+    store_pos(xh, xl, i, wx, zatom ? zatom[i] : 1.f);
     if (b.nc[0] > 0) {
         const int cid = (c[0] * b.nc[1] + c[1]) * b.nc[2] + c[2];
         atom_cell[i] = cid;
@@ -460,14 +460,15 @@ constexpr int kListGridCap = 152 * 16;
 
 }  // namespace
 
-int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, bool wrap_in_place, double* x_ref,
+int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, const float* zatom, bool wrap_in_place,
+                        double* x_ref,
                         float r_list, unsigned* d_err, const unsigned* d_gate, cudaStream_t st)
 {
     const int T = 256;
     const float rv2 = r_list * r_list;
     const bool cells = b.nc[0] > 0;
     const int ncell = cells ? b.nc[0] * b.nc[1] * b.nc[2] : 0;
-    k_bin<<<blocks_for(n, T), T, 0, st>>>(n, pos, wrap_in_place ? 1 : 0, x_ref, nl.xh, nl.xl, nl.atom_cell,
+    k_bin<<<blocks_for(n, T), T, 0, st>>>(n, pos, zatom, wrap_in_place ? 1 : 0, x_ref, nl.xh, nl.xl, nl.atom_cell,
                                           nl.cell_count, b, d_gate);
     if (cells) {
         k_scan<<<1, kScanThreads, 0, st>>>(ncell, nl.cell_count, nl.cell_start, nl.cell_fill, d_gate);

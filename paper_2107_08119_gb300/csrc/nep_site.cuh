@@ -45,14 +45,15 @@ __host__ __device__ __forceinline__ float div_rc(float d, float rc, float inv_rc
     return fmaf(fmaf(-q0, rc, d), inv_rc, q0);
 }
 
-// g_n(d), n = 0..N-1, for d < rc.
+// g_n(d), n = 0..N-1, for d < rc; w multiplies the cutoff function (the
+// multicomponent weight sqrt(Z_i Z_j), 1 for one species).
 template <int N>
-__host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_rc, float (&g)[N])
+__host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_rc, float (&g)[N], float w = 1.f)
 {
     float s, c;
     const float dr = div_rc(d, rc, inv_rc);
     sincospi_f(dr, &s, &c);
-    const float fc = 0.5f * (1.f + c);
+    const float fc = 0.5f * (1.f + c) * w;
     const float t = dr - 1.f;
     const float x = fmaf(2.f * t, t, -1.f);
     float Tm = 1.f, T = x;  // T_{n-1}, T_n
@@ -68,15 +69,15 @@ __host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_r
     }
 }
 
-// (g_n(d), dg_n/dd), n = 0..N-1, for d < rc, as pairs.
+// (g_n(d), dg_n/dd), n = 0..N-1, for d < rc, as pairs; w as in radial_g.
 template <int N>
-__host__ __device__ __forceinline__ void radial_gd(float d, float rc, float inv_rc, float2 (&gd)[N])
+__host__ __device__ __forceinline__ void radial_gd(float d, float rc, float inv_rc, float2 (&gd)[N], float w = 1.f)
 {
     float s, c;
     const float dr = div_rc(d, rc, inv_rc);
     sincospi_f(dr, &s, &c);
-    const float fc = 0.5f * (1.f + c);
-    const float dfc = -0.5f * 3.14159265358979f * inv_rc * s;
+    const float fc = 0.5f * (1.f + c) * w;
+    const float dfc = -0.5f * 3.14159265358979f * inv_rc * s * w;
     const float t = dr - 1.f;
     const float x = fmaf(2.f * t, t, -1.f);
     const float dxdr = 4.f * t * inv_rc;
@@ -99,12 +100,13 @@ __host__ __device__ __forceinline__ void radial_gd(float d, float rc, float inv_
     }
 }
 
-// g_n(d) and dg_n/dd, n = 0..N-1, for d < rc, as two arrays.
+// g_n(d) and dg_n/dd, n = 0..N-1, for d < rc, as two arrays; w as in radial_g.
 template <int N>
-__host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float inv_rc, float (&g)[N], float (&dg)[N])
+__host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float inv_rc, float (&g)[N], float (&dg)[N],
+                                                     float w = 1.f)
 {
     float2 gd[N];
-    radial_gd<N>(d, rc, inv_rc, gd);
+    radial_gd<N>(d, rc, inv_rc, gd, w);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
         g[n] = gd[n].x;
@@ -313,6 +315,7 @@ __host__ __device__ __forceinline__ void network(const float* w, int n_neu, cons
 struct NbSlot {
     int v;
     float h[3], l[3];
+    float z;  // the neighbour's species number
 };
 
 // Slot k of the atom is slots[k * stride + idx]: the global list (stride n,
@@ -329,6 +332,7 @@ __host__ __device__ __forceinline__ void fetch_slot(const SlotTable& T, const fl
     if (k >= 0 && k < cnt) {
         s.v = T.slots[(size_t)k * T.stride + T.idx];
         load_pos(xh, xl, n, s.v & 0xFFFFFF, s.h, s.l);
+        s.z = load_z(xh, s.v & 0xFFFFFF);
     }
 }
 
@@ -337,7 +341,14 @@ struct SiteParams {
     const float* w;  // parameters (shared memory on the device)
     int n_neu;
     float rcR, rcA, rcR2, rcA2, inv_rcR, inv_rcA;
+    int typed;       // multicomponent weighting sqrt(Z_i Z_j) (0: one species, weight 1)
 };
+
+// the multicomponent weight of a pair (Sec. II.A): sqrt(Z_i Z_j), 1 for one species
+__host__ __device__ __forceinline__ float pair_weight(const SiteParams& P, float zi, float zj)
+{
+    return P.typed ? sqrtf(zi * zj) : 1.f;
+}
 
 // Where the partial force of slot k goes: base[k * slot_stride + c * comp_stride].
 // The MD list stores pf[k][c][i] (base = pf + i, strides 3n and n); a
@@ -355,7 +366,7 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
                                                           const float* __restrict__ xh,
                                                           const float* __restrict__ xl, const Box& box,
                                                           const SiteParams& P, const float (&hi)[3],
-                                                          const float (&li)[3], float (&q)[kNdes],
+                                                          const float (&li)[3], float zi, float (&q)[kNdes],
                                                           Harm& S)
 {
     // radial sums are compensated (Kahan): q_0 ~ 4 accumulates ~28 terms and
@@ -386,10 +397,11 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
         float rx, ry, rz;
         pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, rx, ry, rz);
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float w = pair_weight(P, zi, cur.z);
         if (d2 < P.rcR2) {
             const float d = sqrtf(d2);
             float g[kNR];
-            radial_g<kNR>(d, P.rcR, P.inv_rcR, g);
+            radial_g<kNR>(d, P.rcR, P.inv_rcR, g, w);
 #pragma unroll
             for (int a = 0; a < kNR; ++a) {
                 const float y = g[a] - qC[a];
@@ -402,7 +414,7 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
             const float d = sqrtf(d2);
             const float inv = 1.f / d;
             float g[kNA];
-            radial_g<kNA>(d, P.rcA, P.inv_rcA, g);
+            radial_g<kNA>(d, P.rcA, P.inv_rcA, g, w);
             float2 g2[kNA2];
             pair_orders(g, g2);
             sh_pass1(rx * inv, ry * inv, rz * inv, g2, S);
@@ -434,9 +446,9 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
 // from the atom's coefficients A_nlm = 2 c_lm G_nl S_nlm and G_n (Eqs.
 // 23-25): radial G_n g_n' rhat, angular sum_nlm A_nlm grad(g_n Z_lm).
 template <class ArrA, class ArrR>
-__host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, float rz, float d2, const SiteParams& P,
-                                                            const ArrA& A, const ArrR& GR, float& px, float& py,
-                                                            float& pz)
+__host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, float rz, float d2, float w,
+                                                            const SiteParams& P, const ArrA& A, const ArrR& GR,
+                                                            float& px, float& py, float& pz)
 {
     const float d = sqrtf(d2);
     const float inv = 1.f / d;
@@ -445,13 +457,13 @@ __host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, 
     float Vx = 0.f, Vy = 0.f, Vz = 0.f;
     if (d2 < P.rcR2) {
         float2 gd[kNR];
-        radial_gd<kNR>(d, P.rcR, P.inv_rcR, gd);
+        radial_gd<kNR>(d, P.rcR, P.inv_rcR, gd, w);
 #pragma unroll
         for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], gd[a].y, radial);
     }
     if (d2 < P.rcA2) {
         float2 gd[kNA];
-        radial_gd<kNA>(d, P.rcA, P.inv_rcA, gd);
+        radial_gd<kNA>(d, P.rcA, P.inv_rcA, gd, w);
         float2 Vxy = make_float2(0.f, 0.f);
         sh_pass2(ux, uy, uz, A, gd, radial, Vxy, Vz);
         // tangential projection of V, divided by r
@@ -473,10 +485,13 @@ __host__ __device__ __forceinline__ void site_coefficients(int i, bool active, i
                                                            const SiteParams& P, Harm& S,
                                                            float (&GR)[kNR], float& U_hi, float& U_lo)
 {
-    float hi[3], li[3];
-    if (active) load_pos(xh, xl, n, i, hi, li);
+    float hi[3], li[3], zi = 1.f;
+    if (active) {
+        load_pos(xh, xl, n, i, hi, li);
+        zi = load_z(xh, i);
+    }
     float q[kNdes];
-    site_descriptors(i, n, cnt, nbr, xh, xl, box, P, hi, li, q, S);
+    site_descriptors(i, n, cnt, nbr, xh, xl, box, P, hi, li, zi, q, S);
 
     float G[kNdes];
     network(P.w, P.n_neu, q, G, U_hi, U_lo);
@@ -506,8 +521,11 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
     Harm S;
     float GR[kNR];
     site_coefficients(i, active, n, cnt, nbr, xh, xl, box, P, S, GR, U_hi, U_lo);
-    float hi[3], li[3];
-    if (active) load_pos(xh, xl, n, i, hi, li);
+    float hi[3], li[3], zi = 1.f;
+    if (active) {
+        load_pos(xh, xl, n, i, hi, li);
+        zi = load_z(xh, i);
+    }
 
     const float rc2max = P.rcR2 > P.rcA2 ? P.rcR2 : P.rcA2;
     // pass 2: partial forces
@@ -522,7 +540,7 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         if (!(d2 < rc2max)) continue;
         float px, py, pz;
-        pair_partial_force(rx, ry, rz, d2, P, S, GR, px, py, pz);
+        pair_partial_force(rx, ry, rz, d2, pair_weight(P, zi, cur.z), P, S, GR, px, py, pz);
         float* p = out.base + (size_t)k * out.slot_stride;
         p[0] = px;
         p[out.comp_stride] = py;

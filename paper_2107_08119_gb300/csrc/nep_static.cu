@@ -157,7 +157,7 @@ extern "C" int nep_compute_efv_static(const nep_hyper* hp, const float* z, int n
         (rc = cuda_fail(cudaMemsetAsync(err, 0, sizeof(unsigned), st), "cudaMemsetAsync")))
         return rc;
 
-    if ((rc = build_neighbor_list(nl, box, n, const_cast<double*>(pos), false, nullptr, (float)rmax, err, nullptr,
+    if ((rc = build_neighbor_list(nl, box, n, const_cast<double*>(pos), nullptr, false, nullptr, (float)rmax, err, nullptr,
                                   st)))
         return rc;
     ForceArgs fa{z, hp->n_neu, (float)hp->rc_R, (float)hp->rc_A, box};

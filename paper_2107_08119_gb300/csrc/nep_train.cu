@@ -48,7 +48,8 @@ std::atomic<unsigned long long> g_dataset_uid{0};
 
 // ------------------------------------------------------------------ build
 __global__ void k_ds_split(int N, const double* __restrict__ pos, const int* __restrict__ sid,
-                           const Box* __restrict__ boxes, float* __restrict__ xh, float* __restrict__ xl)
+                           const Box* __restrict__ boxes, const float* __restrict__ zat, float* __restrict__ xh,
+                           float* __restrict__ xl)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -62,7 +63,7 @@ __global__ void k_ds_split(int N, const double* __restrict__ pos, const int* __r
         if (w < 0.0) w = 0.0;
         wx[d] = w;
     }
-    store_pos(xh, xl, i, wx);
+    store_pos(xh, xl, i, wx, zat ? zat[i] : 1.f);
 }
 
 __global__ void k_ds_list(int N, const int* __restrict__ sid, const int* __restrict__ sstart,
@@ -155,14 +156,16 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
                           const float* __restrict__ xh, const float* __restrict__ xl,
                           const long long* __restrict__ pstart, const int* __restrict__ pj,
                           const long long* __restrict__ aidx, float rcR2,
-                          float rcA2, float rcR, float rcA, float inv_rcR, float inv_rcA, float* __restrict__ q_out,
-                          float* __restrict__ B_out, PairRec* __restrict__ rec, float* __restrict__ ang)
+                          float rcA2, float rcR, float rcA, float inv_rcR, float inv_rcA, int typed,
+                          float* __restrict__ q_out, float* __restrict__ B_out, PairRec* __restrict__ rec,
+                          float* __restrict__ ang)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const Box b = boxes[sid[i]];
     float hi[3], li[3];
     load_pos(xh, xl, N, i, hi, li);
+    const float zi = load_z(xh, i);
     float qR[kNR], qC[kNR];
     Harm S;
     for (int a = 0; a < kNR; ++a) qR[a] = qC[a] = 0.f;
@@ -178,9 +181,10 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         pair_vector(i, j, v >> 24, hi, li, hj, lj, b, rx, ry, rz);
         const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         const float d = sqrtf(d2);
+        const float wz = typed ? sqrtf(zi * load_z(xh, j)) : 1.f;
         if (d2 < rcR2) {
             float g[kNR];
-            radial_g<kNR>(d, rcR, inv_rcR, g);
+            radial_g<kNR>(d, rcR, inv_rcR, g, wz);
             for (int a = 0; a < kNR; ++a) {
                 const float y = g[a] - qC[a];
                 const float t = qR[a] + y;
@@ -190,7 +194,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         }
         if (d2 < rcA2) {
             float g[kNA];
-            radial_g<kNA>(d, rcA, inv_rcA, g);
+            radial_g<kNA>(d, rcA, inv_rcA, g, wz);
             const float inv = 1.f / d;
             float2 g2[kNA2];
             pair_orders(g, g2);
@@ -220,6 +224,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
         const float d = sqrtf(d2);
         const float inv = 1.f / d;
+        const float wz = typed ? sqrtf(zi * load_z(xh, j)) : 1.f;
         PairRec pr;
         pr.r[0] = r[0];
         pr.r[1] = r[1];
@@ -228,7 +233,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         for (int a = 0; a < kNR; ++a) pr.gd[a] = 0.f;
         if (d2 < rcR2) {
             float g[kNR], dg[kNR];
-            radial_g_dg<kNR>(d, rcR, inv_rcR, g, dg);
+            radial_g_dg<kNR>(d, rcR, inv_rcR, g, dg, wz);
             for (int a = 0; a < kNR; ++a) {
                 pr.gd[a] = dg[a] * inv;
                 for (int c = 0; c < 3; ++c) B[a][c] = fmaf(pr.gd[a], r[c], B[a][c]);
@@ -237,7 +242,7 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         rec[p] = pr;  // owner order: the contraction's owner pass streams i's records
         if (d2 < rcA2) {
             float g[kNA], dg[kNA];
-            radial_g_dg<kNA>(d, rcA, inv_rcA, g, dg);
+            radial_g_dg<kNA>(d, rcA, inv_rcA, g, dg, wz);
             const float u[3] = {r[0] * inv, r[1] * inv, r[2] * inv};
             float Y[kLM], dY[kLM][3];
             sh_eval(u[0], u[1], u[2], Y, dY);
@@ -1031,6 +1036,13 @@ extern "C" {
 int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const double* boxes, const double* pos,
                        const double* e_tar, const double* f_tar, const double* w_tar, nep_dataset** out)
 {
+    return nep_dataset_create_species(m, n_struct, n_atoms, boxes, pos, nullptr, e_tar, f_tar, w_tar, out);
+}
+
+int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, const double* boxes,
+                               const double* pos, const double* z_atom, const double* e_tar, const double* f_tar,
+                               const double* w_tar, nep_dataset** out)
+{
     if (!m || !n_atoms || !boxes || !pos || !e_tar || !f_tar || !w_tar || !out || n_struct < 1) {
         set_error("nep_dataset_create: NULL argument or no structures");
         return NEP_ERR_ARG;
@@ -1074,6 +1086,17 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
         for (int d = 0; d < 3; ++d) hpos[(size_t)d * N + i] = pos[(size_t)3 * i + d];
     std::vector<float> hf((size_t)3 * N);
     for (size_t e = 0; e < hf.size(); ++e) hf[e] = (float)f_tar[e];
+    std::vector<float> hz;
+    if (z_atom) {
+        hz.resize((size_t)N);
+        for (int i = 0; i < N; ++i) {
+            if (!(z_atom[i] > 0.0) || !std::isfinite(z_atom[i])) {
+                set_error("nep_dataset_create_species: the species number of atom %d is not positive", i);
+                return NEP_ERR_ARG;
+            }
+            hz[(size_t)i] = (float)z_atom[i];
+        }
+    }
 
     nep_dataset* ds = new (std::nothrow) nep_dataset();
     if (!ds) {
@@ -1087,6 +1110,8 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     ds->n_chunks = (int)hcb.size();
     long long* bytes = &ds->bytes;
     double* dpos = nullptr;
+    float* dz = nullptr;
+    ds->typed = z_atom ? 1 : 0;
     float*& xh = ds->xh;
     float*& xl = ds->xl;
     int *tmp = nullptr, *cnt = nullptr, *cnta = nullptr;
@@ -1094,6 +1119,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     int rc = NEP_OK;
     auto fail = [&](int code) {
         dfree(dpos);
+        dfree(dz);
         dfree(tmp);
         dfree(cnt);
         dfree(cnta);
@@ -1110,7 +1136,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
         (rc = dalloc(&ds->w_tar, (size_t)6 * S, bytes)) || (rc = dalloc(&dpos, (size_t)3 * N, nullptr)) ||
         (rc = dalloc(&xh, (size_t)4 * N, nullptr)) || (rc = dalloc(&xl, (size_t)4 * N, nullptr)) ||
         (rc = dalloc(&tmp, (size_t)N * kDsCap, nullptr)) || (rc = dalloc(&cnt, N, nullptr)) ||
-        (rc = dalloc(&cnta, N, nullptr)))
+        (rc = dalloc(&cnta, N, nullptr)) || (z_atom && (rc = dalloc(&dz, N, nullptr))))
         return fail(rc);
     cudaError_t e = cudaSuccess;
     auto up = [&](void* dst, const void* src, size_t b) {
@@ -1128,6 +1154,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     up(ds->chunk_begin, hcb.data(), sizeof(int) * hcb.size());
     up(ds->chunk_end, hce.data(), sizeof(int) * hce.size());
     up(dpos, hpos.data(), sizeof(double) * hpos.size());
+    if (z_atom) up(dz, hz.data(), sizeof(float) * hz.size());
     up(ds->e_tar, e_tar, sizeof(double) * S);
     up(ds->f_tar, hf.data(), sizeof(float) * hf.size());
     up(ds->w_tar, w_tar, sizeof(double) * 6 * S);
@@ -1135,7 +1162,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
 
     const float rc2 = (float)(rmax * rmax), rcA2 = (float)(m->hp.rc_A * m->hp.rc_A);
     const float rcR2 = (float)(m->hp.rc_R * m->hp.rc_R);
-    k_ds_split<<<blocks_for(N, 256), 256>>>(N, dpos, ds->sid, ds->boxes, xh, xl);
+    k_ds_split<<<blocks_for(N, 256), 256>>>(N, dpos, ds->sid, ds->boxes, dz, xh, xl);
     k_ds_list<<<blocks_for(N, 128), 128>>>(N, ds->sid, ds->sstart, ds->boxes, xh, xl, rc2, rcA2, tmp, cnt, cnta,
                                            m->d_err);
     if ((rc = cuda_fail(cudaDeviceSynchronize(), "dataset neighbour search"))) return fail(rc);
@@ -1179,8 +1206,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
     k_ds_reverse<<<blocks_for(N, 128), 128>>>(N, ds->pstart, ds->pj, rev, m->d_err);
     k_ds_site<<<blocks_for(N, 64), 64>>>(N, ds->sid, ds->boxes, xh, xl, ds->pstart, ds->pj, ds->aidx, rcR2,
                                          rcA2, (float)m->hp.rc_R, (float)m->hp.rc_A, (float)(1.0 / m->hp.rc_R),
-                                         (float)(1.0 / m->hp.rc_A), ds->q, ds->B,
-                                         ds->rec, ds->ang);
+                                         (float)(1.0 / m->hp.rc_A), ds->typed, ds->q, ds->B, ds->rec, ds->ang);
     rc = cuda_fail(cudaDeviceSynchronize(), "dataset precompute");
     dfree(dastart);
     if (rc) return fail(rc);
@@ -1190,6 +1216,7 @@ int nep_dataset_create(nep_model* m, int n_struct, const int* n_atoms, const dou
         return fail(status_from_bits(bits));
     }
     dfree(dpos);
+    dfree(dz);
     dfree(tmp);
     dfree(cnt);
     dfree(cnta);

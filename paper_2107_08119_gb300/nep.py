@@ -71,6 +71,8 @@ _SIGNATURES = {
     "snes_get_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "snes_run": (C.c_int, [_vp, _vp, C.c_int, _vp, C.c_int, _vp, _vp]),
     "nep_md_set_shc": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "nep_set_species": (C.c_int, [_vp, C.c_int, _vp]),
+    "nep_dataset_create_species": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     "nep_md_get_shc": (C.c_int, [_vp, _vp, C.POINTER(C.c_longlong), _vp]),
     "nep_shc_spectrum": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, C.c_double, C.c_int, _vp, _vp]),
     "nep_dataset_set_shape": (C.c_int, [_vp, _vp]),
@@ -214,6 +216,15 @@ class NEP:
         nbr = torch.empty(self.hyper.max_neighbors, n, dtype=torch.int32, device=dev)
         _check(_lib.nep_get_neighbors(self._h, n, _ptr(cnt), _ptr(nbr), _stream(stream)), "nep_get_neighbors")
         return cnt, nbr
+
+    def set_species(self, z_atom=None):
+        """Per-atom species numbers (atomic numbers) for the multicomponent
+        weighting f_c -> f_c sqrt(Z_i Z_j); None: one species."""
+        if z_atom is None:
+            _check(_lib.nep_set_species(self._h, 0, None), "nep_set_species")
+            return
+        zs = _host(z_atom, np.float64, (-1,))
+        _check(_lib.nep_set_species(self._h, zs.size, zs.ctypes.data_as(_vp)), "nep_set_species")
 
     def profile(self, on: bool = True):
         _check(_lib.nep_profile_enable(self._h, 1 if on else 0), "nep_profile_enable")
@@ -364,7 +375,9 @@ class Dataset:
     structures: list of {"pos": (n, 3), "box": (3, 3)}; e_tar per structure,
     f_tar (N, 3) concatenated, w_tar (n_struct, 6) in the order xx yy zz xy yz zx."""
 
-    def __init__(self, model: NEP, structures, e_tar, f_tar, w_tar):
+    def __init__(self, model: NEP, structures, e_tar, f_tar, w_tar, species=None):
+        """species: per-atom species numbers of the concatenated structures
+        (multicomponent weighting), or None for one species."""
         self.model = model
         n_atoms = _host([len(s["pos"]) for s in structures], np.int32)
         boxes = _host(np.stack([np.asarray(s["box"], np.float64).reshape(3, 3) for s in structures]), np.float64)
@@ -374,9 +387,11 @@ class Dataset:
         f = _host(f_tar, np.float64, (-1, 3))
         w = _host(w_tar, np.float64, (-1, 6))
         out = _vp()
-        _check(_lib.nep_dataset_create(model._h, len(structures), n_atoms.ctypes.data_as(_vp),
-                                       boxes.ctypes.data_as(_vp), pos.ctypes.data_as(_vp), e.ctypes.data_as(_vp),
-                                       f.ctypes.data_as(_vp), w.ctypes.data_as(_vp), C.byref(out)),
+        zs = None if species is None else _host(species, np.float64, (-1,))
+        _check(_lib.nep_dataset_create_species(model._h, len(structures), n_atoms.ctypes.data_as(_vp),
+                                               boxes.ctypes.data_as(_vp), pos.ctypes.data_as(_vp),
+                                               None if zs is None else zs.ctypes.data_as(_vp), e.ctypes.data_as(_vp),
+                                               f.ctypes.data_as(_vp), w.ctypes.data_as(_vp), C.byref(out)),
                "nep_dataset_create")
         self._h = out
         self.n_struct = len(structures)
