@@ -163,6 +163,22 @@ def cpu_oracle_md(seconds: float = 15.0, cells: int = 8, max_steps: int | None =
                       f"{n}-atom {cells}^3-cell block of the same workload (same model, sigma, 300 K)"}
 
 
+def max_over_ranks(vals, dist=None, device="cpu"):
+    """Each value's maximum over the ranks of the process group: the slowest
+    rank sets the whole job's time.  Without a group, the values themselves."""
+    if dist is None:
+        return [float(x) for x in vals]
+    import torch
+    t = torch.tensor([float(x) for x in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_throughput(world: int, units_per_rank: int, steps: int, t_max_ms: float) -> float:
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return world * units_per_rank * steps / (t_max_ms / 1e3)
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: W + K MD steps on the 4,096-atom sample."""
     if rank != 0:
@@ -285,15 +301,8 @@ def run_gpu(args, rank, world, local):
     e2e_s = time.perf_counter() - t0
     md.sync_status()
 
-    t_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        e = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(e, op=dist.ReduceOp.MAX)
-        e2e_s = float(e.item())
-    value = world * n * K / (t_max / 1e3)
+    t_max, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
+    value = job_throughput(world, n, K, t_max)
 
     flops_atom = flops_per_atom(m_r, m_a, hyper.n_neu)
     achieved = flops_atom * n / (site_ms / 1e3) / 1e12
