@@ -80,13 +80,17 @@ __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__
     }
 }
 
-__global__ void k_decide(unsigned* __restrict__ ctl, float thresh2, unsigned long long* __restrict__ rebuilds)
+// use_cond: the step runs from a CUDA graph whose list rebuild sits behind
+// the conditional node `cond`, which this sets.
+__global__ void k_decide(unsigned* __restrict__ ctl, float thresh2, unsigned long long* __restrict__ rebuilds,
+                         cudaGraphConditionalHandle cond, int use_cond)
 {
     const bool go = ctl[kCtlPending] != 0u || __uint_as_float(ctl[kCtlDisp]) > thresh2;
     ctl[kCtlGate] = go ? 1u : 0u;
     ctl[kCtlDisp] = 0u;
     ctl[kCtlPending] = 0u;
     if (go) *rebuilds += 1ull;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
 
 // Second half kick with the HNEMD driving force, E_kin and J per block.
@@ -294,6 +298,23 @@ struct nep_md {
     float* shc_ring = nullptr;   // [n_lags][9][n]
     double* shc_sum = nullptr;   // [n_lags][3]
     double* shc_part = nullptr;  // [chunks][n_lags][3]
+    // one step captured as a CUDA graph (the list rebuild behind a conditional
+    // node), kept while everything it bakes in is unchanged
+    cudaStream_t gcap = nullptr, gcap2 = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    struct GraphKey {
+        const double *pos, *vel;
+        double *thermo, *heat;
+        double dt, t0, tau, fe[3];
+        bool drive;
+        const float* zatom;
+        bool operator==(const GraphKey& o) const
+        {
+            return pos == o.pos && vel == o.vel && thermo == o.thermo && heat == o.heat && dt == o.dt &&
+                   t0 == o.t0 && tau == o.tau && fe[0] == o.fe[0] && fe[1] == o.fe[1] && fe[2] == o.fe[2] &&
+                   drive == o.drive && zatom == o.zatom;
+        }
+    } gkey{};
 };
 
 namespace {
@@ -374,6 +395,9 @@ int nep_md_destroy(nep_md* md)
     if (md->red) cudaFree(md->red);
     if (md->w_atom) cudaFree(md->w_atom);
     free_shc(md);
+    if (md->gexec) cudaGraphExecDestroy(md->gexec);
+    if (md->gcap) cudaStreamDestroy(md->gcap);
+    if (md->gcap2) cudaStreamDestroy(md->gcap2);
     delete md;
     return NEP_OK;
 }
@@ -518,7 +542,6 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     const double rmax = m->hp.rc_R > m->hp.rc_A ? m->hp.rc_R : m->hp.rc_A;
     const double conv = kAmuA2Fs2InEv;
     int rc;
-    const unsigned* gate = md->ctl + kCtlGate;
     if (md->tau > 0.0 && n < 2) {
         set_error("nep_md_step: the thermostat needs at least two atoms");
         return NEP_ERR_ARG;
@@ -551,24 +574,32 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
 
     const double hdtm = 0.5 * dt / (md->mass * conv);
     const float thresh = 0.5f * md->skin;
-    for (int s = 0; s < n_steps; ++s) {
-        Profiler::Slot* pk = m->prof.begin(NEP_PROFILE_STEP, st);
-        k_kick_drift<<<blocks_for(n, 256), 256, 0, st>>>(n, pos, vel, md->ws.force, hdtm, dt, nl.xh, nl.xl, md->x_ref,
-                                                         md->ctl);
-        k_decide<<<1, 1, 0, st>>>(md->ctl, thresh * thresh, md->rebuilds);
-        m->prof.end(pk, st);
-        pk = m->prof.begin(NEP_PROFILE_NEIGHBOR, st);
-        if ((rc = build_neighbor_list(nl, md->box, n, pos, md_zatom(md), true, md->x_ref, md->r_list, m->d_err, gate, st)))
-            return rc;
-        m->prof.end(pk, st);
-        int b1 = 0, b2 = 0, c2 = 0;
+    const double dof_kb = (3.0 * n - 3.0) * kBoltzmannEv;
+
+    // one step in three parts: kick-drift and the rebuild decision, the list
+    // rebuild, then forces, second half kick and the step's sums
+    auto head = [&](cudaStream_t q, bool use_cond, cudaGraphConditionalHandle cond) {
+        Profiler::Slot* pk = m->prof.begin(NEP_PROFILE_STEP, q);
+        k_kick_drift<<<blocks_for(n, 256), 256, 0, q>>>(n, pos, vel, md->ws.force, hdtm, dt, nl.xh, nl.xl, md->x_ref,
+                                                        md->ctl);
+        k_decide<<<1, 1, 0, q>>>(md->ctl, thresh * thresh, md->rebuilds, cond, use_cond ? 1 : 0);
+        m->prof.end(pk, q);
+    };
+    auto rebuild = [&](cudaStream_t q, const unsigned* g) {
+        Profiler::Slot* pk = m->prof.begin(NEP_PROFILE_NEIGHBOR, q);
+        const int r = build_neighbor_list(nl, md->box, n, pos, md_zatom(md), true, md->x_ref, md->r_list, m->d_err, g, q);
+        m->prof.end(pk, q);
+        return r;
+    };
+    auto tail = [&](cudaStream_t q) {
+        int b1 = 0, b2 = 0, c2 = 0, r;
         // spectral heat current: this step's W_i goes to the ring when sampled
         const bool sample = md->shc_lags > 0 && md->shc_step % md->shc_every == 0;
         const int slot = sample ? (int)(md->shc_samples % md->shc_lags) : 0;
         float* w_out = sample ? md->shc_ring + (size_t)slot * 9 * n : (drive ? md->w_atom : nullptr);
-        Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, st);
-        if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
-        m->prof.end(ps, st);
+        Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, q);
+        if ((r = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, q, b1))) return r;
+        m->prof.end(ps, q);
         AssembleArgs aa{};
         aa.rc_max = (float)rmax;
         aa.box = md->box;
@@ -576,35 +607,109 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         aa.half_dt_over_m = hdtm;
         aa.ke_factor = kef;
         aa.heat = heat != nullptr;
-        ps = m->prof.begin(NEP_PROFILE_ASSEMBLE, st);
-        if ((rc = launch_assemble(aa, nl, n, md->ws.force, w_out, part_a, m->d_err, st, b2, c2))) return rc;
-        m->prof.end(ps, st);
-        pk = m->prof.begin(NEP_PROFILE_STEP, st);
-        const double dof_kb = (3.0 * n - 3.0) * kBoltzmannEv;
+        ps = m->prof.begin(NEP_PROFILE_ASSEMBLE, q);
+        if ((r = launch_assemble(aa, nl, n, md->ws.force, w_out, part_a, m->d_err, q, b2, c2))) return r;
+        m->prof.end(ps, q);
+        Profiler::Slot* pk = m->prof.begin(NEP_PROFILE_STEP, q);
         if (drive) {
             // the kick needs the total virial first
-            if ((rc = launch_reduce(part_a, b2, c2, md->red + 1, st))) return rc;
-            k_hnemd_kick<<<nbk, 256, 0, st>>>(n, md->ws.force, w_out, vel, md->fe[0], md->fe[1], md->fe[2],
-                                              md->red + 1, 1.0 / n, hdtm, kef, part_h, m->d_err);
-            k_md_finish<<<1, 32 * 5, 0, st>>>(part_e, b1, part_h, nbk, 4, 10, md->red, thermo, heat, md->ctl, md->t0,
-                                              md->tau, dt, dof_kb);
+            if ((r = launch_reduce(part_a, b2, c2, md->red + 1, q))) return r;
+            k_hnemd_kick<<<nbk, 256, 0, q>>>(n, md->ws.force, w_out, vel, md->fe[0], md->fe[1], md->fe[2],
+                                             md->red + 1, 1.0 / n, hdtm, kef, part_h, m->d_err);
+            k_md_finish<<<1, 32 * 5, 0, q>>>(part_e, b1, part_h, nbk, 4, 10, md->red, thermo, heat, md->ctl, md->t0,
+                                             md->tau, dt, dof_kb);
         } else {
-            k_md_finish<<<1, 32 * (1 + c2), 0, st>>>(part_e, b1, part_a, b2, c2, 1, md->red, thermo, heat, md->ctl,
-                                                     md->t0, md->tau, dt, dof_kb);
+            k_md_finish<<<1, 32 * (1 + c2), 0, q>>>(part_e, b1, part_a, b2, c2, 1, md->red, thermo, heat, md->ctl,
+                                                    md->t0, md->tau, dt, dof_kb);
         }
         if (sample) {  // v is that of J: after the second half kick, before the thermostat
             const int avail = (int)(md->shc_samples + 1 < md->shc_lags ? md->shc_samples + 1 : md->shc_lags);
             const int chunks = (n + kShcChunk - 1) / kShcChunk;
             k_shc_corr<<<dim3((avail + kShcLagsPerBlock - 1) / kShcLagsPerBlock, chunks), 32 * kShcLagsPerBlock, 0,
-                         st>>>(n, md->shc_lags, avail, slot, md->shc_ring, vel, md->shc_part);
-            k_shc_reduce<<<(avail * 3 + 127) / 128, 128, 0, st>>>(md->shc_lags, avail, chunks, md->shc_part,
-                                                                   md->shc_sum);
+                         q>>>(n, md->shc_lags, avail, slot, md->shc_ring, vel, md->shc_part);
+            k_shc_reduce<<<(avail * 3 + 127) / 128, 128, 0, q>>>(md->shc_lags, avail, chunks, md->shc_part,
+                                                                  md->shc_sum);
             ++md->shc_samples;
         }
         if (md->shc_lags > 0) ++md->shc_step;
-        if (md->tau > 0.0 && n > 1) k_scale_v<<<nbk, 256, 0, st>>>(n, vel, md->red);
-        m->prof.end(pk, st);
-        if ((rc = cuda_fail(cudaGetLastError(), "md step kernels"))) return rc;
+        if (md->tau > 0.0 && n > 1) k_scale_v<<<nbk, 256, 0, q>>>(n, vel, md->red);
+        m->prof.end(pk, q);
+        return cuda_fail(cudaGetLastError(), "md step kernels");
+    };
+
+    // Without phase timing and without the per-step host logic of the
+    // spectral heat current, a step runs from a CUDA graph captured once: the
+    // list rebuild is the body of a conditional node that k_decide switches,
+    // so a step without a rebuild launches none of the list kernels.
+    if (!m->prof.on && md->shc_lags == 0) {
+        nep_md::GraphKey key{pos, vel, thermo, heat, dt, md->t0, md->tau, {md->fe[0], md->fe[1], md->fe[2]}, drive,
+                             md_zatom(md)};
+        if (!md->gexec || !(key == md->gkey)) {
+            if (md->gexec) cudaGraphExecDestroy(md->gexec);
+            md->gexec = nullptr;
+            if (!md->gcap && (rc = cuda_fail(cudaStreamCreateWithFlags(&md->gcap, cudaStreamNonBlocking), "stream")))
+                return rc;
+            if (!md->gcap2 && (rc = cuda_fail(cudaStreamCreateWithFlags(&md->gcap2, cudaStreamNonBlocking), "stream")))
+                return rc;
+            cudaGraph_t g = nullptr;
+            cudaGraphConditionalHandle cond;
+            rc = cuda_fail(cudaGraphCreate(&g, 0), "graph create");
+            if (!rc) rc = cuda_fail(cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault), "handle");
+            if (!rc) rc = cuda_fail(cudaStreamBeginCaptureToGraph(md->gcap, g, nullptr, nullptr, 0,
+                                                                  cudaStreamCaptureModeRelaxed), "begin capture");
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            head(md->gcap, true, cond);
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            rc = cuda_fail(cudaStreamGetCaptureInfo(md->gcap, &cs, nullptr, nullptr, &deps, nullptr, &nd), "capture info");
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = cond;
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cnode = nullptr;
+            if (!rc) rc = cuda_fail(cudaGraphAddNode(&cnode, g, deps, nullptr, nd, &cp), "conditional node");
+            if (!rc)
+                rc = cuda_fail(cudaStreamUpdateCaptureDependencies(md->gcap, &cnode, nullptr, 1,
+                                                                   cudaStreamSetCaptureDependencies),
+                               "capture dependencies");
+            if (!rc) {
+                cudaGraph_t body = cp.conditional.phGraph_out[0];
+                rc = cuda_fail(cudaStreamBeginCaptureToGraph(md->gcap2, body, nullptr, nullptr, 0,
+                                                             cudaStreamCaptureModeRelaxed), "begin body capture");
+                if (!rc) {
+                    rc = rebuild(md->gcap2, nullptr);
+                    cudaGraph_t b2 = nullptr;
+                    const cudaError_t e = cudaStreamEndCapture(md->gcap2, &b2);
+                    if (!rc && e != cudaSuccess) rc = cuda_fail(e, "end body capture");
+                }
+            }
+            if (!rc) rc = tail(md->gcap);
+            cudaGraph_t g2 = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(md->gcap, &g2);
+            if (!rc && e != cudaSuccess) rc = cuda_fail(e, "end capture");
+            if (!rc) rc = cuda_fail(cudaGraphInstantiate(&md->gexec, g, 0), "instantiate step graph");
+            cudaGraphDestroy(g);
+            if (rc) {
+                md->gexec = nullptr;
+                return rc;
+            }
+            md->gkey = key;
+        }
+        for (int s = 0; s < n_steps; ++s)
+            if ((rc = cuda_fail(cudaGraphLaunch(md->gexec, st), "launch step graph"))) return rc;
+        return NEP_OK;
+    }
+
+    const unsigned* gate = md->ctl + kCtlGate;
+    for (int s = 0; s < n_steps; ++s) {
+        head(st, false, cudaGraphConditionalHandle{});
+        if ((rc = rebuild(st, gate))) return rc;
+        if ((rc = tail(st))) return rc;
     }
     return NEP_OK;
 }

@@ -151,3 +151,36 @@ def test_md_thermostat_and_drive_errors(N):
     md.set_hnemd([0.0, 0.0, 0.0])     # off
     md.close()
     model.close()
+
+
+@pytest.mark.parametrize("variant", ["nve", "nvt_hnemd"])
+def test_step_graph_equals_eager_steps(N, variant):
+    """Without phase timing a step replays the captured step graph (the list
+    rebuild behind a conditional node); with it the kernels are launched one by
+    one.  Both give bitwise the same trajectory, thermo rows and heat current,
+    through list rebuilds."""
+    import torch
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    n = len(pos)
+    model = N.NEP(z)
+    outs = []
+    for eager in (False, True):
+        md = N.MD(model, n, box, inputs.MASS_SI)
+        if variant == "nvt_hnemd":
+            md.set_thermostat(600.0, 30.0)
+            md.set_hnemd([1e-3, 0.0, -5e-4])
+        p, v = soa(pos), soa(vel)
+        thermo = torch.zeros(60, N.THERMO_COLS, dtype=torch.float64, device="cuda")
+        heat = torch.zeros(60, 3, dtype=torch.float64, device="cuda")
+        model.profile(eager)
+        md.step(p, v, 40, 1.0, thermo, heat)
+        md.step(p, v, 20, 1.0, thermo[40:], heat[40:])   # another key: a recapture
+        model.profile(False)
+        model.profile_read()
+        md.sync_status()
+        outs.append((p.clone(), v.clone(), thermo.clone(), heat.clone(), md.rebuild_count()))
+        md.close()
+    for a, b in zip(outs[0][:4], outs[1][:4]):
+        assert torch.equal(a, b)
+    assert outs[0][4] == outs[1][4] and outs[0][4] >= 1
+    model.close()
