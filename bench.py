@@ -351,7 +351,9 @@ def run_gpu(args, rank, world, local):
                     "h2d_bytes_per_step": int(p.numel() * 8 + v.numel() * 8),
                     "d2h_bytes_per_step": int(p.numel() * 8 + v.numel() * 8 + N.THERMO_COLS * 8),
                     "steps": Ke},
-            "gpu_launches": 13 * K,
+            # per replayed step: kick-drift, decide, site, assembly, finish; per
+            # rebuild the five list kernels of the conditional body
+            "gpu_launches": 5 * K + 5 * rebuilds,
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
         line["force_eval_vs_plain_fp32"] = force_eval_comparison(N, model, p0, box)
