@@ -273,7 +273,9 @@ def run_gpu(args, rank, world, local):
     torch.cuda.synchronize()
     model.profile_read()
     model.profile(True)          # events around each force-pass launch, on the launching stream
+    torch.cuda.nvtx.range_push("md_phases")  # launched one by one: the pass profilers can take apart
     md2.step(p2, v2, K, 1.0, th2, None)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     model.profile(False)
     prof = model.profile_read()
