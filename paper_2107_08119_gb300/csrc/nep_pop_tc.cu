@@ -101,18 +101,21 @@ constexpr int kTileBytes = kTile * 64;   // one 128 x 32 BF16 operand tile
 constexpr int kGroupBytes = 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes + (2 * kTcGroup * 32 + 4) * 4;
 constexpr int kTmemCols = 128;
 
-// Shared memory of one CTA (one 128-atom tile, one member group).  Once GEMM 1
-// has completed its operands are dead and the GEMM-2 A tiles (D of the four
-// members, BF16) take their place:
+// Shared memory of one CTA (one 128-atom tile, one member group).  The group
+// record arrives by one bulk async copy (cp.async.bulk, completion counted on
+// mbar_ld).  Once GEMM 1 has completed its operands are dead and the GEMM-2 A
+// tiles (D of the four members, BF16) take their place:
 //   a    q hi | q lo            -> D of members 0 | 1
 //   grp  w1 hi | w1 lo | ...    -> D of members 2 | 3 | (w1t hi, w1t lo, b1, w2, b2 kept)
 // ~50 KB and 128 TMEM columns per CTA: four CTAs fit on one SM.
 struct PopSmem {
     unsigned char a[2 * kTileBytes];
     unsigned char grp[kGroupBytes];
-    uint64_t mbar;
+    uint64_t mbar;     // MMA completion (phases 0 and 1)
+    uint64_t mbar_ld;  // bulk copy of the group record
     uint32_t tmem_base;
 };
+static_assert(kGroupBytes % 16 == 0, "the group record is copied in 16-byte units");
 
 __device__ __forceinline__ unsigned char* d_tile(PopSmem& S, int m)
 {
@@ -216,6 +219,19 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
     const bool valid = i < N;
     const int gi = blockIdx.x, k0 = gi * kTcGroup;
 
+    // ---- the group's packed operands: one bulk async copy (33.8 KB, L2-resident
+    // records) into shared memory, overlapping the descriptor conversion below
+    if (t == 0) {
+        tc::mbar_init(&S.mbar_ld, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(&S.mbar_ld)),
+                     "r"((uint32_t)kGroupBytes)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(S.grp)),
+                     "l"(packed + (size_t)gi * kGroupBytes), "r"((uint32_t)kGroupBytes), "r"(tc::smem_u32(&S.mbar_ld))
+                     : "memory");
+    }
     // ---- A of GEMM 1: this thread's 16 descriptors of its atom, split BF16, 16-byte stores
 #pragma unroll
     for (int c = 2 * half; c < 2 * half + 2; ++c) {
@@ -241,12 +257,6 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
         *reinterpret_cast<uint4*>(S.a + o) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4*>(S.a + kTileBytes + o) = make_uint4(l[0], l[1], l[2], l[3]);
     }
-    // ---- the group's packed operands (16-byte copies; the records stay in L2)
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(packed + (size_t)gi * kGroupBytes);
-        uint4* dst = reinterpret_cast<uint4*>(S.grp);
-        for (int e = t; e < kGroupBytes / 16; e += blockDim.x) dst[e] = src[e];
-    }
     if (t == 0) {
         tc::mbar_init(&S.mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -256,19 +266,23 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
         tc::tmem_relinquish();
     }
     tc_sync();
+    // the group record has landed (bounded wait; a lost copy latches a timeout)
+    const bool ld_ok = __syncthreads_and(tc::mbar_wait(&S.mbar_ld, 0, kMaxPolls)) != 0;
+    bool ok = ld_ok;
     const uint32_t tb = S.tmem_base;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     const unsigned char* w1t_hi = S.grp + 2 * kW1Bytes;
     const unsigned char* w1t_lo = w1t_hi + kTcGroup * kW1tBytes;
     const float* fb = reinterpret_cast<const float*>(S.grp + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
-    bool ok;
 
     // ---- GEMM 1: H = Q W1^T into TMEM columns [0, 128), member m at [32 m, 32 m + 32)
-    if (t == 0) {
-        mma_split(tb, S.a, S.a + kTileBytes, S.grp, S.grp + kW1Bytes, tc::idesc_bf16_f32(kTile, kTmemCols));
-        tc::mma_commit(&S.mbar);
+    if (ok) {
+        if (t == 0) {
+            mma_split(tb, S.a, S.a + kTileBytes, S.grp, S.grp + kW1Bytes, tc::idesc_bf16_f32(kTile, kTmemCols));
+            tc::mma_commit(&S.mbar);
+        }
+        ok = __syncthreads_and(tc::mbar_wait(&S.mbar, 0, kMaxPolls)) != 0;
     }
-    ok = __syncthreads_and(tc::mbar_wait(&S.mbar, 0, kMaxPolls)) != 0;
     tc::fence_after_sync();
     if (ok) {
         // ---- epilogue 1: x = tanh(H - b1), U, D = w2 (1 - x^2) as BF16 into the GEMM-2 A tiles
@@ -335,6 +349,7 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
     } else if (t == 0) {
         atomicOr(err, kErrTimeout);
     }
+    if (!ld_ok) tc::mbar_wait(&S.mbar_ld, 0, kMaxPolls);  // a copy still in flight (bounded)
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tb, kTmemCols);
