@@ -84,6 +84,7 @@ struct nep_dataset {
     double* U = nullptr;
     double* partials = nullptr;
     unsigned char* packed = nullptr;  // tensor-core operand records
+    unsigned char* qpack = nullptr;   // descriptors as split-BF16 A tiles (tensor cores)
     float* pbuf = nullptr;            // [n_pairs][3][Pst] partial forces p_kji at the receiver's slot
     float* w6 = nullptr;              // [N][6][Pst] virial contributions of each owner
     float* fown = nullptr;            // [N][3][Pst] own force terms G_i . B_i

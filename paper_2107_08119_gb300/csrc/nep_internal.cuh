@@ -329,7 +329,10 @@ size_t pop_tc_packed_bytes(int P);
 // kernel attributes of the tensor-core path; call outside any stream capture
 int prepare_pop_tc();
 // G [N][32][Pst] FP32, U [N][P] FP64 (launches only: capturable)
-int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
+// the descriptors packed as split-BF16 GEMM-1 A tiles, once per training set
+size_t pop_tc_qpack_bytes(int N);
+int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t st);
+int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
                   const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
                   cudaStream_t st);
 

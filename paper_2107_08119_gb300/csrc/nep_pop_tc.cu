@@ -101,9 +101,9 @@ constexpr int kTileBytes = kTile * 64;   // one 128 x 32 BF16 operand tile
 constexpr int kGroupBytes = 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes + (2 * kTcGroup * 32 + 4) * 4;
 constexpr int kTmemCols = 128;
 
-// Shared memory of one CTA (one 128-atom tile, one member group).  The group
-// record arrives by one bulk async copy (cp.async.bulk, completion counted on
-// mbar_ld).  Once GEMM 1 has completed its operands are dead and the GEMM-2 A
+// Shared memory of one CTA (one 128-atom tile, one member group).  The
+// descriptor tiles and the group record arrive by bulk async copies
+// (cp.async.bulk, completion counted on mbar_ld).  Once GEMM 1 has completed its operands are dead and the GEMM-2 A
 // tiles (D of the four members, BF16) take their place:
 //   a    q hi | q lo            -> D of members 0 | 1
 //   grp  w1 hi | w1 lo | ...    -> D of members 2 | 3 | (w1t hi, w1t lo, b1, w2, b2 kept)
@@ -140,6 +140,33 @@ __device__ __forceinline__ void put_split(unsigned char* hi_base, unsigned char*
     const uint32_t o = tc::kmajor_offset(row, k);
     *reinterpret_cast<__nv_bfloat16*>(hi_base + o) = h;
     *reinterpret_cast<__nv_bfloat16*>(lo_base + o) = l;
+}
+
+// The descriptors of every 128-atom tile as the GEMM-1 A operand, split BF16
+// (hi tile, then lo tile, canonical K-major layout; rows past N are zero):
+// one thread per (atom row, 8 descriptors).  Run once per training set.
+__global__ void k_pack_q_tc(int N, int tiles, const float* __restrict__ q, unsigned char* __restrict__ qpack)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tiles * kTile * 4) return;
+    const int tile = e / (kTile * 4), row = (e / 4) % kTile, c = e % 4;
+    const int i = tile * kTile + row;
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = i < N ? q[(size_t)i * kNdes + 8 * c + k] : 0.f;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        __nv_bfloat16 h0, l0, h1, l1;
+        split_bf16(v[2 * k], h0, l0);
+        split_bf16(v[2 * k + 1], h1, l1);
+        h[k] = pack2(h0, h1);
+        l[k] = pack2(l0, l1);
+    }
+    unsigned char* base = qpack + (size_t)tile * 2 * kTileBytes;
+    const uint32_t o = tc::kmajor_offset(row, 8 * c);
+    *reinterpret_cast<uint4*>(base + o) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(base + kTileBytes + o) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // One thread per (group, element) of the packed records.
@@ -206,7 +233,7 @@ __device__ __forceinline__ void tc_sync()
 // G [N][32][Pst] (FP32, member innermost).  Warp w: TMEM lane quarter w & 3 (its 32 atoms),
 // half w >> 2 (members {2h, 2h+1} in epilogue 1, descriptors [16h, 16h+16) in
 // epilogue 2).
-__global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, const float* __restrict__ q,
+__global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, const unsigned char* __restrict__ qpack,
                                                         const unsigned char* __restrict__ packed,
                                                         float* __restrict__ G, double* __restrict__ U, unsigned* err)
 {
@@ -219,43 +246,24 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
     const bool valid = i < N;
     const int gi = blockIdx.x, k0 = gi * kTcGroup;
 
-    // ---- the group's packed operands: one bulk async copy (33.8 KB, L2-resident
-    // records) into shared memory, overlapping the descriptor conversion below
+    // ---- GEMM-1 operands by two bulk async copies: the tile's descriptors as
+    // split BF16 (16 KB, packed once per training set) and the group's packed
+    // weights (33.8 KB, L2-resident records)
     if (t == 0) {
         tc::mbar_init(&S.mbar_ld, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(&S.mbar_ld)),
-                     "r"((uint32_t)kGroupBytes)
+                     "r"((uint32_t)(2 * kTileBytes + kGroupBytes))
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(S.a)),
+                     "l"(qpack + (size_t)blockIdx.y * 2 * kTileBytes), "r"((uint32_t)(2 * kTileBytes)),
+                     "r"(tc::smem_u32(&S.mbar_ld))
                      : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                          tc::smem_u32(S.grp)),
                      "l"(packed + (size_t)gi * kGroupBytes), "r"((uint32_t)kGroupBytes), "r"(tc::smem_u32(&S.mbar_ld))
                      : "memory");
-    }
-    // ---- A of GEMM 1: this thread's 16 descriptors of its atom, split BF16, 16-byte stores
-#pragma unroll
-    for (int c = 2 * half; c < 2 * half + 2; ++c) {
-        float v[8];
-        if (valid) {
-            const float4 a = *reinterpret_cast<const float4*>(q + (size_t)i * kNdes + 8 * c);
-            const float4 b = *reinterpret_cast<const float4*>(q + (size_t)i * kNdes + 8 * c + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = 0.f;
-        }
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            __nv_bfloat16 h0, l0, h1, l1;
-            split_bf16(v[2 * e], h0, l0);
-            split_bf16(v[2 * e + 1], h1, l1);
-            h[e] = pack2(h0, h1);
-            l[e] = pack2(l0, l1);
-        }
-        const uint32_t o = tc::kmajor_offset(row, 8 * c);
-        *reinterpret_cast<uint4*>(S.a + o) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(S.a + kTileBytes + o) = make_uint4(l[0], l[1], l[2], l[3]);
     }
     if (t == 0) {
         tc::mbar_init(&S.mbar, 1);
@@ -365,7 +373,16 @@ int prepare_pop_tc()
                      "population kernel shared memory");
 }
 
-int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float* W1t, const float* b1t,
+size_t pop_tc_qpack_bytes(int N) { return (size_t)((N + kTile - 1) / kTile) * 2 * kTileBytes; }
+
+int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t st)
+{
+    const int tiles = (N + kTile - 1) / kTile;
+    k_pack_q_tc<<<(tiles * kTile * 4 + 255) / 256, 256, 0, st>>>(N, tiles, q, qpack);
+    return cuda_fail(cudaGetLastError(), "pack descriptors for the tensor cores");
+}
+
+int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
                   const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
                   cudaStream_t st)
 {
@@ -377,7 +394,7 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const float* q, const float*
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
     k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
     const size_t smem = sizeof(PopSmem);
-    k_pop_tc<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, q, packed, G, U, err);
+    k_pop_tc<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
 }
 

@@ -949,7 +949,7 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
     k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t, ds->b2t);
     int rc;
     if (precision == NEP_PREC_BF16) {
-        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
+        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
                                 ds->U, m->d_err, st)))
             return rc;
     } else {
@@ -1207,7 +1207,9 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     k_ds_site<<<blocks_for(N, 64), 64>>>(N, ds->sid, ds->boxes, xh, xl, ds->pstart, ds->pj, ds->aidx, rcR2,
                                          rcA2, (float)m->hp.rc_R, (float)m->hp.rc_A, (float)(1.0 / m->hp.rc_R),
                                          (float)(1.0 / m->hp.rc_A), ds->typed, ds->q, ds->B, ds->rec, ds->ang);
-    rc = cuda_fail(cudaDeviceSynchronize(), "dataset precompute");
+    if (!rc && !(rc = dalloc(&ds->qpack, pop_tc_qpack_bytes(N), bytes)))
+        rc = launch_pack_q_tc(N, ds->q, ds->qpack, nullptr);
+    if (!rc) rc = cuda_fail(cudaDeviceSynchronize(), "dataset precompute");
     dfree(dastart);
     if (rc) return fail(rc);
     cudaMemcpy(&bits, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
@@ -1257,6 +1259,7 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->U);
     dfree(ds->partials);
     dfree(ds->packed);
+    dfree(ds->qpack);
     dfree(ds->pbuf);
     dfree(ds->w6);
     dfree(ds->fown);
