@@ -349,8 +349,9 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
 // Contraction, pass 1 (owner side): one warp per atom j, lane l holding
 // members 2l and 2l + 1.  The lane loads its members' G_j once (registers).
 // j's Jacobian records are contiguous (owner order), so the warp stages them
-// into shared memory 32 pairs at a time with coalesced 16-byte loads, all in
-// flight together, and then forms p_kji = G_kj . J_ji pair by pair from
+// into shared memory 32 pairs at a time with 16-byte asynchronous copies
+// (cp.async, requested before G_j is loaded and the own term formed, so the
+// latencies overlap), and then forms p_kji = G_kj . J_ji pair by pair from
 // shared memory (broadcast reads), storing it at the slot of the reverse pair
 // (i -> j) so that pass 2 finds the partial forces acting on i in i's own
 // slot order.  The owner's virial contribution sum_i r_ij (x) p_kji
@@ -374,12 +375,35 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
     const int k0 = 2 * lane;
     const bool ld = k0 < Pst;  // Pst is even: the float2 at k0 is inside the row
     const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    // 16-byte asynchronous copies global -> shared (no register staging)
+    auto cp16 = [](float* dst, const float* src) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                     "l"(src)
+                     : "memory");
+    };
     for (int j = j0 + (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < j1; j += warps) {
+        const long long pe = pstart[j + 1];
+        long long q0 = pstart[j];
+        int nq = (int)min((long long)kOwnerChunk, pe - q0);
+        // the first chunk's pair descriptors and records are requested before
+        // G_j and the own term, so their latencies overlap
+        long long my_ai = lane < nq ? aidx[q0 + lane] : -1;
+        long long my_rv = lane < nq ? rev[q0 + lane] : 0;
+        for (int t = lane; t < nq * kRecFloats / 4; t += 32)
+            cp16(s_rec + 4 * t, reinterpret_cast<const float*>(rec + q0) + 4 * t);
         float2 g[kNdes];
         const float* Gj = G + (size_t)j * kNdes * Pst + k0;
 #pragma unroll
         for (int v = 0; v < kNdes; ++v)
             g[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
+        // this chunk's angular records are the consecutive ones starting at
+        // the first angular pair's index (owner order assigns them in turn)
+        unsigned angmask = __ballot_sync(0xffffffffu, my_ai >= 0);
+        int na = __popc(angmask);
+        long long a0 = na ? __shfl_sync(0xffffffffu, my_ai, __ffs(angmask) - 1) : 0;
+        for (int t = lane; t < na * kAngFloats / 4; t += 32)
+            cp16(s_ang + 4 * t, ang + (size_t)a0 * kAngFloats + 4 * t);
+        asm volatile("cp.async.commit_group;" ::: "memory");
         // own term G_j . B_j (B_j = sum of j's own Jacobians), for pass 2
         {
             const float4* B4 = reinterpret_cast<const float4*>(B + (size_t)j * kNdes * 3);
@@ -403,23 +427,8 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
         float2 w6[6];
 #pragma unroll
         for (int w = 0; w < 6; ++w) w6[w] = make_float2(0.f, 0.f);
-        const long long pe = pstart[j + 1];
-        for (long long q0 = pstart[j]; q0 < pe; q0 += kOwnerChunk) {
-            const int nq = (int)min((long long)kOwnerChunk, pe - q0);
-            // this chunk's angular records are the consecutive ones starting at
-            // the first angular pair's index (owner order assigns them in turn)
-            const long long my_ai = lane < nq ? aidx[q0 + lane] : -1;
-            const long long my_rv = lane < nq ? rev[q0 + lane] : 0;
-            const unsigned angmask = __ballot_sync(0xffffffffu, my_ai >= 0);
-            const int na = __popc(angmask);
-            const long long a0 = na ? __shfl_sync(0xffffffffu, my_ai, __ffs(angmask) - 1) : 0;
-            // stage pair records and angular blocks (16-byte pieces, all lanes)
-            const float4* rsrc = reinterpret_cast<const float4*>(rec + q0);
-            for (int t = lane; t < nq * kRecFloats / 4; t += 32)
-                reinterpret_cast<float4*>(s_rec)[t] = rsrc[t];
-            const float4* asrc = reinterpret_cast<const float4*>(ang + (size_t)a0 * kAngFloats);
-            for (int t = lane; t < na * kAngFloats / 4; t += 32)
-                reinterpret_cast<float4*>(s_ang)[t] = asrc[t];
+        for (;;) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
             __syncwarp();
             for (int t = 0; t < nq; ++t) {
                 const float* pr = s_rec + t * kRecFloats;  // r_ji [0..2], g_n'/r [3..10]
@@ -453,6 +462,19 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
                 w6[5] = __ffma2_rn(bcast2(-r2), pv[0], w6[5]);  // zx
             }
             __syncwarp();  // the stage is refilled by the next chunk
+            q0 += kOwnerChunk;
+            if (q0 >= pe) break;
+            nq = (int)min((long long)kOwnerChunk, pe - q0);
+            my_ai = lane < nq ? aidx[q0 + lane] : -1;
+            my_rv = lane < nq ? rev[q0 + lane] : 0;
+            for (int t = lane; t < nq * kRecFloats / 4; t += 32)
+                cp16(s_rec + 4 * t, reinterpret_cast<const float*>(rec + q0) + 4 * t);
+            angmask = __ballot_sync(0xffffffffu, my_ai >= 0);
+            na = __popc(angmask);
+            a0 = na ? __shfl_sync(0xffffffffu, my_ai, __ffs(angmask) - 1) : 0;
+            for (int t = lane; t < na * kAngFloats / 4; t += 32)
+                cp16(s_ang + 4 * t, ang + (size_t)a0 * kAngFloats + 4 * t);
+            asm volatile("cp.async.commit_group;" ::: "memory");
         }
         if (ld) {
             float* o = w6out + (size_t)j * 6 * Pst + k0;
