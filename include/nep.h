@@ -300,7 +300,8 @@ int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
  *                   lines it has consumed (no write-back of dead data).
  *   [3] threads     128 or 256 threads per block of the FP32 network.
  *   [4] unroll      4 or 8 partial-force slots in flight per warp in the
- *                   second contraction pass.
+ *                   second contraction pass, or 16: staged in shared memory
+ *                   16 slots at a time by asynchronous copies.
  * No shape changes a result bit (every value keeps its writer and its order of
  * summation).  Default {1, 4, 0, 256, 4}.  Errors: NEP_ERR_ARG (NULL, out of range).
  */
@@ -309,7 +310,7 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape);
 /*
  * nep_dataset_tune -- autotuner: times every candidate shape (waves 1, 2, 4
  * x owner warps 4, 8 x discard 0, 1 when waves > 1 x network threads 128, 256
- * in FP32 mode x unroll 4, 8) on `reps` evaluations of an n_pop-member population of fixed
+ * in FP32 mode x unroll 4, 8, 16) on `reps` evaluations of an n_pop-member population of fixed
  * stand-in parameters, with CUDA events on `stream` after one warm-up
  * evaluation each, and keeps the fastest on the dataset.  Synchronises the
  * stream.  shape_out: host int[5] or NULL; ms_out: host, the best shape's

@@ -599,6 +599,87 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
     }
 }
 
+// The receiver pass with the slot rows staged in shared memory: per round a
+// warp requests up to kRecvStage slots of its atom (3 rows each) with 8-byte
+// asynchronous copies (cp.async, no registers held), waits, and sums them in
+// slot order: the same arithmetic as k_contract, twice the bytes in flight.
+constexpr int kRecvStage = 16;
+
+__global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
+    int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
+    const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
+    const float* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
+    double* __restrict__ partials)
+{
+    constexpr int kWarps = kReceiverThreads / 32;
+    __shared__ double red[kWarps][kMaxPop][8];
+    extern __shared__ float2 s_slots[];  // [warps][kRecvStage][3][Pst / 2]
+    const int c = c0 + blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k0 = 2 * lane;
+    const bool on0 = k0 < P, on1 = k0 + 1 < P;
+    const bool ld = k0 < Pst;
+    const int half = Pst / 2;  // float2 per row
+    float2* stage = s_slots + (size_t)warp * kRecvStage * 3 * half;
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+        if (k0 + m < kMaxPop)
+#pragma unroll
+            for (int w = 0; w < 8; ++w) red[warp][k0 + m][w] = 0.0;
+    const int end = chunk_end[c];
+    int i = chunk_begin[c] + warp;
+    RecvAtom cur, nxt;
+    if (i < end) recv_load(cur, i, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
+    for (; i < end; i += kWarps) {
+        if (i + kWarps < end) recv_load(nxt, i + kWarps, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
+        float F[2][3] = {{cur.fo[0].x, cur.fo[1].x, cur.fo[2].x}, {cur.fo[0].y, cur.fo[1].y, cur.fo[2].y}};
+        for (long long p0 = cur.ps; p0 < cur.pe; p0 += kRecvStage) {
+            const int ns = (int)min((long long)kRecvStage, cur.pe - p0);
+            if (ld)
+                for (int t = 0; t < ns * 3; ++t) {
+                    const float* src = pbuf + (size_t)(p0 * 3 + t) * Pst + k0;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                                     (unsigned)__cvta_generic_to_shared(stage + (size_t)t * half + lane)),
+                                 "l"(src)
+                                 : "memory");
+                }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+            if (ld)
+                for (int t = 0; t < ns; ++t)
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const float2 x = stage[(size_t)(3 * t + cc) * half + lane];
+                        F[0][cc] -= x.x;
+                        F[1][cc] -= x.y;
+                    }
+            __syncwarp();  // each lane reads only its own staged words; kept for the reuse order
+        }
+        if (discard) {
+            __syncwarp();
+            discard_l2_lines(pbuf + (size_t)cur.ps * 3 * Pst, pbuf + (size_t)cur.pe * 3 * Pst, lane);
+        }
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            if (!(m == 0 ? on0 : on1)) continue;
+            const float dx = F[m][0] - cur.t[0], dy = F[m][1] - cur.t[1], dz = F[m][2] - cur.t[2];
+            double* r = red[warp][k0 + m];
+            r[0] += m == 0 ? cur.u0 : cur.u1;
+            r[1] += (double)dx * dx + (double)dy * dy + (double)dz * dz;
+#pragma unroll
+            for (int w = 0; w < 6; ++w) r[2 + w] += (double)(m == 0 ? cur.w6[w].x : cur.w6[w].y);
+        }
+        cur = nxt;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
+        const int k = e / 8, w = e % 8;
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) t += red[q][k][w];
+        partials[((size_t)c * P + k) * 8 + w] = t;
+    }
+}
+
 // One block per member: per structure, the chunk sums (fixed order), then the
 // RMSEs of Eqs. 30-32 with energy and virial per atom, and L1, L2 (Eqs. 33-34).
 __global__ void k_loss(int P, int S, int n_par, int N, const int* __restrict__ s_chunk0,
@@ -814,7 +895,7 @@ bool valid_shape(const EvalShape& h)
 {
     return h.waves >= 1 && h.waves <= kMaxWaves && (h.owner_warps == 4 || h.owner_warps == 8) &&
            (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
-           (h.recv_unroll == 4 || h.recv_unroll == 8);
+           (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 16);
 }
 
 }  // namespace
@@ -929,6 +1010,11 @@ int prepare_evaluation(nep_dataset* ds, int P)
     if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, ostage),
                         "contraction shared memory")))
         return rc;
+    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (kReceiverThreads / 32) * kRecvStage * 3 * member_stride(kMaxPop) *
+                                                 (int)sizeof(float)),
+                        "contraction shared memory")))
+        return rc;
     return prepare_pop_tc();
 }
 
@@ -947,9 +1033,17 @@ void launch_contraction(const nep_dataset* ds, int P, int Pst, int c_lo, int c_h
         cudaEventRecord(ev, st);
         cudaStreamWaitEvent(p2, ev, 0);
     }
-    auto recv = sh.recv_unroll == 8 ? k_contract<8> : k_contract<4>;
-    recv<<<c_hi - c_lo, kReceiverThreads, 0, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin, ds->chunk_end, ds->U,
-                                                   ds->pstart, ds->fown, ds->pbuf, ds->w6, ds->f_tar, ds->partials);
+    if (sh.recv_unroll == 16) {
+        const size_t smem = (size_t)(kReceiverThreads / 32) * kRecvStage * 3 * Pst * sizeof(float);
+        k_contract_staged<<<c_hi - c_lo, kReceiverThreads, smem, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin,
+                                                                       ds->chunk_end, ds->U, ds->pstart, ds->fown,
+                                                                       ds->pbuf, ds->w6, ds->f_tar, ds->partials);
+    } else {
+        auto recv = sh.recv_unroll == 8 ? k_contract<8> : k_contract<4>;
+        recv<<<c_hi - c_lo, kReceiverThreads, 0, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin, ds->chunk_end,
+                                                       ds->U, ds->pstart, ds->fown, ds->pbuf, ds->w6, ds->f_tar,
+                                                       ds->partials);
+    }
 }
 
 // Launches of one population evaluation (no allocation, no attribute calls:
@@ -1479,7 +1573,7 @@ int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
     h.recv_unroll = shape[4];
     if (!valid_shape(h)) {
         set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
-                  "receiver unroll 4 or 8",
+                  "receiver unroll 4, 8 or 16 (staged)",
                   kMaxWaves);
         return NEP_ERR_ARG;
     }
@@ -1519,7 +1613,7 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
         for (int ow = 4; ow <= 8; ow += 4)
             for (int dc = 0; dc <= (w > 1 ? 1 : 0); ++dc)
                 for (int mt = 128; mt <= 256; mt += 128)
-                    for (int ru = 4; ru <= 8; ru += 4) {
+                    for (int ru = 4; ru <= 16; ru *= 2) {
                         if (precision == NEP_PREC_BF16 && mt == 128) continue;  // the FP32 network is not launched
                         EvalShape h;
                         h.waves = w;

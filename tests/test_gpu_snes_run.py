@@ -53,7 +53,7 @@ def _all_shapes(precision, N):
         for ow in (4, 8):
             for dc in ((0, 1) if w > 1 else (0,)):
                 for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
-                    for ru in (4, 8):
+                    for ru in (4, 8, 16):
                         out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru))
     return out
 
@@ -93,7 +93,7 @@ def test_autotuner_picks_a_candidate(N, full_set):
 def test_shape_validation(N, full_set):
     model, ds, pop = full_set
     for bad in (dict(waves=0), dict(waves=17), dict(owner_warps=6), dict(discard=2), dict(mlp_threads=64),
-                dict(recv_unroll=2)):
+                dict(recv_unroll=2), dict(recv_unroll=12)):
         with pytest.raises(N.NepError) as e:
             ds.set_shape(**bad)
         assert e.value.code == -1  # NEP_ERR_ARG
