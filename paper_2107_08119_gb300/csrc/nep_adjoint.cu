@@ -140,7 +140,7 @@ __device__ __forceinline__ void adj_pass(float x, float y, float z, const Harm& 
                                          const float (&dg)[kNA], float e, float tx, float ty, float tz,
                                          float (&lam)[kNdes])
 {
-    NEP_SH_LOCALS(x, y, z)
+    NEP_SH_LOCALS_FAST(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) adj_term(A, g, dg, lm, Yv, gx, gy, gz, e, tx, ty, tz, lam);
     NEP_SH_TABLE(NEP_T)
 #undef NEP_T

@@ -45,8 +45,18 @@ __host__ __device__ __forceinline__ float div_rc(float d, float rc, float inv_rc
     return fmaf(fmaf(-q0, rc, d), inv_rc, q0);
 }
 
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum).
+__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 // g_n(d), n = 0..N-1, for d < rc; w multiplies the cutoff function (the
-// multicomponent weight sqrt(Z_i Z_j), 1 for one species).
+// multicomponent weight sqrt(Z_i Z_j), 1 for one species).  x = 2 t^2 - 1
+// with t = d/rc - 1 carried as hi + lo: for d < rc/2 the difference rounds,
+// and the Chebyshev recurrence multiplies an error in x by up to n^2.
 template <int N>
 __host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_rc, float (&g)[N], float w = 1.f)
 {
@@ -54,8 +64,9 @@ __host__ __device__ __forceinline__ void radial_g(float d, float rc, float inv_r
     const float dr = div_rc(d, rc, inv_rc);
     sincospi_f(dr, &s, &c);
     const float fc = 0.5f * (1.f + c) * w;
-    const float t = dr - 1.f;
-    const float x = fmaf(2.f * t, t, -1.f);
+    float t, tl;
+    two_sum(dr, -1.f, t, tl);
+    const float x = fmaf(4.f * t, tl, fmaf(2.f * t, t, -1.f));
     float Tm = 1.f, T = x;  // T_{n-1}, T_n
     const float hfc = 0.5f * fc;
     g[0] = fc;
@@ -121,14 +132,30 @@ __host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float in
 // real spherical harmonic).  Every c_lm is a dyadic rational, exact in FP32.
 // The gradient columns are those of the polynomial extension off the sphere;
 // callers project them onto the tangent plane.  Expects the locals of
-// NEP_SH_LOCALS in scope.
+// NEP_SH_LOCALS in scope; the factors k z^2 - c are formed from the exact
+// square (the rounding of z^2 would otherwise be multiplied by up to 21).
 #define NEP_SH_LOCALS(x, y, z)                                                  \
     const float x2 = x * x, y2 = y * y, z2 = z * z;                             \
     const float xy = x * y, yz = y * z, xz = x * z;                             \
     const float x2my2 = x2 - y2;                                                \
+    const float z2l = fmaf(z, z, -z2); /* z^2 = z2 + z2l exactly */             \
+    const float a5 = fmaf(5.f, z2l, fmaf(5.f, z2, -1.f));                       \
+    const float a7 = fmaf(7.f, z2l, fmaf(7.f, z2, -1.f));                       \
+    const float b7 = fmaf(7.f, z2l, fmaf(7.f, z2, -3.f));                       \
+    const float c21 = fmaf(21.f, z2l, fmaf(21.f, z2, -3.f));                    \
+    const float e19 = fmaf(35.f, z2l, fmaf(35.f, z2, -30.f));                   \
+    (void)x2my2; (void)z2l; (void)a5; (void)a7; (void)b7; (void)c21; (void)e19;
+
+// The same with z^2 rounded once (the partial forces, whose 1e-4 eV/A bar
+// leaves room).
+#define NEP_SH_LOCALS_FAST(x, y, z)                                                \
+    const float x2 = x * x, y2 = y * y, z2 = z * z;                             \
+    const float xy = x * y, yz = y * z, xz = x * z;                             \
+    const float x2my2 = x2 - y2;                                                \
+    const float z2l = 0.f;                                                      \
     const float a5 = 5.f * z2 - 1.f, a7 = 7.f * z2 - 1.f, b7 = 7.f * z2 - 3.f; \
-    const float c21 = 21.f * z2 - 3.f;                                          \
-    (void)x2my2; (void)a5; (void)a7; (void)b7; (void)c21;
+    const float c21 = 21.f * z2 - 3.f, e19 = 35.f * z2 - 30.f;                  \
+    (void)x2my2; (void)z2l; (void)a5; (void)a7; (void)b7; (void)c21; (void)e19;
 
 #define NEP_SH_TABLE(T)                                                                             \
     /* l = 1 */                                                                                     \
@@ -139,13 +166,13 @@ __host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float in
     T(3, xy, y, x, 0.f)                                                                             \
     T(4, yz, 0.f, z, y)                                                                             \
     T(5, xz, z, 0.f, x)                                                                             \
-    T(6, 3.f * z2 - 1.f, 0.f, 0.f, 6.f * z)                                                         \
+    T(6, fmaf(3.f, z2l, fmaf(3.f, z2, -1.f)), 0.f, 0.f, 6.f * z)                                                         \
     T(7, x2my2, 2.f * x, -2.f * y, 0.f)                                                             \
     /* l = 3 */                                                                                     \
     T(8, y * (3.f * x2 - y2), 6.f * xy, 3.f * x2my2, 0.f)                                           \
     T(9, xy * z, yz, xz, xy)                                                                        \
     T(10, y * a5, 0.f, a5, 10.f * yz)                                                               \
-    T(11, z * (5.f * z2 - 3.f), 0.f, 0.f, 15.f * z2 - 3.f)                                          \
+    T(11, z * fmaf(5.f, z2l, fmaf(5.f, z2, -3.f)), 0.f, 0.f, 15.f * z2 - 3.f)                                          \
     T(12, x * a5, a5, 0.f, 10.f * xz)                                                               \
     T(13, z * x2my2, 2.f * xz, -2.f * yz, x2my2)                                                    \
     T(14, x * (x2 - 3.f * y2), 3.f * x2my2, -6.f * xy, 0.f)                                         \
@@ -154,7 +181,7 @@ __host__ __device__ __forceinline__ void radial_g_dg(float d, float rc, float in
     T(16, yz * (3.f * x2 - y2), 6.f * xy * z, 3.f * z * x2my2, y * (3.f * x2 - y2))                  \
     T(17, xy * a7, y * a7, x * a7, 14.f * xy * z)                                                   \
     T(18, yz * b7, 0.f, z * b7, y * c21)                                                            \
-    T(19, z2 * (35.f * z2 - 30.f) + 3.f, 0.f, 0.f, z * (140.f * z2 - 60.f))                         \
+    T(19, fmaf(z2, e19, fmaf(z2l, e19, 3.f)), 0.f, 0.f, z * (140.f * z2 - 60.f))                         \
     T(20, xz * b7, z * b7, 0.f, x * c21)                                                            \
     T(21, x2my2 * a7, 2.f * x * a7, -2.f * y * a7, 14.f * z * x2my2)                                \
     T(22, xz * (x2 - 3.f * y2), 3.f * z * x2my2, -6.f * xy * z, x * (x2 - 3.f * y2))                 \
@@ -229,7 +256,7 @@ __host__ __device__ __forceinline__ void sh_term(const Harm& A, const float2 (&g
 __host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const Harm& A, const float2 (&gd)[kNA],
                                                   float& B, float2& Vxy, float& Vz)
 {
-    NEP_SH_LOCALS(x, y, z)
+    NEP_SH_LOCALS_FAST(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) sh_term(A, gd, lm, Yv, gx, gy, gz, B, Vxy, Vz);
     NEP_SH_TABLE(NEP_T)
 #undef NEP_T
@@ -238,7 +265,7 @@ __host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, con
 // All 24 harmonics and their (unprojected) gradients.
 __host__ __device__ __forceinline__ void sh_eval(float x, float y, float z, float (&Y)[kLM], float (&dY)[kLM][3])
 {
-    NEP_SH_LOCALS(x, y, z)
+    NEP_SH_LOCALS_FAST(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) \
     Y[lm] = Yv;                   \
     dY[lm][0] = gx;               \
@@ -246,14 +273,6 @@ __host__ __device__ __forceinline__ void sh_eval(float x, float y, float z, floa
     dY[lm][2] = gz;
     NEP_SH_TABLE(NEP_T)
 #undef NEP_T
-}
-
-// Error-free sum: s + e == a + b exactly (Knuth's TwoSum).
-__host__ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
 }
 
 // One neuron's compensated (Kahan) pre-activation a - ca = sum_v row_v q_v - b1:
@@ -359,6 +378,36 @@ struct PfOut {
     size_t comp_stride;
 };
 
+// Unit vector r / |r| with each component rounded once from a near-exact
+// value.  The solid harmonics of degree l scale as |u|^l, so an error delta
+// in the length of u enters every harmonic sum of that pair as l * delta: the
+// plain r * (1 / sqrtf(d2)) is off in length by up to ~2.5 ulp, which
+// carried into q_nl (Eq. 13) and the site energy at the 1e-6 eV level.  Here
+// d2 is an unevaluated sum (exact squares, compensated additions), 1/|r| is
+// one Newton step from the FP32 reciprocal square root evaluated in that
+// precision and kept as hi + lo, and each component is r_a (hi + lo) with a
+// single final rounding.
+__host__ __device__ __forceinline__ void unit_vector(float rx, float ry, float rz, float& ux, float& uy, float& uz)
+{
+    const float px = rx * rx, py = ry * ry, pz = rz * rz;
+    const float ex = fmaf(rx, rx, -px), ey = fmaf(ry, ry, -py), ez = fmaf(rz, rz, -pz);
+    float s1, t1, sh, t2;
+    two_sum(px, py, s1, t1);
+    two_sum(s1, pz, sh, t2);
+    const float sl = ((t1 + t2) + (ex + ey)) + ez;  // |r|^2 = sh + sl
+    const float y0 = 1.f / sqrtf(sh);
+    // residual 1 - |r|^2 y0^2, with sh * y0 * y0 split exactly into b + be + ae * y0
+    const float a = sh * y0, ae = fmaf(sh, y0, -a);
+    const float b = a * y0, be = fmaf(a, y0, -b);
+    const float res = fmaf(-ae, y0, (1.f - b) - be) - sl * y0 * y0;
+    const float yh = fmaf(0.5f * y0, res, y0);
+    const float yl = fmaf(0.5f * y0, res, y0 - yh);  // 1/|r| = yh + yl
+    const float qx = rx * yh, qy = ry * yh, qz = rz * yh;
+    ux = qx + fmaf(rx, yl, fmaf(rx, yh, -qx));
+    uy = qy + fmaf(ry, yl, fmaf(ry, yh, -qy));
+    uz = qz + fmaf(rz, yl, fmaf(rz, yh, -qz));
+}
+
 // Pass 1 of atom i: the descriptor vector q (Eqs. 12-13 through the harmonic
 // sums) and the harmonic sums S_nlm themselves.  Every lane of a warp must
 // call it (inactive lanes pass cnt = 0): the ranks are walked in step.
@@ -412,12 +461,13 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
         }
         if (d2 < P.rcA2) {
             const float d = sqrtf(d2);
-            const float inv = 1.f / d;
             float g[kNA];
             radial_g<kNA>(d, P.rcA, P.inv_rcA, g, w);
             float2 g2[kNA2];
             pair_orders(g, g2);
-            sh_pass1(rx * inv, ry * inv, rz * inv, g2, S);
+            float ux, uy, uz;
+            unit_vector(rx, ry, rz, ux, uy, uz);
+            sh_pass1(ux, uy, uz, g2, S);
         }
     }
 

@@ -195,10 +195,11 @@ __global__ void k_ds_site(int N, const int* __restrict__ sid, const Box* __restr
         if (d2 < rcA2) {
             float g[kNA];
             radial_g<kNA>(d, rcA, inv_rcA, g, wz);
-            const float inv = 1.f / d;
             float2 g2[kNA2];
             pair_orders(g, g2);
-            sh_pass1(rx * inv, ry * inv, rz * inv, g2, S);
+            float ux, uy, uz;
+            unit_vector(rx, ry, rz, ux, uy, uz);
+            sh_pass1(ux, uy, uz, g2, S);
         }
     }
     float q[kNdes];
