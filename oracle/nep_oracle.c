@@ -968,6 +968,26 @@ void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, con
         }
 }
 
+/*
+ * Quantum correction of a classical spectral conductivity (Sec. IV.C):
+ * kappa_q(w) = kappa(w) x^2 e^x / (e^x - 1)^2 with x = hbar w / (k_B T),
+ * here x = x_per_omega * omega[k].  The factor is written as the paper states
+ * it, with expm1 for the denominator; its limit 1 at x = 0.  spec [n_omega][3]
+ * is scaled in place.
+ */
+void orc_shc_quantum(int n_omega, const double* omega, double x_per_omega, double* spec)
+{
+    for (int k = 0; k < n_omega; ++k) {
+        const double x = fabs(x_per_omega * omega[k]);
+        double f = 1.0;
+        if (x > 0.0) {
+            const double em1 = expm1(x);
+            f = x * x * exp(x) / (em1 * em1);
+        }
+        for (int a = 0; a < 3; ++a) spec[3 * k + a] *= f;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Loss function, Eqs. 29-34.                                                */
 /* ------------------------------------------------------------------------ */

@@ -65,6 +65,8 @@ int orc_force_loss_grad_z(const orc_hyper* h, const double* z, int n_struct, con
 void orc_shc(int n, int n_samples, int n_lags, const double* W_hist, const double* v_hist, double* K_sum);
 void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, const double* omega, double scale,
                       int window, double* out);
+/* kappa(w) x^2 e^x / (e^x - 1)^2 with x = x_per_omega * omega, in place on spec [n_omega][3]. */
+void orc_shc_quantum(int n_omega, const double* omega, double x_per_omega, double* spec);
 int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms, const double* boxes,
              const double* pos, const double* e_tar, const double* f_tar, const double* w_tar,
              const double* lambdas, double* out);

@@ -93,6 +93,7 @@ def _load():
             "orc_force_loss_grad_z": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D]),
             "orc_shc": (None, [C.c_int, C.c_int, C.c_int, _D, _D, _D]),
             "orc_shc_spectrum": (None, [C.c_int, _D, C.c_double, C.c_int, _D, C.c_double, C.c_int, _D]),
+            "orc_shc_quantum": (None, [C.c_int, _D, C.c_double, _D]),
             "orc_loss": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D]),
             "orc_force_loss_grad": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D]),
             "orc_snes_utilities": (None, [C.c_int, _D]),
@@ -321,6 +322,16 @@ def shc_spectrum(K, dt_s: float, omega, scale: float = 1.0, window: bool = False
     out = np.zeros((om.shape[0], 3))
     _load().orc_shc_spectrum(K.shape[0], _d(K), float(dt_s), om.shape[0], _d(om), float(scale), 1 if window else 0,
                              _d(out))
+    return out
+
+
+def shc_quantum(spec, omega, x_per_omega: float):
+    """The quantum-corrected spectrum kappa(w) x^2 e^x / (e^x - 1)^2,
+    x = x_per_omega * w (Sec. IV.C): spec (n_omega, 3) at the frequencies
+    omega; returns a new array."""
+    out = _f64(spec, (-1, 3)).copy()
+    om = _f64(omega, (-1,))
+    _load().orc_shc_quantum(om.shape[0], _d(om), float(x_per_omega), _d(out))
     return out
 
 

@@ -98,3 +98,50 @@ def test_transform_on_the_dct_grid_is_scipy_dct1(window):
         Kw *= (0.5 * (1.0 + np.cos(np.pi * np.arange(M) / (M - 1))))[:, None]
     want = 0.7 * dt * dct(Kw, type=1, axis=0)
     assert np.allclose(out, want, rtol=1e-12, atol=1e-12)
+
+
+def test_quantum_factor_is_the_oscillator_heat_capacity():
+    """The quantum correction factor at x = hbar w / (k_B T) is the heat
+    capacity of one quantum harmonic oscillator in units of k_B: the T
+    derivative of its mean thermal energy hbar w / (e^{hbar w / k_B T} - 1).
+    Checked by a central difference in the reduced temperature theta = 1/x
+    (energy in units of hbar w), and by the two limits: 1 - x^2/12 + x^4/240
+    at high temperature, x^2 e^{-x} at low temperature."""
+    from oracle import oracle as orc
+    xs = np.array([1e-3, 0.05, 0.3, 1.0, 2.5, 7.0, 15.0])
+    spec = np.ones((len(xs), 3))
+    f = orc.shc_quantum(spec, xs, 1.0)[:, 0]
+
+    def energy(theta):
+        return 1.0 / np.expm1(1.0 / theta)
+
+    for x, fx in zip(xs, f):
+        th, h = 1.0 / x, 1e-5 / x
+        c = (energy(th + h) - energy(th - h)) / (2 * h)
+        assert fx == pytest.approx(c, rel=1e-7)
+    small = np.array([1e-4, 1e-3, 1e-2])
+    fs = orc.shc_quantum(np.ones((3, 3)), small, 1.0)[:, 0]
+    assert np.allclose(fs, 1 - small**2 / 12 + small**4 / 240, rtol=1e-14, atol=0)
+    big = np.array([40.0, 60.0])
+    fb = orc.shc_quantum(np.ones((2, 3)), big, 1.0)[:, 0]
+    assert np.allclose(fb, big**2 * np.exp(-big), rtol=1e-12)
+    # x = 0 (w = 0) is the classical limit, and the factor is even in w
+    assert np.array_equal(orc.shc_quantum(np.ones((1, 3)), [0.0], 3.0), np.ones((1, 3)))
+    assert np.array_equal(orc.shc_quantum(spec, -xs, 1.0), orc.shc_quantum(spec, xs, 1.0))
+
+
+def test_quantum_corrected_flat_spectrum_integrates_to_pi2_over_3():
+    """A flat classical spectrum kappa(w) = 1 corrected and integrated over
+    x = hbar w / k_B T gives int_0^inf x^2 e^x / (e^x - 1)^2 dx = pi^2 / 3;
+    the per-row scaling leaves the three components and their ratios alone."""
+    from scipy.integrate import simpson
+
+    from oracle import oracle as orc
+    x = np.linspace(0.0, 60.0, 60001)
+    spec = np.tile([1.0, 2.0, -0.5], (len(x), 1))
+    f = orc.shc_quantum(spec, x, 1.0)
+    assert simpson(f[:, 0], x=x) == pytest.approx(np.pi**2 / 3, rel=1e-9)
+    assert np.allclose(f[:, 1], 2.0 * f[:, 0]) and np.allclose(f[:, 2], -0.5 * f[:, 0])
+    # omega in other units: x_per_omega scales the argument
+    g = orc.shc_quantum(spec[:5], x[:5] * 4.0, 0.25)
+    assert np.allclose(g, f[:5], rtol=1e-15)
