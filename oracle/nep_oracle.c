@@ -971,9 +971,10 @@ void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, con
 /*
  * Quantum correction of a classical spectral conductivity (Sec. IV.C):
  * kappa_q(w) = kappa(w) x^2 e^x / (e^x - 1)^2 with x = hbar w / (k_B T),
- * here x = x_per_omega * omega[k].  The factor is written as the paper states
- * it, with expm1 for the denominator; its limit 1 at x = 0.  spec [n_omega][3]
- * is scaled in place.
+ * here x = x_per_omega * omega[k].  The factor is the paper's with numerator
+ * and denominator multiplied by e^{-2x}, x^2 e^{-x} / (1 - e^{-x})^2, so that
+ * e^x cannot overflow, and expm1 for the denominator; its limit 1 at x = 0.
+ * spec [n_omega][3] is scaled in place.
  */
 void orc_shc_quantum(int n_omega, const double* omega, double x_per_omega, double* spec)
 {
@@ -981,8 +982,8 @@ void orc_shc_quantum(int n_omega, const double* omega, double x_per_omega, doubl
         const double x = fabs(x_per_omega * omega[k]);
         double f = 1.0;
         if (x > 0.0) {
-            const double em1 = expm1(x);
-            f = x * x * exp(x) / (em1 * em1);
+            const double em = -expm1(-x); /* 1 - e^{-x} */
+            f = x * x * exp(-x) / (em * em);
         }
         for (int a = 0; a < 3; ++a) spec[3 * k + a] *= f;
     }

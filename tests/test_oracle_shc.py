@@ -122,8 +122,8 @@ def test_quantum_factor_is_the_oscillator_heat_capacity():
     small = np.array([1e-4, 1e-3, 1e-2])
     fs = orc.shc_quantum(np.ones((3, 3)), small, 1.0)[:, 0]
     assert np.allclose(fs, 1 - small**2 / 12 + small**4 / 240, rtol=1e-14, atol=0)
-    big = np.array([40.0, 60.0])
-    fb = orc.shc_quantum(np.ones((2, 3)), big, 1.0)[:, 0]
+    big = np.array([40.0, 60.0, 800.0])
+    fb = orc.shc_quantum(np.ones((3, 3)), big, 1.0)[:, 0]
     assert np.allclose(fb, big**2 * np.exp(-big), rtol=1e-12)
     # x = 0 (w = 0) is the classical limit, and the factor is even in w
     assert np.array_equal(orc.shc_quantum(np.ones((1, 3)), [0.0], 3.0), np.ones((1, 3)))
