@@ -238,6 +238,16 @@ int nep_md_get_shc(nep_md* md, double* K, long long* n_samples, void* stream);
  */
 int nep_shc_spectrum(const double* K, int n_lags, double dt_lag, int n_omega, const double* omega, double scale,
                      int window, double* out, void* stream);
+/*
+ * nep_shc_quantum -- the quantum correction of a classical spectral
+ * conductivity (Sec. IV.C): spec[k][a] *= x^2 e^x / (e^x - 1)^2 with
+ * x = x_per_omega * omega[k] (x_per_omega = hbar / (k_B T) in the time unit of
+ * 1/omega), in place; 1 at omega = 0, even in omega.
+ *   omega dev [n_omega]; spec dev [n_omega][3].  All FP64.
+ * Errors: NEP_ERR_ARG (NULL pointers, n_omega < 1, x_per_omega not finite),
+ * NEP_ERR_CUDA.
+ */
+int nep_shc_quantum(const double* omega, int n_omega, double x_per_omega, double* spec, void* stream);
 
 /* Number of neighbour-list builds so far (synchronises `stream`). */
 int nep_md_rebuild_count(nep_md* md, long long* count, void* stream);

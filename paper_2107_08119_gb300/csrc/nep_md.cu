@@ -206,6 +206,28 @@ __global__ void k_shc_spectrum(int n_lags, const double* __restrict__ K, double 
     out[e] = scale * 2.0 * dt * s;
 }
 
+// spec[k][.] *= (h / sinh h)^2 with h = x/2, x = x_per_omega omega[k]: the
+// quantum-correction factor x^2 e^x / (e^x - 1)^2 of Sec. IV.C in a form with
+// no cancellation at small x (1 - h^2/3 below h = 1e-4, where FP64 sinh(h)/h
+// has nothing left to resolve) and none at large x (sinh overflows to inf and
+// the factor to 0).
+__global__ void k_shc_quantum(int n_omega, const double* __restrict__ omega, double x_per_omega,
+                              double* __restrict__ spec)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_omega) return;
+    const double h = fabs(0.5 * x_per_omega * omega[k]);
+    double f;
+    if (h < 1e-4) {
+        f = 1.0 - h * h / 3.0;
+    } else {
+        const double r = h / sinh(h);
+        f = r * r;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) spec[(size_t)k * 3 + a] *= f;
+}
+
 // v *= lambda (the Berendsen factor k_md_finish left in red[14])
 __global__ void k_scale_v(int n, double* __restrict__ vel, const double* __restrict__ red)
 {
@@ -487,6 +509,16 @@ int nep_shc_spectrum(const double* K, int n_lags, double dt_lag, int n_omega, co
     k_shc_spectrum<<<(e + 127) / 128, 128, 0, (cudaStream_t)stream>>>(n_lags, K, dt_lag, n_omega, omega, scale,
                                                                       window ? 1 : 0, out);
     return cuda_fail(cudaGetLastError(), "nep_shc_spectrum");
+}
+
+int nep_shc_quantum(const double* omega, int n_omega, double x_per_omega, double* spec, void* stream)
+{
+    if (!omega || !spec || n_omega < 1 || !std::isfinite(x_per_omega)) {
+        set_error("nep_shc_quantum: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    k_shc_quantum<<<(n_omega + 127) / 128, 128, 0, (cudaStream_t)stream>>>(n_omega, omega, x_per_omega, spec);
+    return cuda_fail(cudaGetLastError(), "nep_shc_quantum");
 }
 
 int nep_md_invalidate(nep_md* md)

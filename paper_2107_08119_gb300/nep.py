@@ -75,6 +75,7 @@ _SIGNATURES = {
     "nep_dataset_create_species": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.POINTER(_vp)]),
     "nep_md_get_shc": (C.c_int, [_vp, _vp, C.POINTER(C.c_longlong), _vp]),
     "nep_shc_spectrum": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, C.c_double, C.c_int, _vp, _vp]),
+    "nep_shc_quantum": (C.c_int, [_vp, C.c_int, C.c_double, _vp, _vp]),
     "nep_dataset_set_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_get_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_tune": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(C.c_float), _vp]),
@@ -511,16 +512,37 @@ def shc_spectrum(K, dt_lag: float, omega, scale: float = 1.0, window: bool = Fal
     return out
 
 
-def kappa_spectrum(K, dt_lag_fs: float, nu_thz, temperature: float, volume: float, fe: float, window: bool = True):
+def shc_quantum(spec, omega, x_per_omega: float, stream=None):
+    """Quantum correction of Sec. IV.C on the device, in place: spec[k] *=
+    x^2 e^x / (e^x - 1)^2 with x = x_per_omega * omega[k].  spec: CUDA
+    float64 (n_omega, 3); omega: CUDA float64 (n_omega,).  Returns spec."""
+    if not (spec.is_cuda and spec.dtype == torch.float64 and spec.is_contiguous() and omega.is_cuda
+            and omega.dtype == torch.float64 and omega.is_contiguous() and spec.shape == (omega.numel(), 3)):
+        raise ValueError("spec (n, 3) and omega (n,) must be contiguous CUDA float64 tensors")
+    _check(_lib.nep_shc_quantum(_ptr(omega), omega.numel(), float(x_per_omega), _ptr(spec), _stream(stream)),
+           "nep_shc_quantum")
+    return spec
+
+
+HBAR_EV_FS = 0.6582119569  # reduced Planck constant, eV fs
+K_B_EV = 8.617333262e-5    # Boltzmann constant, eV/K
+
+
+def kappa_spectrum(K, dt_lag_fs: float, nu_thz, temperature: float, volume: float, fe: float, window: bool = True,
+                   quantum: bool = False):
     """Spectral thermal conductivity kappa(nu) in W / (m K THz) at frequencies
     nu (THz, CUDA float64) from K in eV A/fs at lags dt_lag_fs apart, for a
     driving force fe (1/A) along the direction of interest, temperature (K)
     and volume (A^3): kappa(w) = (2 / (T V F_e)) int K e^{iwt} dt, with
-    int_0^inf kappa(w) dw / (2 pi) the HNEMD conductivity."""
+    int_0^inf kappa(w) dw / (2 pi) the HNEMD conductivity.  quantum=True
+    applies the correction factor of Sec. IV.C at that temperature."""
     omega = 2.0 * np.pi * nu_thz * 1e-3  # rad/fs
     # eV / (A fs K) -> W / (m K) is 1.602176634e6; per THz of nu = w / (2 pi): times 1e-3 (fs -> ps)
     scale = 2.0 / (temperature * volume * fe) * 1.602176634e6 * 1e-3
-    return shc_spectrum(K, dt_lag_fs, omega, scale, window)
+    out = shc_spectrum(K, dt_lag_fs, omega, scale, window)
+    if quantum:
+        shc_quantum(out, omega, HBAR_EV_FS / (K_B_EV * temperature))
+    return out
 
 
 class SNES:

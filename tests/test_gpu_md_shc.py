@@ -96,3 +96,32 @@ def test_shc_errors(N):
         md.shc()
     md.close()
     model.close()
+
+
+def test_quantum_correction_matches_oracle(N):
+    """nep_shc_quantum (h / sinh h)^2 against the oracle's x^2 e^x / (e^x - 1)^2
+    (pinned in test_oracle_shc.py) over x from 0 through the small-h branch
+    to underflow, negative frequencies included; and kappa_spectrum's quantum
+    option is the classical spectrum times that factor at hbar / (k_B T)."""
+    import torch
+
+    from oracle import oracle as orc
+    rng = np.random.default_rng(9)
+    x = np.concatenate([[0.0, 1e-9, 1e-5, 1.99e-4, 2.01e-4], np.linspace(0.01, 80.0, 300), [700.0, 1500.0, 4000.0]])
+    omega = np.concatenate([x, -x[1:20]]) / 0.37
+    spec = rng.normal(size=(len(omega), 3))
+    want = orc.shc_quantum(spec, omega, 0.37)
+    got = N.shc_quantum(torch.tensor(spec, device="cuda"), torch.tensor(omega, device="cuda"), 0.37).cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-300)
+    assert np.array_equal(got[0], spec[0])
+    with pytest.raises(N.NepError):
+        N.shc_quantum(torch.tensor(spec, device="cuda"), torch.tensor(omega, device="cuda"), float("nan"))
+    # through kappa_spectrum at 300 K: 0.5-40 THz, window on
+    K = torch.tensor(np.exp(-np.arange(200) / 30.0)[:, None] * [1.0, 0.5, 0.2], device="cuda")
+    nu = torch.linspace(0.0, 40.0, 81, dtype=torch.float64, device="cuda")
+    cl = N.kappa_spectrum(K, 2.0, nu, 300.0, 2e4, 1e-4).cpu().numpy()
+    qc = N.kappa_spectrum(K, 2.0, nu, 300.0, 2e4, 1e-4, quantum=True).cpu().numpy()
+    w = 2 * np.pi * nu.cpu().numpy() * 1e-3
+    xq = N.HBAR_EV_FS / (N.K_B_EV * 300.0)
+    assert np.allclose(qc, orc.shc_quantum(cl, w, xq), rtol=1e-12, atol=0)
+    assert (np.abs(qc[1:]) < np.abs(cl[1:])).all()  # the factor is below 1 for w > 0
