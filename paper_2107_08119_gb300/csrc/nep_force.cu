@@ -132,6 +132,8 @@ __global__ void k_reduce(const double* __restrict__ partials, int nblocks, int n
     const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= ncomp) return;
     double s = 0.0;
+    // unrolled so that eight loads are in flight ahead of the (ordered) adds
+#pragma unroll 8
     for (int b = lane; b < nblocks; b += 32) s += partials[(size_t)b * ncomp + k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);

@@ -254,6 +254,8 @@ __global__ void k_md_finish(const double* __restrict__ part_e, int nb_e, const d
         const int nb = w == 0 ? nb_e : nb_x;
         const int stride = w == 0 ? 1 : ncomp_x;
         double v = 0.0;
+        // unrolled so that eight loads are in flight ahead of the (ordered) adds
+#pragma unroll 8
         for (int b = lane; b < nb; b += 32) v += src[(size_t)b * stride];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
