@@ -860,7 +860,7 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
     const int p = blockIdx.x * blockDim.x + t;
     if (p >= n_par) return;
     float gm = 0.f, gs = 0.f;
-    constexpr int kBatch = 10;  // draws loaded together, then summed in rank order
+    constexpr int kBatch = 25;  // draws loaded together (two rounds for 50 members), then summed in rank order
     for (int q0 = 0; q0 < P; q0 += kBatch) {
         float rv[kBatch];
 #pragma unroll
