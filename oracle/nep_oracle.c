@@ -989,6 +989,22 @@ void orc_shc_quantum(int n_omega, const double* omega, double x_per_omega, doubl
     }
 }
 
+/*
+ * Running HNEMD conductivity estimate (Sec. II.B): <J>/(T V) = kappa F_e, so
+ * with scale = 1 / (T V F_e) the estimate after step t is scale times the
+ * mean of J over steps 0..t.  J [n][3]; out [n][3]; the sums run in step
+ * order.
+ */
+void orc_hnemd_kappa(int n, const double* J, double scale, double* out)
+{
+    double sum[3] = {0.0, 0.0, 0.0};
+    for (int t = 0; t < n; ++t)
+        for (int a = 0; a < 3; ++a) {
+            sum[a] += J[3 * t + a];
+            out[3 * t + a] = scale * sum[a] / (double)(t + 1);
+        }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Loss function, Eqs. 29-34.                                                */
 /* ------------------------------------------------------------------------ */

@@ -67,6 +67,8 @@ void orc_shc_spectrum(int n_lags, const double* K, double dt_s, int n_omega, con
                       int window, double* out);
 /* kappa(w) x^2 e^x / (e^x - 1)^2 with x = x_per_omega * omega, in place on spec [n_omega][3]. */
 void orc_shc_quantum(int n_omega, const double* omega, double x_per_omega, double* spec);
+/* Running HNEMD estimate: out[t] = scale * mean of J[0..t] (J, out [n][3]). */
+void orc_hnemd_kappa(int n, const double* J, double scale, double* out);
 int orc_loss(const orc_hyper* h, const double* z, int n_struct, const int* n_atoms, const double* boxes,
              const double* pos, const double* e_tar, const double* f_tar, const double* w_tar,
              const double* lambdas, double* out);

@@ -94,6 +94,7 @@ def _load():
             "orc_shc": (None, [C.c_int, C.c_int, C.c_int, _D, _D, _D]),
             "orc_shc_spectrum": (None, [C.c_int, _D, C.c_double, C.c_int, _D, C.c_double, C.c_int, _D]),
             "orc_shc_quantum": (None, [C.c_int, _D, C.c_double, _D]),
+            "orc_hnemd_kappa": (None, [C.c_int, _D, C.c_double, _D]),
             "orc_loss": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D, _D, _D]),
             "orc_force_loss_grad": (C.c_int, [_H, _D, C.c_int, _I, _D, _D, _D, _D, _D]),
             "orc_snes_utilities": (None, [C.c_int, _D]),
@@ -332,6 +333,15 @@ def shc_quantum(spec, omega, x_per_omega: float):
     out = _f64(spec, (-1, 3)).copy()
     om = _f64(omega, (-1,))
     _load().orc_shc_quantum(om.shape[0], _d(om), float(x_per_omega), _d(out))
+    return out
+
+
+def hnemd_kappa(J, scale: float):
+    """Running HNEMD conductivity estimate (Sec. II.B): scale times the mean
+    of the heat current J (n, 3) over steps 0..t, for every t."""
+    J = _f64(J, (-1, 3))
+    out = np.zeros_like(J)
+    _load().orc_hnemd_kappa(J.shape[0], _d(J), float(scale), _d(out))
     return out
 
 

@@ -145,3 +145,18 @@ def test_quantum_corrected_flat_spectrum_integrates_to_pi2_over_3():
     # omega in other units: x_per_omega scales the argument
     g = orc.shc_quantum(spec[:5], x[:5] * 4.0, 0.25)
     assert np.allclose(g, f[:5], rtol=1e-15)
+
+
+def test_running_hnemd_estimate_closed_forms():
+    """The running estimate scale * mean(J[0..t]): a constant current gives the
+    constant; J_t = t gives t / 2; an alternating +-1 gives 1/(t+1) after even
+    steps and 0 after odd ones; the three components are independent."""
+    from oracle import oracle as orc
+    n = 101
+    t = np.arange(n, dtype=float)
+    J = np.stack([np.full(n, 2.5), t, (-1.0) ** t], axis=1)
+    k = orc.hnemd_kappa(J, 0.4)
+    assert np.allclose(k[:, 0], 0.4 * 2.5, rtol=1e-15)
+    assert np.allclose(k[:, 1], 0.4 * t / 2, rtol=1e-15, atol=0)
+    want = np.where(t % 2 == 0, 1.0 / (t + 1), 0.0) * 0.4
+    assert np.allclose(k[:, 2], want, rtol=1e-14, atol=1e-16)
