@@ -248,6 +248,16 @@ int nep_shc_spectrum(const double* K, int n_lags, double dt_lag, int n_omega, co
  * NEP_ERR_CUDA.
  */
 int nep_shc_quantum(const double* omega, int n_omega, double x_per_omega, double* spec, void* stream);
+/*
+ * nep_hnemd_kappa -- running HNEMD conductivity estimate (Sec. II.B):
+ * <J>/(T V) = kappa F_e, so out[t][a] = scale * (sum_{s<=t} J[s][a]) / (t+1)
+ * with scale = 1 / (T V F_e) in the caller's units.  The sums are FP64 in a
+ * fixed order (contiguous segments, then their prefix), so the result is
+ * reproducible bit for bit.
+ *   J dev [n][3] (e.g. the heat series of nep_md_step); out dev [n][3].
+ * Errors: NEP_ERR_ARG (NULL pointers, n < 1), NEP_ERR_CUDA.
+ */
+int nep_hnemd_kappa(const double* J, int n, double scale, double* out, void* stream);
 
 /* Number of neighbour-list builds so far (synchronises `stream`). */
 int nep_md_rebuild_count(nep_md* md, long long* count, void* stream);

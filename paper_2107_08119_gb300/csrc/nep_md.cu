@@ -228,6 +228,45 @@ __global__ void k_shc_quantum(int n_omega, const double* __restrict__ omega, dou
     for (int a = 0; a < 3; ++a) spec[(size_t)k * 3 + a] *= f;
 }
 
+// Running mean of J times scale: thread t of one block owns a contiguous
+// segment of steps; the segment sums are prefixed in order by thread 0, and
+// each thread then walks its segment again from its offset.
+constexpr int kKappaThreads = 256;
+__global__ void __launch_bounds__(kKappaThreads) k_hnemd_kappa(int n, const double* __restrict__ J, double scale,
+                                                               double* __restrict__ out)
+{
+    __shared__ double seg[kKappaThreads][3];
+    const int t = threadIdx.x;
+    const int per = (n + kKappaThreads - 1) / kKappaThreads;
+    const int a = min(n, t * per), b = min(n, a + per);
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int i = a; i < b; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s[c] += J[(size_t)i * 3 + c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) seg[t][c] = s[c];
+    __syncthreads();
+    if (t == 0) {
+        double run[3] = {0.0, 0.0, 0.0};
+        for (int u = 0; u < kKappaThreads; ++u)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double x = seg[u][c];
+                seg[u][c] = run[c];
+                run[c] += x;
+            }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s[c] = seg[t][c];
+    for (int i = a; i < b; ++i)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            s[c] += J[(size_t)i * 3 + c];
+            out[(size_t)i * 3 + c] = scale * s[c] / (double)(i + 1);
+        }
+}
+
 // v *= lambda (the Berendsen factor k_md_finish left in red[14])
 __global__ void k_scale_v(int n, double* __restrict__ vel, const double* __restrict__ red)
 {
@@ -521,6 +560,16 @@ int nep_shc_quantum(const double* omega, int n_omega, double x_per_omega, double
     }
     k_shc_quantum<<<(n_omega + 127) / 128, 128, 0, (cudaStream_t)stream>>>(n_omega, omega, x_per_omega, spec);
     return cuda_fail(cudaGetLastError(), "nep_shc_quantum");
+}
+
+int nep_hnemd_kappa(const double* J, int n, double scale, double* out, void* stream)
+{
+    if (!J || !out || n < 1) {
+        set_error("nep_hnemd_kappa: bad arguments");
+        return NEP_ERR_ARG;
+    }
+    k_hnemd_kappa<<<1, kKappaThreads, 0, (cudaStream_t)stream>>>(n, J, scale, out);
+    return cuda_fail(cudaGetLastError(), "nep_hnemd_kappa");
 }
 
 int nep_md_invalidate(nep_md* md)

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "nep_md_get_shc": (C.c_int, [_vp, _vp, C.POINTER(C.c_longlong), _vp]),
     "nep_shc_spectrum": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, C.c_double, C.c_int, _vp, _vp]),
     "nep_shc_quantum": (C.c_int, [_vp, C.c_int, C.c_double, _vp, _vp]),
+    "nep_hnemd_kappa": (C.c_int, [_vp, C.c_int, C.c_double, _vp, _vp]),
     "nep_dataset_set_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_get_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_tune": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(C.c_float), _vp]),
@@ -522,6 +523,21 @@ def shc_quantum(spec, omega, x_per_omega: float, stream=None):
     _check(_lib.nep_shc_quantum(_ptr(omega), omega.numel(), float(x_per_omega), _ptr(spec), _stream(stream)),
            "nep_shc_quantum")
     return spec
+
+
+def hnemd_kappa(J, temperature: float, volume: float, fe: float, scale: float = None, stream=None):
+    """Running HNEMD conductivity estimate on the device (Sec. II.B):
+    kappa(t) = <J>_{0..t} / (T V F_e) in W / (m K) for J in eV A/fs (the heat
+    series of MD.step), T in K, V in A^3 and the driving force fe (1/A) along
+    the component of interest; `scale` overrides 1 / (T V F_e) and the unit
+    conversion.  J: CUDA float64 (n, 3).  Returns (n, 3)."""
+    if not (J.is_cuda and J.dtype == torch.float64 and J.is_contiguous() and J.dim() == 2 and J.shape[1] == 3):
+        raise ValueError("J must be a contiguous CUDA float64 (n, 3) tensor")
+    if scale is None:
+        scale = 1.602176634e6 / (temperature * volume * fe)  # eV / (A fs K) -> W / (m K)
+    out = torch.empty_like(J)
+    _check(_lib.nep_hnemd_kappa(_ptr(J), J.shape[0], float(scale), _ptr(out), _stream(stream)), "nep_hnemd_kappa")
+    return out
 
 
 HBAR_EV_FS = 0.6582119569  # reduced Planck constant, eV fs

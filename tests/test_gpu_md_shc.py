@@ -125,3 +125,20 @@ def test_quantum_correction_matches_oracle(N):
     xq = N.HBAR_EV_FS / (N.K_B_EV * 300.0)
     assert np.allclose(qc, orc.shc_quantum(cl, w, xq), rtol=1e-12, atol=0)
     assert (np.abs(qc[1:]) < np.abs(cl[1:])).all()  # the factor is below 1 for w > 0
+
+
+@pytest.mark.parametrize("n", [1, 7, 256, 1000, 4099])
+def test_running_hnemd_estimate_matches_oracle(N, n):
+    """nep_hnemd_kappa (segment sums, then their prefix) against the oracle's
+    sums in step order (pinned in test_oracle_shc.py), ragged lengths
+    included; and the W/(m K) conversion of hnemd_kappa."""
+    import torch
+
+    from oracle import oracle as orc
+    J = np.random.default_rng(n).normal(1.0, 3.0, size=(n, 3))
+    got = N.hnemd_kappa(torch.tensor(J, device="cuda"), 0, 0, 0, scale=0.37).cpu().numpy()
+    assert np.allclose(got, orc.hnemd_kappa(J, 0.37), rtol=1e-12, atol=1e-15)
+    k = N.hnemd_kappa(torch.tensor(J, device="cuda"), 300.0, 2.0e4, 1e-4).cpu().numpy()
+    assert np.allclose(k, orc.hnemd_kappa(J, 1.602176634e6 / (300.0 * 2.0e4 * 1e-4)), rtol=1e-12)
+    with pytest.raises(N.NepError):
+        N.hnemd_kappa(torch.zeros(0, 3, dtype=torch.float64, device="cuda"), 300.0, 1.0, 1.0)
