@@ -601,6 +601,17 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
 // Force and per-atom virial of atom i from the stored partial forces
 // (pf[k][i] float4 records, see nep_internal.cuh):
 //   F_i = sum_j (p_ij - p_ji),  W_i^{ab} = sum_j r_ij^a p_ji^b   (Eqs. 4-6).
+// Software-pipelined two slots deep: while slot k is summed, slot k+1's
+// neighbour position and both partial-force records are in flight (their
+// addresses came in one iteration earlier), and slot k+2's list and
+// reverse entries are being loaded, so no gather waits on the load of its
+// own address.  The sums run in slot order.
+struct AsmSlot {
+    int v;
+    float h[3], l[3];
+    float4 po, pq;
+};
+
 __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, float rc2max,
                                                        const int* __restrict__ count, const SlotTable& nbr,
                                                        const int* __restrict__ rev, const float* __restrict__ xh,
@@ -614,24 +625,43 @@ __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, 
     for (int a = 0; a < 3; ++a) F[a] = 0.f;
 #pragma unroll
     for (int a = 0; a < 9; ++a) W[a] = 0.f;
-    NbSlot nx;
-    fetch_slot(nbr, xh, xl, n, 0, cnt, nx);
+    const float4* pf4 = reinterpret_cast<const float4*>(pf);
+    // list value and reverse slot of slot k
+    auto load_idx = [&](int k, int& v, int& kr) {
+        if (k < cnt) {
+            v = nbr.slots[(size_t)k * nbr.stride + nbr.idx];
+            kr = NEP_LDG(rev + (size_t)k * n + i);
+        }
+    };
+    // the gathers of slot k, given its list value and reverse slot
+    auto load_data = [&](int k, int v, int kr, AsmSlot& d) {
+        if (k < cnt) {
+            const int j = v & 0xFFFFFF;
+            d.v = v;
+            load_pos(xh, xl, n, j, d.h, d.l);
+            d.po = NEP_LDG(pf4 + (size_t)k * n + i);
+            d.pq = NEP_LDG(pf4 + (size_t)kr * n + j);
+        }
+    };
+    int v1 = 0, kr1 = 0, v2 = 0, kr2 = 0;
+    load_idx(0, v1, kr1);
+    load_idx(1, v2, kr2);
+    AsmSlot nx;
+    load_data(0, v1, kr1, nx);
     for (int k = 0; k < cnt; ++k) {
-        const NbSlot cur = nx;
-        fetch_slot(nbr, xh, xl, n, k + 1, cnt, nx);
+        const AsmSlot cur = nx;
+        load_data(k + 1, v2, kr2, nx);
+        load_idx(k + 2, v2, kr2);
         const int j = cur.v & 0xFFFFFF;
         float r[3];
         pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, r[0], r[1], r[2]);
         const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
         if (!(d2 < rc2max)) continue;
-        const int kr = rev[(size_t)k * n + i];
         // own p_ij and the neighbour's p_ji: one 16-byte record each
-        const float4 po = NEP_LDG(reinterpret_cast<const float4*>(pf) + (size_t)k * n + i);
-        const float4 pq = NEP_LDG(reinterpret_cast<const float4*>(pf) + (size_t)kr * n + j);
-        const float pji[3] = {pq.x, pq.y, pq.z};
-        F[0] += po.x - pji[0];
-        F[1] += po.y - pji[1];
-        F[2] += po.z - pji[2];
+        const float pji[3] = {cur.pq.x, cur.pq.y, cur.pq.z};
+        F[0] += cur.po.x - pji[0];
+        F[1] += cur.po.y - pji[1];
+        F[2] += cur.po.z - pji[2];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
