@@ -53,3 +53,35 @@ def test_error_paths_need_no_gpu():
         raise AssertionError("expected NEP_ERR_ARG")
     except N.NepError as e:
         assert e.code == -1
+
+
+def test_analysis_entry_points_reject_bad_arguments_without_a_gpu():
+    """The spectral and HNEMD analysis calls check their arguments on the host
+    (NULL buffers, empty lengths, a non-finite x per omega) and return
+    NEP_ERR_ARG with a message, before any device work."""
+    import ctypes as C
+    import math
+
+    from paper_2107_08119_gb300 import build
+    build.build()
+    lib = C.CDLL(build.LIB)
+    lib.nep_last_error.restype = C.c_char_p
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    lib.nep_hnemd_kappa.argtypes = [vp, i, d, vp, vp]
+    lib.nep_shc_quantum.argtypes = [vp, i, d, vp, vp]
+    lib.nep_shc_spectrum.argtypes = [vp, i, d, i, vp, d, i, vp, vp]
+    fake = vp(64)  # never dereferenced: every call below fails its checks first
+    cases = [
+        lambda: lib.nep_hnemd_kappa(None, 5, 1.0, fake, None),
+        lambda: lib.nep_hnemd_kappa(fake, 0, 1.0, fake, None),
+        lambda: lib.nep_hnemd_kappa(fake, 5, 1.0, None, None),
+        lambda: lib.nep_shc_quantum(None, 4, 1.0, fake, None),
+        lambda: lib.nep_shc_quantum(fake, 0, 1.0, fake, None),
+        lambda: lib.nep_shc_quantum(fake, 4, math.nan, fake, None),
+        lambda: lib.nep_shc_quantum(fake, 4, math.inf, fake, None),
+        lambda: lib.nep_shc_spectrum(fake, 0, 1.0, 3, fake, 1.0, 0, fake, None),
+        lambda: lib.nep_shc_spectrum(fake, 8, 0.0, 3, fake, 1.0, 0, fake, None),
+    ]
+    for call in cases:
+        assert call() == -1  # NEP_ERR_ARG
+        assert lib.nep_last_error()
