@@ -280,6 +280,21 @@ const float* nep_md_forces(const nep_md* md);
 int nep_get_neighbors(nep_model* m, int n, int* count, int* nbr, void* stream);
 
 /*
+ * nep_cell_grid -- the cell grid the neighbour-list build uses for a box and
+ * list radius (host only; no CUDA call).  Each direction gets floor(L / r_list)
+ * cells, so every cell edge is at least r_list and the 27 cells around an
+ * atom's cell hold all its neighbours.  A grid of more than 2^22 cells (a
+ * large, sparse box) is coarsened by halving its longest direction until it
+ * fits; edges only grow, so the list stays exact.  Boxes with fewer than 3
+ * cells in some direction use the all-pairs search, reported as 0 0 0.
+ *   box9    host, 9 doubles (orthorhombic).
+ *   r_list  list radius (Angstrom), > 0.
+ *   nc      host, 3 ints: cells per direction.
+ * Errors: NEP_ERR_ARG, NEP_ERR_BOX (as nep_compute_efv).
+ */
+int nep_cell_grid(const double* box9, double r_list, int* nc);
+
+/*
  * Training set for the separable natural evolution strategy (Sec. II.D.2):
  * structures of uneven size evaluated together (Sec. II.E concatenates them
  * into one "super-structure").  nep_dataset_create copies the structures to
@@ -477,12 +492,18 @@ int nep_profile_read(nep_model* m, double* ms, long long* launches);
  * max(rc_R, rc_A); larger inputs return NEP_ERR_ARG.  The call allocates
  * nothing: no cudaMalloc, cudaFree or allocating library routine.
  *
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one array, which keeps
+ * The first call in each CUDA context looks up the array's device address
+ * (cudaGetSymbolAddress, with that context and its device current) and
+ * caches it under the context's id; make that first call before any stream
+ * capture.  A context created later (after cudaDeviceReset, or a caller's
+ * own driver-API context) is a new id, so its first call looks the address
+ * up again.  Every call shares the one array, which keeps
  * the previous call's contents (the parts that must start at zero are cleared
  * by the call itself); calls that overlap on the GPU -- on different streams,
  * or from host threads without ordering between them -- race on it.
+ * One species only: the multicomponent weights of nep_set_species have no
+ * input here, so every pair has weight 1 and n_par must be the
+ * single-species count (N_des + 2) N_neu + 1.
  *   hp          host, hyperparameters as for nep_create.
  *   z           dev, n_par FP32 parameters (layout as in nep_create).
  *   n, box9, pos, e_total, e_atom, force, virial_atom, virial_total, stream:

@@ -126,6 +126,7 @@ int setup_box(const double* box9, double r_list, Box& b)
                 return NEP_ERR_BOX;
             }
     bool cells = true;
+    long long nc[3] = {0, 0, 0};
     for (int d = 0; d < 3; ++d) {
         const double L = box9[4 * d];
         if (!(L > 0.0) || !std::isfinite(L)) {
@@ -138,12 +139,21 @@ int setup_box(const double* box9, double r_list, Box& b)
         }
         b.L[d] = L;
         split_hilo(L, b.Lh[d], b.Ll[d]);
-        b.nc[d] = (int)std::floor(L / r_list);
-        if (b.nc[d] < 3) cells = false;
+        // cells per direction, counted in 64 bits (L / r_list can exceed an int)
+        const double f = std::floor(L / r_list);
+        nc[d] = f > (double)kMaxCells ? (long long)kMaxCells : (long long)f;
+        if (nc[d] < 3) cells = false;
         b.img[d] = (int)std::ceil(r_list / L);
         if (b.img[d] > 2) b.img[d] = 2;
     }
-    if (!cells) b.nc[0] = b.nc[1] = b.nc[2] = 0;
+    // coarsen the grid until it has at most kMaxCells cells: halving the
+    // longest direction keeps every cell edge >= r_list, and a direction over
+    // the cube root of the cap (161) never drops below 3 cells
+    while (cells && nc[0] * nc[1] * nc[2] > (long long)kMaxCells) {
+        const int d = (nc[0] >= nc[1] && nc[0] >= nc[2]) ? 0 : (nc[1] >= nc[2] ? 1 : 2);
+        nc[d] = (nc[d] + 1) / 2;
+    }
+    for (int d = 0; d < 3; ++d) b.nc[d] = cells ? (int)nc[d] : 0;
     for (int d = 0; d < 3; ++d) b.cpl[d] = b.nc[d] / b.L[d];
     return NEP_OK;
 }
@@ -517,6 +527,19 @@ int nep_profile_read(nep_model* m, double* ms, long long* launches)
         if (ms) ms[k] = t[k];
         if (launches) launches[k] = c[k];
     }
+    return NEP_OK;
+}
+
+int nep_cell_grid(const double* box9, double r_list, int* nc)
+{
+    if (!nc || !(r_list > 0.0) || !std::isfinite(r_list)) {
+        set_error("nep_cell_grid: NULL output or a list radius that is not positive and finite");
+        return NEP_ERR_ARG;
+    }
+    Box b;
+    const int rc = setup_box(box9, r_list, b);
+    if (rc) return rc;
+    for (int d = 0; d < 3; ++d) nc[d] = b.nc[d];
     return NEP_OK;
 }
 

@@ -51,6 +51,11 @@ constexpr int kNdes = kNR + kNA * kLmax;  // 32
 constexpr int kMaxNeu = 64;
 constexpr int kMaxAtoms = (1 << 24) - 1;
 constexpr int kImgCenter = 62;       // image code of the zero shift
+// Largest cell grid of the list build (nc[0] nc[1] nc[2]).  A large, sparse
+// box would otherwise need more cells than an int counts; the grid is then
+// made coarser, which stays correct because every cell edge is still at
+// least the list radius.
+constexpr int kMaxCells = 1 << 22;
 
 // device error word bits
 enum : unsigned {

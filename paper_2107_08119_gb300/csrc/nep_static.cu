@@ -15,6 +15,8 @@
 // GPU that loads the library until the process exits).  Every call shares
 // the array, which keeps the previous call's contents; calls that overlap on
 // the GPU (different streams, or host threads without ordering) race on it.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "nep_internal.cuh"
@@ -49,30 +51,76 @@ constexpr size_t kStaticBytes = kOffErr + align256(sizeof(unsigned));
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// The array's device address belongs to a CUDA context (the module is loaded
+// once per context).  It is cached per context, keyed by the driver's context
+// id, which is unique for the life of the process: a new context -- after
+// cudaDeviceReset, or a caller's own driver-API context -- gets a new id and
+// a fresh lookup, never a stale address.  The two driver calls come through
+// the runtime's entry-point query, so the library needs no libcuda link.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
 
-// Device address of the array on the current device.  In host code the
+constexpr int kCachedContexts = 16;
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    unsigned char* addr;
+};
+std::mutex g_setup_mutex;
+ScratchEntry g_scratch_cache[kCachedContexts] = {};
+int g_scratch_next = 0;
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_driver_queried = false;
+
+// Id of the calling thread's current context, 0 if none is current or the
+// driver calls are unavailable.  Caller holds g_setup_mutex.
+unsigned long long current_context_id()
+{
+    if (!g_driver_queried) {
+        g_driver_queried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    }
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the array in the current context.  In host code the
 // array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, with the context (and its device) current.  The
+// first call in a context does that lookup; later calls in it hit the cache.
 int scratch_address(unsigned char** out)
 {
-    int dev = 0;
-    int rc = cuda_fail(cudaGetDevice(&dev), "cudaGetDevice");
-    if (rc) return rc;
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("nep_compute_efv_static: device ordinal %d out of range", dev);
-        return NEP_ERR_ARG;
-    }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        rc = cuda_fail(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress of the static scratch");
-        if (rc) return rc;
-        g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    unsigned long long id = current_context_id();
+    if (id)
+        for (int k = 0; k < kCachedContexts; ++k)
+            if (g_scratch_cache[k].ctx_id == id) {
+                *out = g_scratch_cache[k].addr;
+                return NEP_OK;
+            }
+    void* p = nullptr;
+    const int rc = cuda_fail(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress of the static scratch");
+    if (rc) return rc;
+    // the lookup made the runtime's context current if none was
+    if (!id) id = current_context_id();
+    if (id) {
+        g_scratch_cache[g_scratch_next] = ScratchEntry{id, static_cast<unsigned char*>(p)};
+        g_scratch_next = (g_scratch_next + 1) % kCachedContexts;
     }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<unsigned char*>(p);
     return NEP_OK;
 }
 

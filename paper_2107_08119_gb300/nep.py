@@ -48,6 +48,7 @@ _SIGNATURES = {
     "nep_sync_status": (C.c_int, [_vp, _vp]),
     "nep_heat_current": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "nep_get_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
+    "nep_cell_grid": (C.c_int, [_vp, C.c_double, _vp]),
     "nep_md_create": (C.c_int, [_vp, C.c_int, _vp, C.c_double, C.POINTER(_vp)]),
     "nep_md_destroy": (C.c_int, [_vp]),
     "nep_md_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
@@ -267,6 +268,15 @@ def tc_selftest(A, B, stream=None):
 
 STATIC_MAX_ATOMS = 4096
 STATIC_MAX_NEIGHBORS = 96
+
+
+def cell_grid(box, r_list: float):
+    """Cells per direction of the neighbour-list build for `box` and list
+    radius `r_list` (host only; (0, 0, 0) means the all-pairs search)."""
+    nc = (C.c_int * 3)()
+    _, bp = _box9(box)
+    _check(_lib.nep_cell_grid(bp, float(r_list), nc), "nep_cell_grid")
+    return tuple(nc)
 
 
 def compute_efv_static(z_dev, pos, box, hyper: Hyper = Hyper(max_neighbors=STATIC_MAX_NEIGHBORS), stream=None):

@@ -85,3 +85,32 @@ def test_analysis_entry_points_reject_bad_arguments_without_a_gpu():
     for call in cases:
         assert call() == -1  # NEP_ERR_ARG
         assert lib.nep_last_error()
+
+
+def test_cell_grid_stays_within_int_range_for_large_sparse_boxes():
+    """The cell grid is counted in 64 bits and coarsened to at most 2^22
+    cells: a 10,240 A cube with a 5 A list radius would otherwise need 2048^3
+    cells, a product that wraps to 0 in 32-bit arithmetic.  Every cell edge
+    stays at least the list radius (so the 27-cell stencil still holds every
+    neighbour).  Host-only call: no GPU needed."""
+    from paper_2107_08119_gb300 import build
+    build.build()
+    from paper_2107_08119_gb300 import nep as N
+    import numpy as np
+    cap = 1 << 22
+    for L, r in [((10240.0,) * 3, 5.0), ((1e12, 50.0, 50.0), 6.0), ((3e5, 3e5, 20.0), 6.0),
+                 ((135.75, 135.75, 135.75), 6.0), ((217.2, 217.2, 434.4), 6.0)]:
+        nc = N.cell_grid(np.diag(L), r)
+        assert all(c >= 3 for c in nc), (L, nc)
+        assert int(np.prod(np.array(nc, dtype=np.int64))) <= cap, (L, nc)
+        assert all(L[d] / nc[d] >= r for d in range(3)), (L, nc)
+    # an uncrowded grid is left as floor(L / r_list)
+    assert N.cell_grid(np.diag([135.75] * 3), 6.0) == (22, 22, 22)
+    assert N.cell_grid(np.diag([217.2, 217.2, 434.4]), 6.0) == (36, 36, 72)
+    # edges under three list radii use the all-pairs search
+    assert N.cell_grid(np.diag([10.86] * 3), 6.0) == (0, 0, 0)
+    try:
+        N.cell_grid(np.diag([10.0, 10.0, 10.0]), float("nan"))
+        raise AssertionError("expected NEP_ERR_ARG")
+    except N.NepError as e:
+        assert e.code == -1
