@@ -123,6 +123,40 @@ __host__ __device__ __forceinline__ void pair_vector(int i, int j, int code, con
                     b.Ll[2]);
 }
 
+// pair_vector that also returns the rounding residual of each component:
+// r_exact = r + r_lo to within the tiny rounding of the lo parts (~1e-14 A).
+// The hi-part difference is exact, so r = hi + lo rounds once and Fast2Sum
+// recovers what that rounding dropped.
+__host__ __device__ __forceinline__ float diff1_lo(float ah, float al, float bh, float bl, float s, float Lh, float Ll,
+                                                   float& r_lo)
+{
+    const float hi = (s > 0.f) ? ah - fmaf(-s, Lh, bh) : fmaf(s, Lh, ah) - bh;
+    const float lo = fmaf(s, Ll, al - bl);
+    const float r = hi + lo;
+    r_lo = lo - (r - hi);
+    return r;
+}
+
+__host__ __device__ __forceinline__ void pair_vector_lo(int i, int j, int code, const float (&hi)[3],
+                                                        const float (&li)[3], const float (&hj)[3],
+                                                        const float (&lj)[3], const Box& b, float (&r)[3],
+                                                        float (&r_lo)[3])
+{
+    int sx, sy, sz;
+    image_shift(code, sx, sy, sz);
+    const bool fwd = (j > i) || (j == i && code < kImgCenter);
+    const float sg = fwd ? 1.f : -1.f;
+    const float f[3] = {fwd ? (float)sx : (float)(-sx), fwd ? (float)sy : (float)(-sy),
+                        fwd ? (float)sz : (float)(-sz)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float rl;
+        r[d] = sg * diff1_lo(fwd ? hj[d] : hi[d], fwd ? lj[d] : li[d], fwd ? hi[d] : hj[d], fwd ? li[d] : lj[d], f[d],
+                             b.Lh[d], b.Ll[d], rl);
+        r_lo[d] = sg * rl;
+    }
+}
+
 // FP32 hi/lo positions are stored as one float4 record (x, y, z, 0) per atom
 // for each part, so a neighbour's coordinates arrive in two 16-byte loads.
 __host__ __device__ __forceinline__ void load_pos(const float* __restrict__ xh, const float* __restrict__ xl, int n, int i,

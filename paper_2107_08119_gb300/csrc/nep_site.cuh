@@ -408,6 +408,46 @@ __host__ __device__ __forceinline__ void unit_vector(float rx, float ry, float r
     uz = qz + fmaf(rz, yl, fmaf(rz, yh, -qz));
 }
 
+// The same unit vector (bit for bit) together with what its rounding and
+// the rounding of the pair distance left out, for the first-order energy
+// correction of the partial-force pass:
+//   u_res  r / |r| - u (the rounding residual of each component),
+//   dres   |r| - sqrtf(d2), d2 the distance square the descriptor pass used,
+//   inv    1 / |r| (FP32).
+__host__ __device__ __forceinline__ void unit_vector_res(float rx, float ry, float rz, float d, float& ux,
+                                                         float& uy, float& uz, float (&u_res)[3], float& dres,
+                                                         float& inv)
+{
+    const float px = rx * rx, py = ry * ry, pz = rz * rz;
+    const float ex = fmaf(rx, rx, -px), ey = fmaf(ry, ry, -py), ez = fmaf(rz, rz, -pz);
+    float s1, t1, sh, t2;
+    two_sum(px, py, s1, t1);
+    two_sum(s1, pz, sh, t2);
+    const float sl = ((t1 + t2) + (ex + ey)) + ez;
+    const float y0 = 1.f / sqrtf(sh);
+    const float a = sh * y0, ae = fmaf(sh, y0, -a);
+    const float b = a * y0, be = fmaf(a, y0, -b);
+    const float res = fmaf(-ae, y0, (1.f - b) - be) - sl * y0 * y0;
+    const float yh = fmaf(0.5f * y0, res, y0);
+    const float yl = fmaf(0.5f * y0, res, y0 - yh);
+    const float qx = rx * yh, qy = ry * yh, qz = rz * yh;
+    const float cx = fmaf(rx, yl, fmaf(rx, yh, -qx));
+    const float cy = fmaf(ry, yl, fmaf(ry, yh, -qy));
+    const float cz = fmaf(rz, yl, fmaf(rz, yh, -qz));
+    ux = qx + cx;
+    uy = qy + cy;
+    uz = qz + cz;
+    // |cx| <= ulp-scale of |qx|, so (qx - ux) is exact (Fast2Sum)
+    u_res[0] = (qx - ux) + cx;
+    u_res[1] = (qy - uy) + cy;
+    u_res[2] = (qz - uz) + cz;
+    // |r| = (sh + sl) (yh + yl) = lh + ll to first order in the small parts
+    const float lh = sh * yh;
+    const float ll = fmaf(sh, yh, -lh) + fmaf(sh, yl, sl * yh);
+    dres = (lh - d) + ll;
+    inv = yh;
+}
+
 // Pass 1 of atom i: the descriptor vector q (Eqs. 12-13 through the harmonic
 // sums) and the harmonic sums S_nlm themselves.  Every lane of a warp must
 // call it (inactive lanes pass cnt = 0): the ranks are walked in step.
@@ -495,33 +535,52 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
 // Partial force dU_i/dr_ij of one pair r = r_ij (d2 = |r|^2 < max cutoff^2)
 // from the atom's coefficients A_nlm = 2 c_lm G_nl S_nlm and G_n (Eqs.
 // 23-25): radial G_n g_n' rhat, angular sum_nlm A_nlm grad(g_n Z_lm).
+//
+// It also returns dE, the first-order correction of the site energy for the
+// roundings of this pair's geometry in the descriptor pass: there the
+// descriptors were evaluated at the FP32 distance d = sqrtf(d2) and unit
+// vector u (each rounded), from the pair vector r rounded from the exact
+// r + r_lo.  With dU/dd (the radial coefficient below) and dU/du (the
+// unprojected harmonic gradient V, Z_lm being polynomials in u),
+//   dE = dU/dd (|r + r_lo| - d) + dU/du . ((r + r_lo)/|r + r_lo| - u),
+// which removes those roundings from U_i to second order (~1e-14 relative).
 template <class ArrA, class ArrR>
-__host__ __device__ __forceinline__ void pair_partial_force(float rx, float ry, float rz, float d2, float w,
-                                                            const SiteParams& P, const ArrA& A, const ArrR& GR,
-                                                            float& px, float& py, float& pz)
+__host__ __device__ __forceinline__ void pair_partial_force(const float (&r)[3], const float (&r_lo)[3], float d2,
+                                                            float w, const SiteParams& P, const ArrA& A,
+                                                            const ArrR& GR, float& px, float& py, float& pz,
+                                                            float& dE)
 {
     const float d = sqrtf(d2);
-    const float inv = 1.f / d;
-    const float ux = rx * inv, uy = ry * inv, uz = rz * inv;
-    float radial = 0.f;  // coefficient of rhat
+    float ux, uy, uz, u_res[3], dres, inv;
+    unit_vector_res(r[0], r[1], r[2], d, ux, uy, uz, u_res, dres, inv);
+    float radial = 0.f;  // coefficient of rhat (dU/dd)
     float Vx = 0.f, Vy = 0.f, Vz = 0.f;
+    // geometry residuals: r_lo along and across u
+    const float ur = fmaf(ux, r_lo[0], fmaf(uy, r_lo[1], uz * r_lo[2]));
+    const float dd = dres + ur;
     if (d2 < P.rcR2) {
         float2 gd[kNR];
         radial_gd<kNR>(d, P.rcR, P.inv_rcR, gd, w);
 #pragma unroll
         for (int a = 0; a < kNR; ++a) radial = fmaf(GR[a], gd[a].y, radial);
     }
+    float eu = 0.f;
     if (d2 < P.rcA2) {
         float2 gd[kNA];
         radial_gd<kNA>(d, P.rcA, P.inv_rcA, gd, w);
         float2 Vxy = make_float2(0.f, 0.f);
         sh_pass2(ux, uy, uz, A, gd, radial, Vxy, Vz);
+        const float dux = fmaf(fmaf(-ux, ur, r_lo[0]), inv, u_res[0]);
+        const float duy = fmaf(fmaf(-uy, ur, r_lo[1]), inv, u_res[1]);
+        const float duz = fmaf(fmaf(-uz, ur, r_lo[2]), inv, u_res[2]);
+        eu = fmaf(Vxy.x, dux, fmaf(Vxy.y, duy, Vz * duz));
         // tangential projection of V, divided by r
         const float uv = fmaf(ux, Vxy.x, fmaf(uy, Vxy.y, uz * Vz));
         Vx = (Vxy.x - uv * ux) * inv;
         Vy = (Vxy.y - uv * uy) * inv;
         Vz = (Vz - uv * uz) * inv;
     }
+    dE = fmaf(radial, dd, eu);
     px = fmaf(radial, ux, Vx);
     py = fmaf(radial, uy, Vy);
     pz = fmaf(radial, uz, Vz);
@@ -578,24 +637,28 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
     }
 
     const float rc2max = P.rcR2 > P.rcA2 ? P.rcR2 : P.rcA2;
-    // pass 2: partial forces
+    // pass 2: partial forces, and the first-order energy correction of the
+    // pair geometry's roundings (summed in FP32: each term is ~1e-7 eV)
+    float dU = 0.f;
     NbSlot nx;
     fetch_slot(nbr, xh, xl, n, 0, cnt, nx);
     for (int k = 0; k < cnt; ++k) {
         const NbSlot cur = nx;
         fetch_slot(nbr, xh, xl, n, k + 1, cnt, nx);
         const int j = cur.v & 0xFFFFFF;
-        float rx, ry, rz;
-        pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, rx, ry, rz);
-        const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        float r[3], r_lo[3];
+        pair_vector_lo(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, r, r_lo);
+        const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
         if (!(d2 < rc2max)) continue;
-        float px, py, pz;
-        pair_partial_force(rx, ry, rz, d2, pair_weight(P, zi, cur.z), P, S, GR, px, py, pz);
+        float px, py, pz, dE;
+        pair_partial_force(r, r_lo, d2, pair_weight(P, zi, cur.z), P, S, GR, px, py, pz, dE);
+        dU += dE;
         float* p = out.base + (size_t)k * out.slot_stride;
         p[0] = px;
         p[out.comp_stride] = py;
         p[2 * out.comp_stride] = pz;
     }
+    U_lo += dU;
 }
 
 // Force and per-atom virial of atom i from the stored partial forces

@@ -189,53 +189,52 @@ def test_full_size_config3_sampled(N, orc):
 
 
 def test_full_size_molten_after_md_sampled(N, orc):
-    """The configuration the MD benchmark times: the 125,000-atom workload after
-    600 velocity-Verlet steps on the GPU, by which the random-weight potential
-    has melted the crystal (ragged neighbour counts, pairs near every cutoff,
-    the list rebuilt many times).  Forces of the final positions on the GPU
-    against the oracle for 1,500 atoms: every atom whose count within r_c^R is
-    the smallest or largest of the box, plus a seeded random sample.
-
-    Forces and virials meet their bars everywhere.  The per-atom energy meets
-    1e-6 eV for all but a rare tail: in this disordered state the FP32 error
-    of U_i is about 1.7e-7 eV rms (the FP32 floor, every per-pair value
-    correctly rounded, is about 1.4e-7), and roughly one atom in a thousand
-    lies between 1e-6 and 1.5e-6 eV.  The test asserts exactly that: at most
-    0.2 % of the sampled atoms above 1e-6 eV, none above 1.5e-6 eV, and an rms
-    below 2.5e-7 eV."""
+    """The configuration the MD benchmark times: the 125,000-atom workload
+    after 600, 650 and 700 velocity-Verlet steps on the GPU, by which the
+    random-weight potential has melted the crystal (ragged neighbour counts,
+    pairs near every cutoff, the list rebuilt many times).  At each of the
+    three snapshots the GPU's site energies, forces and virials of the final
+    positions are checked against the oracle for 4,000 atoms (12,000 in all):
+    the 100 atoms with the fewest and the 100 with the most neighbours within
+    r_c^R (counted on the CPU by a periodic k-d tree), plus a seeded random
+    sample.  Every sampled atom meets the per-atom bars: 1e-6 eV for U_i,
+    1e-4 eV/A for F_i and 1e-4 eV for W_i."""
     import torch
+    from scipy.spatial import cKDTree
     pos, vel, box, z = inputs.config2()
     model = N.NEP(z)
     md = N.MD(model, len(pos), box, inputs.MASS_SI)
     p, v = soa(pos), soa(vel)
-    md.step(p, v, 600, 1.0)
-    md.sync_status()
-    assert md.rebuild_count() >= 50
-    x = aos(p)
-    out = model.compute(p, box)
-    # the crystal's 28 neighbours within r_c^R are gone
     L = np.diag(box)
     rng = np.random.default_rng(12)
-    probe = rng.choice(len(x), 4000, replace=False)
-    counts = []
-    for i in probe:
-        d = x - x[i]
-        d -= L * np.round(d / L)
-        counts.append(int((np.einsum("ij,ij->i", d, d) < 25.0).sum()) - 1)
-    counts = np.array(counts)
-    assert counts.std() > 1.0, counts.std()
-    ext = probe[np.argsort(counts)]
-    idx = np.unique(np.concatenate([ext[:100], ext[-100:], rng.choice(len(x), 1300, replace=False)]))
-    U, F, W = orc.efv_sample(orc.NepHyper(), f32_exact(z), x, box, idx)
-    eU = np.abs(out["e_atom"].cpu().numpy()[idx] - U)
-    dU, rms = eU.max(), np.sqrt((eU ** 2).mean())
-    dF = np.abs(aos(out["force"])[idx] - F).max()
-    dW = np.abs(virial_aos(out["virial_atom"])[idx] - W).max()
-    over = int((eU > TOL_U).sum())
-    print(f"molten 125k atoms, {len(idx)} sampled: max |dU| {dU:.2e} (rms {rms:.2e}, {over} above {TOL_U:.0e}), "
-          f"|dF| {dF:.2e}, |dW| {dW:.2e}; neighbours within r_c^R {counts.min()}-{counts.max()}")
-    assert dF <= TOL_F and dW <= TOL_W, (dF, dW)
-    assert rms <= 2.5e-7 and dU <= 1.5e-6 and over <= 0.002 * len(idx), (rms, dU, over)
+    errs = []
+    for snap, steps in enumerate((600, 50, 50)):
+        md.step(p, v, steps, 1.0)
+        md.sync_status()
+        x = aos(p)
+        out = model.compute(p, box)
+        xw = np.mod(x, L)
+        xw = np.where(xw >= L, 0.0, xw)  # x mod L can round up to L
+        counts = np.asarray(cKDTree(xw, boxsize=L).query_ball_point(xw, 5.0, return_length=True)) - 1
+        # the crystal's 28 neighbours within r_c^R are gone
+        assert counts.std() > 1.0, counts.std()
+        order = np.argsort(counts, kind="stable")
+        ext = np.concatenate([order[:100], order[-100:]])
+        rest = np.setdiff1d(np.arange(len(x)), ext)
+        idx = np.unique(np.concatenate([ext, rng.choice(rest, 4000 - len(ext), replace=False)]))
+        assert len(idx) == 4000
+        U, F, W = orc.efv_sample(orc.NepHyper(), f32_exact(z), x, box, idx)
+        eU = np.abs(out["e_atom"].cpu().numpy()[idx] - U)
+        dF = np.abs(aos(out["force"])[idx] - F).max()
+        dW = np.abs(virial_aos(out["virial_atom"])[idx] - W).max()
+        print(f"molten 125k atoms, snapshot {snap} ({md.rebuild_count()} rebuilds): max |dU| {eU.max():.2e} "
+              f"(rms {np.sqrt((eU ** 2).mean()):.2e}), |dF| {dF:.2e}, |dW| {dW:.2e}; "
+              f"neighbours within r_c^R {counts.min()}-{counts.max()}")
+        assert dF <= TOL_F and dW <= TOL_W, (snap, dF, dW)
+        errs.append(eU)
+    eU = np.concatenate(errs)
+    assert md.rebuild_count() >= 50
+    assert eU.max() <= TOL_U, (eU.max(), int((eU > TOL_U).sum()))
     md.close()
     model.close()
     torch.cuda.synchronize()
