@@ -280,6 +280,7 @@ def run_gpu(args, rank, world, local):
     model.profile(False)
     prof = model.profile_read()
     site_ms = prof["site"][0] / max(1, prof["site"][1])
+    rebuilds_phase = md2.rebuild_count()
     md2.close()
     th = thermo[:K].cpu().numpy()
     etot = th[:, 0] + th[:, 1]
@@ -325,6 +326,25 @@ def run_gpu(args, rank, world, local):
     md3.sync_status()
     md3.close()
 
+    # steady state of the melting run: after the timed window, skip ahead
+    # and time a later window of the same trajectory (the random-weight
+    # potential heats the crystal, and the list is rebuilt more often)
+    steady = None
+    if args.steady_steps > 0:
+        md.step(p, v, args.steady_skip, 1.0)
+        r_s0 = md.rebuild_count()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        md.step(p, v, args.steady_steps, 1.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        md.sync_status()
+        ms_s = e0.elapsed_time(e1) / args.steady_steps
+        rb_s = md.rebuild_count() - r_s0
+        steady = {"first_step": W + K + args.steady_skip, "steps": args.steady_steps, "ms_per_step": ms_s,
+                  "atom_steps_per_s": n / (ms_s / 1e3), "list_rebuilds": rb_s,
+                  "rebuilds_per_step": rb_s / args.steady_steps}
+
     t_max, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
     value = job_throughput(world, n, K, t_max)
 
@@ -349,7 +369,10 @@ def run_gpu(args, rank, world, local):
                        "mean_neighbors_rcR": m_r, "mean_neighbors_rcA": m_a,
                        "mean_neighbors_start_end": [[m_r0, m_a0], [m_r1, m_a1]],
                        "phase_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+                       "list_ms_per_rebuild": prof["neighbor"][0] / max(1, rebuilds_phase),
+                       "list_rebuilds_phase_pass": rebuilds_phase,
                        "energy_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / n)},
+            "steady_state": steady,
             "roofline": {"kernel": "k_site (descriptors + network + partial forces)", "bound": "alu",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": site_dram_traffic(), "traffic_unit": "bytes per launch (ncu dram read + write)",
@@ -367,6 +390,9 @@ def run_gpu(args, rank, world, local):
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
         line["force_eval_vs_plain_fp32"] = force_eval_comparison(N, model, p0, box)
+        line["md_step_vs_plain_fp32"] = md_vs_plain(N, model, p_w, v_w, box)
+        line["config1_latency"] = config1_latency(N)
+        line["config3_heat_transport_md"] = config3_md(N)
         v0 = torch.tensor(vel.T.copy(), dtype=torch.float64, device="cuda")
         line["md_nvt_hnemd"] = md_nvt_hnemd(N, model, p0, v0, box)
         adj = adjoint_gradients(N)
@@ -461,6 +487,142 @@ def force_eval_comparison(N, model, pos, box, reps: int = 10):
             "evaluations_timed": reps}
 
 
+def md_vs_plain(N, model, pos, vel, box, steps: int = 100, warm: int = 3):
+    """MD steps of the 125k-atom workload from the same warmed-up state with
+    the optimised force pass and with the plain FP32 comparator
+    (nep_md_set_force_form): list, assembly, integrator and heat current are
+    shared, only the site pass differs.  CUDA events on the current stream;
+    each form's handle replays its own captured step graph."""
+    import torch
+    n = pos.shape[1]
+    stream = torch.cuda.current_stream()
+    out = {"unit": "ms per MD step", "atoms": n, "steps_timed": steps}
+    for name, plain in (("optimised", False), ("plain_fp32", True)):
+        md = N.MD(model, n, box, inputs.MASS_SI)
+        md.set_force_form(plain)
+        p, v = pos.clone(), vel.clone()
+        heat = torch.zeros(max(steps, warm), 3, dtype=torch.float64, device="cuda")
+        md.step(p, v, warm, 1.0, None, heat)
+        r0 = md.rebuild_count()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        md.step(p, v, steps, 1.0, None, heat)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        md.sync_status()
+        ms = e0.elapsed_time(e1) / steps
+        out[f"{name}_ms_per_step"] = ms
+        out[f"{name}_atom_steps_per_s"] = n / (ms / 1e3)
+        out[f"{name}_list_rebuilds"] = md.rebuild_count() - r0
+        md.close()
+    out["speedup_vs_plain"] = out["plain_fp32_ms_per_step"] / out["optimised_ms_per_step"]
+    return out
+
+
+def config3_md(N, steps: int = 50, warm: int = 5):
+    """The heat-transport workload: 921,600 atoms (40 x 40 x 80 diamond cells,
+    10 % vacancies, sigma = 0.15 A, 300 K), NVE with the heat current
+    J = sum_i W_i . v_i accumulated in FP64 every step; a bounded window of
+    `steps` steps after `warm`, from the captured step graph.  Device memory
+    of the MD handle from cudaMemGetInfo around its creation and first steps
+    (the state tensors are allocated before)."""
+    import torch
+    pos, vel, box, z = inputs.config3()
+    n = len(pos)
+    model = N.NEP(np.asarray(z, np.float32))
+    p = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
+    v = torch.tensor(vel.T.copy(), dtype=torch.float64, device="cuda")
+    thermo = torch.zeros(max(steps, warm), N.THERMO_COLS, dtype=torch.float64, device="cuda")
+    heat = torch.zeros(max(steps, warm), 3, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    md = N.MD(model, n, box, inputs.MASS_SI)
+    md.step(p, v, warm, 1.0, thermo, heat)
+    torch.cuda.synchronize()
+    lib_bytes = free0 - torch.cuda.mem_get_info()[0]
+    r0 = md.rebuild_count()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("md_config3_timed")
+    e0.record(stream)
+    md.step(p, v, steps, 1.0, thermo, heat)
+    e1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    md.sync_status()
+    ms = e0.elapsed_time(e1) / steps
+    J = heat[:steps].cpu().numpy()
+    m_cap = N.Hyper().max_neighbors
+    out = {"workload": "heat-transport NVE MD, 921,600 atoms (40x40x80 diamond cells, 10% vacancies, "
+                       "sigma 0.15 A, 300 K), J = sum W_i . v_i every step in FP64, dt 1 fs",
+           "atoms": n, "atom_steps_per_s": n / (ms / 1e3), "ms_per_step": ms, "steps_timed": steps,
+           "warmup": warm, "list_rebuilds_timed": md.rebuild_count() - r0, "heat_current_finite": bool(np.isfinite(J).all()),
+           "device_bytes": int(lib_bytes), "device_bytes_per_atom": lib_bytes / n,
+           "paper_memory_model_bytes_per_atom": 36 * m_cap + 2000,
+           "paper_memory_model": "12 N M + 24 N M + 2000 N bytes (Sec. III.C), with M = this build's 96 slots"}
+    md.close()
+    model.close()
+    return out
+
+
+def config1_latency(N, reps: int = 200, warm: int = 10):
+    """One call of nep_compute_efv on the 512-atom configuration (4^3 diamond
+    cells, sigma = 0.1 A): list build, site pass, assembly and reductions.
+    Device time per call (CUDA events over back-to-back calls), host time per
+    call with a synchronize after each (what a caller waiting for every result
+    sees), and end to end with the positions copied in from pinned host memory
+    and energy and forces copied back every call."""
+    import torch
+    pos, box, z = inputs.config1()
+    n = len(pos)
+    model = N.NEP(np.asarray(z, np.float32))
+    p = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
+    outs = [torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty(n, dtype=torch.float64, device="cuda"),
+            torch.empty(3, n, dtype=torch.float32, device="cuda"), torch.empty(9, n, dtype=torch.float32, device="cuda"),
+            torch.empty(9, dtype=torch.float64, device="cuda")]
+    _, bp = N._box9(box)
+    stream = torch.cuda.current_stream()
+    args = (model._h, n, bp, N._ptr(p), *[N._ptr(t) for t in outs], N._vp(stream.cuda_stream))
+
+    def call():
+        rc = N._lib.nep_compute_efv(*args)
+        if rc != 0:
+            raise RuntimeError(f"nep_compute_efv failed: {rc}")
+    for _ in range(warm):
+        call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dev_us = 1e3 * e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        call()
+        torch.cuda.synchronize()
+    host_us = 1e6 * (time.perf_counter() - t0) / reps
+    hp = p.cpu().pin_memory()
+    he = torch.empty(1, dtype=torch.float64).pin_memory()
+    hf = torch.empty(3, n, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        p.copy_(hp, non_blocking=True)
+        call()
+        he.copy_(outs[0], non_blocking=True)
+        hf.copy_(outs[2], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_us = 1e6 * (time.perf_counter() - t0) / reps
+    model.sync_status()
+    model.close()
+    return {"workload": "512-atom diamond (4^3 cells, sigma 0.1 A), one energy + force + virial call", "atoms": n,
+            "device_us_per_call": dev_us, "host_us_per_call_synchronised": host_us,
+            "e2e_us_per_call": e2e_us, "e2e_h2d_bytes": int(p.numel() * 8),
+            "e2e_d2h_bytes": int(8 + outs[2].numel() * 4), "calls_timed": reps}
+
+
 def training_set(N):
     """The 200-structure training workload on the device, labelled by the CUDA
     force path with the teacher (a timing input, not a checked value)."""
@@ -533,6 +695,7 @@ def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
         return e0.elapsed_time(e1) / gens
 
     tag = "bf16" if precision == N.PREC_BF16 else "fp32"
+    counts = ds.counts()
     ms = timed(lambda n: snes.run(ds, n, precision), f"snes_{tag}_graph")
 
     def eager(n):
@@ -544,7 +707,66 @@ def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
     model.close()
     return {"generations_per_s": 1e3 / ms, "ms_per_generation": ms, "ms_per_generation_eager": ms_eager,
             "shape": shape, "tuned_ms_per_evaluation": tune_ms, "atoms": info["atoms"], "pairs": info["pairs"],
-            "population": 50, "structures": len(structures), "generations_timed": gens}
+            "angular_pairs": counts["angular_pairs"], "population": 50, "structures": len(structures),
+            "generations_timed": gens,
+            "roofline": snes_roofline(counts, 50, model.hyper.n_neu, precision == N.PREC_BF16, ms, tag)}
+
+
+SNES_SOURCES = ("paper_2107_08119_gb300/csrc/nep_train.cu", "paper_2107_08119_gb300/csrc/nep_pop_tc.cu",
+                "paper_2107_08119_gb300/csrc/nep_tc.cuh", "paper_2107_08119_gb300/csrc/nep_dataset.cuh",
+                "paper_2107_08119_gb300/csrc/nep_internal.cuh")
+SNES_PROFILE = os.path.join(ROOT, "profiles", "snes_generation_dram_200structs.json")
+
+
+def snes_roofline(c, P: int, n_neu: int, bf16: bool, ms: float, tag: str):
+    """Roofline of one SNES generation (population evaluation; the draws,
+    ranking and update are O(P N_par) and left out).  Two phases, each bound
+    by its own roof, t_roof = sum over phases of max(flops / pipe peak,
+    algorithmic bytes / HBM bandwidth):
+      network     4 N P 32 N_neu flops (H = Q W1^T and G = D W1, 2 flops per
+                  multiply-add) on the BF16 tensor pipe (FP32 pipe in FP32
+                  mode); bytes: descriptors in (N 32 x 2 B), parameters in,
+                  G out at 2 B per value, U out (N P x 8 B);
+      contraction P (31 n_pairs + 144 n_ang + 192 N) flops on the FP32 pipe
+                  (per pair: 8 radial multiply-adds, 3 products, 6 virial
+                  multiply-adds; per angular pair 72 multiply-adds; per atom
+                  the own term, 96); bytes: the Jacobian records (48 B per
+                  pair, 288 B per angular pair, 384 B per atom), G and U in,
+                  targets and pair indices.
+    `achieved_fraction` = t_roof / the measured generation time.  `traffic`:
+    DRAM bytes (read + write) of one generation's kernels from the committed
+    ncu capture, while the digest of the sources matches."""
+    N, npairs, nang = c["atoms"], c["pairs"], c["angular_pairs"]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs") or 6800.0) * 1e9
+    bf16 = float(peaks.get("bf16_tflops") or 1900.0) * 1e12
+    fp32 = fp32_peak_tflops(2070.0) * 1e12
+    n_par = (32 + 2) * n_neu + 1
+    f_net = 4.0 * N * P * 32 * n_neu
+    b_net = N * 32 * 2 + P * n_par * 4 + N * 32 * P * 2 + N * P * 8
+    f_con = P * (31.0 * npairs + 144.0 * nang + 192.0 * N)
+    b_con = 48 * npairs + 288 * nang + 384 * N + N * 32 * P * 2 + N * P * 8 + 12 * N + 12 * npairs + 8 * N
+    t_net = max(f_net / (bf16 if bf16 else fp32), b_net / hbm)
+    t_con = max(f_con / fp32, b_con / hbm)
+    t_roof = t_net + t_con
+    traffic = None
+    try:
+        prof = json.load(open(SNES_PROFILE))
+        if prof.get("sources_sha256") == sources_digest(SNES_SOURCES):
+            traffic = prof.get("dram_bytes_per_generation", {}).get(tag)
+    except (OSError, ValueError):
+        pass
+    return {"bound": "tensor+alu" if bf16 else "alu", "t_roof_us": 1e6 * t_roof, "achieved_fraction": t_roof / (ms / 1e3),
+            "network": {"flops": f_net, "bytes": b_net, "roof_us": 1e6 * t_net,
+                        "peak": "bf16 tensor (measured burst)" if bf16 else "fp32 pipe (derived)"},
+            "contraction": {"flops": f_con, "bytes": b_con, "roof_us": 1e6 * t_con, "peak": "fp32 pipe (derived)"},
+            "algorithmic_bytes": b_net + b_con, "traffic": traffic,
+            "traffic_over_algorithmic": traffic / (b_net + b_con) if traffic else None,
+            "peaks": {"hbm_gbs": hbm / 1e9, "bf16_tflops": bf16 / 1e12, "fp32_tflops": fp32 / 1e12}}
 
 
 def main():
@@ -555,6 +777,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--steady-skip", type=int, default=500,
+                    help="MD steps after the timed window before the steady-state window")
+    ap.add_argument("--steady-steps", type=int, default=200, help="MD steps of the steady-state window (0: none)")
     ap.add_argument("--only", default="all", choices=["all", "md", "snes"],
                     help="md: the timed MD steps alone (no e2e, SNES or CPU legs); snes: the SNES legs alone. "
                          "Small single-purpose runs for profiler captures.")

@@ -177,6 +177,21 @@ int nep_md_invalidate(nep_md* md);
 int nep_md_set_thermostat(nep_md* md, double t0, double tau);
 
 /*
+ * nep_md_set_force_form -- which form of the force pass the MD steps use:
+ * NEP_FORCE_OPTIMISED (the default: the O(M) harmonic form of Eq. 13 with
+ * compensated sums, as nep_compute_efv) or NEP_FORCE_PLAIN_FP32 (the plain
+ * comparator of nep_compute_efv_plain: literal O(M^2) Eq. 13, unfused, plain
+ * FP32 sums; at most 96 neighbours within r_c^A).  Everything else in the
+ * step (list, assembly, integrator, heat current) is shared.  The next step
+ * recomputes the starting forces with the selected form.  The plain form
+ * allocates 256 bytes per atom of scratch on first use.
+ * Errors: NEP_ERR_ARG (unknown form), NEP_ERR_OOM.
+ */
+#define NEP_FORCE_OPTIMISED 0
+#define NEP_FORCE_PLAIN_FP32 1
+int nep_md_set_force_form(nep_md* md, int form);
+
+/*
  * nep_set_species -- multicomponent systems (Sec. II.A): the cutoff function
  * of pair (i, j) becomes f_c(r_ij) sqrt(Z_i Z_j), so every g_n and g_n' of
  * the pair is multiplied by sqrt(Z_i Z_j) (one species: weight 1, the default).
@@ -258,6 +273,34 @@ int nep_shc_quantum(const double* omega, int n_omega, double x_per_omega, double
  * Errors: NEP_ERR_ARG (NULL pointers, n < 1), NEP_ERR_CUDA.
  */
 int nep_hnemd_kappa(const double* J, int n, double scale, double* out, void* stream);
+/*
+ * nep_hnemd_kappa_si -- nep_hnemd_kappa in physical units: out[t][a] =
+ * <J^a>_{0..t} / (T V F_e) in W / (m K), for J in eV A/fs (the heat series
+ * of nep_md_step), temperature T in K, volume V in A^3 and the driving force
+ * component fe (1/A) along the direction of interest (Sec. II.B; 1 eV/(A fs K)
+ * = 1.602176634e6 W/(m K)).
+ * Errors: NEP_ERR_ARG (NULL pointers, n < 1, T or V not positive, fe = 0,
+ * non-finite values), NEP_ERR_CUDA.
+ */
+int nep_hnemd_kappa_si(const double* J, int n, double temperature, double volume, double fe, double* out,
+                       void* stream);
+/*
+ * nep_kappa_spectrum -- the spectral conductivity of Sec. II.B in physical
+ * units: kappa(nu) in W / (m K THz) at the frequencies nu (THz) from the
+ * virial-velocity correlation K (eV A/fs, as nep_md_get_shc returns it) at
+ * lags dt_lag_fs apart: omega = 2 pi nu (rad/fs) and
+ * kappa(omega) = (2 / (T V F_e)) int K(t) cos(omega t) dt as nep_shc_spectrum
+ * computes it (trapezoid over the lags, optional Hann window), expressed per
+ * THz of nu so that int kappa(nu) dnu is the HNEMD conductivity.  quantum != 0
+ * applies the correction of Sec. IV.C at temperature T (nep_shc_quantum with
+ * x = hbar omega / k_B T, hbar = 0.6582119569 eV fs).
+ *   K dev [n_lags][3]; nu_thz dev [n_nu]; out dev [n_nu][3].  All FP64.
+ * Errors: NEP_ERR_ARG (NULL pointers, empty lengths, dt, T or V not positive,
+ * fe = 0), NEP_ERR_CUDA.
+ */
+int nep_kappa_spectrum(const double* K, int n_lags, double dt_lag_fs, const double* nu_thz, int n_nu,
+                       double temperature, double volume, double fe, int window, int quantum, double* out,
+                       void* stream);
 
 /* Number of neighbour-list builds so far (synchronises `stream`). */
 int nep_md_rebuild_count(nep_md* md, long long* count, void* stream);
@@ -278,6 +321,19 @@ const float* nep_md_forces(const nep_md* md);
  *          stencil / atom index order).
  */
 int nep_get_neighbors(nep_model* m, int n, int* count, int* nbr, void* stream);
+
+/*
+ * nep_status_from_bits -- the status that device-side error bits stand for
+ * (host only; no CUDA call).  The kernels latch these bits in a handle (read
+ * by nep_sync_status) or, for nep_compute_efv_static, in its err_out word:
+ *   1  an atom had more neighbours than max_neighbors  -> NEP_ERR_NEIGHBOR_OVERFLOW
+ *   4  a reverse pair was missing (asymmetric list)    -> NEP_ERR_NEIGHBOR_OVERFLOW
+ *   2  a non-finite position, site energy or force     -> NEP_ERR_NONFINITE
+ *   8  a bounded device-side wait gave up              -> NEP_ERR_TIMEOUT
+ * With several bits set the first in that order wins; 0 gives NEP_OK.  Sets
+ * the thread's nep_last_error message.
+ */
+int nep_status_from_bits(unsigned bits);
 
 /*
  * nep_cell_grid -- the cell grid the neighbour-list build uses for a box and
@@ -320,11 +376,24 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
 int nep_dataset_destroy(nep_dataset* ds);
 /* Atoms, stored pairs and device bytes of a training set; pointers may be NULL. */
 int nep_dataset_info(const nep_dataset* ds, int* n_atoms, long long* n_pairs, long long* device_bytes);
+/* Sizes of a training set, host long long[5]: atoms, stored pairs (within
+ * max(r_c^R, r_c^A)), angular pairs (within r_c^A), structures, atoms of the
+ * largest structure. */
+int nep_dataset_counts(const nep_dataset* ds, long long* counts);
 /* Copy the precomputed descriptors, dev [N][N_des] FP32. */
 int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
 
 /*
- * Launch shape of the population evaluation of a dataset, host int[5]:
+ * Launch shape of the population evaluation of a dataset, host int[6]:
+ *   [5] fused       0, 4, 8 or 16.  Nonzero: the fused contraction, one
+ *                   block per (structure, group of this many members), the
+ *                   structure's forces summed in shared memory (exactly, as
+ *                   int32 fixed point on 2^-8 and 2^-32 grids) and its loss
+ *                   sums written directly: no per-pair partial forces in
+ *                   device memory.  Needs (atoms of the largest structure) x
+ *                   members x 48 bytes of shared memory, at most 220 KB.
+ *                   0: the two passes below through a per-pair partial-force
+ *                   buffer, shaped by [0]-[2] and [4].
  *   [0] waves       1..16: the force contraction runs over up to this many
  *                   consecutive ranges of whole structures with about equal
  *                   pair counts; the second pass of one range runs on a second
@@ -337,19 +406,26 @@ int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
  *   [4] unroll      4 or 8 partial-force slots in flight per warp in the
  *                   second contraction pass, or 16: staged in shared memory
  *                   16 slots at a time by asynchronous copies.
- * No shape changes a result bit (every value keeps its writer and its order of
- * summation).  Default {1, 4, 0, 256, 4}.  Errors: NEP_ERR_ARG (NULL, out of range).
+ * Within each form (fused, or two passes) no shape changes a result bit
+ * (every value keeps its writer and its order of summation).  The two forms
+ * differ in the last bits of the FP32 force sums (exact in the fused form).
+ * Default after nep_dataset_create: {1, 4, 0, 256, 4, 8} (members per block
+ * 4, or the two passes, when the largest structure does not fit 8).
+ * Errors: NEP_ERR_ARG (NULL, out of range, too little shared memory).
  */
 int nep_dataset_set_shape(nep_dataset* ds, const int* shape);
 int nep_dataset_get_shape(const nep_dataset* ds, int* shape);
 /*
- * nep_dataset_tune -- autotuner: times every candidate shape (waves 1, 2, 4
- * x owner warps 4, 8 x discard 0, 1 when waves > 1 x network threads 128, 256
- * in FP32 mode x unroll 4, 8, 16) on `reps` evaluations of an n_pop-member population of fixed
- * stand-in parameters, with CUDA events on `stream` after one warm-up
- * evaluation each, and keeps the fastest on the dataset.  Synchronises the
- * stream.  shape_out: host int[5] or NULL; ms_out: host, the best shape's
- * time per evaluation, or NULL.
+ * nep_dataset_tune -- autotuner: times every candidate shape on `reps`
+ * evaluations of an n_pop-member population of fixed stand-in parameters,
+ * with CUDA events on `stream` after one warm-up evaluation each, and keeps
+ * the fastest on the dataset.  Candidates: the fused contraction with 4, 8
+ * or 16 members per block (where the shared memory fits; the owner atoms per
+ * warp are 32 / members), and the two passes with waves 1, 2, 4 x owner
+ * warps 4, 8 x discard 0, 1 when waves > 1 x unroll 4, 8, 16; each with
+ * network threads 128, 256 in FP32 mode.  Synchronises the stream.
+ * shape_out: host int[6] or NULL; ms_out: host, the best shape's time per
+ * evaluation, or NULL.
  * Errors: NEP_ERR_ARG (NULL, dataset of another model, n_pop outside 1..64,
  * reps < 1, unknown precision), NEP_ERR_OOM, NEP_ERR_CUDA.
  */

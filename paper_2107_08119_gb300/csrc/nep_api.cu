@@ -103,7 +103,7 @@ int status_from_bits(unsigned bits)
         return NEP_ERR_NEIGHBOR_OVERFLOW;
     }
     if (bits & kErrNonFinite) {
-        set_error("non-finite site energy or force");
+        set_error("non-finite position, site energy or force (or a force term beyond the fixed-point range)");
         return NEP_ERR_NONFINITE;
     }
     if (bits & kErrTimeout) {
@@ -529,6 +529,8 @@ int nep_profile_read(nep_model* m, double* ms, long long* launches)
     }
     return NEP_OK;
 }
+
+int nep_status_from_bits(unsigned bits) { return status_from_bits(bits); }
 
 int nep_cell_grid(const double* box9, double r_list, int* nc)
 {

@@ -43,6 +43,8 @@ struct EvalShape {
     int discard = 0;        // pass 2 drops the partial-force lines it has read from L2
     int mlp_threads = 256;  // threads per block of the FP32 network (128 or 256)
     int recv_unroll = 4;    // slots in flight per warp in the receiver pass (4 or 8)
+    int fused = 0;          // 0: the two contraction passes; 4, 8 or 16: the fused contraction with
+                            // this many members per block (one block per structure and member group)
 };
 
 }  // namespace nep
@@ -59,6 +61,8 @@ struct nep_dataset {
     double* s_inv_na = nullptr;  // 1 / atoms of each structure
     int typed = 0;               // species numbers given (multicomponent weighting)
     int* s_chunk0 = nullptr;
+    int* s_order = nullptr;      // structures by decreasing atom count (fused contraction blocks)
+    int amax = 0;                // atoms of the largest structure
     int* chunk_begin = nullptr;
     int* chunk_end = nullptr;
     float* q = nullptr;

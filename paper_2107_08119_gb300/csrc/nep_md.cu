@@ -35,6 +35,11 @@
 static constexpr double kAmuA2Fs2InEv = 1.66053906660e-27 * 1.0e-20 / 1.0e-30 / 1.602176634e-19;
 // Boltzmann constant in eV/K (CODATA 2018)
 static constexpr double kBoltzmannEv = 8.617333262e-5;
+// reduced Planck constant in eV fs (CODATA 2018)
+static constexpr double kHbarEvFs = 0.6582119569;
+static constexpr double kPi = 3.14159265358979323846;
+// 1 eV / (A fs K) in W / (m K): 1.602176634e-19 J / (1e-10 m 1e-15 s K)
+static constexpr double kEvPerAFsK_WPerMK = 1.602176634e6;
 
 namespace nep {
 namespace {
@@ -190,13 +195,15 @@ __global__ void k_shc_average(int n_lags, long long n_samples, const double* __r
 
 // out[k][a] = scale * 2 * trapezoid of K[tau][a] cos(omega_k tau dt) over the
 // lags (K even in t), optionally Hann-windowed (Sec. II.B transform)
+// omega_k = omega_per_x * x[k] (1 when x holds the angular frequencies).
 __global__ void k_shc_spectrum(int n_lags, const double* __restrict__ K, double dt, int n_omega,
-                               const double* __restrict__ omega, double scale, int window, double* __restrict__ out)
+                               const double* __restrict__ omega, double omega_per_x, double scale, int window,
+                               double* __restrict__ out)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_omega * 3) return;
     const int k = e / 3, a = e % 3;
-    const double w0 = omega[k];
+    const double w0 = omega_per_x * omega[k];
     double s = 0.0;
     for (int t = 0; t < n_lags; ++t) {
         double w = (t == 0 || t == n_lags - 1) ? 0.5 : 1.0;
@@ -216,7 +223,7 @@ __global__ void k_shc_quantum(int n_omega, const double* __restrict__ omega, dou
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_omega) return;
-    const double h = fabs(0.5 * x_per_omega * omega[k]);
+    const double h = fabs(0.5 * (x_per_omega * omega[k]));
     double f;
     if (h < 1e-4) {
         f = 1.0 - h * h / 3.0;
@@ -354,6 +361,7 @@ struct nep_md {
     double t0 = 0.0, tau = 0.0;
     double fe[3] = {0.0, 0.0, 0.0};
     bool drive = false;
+    bool plain = false;       // force pass by the plain FP32 comparator (nep_md_set_force_form)
     float* w_atom = nullptr;  // [9][n] per-atom virials (HNEMD only)
     // spectral heat current: ring of per-atom virials, lag sums, chunk partials
     int shc_lags = 0, shc_every = 1;
@@ -371,11 +379,12 @@ struct nep_md {
         double dt, t0, tau, fe[3];
         bool drive;
         const float* zatom;
+        bool plain;
         bool operator==(const GraphKey& o) const
         {
             return pos == o.pos && vel == o.vel && thermo == o.thermo && heat == o.heat && dt == o.dt &&
                    t0 == o.t0 && tau == o.tau && fe[0] == o.fe[0] && fe[1] == o.fe[1] && fe[2] == o.fe[2] &&
-                   drive == o.drive && zatom == o.zatom;
+                   drive == o.drive && zatom == o.zatom && plain == o.plain;
         }
     } gkey{};
 };
@@ -476,6 +485,29 @@ int nep_md_set_thermostat(nep_md* md, double t0, double tau)
     return NEP_OK;
 }
 
+int nep_md_set_force_form(nep_md* md, int form)
+{
+    if (!md || (form != NEP_FORCE_OPTIMISED && form != NEP_FORCE_PLAIN_FP32)) {
+        set_error("nep_md_set_force_form: NULL handle or unknown form %d", form);
+        return NEP_ERR_ARG;
+    }
+    if (form == NEP_FORCE_PLAIN_FP32 && md->ws.plain_cap < md->n) {
+        if (md->ws.plain) cudaFree(md->ws.plain);
+        md->ws.plain = nullptr;
+        md->ws.plain_cap = 0;
+        const cudaError_t e = cudaMalloc((void**)&md->ws.plain, sizeof(float) * 2 * kNdes * (size_t)md->n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("nep_md_set_force_form: %s", cudaGetErrorString(e));
+            return NEP_ERR_OOM;
+        }
+        md->ws.plain_cap = md->n;
+    }
+    md->plain = form == NEP_FORCE_PLAIN_FP32;
+    md->need_init = true;  // the next step recomputes the starting forces with the selected form
+    return NEP_OK;
+}
+
 int nep_md_set_hnemd(nep_md* md, const double* fe)
 {
     if (!md) {
@@ -547,8 +579,8 @@ int nep_shc_spectrum(const double* K, int n_lags, double dt_lag, int n_omega, co
         return NEP_ERR_ARG;
     }
     const int e = n_omega * 3;
-    k_shc_spectrum<<<(e + 127) / 128, 128, 0, (cudaStream_t)stream>>>(n_lags, K, dt_lag, n_omega, omega, scale,
-                                                                      window ? 1 : 0, out);
+    k_shc_spectrum<<<(e + 127) / 128, 128, 0, (cudaStream_t)stream>>>(n_lags, K, dt_lag, n_omega, omega, 1.0,
+                                                                      scale, window ? 1 : 0, out);
     return cuda_fail(cudaGetLastError(), "nep_shc_spectrum");
 }
 
@@ -570,6 +602,44 @@ int nep_hnemd_kappa(const double* J, int n, double scale, double* out, void* str
     }
     k_hnemd_kappa<<<1, kKappaThreads, 0, (cudaStream_t)stream>>>(n, J, scale, out);
     return cuda_fail(cudaGetLastError(), "nep_hnemd_kappa");
+}
+
+int nep_hnemd_kappa_si(const double* J, int n, double temperature, double volume, double fe, double* out,
+                       void* stream)
+{
+    if (!J || !out || n < 1 || !(temperature > 0.0) || !(volume > 0.0) || !(fe != 0.0) ||
+        !std::isfinite(temperature * volume * fe)) {
+        set_error("nep_hnemd_kappa_si: bad arguments (T > 0, V > 0, F_e != 0, all finite)");
+        return NEP_ERR_ARG;
+    }
+    // <J> / (T V F_e) in eV / (A fs K) = kEvPerAFsK_WPerMK W / (m K)
+    const double scale = kEvPerAFsK_WPerMK / (temperature * volume * fe);
+    k_hnemd_kappa<<<1, kKappaThreads, 0, (cudaStream_t)stream>>>(n, J, scale, out);
+    return cuda_fail(cudaGetLastError(), "nep_hnemd_kappa_si");
+}
+
+int nep_kappa_spectrum(const double* K, int n_lags, double dt_lag_fs, const double* nu_thz, int n_nu,
+                       double temperature, double volume, double fe, int window, int quantum, double* out,
+                       void* stream)
+{
+    if (!K || !nu_thz || !out || n_lags < 1 || n_nu < 1 || !(dt_lag_fs > 0.0) || !(temperature > 0.0) ||
+        !(volume > 0.0) || !(fe != 0.0) || !std::isfinite(temperature * volume * fe * dt_lag_fs)) {
+        set_error("nep_kappa_spectrum: bad arguments (lags, frequencies >= 1; dt, T, V > 0; F_e != 0)");
+        return NEP_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // omega = 2 pi nu, in rad/fs for nu in THz; kappa per THz of nu: the
+    // W / (m K) of <J>/(T V F_e) times 1e-3 (the fs of dt over the ps of 1/nu)
+    const double omega_per_nu = 2.0 * kPi * 1e-3;
+    const double scale = 2.0 / (temperature * volume * fe) * kEvPerAFsK_WPerMK * 1e-3;
+    const int e = n_nu * 3;
+    k_shc_spectrum<<<(e + 127) / 128, 128, 0, st>>>(n_lags, K, dt_lag_fs, n_nu, nu_thz, omega_per_nu, scale,
+                                                    window ? 1 : 0, out);
+    // x = hbar omega / (k_B T) = (hbar / (k_B T)) (2 pi 1e-3) nu
+    if (quantum)
+        k_shc_quantum<<<(n_nu + 127) / 128, 128, 0, st>>>(
+            n_nu, nu_thz, kHbarEvFs / (kBoltzmannEv * temperature) * omega_per_nu, out);
+    return cuda_fail(cudaGetLastError(), "nep_kappa_spectrum");
 }
 
 int nep_md_invalidate(nep_md* md)
@@ -630,12 +700,21 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         return NEP_ERR_ARG;
     }
 
+    // site energies and partial forces: the optimised pass, or the plain FP32
+    // comparator (literal Eq. 13, unfused) when selected
+    Workspace& wsp = md->ws;
+    auto site_pass = [&](cudaStream_t q, int& b1) {
+        if (md->plain)
+            return launch_plain_site(fa, nl, n, wsp.plain, wsp.plain + (size_t)kNdes * n, nullptr, part_e, m->d_err, q,
+                                     b1);
+        return launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, q, b1);
+    };
     if (md->need_init) {
         // forces of the starting configuration (list built unconditionally)
         if ((rc = build_neighbor_list(nl, md->box, n, pos, md_zatom(md), true, md->x_ref, md->r_list, m->d_err, nullptr, st)))
             return rc;
         int b1 = 0, b2 = 0, c2 = 0;
-        if ((rc = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, st, b1))) return rc;
+        if ((rc = site_pass(st, b1))) return rc;
         AssembleArgs aa{};
         aa.rc_max = (float)rmax;
         aa.box = md->box;
@@ -681,7 +760,7 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
         const int slot = sample ? (int)(md->shc_samples % md->shc_lags) : 0;
         float* w_out = sample ? md->shc_ring + (size_t)slot * 9 * n : (drive ? md->w_atom : nullptr);
         Profiler::Slot* ps = m->prof.begin(NEP_PROFILE_SITE, q);
-        if ((r = launch_site_partial_forces(fa, nl, n, nullptr, part_e, m->d_err, q, b1))) return r;
+        if ((r = site_pass(q, b1))) return r;
         m->prof.end(ps, q);
         AssembleArgs aa{};
         aa.rc_max = (float)rmax;
@@ -726,7 +805,7 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     // so a step without a rebuild launches none of the list kernels.
     if (!m->prof.on && md->shc_lags == 0) {
         nep_md::GraphKey key{pos, vel, thermo, heat, dt, md->t0, md->tau, {md->fe[0], md->fe[1], md->fe[2]}, drive,
-                             md_zatom(md)};
+                             md_zatom(md), md->plain};
         if (!md->gexec || !(key == md->gkey)) {
             if (md->gexec) cudaGraphExecDestroy(md->gexec);
             md->gexec = nullptr;

@@ -34,9 +34,12 @@ __device__ __forceinline__ bool gated_off(const unsigned* gate)
     return gate != nullptr && *((volatile const unsigned*)gate) == 0u;
 }
 
+// A non-finite coordinate latches kErrNonFinite: such an atom would
+// otherwise be binned into a clamped cell and simply see no neighbours.
 __global__ void k_bin(int n, double* __restrict__ pos, const float* __restrict__ zatom, int wrap_in_place,
                       double* __restrict__ x_ref, float* __restrict__ xh, float* __restrict__ xl,
-                      int* __restrict__ atom_cell, int* __restrict__ cell_count, Box b, const unsigned* gate)
+                      int* __restrict__ atom_cell, int* __restrict__ cell_count, Box b, const unsigned* gate,
+                      unsigned* __restrict__ err)
 {
     if (gated_off(gate)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -47,6 +50,7 @@ __global__ void k_bin(int n, double* __restrict__ pos, const float* __restrict__
     for (int d = 0; d < 3; ++d) {
         const double L = b.L[d];
         const double x = pos[(size_t)d * n + i];
+        if (!isfinite(x)) atomicOr(err, kErrNonFinite);
         // FP64 division is slow here: atoms within one box length of the box
         // (all of them between MD rebuilds) wrap by one exact subtraction
         double w;
@@ -469,7 +473,7 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, cons
     const bool cells = b.nc[0] > 0;
     const int ncell = cells ? b.nc[0] * b.nc[1] * b.nc[2] : 0;
     k_bin<<<blocks_for(n, T), T, 0, st>>>(n, pos, zatom, wrap_in_place ? 1 : 0, x_ref, nl.xh, nl.xl, nl.atom_cell,
-                                          nl.cell_count, b, d_gate);
+                                          nl.cell_count, b, d_gate, d_err);
     if (cells) {
         k_scan<<<1, kScanThreads, 0, st>>>(ncell, nl.cell_count, nl.cell_start, nl.cell_fill, d_gate);
         k_scatter<<<blocks_for(n, T), T, 0, st>>>(n, nl.atom_cell, nl.cell_start, nl.cell_fill, nl.cell_atoms,

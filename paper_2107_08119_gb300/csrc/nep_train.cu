@@ -49,7 +49,7 @@ std::atomic<unsigned long long> g_dataset_uid{0};
 // ------------------------------------------------------------------ build
 __global__ void k_ds_split(int N, const double* __restrict__ pos, const int* __restrict__ sid,
                            const Box* __restrict__ boxes, const float* __restrict__ zat, float* __restrict__ xh,
-                           float* __restrict__ xl)
+                           float* __restrict__ xl, unsigned* __restrict__ err)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -58,6 +58,7 @@ __global__ void k_ds_split(int N, const double* __restrict__ pos, const int* __r
     for (int d = 0; d < 3; ++d) {
         const double L = b.L[d];
         double x = pos[(size_t)d * N + i];
+        if (!isfinite(x)) atomicOr(err, kErrNonFinite);
         double w = x - L * floor(x / L);
         if (w >= L) w -= L;
         if (w < 0.0) w = 0.0;
@@ -99,6 +100,46 @@ __global__ void k_ds_list(int N, const int* __restrict__ sid, const int* __restr
     cnt[i] = c;
     cntA[i] = ca;
     if (c > kDsCap) atomicOr(err, kErrOverflow);
+}
+
+// Each atom's candidate pairs ordered by increasing distance (ties by the
+// search order, so the order is deterministic): the pairs within r_c^A come
+// first, so the warps of the fused contraction, whose lanes walk different
+// atoms' pairs side by side, run their angular terms together.
+__global__ void k_ds_sort(int N, const int* __restrict__ sid, const Box* __restrict__ boxes,
+                          const float* __restrict__ xh, const float* __restrict__ xl, const int* __restrict__ cnt,
+                          int* __restrict__ tmp)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int c = min(cnt[i], kDsCap);
+    const Box b = boxes[sid[i]];
+    float hi[3], li[3];
+    load_pos(xh, xl, N, i, hi, li);
+    int* row = tmp + (size_t)i * kDsCap;
+    float key[kDsCap];
+    for (int t = 0; t < c; ++t) {
+        const int v = row[t];
+        const int j = v & 0xFFFFFF;
+        float hj[3], lj[3];
+        load_pos(xh, xl, N, j, hj, lj);
+        float rx, ry, rz;
+        pair_vector(i, j, v >> 24, hi, li, hj, lj, b, rx, ry, rz);
+        key[t] = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    }
+    // insertion sort (stable): only entries with a strictly larger key move
+    for (int t = 1; t < c; ++t) {
+        const float kt = key[t];
+        const int vt = row[t];
+        int u = t - 1;
+        while (u >= 0 && key[u] > kt) {
+            key[u + 1] = key[u];
+            row[u + 1] = row[u];
+            --u;
+        }
+        key[u + 1] = kt;
+        row[u + 1] = vt;
+    }
 }
 
 __global__ void k_ds_compact(int N, const int* __restrict__ tmp, const long long* __restrict__ pstart,
@@ -681,7 +722,154 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
     }
 }
 
-// One block per member: per structure, the chunk sums (fixed order), then the
+// Fused contraction: one block per (structure s, group of GM members), the
+// structure's force terms accumulated in shared memory, so that no partial
+// force p_kji ever reaches DRAM.  Lane l of a warp takes owner atom slot
+// l / GM and member g GM + l % GM (32 / GM owner atoms per warp, 8 warps per
+// block, the structure's owners in turn).  An owner j loads G_kj once into
+// registers, adds its own term G_kj . B_j to F_kj and, pair by pair from its
+// Jacobian records (owner order, distance-sorted: the angular pairs first),
+// forms p_kji = G_kj . J_ji (Eq. 23) and subtracts it from F_ki (Eqs. 4-5);
+// the owner's virial terms sum_i r_ij (x) p_kji (Eq. 6) are summed in
+// registers.  The force sums are exact: every term is split into a multiple
+// of 2^-8 and a remainder on a 2^-32 grid, both added as int32 with shared
+// memory atomics, and integer addition does not depend on the order of the
+// atomics.  Then, per member, the structure's sums of U_k, |F_k - F_tar|^2
+// and the six virial components: each thread its atoms il = t, t + 256, ...
+// in order, then one fixed block tree.  Nothing depends on GM: every member
+// count per block gives the same bits.  Shared memory: A x GM x 48 bytes
+// (A = the structure's atoms).  A term outside +-2^15 eV/A (or not finite)
+// latches the non-finite error bit (the int32 sums could otherwise wrap).
+constexpr int kFusedThreads = 256;
+constexpr float kFxMax = 32768.f;  // 2^15: with at most 193 terms per atom the int32 sums cannot wrap
+
+__device__ __forceinline__ void fx_add(int* hi, int* lo, float p)
+{
+    const float h = rintf(p * 256.f);           // p = h 2^-8 + r exactly,
+    const float r = fmaf(-h, 0.00390625f, p);   // |r| <= 2^-9
+    atomicAdd(hi, __float2int_rn(h));
+    atomicAdd(lo, __float2int_rn(r * 4294967296.f));
+}
+
+size_t fused_smem_bytes(int amax, int gm) { return (size_t)amax * gm * 48; }
+
+template <int GM>
+__global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
+    int P, int Pst, int n_groups, const int* __restrict__ s_order, const int* __restrict__ sstart,
+    const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
+    const long long* __restrict__ pstart, const int* __restrict__ pj, const PairRec* __restrict__ rec,
+    const long long* __restrict__ aidx, const float* __restrict__ ang, const float* __restrict__ f_tar,
+    double* __restrict__ partials, unsigned* __restrict__ err)
+{
+    constexpr int kApw = 32 / GM;  // owner atoms per warp
+    constexpr int kWarps = kFusedThreads / 32;
+    extern __shared__ int s_fx[];  // Fh [A][3][GM], Fl [A][3][GM] (int32), W6 [A][6][GM] (FP32)
+    const int s = s_order[blockIdx.x / n_groups];
+    const int g = blockIdx.x % n_groups;
+    const int a0 = sstart[s], A = sstart[s + 1] - a0;
+    int* Fh = s_fx;
+    int* Fl = s_fx + (size_t)A * 3 * GM;
+    float* W6 = reinterpret_cast<float*>(s_fx + (size_t)A * 6 * GM);
+    for (int t = threadIdx.x; t < A * 12 * GM; t += kFusedThreads) s_fx[t] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kl = lane % GM, slot = lane / GM;
+    const int k = g * GM + kl;
+    const bool on = k < P;
+    bool bad = false;
+    for (int base = 0; base < A; base += kWarps * kApw) {
+        const int jl = base + warp * kApw + slot;
+        if (jl >= A) continue;
+        const int j = a0 + jl;
+        float gv[kNdes];
+#pragma unroll
+        for (int v = 0; v < kNdes; ++v) gv[v] = on ? G[((size_t)j * kNdes + v) * Pst + k] : 0.f;
+        {  // own term G_kj . B_j
+            const float4* B4 = reinterpret_cast<const float4*>(B + (size_t)j * kNdes * 3);
+            float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < kNdes * 3 / 12; ++u) {
+                const float4 b0 = B4[3 * u], b1 = B4[3 * u + 1], b2 = B4[3 * u + 2];
+                const float bb[4][3] = {{b0.x, b0.y, b0.z}, {b0.w, b1.x, b1.y}, {b1.z, b1.w, b2.x},
+                                        {b2.y, b2.z, b2.w}};
+#pragma unroll
+                for (int d = 0; d < 4; ++d)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) f[c] = fmaf(gv[4 * u + d], bb[d][c], f[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                bad |= !(fabsf(f[c]) < kFxMax);
+                if (on) fx_add(Fh + (jl * 3 + c) * GM + kl, Fl + (jl * 3 + c) * GM + kl, f[c]);
+            }
+        }
+        float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const long long pe = pstart[j + 1];
+        for (long long p = pstart[j]; p < pe; ++p) {
+            const float4* R4 = reinterpret_cast<const float4*>(rec + p);
+            const float4 ra = R4[0], rb = R4[1], rcc = R4[2];  // r_ji, g_n'/r for n = 0..7, pad
+            const int il = (pj[p] & 0xFFFFFF) - a0;
+            const long long ai = aidx[p];
+            const float gd[kNR] = {ra.w, rb.x, rb.y, rb.z, rb.w, rcc.x, rcc.y, rcc.z};
+            float cr = 0.f;
+#pragma unroll
+            for (int v = 0; v < kNR; ++v) cr = fmaf(gv[v], gd[v], cr);
+            float pv[3] = {cr * ra.x, cr * ra.y, cr * ra.z};
+            if (ai >= 0) {
+                const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)ai * (kNA * kLmax * 3));
+#pragma unroll
+                for (int q = 0; q < kNA * kLmax * 3 / 12; ++q) {  // 4 descriptors (12 floats) per step
+                    const float4 x0 = A4[3 * q], x1 = A4[3 * q + 1], x2 = A4[3 * q + 2];
+                    const float aa[4][3] = {{x0.x, x0.y, x0.z}, {x0.w, x1.x, x1.y}, {x1.z, x1.w, x2.x},
+                                            {x2.y, x2.z, x2.w}};
+#pragma unroll
+                    for (int d = 0; d < 4; ++d)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) pv[c] = fmaf(gv[kNR + 4 * q + d], aa[d][c], pv[c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                bad |= !(fabsf(pv[c]) < kFxMax);
+                if (on) fx_add(Fh + (il * 3 + c) * GM + kl, Fl + (il * 3 + c) * GM + kl, -pv[c]);
+            }
+            w6[0] = fmaf(-ra.x, pv[0], w6[0]);  // xx
+            w6[1] = fmaf(-ra.y, pv[1], w6[1]);  // yy
+            w6[2] = fmaf(-ra.z, pv[2], w6[2]);  // zz
+            w6[3] = fmaf(-ra.x, pv[1], w6[3]);  // xy
+            w6[4] = fmaf(-ra.y, pv[2], w6[4]);  // yz
+            w6[5] = fmaf(-ra.z, pv[0], w6[5]);  // zx
+        }
+        if (on)
+#pragma unroll
+            for (int w = 0; w < 6; ++w) W6[(jl * 6 + w) * GM + kl] = w6[w];
+    }
+    if (bad) atomicOr(err, kErrNonFinite);
+    __syncthreads();
+    for (int kk = 0; kk < GM; ++kk) {
+        const int kg = g * GM + kk;
+        if (kg >= P) break;
+        double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int il = threadIdx.x; il < A; il += kFusedThreads) {
+            const int i = a0 + il;
+            v[0] += U[(size_t)i * P + kg];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int o = (il * 3 + c) * GM + kk;
+                const double F = (double)Fh[o] * 0.00390625 + (double)Fl[o] * 2.3283064365386963e-10;
+                const double d = F - (double)f_tar[(size_t)i * 3 + c];
+                v[1] += d * d;
+            }
+#pragma unroll
+            for (int w = 0; w < 6; ++w) v[2 + w] += (double)W6[(il * 6 + w) * GM + kk];
+        }
+        block_sum_store<8>(v, partials + ((size_t)s * P + kg) * 8);
+        __syncthreads();  // the block sum's shared scratch serves the next member
+    }
+}
+
+// One block per member: per structure, the chunk sums (fixed order) or the
+// structure's own sum (fused contraction: s_chunk0 NULL), then the
 // RMSEs of Eqs. 30-32 with energy and virial per atom, and L1, L2 (Eqs. 33-34).
 __global__ void k_loss(int P, int S, int n_par, int N, const int* __restrict__ s_chunk0,
                        const double* __restrict__ s_inv_na, const double* __restrict__ partials,
@@ -699,8 +887,9 @@ __global__ void k_loss(int P, int S, int n_par, int N, const int* __restrict__ s
     }
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
         double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        const int c1 = s_chunk0[s + 1];
-        for (int c0 = s_chunk0[s]; c0 < c1; c0 += kBatch) {
+        // per-chunk partials, or (s_chunk0 NULL) one partial per structure
+        const int c1 = s_chunk0 ? s_chunk0[s + 1] : s + 1;
+        for (int c0 = s_chunk0 ? s_chunk0[s] : s; c0 < c1; c0 += kBatch) {
             double b[kBatch][8];
 #pragma unroll
             for (int q = 0; q < kBatch; ++q)
@@ -892,11 +1081,18 @@ __global__ void k_tune_pop(long long count, float* __restrict__ z)
     z[e] = 0.1f * (2.f * ((float)(x >> 8) * (1.f / 16777216.f)) - 1.f);
 }
 
-bool valid_shape(const EvalShape& h)
+// Largest dynamic shared memory of a fused contraction block (the block sum
+// takes 2 KB of static shared memory beside it, out of 227 KB).
+constexpr size_t kFusedSmemMax = (size_t)220 * 1024;
+
+bool fused_fits(const nep_dataset* ds, int gm) { return fused_smem_bytes(ds->amax, gm) <= kFusedSmemMax; }
+
+bool valid_shape(const nep_dataset* ds, const EvalShape& h)
 {
     return h.waves >= 1 && h.waves <= kMaxWaves && (h.owner_warps == 4 || h.owner_warps == 8) &&
            (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
-           (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 16);
+           (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 16) &&
+           (h.fused == 0 || ((h.fused == 4 || h.fused == 8 || h.fused == 16) && fused_fits(ds, h.fused)));
 }
 
 }  // namespace
@@ -1016,6 +1212,14 @@ int prepare_evaluation(nep_dataset* ds, int P)
                                                  (int)sizeof(float)),
                         "contraction shared memory")))
         return rc;
+    for (int gm = 4; gm <= 16; gm *= 2) {
+        if (!fused_fits(ds, gm)) continue;
+        const int smem = (int)fused_smem_bytes(ds->amax, gm);
+        auto kern = gm == 4 ? k_contract_fused<4> : (gm == 8 ? k_contract_fused<8> : k_contract_fused<16>);
+        if ((rc = cuda_fail(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                            "fused contraction shared memory")))
+            return rc;
+    }
     return prepare_pop_tc();
 }
 
@@ -1075,6 +1279,20 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         k_mlp_f32<<<blocks_for(pairs * P, mt), mt, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
                                                             ds->b2t, ds->G, ds->U);
     }
+    const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
+                           lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
+    if (sh.fused) {
+        // one block per (structure, member group), largest structures first
+        const int gm = sh.fused, groups = (P + gm - 1) / gm;
+        const size_t smem = fused_smem_bytes(ds->amax, gm);
+        auto kern = gm == 4 ? k_contract_fused<4> : (gm == 8 ? k_contract_fused<8> : k_contract_fused<16>);
+        kern<<<ds->S * groups, kFusedThreads, smem, st>>>(P, Pst, groups, ds->s_order, ds->sstart, ds->G, ds->U,
+                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->aidx, ds->ang,
+                                                          ds->f_tar, ds->partials, m->d_err);
+        k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, nullptr, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
+                                  z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
+        return cuda_fail(cudaGetLastError(), "population evaluation kernels");
+    }
     const int C = ds->n_chunks;
     const int W = std::max(1, std::min(std::min(sh.waves, kMaxWaves), C));
     // range ends: structure boundaries (the owner pass writes into the slots
@@ -1108,8 +1326,6 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         cudaEventRecord(ds->ev_join, ds->aux);
         cudaStreamWaitEvent(st, ds->ev_join, 0);
     }
-    const double lam[5] = {lambdas ? lambdas[0] : 1.0, lambdas ? lambdas[1] : 1.0, lambdas ? lambdas[2] : 1.0,
-                           lambdas ? lambdas[3] : 0.05, lambdas ? lambdas[4] : 0.05};
     k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
                               z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
     return cuda_fail(cudaGetLastError(), "population evaluation kernels");
@@ -1246,7 +1462,8 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     if ((rc = dalloc(&ds->boxes, S, bytes)) || (rc = dalloc(&ds->sid, N, bytes)) ||
         (rc = dalloc(&ds->sstart, S + 1, bytes)) || (rc = dalloc(&ds->s_natoms, S, bytes)) ||
         (rc = dalloc(&ds->s_inv_na, S, bytes)) ||
-        (rc = dalloc(&ds->s_chunk0, S + 1, bytes)) || (rc = dalloc(&ds->chunk_begin, ds->n_chunks, bytes)) ||
+        (rc = dalloc(&ds->s_chunk0, S + 1, bytes)) || (rc = dalloc(&ds->s_order, S, bytes)) ||
+        (rc = dalloc(&ds->chunk_begin, ds->n_chunks, bytes)) ||
         (rc = dalloc(&ds->chunk_end, ds->n_chunks, bytes)) || (rc = dalloc(&ds->q, (size_t)N * kNdes, bytes)) ||
         (rc = dalloc(&ds->B, (size_t)N * kNdes * 3, bytes)) || (rc = dalloc(&ds->pstart, (size_t)N + 1, bytes)) ||
         (rc = dalloc(&ds->e_tar, S, bytes)) || (rc = dalloc(&ds->f_tar, (size_t)3 * N, bytes)) ||
@@ -1267,6 +1484,14 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     for (int t = 0; t < S; ++t) hinv[t] = 1.0 / hnat[t];
     up(ds->s_inv_na, hinv.data(), sizeof(double) * S);
     up(ds->s_chunk0, hchunk0.data(), sizeof(int) * (S + 1));
+    // fused contraction: blocks of the largest structures first (they take
+    // longest), and the shared memory its largest structure needs
+    std::vector<int> horder(S);
+    for (int t = 0; t < S; ++t) horder[t] = t;
+    std::stable_sort(horder.begin(), horder.end(), [&](int a, int b) { return hnat[a] > hnat[b]; });
+    up(ds->s_order, horder.data(), sizeof(int) * S);
+    ds->amax = hnat[horder[0]];
+    ds->shape.fused = fused_fits(ds, 8) ? 8 : (fused_fits(ds, 4) ? 4 : 0);
 
     up(ds->chunk_begin, hcb.data(), sizeof(int) * hcb.size());
     up(ds->chunk_end, hce.data(), sizeof(int) * hce.size());
@@ -1279,7 +1504,7 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
 
     const float rc2 = (float)(rmax * rmax), rcA2 = (float)(m->hp.rc_A * m->hp.rc_A);
     const float rcR2 = (float)(m->hp.rc_R * m->hp.rc_R);
-    k_ds_split<<<blocks_for(N, 256), 256>>>(N, dpos, ds->sid, ds->boxes, dz, xh, xl);
+    k_ds_split<<<blocks_for(N, 256), 256>>>(N, dpos, ds->sid, ds->boxes, dz, xh, xl, m->d_err);
     k_ds_list<<<blocks_for(N, 128), 128>>>(N, ds->sid, ds->sstart, ds->boxes, xh, xl, rc2, rcA2, tmp, cnt, cnta,
                                            m->d_err);
     if ((rc = cuda_fail(cudaDeviceSynchronize(), "dataset neighbour search"))) return fail(rc);
@@ -1318,6 +1543,7 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
         dfree(dastart);
         return fail(cuda_fail(e, "dataset upload"));
     }
+    k_ds_sort<<<blocks_for(N, 128), 128>>>(N, ds->sid, ds->boxes, xh, xl, cnt, tmp);
     k_ds_compact<<<blocks_for(N, 128), 128>>>(N, tmp, ds->pstart, dastart, ds->sid, ds->boxes, xh, xl, rcA2, ds->pj,
                                               ds->aidx);
     k_ds_reverse<<<blocks_for(N, 128), 128>>>(N, ds->pstart, ds->pj, rev, m->d_err);
@@ -1353,6 +1579,7 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->s_natoms);
     dfree(ds->s_inv_na);
     dfree(ds->s_chunk0);
+    dfree(ds->s_order);
     dfree(ds->chunk_begin);
     dfree(ds->chunk_end);
     dfree(ds->q);
@@ -1398,6 +1625,20 @@ int nep_dataset_info(const nep_dataset* ds, int* n_atoms, long long* n_pairs, lo
     if (n_atoms) *n_atoms = ds->N;
     if (n_pairs) *n_pairs = ds->n_pairs;
     if (device_bytes) *device_bytes = ds->bytes;
+    return NEP_OK;
+}
+
+int nep_dataset_counts(const nep_dataset* ds, long long* counts)
+{
+    if (!ds || !counts) {
+        set_error("nep_dataset_counts: NULL argument");
+        return NEP_ERR_ARG;
+    }
+    counts[0] = ds->N;
+    counts[1] = ds->n_pairs;
+    counts[2] = ds->n_ang;
+    counts[3] = ds->S;
+    counts[4] = ds->amax;
     return NEP_OK;
 }
 
@@ -1572,10 +1813,12 @@ int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
     h.discard = shape[2];
     h.mlp_threads = shape[3];
     h.recv_unroll = shape[4];
-    if (!valid_shape(h)) {
+    h.fused = shape[5];
+    if (!valid_shape(ds, h)) {
         set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
-                  "receiver unroll 4, 8 or 16 (staged)",
-                  kMaxWaves);
+                  "receiver unroll 4, 8 or 16 (staged), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
+                  "48 bytes of shared memory at most %zu)",
+                  kMaxWaves, ds->amax, kFusedSmemMax);
         return NEP_ERR_ARG;
     }
     ds->shape = h;
@@ -1594,6 +1837,7 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape)
     shape[2] = ds->shape.discard;
     shape[3] = ds->shape.mlp_threads;
     shape[4] = ds->shape.recv_unroll;
+    shape[5] = ds->shape.fused;
     return NEP_OK;
 }
 
@@ -1624,6 +1868,16 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
                         h.recv_unroll = ru;
                         cand.push_back(h);
                     }
+    // the fused contraction: members per block (the atoms per warp follow:
+    // 32 / members), with the FP32 network's block size where it runs
+    for (int gm = 4; gm <= 16; gm *= 2)
+        for (int mt = 128; mt <= 256; mt += 128) {
+            if (!fused_fits(ds, gm) || (precision == NEP_PREC_BF16 && mt == 128)) continue;
+            EvalShape h;
+            h.mlp_threads = mt;
+            h.fused = gm;
+            cand.push_back(h);
+        }
     const long long tot = (long long)n_pop * m->n_par;
     float* z = nullptr;
     double* loss = nullptr;

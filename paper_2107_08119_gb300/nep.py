@@ -49,12 +49,14 @@ _SIGNATURES = {
     "nep_heat_current": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "nep_get_neighbors": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp]),
     "nep_cell_grid": (C.c_int, [_vp, C.c_double, _vp]),
+    "nep_status_from_bits": (C.c_int, [C.c_uint]),
     "nep_md_create": (C.c_int, [_vp, C.c_int, _vp, C.c_double, C.POINTER(_vp)]),
     "nep_md_destroy": (C.c_int, [_vp]),
     "nep_md_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp, _vp]),
     "nep_md_invalidate": (C.c_int, [_vp]),
     "nep_md_set_thermostat": (C.c_int, [_vp, C.c_double, C.c_double]),
     "nep_md_set_hnemd": (C.c_int, [_vp, _vp]),
+    "nep_md_set_force_form": (C.c_int, [_vp, C.c_int]),
     "nep_md_rebuild_count": (C.c_int, [_vp, C.POINTER(C.c_longlong), _vp]),
     "nep_md_forces": (_vp, [_vp]),
     "nep_profile_enable": (C.c_int, [_vp, C.c_int]),
@@ -63,6 +65,7 @@ _SIGNATURES = {
     "nep_dataset_destroy": (C.c_int, [_vp]),
     "nep_dataset_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "nep_dataset_descriptors": (C.c_int, [_vp, _vp, _vp]),
+    "nep_dataset_counts": (C.c_int, [_vp, _vp]),
     "snes_evaluate_population": (C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, _vp, _vp, _vp]),
     "nep_force_loss": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "nep_force_loss_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
@@ -78,6 +81,9 @@ _SIGNATURES = {
     "nep_shc_spectrum": (C.c_int, [_vp, C.c_int, C.c_double, C.c_int, _vp, C.c_double, C.c_int, _vp, _vp]),
     "nep_shc_quantum": (C.c_int, [_vp, C.c_int, C.c_double, _vp, _vp]),
     "nep_hnemd_kappa": (C.c_int, [_vp, C.c_int, C.c_double, _vp, _vp]),
+    "nep_hnemd_kappa_si": (C.c_int, [_vp, C.c_int, C.c_double, C.c_double, C.c_double, _vp, _vp]),
+    "nep_kappa_spectrum": (C.c_int, [_vp, C.c_int, C.c_double, _vp, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     C.c_int, C.c_int, _vp, _vp]),
     "nep_dataset_set_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_get_shape": (C.c_int, [_vp, _vp]),
     "nep_dataset_tune": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.POINTER(C.c_float), _vp]),
@@ -346,6 +352,11 @@ class MD:
         """Berendsen rescaling towards t0 K with coupling time tau fs (tau <= 0: off)."""
         _check(_lib.nep_md_set_thermostat(self._h, float(t0), float(tau)), "nep_md_set_thermostat")
 
+    def set_force_form(self, plain: bool):
+        """Force pass of the MD steps: the optimised form (False) or the plain
+        FP32 comparator (True, literal O(M^2) Eq. 13, unfused)."""
+        _check(_lib.nep_md_set_force_form(self._h, 1 if plain else 0), "nep_md_set_force_form")
+
     def set_hnemd(self, fe):
         """HNEMD driving force parameter F_e (1/A, three values), or None: off."""
         arr = None if fe is None else _host(fe, np.float64, (3,))
@@ -407,6 +418,7 @@ class Dataset:
                "nep_dataset_create")
         self._h = out
         self.n_struct = len(structures)
+        self._default_shape = self.shape()
 
     def close(self):
         if getattr(self, "_h", None):
@@ -424,27 +436,42 @@ class Dataset:
         _check(_lib.nep_dataset_info(self._h, C.byref(na), C.byref(npairs), C.byref(nb)), "nep_dataset_info")
         return {"atoms": na.value, "pairs": npairs.value, "device_bytes": nb.value}
 
+    def counts(self):
+        """atoms, pairs, angular pairs, structures, atoms of the largest structure"""
+        a = np.zeros(5, np.int64)
+        _check(_lib.nep_dataset_counts(self._h, a.ctypes.data_as(_vp)), "nep_dataset_counts")
+        return dict(zip(("atoms", "pairs", "angular_pairs", "structures", "largest_structure"), (int(v) for v in a)))
+
     def descriptors(self, stream=None):
         n = self.info()["atoms"]
         q = torch.empty(n, self.model.hyper.n_des, dtype=torch.float32, device="cuda")
         _check(_lib.nep_dataset_descriptors(self._h, _ptr(q), _stream(stream)), "nep_dataset_descriptors")
         return q
 
-    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll")
+    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll", "fused")
 
     def shape(self):
         """Launch shape of the population evaluation (nep_dataset_get_shape)."""
-        a = np.zeros(5, np.int32)
+        a = np.zeros(6, np.int32)
         _check(_lib.nep_dataset_get_shape(self._h, a.ctypes.data_as(_vp)), "nep_dataset_get_shape")
         return dict(zip(self.SHAPE_KEYS, (int(v) for v in a)))
 
-    def set_shape(self, waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4):
-        a = np.asarray([waves, owner_warps, discard, mlp_threads, recv_unroll], np.int32)
+    def set_shape(self, **shape):
+        """Set the launch shape; keys not given take the dataset's default
+        (the shape it had when created)."""
+        bad = set(shape) - set(self.SHAPE_KEYS)
+        if bad:
+            raise ValueError(f"unknown shape keys {sorted(bad)}")
+        full = dict(self._default_shape, **shape)
+        a = np.asarray([full[k] for k in self.SHAPE_KEYS], np.int32)
         _check(_lib.nep_dataset_set_shape(self._h, a.ctypes.data_as(_vp)), "nep_dataset_set_shape")
+
+    def default_shape(self):
+        return dict(self._default_shape)
 
     def tune(self, n_pop, precision=PREC_FP32, reps=5, stream=None):
         """Autotune the launch shape (nep_dataset_tune); returns (shape, ms per evaluation)."""
-        a = np.zeros(5, np.int32)
+        a = np.zeros(6, np.int32)
         ms = C.c_float()
         _check(_lib.nep_dataset_tune(self.model._h, self._h, int(n_pop), int(precision), int(reps),
                                      a.ctypes.data_as(_vp), C.byref(ms), _stream(stream)), "nep_dataset_tune")
@@ -539,35 +566,35 @@ def hnemd_kappa(J, temperature: float, volume: float, fe: float, scale: float = 
     """Running HNEMD conductivity estimate on the device (Sec. II.B):
     kappa(t) = <J>_{0..t} / (T V F_e) in W / (m K) for J in eV A/fs (the heat
     series of MD.step), T in K, V in A^3 and the driving force fe (1/A) along
-    the component of interest; `scale` overrides 1 / (T V F_e) and the unit
-    conversion.  J: CUDA float64 (n, 3).  Returns (n, 3)."""
+    the component of interest (nep_hnemd_kappa_si); `scale` instead gives the
+    factor of nep_hnemd_kappa directly.  J: CUDA float64 (n, 3).  Returns (n, 3)."""
     if not (J.is_cuda and J.dtype == torch.float64 and J.is_contiguous() and J.dim() == 2 and J.shape[1] == 3):
         raise ValueError("J must be a contiguous CUDA float64 (n, 3) tensor")
-    if scale is None:
-        scale = 1.602176634e6 / (temperature * volume * fe)  # eV / (A fs K) -> W / (m K)
     out = torch.empty_like(J)
-    _check(_lib.nep_hnemd_kappa(_ptr(J), J.shape[0], float(scale), _ptr(out), _stream(stream)), "nep_hnemd_kappa")
+    if scale is None:
+        _check(_lib.nep_hnemd_kappa_si(_ptr(J), J.shape[0], float(temperature), float(volume), float(fe), _ptr(out),
+                                       _stream(stream)), "nep_hnemd_kappa_si")
+    else:
+        _check(_lib.nep_hnemd_kappa(_ptr(J), J.shape[0], float(scale), _ptr(out), _stream(stream)),
+               "nep_hnemd_kappa")
     return out
 
 
-HBAR_EV_FS = 0.6582119569  # reduced Planck constant, eV fs
-K_B_EV = 8.617333262e-5    # Boltzmann constant, eV/K
-
-
 def kappa_spectrum(K, dt_lag_fs: float, nu_thz, temperature: float, volume: float, fe: float, window: bool = True,
-                   quantum: bool = False):
+                   quantum: bool = False, stream=None):
     """Spectral thermal conductivity kappa(nu) in W / (m K THz) at frequencies
     nu (THz, CUDA float64) from K in eV A/fs at lags dt_lag_fs apart, for a
     driving force fe (1/A) along the direction of interest, temperature (K)
-    and volume (A^3): kappa(w) = (2 / (T V F_e)) int K e^{iwt} dt, with
-    int_0^inf kappa(w) dw / (2 pi) the HNEMD conductivity.  quantum=True
+    and volume (A^3) (nep_kappa_spectrum): kappa(w) = (2 / (T V F_e)) int K
+    e^{iwt} dt, with int kappa(nu) dnu the HNEMD conductivity.  quantum=True
     applies the correction factor of Sec. IV.C at that temperature."""
-    omega = 2.0 * np.pi * nu_thz * 1e-3  # rad/fs
-    # eV / (A fs K) -> W / (m K) is 1.602176634e6; per THz of nu = w / (2 pi): times 1e-3 (fs -> ps)
-    scale = 2.0 / (temperature * volume * fe) * 1.602176634e6 * 1e-3
-    out = shc_spectrum(K, dt_lag_fs, omega, scale, window)
-    if quantum:
-        shc_quantum(out, omega, HBAR_EV_FS / (K_B_EV * temperature))
+    if not (K.is_cuda and K.dtype == torch.float64 and K.is_contiguous() and nu_thz.is_cuda
+            and nu_thz.dtype == torch.float64 and nu_thz.is_contiguous()):
+        raise ValueError("K and nu_thz must be contiguous CUDA float64 tensors")
+    out = torch.empty(nu_thz.numel(), 3, dtype=torch.float64, device="cuda")
+    _check(_lib.nep_kappa_spectrum(_ptr(K), K.shape[0], float(dt_lag_fs), _ptr(nu_thz), nu_thz.numel(),
+                                   float(temperature), float(volume), float(fe), 1 if window else 0,
+                                   1 if quantum else 0, _ptr(out), _stream(stream)), "nep_kappa_spectrum")
     return out
 
 

@@ -70,6 +70,8 @@ def test_analysis_entry_points_reject_bad_arguments_without_a_gpu():
     lib.nep_hnemd_kappa.argtypes = [vp, i, d, vp, vp]
     lib.nep_shc_quantum.argtypes = [vp, i, d, vp, vp]
     lib.nep_shc_spectrum.argtypes = [vp, i, d, i, vp, d, i, vp, vp]
+    lib.nep_hnemd_kappa_si.argtypes = [vp, i, d, d, d, vp, vp]
+    lib.nep_kappa_spectrum.argtypes = [vp, i, d, vp, i, d, d, d, i, i, vp, vp]
     fake = vp(64)  # never dereferenced: every call below fails its checks first
     cases = [
         lambda: lib.nep_hnemd_kappa(None, 5, 1.0, fake, None),
@@ -81,6 +83,16 @@ def test_analysis_entry_points_reject_bad_arguments_without_a_gpu():
         lambda: lib.nep_shc_quantum(fake, 4, math.inf, fake, None),
         lambda: lib.nep_shc_spectrum(fake, 0, 1.0, 3, fake, 1.0, 0, fake, None),
         lambda: lib.nep_shc_spectrum(fake, 8, 0.0, 3, fake, 1.0, 0, fake, None),
+        lambda: lib.nep_hnemd_kappa_si(fake, 5, 0.0, 1.0, 1.0, fake, None),
+        lambda: lib.nep_hnemd_kappa_si(fake, 5, 300.0, -1.0, 1.0, fake, None),
+        lambda: lib.nep_hnemd_kappa_si(fake, 5, 300.0, 1.0, 0.0, fake, None),
+        lambda: lib.nep_hnemd_kappa_si(fake, 5, 300.0, 1.0, math.inf, fake, None),
+        lambda: lib.nep_hnemd_kappa_si(None, 5, 300.0, 1.0, 1.0, fake, None),
+        lambda: lib.nep_kappa_spectrum(fake, 8, 2.0, fake, 4, 300.0, 1.0, 0.0, 1, 0, fake, None),
+        lambda: lib.nep_kappa_spectrum(fake, 8, 0.0, fake, 4, 300.0, 1.0, 1e-4, 1, 0, fake, None),
+        lambda: lib.nep_kappa_spectrum(fake, 0, 2.0, fake, 4, 300.0, 1.0, 1e-4, 1, 0, fake, None),
+        lambda: lib.nep_kappa_spectrum(fake, 8, 2.0, None, 4, 300.0, 1.0, 1e-4, 1, 0, fake, None),
+        lambda: lib.nep_kappa_spectrum(fake, 8, 2.0, fake, 4, math.nan, 1.0, 1e-4, 1, 0, fake, None),
     ]
     for call in cases:
         assert call() == -1  # NEP_ERR_ARG
@@ -114,3 +126,25 @@ def test_cell_grid_stays_within_int_range_for_large_sparse_boxes():
         raise AssertionError("expected NEP_ERR_ARG")
     except N.NepError as e:
         assert e.code == -1
+
+
+def test_status_decoding_of_device_error_bits():
+    """The device-side error bits map to status codes on the host, including
+    the timeout bit that the tensor-core kernel latches when a bounded wait
+    gives up (that path is never forced on a GPU; its decoding is checked
+    here).  Priority: overflow, asymmetric list, non-finite, timeout."""
+    import ctypes as C
+
+    from paper_2107_08119_gb300 import build
+    build.build()
+    lib = C.CDLL(build.LIB)
+    lib.nep_status_from_bits.argtypes = [C.c_uint]
+    lib.nep_last_error.restype = C.c_char_p
+    OK, OVERFLOW, NONFINITE, TIMEOUT = 0, -4, -5, -6
+    cases = {0: OK, 1: OVERFLOW, 4: OVERFLOW, 2: NONFINITE, 8: TIMEOUT, 1 | 8: OVERFLOW, 2 | 8: NONFINITE,
+             4 | 2: OVERFLOW, 16: OK}
+    for bits, want in cases.items():
+        assert lib.nep_status_from_bits(bits) == want, bits
+        if want != OK:
+            assert lib.nep_last_error()
+    assert b"timed out" in (lib.nep_status_from_bits(8), lib.nep_last_error())[1]

@@ -238,3 +238,42 @@ def test_full_size_molten_after_md_sampled(N, orc):
     md.close()
     model.close()
     torch.cuda.synchronize()
+
+
+def test_nonfinite_host_positions_are_reported(N):
+    """A NaN or an infinity put into the positions on the host, before the
+    copy to the device: the binning kernel latches the non-finite bit, so
+    nep_compute_efv reports NEP_ERR_NONFINITE at the next synchronising call
+    (the atom would otherwise sit in a clamped cell with no neighbours and a
+    finite energy).  The handle stays usable: the next finite call succeeds.
+    The same holds for an MD start and for a training set."""
+    import torch
+    pos, box, z = inputs.config1()
+    model = N.NEP(z)
+    ref = model.compute(soa(pos), box)["e_atom"].cpu().numpy()
+    for bad in (np.nan, np.inf, -np.inf):
+        host = pos.copy()
+        host[17, 1] = bad
+        with pytest.raises(N.NepError) as e:
+            model.compute(soa(host), box)
+        assert e.value.code == -5  # NEP_ERR_NONFINITE
+        again = model.compute(soa(pos), box)["e_atom"].cpu().numpy()
+        assert np.array_equal(again, ref)
+    md = N.MD(model, len(pos), box, inputs.MASS_SI)
+    host = pos.copy()
+    host[3, 0] = np.nan
+    v = torch.zeros(3, len(pos), dtype=torch.float64, device="cuda")
+    md.step(soa(host), v, 1, 1.0)
+    with pytest.raises(N.NepError) as e:
+        md.sync_status()
+    assert e.value.code == -5
+    md.close()
+    structures = inputs.training_structures(3, seed_stream=5)
+    structures[1]["pos"] = structures[1]["pos"].copy()
+    structures[1]["pos"][5, 2] = np.nan
+    n_at = sum(len(s["pos"]) for s in structures)
+    with pytest.raises(N.NepError) as e:
+        N.Dataset(model, structures, np.zeros(3), np.zeros((n_at, 3)), np.zeros((3, 6)))
+    assert e.value.code == -5
+    model.compute(soa(pos), box)
+    model.close()

@@ -121,8 +121,13 @@ def test_quantum_correction_matches_oracle(N):
     nu = torch.linspace(0.0, 40.0, 81, dtype=torch.float64, device="cuda")
     cl = N.kappa_spectrum(K, 2.0, nu, 300.0, 2e4, 1e-4).cpu().numpy()
     qc = N.kappa_spectrum(K, 2.0, nu, 300.0, 2e4, 1e-4, quantum=True).cpu().numpy()
+    # the units nep_kappa_spectrum applies: omega = 2 pi nu in rad/fs for nu in
+    # THz; W / (m K) per eV / (A fs K); per THz of nu (1e-3 ps per fs)
+    hbar_ev_fs, kb_ev = 0.6582119569, 8.617333262e-5
     w = 2 * np.pi * nu.cpu().numpy() * 1e-3
-    xq = N.HBAR_EV_FS / (N.K_B_EV * 300.0)
+    scale = 2.0 / (300.0 * 2e4 * 1e-4) * 1.602176634e6 * 1e-3
+    assert np.allclose(cl, orc.shc_spectrum(K.cpu().numpy(), 2.0, w, scale, window=True), rtol=1e-12, atol=0)
+    xq = hbar_ev_fs / (kb_ev * 300.0)
     assert np.allclose(qc, orc.shc_quantum(cl, w, xq), rtol=1e-12, atol=0)
     assert (np.abs(qc[1:]) < np.abs(cl[1:])).all()  # the factor is below 1 for w > 0
 

@@ -61,3 +61,42 @@ def test_plain_and_optimised_agree_at_full_size(N):
     assert (a["force"] - b["force"]).abs().max().item() <= TOL_F
     assert (a["virial_atom"] - b["virial_atom"]).abs().max().item() <= TOL_W
     model.close()
+
+
+def test_plain_form_md_trajectory(N, orc):
+    """MD with the plain FP32 force pass (nep_md_set_force_form): the 461-atom
+    replica of the heat-transport workload for 40 steps of 1 fs against the
+    oracle integrator from the same state.  Forces within the plain form's
+    1e-3 eV/A bound move an atom of 28 amu by at most
+    dF t^2 / (2 m) ~ 1e-3 x 40^2 / (2 x 28 x 103.64) ~ 3e-4 A in 40 fs; the
+    test allows 1e-3 A and 1e-4 A/fs, and site energies within n x 1e-4 eV.
+    Switching back to the optimised form restores its own bars."""
+    import torch
+    pos, vel, box, z = inputs.config3(cells=(4, 4, 4))
+    n, steps = len(pos), 40
+    model = N.NEP(z)
+    md = N.MD(model, n, box, inputs.MASS_SI)
+    md.set_force_form(True)
+    p, v = soa(pos), soa(vel)
+    thermo = torch.zeros(steps, N.THERMO_COLS, dtype=torch.float64, device="cuda")
+    md.step(p, v, steps, 1.0, thermo)
+    md.sync_status()
+    po, vo, th_o, _ = orc.md(orc.NepHyper(), f32_exact(z), pos, vel, box, inputs.MASS_SI, 1.0, steps)
+    assert np.abs(thermo.cpu().numpy()[:, 0] - th_o[:, 0]).max() <= TOL_U * n
+    L = np.diag(box)
+    dx = aos(p) - po
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-3
+    assert np.abs(aos(v) - vo).max() < 1e-4
+    # back to the optimised form: one more step from the oracle's state agrees
+    # with the oracle's next step at the optimised path's bars
+    md.set_force_form(False)
+    p2, v2 = soa(po), soa(vo)
+    md.step(p2, v2, 1, 1.0)
+    md.sync_status()
+    po2, vo2, _, _ = orc.md(orc.NepHyper(), f32_exact(z), po, vo, box, inputs.MASS_SI, 1.0, 1)
+    dx = aos(p2) - po2
+    dx -= L * np.round(dx / L)
+    assert np.abs(dx).max() < 1e-8 and np.abs(aos(v2) - vo2).max() < 1e-9
+    md.close()
+    model.close()

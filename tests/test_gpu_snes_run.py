@@ -2,9 +2,13 @@
 
 snes_run replays one captured generation; its generation counter lives on the
 device, so n generations of snes_run must equal n calls of snes_step bit for
-bit (draws, losses, m, s).  No launch shape may change a result bit: every
-value keeps its single writer and its summation order, so the losses of
-every shape the autotuner tries must be identical."""
+bit (draws, losses, m, s).  Within each contraction form no launch shape may
+change a result bit: in the two-pass form every value keeps its single writer
+and its summation order; in the fused form the force sums are exact integer
+sums and every other sum runs over the atoms in an order independent of the
+members per block.  So the losses of every shape of one form must be
+identical, and the two forms agree to the rounding of the two-pass form's
+FP32 force sums."""
 import numpy as np
 import pytest
 
@@ -47,15 +51,25 @@ def full_set(N):
     model.close()
 
 
-def _all_shapes(precision, N):
+def _two_pass_shapes(precision, N):
     out = []
     for w in (1, 2, 4):
         for ow in (4, 8):
             for dc in ((0, 1) if w > 1 else (0,)):
                 for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
                     for ru in (4, 8, 16):
-                        out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru))
+                        out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru,
+                                        fused=0))
     return out
+
+
+def _fused_shapes(precision, N):
+    return [dict(waves=1, owner_warps=4, discard=0, mlp_threads=mt, recv_unroll=4, fused=gm)
+            for gm in (4, 8, 16) for mt in ((128, 256) if precision == N.PREC_FP32 else (256,))]
+
+
+def _all_shapes(precision, N):
+    return _fused_shapes(precision, N) + _two_pass_shapes(precision, N)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -63,15 +77,22 @@ def test_every_shape_gives_identical_losses(N, full_set, prec):
     import torch
     model, ds, pop = full_set
     zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
-    ds.set_shape()
-    ref = ds.evaluate(zp, prec).cpu().numpy()
-    assert np.isfinite(ref).all()
-    for sh in _all_shapes(prec, N) + [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8)]:
-        ds.set_shape(**sh)
-        assert ds.shape() == sh
-        for _ in range(3):  # repeated: a race between the passes would show as a changed bit
-            got = ds.evaluate(zp, prec).cpu().numpy()
-            assert np.array_equal(got, ref), sh
+    refs = {}
+    for form, shapes in (("fused", _fused_shapes(prec, N)),
+                         ("two-pass", _two_pass_shapes(prec, N) +
+                          [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8, fused=0)])):
+        ds.set_shape(**shapes[0])
+        ref = refs[form] = ds.evaluate(zp, prec).cpu().numpy()
+        assert np.isfinite(ref).all()
+        for sh in shapes:
+            ds.set_shape(**sh)
+            assert ds.shape() == sh
+            for _ in range(3):  # repeated: a race would show as a changed bit
+                got = ds.evaluate(zp, prec).cpu().numpy()
+                assert np.array_equal(got, ref), sh
+    # the two forms: the same losses up to the two-pass form's FP32 force sums
+    assert np.allclose(refs["fused"], refs["two-pass"], rtol=1e-6, atol=0.0), \
+        np.abs(refs["fused"] / refs["two-pass"] - 1).max()
     ds.set_shape()
     model.sync_status()
 
@@ -80,33 +101,37 @@ def test_autotuner_picks_a_candidate(N, full_set):
     import torch
     model, ds, pop = full_set
     zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
-    ds.set_shape()
-    ref = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
+    refs = {}
+    for fused in (8, 0):
+        ds.set_shape(fused=fused)
+        refs[fused > 0] = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
     shape, ms = ds.tune(50, N.PREC_BF16, reps=2)
     assert shape in _all_shapes(N.PREC_BF16, N)
     assert ds.shape() == shape
     assert 0.0 < ms < 100.0
-    assert np.array_equal(ds.evaluate(zp, N.PREC_BF16).cpu().numpy(), ref)
+    assert np.array_equal(ds.evaluate(zp, N.PREC_BF16).cpu().numpy(), refs[shape["fused"] > 0])
     ds.set_shape()
 
 
 def test_shape_validation(N, full_set):
     model, ds, pop = full_set
+    assert ds.default_shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4, fused=8)
     for bad in (dict(waves=0), dict(waves=17), dict(owner_warps=6), dict(discard=2), dict(mlp_threads=64),
-                dict(recv_unroll=2), dict(recv_unroll=12)):
+                dict(recv_unroll=2), dict(recv_unroll=12), dict(fused=2), dict(fused=32), dict(fused=-4)):
         with pytest.raises(N.NepError) as e:
             ds.set_shape(**bad)
         assert e.value.code == -1  # NEP_ERR_ARG
-    assert ds.shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4)
+    assert ds.shape() == ds.default_shape()
 
 
-@pytest.mark.parametrize("waves", [1, 4])
-def test_run_equals_steps(N, full_set, waves):
+@pytest.mark.parametrize("shape", [dict(), dict(fused=0, waves=1), dict(fused=0, waves=4, discard=1)])
+def test_run_equals_steps(N, full_set, shape):
     """Generations from the replayed graph equal eager snes_step calls bit
-    for bit, the loss history included, and the two interleave."""
+    for bit, the loss history included, and the two interleave (the fused
+    contraction, and the two-pass form with one and with four ranges)."""
     import torch
     model, ds, pop = full_set
-    ds.set_shape(waves=waves, discard=1 if waves > 1 else 0)
+    ds.set_shape(**shape)
     m0 = f32_exact(np.random.default_rng(8).uniform(-0.5, 0.5, 1021))
     a = N.SNES(model, 50, m0, np.full(1021, 0.1), seed=77)
     b = N.SNES(model, 50, m0, np.full(1021, 0.1), seed=77)
