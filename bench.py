@@ -393,6 +393,7 @@ def run_gpu(args, rank, world, local):
         line["md_step_vs_plain_fp32"] = md_vs_plain(N, model, p_w, v_w, box)
         line["config1_latency"] = config1_latency(N)
         line["config3_heat_transport_md"] = config3_md(N)
+        line["pbte_split_model"] = pbte_split_model(N)
         v0 = torch.tensor(vel.T.copy(), dtype=torch.float64, device="cuda")
         line["md_nvt_hnemd"] = md_nvt_hnemd(N, model, p0, v0, box)
         adj = adjoint_gradients(N)
@@ -566,6 +567,58 @@ def config3_md(N, steps: int = 50, warm: int = 5):
     return out
 
 
+def pbte_split_model(N, reps: int = 10, md_steps: int = 50, warm: int = 3):
+    """The split-hyperparameter model of the paper's PbTe potential (r_c^R = 8 A,
+    n_max^R = 12; r_c^A = 4 A, n_max^A = 6; l_max = 4; 41-40-1 network) on a
+    two-species rocksalt box of 25^3 cells (125,000 atoms, a = 6.46 A, sigma =
+    0.1 A, weights sqrt(Z_i Z_j) with Z = 82, 52): one force evaluation
+    through nep_compute_efv (list, site pass, assembly, reductions) and NVE MD
+    steps (one mass, 1 A skin), CUDA events on the current stream."""
+    import torch
+    pos, vel, box, z, Z = inputs.config_pbte((25, 25, 25))
+    n = len(pos)
+    hyper = N.Hyper(max_neighbors=128, **inputs.PBTE_HYPER)
+    model = N.NEP(np.asarray(z, np.float32), hyper)
+    model.set_species(Z)
+    p = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        model.compute(p, box, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        model.compute(p, box, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    model.sync_status()
+    ms_eval = e0.elapsed_time(e1) / reps
+    model.close()
+    hyper_md = N.Hyper(max_neighbors=160, **inputs.PBTE_HYPER)
+    model = N.NEP(np.asarray(z, np.float32), hyper_md)
+    model.set_species(Z)
+    md = N.MD(model, n, box, inputs.MASS_PBTE)
+    v = torch.tensor(vel.T.copy(), dtype=torch.float64, device="cuda")
+    p = torch.tensor(pos.T.copy(), dtype=torch.float64, device="cuda")
+    md.step(p, v, warm, 1.0)
+    r0 = md.rebuild_count()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    md.step(p, v, md_steps, 1.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    md.sync_status()
+    ms_md = e0.elapsed_time(e1) / md_steps
+    out = {"workload": "PbTe-like rocksalt, 125,000 atoms (25^3 cells, a 6.46 A, sigma 0.1 A), two species "
+                       "weighted sqrt(Z_i Z_j), NEP 41-40-1 (r_c^R 8 A, n_max^R 12; r_c^A 4 A, n_max^A 6)",
+           "atoms": n, "force_eval_ms": ms_eval, "force_evals_per_s": 1e3 / ms_eval,
+           "md_ms_per_step": ms_md, "md_atom_steps_per_s": n / (ms_md / 1e3), "md_steps_timed": md_steps,
+           "md_list_rebuilds": md.rebuild_count() - r0}
+    md.close()
+    model.close()
+    return out
+
+
 def config1_latency(N, reps: int = 200, warm: int = 10):
     """One call of nep_compute_efv on the 512-atom configuration (4^3 diamond
     cells, sigma = 0.1 A): list build, site pass, assembly and reductions.
@@ -718,7 +771,7 @@ SNES_SOURCES = ("paper_2107_08119_gb300/csrc/nep_train.cu", "paper_2107_08119_gb
 SNES_PROFILE = os.path.join(ROOT, "profiles", "snes_generation_dram_200structs.json")
 
 
-def snes_roofline(c, P: int, n_neu: int, bf16: bool, ms: float, tag: str):
+def snes_roofline(c, P: int, n_neu: int, tensor: bool, ms: float, tag: str):
     """Roofline of one SNES generation (population evaluation; the draws,
     ranking and update are O(P N_par) and left out).  Two phases, each bound
     by its own roof, t_roof = sum over phases of max(flops / pipe peak,
@@ -743,14 +796,14 @@ def snes_roofline(c, P: int, n_neu: int, bf16: bool, ms: float, tag: str):
     except (OSError, ValueError):
         pass
     hbm = float(peaks.get("hbm_gbs") or 6800.0) * 1e9
-    bf16 = float(peaks.get("bf16_tflops") or 1900.0) * 1e12
+    bf16_peak = float(peaks.get("bf16_tflops") or 1900.0) * 1e12
     fp32 = fp32_peak_tflops(2070.0) * 1e12
     n_par = (32 + 2) * n_neu + 1
     f_net = 4.0 * N * P * 32 * n_neu
     b_net = N * 32 * 2 + P * n_par * 4 + N * 32 * P * 2 + N * P * 8
     f_con = P * (31.0 * npairs + 144.0 * nang + 192.0 * N)
     b_con = 48 * npairs + 288 * nang + 384 * N + N * 32 * P * 2 + N * P * 8 + 12 * N + 12 * npairs + 8 * N
-    t_net = max(f_net / (bf16 if bf16 else fp32), b_net / hbm)
+    t_net = max(f_net / (bf16_peak if tensor else fp32), b_net / hbm)
     t_con = max(f_con / fp32, b_con / hbm)
     t_roof = t_net + t_con
     traffic = None
@@ -760,13 +813,14 @@ def snes_roofline(c, P: int, n_neu: int, bf16: bool, ms: float, tag: str):
             traffic = prof.get("dram_bytes_per_generation", {}).get(tag)
     except (OSError, ValueError):
         pass
-    return {"bound": "tensor+alu" if bf16 else "alu", "t_roof_us": 1e6 * t_roof, "achieved_fraction": t_roof / (ms / 1e3),
+    return {"bound": "tensor+alu" if tensor else "alu", "t_roof_us": 1e6 * t_roof,
+            "achieved_fraction": t_roof / (ms / 1e3),
             "network": {"flops": f_net, "bytes": b_net, "roof_us": 1e6 * t_net,
-                        "peak": "bf16 tensor (measured burst)" if bf16 else "fp32 pipe (derived)"},
+                        "peak": "bf16 tensor (measured burst)" if tensor else "fp32 pipe (derived)"},
             "contraction": {"flops": f_con, "bytes": b_con, "roof_us": 1e6 * t_con, "peak": "fp32 pipe (derived)"},
             "algorithmic_bytes": b_net + b_con, "traffic": traffic,
             "traffic_over_algorithmic": traffic / (b_net + b_con) if traffic else None,
-            "peaks": {"hbm_gbs": hbm / 1e9, "bf16_tflops": bf16 / 1e12, "fp32_tflops": fp32 / 1e12}}
+            "peaks": {"hbm_gbs": hbm / 1e9, "bf16_tflops": bf16_peak / 1e12, "fp32_tflops": fp32 / 1e12}}
 
 
 def main():

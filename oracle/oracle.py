@@ -19,20 +19,25 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "nep_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# NEP_ORACLE_LIB names a prebuilt copy of the library to load instead (the
+# planted-mistake test compiles altered copies and runs the pins on them)
+_PREBUILT = os.environ.get("NEP_ORACLE_LIB")
+_LIB_PATH = _PREBUILT or os.path.join(_HERE, "liboracle.so")
+GCC_FLAGS = ["-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off"]
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, OpenMP, strict IEEE: no fast-math)."""
+    if _PREBUILT:
+        return _LIB_PATH
     with _lock:
         stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "nep_oracle.h")))
         if force or stale:
             tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-            cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-fno-fast-math",
-                   "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+            cmd = ["gcc"] + GCC_FLAGS + [_SRC, "-o", tmp, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -67,9 +67,9 @@ int check_hyper(const nep_hyper* hp)
         set_error("invalid hyperparameters (cutoffs > 0, skin >= 0, 1 <= max_neighbors <= 384, n_neu >= 1)");
         return NEP_ERR_ARG;
     }
-    if (hp->n_max_R + 1 != kNR || hp->n_max_A + 1 != kNA || hp->l_max != kLmax || hp->n_neu > kMaxNeu) {
-        set_error("this build has kernels for n_max_R=%d, n_max_A=%d, l_max=%d, n_neu<=%d", kNR - 1, kNA - 1, kLmax,
-                  kMaxNeu);
+    if (!(sizes_default(*hp) || sizes_split(*hp)) || hp->l_max != kLmax || hp->n_neu > kMaxNeu) {
+        set_error("this build has kernels for (n_max_R, n_max_A) = (%d, %d) or (12, 6), l_max=%d, n_neu<=%d",
+                  kNR - 1, kNA - 1, kLmax, kMaxNeu);
         return NEP_ERR_UNSUPPORTED;
     }
     return NEP_OK;
@@ -424,6 +424,10 @@ int compute_efv(nep_model* m, int n, const double* box9, const double* pos, doub
         set_error("nep_compute_efv: species were set for %d atoms, not %d (nep_set_species)", m->zatom_n, n);
         return NEP_ERR_ARG;
     }
+    if (plain && !sizes_default(m->hp)) {
+        set_error("nep_compute_efv_plain: the plain comparator has kernels for the 32-descriptor model only");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (m->zatom && plain) {
         set_error("nep_compute_efv_plain: the plain comparator has one species only");
         return NEP_ERR_UNSUPPORTED;
@@ -443,6 +447,8 @@ int compute_efv(nep_model* m, int n, const double* box9, const double* pos, doub
         return rc;
     m->prof.end(pn, st);
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, box};
+    fa.nr = m->hp.n_max_R + 1;
+    fa.na = m->hp.n_max_A + 1;
     fa.typed = m->zatom != nullptr;
     // partial sums: energies in [0, nblocks), assembly totals after them
     double* part_e = m->ws.partials;

@@ -73,6 +73,7 @@ struct nep_dataset {
     int* pj = nullptr;
     long long* rev = nullptr;   // slot of the reverse pair (j -> i) of each pair
     long long* aidx = nullptr;
+    long long* astart = nullptr;  // first angular Jacobian block of each atom [N + 1] (owner order)
     nep::PairRec* rec = nullptr;
     float* ang = nullptr;
     double* e_tar = nullptr;

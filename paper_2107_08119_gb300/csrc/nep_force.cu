@@ -43,7 +43,8 @@ __device__ __forceinline__ void stage_slots(const int* __restrict__ nbr, int n, 
 }
 
 // STAGED: the neighbour capacity fits the shared-memory staging (m_cap <= kStageSlots).
-template <bool STAGED>
+// D: descriptor sizes of the model (DescSi: 32 descriptors, DescPbTe: 41).
+template <bool STAGED, class D>
 __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const int* __restrict__ count,
                                                        const int* __restrict__ nbr, const float* __restrict__ xh,
                                                        const float* __restrict__ xl, Box box,
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const i
     const SlotTable T = STAGED ? SlotTable{s_nbr, kSiteThreads, (int)threadIdx.x} : SlotTable{nbr, n, i};
     float uh, ul;
     const PfOut out{pf + 4 * (size_t)(active ? i : 0), (size_t)4 * n, 1};
-    site_partial_forces(active ? i : 0, active, n, cnt, T, xh, xl, box, P, out, uh, ul);
+    site_partial_forces<D>(active ? i : 0, active, n, cnt, T, xh, xl, box, P, out, uh, ul);
     if (active) {
         e[0] = (double)uh + (double)ul;
         if (e_atom) e_atom[i] = e[0];
@@ -142,10 +143,9 @@ __global__ void k_reduce(const double* __restrict__ partials, int nblocks, int n
 
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
-}  // namespace
-
-int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, double* e_partials,
-                               unsigned* d_err, cudaStream_t st, int& nblocks)
+template <class D>
+int launch_site(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, double* e_partials, unsigned* d_err,
+                cudaStream_t st, int& nblocks)
 {
     SiteParams P;
     P.w = nullptr;
@@ -157,19 +157,33 @@ int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, doub
     P.inv_rcR = 1.f / a.rcR;
     P.inv_rcA = 1.f / a.rcA;
     P.typed = a.typed;
-    const int n_par = (kNdes + 2) * a.n_neu + 1;
+    const int n_par = (D::Ndes + 2) * a.n_neu + 1;
     nblocks = blocks_for(n, kSiteThreads);
     const size_t smem = (((size_t)n_par + 31) / 32 * 32 + (size_t)kStageSlots * kSiteThreads) * sizeof(float);
     const bool staged = a.box.nc[0] >= 0 && nl.m_cap <= kStageSlots;
     if (staged) {
-        int rc = cuda_fail(cudaFuncSetAttribute(k_site<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        int rc = cuda_fail(cudaFuncSetAttribute(k_site<true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                            "site kernel shared memory");
         if (rc) return rc;
     }
-    auto kern = staged ? k_site<true> : k_site<false>;
-    kern<<<nblocks, kSiteThreads, staged ? smem : (((size_t)n_par + 31) / 32 * 32) * sizeof(float), st>>>(n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box,
-                                                                  a.z, n_par, P, nl.pf, e_atom, e_partials, d_err);
+    auto kern = staged ? k_site<true, D> : k_site<false, D>;
+    kern<<<nblocks, kSiteThreads, staged ? smem : (((size_t)n_par + 31) / 32 * 32) * sizeof(float), st>>>(
+        n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box, a.z, n_par, P, nl.pf, e_atom, e_partials, d_err);
     return cuda_fail(cudaGetLastError(), "site kernel");
+}
+
+}  // namespace
+
+int launch_site_partial_forces(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, double* e_partials,
+                               unsigned* d_err, cudaStream_t st, int& nblocks)
+{
+    if (a.nr == DescPbTe::NR && a.na == DescPbTe::NA)
+        return launch_site<DescPbTe>(a, nl, n, e_atom, e_partials, d_err, st, nblocks);
+    if (a.nr != DescSi::NR || a.na != DescSi::NA) {
+        set_error("no site kernel for %d radial and %d angular orders", a.nr, a.na);
+        return NEP_ERR_UNSUPPORTED;
+    }
+    return launch_site<DescSi>(a, nl, n, e_atom, e_partials, d_err, st, nblocks);
 }
 
 int launch_assemble(const AssembleArgs& a, NeighborList& nl, int n, float* force, float* virial_atom,

@@ -320,7 +320,16 @@ struct ForceArgs {
     float rcR, rcA;
     Box box;
     int typed = 0;           // species numbers in the position records are used (multicomponent)
+    int nr = kNR;            // radial orders n_max^R + 1 (8, or 13 for the split model)
+    int na = kNA;            // angular radial orders n_max^A + 1 (6, or 7)
 };
+// The descriptor sizes with force-path kernels: the 32-descriptor model
+// (n_max^R = 7, n_max^A = 5) and the split 41-descriptor model (12, 6),
+// both with l_max = 4.  Only the force path (energies, forces, virials, MD)
+// has kernels for the second; training sets, the plain comparator and the
+// allocation-free call need the first.
+inline bool sizes_default(const nep_hyper& h) { return h.n_max_R == kNR - 1 && h.n_max_A == kNA - 1; }
+inline bool sizes_split(const nep_hyper& h) { return h.n_max_R == 12 && h.n_max_A == 6; }
 // the site pass runs kSiteAtomsPerBlock atoms per block; its per-block
 // energy partials need site_blocks(n) slots, which also bounds the block
 // counts of the assembly and of the plain comparator

@@ -491,6 +491,10 @@ int nep_md_set_force_form(nep_md* md, int form)
         set_error("nep_md_set_force_form: NULL handle or unknown form %d", form);
         return NEP_ERR_ARG;
     }
+    if (form == NEP_FORCE_PLAIN_FP32 && !sizes_default(md->m->hp)) {
+        set_error("nep_md_set_force_form: the plain comparator has kernels for the 32-descriptor model only");
+        return NEP_ERR_UNSUPPORTED;
+    }
     if (form == NEP_FORCE_PLAIN_FP32 && md->ws.plain_cap < md->n) {
         if (md->ws.plain) cudaFree(md->ws.plain);
         md->ws.plain = nullptr;
@@ -687,6 +691,8 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     const int nbk = blocks_for(n, 256);
     const double kef = 0.5 * md->mass * kAmuA2Fs2InEv;
     ForceArgs fa{m->d_z, m->hp.n_neu, (float)m->hp.rc_R, (float)m->hp.rc_A, md->box};
+    fa.nr = m->hp.n_max_R + 1;
+    fa.na = m->hp.n_max_A + 1;
     fa.typed = md_zatom(md) != nullptr;
     if (m->zatom && !fa.typed) {
         set_error("nep_md_step: species were set for %d atoms, not %d", m->zatom_n, n);

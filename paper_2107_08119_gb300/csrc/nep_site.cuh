@@ -202,36 +202,61 @@ __host__ __device__ __forceinline__ constexpr float sh_c(int lm)
 // l of harmonic index lm (0-based l - 1)
 __host__ __device__ __forceinline__ constexpr int sh_l(int lm) { return lm < 3 ? 0 : (lm < 8 ? 1 : (lm < 15 ? 2 : 3)); }
 
+// Descriptor sizes of a model: NR radial orders (n_max^R + 1), NA angular
+// radial orders (n_max^A + 1), l = 1..4; N_des = NR + 4 NA (Eq. 16).  The
+// site functions below are templates over these sizes: Desc<8, 6> is the
+// 32-descriptor model of the Si workloads, Desc<13, 7> the 41-descriptor
+// model with the split hyperparameters of the paper's PbTe potential.
+template <int NR_, int NA_>
+struct Desc {
+    static constexpr int NR = NR_;
+    static constexpr int NA = NA_;
+    static constexpr int NA2 = (NA_ + 1) / 2;  // angular orders in pairs (odd NA: the last pair's y is unused)
+    static constexpr int Ndes = NR_ + NA_ * kLmax;
+};
+using DescSi = Desc<kNR, kNA>;
+using DescPbTe = Desc<13, 7>;
+static_assert(DescSi::Ndes == kNdes, "the default model has 32 descriptors");
+static_assert(DescPbTe::Ndes == 41, "the split model has 41 descriptors");
+
 // Harmonic sums S_nlm of one atom (later the coefficients A_nlm), the radial
 // orders in pairs (2p, 2p + 1) so that one packed f32x2 FMA updates two.
-constexpr int kNA2 = kNA / 2;
-static_assert(kNA % 2 == 0, "angular radial orders are paired");
-typedef float2 Harm[kNA2][kLM];
+template <class D>
+using HarmT = float2[D::NA2][kLM];
+constexpr int kNA2 = DescSi::NA2;
+typedef HarmT<DescSi> Harm;
 
-__host__ __device__ __forceinline__ float& harm(Harm& S, int n, int lm)
+template <int N2>
+__host__ __device__ __forceinline__ float& harm(float2 (&S)[N2][kLM], int n, int lm)
 {
     return (n & 1) ? S[n >> 1][lm].y : S[n >> 1][lm].x;
 }
-__host__ __device__ __forceinline__ float harm(const Harm& S, int n, int lm)
+template <int N2>
+__host__ __device__ __forceinline__ float harm(const float2 (&S)[N2][kLM], int n, int lm)
 {
     return (n & 1) ? S[n >> 1][lm].y : S[n >> 1][lm].x;
 }
 
-// g_n paired as (g_2p, g_2p+1)
-__host__ __device__ __forceinline__ void pair_orders(const float (&g)[kNA], float2 (&g2)[kNA2])
+// g_n paired as (g_2p, g_2p+1); an odd last order is paired with 0
+template <int NA, int N2>
+__host__ __device__ __forceinline__ void pair_orders(const float (&g)[NA], float2 (&g2)[N2])
 {
+    static_assert(N2 == (NA + 1) / 2, "paired orders");
 #pragma unroll
-    for (int p = 0; p < kNA2; ++p) g2[p] = make_float2(g[2 * p], g[2 * p + 1]);
+    for (int p = 0; p < N2; ++p) g2[p] = make_float2(g[2 * p], 2 * p + 1 < NA ? g[2 * p + 1] : 0.f);
 }
 
 // S[n][lm] += g[n] * Y_lm(u), two radial orders per packed FMA
-__host__ __device__ __forceinline__ void sh_acc(Harm& S, const float2 (&g2)[kNA2], int lm, float Y)
+template <int N2>
+__host__ __device__ __forceinline__ void sh_acc(float2 (&S)[N2][kLM], const float2 (&g2)[N2], int lm, float Y)
 {
 #pragma unroll
-    for (int p = 0; p < kNA2; ++p) S[p][lm] = ffma2(g2[p], bcast2(Y), S[p][lm]);
+    for (int p = 0; p < N2; ++p) S[p][lm] = ffma2(g2[p], bcast2(Y), S[p][lm]);
 }
 
-__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float2 (&g)[kNA2], Harm& S)
+template <int N2>
+__host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, const float2 (&g)[N2],
+                                                  float2 (&S)[N2][kLM])
 {
     NEP_SH_LOCALS(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) sh_acc(S, g, lm, Yv);
@@ -242,19 +267,21 @@ __host__ __device__ __forceinline__ void sh_pass1(float x, float y, float z, con
 // One harmonic's contribution to the angular partial force:
 //   (cg, cd) = sum_n A[n][lm] (g_n, g_n')   (one packed FMA per order)
 //   B += cd Y, V += cg grad_u Y             ((Vx, Vy) packed).
-__host__ __device__ __forceinline__ void sh_term(const Harm& A, const float2 (&gd)[kNA], int lm, float Y, float gx,
-                                                 float gy, float gz, float& B, float2& Vxy, float& Vz)
+template <int NA, int N2>
+__host__ __device__ __forceinline__ void sh_term(const float2 (&A)[N2][kLM], const float2 (&gd)[NA], int lm, float Y,
+                                                 float gx, float gy, float gz, float& B, float2& Vxy, float& Vz)
 {
     float2 c = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int n = 0; n < kNA; ++n) c = ffma2(bcast2(harm(A, n, lm)), gd[n], c);
+    for (int n = 0; n < NA; ++n) c = ffma2(bcast2(harm(A, n, lm)), gd[n], c);
     B = fmaf(c.y, Y, B);
     Vxy = ffma2(bcast2(c.x), make_float2(gx, gy), Vxy);
     Vz = fmaf(c.x, gz, Vz);
 }
 
-__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const Harm& A, const float2 (&gd)[kNA],
-                                                  float& B, float2& Vxy, float& Vz)
+template <int NA, int N2>
+__host__ __device__ __forceinline__ void sh_pass2(float x, float y, float z, const float2 (&A)[N2][kLM],
+                                                  const float2 (&gd)[NA], float& B, float2& Vxy, float& Vz)
 {
     NEP_SH_LOCALS_FAST(x, y, z)
 #define NEP_T(lm, Yv, gx, gy, gz) sh_term(A, gd, lm, Yv, gx, gy, gz, B, Vxy, Vz);
@@ -288,8 +315,9 @@ __host__ __device__ __forceinline__ void kahan_step(float w, float qv, float& a,
 
 // Adds neuron mu's output w2 x to the compensated sum (s, c) and its share
 // w2 (1 - x^2) w1_mu of G.
+template <int ND>
 __host__ __device__ __forceinline__ void neuron_out(float w2, float xm, const float* row, float& s, float& c,
-                                                    float (&G)[kNdes])
+                                                    float (&G)[ND])
 {
     const float p = w2 * xm;
     const float ep = fmaf(w2, xm, -p);
@@ -299,27 +327,28 @@ __host__ __device__ __forceinline__ void neuron_out(float w2, float xm, const fl
     c += e + ep;
     const float d = w2 * fmaf(-xm, xm, 1.f);
 #pragma unroll
-    for (int v = 0; v < kNdes; ++v) G[v] = fmaf(d, row[v], G[v]);
+    for (int v = 0; v < ND; ++v) G[v] = fmaf(d, row[v], G[v]);
 }
 
 // Network of Eqs. 21-22 and its input gradient.  w points at the parameter
-// vector [w1 (n_neu x 32), b1, w2, b2].  The pre-activations and the output
+// vector [w1 (n_neu x N_des), b1, w2, b2].  The pre-activations and the output
 // sum are compensated (rounding errors carried along) because the site energy
 // must hold ~1e-7 relative accuracy.  Returns U as hi + lo.
-__host__ __device__ __forceinline__ void network(const float* w, int n_neu, const float (&q)[kNdes],
-                                                 float (&G)[kNdes], float& U_hi, float& U_lo)
+template <int ND>
+__host__ __device__ __forceinline__ void network(const float* w, int n_neu, const float (&q)[ND], float (&G)[ND],
+                                                 float& U_hi, float& U_lo)
 {
-    const float* b1 = w + n_neu * kNdes;
+    const float* b1 = w + n_neu * ND;
     const float* w2 = b1 + n_neu;
     const float b2 = w2[n_neu];
 #pragma unroll
-    for (int v = 0; v < kNdes; ++v) G[v] = 0.f;
+    for (int v = 0; v < ND; ++v) G[v] = 0.f;
     float s = 0.f, c = 0.f;
     for (int mu = 0; mu < n_neu; ++mu) {
-        const float* row = w + mu * kNdes;
+        const float* row = w + mu * ND;
         float a = -b1[mu], ca = 0.f;
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) kahan_step(row[v], q[v], a, ca);
+        for (int v = 0; v < ND; ++v) kahan_step(row[v], q[v], a, ca);
         neuron_out(w2[mu], tanhf(a - ca), row, s, c, G);
     }
     float t, e;
@@ -451,13 +480,15 @@ __host__ __device__ __forceinline__ void unit_vector_res(float rx, float ry, flo
 // Pass 1 of atom i: the descriptor vector q (Eqs. 12-13 through the harmonic
 // sums) and the harmonic sums S_nlm themselves.  Every lane of a warp must
 // call it (inactive lanes pass cnt = 0): the ranks are walked in step.
+template <class D = DescSi>
 __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt, const SlotTable& nbr,
                                                           const float* __restrict__ xh,
                                                           const float* __restrict__ xl, const Box& box,
                                                           const SiteParams& P, const float (&hi)[3],
-                                                          const float (&li)[3], float zi, float (&q)[kNdes],
-                                                          Harm& S)
+                                                          const float (&li)[3], float zi, float (&q)[D::Ndes],
+                                                          HarmT<D>& S)
 {
+    constexpr int kNR = D::NR, kNA = D::NA, kNA2 = D::NA2;
     // radial sums are compensated (Kahan): q_0 ~ 4 accumulates ~28 terms and
     // its plain FP32 rounding dominates the site-energy error budget
     float qR[kNR], qC[kNR];
@@ -544,12 +575,13 @@ __host__ __device__ __forceinline__ void site_descriptors(int i, int n, int cnt,
 // unprojected harmonic gradient V, Z_lm being polynomials in u),
 //   dE = dU/dd (|r + r_lo| - d) + dU/du . ((r + r_lo)/|r + r_lo| - u),
 // which removes those roundings from U_i to second order (~1e-14 relative).
-template <class ArrA, class ArrR>
+template <class D, class ArrA, class ArrR>
 __host__ __device__ __forceinline__ void pair_partial_force(const float (&r)[3], const float (&r_lo)[3], float d2,
                                                             float w, const SiteParams& P, const ArrA& A,
                                                             const ArrR& GR, float& px, float& py, float& pz,
                                                             float& dE)
 {
+    constexpr int kNR = D::NR, kNA = D::NA;
     const float d = sqrtf(d2);
     float ux, uy, uz, u_res[3], dres, inv;
     unit_vector_res(r[0], r[1], r[2], d, ux, uy, uz, u_res, dres, inv);
@@ -588,19 +620,21 @@ __host__ __device__ __forceinline__ void pair_partial_force(const float (&r)[3],
 
 // Pass 1 and the network of atom i: site energy (hi + lo) and the
 // coefficients A (kNA x kLM, in place of the harmonic sums S) and GR.
+template <class D = DescSi>
 __host__ __device__ __forceinline__ void site_coefficients(int i, bool active, int n, int cnt, const SlotTable& nbr,
                                                            const float* __restrict__ xh,
                                                            const float* __restrict__ xl, const Box& box,
-                                                           const SiteParams& P, Harm& S,
-                                                           float (&GR)[kNR], float& U_hi, float& U_lo)
+                                                           const SiteParams& P, HarmT<D>& S,
+                                                           float (&GR)[D::NR], float& U_hi, float& U_lo)
 {
+    constexpr int kNR = D::NR, kNA = D::NA, kNdes = D::Ndes;
     float hi[3], li[3], zi = 1.f;
     if (active) {
         load_pos(xh, xl, n, i, hi, li);
         zi = load_z(xh, i);
     }
     float q[kNdes];
-    site_descriptors(i, n, cnt, nbr, xh, xl, box, P, hi, li, zi, q, S);
+    site_descriptors<D>(i, n, cnt, nbr, xh, xl, box, P, hi, li, zi, q, S);
 
     float G[kNdes];
     network(P.w, P.n_neu, q, G, U_hi, U_lo);
@@ -621,15 +655,16 @@ __host__ __device__ __forceinline__ void site_coefficients(int i, bool active, i
 // energy and the partial forces dU_i/dr_ij of its first cnt slots (written
 // through `out` for slots within max(rc_R, rc_A); other slots are left
 // untouched).
+template <class D = DescSi>
 __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active, int n, int cnt,
                                                              const SlotTable& nbr, const float* __restrict__ xh,
                                                              const float* __restrict__ xl, const Box& box,
                                                              const SiteParams& P, const PfOut& out, float& U_hi,
                                                              float& U_lo)
 {
-    Harm S;
-    float GR[kNR];
-    site_coefficients(i, active, n, cnt, nbr, xh, xl, box, P, S, GR, U_hi, U_lo);
+    HarmT<D> S;
+    float GR[D::NR];
+    site_coefficients<D>(i, active, n, cnt, nbr, xh, xl, box, P, S, GR, U_hi, U_lo);
     float hi[3], li[3], zi = 1.f;
     if (active) {
         load_pos(xh, xl, n, i, hi, li);
@@ -651,7 +686,7 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
         const float d2 = fmaf(r[0], r[0], fmaf(r[1], r[1], r[2] * r[2]));
         if (!(d2 < rc2max)) continue;
         float px, py, pz, dE;
-        pair_partial_force(r, r_lo, d2, pair_weight(P, zi, cur.z), P, S, GR, px, py, pz, dE);
+        pair_partial_force<D>(r, r_lo, d2, pair_weight(P, zi, cur.z), P, S, GR, px, py, pz, dE);
         dU += dE;
         float* p = out.base + (size_t)k * out.slot_stride;
         p[0] = px;

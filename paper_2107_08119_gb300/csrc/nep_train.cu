@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
     int P, int Pst, int n_groups, const int* __restrict__ s_order, const int* __restrict__ sstart,
     const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
     const long long* __restrict__ pstart, const int* __restrict__ pj, const PairRec* __restrict__ rec,
-    const long long* __restrict__ aidx, const float* __restrict__ ang, const float* __restrict__ f_tar,
+    const long long* __restrict__ astart, const float* __restrict__ ang, const float* __restrict__ f_tar,
     double* __restrict__ partials, unsigned* __restrict__ err)
 {
     constexpr int kApw = 32 / GM;  // owner atoms per warp
@@ -804,19 +804,23 @@ __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
             }
         }
         float w6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const long long pe = pstart[j + 1];
-        for (long long p = pstart[j]; p < pe; ++p) {
+        // distance-sorted pairs: j's angular pairs are its first ones, and
+        // their Jacobian blocks are consecutive from astart[j] (owner order)
+        const long long p0 = pstart[j], pe = pstart[j + 1];
+        const long long a0j = astart[j];
+        const int na = (int)(astart[j + 1] - a0j), np = (int)(pe - p0);
+        auto pair_term = [&](int t, bool angular) {
+            const long long p = p0 + t;
             const float4* R4 = reinterpret_cast<const float4*>(rec + p);
             const float4 ra = R4[0], rb = R4[1], rcc = R4[2];  // r_ji, g_n'/r for n = 0..7, pad
             const int il = (pj[p] & 0xFFFFFF) - a0;
-            const long long ai = aidx[p];
             const float gd[kNR] = {ra.w, rb.x, rb.y, rb.z, rb.w, rcc.x, rcc.y, rcc.z};
             float cr = 0.f;
 #pragma unroll
             for (int v = 0; v < kNR; ++v) cr = fmaf(gv[v], gd[v], cr);
             float pv[3] = {cr * ra.x, cr * ra.y, cr * ra.z};
-            if (ai >= 0) {
-                const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)ai * (kNA * kLmax * 3));
+            if (angular) {
+                const float4* A4 = reinterpret_cast<const float4*>(ang + (size_t)(a0j + t) * (kNA * kLmax * 3));
 #pragma unroll
                 for (int q = 0; q < kNA * kLmax * 3 / 12; ++q) {  // 4 descriptors (12 floats) per step
                     const float4 x0 = A4[3 * q], x1 = A4[3 * q + 1], x2 = A4[3 * q + 2];
@@ -839,7 +843,11 @@ __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
             w6[3] = fmaf(-ra.x, pv[1], w6[3]);  // xy
             w6[4] = fmaf(-ra.y, pv[2], w6[4]);  // yz
             w6[5] = fmaf(-ra.z, pv[0], w6[5]);  // zx
-        }
+        };
+#pragma unroll 2
+        for (int t = 0; t < na; ++t) pair_term(t, true);
+#pragma unroll 2
+        for (int t = na; t < np; ++t) pair_term(t, false);
         if (on)
 #pragma unroll
             for (int w = 0; w < 6; ++w) W6[(jl * 6 + w) * GM + kl] = w6[w];
@@ -1287,7 +1295,7 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         const size_t smem = fused_smem_bytes(ds->amax, gm);
         auto kern = gm == 4 ? k_contract_fused<4> : (gm == 8 ? k_contract_fused<8> : k_contract_fused<16>);
         kern<<<ds->S * groups, kFusedThreads, smem, st>>>(P, Pst, groups, ds->s_order, ds->sstart, ds->G, ds->U,
-                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->aidx, ds->ang,
+                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->astart, ds->ang,
                                                           ds->f_tar, ds->partials, m->d_err);
         k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, nullptr, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
                                   z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
@@ -1379,6 +1387,10 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     if (!m || !n_atoms || !boxes || !pos || !e_tar || !f_tar || !w_tar || !out || n_struct < 1) {
         set_error("nep_dataset_create: NULL argument or no structures");
         return NEP_ERR_ARG;
+    }
+    if (!sizes_default(m->hp)) {
+        set_error("nep_dataset_create: training sets have kernels for the 32-descriptor model only");
+        return NEP_ERR_UNSUPPORTED;
     }
     *out = nullptr;
     long long Nl = 0;
@@ -1531,18 +1543,15 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     ds->h_cpairs.resize(hcb.size() + 1);
     for (size_t c = 0; c < hcb.size(); ++c) ds->h_cpairs[c] = hps[hcb[c]];
     ds->h_cpairs[hcb.size()] = hps[N];
-    long long* dastart = nullptr;
+    long long*& dastart = ds->astart;
     if ((rc = dalloc(&ds->pj, (size_t)ds->n_pairs, bytes)) || (rc = dalloc(&ds->aidx, (size_t)ds->n_pairs, bytes)) ||
         (rc = dalloc(&ds->rec, (size_t)ds->n_pairs, bytes)) ||
         (rc = dalloc(&ds->ang, (size_t)ds->n_ang * kNA * kLmax * 3, bytes)) ||
-        (rc = dalloc(&rev, (size_t)ds->n_pairs, bytes)) || (rc = dalloc(&dastart, (size_t)N + 1, nullptr)))
+        (rc = dalloc(&rev, (size_t)ds->n_pairs, bytes)) || (rc = dalloc(&dastart, (size_t)N + 1, bytes)))
         return fail(rc);
     up(ds->pstart, hps.data(), sizeof(long long) * (N + 1));
     up(dastart, has.data(), sizeof(long long) * (N + 1));
-    if (e != cudaSuccess) {
-        dfree(dastart);
-        return fail(cuda_fail(e, "dataset upload"));
-    }
+    if (e != cudaSuccess) return fail(cuda_fail(e, "dataset upload"));
     k_ds_sort<<<blocks_for(N, 128), 128>>>(N, ds->sid, ds->boxes, xh, xl, cnt, tmp);
     k_ds_compact<<<blocks_for(N, 128), 128>>>(N, tmp, ds->pstart, dastart, ds->sid, ds->boxes, xh, xl, rcA2, ds->pj,
                                               ds->aidx);
@@ -1553,7 +1562,6 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     if (!rc && !(rc = dalloc(&ds->qpack, pop_tc_qpack_bytes(N), bytes)))
         rc = launch_pack_q_tc(N, ds->q, ds->qpack, nullptr);
     if (!rc) rc = cuda_fail(cudaDeviceSynchronize(), "dataset precompute");
-    dfree(dastart);
     if (rc) return fail(rc);
     cudaMemcpy(&bits, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (bits) {
@@ -1580,6 +1588,7 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->s_inv_na);
     dfree(ds->s_chunk0);
     dfree(ds->s_order);
+    dfree(ds->astart);
     dfree(ds->chunk_begin);
     dfree(ds->chunk_end);
     dfree(ds->q);

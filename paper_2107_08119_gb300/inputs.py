@@ -21,6 +21,15 @@ KB_EV = 8.617333262e-5  # Boltzmann constant (eV/K)
 # 1 amu A^2/fs^2 in eV, from the CODATA 2018 atomic mass constant and elementary charge
 AMU_A2_FS2_EV = 1.66053906660e-27 * 1.0e-20 / 1.0e-30 / 1.602176634e-19
 
+# PbTe-like two-species rocksalt (the paper's PbTe model, Table I: r_c^R = 8 A,
+# n_max^R = 12, r_c^A = 4 A, n_max^A = 6, l_max = 4, 40 neurons, 41 descriptors)
+A_PBTE = 6.46           # rocksalt PbTe lattice constant (Angstrom)
+Z_PB, Z_TE = 82.0, 52.0  # atomic numbers: the multicomponent weights sqrt(Z_i Z_j)
+MASS_PBTE = 167.4       # amu: the mean of Pb (207.2) and Te (127.6); the MD here takes one mass
+PBTE_HYPER = dict(n_max_R=12, n_max_A=6, l_max=4, n_neu=40, rc_R=8.0, rc_A=4.0)
+
+_ROCKSALT_CATION = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+
 _DIAMOND_BASIS = np.array([
     [0.00, 0.00, 0.00], [0.00, 0.50, 0.50], [0.50, 0.00, 0.50], [0.50, 0.50, 0.00],
     [0.25, 0.25, 0.25], [0.25, 0.75, 0.75], [0.75, 0.25, 0.75], [0.75, 0.75, 0.25],
@@ -39,6 +48,18 @@ def diamond(n1: int, n2: int, n3: int, a: float = A_SI):
     pos = (cells[:, None, :] + _DIAMOND_BASIS[None, :, :]).reshape(-1, 3) * a
     box = np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
     return pos, box
+
+
+def rocksalt(n1: int, n2: int, n3: int, a: float = A_PBTE):
+    """Rocksalt supercell: positions (8 n1 n2 n3, 3), species numbers (Pb on
+    the fcc sites, Te shifted by a/2 along x), box (3, 3)."""
+    ii, jj, kk = np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij")
+    cells = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1).astype(np.float64)
+    basis = np.concatenate([_ROCKSALT_CATION, _ROCKSALT_CATION + [0.5, 0.0, 0.0]])
+    pos = (cells[:, None, :] + basis[None, :, :]).reshape(-1, 3) * a
+    Z = np.tile(np.array([Z_PB] * 4 + [Z_TE] * 4), len(cells))
+    box = np.diag([n1 * a, n2 * a, n3 * a]).astype(np.float64)
+    return pos, Z, box
 
 
 def displace(pos, sigma: float, rng: np.random.Generator):
@@ -101,6 +122,34 @@ def config3(cells=(40, 40, 80), vacancy_fraction: float = 0.1, n_par: int = 1021
     vel = maxwell_boltzmann(pos.shape[0], temperature, MASS_SI, rng)
     z = random_z(n_par, rng)
     return pos, vel, box, z
+
+
+def config_pbte(cells=(4, 4, 4), sigma: float = 0.1, temperature: float = 300.0):
+    """PbTe-like two-species workload for the split-hyperparameter model:
+    rocksalt cells (a = 6.46 A), seeded displacements sigma = 0.1 A,
+    Maxwell-Boltzmann velocities at 300 K with the one mass MASS_PBTE, and a
+    parameter vector of the 41-40-1 network drawn U(-1/2, 1/2) with the
+    input-layer weights matched to the scale of the weighted descriptors:
+    the weights sqrt(Z_i Z_j) (atomic numbers 82 and 52) make the radial
+    descriptors ~Zbar and the angular ones ~Zbar^2 times larger than for one
+    species of weight 1 (Zbar = sqrt(82 x 52)), so the columns of w1 for the
+    13 radial descriptors are divided by Zbar and those for the 28 angular
+    ones by Zbar^2 (a trained potential's weights match its inputs; random
+    U(-1/2, 1/2) weights on descriptors of ~1e3 would saturate the network).
+    Returns (pos, vel, box, z, Z) with Z the atomic number of every atom."""
+    rng = rng_for(6, stream=int(np.prod(cells)))
+    pos, Z, box = rocksalt(*cells)
+    pos = displace(pos, sigma, rng)
+    vel = maxwell_boltzmann(pos.shape[0], temperature, MASS_PBTE, rng)
+    n_r = PBTE_HYPER["n_max_R"] + 1
+    n_des = n_r + (PBTE_HYPER["n_max_A"] + 1) * PBTE_HYPER["l_max"]
+    n_neu = PBTE_HYPER["n_neu"]
+    z = random_z((n_des + 2) * n_neu + 1, rng)
+    zbar = np.sqrt(Z_PB * Z_TE)
+    w1 = z[:n_neu * n_des].reshape(n_neu, n_des)
+    w1[:, :n_r] /= zbar
+    w1[:, n_r:] /= zbar ** 2
+    return pos, vel, box, z, Z
 
 
 def training_structures(n_struct: int = 200, seed_stream: int = 0):
