@@ -433,7 +433,10 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
                      float* ms_out, void* stream);
 
 #define NEP_PREC_FP32 0 /* network of every member in FP32 (CUDA cores) */
-#define NEP_PREC_BF16 1 /* population GEMMs in BF16 with FP32 accumulation (tensor cores) */
+/* population GEMMs in BF16 with FP32 accumulation (tensor cores); the
+ * two-pass contraction keeps its per-pair partial forces in FP16 (each loss
+ * term averages that rounding over all force components: ~1e-6 relative) */
+#define NEP_PREC_BF16 1
 #define NEP_LOSS_COLS 6 /* L, L_e, L_f, L_v, L_1, L_2 */
 
 /*

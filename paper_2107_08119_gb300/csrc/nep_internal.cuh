@@ -380,9 +380,10 @@ int prepare_pop_tc();
 // the descriptors packed as split-BF16 GEMM-1 A tiles, once per training set
 size_t pop_tc_qpack_bytes(int N);
 int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t st);
+// G: FP32, or FP16 when g_half
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
-                  const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
-                  cudaStream_t st);
+                  const float* w2t, const float* b2t, unsigned char* packed, void* G, bool g_half, double* U,
+                  unsigned* err, cudaStream_t st);
 
 }  // namespace nep
 

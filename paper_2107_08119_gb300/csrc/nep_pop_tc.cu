@@ -230,12 +230,14 @@ __device__ __forceinline__ void tc_sync()
 
 // Grid (member groups of 4, atom tiles of 128), groups fastest so the CTAs
 // that fill one tile's G rows run together.  Outputs U [N][P] (FP64) and
-// G [N][32][Pst] (FP32, member innermost).  Warp w: TMEM lane quarter w & 3 (its 32 atoms),
+// G [N][32][Pst] (member innermost; FP32, or FP16 when GH: the contraction
+// then reads half the bytes).  The network's arithmetic is the same either way.  Warp w: TMEM lane quarter w & 3 (its 32 atoms),
 // half w >> 2 (members {2h, 2h+1} in epilogue 1, descriptors [16h, 16h+16) in
 // epilogue 2).
+template <bool GH>
 __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, const unsigned char* __restrict__ qpack,
                                                         const unsigned char* __restrict__ packed,
-                                                        float* __restrict__ G, double* __restrict__ U, unsigned* err)
+                                                        void* __restrict__ Gv, double* __restrict__ U, unsigned* err)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     PopSmem& S = *reinterpret_cast<PopSmem*>(smem_raw);
@@ -345,14 +347,24 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
             for (int c = 0; c < 2; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(32 * m + 16 * half + 8 * c), r[m][c]);
         tc::tmem_ld_wait();
         if (valid) {
-            float* out = G + ((size_t)i * kNdes + 16 * half) * Pst + k0;
+            const size_t o0 = ((size_t)i * kNdes + 16 * half) * Pst + k0;
 #pragma unroll
             for (int c = 0; c < 2; ++c)
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    *reinterpret_cast<float4*>(out + (size_t)(8 * c + e) * Pst) =
-                        make_float4(__uint_as_float(r[0][c][e]), __uint_as_float(r[1][c][e]),
-                                    __uint_as_float(r[2][c][e]), __uint_as_float(r[3][c][e]));
+                for (int e = 0; e < 8; ++e) {
+                    const size_t o = o0 + (size_t)(8 * c + e) * Pst;
+                    const float g0 = __uint_as_float(r[0][c][e]), g1 = __uint_as_float(r[1][c][e]);
+                    const float g2 = __uint_as_float(r[2][c][e]), g3 = __uint_as_float(r[3][c][e]);
+                    if (GH) {  // four members as one 8-byte piece (k0 and Pst are multiples of 4)
+                        const __half2 a = __floats2half2_rn(g0, g1), b = __floats2half2_rn(g2, g3);
+                        uint2 v;
+                        v.x = *reinterpret_cast<const uint32_t*>(&a);
+                        v.y = *reinterpret_cast<const uint32_t*>(&b);
+                        *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(Gv) + o) = v;
+                    } else {
+                        *reinterpret_cast<float4*>(reinterpret_cast<float*>(Gv) + o) = make_float4(g0, g1, g2, g3);
+                    }
+                }
         }
     } else if (t == 0) {
         atomicOr(err, kErrTimeout);
@@ -369,8 +381,11 @@ size_t pop_tc_packed_bytes(int P) { return (size_t)((P + kTcGroup - 1) / kTcGrou
 
 int prepare_pop_tc()
 {
-    return cuda_fail(cudaFuncSetAttribute(k_pop_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PopSmem)),
-                     "population kernel shared memory");
+    int rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(PopSmem)), "population kernel shared memory");
+    if (rc) return rc;
+    return cuda_fail(cudaFuncSetAttribute(k_pop_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sizeof(PopSmem)), "population kernel shared memory");
 }
 
 size_t pop_tc_qpack_bytes(int N) { return (size_t)((N + kTile - 1) / kTile) * 2 * kTileBytes; }
@@ -383,8 +398,8 @@ int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t s
 }
 
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
-                  const float* w2t, const float* b2t, unsigned char* packed, float* G, double* U, unsigned* err,
-                  cudaStream_t st)
+                  const float* w2t, const float* b2t, unsigned char* packed, void* G, bool g_half, double* U,
+                  unsigned* err, cudaStream_t st)
 {
     if (n_neu > 32 || Pst % 4 != 0 || Pst < P) {
         set_error("tensor-core population path needs n_neu <= 32 and a member stride that is a multiple of 4");
@@ -394,7 +409,8 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, 
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
     k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
     const size_t smem = sizeof(PopSmem);
-    k_pop_tc<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
+    auto kern = g_half ? k_pop_tc<true> : k_pop_tc<false>;
+    kern<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
 }
 

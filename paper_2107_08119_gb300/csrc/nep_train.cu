@@ -32,6 +32,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "nep_dataset.cuh"
 
 namespace nep {
@@ -399,15 +401,31 @@ __global__ void __launch_bounds__(256) k_mlp_f32(int N, int P, int Pst, int n_ne
 // slot order.  The owner's virial contribution sum_i r_ij (x) p_kji
 // (r_ij = -r_ji) goes to W6[j][w][k].  No atomics: every value has one writer.
 // A launch covers the owners j0 <= j < j1 (a range of whole structures).
+// Element type of the partial-force buffer: FP32, or FP16 in the BF16
+// precision mode (half the DRAM traffic of the two passes; each loss term
+// averages the per-term rounding over all force components).  Two members
+// are stored and loaded together.
+__device__ __forceinline__ void pb_store2(float* o, float2 v) { *reinterpret_cast<float2*>(o) = v; }
+__device__ __forceinline__ void pb_store2(__half* o, float2 v)
+{
+    *reinterpret_cast<__half2*>(o) = __floats2half2_rn(v.x, v.y);
+}
+__device__ __forceinline__ float2 pb_load2(const float* o) { return *reinterpret_cast<const float2*>(o); }
+__device__ __forceinline__ float2 pb_load2(const __half* o)
+{
+    return __half22float2(*reinterpret_cast<const __half2*>(o));
+}
+
 constexpr int kOwnerChunk = 32;                                     // pairs staged per round
 constexpr int kRecFloats = (int)(sizeof(PairRec) / sizeof(float));  // 12
 constexpr int kAngFloats = kNA * kLmax * 3;                         // 72
 constexpr int kOwnerStage = kOwnerChunk * (kRecFloats + kAngFloats);  // floats per warp
 
+template <class PT>
 __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
-    int j0, int j1, int P, int Pst, const float* __restrict__ G, const float* __restrict__ B,
+    int j0, int j1, int P, int Pst, const PT* __restrict__ G, const float* __restrict__ B,
     const long long* __restrict__ pstart, const long long* __restrict__ rev, const PairRec* __restrict__ rec,
-    const long long* __restrict__ aidx, const float* __restrict__ ang, float* __restrict__ pbuf,
+    const long long* __restrict__ aidx, const float* __restrict__ ang, PT* __restrict__ pbuf,
     float* __restrict__ w6out, float* __restrict__ fown)
 {
     extern __shared__ float4 s_stage4[];
@@ -434,10 +452,9 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
         for (int t = lane; t < nq * kRecFloats / 4; t += 32)
             cp16(s_rec + 4 * t, reinterpret_cast<const float*>(rec + q0) + 4 * t);
         float2 g[kNdes];
-        const float* Gj = G + (size_t)j * kNdes * Pst + k0;
+        const PT* Gj = G + (size_t)j * kNdes * Pst + k0;
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v)
-            g[v] = ld ? *reinterpret_cast<const float2*>(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
+        for (int v = 0; v < kNdes; ++v) g[v] = ld ? pb_load2(Gj + (size_t)v * Pst) : make_float2(0.f, 0.f);
         // this chunk's angular records are the consecutive ones starting at
         // the first angular pair's index (owner order assigns them in turn)
         unsigned angmask = __ballot_sync(0xffffffffu, my_ai >= 0);
@@ -492,9 +509,9 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
                     }
                 }
                 if (ld) {
-                    float* o = pbuf + (size_t)rq * 3 * Pst + k0;
+                    PT* o = pbuf + (size_t)rq * 3 * Pst + k0;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(o + (size_t)c * Pst) = pv[c];
+                    for (int c = 0; c < 3; ++c) pb_store2(o + (size_t)c * Pst, pv[c]);
                 }
                 w6[0] = __ffma2_rn(bcast2(-r0), pv[0], w6[0]);  // xx
                 w6[1] = __ffma2_rn(bcast2(-r1), pv[1], w6[1]);  // yy
@@ -541,7 +558,7 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
 // with a neighbouring atom's slots are left alone.
 constexpr int kReceiverThreads = 256;
 
-__device__ __forceinline__ void discard_l2_lines(const float* lo, const float* hi, int lane)
+__device__ __forceinline__ void discard_l2_lines(const void* lo, const void* hi, int lane)
 {
     const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, b = (uintptr_t)hi & ~(uintptr_t)127;
     for (uintptr_t l = a + (uintptr_t)lane * 128; l < b; l += 32 * 128)
@@ -576,11 +593,11 @@ __device__ __forceinline__ void recv_load(RecvAtom& a, int i, int P, int Pst, in
     a.pe = pstart[i + 1];
 }
 
-template <int UNROLL>
+template <int UNROLL, class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
     int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
     const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
-    const float* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
+    const PT* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
     double* __restrict__ partials)
 {
     constexpr int kWarps = kReceiverThreads / 32;
@@ -606,10 +623,10 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
         if (ld) {
 #pragma unroll UNROLL
             for (long long p = cur.ps; p < cur.pe; ++p) {
-                const float* o = pbuf + (size_t)p * 3 * Pst + k0;
+                const PT* o = pbuf + (size_t)p * 3 * Pst + k0;
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
-                    const float2 x = *reinterpret_cast<const float2*>(o + (size_t)cc * Pst);
+                    const float2 x = pb_load2(o + (size_t)cc * Pst);
                     F[0][cc] -= x.x;
                     F[1][cc] -= x.y;
                 }
@@ -647,22 +664,24 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
 // slot order: the same arithmetic as k_contract, twice the bytes in flight.
 constexpr int kRecvStage = 16;
 
+template <class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
     int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
     const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
-    const float* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
+    const PT* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
     double* __restrict__ partials)
 {
     constexpr int kWarps = kReceiverThreads / 32;
+    constexpr int kPair = 2 * (int)sizeof(PT);  // bytes of one lane's two members
     __shared__ double red[kWarps][kMaxPop][8];
-    extern __shared__ float2 s_slots[];  // [warps][kRecvStage][3][Pst / 2]
+    extern __shared__ __align__(16) unsigned char s_slots_raw[];  // [warps][kRecvStage][3][Pst / 2] member pairs
     const int c = c0 + blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = 2 * lane;
     const bool on0 = k0 < P, on1 = k0 + 1 < P;
     const bool ld = k0 < Pst;
-    const int half = Pst / 2;  // float2 per row
-    float2* stage = s_slots + (size_t)warp * kRecvStage * 3 * half;
+    const int half = Pst / 2;  // member pairs per row
+    unsigned char* stage = s_slots_raw + (size_t)warp * kRecvStage * 3 * half * kPair;
 #pragma unroll
     for (int m = 0; m < 2; ++m)
         if (k0 + m < kMaxPop)
@@ -679,18 +698,21 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
             const int ns = (int)min((long long)kRecvStage, cur.pe - p0);
             if (ld)
                 for (int t = 0; t < ns * 3; ++t) {
-                    const float* src = pbuf + (size_t)(p0 * 3 + t) * Pst + k0;
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
-                                     (unsigned)__cvta_generic_to_shared(stage + (size_t)t * half + lane)),
-                                 "l"(src)
-                                 : "memory");
+                    const PT* src = pbuf + (size_t)(p0 * 3 + t) * Pst + k0;
+                    const unsigned dst =
+                        (unsigned)__cvta_generic_to_shared(stage + ((size_t)t * half + lane) * kPair);
+                    if (kPair == 8)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+                    else
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
                 }
             asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
             if (ld)
                 for (int t = 0; t < ns; ++t)
 #pragma unroll
                     for (int cc = 0; cc < 3; ++cc) {
-                        const float2 x = stage[(size_t)(3 * t + cc) * half + lane];
+                        const float2 x =
+                            pb_load2(reinterpret_cast<const PT*>(stage + ((size_t)(3 * t + cc) * half + lane) * kPair));
                         F[0][cc] -= x.x;
                         F[1][cc] -= x.y;
                     }
@@ -753,15 +775,19 @@ __device__ __forceinline__ void fx_add(int* hi, int* lo, float p)
 
 size_t fused_smem_bytes(int amax, int gm) { return (size_t)amax * gm * 48; }
 
-template <int GM>
+__device__ __forceinline__ float g_load(const float* p) { return *p; }
+__device__ __forceinline__ float g_load(const __half* p) { return __half2float(*p); }
+
+template <int GM, class GT>
 __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
     int P, int Pst, int n_groups, const int* __restrict__ s_order, const int* __restrict__ sstart,
-    const float* __restrict__ G, const double* __restrict__ U, const float* __restrict__ B,
+    const void* __restrict__ Gv, const double* __restrict__ U, const float* __restrict__ B,
     const long long* __restrict__ pstart, const int* __restrict__ pj, const PairRec* __restrict__ rec,
     const long long* __restrict__ astart, const float* __restrict__ ang, const float* __restrict__ f_tar,
     double* __restrict__ partials, unsigned* __restrict__ err)
 {
     constexpr int kApw = 32 / GM;  // owner atoms per warp
+    const GT* __restrict__ G = reinterpret_cast<const GT*>(Gv);
     constexpr int kWarps = kFusedThreads / 32;
     extern __shared__ int s_fx[];  // Fh [A][3][GM], Fl [A][3][GM] (int32), W6 [A][6][GM] (FP32)
     const int s = s_order[blockIdx.x / n_groups];
@@ -783,7 +809,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
         const int j = a0 + jl;
         float gv[kNdes];
 #pragma unroll
-        for (int v = 0; v < kNdes; ++v) gv[v] = on ? G[((size_t)j * kNdes + v) * Pst + k] : 0.f;
+        for (int v = 0; v < kNdes; ++v) gv[v] = on ? g_load(G + ((size_t)j * kNdes + v) * Pst + k) : 0.f;
         {  // own term G_kj . B_j
             const float4* B4 = reinterpret_cast<const float4*>(B + (size_t)j * kNdes * 3);
             float f[3] = {0.f, 0.f, 0.f};
@@ -874,6 +900,17 @@ __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
         block_sum_store<8>(v, partials + ((size_t)s * P + kg) * 8);
         __syncthreads();  // the block sum's shared scratch serves the next member
     }
+}
+
+// The fused contraction for GM members per block, reading G in FP16 (gh) or FP32.
+typedef void (*FusedKernel)(int, int, int, const int*, const int*, const void*, const double*, const float*,
+                            const long long*, const int*, const PairRec*, const long long*, const float*, const float*,
+                            double*, unsigned*);
+FusedKernel fused_kernel(int gm, bool gh)
+{
+    if (gm == 4) return gh ? k_contract_fused<4, __half> : k_contract_fused<4, float>;
+    if (gm == 8) return gh ? k_contract_fused<8, __half> : k_contract_fused<8, float>;
+    return gh ? k_contract_fused<16, __half> : k_contract_fused<16, float>;
 }
 
 // One block per member: per structure, the chunk sums (fixed order) or the
@@ -1212,51 +1249,70 @@ int prepare_evaluation(nep_dataset* ds, int P)
             return rc;
     }
     const int ostage = (kOwnerMaxThreads / 32) * kOwnerStage * (int)sizeof(float);
-    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, ostage),
-                        "contraction shared memory")))
-        return rc;
-    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (kReceiverThreads / 32) * kRecvStage * 3 * member_stride(kMaxPop) *
-                                                 (int)sizeof(float)),
-                        "contraction shared memory")))
+    const int rstage = (kReceiverThreads / 32) * kRecvStage * 3 * member_stride(kMaxPop) * (int)sizeof(float);
+    if ((rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ostage), "contraction shared memory")) ||
+        (rc = cuda_fail(cudaFuncSetAttribute(k_contract_owner<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ostage), "contraction shared memory")) ||
+        (rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             rstage), "contraction shared memory")) ||
+        (rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             rstage / 2), "contraction shared memory")))
         return rc;
     for (int gm = 4; gm <= 16; gm *= 2) {
         if (!fused_fits(ds, gm)) continue;
         const int smem = (int)fused_smem_bytes(ds->amax, gm);
-        auto kern = gm == 4 ? k_contract_fused<4> : (gm == 8 ? k_contract_fused<8> : k_contract_fused<16>);
-        if ((rc = cuda_fail(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
-                            "fused contraction shared memory")))
-            return rc;
+        for (int h = 0; h < 2; ++h)
+            if ((rc = cuda_fail(cudaFuncSetAttribute(fused_kernel(gm, h != 0),
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                                "fused contraction shared memory")))
+                return rc;
     }
     return prepare_pop_tc();
 }
 
 // The two contraction passes over the chunk range [c_lo, c_hi) (whole
 // structures): pass 1 on st, pass 2 on `p2`.
-void launch_contraction(const nep_dataset* ds, int P, int Pst, int c_lo, int c_hi, cudaStream_t st,
-                        cudaStream_t p2, bool fork, cudaEvent_t ev)
+template <class PT>
+void launch_contraction_t(const nep_dataset* ds, int P, int Pst, int c_lo, int c_hi, cudaStream_t st,
+                          cudaStream_t p2, bool fork, cudaEvent_t ev)
 {
     const EvalShape& sh = ds->shape;
     const int ow = sh.owner_warps == 8 ? 8 : 4;
     const int a0 = ds->h_cb[c_lo], a1 = ds->h_ce[c_hi - 1];
     const size_t ostage = (size_t)ow * kOwnerStage * sizeof(float);
-    k_contract_owner<<<std::min(blocks_for(a1 - a0, ow), 152 * 64 / ow), 32 * ow, ostage, st>>>(
-        a0, a1, P, Pst, ds->G, ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang, ds->pbuf, ds->w6, ds->fown);
+    PT* pbuf = reinterpret_cast<PT*>(ds->pbuf);
+    k_contract_owner<PT><<<std::min(blocks_for(a1 - a0, ow), 152 * 64 / ow), 32 * ow, ostage, st>>>(
+        a0, a1, P, Pst, reinterpret_cast<const PT*>(ds->G), ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang,
+        pbuf, ds->w6, ds->fown);
     if (fork) {
         cudaEventRecord(ev, st);
         cudaStreamWaitEvent(p2, ev, 0);
     }
     if (sh.recv_unroll == 16) {
-        const size_t smem = (size_t)(kReceiverThreads / 32) * kRecvStage * 3 * Pst * sizeof(float);
-        k_contract_staged<<<c_hi - c_lo, kReceiverThreads, smem, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin,
-                                                                       ds->chunk_end, ds->U, ds->pstart, ds->fown,
-                                                                       ds->pbuf, ds->w6, ds->f_tar, ds->partials);
+        const size_t smem = (size_t)(kReceiverThreads / 32) * kRecvStage * 3 * Pst * sizeof(PT);
+        k_contract_staged<PT><<<c_hi - c_lo, kReceiverThreads, smem, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin,
+                                                                           ds->chunk_end, ds->U, ds->pstart,
+                                                                           ds->fown, pbuf, ds->w6, ds->f_tar,
+                                                                           ds->partials);
     } else {
-        auto recv = sh.recv_unroll == 8 ? k_contract<8> : k_contract<4>;
+        auto recv = sh.recv_unroll == 8 ? k_contract<8, PT> : k_contract<4, PT>;
         recv<<<c_hi - c_lo, kReceiverThreads, 0, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin, ds->chunk_end,
-                                                       ds->U, ds->pstart, ds->fown, ds->pbuf, ds->w6, ds->f_tar,
+                                                       ds->U, ds->pstart, ds->fown, pbuf, ds->w6, ds->f_tar,
                                                        ds->partials);
     }
+}
+
+// The two contraction passes over the chunk range [c_lo, c_hi) (whole
+// structures): pass 1 on st, pass 2 on `p2`; the partial forces in FP16 when
+// `half` (BF16 precision mode), else FP32.
+void launch_contraction(const nep_dataset* ds, int P, int Pst, int c_lo, int c_hi, cudaStream_t st,
+                        cudaStream_t p2, bool fork, cudaEvent_t ev, bool half)
+{
+    if (half)
+        launch_contraction_t<__half>(ds, P, Pst, c_lo, c_hi, st, p2, fork, ev);
+    else
+        launch_contraction_t<float>(ds, P, Pst, c_lo, c_hi, st, p2, fork, ev);
 }
 
 // Launches of one population evaluation (no allocation, no attribute calls:
@@ -1278,8 +1334,10 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
     k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t, ds->b2t);
     int rc;
     if (precision == NEP_PREC_BF16) {
+        // G in FP16: the contraction reads half the bytes (the loss terms
+        // average its rounding over all force components)
         if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
-                                ds->U, m->d_err, st)))
+                                true, ds->U, m->d_err, st)))
             return rc;
     } else {
         const long long pairs = (ds->N + 1) / 2;
@@ -1293,10 +1351,10 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         // one block per (structure, member group), largest structures first
         const int gm = sh.fused, groups = (P + gm - 1) / gm;
         const size_t smem = fused_smem_bytes(ds->amax, gm);
-        auto kern = gm == 4 ? k_contract_fused<4> : (gm == 8 ? k_contract_fused<8> : k_contract_fused<16>);
-        kern<<<ds->S * groups, kFusedThreads, smem, st>>>(P, Pst, groups, ds->s_order, ds->sstart, ds->G, ds->U,
-                                                          ds->B, ds->pstart, ds->pj, ds->rec, ds->astart, ds->ang,
-                                                          ds->f_tar, ds->partials, m->d_err);
+        const bool gh = precision == NEP_PREC_BF16;
+        fused_kernel(gm, gh)<<<ds->S * groups, kFusedThreads, smem, st>>>(
+            P, Pst, groups, ds->s_order, ds->sstart, ds->G, ds->U, ds->B, ds->pstart, ds->pj, ds->rec, ds->astart,
+            ds->ang, ds->f_tar, ds->partials, m->d_err);
         k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, nullptr, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
                                   z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
         return cuda_fail(cudaGetLastError(), "population evaluation kernels");
@@ -1324,11 +1382,11 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         }
     }
     if (n_ranges == 1) {
-        launch_contraction(ds, P, Pst, 0, C, st, st, false, nullptr);
+        launch_contraction(ds, P, Pst, 0, C, st, st, false, nullptr, precision == NEP_PREC_BF16);
     } else {
         int c_lo = 0;
         for (int w = 0; w < n_ranges; ++w) {
-            launch_contraction(ds, P, Pst, c_lo, ends[w], st, ds->aux, true, ds->ev_wave[w]);
+            launch_contraction(ds, P, Pst, c_lo, ends[w], st, ds->aux, true, ds->ev_wave[w], precision == NEP_PREC_BF16);
             c_lo = ends[w];
         }
         cudaEventRecord(ds->ev_join, ds->aux);

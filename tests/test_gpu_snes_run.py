@@ -90,8 +90,11 @@ def test_every_shape_gives_identical_losses(N, full_set, prec):
             for _ in range(3):  # repeated: a race would show as a changed bit
                 got = ds.evaluate(zp, prec).cpu().numpy()
                 assert np.array_equal(got, ref), sh
-    # the two forms: the same losses up to the two-pass form's FP32 force sums
-    assert np.allclose(refs["fused"], refs["two-pass"], rtol=1e-6, atol=0.0), \
+    # the two forms: the same losses up to the two-pass form's force sums
+    # (FP32; in BF16 mode its partial forces pass through FP16, ~1e-6 relative
+    # in each loss term after the average over all force components)
+    rtol = 1e-6 if prec == N.PREC_FP32 else 2e-5
+    assert np.allclose(refs["fused"], refs["two-pass"], rtol=rtol, atol=0.0), \
         np.abs(refs["fused"] / refs["two-pass"] - 1).max()
     ds.set_shape()
     model.sync_status()
