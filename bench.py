@@ -344,6 +344,25 @@ def run_gpu(args, rank, world, local):
         steady = {"first_step": W + K + args.steady_skip, "steps": args.steady_steps, "ms_per_step": ms_s,
                   "atom_steps_per_s": n / (ms_s / 1e3), "list_rebuilds": rb_s,
                   "rebuilds_per_step": rb_s / args.steady_steps}
+        # the cost of one rebuild on the molten state: a phase-timed stretch
+        # (kernels launched one by one), its list time net of the gated list
+        # launches of the steps without a rebuild (their cost per step taken
+        # from the crystal phase pass when that had no rebuild)
+        model.profile_read()
+        model.profile(True)
+        r_p0 = md.rebuild_count()
+        md.step(p, v, args.steady_phase_steps, 1.0)
+        torch.cuda.synchronize()
+        model.profile(False)
+        prof_m = model.profile_read()
+        rb_p = md.rebuild_count() - r_p0
+        steady["phase_ms_per_step"] = {k: v_[0] / args.steady_phase_steps for k, v_ in prof_m.items()}
+        steady["phase_steps"] = args.steady_phase_steps
+        steady["phase_list_rebuilds"] = rb_p
+        if rebuilds_phase == 0 and rb_p > 0:
+            gate = prof["neighbor"][0] / K
+            steady["list_gate_ms_per_step"] = gate
+            steady["list_ms_per_rebuild"] = (prof_m["neighbor"][0] - gate * (args.steady_phase_steps - rb_p)) / rb_p
 
     t_max, e2e_s = max_over_ranks([ms, e2e_s], dist, "cuda")
     value = job_throughput(world, n, K, t_max)
@@ -369,7 +388,6 @@ def run_gpu(args, rank, world, local):
                        "mean_neighbors_rcR": m_r, "mean_neighbors_rcA": m_a,
                        "mean_neighbors_start_end": [[m_r0, m_a0], [m_r1, m_a1]],
                        "phase_ms_per_step": {k: v[0] / K for k, v in prof.items()},
-                       "list_ms_per_rebuild": prof["neighbor"][0] / max(1, rebuilds_phase),
                        "list_rebuilds_phase_pass": rebuilds_phase,
                        "energy_drift_eV_per_atom": float(np.abs(etot - etot[0]).max() / n)},
             "steady_state": steady,
@@ -834,6 +852,8 @@ def main():
     ap.add_argument("--steady-skip", type=int, default=500,
                     help="MD steps after the timed window before the steady-state window")
     ap.add_argument("--steady-steps", type=int, default=200, help="MD steps of the steady-state window (0: none)")
+    ap.add_argument("--steady-phase-steps", type=int, default=30,
+                    help="phase-timed MD steps after the steady-state window (the cost of one rebuild)")
     ap.add_argument("--only", default="all", choices=["all", "md", "snes"],
                     help="md: the timed MD steps alone (no e2e, SNES or CPU legs); snes: the SNES legs alone. "
                          "Small single-purpose runs for profiler captures.")

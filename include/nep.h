@@ -403,7 +403,7 @@ int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
  *   [2] discard     0 or 1: the second pass drops from L2 the partial-force
  *                   lines it has consumed (no write-back of dead data).
  *   [3] threads     128 or 256 threads per block of the FP32 network.
- *   [4] unroll      4 or 8 partial-force slots in flight per warp in the
+ *   [4] unroll      4, 8 or 12 partial-force slots in flight per warp in the
  *                   second contraction pass, or 16: staged in shared memory
  *                   16 slots at a time by asynchronous copies.
  * Within each form (fused, or two passes) no shape changes a result bit
@@ -422,7 +422,7 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape);
  * the fastest on the dataset.  Candidates: the fused contraction with 4, 8
  * or 16 members per block (where the shared memory fits; the owner atoms per
  * warp are 32 / members), and the two passes with waves 1, 2, 4 x owner
- * warps 4, 8 x discard 0, 1 when waves > 1 x unroll 4, 8, 16; each with
+ * warps 4, 8 x discard 0, 1 when waves > 1 x unroll 4, 8, 12, 16; each with
  * network threads 128, 256 in FP32 mode.  Synchronises the stream.
  * shape_out: host int[6] or NULL; ms_out: host, the best shape's time per
  * evaluation, or NULL.

@@ -42,7 +42,7 @@ struct EvalShape {
     int owner_warps = 4;    // warps per block of the owner pass (4 or 8)
     int discard = 0;        // pass 2 drops the partial-force lines it has read from L2
     int mlp_threads = 256;  // threads per block of the FP32 network (128 or 256)
-    int recv_unroll = 4;    // slots in flight per warp in the receiver pass (4 or 8)
+    int recv_unroll = 4;    // slots in flight per warp in the receiver pass (4, 8 or 12; 16: staged)
     int fused = 0;          // 0: the two contraction passes; 4, 8 or 16: the fused contraction with
                             // this many members per block (one block per structure and member group)
 };

@@ -1136,7 +1136,7 @@ bool valid_shape(const nep_dataset* ds, const EvalShape& h)
 {
     return h.waves >= 1 && h.waves <= kMaxWaves && (h.owner_warps == 4 || h.owner_warps == 8) &&
            (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
-           (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 16) &&
+           (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 12 || h.recv_unroll == 16) &&
            (h.fused == 0 || ((h.fused == 4 || h.fused == 8 || h.fused == 16) && fused_fits(ds, h.fused)));
 }
 
@@ -1296,7 +1296,7 @@ void launch_contraction_t(const nep_dataset* ds, int P, int Pst, int c_lo, int c
                                                                            ds->fown, pbuf, ds->w6, ds->f_tar,
                                                                            ds->partials);
     } else {
-        auto recv = sh.recv_unroll == 8 ? k_contract<8, PT> : k_contract<4, PT>;
+        auto recv = sh.recv_unroll == 12 ? k_contract<12, PT> : (sh.recv_unroll == 8 ? k_contract<8, PT> : k_contract<4, PT>);
         recv<<<c_hi - c_lo, kReceiverThreads, 0, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin, ds->chunk_end,
                                                        ds->U, ds->pstart, ds->fown, pbuf, ds->w6, ds->f_tar,
                                                        ds->partials);
@@ -1883,7 +1883,7 @@ int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
     h.fused = shape[5];
     if (!valid_shape(ds, h)) {
         set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
-                  "receiver unroll 4, 8 or 16 (staged), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
+                  "receiver unroll 4, 8, 12 or 16 (staged), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
                   "48 bytes of shared memory at most %zu)",
                   kMaxWaves, ds->amax, kFusedSmemMax);
         return NEP_ERR_ARG;
@@ -1925,7 +1925,7 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
         for (int ow = 4; ow <= 8; ow += 4)
             for (int dc = 0; dc <= (w > 1 ? 1 : 0); ++dc)
                 for (int mt = 128; mt <= 256; mt += 128)
-                    for (int ru = 4; ru <= 16; ru *= 2) {
+                    for (int ru : {4, 8, 12, 16}) {
                         if (precision == NEP_PREC_BF16 && mt == 128) continue;  // the FP32 network is not launched
                         EvalShape h;
                         h.waves = w;
