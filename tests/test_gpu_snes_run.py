@@ -162,3 +162,37 @@ def test_run_equals_steps(N, full_set, shape):
     b.close()
     ds.set_shape()
     model.sync_status()
+
+
+def test_fused_shape_follows_the_largest_structure(N):
+    """The fused contraction keeps a structure's force sums in shared memory
+    (atoms x members x 48 bytes, at most 220 KB): with a 600-atom structure in
+    the set, 8 or 16 members per block do not fit, the default becomes 4
+    members per block, the larger shapes are rejected, and the fused and
+    two-pass forms agree."""
+    import torch
+    rng = np.random.default_rng(11)
+    pos, box = inputs.diamond(5, 5, 3)
+    big = {"pos": inputs.displace(pos, 0.1, rng), "box": box}
+    structures = inputs.training_structures(6, seed_stream=13) + [big]
+    assert len(big["pos"]) == 600
+    model = N.NEP(f32_exact(inputs.random_z(1021, rng)).astype(np.float32))
+    E, F, W = _gpu_labels(N, model, structures)
+    ds = N.Dataset(model, structures, E, F, W)
+    assert ds.counts()["largest_structure"] == 600
+    assert ds.shape()["fused"] == 4
+    for bad in (8, 16):
+        with pytest.raises(N.NepError) as e:
+            ds.set_shape(fused=bad)
+        assert e.value.code == -1
+    zp = torch.tensor(f32_exact(rng.normal(0.0, 0.1, size=(12, 1021))), dtype=torch.float32, device="cuda")
+    for prec in (N.PREC_FP32, N.PREC_BF16):
+        ds.set_shape(fused=4)
+        a = ds.evaluate(zp, prec).cpu().numpy()
+        ds.set_shape(fused=0)
+        b = ds.evaluate(zp, prec).cpu().numpy()
+        assert np.isfinite(a).all()
+        assert np.allclose(a, b, rtol=1e-6 if prec == N.PREC_FP32 else 2e-5, atol=0.0), np.abs(a / b - 1).max()
+    model.sync_status()
+    ds.close()
+    model.close()
