@@ -24,6 +24,7 @@ namespace {
 constexpr int kSiteThreads = kSiteAtomsPerBlock;  // one thread per atom
 constexpr int kAsmThreads = 128;
 constexpr int kStageSlots = 96;  // slots per atom staged in shared memory
+static_assert(kStageSlots <= 256, "original slot numbers are stored in one byte");
 
 // Copy the block's neighbour slots (slot-major: slot k of the block's atoms is
 // one contiguous run) into shared memory with 4-byte asynchronous copies, all
@@ -40,6 +41,50 @@ __device__ __forceinline__ void stage_slots(const int* __restrict__ nbr, int n, 
                          : "memory");
         }
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
+// Compacts a thread's staged slot column (cnt entries, s_col[k * kSiteThreads])
+// in place to the slots within rc2max, in their order, and records each kept
+// entry's original slot in o_col; returns the number kept.  The test is the
+// one the site passes apply (the same pair vector and distance square), so
+// the passes see exactly the slots they would have used; slots beyond the
+// cutoff (about 40 % of a Verlet list with a 1 A skin) then cost no loop
+// iteration there.  Four slots are gathered at a time.
+__device__ __forceinline__ int compact_slots(int i, int cnt, int* s_col, unsigned char* o_col,
+                                             const float* __restrict__ xh, const float* __restrict__ xl, int n,
+                                             const Box& box, float rc2max)
+{
+    float hi[3], li[3];
+    load_pos(xh, xl, n, i, hi, li);
+    int kept = 0;
+    for (int k0 = 0; k0 < cnt; k0 += 4) {
+        int v[4];
+        float4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (k0 + u < cnt) ? s_col[(k0 + u) * kSiteThreads] : 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = v[u] & 0xFFFFFF;  // 0 past the end: a valid atom
+            a[u] = NEP_LDG(reinterpret_cast<const float4*>(xh) + j);
+            b[u] = NEP_LDG(reinterpret_cast<const float4*>(xl) + j);
+        }
+        // every read of this group precedes the writes, and kept <= k0 + u
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k0 + u < cnt) {
+                const float hj[3] = {a[u].x, a[u].y, a[u].z}, lj[3] = {b[u].x, b[u].y, b[u].z};
+                float rx, ry, rz;
+                pair_vector(i, v[u] & 0xFFFFFF, v[u] >> 24, hi, li, hj, lj, box, rx, ry, rz);
+                const float d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                if (d2 < rc2max) {
+                    s_col[kept * kSiteThreads] = v[u];
+                    o_col[kept * kSiteThreads] = (unsigned char)(k0 + u);
+                    ++kept;
+                }
+            }
+        }
+    }
+    return kept;
 }
 
 // STAGED: the neighbour capacity fits the shared-memory staging (m_cap <= kStageSlots).
@@ -60,11 +105,18 @@ __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const i
     // every lane runs the site function (the warp walks neighbour ranks in
     // step); lanes past the last atom see no neighbours and store nothing
     const bool active = i < n;
-    const int cnt = active ? min(count[i], m_cap) : 0;
+    int cnt = active ? min(count[i], m_cap) : 0;
     int* s_nbr = reinterpret_cast<int*>(s_w + ((n_par + 31) / 32) * 32);
-    if (STAGED) stage_slots(nbr, n, i, active, cnt, s_nbr);
+    unsigned char* s_orig = reinterpret_cast<unsigned char*>(s_nbr + kStageSlots * kSiteThreads);
+    if (STAGED) {
+        stage_slots(nbr, n, i, active, cnt, s_nbr);
+        if (active)
+            cnt = compact_slots(i, cnt, s_nbr + threadIdx.x, s_orig + threadIdx.x, xh, xl, n, box,
+                                fmaxf(P.rcR2, P.rcA2));
+    }
     __syncthreads();
-    const SlotTable T = STAGED ? SlotTable{s_nbr, kSiteThreads, (int)threadIdx.x} : SlotTable{nbr, n, i};
+    const SlotTable T = STAGED ? SlotTable{s_nbr, kSiteThreads, (int)threadIdx.x, s_orig}
+                               : SlotTable{nbr, n, i};
     float uh, ul;
     const PfOut out{pf + 4 * (size_t)(active ? i : 0), (size_t)4 * n, 1};
     site_partial_forces<D>(active ? i : 0, active, n, cnt, T, xh, xl, box, P, out, uh, ul);
@@ -159,7 +211,9 @@ int launch_site(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, dou
     P.typed = a.typed;
     const int n_par = (D::Ndes + 2) * a.n_neu + 1;
     nblocks = blocks_for(n, kSiteThreads);
-    const size_t smem = (((size_t)n_par + 31) / 32 * 32 + (size_t)kStageSlots * kSiteThreads) * sizeof(float);
+    // weights, the staged slots and their original slot numbers (one byte each)
+    const size_t smem = (((size_t)n_par + 31) / 32 * 32 + (size_t)kStageSlots * kSiteThreads) * sizeof(float) +
+                        (size_t)kStageSlots * kSiteThreads;
     const bool staged = a.box.nc[0] >= 0 && nl.m_cap <= kStageSlots;
     if (staged) {
         int rc = cuda_fail(cudaFuncSetAttribute(k_site<true, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),

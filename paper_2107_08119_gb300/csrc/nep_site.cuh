@@ -326,6 +326,21 @@ __host__ __device__ __forceinline__ void neuron_out(float w2, float xm, const fl
     s = t;
     c += e + ep;
     const float d = w2 * fmaf(-xm, xm, 1.f);
+#ifdef __CUDA_ARCH__
+    if constexpr (ND % 4 == 0) {
+        // the row is 16-byte aligned (shared memory, ND floats per row)
+        const float4* row4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+        for (int v = 0; v < ND; v += 4) {
+            const float4 t = row4[v / 4];
+            G[v] = fmaf(d, t.x, G[v]);
+            G[v + 1] = fmaf(d, t.y, G[v + 1]);
+            G[v + 2] = fmaf(d, t.z, G[v + 2]);
+            G[v + 3] = fmaf(d, t.w, G[v + 3]);
+        }
+        return;
+    }
+#endif
 #pragma unroll
     for (int v = 0; v < ND; ++v) G[v] = fmaf(d, row[v], G[v]);
 }
@@ -346,10 +361,34 @@ __host__ __device__ __forceinline__ void network(const float* w, int n_neu, cons
     float s = 0.f, c = 0.f;
     for (int mu = 0; mu < n_neu; ++mu) {
         const float* row = w + mu * ND;
-        float a = -b1[mu], ca = 0.f;
+        // four interleaved compensated chains (descriptor v in chain v mod 4),
+        // so that consecutive steps do not wait on each other, joined by
+        // error-free sums
+        float a[4] = {-b1[mu], 0.f, 0.f, 0.f}, ca[4] = {0.f, 0.f, 0.f, 0.f};
+#ifdef __CUDA_ARCH__
+        if constexpr (ND % 4 == 0) {
+            // 16-byte loads of the row (shared memory, aligned for ND % 4 == 0)
+            const float4* row4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
-        for (int v = 0; v < ND; ++v) kahan_step(row[v], q[v], a, ca);
-        neuron_out(w2[mu], tanhf(a - ca), row, s, c, G);
+            for (int v = 0; v < ND; v += 4) {
+                const float4 t = row4[v / 4];
+                kahan_step(t.x, q[v], a[0], ca[0]);
+                kahan_step(t.y, q[v + 1], a[1], ca[1]);
+                kahan_step(t.z, q[v + 2], a[2], ca[2]);
+                kahan_step(t.w, q[v + 3], a[3], ca[3]);
+            }
+        } else
+#endif
+        {
+#pragma unroll
+            for (int v = 0; v < ND; ++v) kahan_step(row[v], q[v], a[v & 3], ca[v & 3]);
+        }
+        float s01, e01, s23, e23, sa, ea;
+        two_sum(a[0], a[1], s01, e01);
+        two_sum(a[2], a[3], s23, e23);
+        two_sum(s01, s23, sa, ea);
+        const float comp = ((ca[0] + ca[1]) + (ca[2] + ca[3])) - ((e01 + e23) + ea);
+        neuron_out(w2[mu], tanhf(sa - comp), row, s, c, G);
     }
     float t, e;
     two_sum(s, -b2, t, e);
@@ -372,6 +411,9 @@ struct SlotTable {
     const int* slots;
     int stride;
     int idx;
+    // for a compacted table (only the slots within the cutoff, in their
+    // order): the original slot of entry k at orig[k * stride + idx]
+    const unsigned char* orig = nullptr;
 };
 
 __host__ __device__ __forceinline__ void fetch_slot(const SlotTable& T, const float* __restrict__ xh,
@@ -688,7 +730,8 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
         float px, py, pz, dE;
         pair_partial_force<D>(r, r_lo, d2, pair_weight(P, zi, cur.z), P, S, GR, px, py, pz, dE);
         dU += dE;
-        float* p = out.base + (size_t)k * out.slot_stride;
+        const int ko = nbr.orig ? (int)nbr.orig[(size_t)k * nbr.stride + nbr.idx] : k;
+        float* p = out.base + (size_t)ko * out.slot_stride;
         p[0] = px;
         p[out.comp_stride] = py;
         p[2 * out.comp_stride] = pz;
