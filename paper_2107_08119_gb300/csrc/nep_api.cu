@@ -174,6 +174,7 @@ int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_par
         dev_free(nl.xl);
         dev_free(nl.atom_cell);
         dev_free(nl.cell_atoms);
+        dev_free(nl.mask);
         dev_free(ws.force);
         nl.n_cap = nl.m_cap = 0;
         ws.force_cap = 0;
@@ -183,7 +184,8 @@ int ensure_workspace(Workspace& ws, int n, int m_cap, int ncell, int nblocks_par
             (rc = dev_alloc(&nl.vala, N * M, "neighbour list copy")) ||
             (rc = dev_alloc(&nl.pf, N * M * 4, "partial forces")) || (rc = dev_alloc(&nl.xh, N * 4, "positions")) ||
             (rc = dev_alloc(&nl.xl, N * 4, "positions")) || (rc = dev_alloc(&nl.atom_cell, N, "cell index")) ||
-            (rc = dev_alloc(&nl.cell_atoms, N, "cell atoms")) || (rc = dev_alloc(&ws.force, N * 3, "forces")))
+            (rc = dev_alloc(&nl.cell_atoms, N, "cell atoms")) || (rc = dev_alloc(&nl.mask, N * 3, "slot masks")) ||
+            (rc = dev_alloc(&ws.force, N * 3, "forces")))
             return rc;
         nl.n_cap = n;
         nl.m_cap = m_cap;
@@ -229,6 +231,7 @@ void free_workspace(Workspace& ws)
     dev_free(nl.cell_start);
     dev_free(nl.cell_fill);
     dev_free(nl.cell_atoms);
+    dev_free(nl.mask);
     dev_free(ws.partials);
     dev_free(ws.force);
     dev_free(ws.plain);

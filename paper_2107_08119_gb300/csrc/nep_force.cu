@@ -49,11 +49,13 @@ __device__ __forceinline__ void stage_slots(const int* __restrict__ nbr, int n, 
 // one the site passes apply (the same pair vector and distance square), so
 // the passes see exactly the slots they would have used; slots beyond the
 // cutoff (about 40 % of a Verlet list with a 1 A skin) then cost no loop
-// iteration there.  Four slots are gathered at a time.
+// iteration there.  Four slots are gathered at a time.  Bit k of mb is set
+// for each kept slot k.
 __device__ __forceinline__ int compact_slots(int i, int cnt, int* s_col, unsigned char* o_col,
                                              const float* __restrict__ xh, const float* __restrict__ xl, int n,
-                                             const Box& box, float rc2max)
+                                             const Box& box, float rc2max, unsigned (&mb)[3])
 {
+    mb[0] = mb[1] = mb[2] = 0u;
     float hi[3], li[3];
     load_pos(xh, xl, n, i, hi, li);
     int kept = 0;
@@ -80,6 +82,8 @@ __device__ __forceinline__ int compact_slots(int i, int cnt, int* s_col, unsigne
                     s_col[kept * kSiteThreads] = v[u];
                     o_col[kept * kSiteThreads] = (unsigned char)(k0 + u);
                     ++kept;
+                    const int k = k0 + u;
+                    mb[k >> 5] |= 1u << (k & 31);
                 }
             }
         }
@@ -95,7 +99,8 @@ __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const i
                                                        const float* __restrict__ xl, Box box,
                                                        const float* __restrict__ z, int n_par, SiteParams P,
                                                        float* __restrict__ pf, double* __restrict__ e_atom,
-                                                       double* __restrict__ e_partials, unsigned* err)
+                                                       double* __restrict__ e_partials, unsigned* err,
+                                                       unsigned* __restrict__ mask)
 {
     extern __shared__ float s_w[];
     for (int t = threadIdx.x; t < n_par; t += blockDim.x) s_w[t] = z[t];
@@ -110,9 +115,16 @@ __global__ void __launch_bounds__(kSiteThreads) k_site(int n, int m_cap, const i
     unsigned char* s_orig = reinterpret_cast<unsigned char*>(s_nbr + kStageSlots * kSiteThreads);
     if (STAGED) {
         stage_slots(nbr, n, i, active, cnt, s_nbr);
-        if (active)
+        if (active) {
+            unsigned mb[3];
             cnt = compact_slots(i, cnt, s_nbr + threadIdx.x, s_orig + threadIdx.x, xh, xl, n, box,
-                                fmaxf(P.rcR2, P.rcA2));
+                                fmaxf(P.rcR2, P.rcA2), mb);
+            if (mask) {
+                mask[i] = mb[0];
+                mask[(size_t)n + i] = mb[1];
+                mask[(size_t)2 * n + i] = mb[2];
+            }
+        }
     }
     __syncthreads();
     const SlotTable T = STAGED ? SlotTable{s_nbr, kSiteThreads, (int)threadIdx.x, s_orig}
@@ -136,7 +148,8 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(int n, int m_cap, floa
                                                           Box box, const float* __restrict__ pf,
                                                           float* __restrict__ force, float* __restrict__ virial_atom,
                                                           double* __restrict__ partials, unsigned* err,
-                                                          double* __restrict__ vel, double hdtm, double kef)
+                                                          double* __restrict__ vel, double hdtm, double kef,
+                                                          const unsigned* __restrict__ mask)
 {
     constexpr int K = MD ? 13 : 9;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,7 +161,7 @@ __global__ void __launch_bounds__(kAsmThreads) k_assemble(int n, int m_cap, floa
         // memory (as the site pass does) cost this pass occupancy and time
         const SlotTable T{nbr, n, i};
         float F[3], W[9];
-        assemble_atom(i, n, m_cap, rc2max, count, T, rev, xh, xl, box, pf, F, W);
+        assemble_atom(i, n, m_cap, rc2max, count, T, rev, xh, xl, box, pf, F, W, mask);
         if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) atomicOr(err, kErrNonFinite);
         if (force) {
             force[i] = F[0];
@@ -222,7 +235,9 @@ int launch_site(const ForceArgs& a, NeighborList& nl, int n, double* e_atom, dou
     }
     auto kern = staged ? k_site<true, D> : k_site<false, D>;
     kern<<<nblocks, kSiteThreads, staged ? smem : (((size_t)n_par + 31) / 32 * 32) * sizeof(float), st>>>(
-        n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box, a.z, n_par, P, nl.pf, e_atom, e_partials, d_err);
+        n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box, a.z, n_par, P, nl.pf, e_atom, e_partials, d_err,
+        staged ? nl.mask : nullptr);
+    nl.mask_set = staged && nl.mask != nullptr;
     return cuda_fail(cudaGetLastError(), "site kernel");
 }
 
@@ -250,7 +265,8 @@ int launch_assemble(const AssembleArgs& a, NeighborList& nl, int n, float* force
     auto kern = md ? k_assemble<true> : k_assemble<false>;
     kern<<<nblocks, kAsmThreads, 0, st>>>(n, nl.m_cap, rc2, nl.count, nl.nbr, nl.rev, nl.xh, nl.xl, a.box, nl.pf,
                                           force, virial_atom, partials, d_err, md ? a.vel : nullptr,
-                                          md ? a.half_dt_over_m : 0.0, md ? a.ke_factor : 0.0);
+                                          md ? a.half_dt_over_m : 0.0, md ? a.ke_factor : 0.0,
+                                          nl.mask_set ? nl.mask : nullptr);
     return cuda_fail(cudaGetLastError(), "assemble kernel");
 }
 

@@ -286,6 +286,12 @@ struct NeighborList {
     int* cell_start = nullptr;
     int* cell_fill = nullptr;
     int* cell_atoms = nullptr;
+    // [3][n] words: bit k of atom i set when slot k lies within the cutoff,
+    // written by the site pass when it compacts its staged slots; `mask_set`
+    // (host) says whether the last site pass launched wrote them, so that
+    // the assembly skips the other slots' loads.
+    unsigned* mask = nullptr;
+    bool mask_set = false;
 };
 
 struct Workspace {

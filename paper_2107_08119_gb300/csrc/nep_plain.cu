@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_pf(int n, int m_cap, co
 int launch_plain_site(const ForceArgs& a, NeighborList& nl, int n, float* q, float* G, double* e_atom,
                       double* e_partials, unsigned* d_err, cudaStream_t st, int& nblocks)
 {
+    nl.mask_set = false;  // the assembly tests every slot's distance itself
     nblocks = (n + kPlainThreads - 1) / kPlainThreads;
     k_plain_desc<<<nblocks, kPlainThreads, 0, st>>>(n, nl.m_cap, nl.count, nl.nbr, nl.xh, nl.xl, a.box, a.rcR, a.rcA,
                                                     q, d_err);

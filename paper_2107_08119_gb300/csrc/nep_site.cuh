@@ -742,11 +742,24 @@ __host__ __device__ __forceinline__ void site_partial_forces(int i, bool active,
 // Force and per-atom virial of atom i from the stored partial forces
 // (pf[k][i] float4 records, see nep_internal.cuh):
 //   F_i = sum_j (p_ij - p_ji),  W_i^{ab} = sum_j r_ij^a p_ji^b   (Eqs. 4-6).
+// With `mask` (the site pass's in-cutoff slot bits, [3][n]) the slots
+// outside the cutoff issue no loads at all; without it every slot is
+// loaded and tested.
 // Software-pipelined two slots deep: while slot k is summed, slot k+1's
 // neighbour position and both partial-force records are in flight (their
 // addresses came in one iteration earlier), and slot k+2's list and
 // reverse entries are being loaded, so no gather waits on the load of its
 // own address.  The sums run in slot order.
+// count of leading zero bits of a nonzero word
+__host__ __device__ __forceinline__ int clz32(unsigned x)
+{
+#ifdef __CUDA_ARCH__
+    return __clz((int)x);
+#else
+    return __builtin_clz(x);
+#endif
+}
+
 struct AsmSlot {
     int v;
     float h[3], l[3];
@@ -757,11 +770,21 @@ __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, 
                                                        const int* __restrict__ count, const SlotTable& nbr,
                                                        const int* __restrict__ rev, const float* __restrict__ xh,
                                                        const float* __restrict__ xl, const Box& box,
-                                                       const float* __restrict__ pf, float (&F)[3], float (&W)[9])
+                                                       const float* __restrict__ pf, float (&F)[3], float (&W)[9],
+                                                       const unsigned* __restrict__ mask = nullptr)
 {
     float hi[3], li[3];
     load_pos(xh, xl, n, i, hi, li);
-    const int cnt = imin(count[i], m_cap);
+    int cnt = imin(count[i], m_cap);
+    unsigned mb[3] = {~0u, ~0u, ~0u};
+    if (mask) {
+        mb[0] = mask[i];
+        mb[1] = mask[(size_t)n + i];
+        mb[2] = mask[(size_t)2 * n + i];
+        // the loop ends after the last kept slot
+        cnt = mb[2] ? 96 - clz32(mb[2]) : mb[1] ? 64 - clz32(mb[1]) : mb[0] ? 32 - clz32(mb[0]) : 0;
+    }
+    auto kept = [&](int k) { return ((k < 32 ? mb[0] >> k : k < 64 ? mb[1] >> (k - 32) : mb[2] >> (k - 64)) & 1u) != 0u; };
 #pragma unroll
     for (int a = 0; a < 3; ++a) F[a] = 0.f;
 #pragma unroll
@@ -769,14 +792,14 @@ __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, 
     const float4* pf4 = reinterpret_cast<const float4*>(pf);
     // list value and reverse slot of slot k
     auto load_idx = [&](int k, int& v, int& kr) {
-        if (k < cnt) {
+        if (k < cnt && kept(k)) {
             v = nbr.slots[(size_t)k * nbr.stride + nbr.idx];
             kr = NEP_LDG(rev + (size_t)k * n + i);
         }
     };
     // the gathers of slot k, given its list value and reverse slot
     auto load_data = [&](int k, int v, int kr, AsmSlot& d) {
-        if (k < cnt) {
+        if (k < cnt && kept(k)) {
             const int j = v & 0xFFFFFF;
             d.v = v;
             load_pos(xh, xl, n, j, d.h, d.l);
@@ -793,6 +816,7 @@ __host__ __device__ __forceinline__ void assemble_atom(int i, int n, int m_cap, 
         const AsmSlot cur = nx;
         load_data(k + 1, v2, kr2, nx);
         load_idx(k + 2, v2, kr2);
+        if (!kept(k)) continue;
         const int j = cur.v & 0xFFFFFF;
         float r[3];
         pair_vector(i, j, cur.v >> 24, hi, li, cur.h, cur.l, box, r[0], r[1], r[2]);
