@@ -45,6 +45,8 @@ struct EvalShape {
     int recv_unroll = 4;    // slots in flight per warp in the receiver pass (4, 8 or 12; 16: staged)
     int fused = 0;          // 0: the two contraction passes; 4, 8 or 16: the fused contraction with
                             // this many members per block (one block per structure and member group)
+    int owner_tc = 0;       // 1: in BF16 precision the first of the two passes runs on the tensor
+                            // cores (FP16 Jacobian rows x FP16 G, FP32 accumulation)
 };
 
 }  // namespace nep
@@ -93,6 +95,13 @@ struct nep_dataset {
     float* pbuf = nullptr;            // [n_pairs][3][Pst] partial forces p_kji at the receiver's slot
     float* w6 = nullptr;              // [N][6][Pst] virial contributions of each owner
     float* fown = nullptr;            // [N][3][Pst] own force terms G_i . B_i
+    // the tensor-core owner pass: tiles in owner order, their FP16 Jacobian
+    // rows and row scales (built with the set), first tile of each owner (host)
+    nep::OwnerTile* tiles = nullptr;
+    int n_tiles = 0;
+    unsigned char* apack = nullptr;
+    float* rowscale = nullptr;
+    std::vector<int> h_tile0;
     // force-loss adjoint scratch (grown on demand, nep_adjoint.cu)
     nep::AdjointScratch adj;
     // launch shape of the evaluation (nep_dataset_set_shape / nep_dataset_tune)

@@ -386,10 +386,46 @@ int prepare_pop_tc();
 // the descriptors packed as split-BF16 GEMM-1 A tiles, once per training set
 size_t pop_tc_qpack_bytes(int N);
 int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t st);
-// G: FP32, or FP16 when g_half
+// Layout of G written by the population network:
+//   kGRowsF32  [N][32][Pst] FP32;   kGRowsF16  [N][32][Pst] FP16;
+//   kGTilesF16 per atom the tensor-core B tile of the owner pass: members
+//              as rows of a K-major [8 ceil(Pst / 8)] x 32 FP16 tile
+//              (owner_tc_g_bytes(Pst) bytes per atom, nep_tc.cuh layout).
+enum GLayout { kGRowsF32 = 0, kGRowsF16 = 1, kGTilesF16 = 2 };
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
-                  const float* w2t, const float* b2t, unsigned char* packed, void* G, bool g_half, double* U,
+                  const float* w2t, const float* b2t, unsigned char* packed, void* G, int g_layout, double* U,
                   unsigned* err, cudaStream_t st);
+
+// The first contraction pass on the tensor cores (BF16 precision mode).  A
+// tile is up to 128 rows of one owner atom j: three per pair (the Jacobian
+// rows d p / d G of components x, y, z), and in the owner's first tile three
+// rows of its own term (B_j) and six of its virial contribution
+// (-sum_pairs r^a J^b, components xx yy zz xy yz zx).
+struct OwnerTile {
+    int j;           // owner atom
+    int nt;          // pairs in this tile
+    int extra;       // 1: the own-term and virial rows follow the pair rows
+    int groups;      // 8-row groups stored
+    long long q0;    // first pair (owner order)
+    long long row0;  // first row of the tile in the packed operand (multiple of 8)
+};
+constexpr int kOwnerTcPairs = 39;  // pairs of a first tile (3 x 39 + 9 <= 128 rows)
+constexpr int kOwnerTcMorePairs = 42;  // pairs of each further tile
+// bytes of one atom's G tile in the kGTilesF16 layout
+__host__ __device__ inline size_t owner_tc_g_bytes(int Pst) { return (size_t)((Pst + 7) / 8) * 512; }
+struct PairRec;
+// packs the Jacobian rows of every tile as FP16 (each row scaled by a power
+// of two, kept in rowscale, so that its largest entry lies in [2^13, 2^14));
+// once per training set
+int launch_pack_owner_tc(int n_tiles, const OwnerTile* tiles, const PairRec* rec, const long long* aidx,
+                         const float* ang, const float* B, const long long* pstart, unsigned char* apack,
+                         float* rowscale, cudaStream_t st);
+int prepare_owner_tc();
+// tiles [t0, t1): partial forces p_kji (FP16, at the receiver's slot rev[q]),
+// own terms and virial terms (FP32), as the CUDA-core owner pass writes them
+int launch_owner_tc(int t0, int t1, const OwnerTile* tiles, const unsigned char* apack, const float* rowscale,
+                    const void* G, int Pst, const long long* rev, void* pbuf, float* fown, float* w6, unsigned* err,
+                    cudaStream_t st);
 
 }  // namespace nep
 

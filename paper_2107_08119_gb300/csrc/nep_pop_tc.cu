@@ -16,6 +16,9 @@
 // descriptors x 4 members as 16-byte pieces.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
+#include "nep_dataset.cuh"
 #include "nep_internal.cuh"
 #include "nep_tc.cuh"
 
@@ -63,7 +66,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const __nv_bfloat16* __rest
     if (t == 0) {
         const uint32_t idesc = tc::idesc_bf16_f32(kTile, N);
         for (int ks = 0; ks < 2; ++ks)
-            tc::mma_bf16(tb, tc::smem_desc(tc::smem_u32(sA) + ks * 256, 128, 512),
+            tc::mma_kind_f16(tb, tc::smem_desc(tc::smem_u32(sA) + ks * 256, 128, 512),
                          tc::smem_desc(tc::smem_u32(sB) + ks * 256, 128, 512), idesc, ks > 0);
         tc::mma_commit(&mbar);
     }
@@ -214,7 +217,7 @@ __device__ __forceinline__ void mma_split(uint32_t d_tmem, const unsigned char* 
     const int np = a_lo ? 3 : 2;
     for (int p = 0; p < np; ++p)
         for (int ks = 0; ks < 2; ++ks)
-            tc::mma_bf16(d_tmem, tc::smem_desc(tc::smem_u32(as[p]) + ks * 256, 128, 512),
+            tc::mma_kind_f16(d_tmem, tc::smem_desc(tc::smem_u32(as[p]) + ks * 256, 128, 512),
                          tc::smem_desc(tc::smem_u32(bs[p]) + ks * 256, 128, 512), idesc, p > 0 || ks > 0);
 }
 
@@ -229,12 +232,14 @@ __device__ __forceinline__ void tc_sync()
 }
 
 // Grid (member groups of 4, atom tiles of 128), groups fastest so the CTAs
-// that fill one tile's G rows run together.  Outputs U [N][P] (FP64) and
-// G [N][32][Pst] (member innermost; FP32, or FP16 when GH: the contraction
-// then reads half the bytes).  The network's arithmetic is the same either way.  Warp w: TMEM lane quarter w & 3 (its 32 atoms),
-// half w >> 2 (members {2h, 2h+1} in epilogue 1, descriptors [16h, 16h+16) in
+// that fill one tile's G rows run together.  Outputs U [N][P] (FP64) and G in
+// the layout GL (GLayout: [N][32][Pst] with the members innermost in FP32 or
+// FP16, or FP16 per-atom tensor-core tiles for the owner pass; FP16 halves
+// the bytes the contraction reads).  The network's arithmetic is the same
+// for every layout.  Warp w: TMEM lane quarter w & 3 (its 32 atoms), half
+// w >> 2 (members {2h, 2h+1} in epilogue 1, descriptors [16h, 16h+16) in
 // epilogue 2).
-template <bool GH>
+template <int GL>
 __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, const unsigned char* __restrict__ qpack,
                                                         const unsigned char* __restrict__ packed,
                                                         void* __restrict__ Gv, double* __restrict__ U, unsigned* err)
@@ -304,17 +309,23 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
             tc::tmem_ld_wait();
             float u = 0.f;
             unsigned char* D = d_tile(S, m);
+            // b1 and w2 of the member's 32 neurons: 16-byte broadcast loads
+            const float4* b14 = reinterpret_cast<const float4*>(fb + m * 32);
+            const float4* w24 = reinterpret_cast<const float4*>(fb + kTcGroup * 32 + m * 32);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 uint32_t d[4];
+                const float4 ba = b14[2 * c], bb = b14[2 * c + 1], wa = w24[2 * c], wb = w24[2 * c + 1];
+                const float b1v[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                const float w2v[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     __nv_bfloat16 dd[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const int mu = 8 * c + 2 * e + h;
-                        const float x = tanhf(__uint_as_float(r[c][2 * e + h]) - fb[m * 32 + mu]);
-                        const float w2 = fb[kTcGroup * 32 + m * 32 + mu];
+                        const int mu = 2 * e + h;
+                        const float x = tanhf(__uint_as_float(r[c][mu]) - b1v[mu]);
+                        const float w2 = w2v[mu];
                         u = fmaf(w2, x, u);
                         dd[h] = __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
                     }
@@ -346,7 +357,24 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
 #pragma unroll
             for (int c = 0; c < 2; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(32 * m + 16 * half + 8 * c), r[m][c]);
         tc::tmem_ld_wait();
-        if (valid) {
+        if (valid && GL == kGTilesF16) {
+            // member k0 + m's descriptors [16 half + 8 c, + 8) are 16 contiguous bytes
+            unsigned char* base = reinterpret_cast<unsigned char*>(Gv) + (size_t)i * owner_tc_g_bytes(Pst);
+#pragma unroll
+            for (int m = 0; m < kTcGroup; ++m)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __half2 v = __floats2half2_rn(__uint_as_float(r[m][c][2 * e]),
+                                                            __uint_as_float(r[m][c][2 * e + 1]));
+                        h[e] = *reinterpret_cast<const uint32_t*>(&v);
+                    }
+                    *reinterpret_cast<uint4*>(base + tc::kmajor_offset(k0 + m, 16 * half + 8 * c)) =
+                        make_uint4(h[0], h[1], h[2], h[3]);
+                }
+        } else if (valid) {
             const size_t o0 = ((size_t)i * kNdes + 16 * half) * Pst + k0;
 #pragma unroll
             for (int c = 0; c < 2; ++c)
@@ -355,7 +383,7 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
                     const size_t o = o0 + (size_t)(8 * c + e) * Pst;
                     const float g0 = __uint_as_float(r[0][c][e]), g1 = __uint_as_float(r[1][c][e]);
                     const float g2 = __uint_as_float(r[2][c][e]), g3 = __uint_as_float(r[3][c][e]);
-                    if (GH) {  // four members as one 8-byte piece (k0 and Pst are multiples of 4)
+                    if (GL == kGRowsF16) {  // four members as one 8-byte piece (k0 and Pst are multiples of 4)
                         const __half2 a = __floats2half2_rn(g0, g1), b = __floats2half2_rn(g2, g3);
                         uint2 v;
                         v.x = *reinterpret_cast<const uint32_t*>(&a);
@@ -375,17 +403,277 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
     if (warp == 0) tc::tmem_dealloc(tb, kTmemCols);
 }
 
+// ------------------------------------------------------------ owner pass
+// The first contraction pass of the BF16 precision mode on the tensor cores.
+// For owner atom j with input gradients G_kj (member k, 32 descriptors) and
+// the Jacobians J_q = d q_j / d r of its pairs q, every output of the pass is
+// a dot product over the 32 descriptors with G_kj:
+//   p_kq^c = sum_d G_kj,d J_q,d^c                       (Eq. 23, partial force)
+//   F_kj^c (own term) = sum_d G_kj,d B_j,d^c           (B_j = d q_j / d r_j)
+//   W_kj^ab = sum_q -r_q^a p_kq^b = sum_d G_kj,d V_j,d^ab,  V_j^ab = -sum_q r_q^a J_q^b
+// so one MMA per tile, D[row][k] = sum_d A[row][d] G[k][d], forms them all
+// for every member: A holds a row per (pair, component), own-term component
+// and virial component (FP16, packed once per training set), B the owner's G
+// tile (FP16, written by the population network), D sits in TMEM.
+
+// J_q,d^c: radial orders d < 8 from the pair record (g_n'/r times r^c), the
+// 24 angular descriptors from the pair's angular block (zero beyond r_c^A)
+__device__ __forceinline__ float owner_jac(const PairRec& R, long long ai, const float* __restrict__ ang, int d,
+                                           int c)
+{
+    return d < kNR ? R.gd[d] * R.r[c] : (ai >= 0 ? ang[(size_t)ai * (kNA * kLmax * 3) + 3 * (d - kNR) + c] : 0.f);
+}
+
+// One block per tile, one thread per row (rows of the padded groups past the
+// tile's rows are zero).
+__global__ void __launch_bounds__(128) k_pack_owner_tc(const OwnerTile* __restrict__ tiles,
+                                                       const PairRec* __restrict__ rec,
+                                                       const long long* __restrict__ aidx,
+                                                       const float* __restrict__ ang, const float* __restrict__ B,
+                                                       const long long* __restrict__ pstart,
+                                                       unsigned char* __restrict__ apack, float* __restrict__ rowscale)
+{
+    const OwnerTile T = tiles[blockIdx.x];
+    const int r = threadIdx.x;
+    if (r >= 8 * T.groups) return;
+    const int np = 3 * T.nt;
+    float v[kNdes];
+#pragma unroll
+    for (int d = 0; d < kNdes; ++d) v[d] = 0.f;
+    if (r < np) {
+        const long long q = T.q0 + r / 3;
+        const int c = r % 3;
+        const PairRec R = rec[q];
+        const long long ai = aidx[q];
+#pragma unroll
+        for (int d = 0; d < kNdes; ++d) v[d] = owner_jac(R, ai, ang, d, c);
+    } else if (T.extra && r < np + 3) {
+        const int c = r - np;
+#pragma unroll
+        for (int d = 0; d < kNdes; ++d) v[d] = B[((size_t)T.j * kNdes + d) * 3 + c];
+    } else if (T.extra && r < np + 9) {
+        // xx yy zz xy yz zx
+        const int w = r - np - 3, a = w < 3 ? w : w - 3, b = w < 3 ? w : (w - 2) % 3;
+        for (long long q = pstart[T.j]; q < pstart[T.j + 1]; ++q) {
+            const PairRec R = rec[q];
+            const long long ai = aidx[q];
+            const float ra = -R.r[a];
+#pragma unroll
+            for (int d = 0; d < kNdes; ++d) v[d] = fmaf(ra, owner_jac(R, ai, ang, d, b), v[d]);
+        }
+    }
+    // power-of-two row scale: the largest |entry| goes to [2^13, 2^14), far
+    // from both ends of the FP16 range; the pass multiplies it back (exactly)
+    float mx = 0.f;
+#pragma unroll
+    for (int d = 0; d < kNdes; ++d) mx = fmaxf(mx, fabsf(v[d]));
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);  // mx in [2^(e-1), 2^e)
+    const int sh = mx > 0.f ? max(-100, min(100, 14 - e)) : 0;
+    rowscale[T.row0 + r] = ldexpf(1.f, -sh);
+    unsigned char* tile = apack + (size_t)T.row0 * 64;
+#pragma unroll
+    for (int kc = 0; kc < kNdes / 8; ++kc) {
+        uint32_t h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const __half2 p = __floats2half2_rn(ldexpf(v[8 * kc + 2 * u], sh), ldexpf(v[8 * kc + 2 * u + 1], sh));
+            h[u] = *reinterpret_cast<const uint32_t*>(&p);
+        }
+        *reinterpret_cast<uint4*>(tile + tc::kmajor_offset(r, 8 * kc)) = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+}
+
+// The owner pass proper: a persistent CTA walks tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Shared memory holds two stages (A tile 8 KB,
+// G tile 4 KB), filled by bulk async copies one tile ahead; thread 0 issues
+// the copies and the two K = 16 MMAs into 64 TMEM columns; after the MMA has
+// completed the four warps read their TMEM lane quarter (thread = tile row)
+// into shared memory, and then each warp stores whole rows for members
+// 0..Pst-1 (one coalesced store per row): a pair row p_kq^c in FP16 at the
+// receiver's slot rev[q], own-term and virial rows in FP32.  Every
+// wait is bounded: a timeout latches NEP_ERR_TIMEOUT, the CTA waits (bounded)
+// for its copies and MMA still in flight, frees its TMEM and returns.
+constexpr int kOtcThreads = 128;
+constexpr int kOtcATile = 128 * 64;  // 128 rows x 32 FP16
+constexpr int kOtcBTile = 64 * 64;   // up to 64 members x 32 FP16
+constexpr int kOtcCols = 64;         // TMEM columns (members)
+// epilogue staging of the FP16 pair rows: 64 halves per row at a stride of
+// 36 words (16-byte row writes by one thread each take the minimum four
+// wavefronts), and each row's destination
+constexpr int kOtcRowWords = 36;
+constexpr int kOtcStageH = 128 * kOtcRowWords * 4;
+constexpr int kOtcBars = 64;
+constexpr int kOtcSmem = 2 * (kOtcATile + kOtcBTile) + kOtcBars + kOtcStageH + 128 * 8;
+
+__global__ void __launch_bounds__(kOtcThreads) k_owner_tc(int t0, int t1, const OwnerTile* __restrict__ tiles,
+                                                          const unsigned char* __restrict__ apack,
+                                                          const float* __restrict__ rowscale,
+                                                          const unsigned char* __restrict__ Gt, int Pst,
+                                                          const long long* __restrict__ rev, __half* __restrict__ pbuf,
+                                                          float* __restrict__ fown, float* __restrict__ w6,
+                                                          unsigned* err)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    unsigned char* sA = sm;                       // [2][kOtcATile]
+    unsigned char* sB = sm + 2 * kOtcATile;       // [2][kOtcBTile]
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + 2 * (kOtcATile + kOtcBTile));  // [2]
+    uint64_t* mbar = full + 2;
+    uint32_t* tmem_base = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint32_t* stage_h = reinterpret_cast<uint32_t*>(sm + 2 * (kOtcATile + kOtcBTile) + kOtcBars);
+    __half** dst = reinterpret_cast<__half**>(stage_h + 128 * kOtcRowWords);
+    const int t = threadIdx.x, warp = t >> 5;
+    const uint32_t gbytes = (uint32_t)owner_tc_g_bytes(Pst);
+    const int nmem = 8 * ((Pst + 7) / 8);          // G rows copied
+    const int N = nmem < 16 ? 16 : (nmem + 15) / 16 * 16;  // MMA N (rows past nmem: unused columns)
+    const int c8 = (Pst + 7) / 8;                  // 8-column TMEM loads per row
+    if (t == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tmem_base, kOtcCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = *tmem_base;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // copies issued / completions waited per stage, MMAs issued / waited
+    unsigned issued[2] = {0u, 0u}, waited[2] = {0u, 0u}, mma_issued = 0u, mma_waited = 0u;
+    auto issue = [&](int tile, int s) {
+        if (t == 0) {
+            const OwnerTile T = tiles[tile];
+            const uint32_t abytes = (uint32_t)T.groups * 512u;
+            const uint32_t bar = tc::smem_u32(&full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(abytes + gbytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    tc::smem_u32(sA + s * kOtcATile)),
+                "l"(apack + (size_t)T.row0 * 64), "r"(abytes), "r"(bar)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    tc::smem_u32(sB + s * kOtcBTile)),
+                "l"(Gt + (size_t)T.j * gbytes), "r"(gbytes), "r"(bar)
+                : "memory");
+        }
+        ++issued[s];
+    };
+    bool ok = true;
+    int tile = t0 + (int)blockIdx.x;
+    OwnerTile Tn;  // the next tile's record, loaded one tile ahead
+    if (tile < t1) {
+        issue(tile, 0);
+        Tn = tiles[tile];
+    }
+    for (int it = 0; tile < t1; ++it, tile += (int)gridDim.x) {
+        const int s = it & 1;
+        const OwnerTile T = Tn;
+        if (tile + (int)gridDim.x < t1) Tn = tiles[tile + (int)gridDim.x];
+        // this tile's row scales and destinations, loaded before the waits
+        const int np = 3 * T.nt, rows = np + (T.extra ? 9 : 0);
+        const float sc = t < rows ? rowscale[T.row0 + t] : 0.f;
+        const long long rq = t < np ? rev[T.q0 + t / 3] : 0;
+        ok = __syncthreads_and(tc::mbar_wait(&full[s], waited[s] & 1u, kMaxPolls)) != 0;
+        if (!ok) break;
+        ++waited[s];
+        tc::fence_after_sync();
+        if (t == 0) {
+            const uint32_t idesc = tc::idesc_f16_f32(128, N);
+            const uint32_t a = tc::smem_u32(sA + s * kOtcATile), b = tc::smem_u32(sB + s * kOtcBTile);
+            for (int ks = 0; ks < 2; ++ks)
+                tc::mma_kind_f16(tb, tc::smem_desc(a + ks * 256, 128, 512), tc::smem_desc(b + ks * 256, 128, 512),
+                                 idesc, ks > 0);
+            tc::mma_commit(mbar);
+        }
+        ++mma_issued;
+        // the other stage's previous tile has been consumed by its MMA (waited
+        // in the previous iteration): refill it with the next tile
+        if (tile + (int)gridDim.x < t1) issue(tile + (int)gridDim.x, s ^ 1);
+        ok = __syncthreads_and(tc::mbar_wait(mbar, mma_waited & 1u, kMaxPolls)) != 0;
+        if (!ok) break;
+        ++mma_waited;
+        tc::fence_after_sync();
+        // ---- epilogue, 1: thread t takes tile row t (TMEM lane t): a pair row
+        // to shared memory as FP16, an own-term or virial row straight to its
+        // FP32 destination (columns past Pst are staged but never stored)
+        uint32_t d[8][8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < c8) tc::tmem_ld8(tb + lane_base + (uint32_t)(8 * c), d[c]);
+        tc::tmem_ld_wait();
+        if (t < np) {
+            dst[t] = pbuf + ((size_t)rq * 3 + t % 3) * Pst;
+            uint4* row = reinterpret_cast<uint4*>(stage_h + t * kOtcRowWords);
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < c8) {
+                    uint32_t h[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const __half2 v = __floats2half2_rn(__uint_as_float(d[c][2 * u]) * sc,
+                                                            __uint_as_float(d[c][2 * u + 1]) * sc);
+                        h[u] = *reinterpret_cast<const uint32_t*>(&v);
+                    }
+                    row[c] = make_uint4(h[0], h[1], h[2], h[3]);
+                }
+        } else if (t < rows) {
+            const int e = t - np;
+            float* o = e < 3 ? fown + ((size_t)T.j * 3 + e) * Pst : w6 + ((size_t)T.j * 6 + (e - 3)) * Pst;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (8 * c + 4 * h < Pst)  // Pst is a multiple of 4
+                        *reinterpret_cast<float4*>(o + 8 * c + 4 * h) =
+                            make_float4(__uint_as_float(d[c][4 * h]) * sc, __uint_as_float(d[c][4 * h + 1]) * sc,
+                                        __uint_as_float(d[c][4 * h + 2]) * sc, __uint_as_float(d[c][4 * h + 3]) * sc);
+        }
+        __syncthreads();
+        // ---- 2: the pair rows, two per warp step: half-warp h stores row
+        // r + h as Pst / 4 pieces of 8 bytes (one coalesced row)
+        {
+            const int lane = t & 31, hw = lane >> 4, piece = lane & 15;
+            for (int r = 2 * warp + hw; r - hw < np; r += 2 * (kOtcThreads / 32))
+                if (r < np && 4 * piece < Pst)
+                    reinterpret_cast<uint2*>(dst[r])[piece] =
+                        reinterpret_cast<const uint2*>(stage_h + r * kOtcRowWords)[piece];
+        }
+        // every lane has read TMEM before the next MMA overwrites it
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (!ok) {
+        if (t == 0) atomicOr(err, kErrTimeout);
+        // what is still in flight lands before the TMEM and the CTA go (bounded)
+        if (mma_issued > mma_waited) tc::mbar_wait(mbar, mma_waited & 1u, kMaxPolls);
+        for (int s = 0; s < 2; ++s)
+            if (issued[s] > waited[s]) tc::mbar_wait(&full[s], waited[s] & 1u, kMaxPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tb, kOtcCols);
+}
 }  // namespace
 
 size_t pop_tc_packed_bytes(int P) { return (size_t)((P + kTcGroup - 1) / kTcGroup) * kGroupBytes; }
 
 int prepare_pop_tc()
 {
-    int rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    int rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc<kGRowsF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)sizeof(PopSmem)), "population kernel shared memory");
-    if (rc) return rc;
-    return cuda_fail(cudaFuncSetAttribute(k_pop_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sizeof(PopSmem)), "population kernel shared memory");
+    if (!rc)
+        rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc<kGRowsF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(PopSmem)), "population kernel shared memory");
+    if (!rc)
+        rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc<kGTilesF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(PopSmem)), "population kernel shared memory");
+    return rc;
 }
 
 size_t pop_tc_qpack_bytes(int N) { return (size_t)((N + kTile - 1) / kTile) * 2 * kTileBytes; }
@@ -398,7 +686,7 @@ int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t s
 }
 
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
-                  const float* w2t, const float* b2t, unsigned char* packed, void* G, bool g_half, double* U,
+                  const float* w2t, const float* b2t, unsigned char* packed, void* G, int g_layout, double* U,
                   unsigned* err, cudaStream_t st)
 {
     if (n_neu > 32 || Pst % 4 != 0 || Pst < P) {
@@ -409,9 +697,41 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, 
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
     k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
     const size_t smem = sizeof(PopSmem);
-    auto kern = g_half ? k_pop_tc<true> : k_pop_tc<false>;
+    auto kern = g_layout == kGTilesF16 ? k_pop_tc<kGTilesF16>
+                                       : (g_layout == kGRowsF16 ? k_pop_tc<kGRowsF16> : k_pop_tc<kGRowsF32>);
     kern<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
+}
+
+int launch_pack_owner_tc(int n_tiles, const OwnerTile* tiles, const PairRec* rec, const long long* aidx,
+                         const float* ang, const float* B, const long long* pstart, unsigned char* apack,
+                         float* rowscale, cudaStream_t st)
+{
+    if (n_tiles > 0)
+        k_pack_owner_tc<<<n_tiles, 128, 0, st>>>(tiles, rec, aidx, ang, B, pstart, apack, rowscale);
+    return cuda_fail(cudaGetLastError(), "pack owner-pass tiles");
+}
+
+int prepare_owner_tc()
+{
+    return cuda_fail(cudaFuncSetAttribute(k_owner_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kOtcSmem),
+                     "owner-pass shared memory");
+}
+
+int launch_owner_tc(int t0, int t1, const OwnerTile* tiles, const unsigned char* apack, const float* rowscale,
+                    const void* G, int Pst, const long long* rev, void* pbuf, float* fown, float* w6, unsigned* err,
+                    cudaStream_t st)
+{
+    if (Pst < 4 || Pst > kOtcCols || Pst % 4 != 0) {
+        set_error("tensor-core owner pass: member stride %d outside 4..%d or not a multiple of 4", Pst, kOtcCols);
+        return NEP_ERR_UNSUPPORTED;
+    }
+    if (t1 <= t0) return NEP_OK;
+    const int grid = std::min(t1 - t0, 152 * 5);  // five CTAs per SM (registers and shared memory)
+    k_owner_tc<<<grid, kOtcThreads, kOtcSmem, st>>>(t0, t1, tiles, apack, rowscale,
+                                                    static_cast<const unsigned char*>(G), Pst, rev,
+                                                    static_cast<__half*>(pbuf), fown, w6, err);
+    return cuda_fail(cudaGetLastError(), "tensor-core owner pass");
 }
 
 }  // namespace nep

@@ -338,11 +338,12 @@ __host__ __device__ __forceinline__ void neuron_out(float w2, float xm, const fl
             G[v + 2] = fmaf(d, t.z, G[v + 2]);
             G[v + 3] = fmaf(d, t.w, G[v + 3]);
         }
-        return;
-    }
+    } else
 #endif
+    {
 #pragma unroll
-    for (int v = 0; v < ND; ++v) G[v] = fmaf(d, row[v], G[v]);
+        for (int v = 0; v < ND; ++v) G[v] = fmaf(d, row[v], G[v]);
+    }
 }
 
 // Network of Eqs. 21-22 and its input gradient.  w points at the parameter

@@ -1,6 +1,6 @@
 // nep_tc.cuh -- Blackwell (sm_100 family) tensor-core building blocks in
-// inline PTX: TMEM allocation, tcgen05.mma (kind::f16 with BF16 operands and
-// FP32 accumulation), commit to an mbarrier, bounded mbarrier waits, TMEM
+// inline PTX: TMEM allocation, tcgen05.mma (kind::f16 with BF16 or FP16
+// operands and FP32 accumulation), commit to an mbarrier, bounded mbarrier waits, TMEM
 // loads and the proxy/ordering fences they need.
 //
 // Operands live in shared memory in the canonical K-major layout without
@@ -53,6 +53,16 @@ __host__ __device__ __forceinline__ uint32_t idesc_bf16_f32(int M, int N)
     return d;
 }
 
+// The same with A and B in FP16 (both operands of one MMA have one type).
+__host__ __device__ __forceinline__ uint32_t idesc_f16_f32(int M, int N)
+{
+    uint32_t d = 0;
+    d |= 1u << 4;  // D format: FP32; A and B format fields 0: FP16
+    d |= (uint32_t)((N >> 3) & 0x3F) << 17;
+    d |= (uint32_t)((M >> 4) & 0x1F) << 24;
+    return d;
+}
+
 // ---- TMEM allocation (one full warp executes these) ----
 __device__ __forceinline__ void tmem_alloc(uint32_t* smem_result, uint32_t ncols)
 {
@@ -71,8 +81,8 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// ---- MMA (one thread issues) ----
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+// ---- MMA (one thread issues; the operand types come from idesc) ----
+__device__ __forceinline__ void mma_kind_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          bool accumulate)
 {
     asm volatile(

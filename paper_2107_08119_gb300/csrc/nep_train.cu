@@ -30,6 +30,7 @@
 #include <atomic>
 #include <cmath>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -1137,7 +1138,8 @@ bool valid_shape(const nep_dataset* ds, const EvalShape& h)
     return h.waves >= 1 && h.waves <= kMaxWaves && (h.owner_warps == 4 || h.owner_warps == 8) &&
            (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
            (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 12 || h.recv_unroll == 16) &&
-           (h.fused == 0 || ((h.fused == 4 || h.fused == 8 || h.fused == 16) && fused_fits(ds, h.fused)));
+           (h.fused == 0 || ((h.fused == 4 || h.fused == 8 || h.fused == 16) && fused_fits(ds, h.fused))) &&
+           (h.owner_tc == 0 || h.owner_tc == 1);
 }
 
 }  // namespace
@@ -1268,6 +1270,7 @@ int prepare_evaluation(nep_dataset* ds, int P)
                                 "fused contraction shared memory")))
                 return rc;
     }
+    if ((rc = prepare_owner_tc())) return rc;
     return prepare_pop_tc();
 }
 
@@ -1282,9 +1285,16 @@ void launch_contraction_t(const nep_dataset* ds, int P, int Pst, int c_lo, int c
     const int a0 = ds->h_cb[c_lo], a1 = ds->h_ce[c_hi - 1];
     const size_t ostage = (size_t)ow * kOwnerStage * sizeof(float);
     PT* pbuf = reinterpret_cast<PT*>(ds->pbuf);
-    k_contract_owner<PT><<<std::min(blocks_for(a1 - a0, ow), 152 * 64 / ow), 32 * ow, ostage, st>>>(
-        a0, a1, P, Pst, reinterpret_cast<const PT*>(ds->G), ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx, ds->ang,
-        pbuf, ds->w6, ds->fown);
+    if (std::is_same<PT, __half>::value && sh.owner_tc) {
+        // the owners' tiles, G in the tensor-core tile layout (a launch error
+        // is read back by the caller's cudaGetLastError)
+        launch_owner_tc(ds->h_tile0[a0], ds->h_tile0[a1], ds->tiles, ds->apack, ds->rowscale, ds->G, Pst, ds->rev,
+                        pbuf, ds->fown, ds->w6, ds->m->d_err, st);
+    } else {
+        k_contract_owner<PT><<<std::min(blocks_for(a1 - a0, ow), 152 * 64 / ow), 32 * ow, ostage, st>>>(
+            a0, a1, P, Pst, reinterpret_cast<const PT*>(ds->G), ds->B, ds->pstart, ds->rev, ds->rec, ds->aidx,
+            ds->ang, pbuf, ds->w6, ds->fown);
+    }
     if (fork) {
         cudaEventRecord(ev, st);
         cudaStreamWaitEvent(p2, ev, 0);
@@ -1336,8 +1346,9 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
     if (precision == NEP_PREC_BF16) {
         // G in FP16: the contraction reads half the bytes (the loss terms
         // average its rounding over all force components)
+        const int layout = !sh.fused && sh.owner_tc ? kGTilesF16 : kGRowsF16;
         if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
-                                true, ds->U, m->d_err, st)))
+                                layout, ds->U, m->d_err, st)))
             return rc;
     } else {
         const long long pairs = (ds->N + 1) / 2;
@@ -1619,6 +1630,43 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
                                          (float)(1.0 / m->hp.rc_A), ds->typed, ds->q, ds->B, ds->rec, ds->ang);
     if (!rc && !(rc = dalloc(&ds->qpack, pop_tc_qpack_bytes(N), bytes)))
         rc = launch_pack_q_tc(N, ds->q, ds->qpack, nullptr);
+    // tiles of the tensor-core owner pass: per owner a first tile with up to
+    // kOwnerTcPairs pairs and the own-term and virial rows, further tiles of
+    // up to kOwnerTcMorePairs pairs
+    if (!rc) {
+        std::vector<OwnerTile> ht;
+        ds->h_tile0.assign((size_t)N + 1, 0);
+        long long row0 = 0;
+        for (int j = 0; j < N; ++j) {
+            ds->h_tile0[j] = (int)ht.size();
+            long long q = hps[j];
+            bool first = true;
+            do {
+                const int cap = first ? kOwnerTcPairs : kOwnerTcMorePairs;
+                OwnerTile T;
+                T.j = j;
+                T.nt = (int)std::min<long long>(cap, hps[j + 1] - q);
+                T.extra = first ? 1 : 0;
+                const int rows = 3 * T.nt + (first ? 9 : 0);
+                T.groups = (rows + 7) / 8;
+                T.q0 = q;
+                T.row0 = row0;
+                row0 += 8 * T.groups;
+                q += T.nt;
+                first = false;
+                ht.push_back(T);
+            } while (q < hps[j + 1]);
+        }
+        ds->h_tile0[N] = (int)ht.size();
+        ds->n_tiles = (int)ht.size();
+        if ((rc = dalloc(&ds->tiles, ht.size(), bytes)) || (rc = dalloc(&ds->apack, (size_t)row0 * 64, bytes)) ||
+            (rc = dalloc(&ds->rowscale, (size_t)row0, bytes)))
+            return fail(rc);
+        up(ds->tiles, ht.data(), sizeof(OwnerTile) * ht.size());
+        if (e != cudaSuccess) return fail(cuda_fail(e, "dataset upload"));
+        rc = launch_pack_owner_tc(ds->n_tiles, ds->tiles, ds->rec, ds->aidx, ds->ang, ds->B, ds->pstart, ds->apack,
+                                  ds->rowscale, nullptr);
+    }
     if (!rc) rc = cuda_fail(cudaDeviceSynchronize(), "dataset precompute");
     if (rc) return fail(rc);
     cudaMemcpy(&bits, m->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost);
@@ -1674,6 +1722,9 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->pbuf);
     dfree(ds->w6);
     dfree(ds->fown);
+    dfree(ds->tiles);
+    dfree(ds->apack);
+    dfree(ds->rowscale);
     free_adjoint(ds->adj);
     for (int w = 0; w < kMaxWaves; ++w)
         if (ds->ev_wave[w]) cudaEventDestroy(ds->ev_wave[w]);
@@ -1881,10 +1932,11 @@ int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
     h.mlp_threads = shape[3];
     h.recv_unroll = shape[4];
     h.fused = shape[5];
+    h.owner_tc = shape[6];
     if (!valid_shape(ds, h)) {
         set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
                   "receiver unroll 4, 8, 12 or 16 (staged), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
-                  "48 bytes of shared memory at most %zu)",
+                  "48 bytes of shared memory at most %zu), owner_tc 0 or 1",
                   kMaxWaves, ds->amax, kFusedSmemMax);
         return NEP_ERR_ARG;
     }
@@ -1905,6 +1957,7 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape)
     shape[3] = ds->shape.mlp_threads;
     shape[4] = ds->shape.recv_unroll;
     shape[5] = ds->shape.fused;
+    shape[6] = ds->shape.owner_tc;
     return NEP_OK;
 }
 
@@ -1934,6 +1987,11 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
                         h.mlp_threads = mt;
                         h.recv_unroll = ru;
                         cand.push_back(h);
+                        // BF16: the owner pass on the tensor cores (owner warps do not apply)
+                        if (precision == NEP_PREC_BF16 && ow == 4) {
+                            h.owner_tc = 1;
+                            cand.push_back(h);
+                        }
                     }
     // the fused contraction: members per block (the atoms per warp follow:
     // 32 / members), with the FP32 network's block size where it runs

@@ -448,11 +448,11 @@ class Dataset:
         _check(_lib.nep_dataset_descriptors(self._h, _ptr(q), _stream(stream)), "nep_dataset_descriptors")
         return q
 
-    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll", "fused")
+    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll", "fused", "owner_tc")
 
     def shape(self):
         """Launch shape of the population evaluation (nep_dataset_get_shape)."""
-        a = np.zeros(6, np.int32)
+        a = np.zeros(len(self.SHAPE_KEYS), np.int32)
         _check(_lib.nep_dataset_get_shape(self._h, a.ctypes.data_as(_vp)), "nep_dataset_get_shape")
         return dict(zip(self.SHAPE_KEYS, (int(v) for v in a)))
 
@@ -471,7 +471,7 @@ class Dataset:
 
     def tune(self, n_pop, precision=PREC_FP32, reps=5, stream=None):
         """Autotune the launch shape (nep_dataset_tune); returns (shape, ms per evaluation)."""
-        a = np.zeros(6, np.int32)
+        a = np.zeros(len(self.SHAPE_KEYS), np.int32)
         ms = C.c_float()
         _check(_lib.nep_dataset_tune(self.model._h, self._h, int(n_pop), int(precision), int(reps),
                                      a.ctypes.data_as(_vp), C.byref(ms), _stream(stream)), "nep_dataset_tune")

@@ -8,7 +8,9 @@ and its summation order; in the fused form the force sums are exact integer
 sums and every other sum runs over the atoms in an order independent of the
 members per block.  So the losses of every shape of one form must be
 identical, and the two forms agree to the rounding of the two-pass form's
-FP32 force sums."""
+FP32 force sums.  In BF16 precision the two-pass form with its first pass on
+the tensor cores (owner_tc) is a third form: FP16 Jacobian rows, the same
+losses to ~1e-4 relative."""
 import numpy as np
 import pytest
 
@@ -59,17 +61,28 @@ def _two_pass_shapes(precision, N):
                 for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
                     for ru in (4, 8, 12, 16):
                         out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru,
-                                        fused=0))
+                                        fused=0, owner_tc=0))
     return out
 
 
+def _tc_shapes():
+    """Two-pass shapes with the first pass on the tensor cores (BF16)."""
+    return [dict(waves=w, owner_warps=4, discard=dc, mlp_threads=256, recv_unroll=ru, fused=0, owner_tc=1)
+            for w in (1, 2, 4) for dc in ((0, 1) if w > 1 else (0,)) for ru in (4, 8, 12, 16)]
+
+
 def _fused_shapes(precision, N):
-    return [dict(waves=1, owner_warps=4, discard=0, mlp_threads=mt, recv_unroll=4, fused=gm)
+    return [dict(waves=1, owner_warps=4, discard=0, mlp_threads=mt, recv_unroll=4, fused=gm, owner_tc=0)
             for gm in (4, 8, 16) for mt in ((128, 256) if precision == N.PREC_FP32 else (256,))]
 
 
 def _all_shapes(precision, N):
-    return _fused_shapes(precision, N) + _two_pass_shapes(precision, N)
+    return (_fused_shapes(precision, N) + _two_pass_shapes(precision, N) +
+            (_tc_shapes() if precision == N.PREC_BF16 else []))
+
+
+def _form(shape):
+    return "fused" if shape["fused"] else ("two-pass-tc" if shape["owner_tc"] else "two-pass")
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -78,9 +91,16 @@ def test_every_shape_gives_identical_losses(N, full_set, prec):
     model, ds, pop = full_set
     zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
     refs = {}
-    for form, shapes in (("fused", _fused_shapes(prec, N)),
-                         ("two-pass", _two_pass_shapes(prec, N) +
-                          [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8, fused=0)])):
+    extra = [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8, fused=0, owner_tc=0)]
+    forms = [("fused", _fused_shapes(prec, N))]
+    if prec == N.PREC_FP32:
+        # owner_tc does not apply in FP32: the same form, the same bits
+        forms.append(("two-pass", _two_pass_shapes(prec, N) + extra +
+                      [dict(sh, mlp_threads=256) for sh in _tc_shapes()]))
+    else:
+        forms.append(("two-pass", _two_pass_shapes(prec, N) + extra))
+        forms.append(("two-pass-tc", _tc_shapes() + [dict(extra[0], owner_tc=1)]))
+    for form, shapes in forms:
         ds.set_shape(**shapes[0])
         ref = refs[form] = ds.evaluate(zp, prec).cpu().numpy()
         assert np.isfinite(ref).all()
@@ -96,6 +116,11 @@ def test_every_shape_gives_identical_losses(N, full_set, prec):
     rtol = 1e-6 if prec == N.PREC_FP32 else 2e-5
     assert np.allclose(refs["fused"], refs["two-pass"], rtol=rtol, atol=0.0), \
         np.abs(refs["fused"] / refs["two-pass"] - 1).max()
+    if "two-pass-tc" in refs:
+        # FP16 Jacobian rows (11-bit significands) instead of FP32 ones
+        rel = np.abs(refs["two-pass-tc"] / refs["two-pass"] - 1)
+        print(f"owner pass on the tensor cores: loss terms within {rel.max(axis=0)} relative")
+        assert rel.max() <= 2e-4, rel.max(axis=0)
     ds.set_shape()
     model.sync_status()
 
@@ -105,29 +130,32 @@ def test_autotuner_picks_a_candidate(N, full_set):
     model, ds, pop = full_set
     zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
     refs = {}
-    for fused in (8, 0):
-        ds.set_shape(fused=fused)
-        refs[fused > 0] = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
+    for sh in (dict(fused=8), dict(fused=0), dict(fused=0, owner_tc=1)):
+        ds.set_shape(**sh)
+        refs[_form(ds.shape())] = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
     shape, ms = ds.tune(50, N.PREC_BF16, reps=2)
     assert shape in _all_shapes(N.PREC_BF16, N)
     assert ds.shape() == shape
     assert 0.0 < ms < 100.0
-    assert np.array_equal(ds.evaluate(zp, N.PREC_BF16).cpu().numpy(), refs[shape["fused"] > 0])
+    assert np.array_equal(ds.evaluate(zp, N.PREC_BF16).cpu().numpy(), refs[_form(shape)])
     ds.set_shape()
 
 
 def test_shape_validation(N, full_set):
     model, ds, pop = full_set
-    assert ds.default_shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4, fused=8)
+    assert ds.default_shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4, fused=8,
+                                      owner_tc=0)
     for bad in (dict(waves=0), dict(waves=17), dict(owner_warps=6), dict(discard=2), dict(mlp_threads=64),
-                dict(recv_unroll=2), dict(recv_unroll=6), dict(fused=2), dict(fused=32), dict(fused=-4)):
+                dict(recv_unroll=2), dict(recv_unroll=6), dict(fused=2), dict(fused=32), dict(fused=-4),
+                dict(owner_tc=2), dict(owner_tc=-1)):
         with pytest.raises(N.NepError) as e:
             ds.set_shape(**bad)
         assert e.value.code == -1  # NEP_ERR_ARG
     assert ds.shape() == ds.default_shape()
 
 
-@pytest.mark.parametrize("shape", [dict(), dict(fused=0, waves=1), dict(fused=0, waves=4, discard=1)])
+@pytest.mark.parametrize("shape", [dict(), dict(fused=0, waves=1), dict(fused=0, waves=4, discard=1),
+                                   dict(fused=0, owner_tc=1), dict(fused=0, waves=4, owner_tc=1)])
 def test_run_equals_steps(N, full_set, shape):
     """Generations from the replayed graph equal eager snes_step calls bit
     for bit, the loss history included, and the two interleave (the fused

@@ -50,7 +50,8 @@ def test_bf16_population_losses_track_fp32(N, orc):
     FP64 oracle with the teacher: BF16 GEMMs with FP32 accumulation give each
     loss term (total, L_e, L_f, L_v) within 1e-3 relative of the FP32 path,
     L_1 and L_2 (functions of z alone) identical, and the same fitness
-    ranking; in both the fused and the two-pass contraction."""
+    ranking; in the fused and the two-pass contraction, the latter also with
+    its first pass on the tensor cores."""
     import torch
     structures, teacher, pop = inputs.config4()
     teacher = f32_exact(teacher)
@@ -58,14 +59,14 @@ def test_bf16_population_losses_track_fp32(N, orc):
     model = N.NEP(teacher.astype(np.float32))
     ds = N.Dataset(model, structures, E, F, W)
     zp = torch.tensor(f32_exact(pop), dtype=torch.float32, device="cuda")
-    for fused in (8, 0):
-        ds.set_shape(fused=fused)
+    for fused, otc in ((8, 0), (0, 0), (0, 1)):
+        ds.set_shape(fused=fused, owner_tc=otc)
         l32 = ds.evaluate(zp, N.PREC_FP32).cpu().numpy()
         l16 = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
         model.sync_status()
         rel = np.abs(l16 - l32) / np.abs(l32)
         for col in range(4):
-            assert rel[:, col].max() <= 1e-3, (fused, col, rel[:, col].max())
+            assert rel[:, col].max() <= 1e-3, (fused, otc, col, rel[:, col].max())
         assert np.array_equal(l16[:, 4:6], l32[:, 4:6])
         assert list(np.argsort(l16[:, 0], kind="stable")) == list(np.argsort(l32[:, 0], kind="stable"))
         # deterministic
