@@ -405,7 +405,10 @@ int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
  *   [3] threads     128 or 256 threads per block of the FP32 network.
  *   [4] unroll      4, 8 or 12 partial-force slots in flight per warp in the
  *                   second contraction pass, or 16: staged in shared memory
- *                   16 slots at a time by asynchronous copies.
+ *                   16 slots at a time by asynchronous copies, or 1: each
+ *                   atom's contiguous slot rows brought into shared memory by
+ *                   bulk asynchronous copies, two pieces of up to 4 KB ahead
+ *                   per warp.
  *   [6] owner_tc    0 or 1.  1 with the two passes in NEP_PREC_BF16: the
  *                   first pass on the tensor cores (tcgen05, FP16 x FP16 with
  *                   FP32 accumulation): per owner atom one MMA of its FP16

@@ -23,7 +23,8 @@
 //   k_contract_owner  warp per atom j, two members per lane: p_kji for j's
 //               pairs from G_j held in registers, stored at the reverse slot
 //   k_contract  warp per atom i: F_i from its slots' p_kji, |F - F_tar|^2,
-//               U and W summed per chunk of 32 atoms
+//               U and W summed per chunk of 32 atoms (k_contract_bulk: the
+//               same, the slot rows arriving by bulk copies)
 //   k_loss      per member: per-structure sums in a fixed order, RMSEs
 // SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r), k_snes_update.
 #include <algorithm>
@@ -36,6 +37,7 @@
 #include <cuda_fp16.h>
 
 #include "nep_dataset.cuh"
+#include "nep_tc.cuh"
 
 namespace nep {
 namespace {
@@ -594,6 +596,41 @@ __device__ __forceinline__ void recv_load(RecvAtom& a, int i, int P, int Pst, in
     a.pe = pstart[i + 1];
 }
 
+// A warp's running sums over its atoms of one chunk, for the lane's two
+// members: U in FP64 (site energies come as FP64), the squared force
+// residuals and the owner virial terms in FP32 (a warp takes at most
+// kChunkAtoms / 8 = 4 atoms of a chunk; the FP64 pipe is slow on this part, so
+// the per-atom terms stay off it), converted once per chunk to FP64.
+struct RecvAcc {
+    double u[2] = {0.0, 0.0};
+    float f[2] = {0.f, 0.f};
+    float w[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
+    __device__ __forceinline__ void add(const RecvAtom& a, const float (&F)[2][3])
+    {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const float dx = F[m][0] - a.t[0], dy = F[m][1] - a.t[1], dz = F[m][2] - a.t[2];
+            u[m] += m == 0 ? a.u0 : a.u1;
+            f[m] += fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+#pragma unroll
+            for (int c = 0; c < 6; ++c) w[m][c] += m == 0 ? a.w6[c].x : a.w6[c].y;
+        }
+    }
+    // the lane's rows red[k0], red[k0 + 1] (members past kMaxPop have none)
+    __device__ __forceinline__ void store(double (*red)[8], int k0) const
+    {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            if (k0 + m >= kMaxPop) continue;
+            double* r = red[k0 + m];
+            r[0] = u[m];
+            r[1] = (double)f[m];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) r[2 + c] = (double)w[m][c];
+        }
+    }
+};
+
 template <int UNROLL, class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
     int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
@@ -609,11 +646,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
     const bool on0 = k0 < P, on1 = k0 + 1 < P;
     const bool ld = k0 < Pst;
     // per-lane running sums live in shared memory (this lane's slots only)
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-        if (k0 + m < kMaxPop)
-#pragma unroll
-            for (int w = 0; w < 8; ++w) red[warp][k0 + m][w] = 0.0;
+    RecvAcc acc;
     const int end = chunk_end[c];
     int i = chunk_begin[c] + warp;
     RecvAtom cur, nxt;
@@ -637,18 +670,10 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
             __syncwarp();
             discard_l2_lines(pbuf + (size_t)cur.ps * 3 * Pst, pbuf + (size_t)cur.pe * 3 * Pst, lane);
         }
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            if (!(m == 0 ? on0 : on1)) continue;
-            const float dx = F[m][0] - cur.t[0], dy = F[m][1] - cur.t[1], dz = F[m][2] - cur.t[2];
-            double* r = red[warp][k0 + m];
-            r[0] += m == 0 ? cur.u0 : cur.u1;
-            r[1] += (double)dx * dx + (double)dy * dy + (double)dz * dz;
-#pragma unroll
-            for (int w = 0; w < 6; ++w) r[2 + w] += (double)(m == 0 ? cur.w6[w].x : cur.w6[w].y);
-        }
+        acc.add(cur, F);
         cur = nxt;
     }
+    acc.store(red[warp], k0);
     __syncthreads();
     for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
         const int k = e / 8, w = e % 8;
@@ -683,11 +708,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
     const bool ld = k0 < Pst;
     const int half = Pst / 2;  // member pairs per row
     unsigned char* stage = s_slots_raw + (size_t)warp * kRecvStage * 3 * half * kPair;
-#pragma unroll
-    for (int m = 0; m < 2; ++m)
-        if (k0 + m < kMaxPop)
-#pragma unroll
-            for (int w = 0; w < 8; ++w) red[warp][k0 + m][w] = 0.0;
+    RecvAcc acc;
     const int end = chunk_end[c];
     int i = chunk_begin[c] + warp;
     RecvAtom cur, nxt;
@@ -723,18 +744,143 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
             __syncwarp();
             discard_l2_lines(pbuf + (size_t)cur.ps * 3 * Pst, pbuf + (size_t)cur.pe * 3 * Pst, lane);
         }
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            if (!(m == 0 ? on0 : on1)) continue;
-            const float dx = F[m][0] - cur.t[0], dy = F[m][1] - cur.t[1], dz = F[m][2] - cur.t[2];
-            double* r = red[warp][k0 + m];
-            r[0] += m == 0 ? cur.u0 : cur.u1;
-            r[1] += (double)dx * dx + (double)dy * dy + (double)dz * dz;
-#pragma unroll
-            for (int w = 0; w < 6; ++w) r[2 + w] += (double)(m == 0 ? cur.w6[w].x : cur.w6[w].y);
-        }
+        acc.add(cur, F);
         cur = nxt;
     }
+    acc.store(red[warp], k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
+        const int k = e / 8, w = e % 8;
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) t += red[q][k][w];
+        partials[((size_t)c * P + k) * 8 + w] = t;
+    }
+}
+
+// The receiver pass with each atom's slot rows brought into shared memory by
+// bulk asynchronous copies (cp.async.bulk, completion counted on an
+// mbarrier).  A receiver's slots are contiguous in the partial-force buffer,
+// so lane 0 of a warp requests them as pieces of at most kBulkStage bytes,
+// two pieces ahead of the lanes' sums (two buffers per warp); a piece's
+// first and last bytes are rounded out to 16-byte boundaries (the buffer is
+// allocated in FP32 units, so in FP16 mode the rounded end stays inside it;
+// FP32 slots are multiples of 48 bytes and need no rounding).  The lanes add
+// from shared memory in slot order: the same atoms per warp, terms and order
+// of summation as k_contract, hence the same bits.  Every wait is bounded: a
+// copy that does not land latches NEP_ERR_TIMEOUT and the warp stops summing;
+// it then waits (bounded) for its copies still in flight before the block
+// exits, so no copy writes into shared memory another block owns.
+constexpr int kBulkStage = 4096;           // payload bytes of one piece
+constexpr int kBulkBuf = kBulkStage + 32;  // + the rounding at both ends (16-byte multiple)
+constexpr int kBulkSmem = (kReceiverThreads / 32) * 2 * kBulkBuf;
+constexpr uint32_t kBulkPolls = 1u << 22;
+
+template <class PT>
+__global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
+    int c0, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
+    const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
+    const PT* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
+    double* __restrict__ partials, unsigned* __restrict__ err)
+{
+    constexpr int kWarps = kReceiverThreads / 32;
+    __shared__ double red[kWarps][kMaxPop][8];
+    __shared__ __align__(8) uint64_t bar[kWarps][2];
+    extern __shared__ __align__(128) unsigned char s_bulk[];  // [warps][2][kBulkBuf]
+    const int c = c0 + blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k0 = 2 * lane;
+    const bool on0 = k0 < P, on1 = k0 + 1 < P;
+    const bool ld = k0 < Pst;
+    const long long slot_bytes = 3LL * Pst * (long long)sizeof(PT);
+    const long long per_piece = kBulkStage / slot_bytes;  // >= 5 slots (Pst <= 64)
+    unsigned char* buf = s_bulk + (size_t)warp * 2 * kBulkBuf;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(pbuf);
+    RecvAcc acc;
+    if (lane == 0) {
+        tc::mbar_init(&bar[warp][0], 1);
+        tc::mbar_init(&bar[warp][1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int end = chunk_end[c];
+    // producer cursor: atom pa, its next slot pp and its slot end pend
+    int pa = chunk_begin[c] + warp;
+    long long pp = 0, pend = 0;
+    if (pa < end) {
+        pp = pstart[pa];
+        pend = pstart[pa + 1];
+    }
+    unsigned n_issued = 0, n_waited = 0;  // piece n: buffer n & 1, barrier phase parity (n >> 1) & 1
+    // requests the next piece of this warp's atoms, if any
+    auto issue = [&]() {
+        while (pa < end && pp >= pend) {
+            pa += kWarps;
+            if (pa < end) {
+                pp = pstart[pa];
+                pend = pstart[pa + 1];
+            }
+        }
+        if (pa >= end) return;
+        const long long q1 = min(pend, pp + per_piece);
+        const size_t b0 = (size_t)(pp * slot_bytes), b1 = (size_t)(q1 * slot_bytes);
+        const size_t a0 = b0 & ~(size_t)15, a1 = (b1 + 15) & ~(size_t)15;
+        const int s = (int)(n_issued & 1u);
+        if (lane == 0) {
+            const uint32_t bb = tc::smem_u32(&bar[warp][s]);
+            // the buffer's previous piece was read by ordinary loads (ordered by the __syncwarp before this call)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"((uint32_t)(a1 - a0))
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             tc::smem_u32(buf + s * kBulkBuf)),
+                         "l"(src + a0), "r"((uint32_t)(a1 - a0)), "r"(bb)
+                         : "memory");
+        }
+        pp = q1;
+        ++n_issued;
+    };
+    issue();
+    issue();
+    bool ok = true;
+    int i = chunk_begin[c] + warp;
+    RecvAtom cur, nxt;
+    if (i < end) recv_load(cur, i, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
+    for (; ok && i < end; i += kWarps) {
+        if (i + kWarps < end) recv_load(nxt, i + kWarps, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
+        float F[2][3] = {{cur.fo[0].x, cur.fo[1].x, cur.fo[2].x}, {cur.fo[0].y, cur.fo[1].y, cur.fo[2].y}};
+        for (long long q0 = cur.ps; q0 < cur.pe; q0 += per_piece) {
+            const long long q1 = min(cur.pe, q0 + per_piece);
+            const int s = (int)(n_waited & 1u);
+            ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar[warp][s], (n_waited >> 1) & 1u, kBulkPolls));
+            if (!ok) break;
+            ++n_waited;
+            const size_t b0 = (size_t)(q0 * slot_bytes);
+            const unsigned char* base = buf + s * kBulkBuf + (b0 - (b0 & ~(size_t)15));
+            if (ld)
+                for (long long q = q0; q < q1; ++q) {
+                    const PT* o = reinterpret_cast<const PT*>(base + (size_t)((q - q0) * slot_bytes)) + k0;
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        const float2 x = pb_load2(o + (size_t)cc * Pst);
+                        F[0][cc] -= x.x;
+                        F[1][cc] -= x.y;
+                    }
+                }
+            __syncwarp();  // every lane has read the buffer before it is refilled
+            issue();
+        }
+        if (!ok) break;
+        acc.add(cur, F);
+        cur = nxt;
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(err, kErrTimeout);
+        // the copies still in flight land before the block's shared memory goes (bounded)
+        for (; n_waited < n_issued; ++n_waited)
+            tc::mbar_wait(&bar[warp][n_waited & 1u], (n_waited >> 1) & 1u, kBulkPolls);
+    }
+    acc.store(red[warp], k0);
     __syncthreads();
     for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
         const int k = e / 8, w = e % 8;
@@ -1137,7 +1283,7 @@ bool valid_shape(const nep_dataset* ds, const EvalShape& h)
 {
     return h.waves >= 1 && h.waves <= kMaxWaves && (h.owner_warps == 4 || h.owner_warps == 8) &&
            (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
-           (h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 12 || h.recv_unroll == 16) &&
+           (h.recv_unroll == 1 || h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 12 || h.recv_unroll == 16) &&
            (h.fused == 0 || ((h.fused == 4 || h.fused == 8 || h.fused == 16) && fused_fits(ds, h.fused))) &&
            (h.owner_tc == 0 || h.owner_tc == 1);
 }
@@ -1259,7 +1405,11 @@ int prepare_evaluation(nep_dataset* ds, int P)
         (rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              rstage), "contraction shared memory")) ||
         (rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             rstage / 2), "contraction shared memory")))
+                                             rstage / 2), "contraction shared memory")) ||
+        (rc = cuda_fail(cudaFuncSetAttribute(k_contract_bulk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kBulkSmem), "contraction shared memory")) ||
+        (rc = cuda_fail(cudaFuncSetAttribute(k_contract_bulk<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kBulkSmem), "contraction shared memory")))
         return rc;
     for (int gm = 4; gm <= 16; gm *= 2) {
         if (!fused_fits(ds, gm)) continue;
@@ -1299,7 +1449,12 @@ void launch_contraction_t(const nep_dataset* ds, int P, int Pst, int c_lo, int c
         cudaEventRecord(ev, st);
         cudaStreamWaitEvent(p2, ev, 0);
     }
-    if (sh.recv_unroll == 16) {
+    if (sh.recv_unroll == 1) {
+        k_contract_bulk<PT><<<c_hi - c_lo, kReceiverThreads, kBulkSmem, p2>>>(c_lo, P, Pst, ds->chunk_begin,
+                                                                              ds->chunk_end, ds->U, ds->pstart,
+                                                                              ds->fown, pbuf, ds->w6, ds->f_tar,
+                                                                              ds->partials, ds->m->d_err);
+    } else if (sh.recv_unroll == 16) {
         const size_t smem = (size_t)(kReceiverThreads / 32) * kRecvStage * 3 * Pst * sizeof(PT);
         k_contract_staged<PT><<<c_hi - c_lo, kReceiverThreads, smem, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin,
                                                                            ds->chunk_end, ds->U, ds->pstart,
@@ -1935,7 +2090,7 @@ int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
     h.owner_tc = shape[6];
     if (!valid_shape(ds, h)) {
         set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
-                  "receiver unroll 4, 8, 12 or 16 (staged), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
+                  "receiver unroll 4, 8, 12, 16 (staged) or 1 (bulk copies), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
                   "48 bytes of shared memory at most %zu), owner_tc 0 or 1",
                   kMaxWaves, ds->amax, kFusedSmemMax);
         return NEP_ERR_ARG;
@@ -1978,7 +2133,7 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
         for (int ow = 4; ow <= 8; ow += 4)
             for (int dc = 0; dc <= (w > 1 ? 1 : 0); ++dc)
                 for (int mt = 128; mt <= 256; mt += 128)
-                    for (int ru : {4, 8, 12, 16}) {
+                    for (int ru : {1, 4, 8, 12, 16}) {
                         if (precision == NEP_PREC_BF16 && mt == 128) continue;  // the FP32 network is not launched
                         EvalShape h;
                         h.waves = w;

@@ -59,7 +59,7 @@ def _two_pass_shapes(precision, N):
         for ow in (4, 8):
             for dc in ((0, 1) if w > 1 else (0,)):
                 for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
-                    for ru in (4, 8, 12, 16):
+                    for ru in (1, 4, 8, 12, 16):
                         out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru,
                                         fused=0, owner_tc=0))
     return out
@@ -68,7 +68,7 @@ def _two_pass_shapes(precision, N):
 def _tc_shapes():
     """Two-pass shapes with the first pass on the tensor cores (BF16)."""
     return [dict(waves=w, owner_warps=4, discard=dc, mlp_threads=256, recv_unroll=ru, fused=0, owner_tc=1)
-            for w in (1, 2, 4) for dc in ((0, 1) if w > 1 else (0,)) for ru in (4, 8, 12, 16)]
+            for w in (1, 2, 4) for dc in ((0, 1) if w > 1 else (0,)) for ru in (1, 4, 8, 12, 16)]
 
 
 def _fused_shapes(precision, N):
@@ -146,7 +146,7 @@ def test_shape_validation(N, full_set):
     assert ds.default_shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4, fused=8,
                                       owner_tc=0)
     for bad in (dict(waves=0), dict(waves=17), dict(owner_warps=6), dict(discard=2), dict(mlp_threads=64),
-                dict(recv_unroll=2), dict(recv_unroll=6), dict(fused=2), dict(fused=32), dict(fused=-4),
+                dict(recv_unroll=0), dict(recv_unroll=2), dict(recv_unroll=6), dict(fused=2), dict(fused=32), dict(fused=-4),
                 dict(owner_tc=2), dict(owner_tc=-1)):
         with pytest.raises(N.NepError) as e:
             ds.set_shape(**bad)
