@@ -384,7 +384,7 @@ int nep_dataset_counts(const nep_dataset* ds, long long* counts);
 int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
 
 /*
- * Launch shape of the population evaluation of a dataset, host int[7]:
+ * Launch shape of the population evaluation of a dataset, host int[8]:
  *   [5] fused       0, 4, 8 or 16.  Nonzero: the fused contraction, one
  *                   block per (structure, group of this many members), the
  *                   structure's forces summed in shared memory (exactly, as
@@ -416,12 +416,17 @@ int nep_dataset_descriptors(const nep_dataset* ds, float* q, void* stream);
  *                   dataset, each row scaled by a power of two) with its
  *                   members' FP16 input gradients; [1] does not apply.
  *                   Ignored in NEP_PREC_FP32 and by the fused form.
+ *   [7] pop_pipe    0 or 1.  1 in NEP_PREC_BF16: the population network as
+ *                   one persistent CTA per SM and member group, with the
+ *                   bulk copies, both GEMMs and the epilogues of successive
+ *                   128-atom tiles overlapped on separate warps (the same
+ *                   arithmetic, the same bits).  Ignored in NEP_PREC_FP32.
  * Within each form (fused, two passes, two passes with owner_tc in BF16) no
  * shape changes a result bit (every value keeps its writer and its order of
  * summation).  The fused and two-pass forms differ in the last bits of the
  * FP32 force sums (exact in the fused form); owner_tc rounds the Jacobians
  * to FP16 (~1e-4 relative in the loss terms).
- * Default after nep_dataset_create: {1, 4, 0, 256, 4, 8, 0} (members per
+ * Default after nep_dataset_create: {1, 4, 0, 256, 4, 8, 0, 0} (members per
  * block 4, or the two passes, when the largest structure does not fit 8).
  * Errors: NEP_ERR_ARG (NULL, out of range, too little shared memory).
  */
@@ -434,10 +439,11 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape);
  * the fastest on the dataset.  Candidates: the fused contraction with 4, 8
  * or 16 members per block (where the shared memory fits; the owner atoms per
  * warp are 32 / members), and the two passes with waves 1, 2, 4 x owner
- * warps 4, 8 x discard 0, 1 when waves > 1 x unroll 4, 8, 12, 16; each with
- * network threads 128, 256 in FP32 mode; in BF16 mode also every two-pass
- * candidate with owner_tc 1.  Synchronises the stream.
- * shape_out: host int[7] or NULL; ms_out: host, the best shape's time per
+ * warps 4, 8 x discard 0, 1 when waves > 1 x unroll 1, 4, 8, 12, 16; each
+ * with network threads 128, 256 in FP32 mode; in BF16 mode also every
+ * two-pass candidate with owner_tc 1, and every candidate with pop_pipe 0
+ * and 1.  Synchronises the stream.
+ * shape_out: host int[8] or NULL; ms_out: host, the best shape's time per
  * evaluation, or NULL.
  * Errors: NEP_ERR_ARG (NULL, dataset of another model, n_pop outside 1..64,
  * reps < 1, unknown precision), NEP_ERR_OOM, NEP_ERR_CUDA.

@@ -47,6 +47,8 @@ struct EvalShape {
                             // this many members per block (one block per structure and member group)
     int owner_tc = 0;       // 1: in BF16 precision the first of the two passes runs on the tensor
                             // cores (FP16 Jacobian rows x FP16 G, FP32 accumulation)
+    int pop_pipe = 0;       // 1: in BF16 precision the population network runs as the pipelined
+                            // persistent kernel (same bits)
 };
 
 }  // namespace nep
@@ -90,6 +92,8 @@ struct nep_dataset {
     float* G = nullptr;
     double* U = nullptr;
     double* partials = nullptr;
+    double* loss_part = nullptr;     // [P][kLossSplit][5] block sums of the loss kernel
+    unsigned* loss_count = nullptr;  // [P] blocks of the loss kernel done (zero between evaluations)
     unsigned char* packed = nullptr;  // tensor-core operand records
     unsigned char* qpack = nullptr;   // descriptors as split-BF16 A tiles (tensor cores)
     float* pbuf = nullptr;            // [n_pairs][3][Pst] partial forces p_kji at the receiver's slot

@@ -125,6 +125,14 @@ __device__ __forceinline__ unsigned char* d_tile(PopSmem& S, int m)
     return m < 2 ? S.a + m * kTileBytes : S.grp + (m - 2) * kTileBytes;
 }
 
+// tanh(a) = 1 - 2 / (1 + e^(2a)) with the hardware exponential (__expf) and a
+// fast division: absolute error of order 1e-7 for small |a| (the subtraction
+// from 1), saturating to +-1 where e^(2a) over- or underflows.  The BF16
+// mode's network only: D = w2 (1 - x^2) is rounded to BF16 for GEMM 2 and the
+// losses are held to 1e-3 of the FP32 path, against an error of about 1e-6 eV
+// per atom that this gives U.
+__device__ __forceinline__ float tanh_fast(float a) { return 1.f - __fdividef(2.f, 1.f + __expf(2.f * a)); }
+
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo)
 {
     hi = __float2bfloat16_rn(x);
@@ -172,11 +180,11 @@ __global__ void k_pack_q_tc(int N, int tiles, const float* __restrict__ q, unsig
     *reinterpret_cast<uint4*>(base + kTileBytes + o) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-// One thread per (group, element) of the packed records.
-__global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ W1t, const float* __restrict__ b1t,
-                          const float* __restrict__ w2t, const float* __restrict__ b2t,
-                          unsigned char* __restrict__ packed)
+// One thread per (group, element) of the packed records, read straight from
+// the population z [P][n_par] (layout w1 [n_neu][32], b1, w2, b2 per member).
+__global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigned char* __restrict__ packed)
 {
+    const int n_par = (kNdes + 2) * n_neu + 1;
     const int groups = (P + kTcGroup - 1) / kTcGroup;
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;  // w1 elems, w1t elems, bias rows
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,7 +195,7 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ W1t, const
     if (r < kTile * 32) {  // GEMM-1 B row = 32 m + mu, column nu
         const int row = r / 32, nu = r % 32, m = row / 32, mu = row % 32;
         const bool on = m < mg && mu < n_neu;
-        put_split(rec, rec + kW1Bytes, row, nu, on ? W1t[((size_t)mu * kNdes + nu) * P + k0 + m] : 0.f);
+        put_split(rec, rec + kW1Bytes, row, nu, on ? z[(size_t)(k0 + m) * n_par + mu * kNdes + nu] : 0.f);
         return;
     }
     int t = r - kTile * 32;
@@ -195,16 +203,17 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ W1t, const
         const int m = t / 1024, nu = (t / 32) % 32, mu = t % 32;
         const bool on = m < mg && mu < n_neu;
         unsigned char* hi = rec + 2 * kW1Bytes + m * kW1tBytes;
-        put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, on ? W1t[((size_t)mu * kNdes + nu) * P + k0 + m] : 0.f);
+        put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, on ? z[(size_t)(k0 + m) * n_par + mu * kNdes + nu] : 0.f);
         return;
     }
     t -= kTcGroup * 32 * 32;
     float* fb = reinterpret_cast<float*>(rec + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
     const int m = t / 32, mu = t % 32;
     const bool on = m < mg && mu < n_neu;
-    fb[m * 32 + mu] = on ? b1t[(size_t)mu * P + k0 + m] : 0.f;
-    fb[kTcGroup * 32 + m * 32 + mu] = on ? w2t[(size_t)mu * P + k0 + m] : 0.f;
-    if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? b2t[k0 + m] : 0.f;
+    const float* zk = z + (size_t)(k0 + m) * n_par;
+    fb[m * 32 + mu] = on ? zk[n_neu * kNdes + mu] : 0.f;
+    fb[kTcGroup * 32 + m * 32 + mu] = on ? zk[n_neu * kNdes + n_neu + mu] : 0.f;
+    if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? zk[n_neu * (kNdes + 2)] : 0.f;
 }
 
 // Issue the split-BF16 products of one K = 32 tile pair into d_tmem:
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const int mu = 2 * e + h;
-                        const float x = tanhf(__uint_as_float(r[c][mu]) - b1v[mu]);
+                        const float x = tanh_fast(__uint_as_float(r[c][mu]) - b1v[mu]);
                         const float w2 = w2v[mu];
                         u = fmaf(w2, x, u);
                         dd[h] = __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
@@ -401,6 +410,295 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tb, kTmemCols);
+}
+
+// ------------------------------------------------------- pipelined population
+// The same network as k_pop_tc, as a persistent kernel with its roles on
+// separate warps, so that the copies, both GEMMs and the epilogues of
+// successive 128-atom tiles overlap.  One CTA per SM keeps one member group's
+// packed record resident and walks its share of the tiles (CTA c: group
+// c mod groups, tiles c / groups, c / groups + CTAs per group, ...):
+//   warp 16, lane 0  bulk copies: the record once, then each tile's split
+//                    BF16 descriptors into one of kPipeQ stages;
+//   warp 17, lane 0  the MMAs: GEMM 1 of tile n into TMEM buffer n mod
+//                    kPipeT (128 columns each) up to kPipeT - 1 tiles ahead,
+//                    GEMM 2 of tile n into the same buffer once its D is in
+//                    shared memory (D buffer n mod 2);
+//   warps 0-15       the epilogues in the order E1(0) E1(1) E2(0) E1(2)
+//                    E2(1) ...: warp w reads TMEM lane quarter w & 3;
+//                    epilogue 1 takes member w >> 2 (tanh, U, D as BF16),
+//                    epilogue 2 descriptors [8 (w >> 2), + 8) of all four
+//                    members (G).
+// A TMEM buffer is freed when epilogue 2 of its tile has read it, so with
+// four buffers GEMM 1 runs three tiles ahead of the epilogues.  Every value
+// is formed by the same operations in the same order as in k_pop_tc, so the
+// two kernels give the same bits.  mbarriers order the roles; every wait is
+// bounded, and a wait that runs out latches NEP_ERR_TIMEOUT and raises a flag
+// on which every role stops; the copy and MMA threads then wait (bounded) for
+// their own work in flight before the CTA frees its TMEM.
+constexpr int kPipeEpiWarps = 16;
+constexpr int kPipeThreads = (kPipeEpiWarps + 2) * 32;
+constexpr int kPipeT = 4;  // TMEM buffers of 128 columns (512 columns: one CTA per SM)
+constexpr int kPipeQ = 3;  // descriptor stages
+constexpr int kPipeD = 2;  // D buffers
+struct PipeSmem {
+    unsigned char q[kPipeQ][2 * kTileBytes];        // descriptor stages (hi | lo)
+    unsigned char d[kPipeD][kTcGroup][kTileBytes];  // D of the four members, per buffer
+    unsigned char grp[kGroupBytes];                 // the group's packed record
+    uint64_t q_full[kPipeQ], q_empty[kPipeQ], g1_done[kPipeT], g2_done[kPipeT], tmem_free[kPipeT], d_ready[kPipeD];
+    uint64_t grp_full, mma_all;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// Bounded wait that also gives up once another role has raised the abort flag.
+__device__ __forceinline__ bool pipe_wait(uint64_t* bar, uint32_t parity, volatile int* abort)
+{
+    const uint32_t a = tc::smem_u32(bar);
+    for (uint32_t it = 0; it < kMaxPolls; ++it) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 31u) == 31u && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+__device__ __forceinline__ void pipe_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc::smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+                 : "memory");
+}
+
+template <int GL>
+__global__ void __launch_bounds__(kPipeThreads, 1) k_pop_tc_pipe(int N, int P, int Pst, int groups,
+                                                                 const unsigned char* __restrict__ qpack,
+                                                                 const unsigned char* __restrict__ packed,
+                                                                 void* __restrict__ Gv, double* __restrict__ U,
+                                                                 unsigned* err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    PipeSmem& S = *reinterpret_cast<PipeSmem*>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int g = blockIdx.x % groups, k0 = g * kTcGroup;
+    const int sub = blockIdx.x / groups, nsub = gridDim.x / groups;
+    const int tiles = (N + kTile - 1) / kTile;
+    const int cnt = sub < tiles ? (tiles - sub + nsub - 1) / nsub : 0;  // this CTA's tiles
+    volatile int* abort = &S.abort;
+    if (t == 0) {
+        for (int b = 0; b < kPipeQ; ++b) {
+            tc::mbar_init(&S.q_full[b], 1);
+            tc::mbar_init(&S.q_empty[b], 1);
+        }
+        for (int b = 0; b < kPipeT; ++b) {
+            tc::mbar_init(&S.g1_done[b], 1);
+            tc::mbar_init(&S.g2_done[b], 1);
+            tc::mbar_init(&S.tmem_free[b], kPipeEpiWarps);
+        }
+        for (int b = 0; b < kPipeD; ++b) tc::mbar_init(&S.d_ready[b], kPipeEpiWarps);
+        tc::mbar_init(&S.grp_full, 1);
+        tc::mbar_init(&S.mma_all, 1);
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kPipeEpiWarps) {
+        tc::tmem_alloc(&S.tmem_base, kPipeT * kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = S.tmem_base;
+    const unsigned char* w1t_hi = S.grp + 2 * kW1Bytes;
+    const unsigned char* w1t_lo = w1t_hi + kTcGroup * kW1tBytes;
+    const float* fb = reinterpret_cast<const float*>(S.grp + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
+
+    if (warp == kPipeEpiWarps) {
+        // ---------------------------------------------------------- copies
+        if (lane == 0 && cnt > 0) {
+            unsigned issued[kPipeQ] = {};
+            bulk_copy(S.grp, packed + (size_t)g * kGroupBytes, (uint32_t)kGroupBytes, &S.grp_full);
+            for (int n = 0; n < cnt; ++n) {
+                const int s = n % kPipeQ, use = n / kPipeQ;
+                // the stage's previous tile (n - kPipeQ) has been read by its GEMM 1
+                if (use > 0 && !pipe_wait(&S.q_empty[s], (use - 1) & 1, abort)) break;
+                bulk_copy(S.q[s], qpack + (size_t)(sub + n * nsub) * 2 * kTileBytes, (uint32_t)(2 * kTileBytes),
+                          &S.q_full[s]);
+                ++issued[s];
+            }
+            if (*abort) {  // what is in flight lands before the CTA goes (bounded)
+                tc::mbar_wait(&S.grp_full, 0, kMaxPolls);
+                for (int s = 0; s < kPipeQ; ++s)
+                    if (issued[s]) tc::mbar_wait(&S.q_full[s], (issued[s] - 1) & 1, kMaxPolls);
+            }
+        }
+    } else if (warp == kPipeEpiWarps + 1) {
+        // ------------------------------------------------------------ MMAs
+        if (lane == 0 && cnt > 0) {
+            const uint32_t id1 = tc::idesc_bf16_f32(kTile, kTmemCols), id2 = tc::idesc_bf16_f32(kTile, 32);
+            bool ok = pipe_wait(&S.grp_full, 0, abort);
+            auto gemm1 = [&](int n) {
+                const int s = n % kPipeQ, b = n % kPipeT;
+                if (!pipe_wait(&S.q_full[s], (n / kPipeQ) & 1, abort)) return false;
+                // TMEM buffer b is free once epilogue 2 of tile n - kPipeT has read it
+                if (n >= kPipeT && !pipe_wait(&S.tmem_free[b], (n / kPipeT - 1) & 1, abort)) return false;
+                tc::fence_after_sync();
+                mma_split(tb + (uint32_t)(b * kTmemCols), S.q[s], S.q[s] + kTileBytes, S.grp, S.grp + kW1Bytes, id1);
+                tc::mma_commit(&S.g1_done[b]);
+                tc::mma_commit(&S.q_empty[s]);
+                return true;
+            };
+            // GEMM 1 runs kPipeT - 1 tiles ahead: G1(n + kPipeT - 1) waits for
+            // epilogue 2 of tile n - 1, which the epilogues reach after
+            // epilogue 1 of tile n (the D that G2(n) needs)
+            for (int n = 0; ok && n < kPipeT - 1 && n < cnt; ++n) ok = gemm1(n);
+            for (int n = 0; ok && n < cnt; ++n) {
+                const int b = n % kPipeT, db = n % kPipeD;
+                if (!(ok = pipe_wait(&S.d_ready[db], (n / kPipeD) & 1, abort))) break;
+                tc::fence_after_sync();
+                for (int m = 0; m < kTcGroup; ++m)
+                    mma_split(tb + (uint32_t)(b * kTmemCols + 32 * m), S.d[db][m], nullptr, w1t_hi + m * kW1tBytes,
+                              w1t_lo + m * kW1tBytes, id2);
+                tc::mma_commit(&S.g2_done[b]);
+                if (n + kPipeT - 1 < cnt) ok = gemm1(n + kPipeT - 1);
+            }
+            // every MMA issued has completed before TMEM is freed (bounded)
+            tc::mma_commit(&S.mma_all);
+            tc::mbar_wait(&S.mma_all, 0, kMaxPolls);
+        }
+    } else {
+        // ------------------------------------------------------- epilogues
+        const int quarter = warp & 3, part = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        bool ok = cnt > 0 && pipe_wait(&S.grp_full, 0, abort);
+        // epilogue 1 of tile n: member `part`
+        auto epi1 = [&](int n) {
+            const int b = n % kPipeT, db = n % kPipeD, m = part;
+            if (!pipe_wait(&S.g1_done[b], (n / kPipeT) & 1, abort)) return false;
+            tc::fence_after_sync();
+            const int i = (sub + n * nsub) * kTile + row;
+            uint32_t r[4][8];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(b * kTmemCols + 32 * m + 8 * c), r[c]);
+            tc::tmem_ld_wait();
+            float u = 0.f;
+            unsigned char* D = S.d[db][m];
+            const float4* b14 = reinterpret_cast<const float4*>(fb + m * 32);
+            const float4* w24 = reinterpret_cast<const float4*>(fb + kTcGroup * 32 + m * 32);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t d[4];
+                const float4 ba = b14[2 * c], bb = b14[2 * c + 1], wa = w24[2 * c], wb = w24[2 * c + 1];
+                const float b1v[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
+                const float w2v[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    __nv_bfloat16 dd[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int mu = 2 * e + h;
+                        const float x = tanh_fast(__uint_as_float(r[c][mu]) - b1v[mu]);
+                        const float w2 = w2v[mu];
+                        u = fmaf(w2, x, u);
+                        dd[h] = __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
+                    }
+                    d[e] = pack2(dd[0], dd[1]);
+                }
+                *reinterpret_cast<uint4*>(D + tc::kmajor_offset(row, 8 * c)) = make_uint4(d[0], d[1], d[2], d[3]);
+            }
+            // D is visible to the tensor core, and this warp's TMEM reads are done
+            tc::fence_proxy_async_smem();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) pipe_arrive(&S.d_ready[db]);
+            if (i < N && k0 + m < P) U[(size_t)i * P + k0 + m] = (double)u - (double)fb[2 * kTcGroup * 32 + m];
+            return true;
+        };
+        // epilogue 2 of tile n: descriptors [8 part, 8 part + 8) of the four members
+        auto epi2 = [&](int n) {
+            const int b = n % kPipeT;
+            if (!pipe_wait(&S.g2_done[b], (n / kPipeT) & 1, abort)) return false;
+            tc::fence_after_sync();
+            const int i = (sub + n * nsub) * kTile + row;
+            uint32_t r[kTcGroup][8];
+#pragma unroll
+            for (int m = 0; m < kTcGroup; ++m)
+                tc::tmem_ld8(tb + lane_base + (uint32_t)(b * kTmemCols + 32 * m + 8 * part), r[m]);
+            tc::tmem_ld_wait();
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) pipe_arrive(&S.tmem_free[b]);
+            if (i < N) {
+                if (GL == kGTilesF16) {
+                    // rows k0..k0+3 of K-chunk `part` are 64 contiguous bytes
+                    // (32-byte aligned): two 32-byte stores, whole sectors
+                    unsigned char* base = reinterpret_cast<unsigned char*>(Gv) + (size_t)i * owner_tc_g_bytes(Pst);
+                    uint32_t h[kTcGroup][4];
+#pragma unroll
+                    for (int m = 0; m < kTcGroup; ++m)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __half2 v = __floats2half2_rn(__uint_as_float(r[m][2 * e]),
+                                                                __uint_as_float(r[m][2 * e + 1]));
+                            h[m][e] = *reinterpret_cast<const uint32_t*>(&v);
+                        }
+                    unsigned char* dst = base + tc::kmajor_offset(k0, 8 * part);
+#pragma unroll
+                    for (int hp = 0; hp < 2; ++hp)
+                        asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst + 32 * hp),
+                                     "r"(h[2 * hp][0]), "r"(h[2 * hp][1]), "r"(h[2 * hp][2]), "r"(h[2 * hp][3]),
+                                     "r"(h[2 * hp + 1][0]), "r"(h[2 * hp + 1][1]), "r"(h[2 * hp + 1][2]),
+                                     "r"(h[2 * hp + 1][3])
+                                     : "memory");
+                } else {
+                    const size_t o0 = ((size_t)i * kNdes + 8 * part) * Pst + k0;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const size_t o = o0 + (size_t)e * Pst;
+                        const float g0 = __uint_as_float(r[0][e]), g1 = __uint_as_float(r[1][e]);
+                        const float g2 = __uint_as_float(r[2][e]), g3 = __uint_as_float(r[3][e]);
+                        if (GL == kGRowsF16) {
+                            const __half2 a = __floats2half2_rn(g0, g1), c = __floats2half2_rn(g2, g3);
+                            uint2 v;
+                            v.x = *reinterpret_cast<const uint32_t*>(&a);
+                            v.y = *reinterpret_cast<const uint32_t*>(&c);
+                            *reinterpret_cast<uint2*>(reinterpret_cast<__half*>(Gv) + o) = v;
+                        } else {
+                            *reinterpret_cast<float4*>(reinterpret_cast<float*>(Gv) + o) = make_float4(g0, g1, g2, g3);
+                        }
+                    }
+                }
+            }
+            return true;
+        };
+        if (ok) ok = epi1(0);
+        for (int n = 0; ok && n < cnt; ++n) {
+            if (n + 1 < cnt && !(ok = epi1(n + 1))) break;
+            ok = epi2(n);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0 && S.abort) atomicOr(err, kErrTimeout);
+    if (warp == kPipeEpiWarps) tc::tmem_dealloc(tb, kPipeT * kTmemCols);
 }
 
 // ------------------------------------------------------------ owner pass
@@ -673,6 +971,12 @@ int prepare_pop_tc()
     if (!rc)
         rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc<kGTilesF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)sizeof(PopSmem)), "population kernel shared memory");
+    if (!rc)
+        rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc_pipe<kGRowsF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(PipeSmem)), "population kernel shared memory");
+    if (!rc)
+        rc = cuda_fail(cudaFuncSetAttribute(k_pop_tc_pipe<kGTilesF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)sizeof(PipeSmem)), "population kernel shared memory");
     return rc;
 }
 
@@ -685,9 +989,8 @@ int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t s
     return cuda_fail(cudaGetLastError(), "pack descriptors for the tensor cores");
 }
 
-int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* W1t, const float* b1t,
-                  const float* w2t, const float* b2t, unsigned char* packed, void* G, int g_layout, double* U,
-                  unsigned* err, cudaStream_t st)
+int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* z, unsigned char* packed,
+                  void* G, int g_layout, double* U, unsigned* err, bool pipelined, cudaStream_t st)
 {
     if (n_neu > 32 || Pst % 4 != 0 || Pst < P) {
         set_error("tensor-core population path needs n_neu <= 32 and a member stride that is a multiple of 4");
@@ -695,11 +998,23 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, 
     }
     const int groups = (P + kTcGroup - 1) / kTcGroup;
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
-    k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, W1t, b1t, w2t, b2t, packed);
+    k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, z, packed);
+    const int tiles = (N + kTile - 1) / kTile;
+    if (pipelined && g_layout != kGRowsF32) {
+        // one CTA per SM, each keeping one member group's record: as many
+        // CTAs per group as fit on the SMs, at most one per tile
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int nsub = std::max(1, std::min(tiles, nsm / groups));
+        auto kp = g_layout == kGTilesF16 ? k_pop_tc_pipe<kGTilesF16> : k_pop_tc_pipe<kGRowsF16>;
+        kp<<<groups * nsub, kPipeThreads, sizeof(PipeSmem), st>>>(N, P, Pst, groups, qpack, packed, G, U, err);
+        return cuda_fail(cudaGetLastError(), "population tensor-core kernel (pipelined)");
+    }
     const size_t smem = sizeof(PopSmem);
     auto kern = g_layout == kGTilesF16 ? k_pop_tc<kGTilesF16>
                                        : (g_layout == kGRowsF16 ? k_pop_tc<kGRowsF16> : k_pop_tc<kGRowsF32>);
-    kern<<<dim3(groups, (N + kTile - 1) / kTile), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
+    kern<<<dim3(groups, tiles), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
 }
 

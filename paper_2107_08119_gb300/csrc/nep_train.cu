@@ -16,7 +16,8 @@
 //   F_ki = G_ki . B_i - sum_j p_kji                                (Eqs. 4-5)
 //   W_k  = sum_i sum_j r_ij (x) p_kji                              (Eq. 6)
 // and the RMSEs of Eqs. 29-34.  Kernels per evaluation:
-//   k_pack      z_pop -> member-innermost weight layout
+//   k_pack      z_pop -> member-innermost weight layout (FP32 network; the
+//               tensor-core records are packed from z_pop by k_pack_tc)
 //   k_mlp_f32   FP32 network per (atom pair, member): U [N][P] and
 //               G [N][32][Pst] (member innermost, Pst = P rounded up to 4)
 //   k_pop_tc    the same network as BF16 tensor-core GEMMs (nep_pop_tc.cu)
@@ -616,20 +617,49 @@ struct RecvAcc {
             for (int c = 0; c < 6; ++c) w[m][c] += m == 0 ? a.w6[c].x : a.w6[c].y;
         }
     }
-    // the lane's rows red[k0], red[k0 + 1] (members past kMaxPop have none)
-    __device__ __forceinline__ void store(double (*red)[8], int k0) const
+    // the lane's rows of the warp's slice (members past kMaxPop have none)
+    __device__ __forceinline__ void store(double* ru, float (*rf)[7], int k0) const
     {
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             if (k0 + m >= kMaxPop) continue;
-            double* r = red[k0 + m];
-            r[0] = u[m];
-            r[1] = (double)f[m];
+            ru[k0 + m] = u[m];
+            rf[k0 + m][0] = f[m];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) r[2 + c] = (double)w[m][c];
+            for (int c = 0; c < 6; ++c) rf[k0 + m][1 + c] = w[m][c];
         }
     }
 };
+
+// Per-warp sums of a receiver block: U in FP64, the other seven terms in FP32.
+template <int W>
+struct RecvRed {
+    double u[W][kMaxPop];
+    float f[W][kMaxPop][7];
+};
+
+// The chunk's partials in a fixed order (warps 0..W-1): U summed in FP64,
+// the squared force residuals and virial terms in FP32 and converted once.
+template <int W>
+__device__ __forceinline__ void recv_chunk_store(const RecvRed<W>& red, int P, double* __restrict__ out)
+{
+    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
+        const int k = e / 8, w = e % 8;
+        double t;
+        if (w == 0) {
+            double a = 0.0;
+#pragma unroll
+            for (int q = 0; q < W; ++q) a += red.u[q][k];
+            t = a;
+        } else {
+            float a = 0.f;
+#pragma unroll
+            for (int q = 0; q < W; ++q) a += red.f[q][k][w - 1];
+            t = (double)a;
+        }
+        out[(size_t)k * 8 + w] = t;
+    }
+}
 
 template <int UNROLL, class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
@@ -639,7 +669,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
     double* __restrict__ partials)
 {
     constexpr int kWarps = kReceiverThreads / 32;
-    __shared__ double red[kWarps][kMaxPop][8];
+    __shared__ RecvRed<kWarps> red;
     const int c = c0 + blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = 2 * lane;
@@ -673,15 +703,9 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
         acc.add(cur, F);
         cur = nxt;
     }
-    acc.store(red[warp], k0);
+    acc.store(red.u[warp], red.f[warp], k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
-        const int k = e / 8, w = e % 8;
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) t += red[q][k][w];
-        partials[((size_t)c * P + k) * 8 + w] = t;
-    }
+    recv_chunk_store(red, P, partials + (size_t)c * P * 8);
 }
 
 // The receiver pass with the slot rows staged in shared memory: per round a
@@ -699,7 +723,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
 {
     constexpr int kWarps = kReceiverThreads / 32;
     constexpr int kPair = 2 * (int)sizeof(PT);  // bytes of one lane's two members
-    __shared__ double red[kWarps][kMaxPop][8];
+    __shared__ RecvRed<kWarps> red;
     extern __shared__ __align__(16) unsigned char s_slots_raw[];  // [warps][kRecvStage][3][Pst / 2] member pairs
     const int c = c0 + blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -747,15 +771,9 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
         acc.add(cur, F);
         cur = nxt;
     }
-    acc.store(red[warp], k0);
+    acc.store(red.u[warp], red.f[warp], k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
-        const int k = e / 8, w = e % 8;
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) t += red[q][k][w];
-        partials[((size_t)c * P + k) * 8 + w] = t;
-    }
+    recv_chunk_store(red, P, partials + (size_t)c * P * 8);
 }
 
 // The receiver pass with each atom's slot rows brought into shared memory by
@@ -784,7 +802,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
     double* __restrict__ partials, unsigned* __restrict__ err)
 {
     constexpr int kWarps = kReceiverThreads / 32;
-    __shared__ double red[kWarps][kMaxPop][8];
+    __shared__ RecvRed<kWarps> red;
     __shared__ __align__(8) uint64_t bar[kWarps][2];
     extern __shared__ __align__(128) unsigned char s_bulk[];  // [warps][2][kBulkBuf]
     const int c = c0 + blockIdx.x;
@@ -880,15 +898,9 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
         for (; n_waited < n_issued; ++n_waited)
             tc::mbar_wait(&bar[warp][n_waited & 1u], (n_waited >> 1) & 1u, kBulkPolls);
     }
-    acc.store(red[warp], k0);
+    acc.store(red.u[warp], red.f[warp], k0);
     __syncthreads();
-    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
-        const int k = e / 8, w = e % 8;
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < kWarps; ++q) t += red[q][k][w];
-        partials[((size_t)c * P + k) * 8 + w] = t;
-    }
+    recv_chunk_store(red, P, partials + (size_t)c * P * 8);
 }
 
 // Fused contraction: one block per (structure s, group of GM members), the
@@ -1060,38 +1072,79 @@ FusedKernel fused_kernel(int gm, bool gh)
     return gh ? k_contract_fused<16, __half> : k_contract_fused<16, float>;
 }
 
-// One block per member: per structure, the chunk sums (fixed order) or the
-// structure's own sum (fused contraction: s_chunk0 NULL), then the
-// RMSEs of Eqs. 30-32 with energy and virial per atom, and L1, L2 (Eqs. 33-34).
-__global__ void k_loss(int P, int S, int n_par, int N, const int* __restrict__ s_chunk0,
-                       const double* __restrict__ s_inv_na, const double* __restrict__ partials,
-                       const double* __restrict__ e_tar, const double* __restrict__ w_tar,
-                       const float* __restrict__ z, double l_e, double l_f, double l_v, double l_1, double l_2,
-                       double* __restrict__ loss)
+// kLossSplit blocks per member (grid P x kLossSplit), block q taking the
+// structures s = q, q + kLossSplit, ...: per structure, the chunk sums (fixed
+// order) or the structure's own sum (fused contraction: s_chunk0 NULL), then
+// the squared per-atom energy and virial errors; with its share of the
+// parameters for L1, L2.  The member's last block adds the blocks' sums in
+// order and forms the RMSEs of Eqs. 30-32 and L1, L2 (Eqs. 33-34).  FP64
+// arithmetic is slow on this part, so the work is spread over four times as
+// many SMs as members and the parameter sums run in FP32 (four values per
+// thread) before their conversion.
+constexpr int kLossSplit = 4;     // blocks per member, each over every fourth structure
+constexpr int kLossThreads = 64;
+
+// Reciprocals of the loss means' counts: structures S (L_e), force
+// components 3N (L_f), virial components 6S (L_v), parameters (L_1, L_2).
+struct LossInv {
+    double S, F, V, P;
+};
+
+inline LossInv loss_inv(int S, int N, int n_par)
 {
-    constexpr int kBatch = 8;  // chunks whose loads are issued together (summed in order)
-    const int k = blockIdx.x;
+    return LossInv{1.0 / S, 1.0 / (3.0 * N), 1.0 / (6.0 * S), 1.0 / n_par};
+}
+
+// sqrt(x), x >= 0: the FP32 root refined by one Newton step in FP64, y + (x -
+// y^2) / (2 y), the step's divisor in FP32 (relative error of order 1e-14; the
+// FP64 square root is a long serial sequence on this part).  Outside the FP32
+// range (and for 0, infinity or NaN) the library root.
+__device__ __forceinline__ double sqrt_refined(double x)
+{
+    if (!(x > 1e-30 && x < 1e30)) return sqrt(x);
+    const float yf = sqrtf((float)x);
+    const double y = (double)yf;
+    return fma(fma(-y, y, x), (double)(0.5f / yf), y);
+}
+
+__global__ void __launch_bounds__(kLossThreads) k_loss(int P, int S, int n_par, int N, const int* __restrict__ s_chunk0,
+                                                       const double* __restrict__ s_inv_na,
+                                                       const double* __restrict__ partials,
+                                                       const double* __restrict__ e_tar, const double* __restrict__ w_tar,
+                                                       const float* __restrict__ z, double l_e, double l_f, double l_v,
+                                                       double l_1, double l_2, LossInv inv, double* __restrict__ part,
+                                                       unsigned* __restrict__ count, double* __restrict__ loss)
+{
+    constexpr int kBatch = 4;  // chunks whose loads are issued together (summed in order)
+    const int k = blockIdx.x, q = blockIdx.y, nq = gridDim.y;
+    const int stride = nq * blockDim.x;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // se, sf, sv, l1, l2
-    for (int p = threadIdx.x; p < n_par; p += blockDim.x) {
-        const double zz = (double)z[(size_t)k * n_par + p];
-        acc[3] += fabs(zz);
-        acc[4] += zz * zz;
+    {
+        // this thread's parameters (a few per member): FP32 sums, one conversion
+        float a1 = 0.f, a2 = 0.f;
+        for (int p = q + nq * threadIdx.x; p < n_par; p += stride) {
+            const float zz = z[(size_t)k * n_par + p];
+            a1 += fabsf(zz);
+            a2 = fmaf(zz, zz, a2);
+        }
+        acc[3] = (double)a1;
+        acc[4] = (double)a2;
     }
-    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    for (int s = q + nq * threadIdx.x; s < S; s += stride) {
         double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         // per-chunk partials, or (s_chunk0 NULL) one partial per structure
         const int c1 = s_chunk0 ? s_chunk0[s + 1] : s + 1;
         for (int c0 = s_chunk0 ? s_chunk0[s] : s; c0 < c1; c0 += kBatch) {
             double b[kBatch][8];
 #pragma unroll
-            for (int q = 0; q < kBatch; ++q)
+            for (int r = 0; r < kBatch; ++r)
 #pragma unroll
-                for (int w = 0; w < 8; ++w) b[q][w] = c0 + q < c1 ? partials[((size_t)(c0 + q) * P + k) * 8 + w] : 0.0;
+                for (int w = 0; w < 8; ++w) b[r][w] = c0 + r < c1 ? partials[((size_t)(c0 + r) * P + k) * 8 + w] : 0.0;
 #pragma unroll
-            for (int q = 0; q < kBatch; ++q)
-                if (c0 + q < c1)
+            for (int r = 0; r < kBatch; ++r)
+                if (c0 + r < c1)
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) v[w] += b[q][w];
+                    for (int w = 0; w < 8; ++w) v[w] += b[r][w];
         }
         const double inv = s_inv_na[s];  // per-atom energies and virials (FP64 division is slow here)
         const double de = (v[0] - e_tar[s]) * inv;
@@ -1102,20 +1155,34 @@ __global__ void k_loss(int P, int S, int n_par, int N, const int* __restrict__ s
             acc[2] += dv * dv;
         }
     }
-    __shared__ double tot[5];
-    block_sum_store<5>(acc, tot);
+    // the block's five sums; the last of the member's nq blocks (counted)
+    // adds the nq rows in order and forms the losses, then clears the count
+    // for the next evaluation
+    double* row = part + ((size_t)k * nq + q) * 5;
+    block_sum_store<5>(acc, row);
+    __shared__ int last;
+    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double Le = sqrt(tot[0] / S), Lf = sqrt(tot[1] / (3.0 * N)), Lv = sqrt(tot[2] / (6.0 * S));
-        const double L1 = tot[3] / n_par, L2 = sqrt(tot[4] / n_par);
-        double* out = loss + (size_t)k * 6;
-        out[0] = l_e * Le + l_f * Lf + l_v * Lv + l_1 * L1 + l_2 * L2;
-        out[1] = Le;
-        out[2] = Lf;
-        out[3] = Lv;
-        out[4] = L1;
-        out[5] = L2;
+    if (threadIdx.x == 0) last = atomicAdd(&count[k], 1u) == (unsigned)(nq - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // thread c forms term c: the mean over its count (reciprocals from the
+    // host: FP64 division is a long serial sequence here), then the root
+    __shared__ double L[5];
+    if (threadIdx.x < 5) {
+        const int c = threadIdx.x;
+        double t = 0.0;
+        for (int r = 0; r < nq; ++r) t += __ldcg(part + ((size_t)k * nq + r) * 5 + c);
+        const double mean = t * (c == 0 ? inv.S : c == 1 ? inv.F : c == 2 ? inv.V : inv.P);
+        L[c] = c == 3 ? mean : sqrt_refined(mean);
     }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    count[k] = 0u;
+    double* out = loss + (size_t)k * 6;
+    out[0] = l_e * L[0] + l_f * L[1] + l_v * L[2] + l_1 * L[3] + l_2 * L[4];
+    for (int c = 0; c < 5; ++c) out[1 + c] = L[c];
 }
 
 // ------------------------------------------------------------------ SNES
@@ -1215,7 +1282,17 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
 {
     __shared__ int order[kMaxPop];
     __shared__ float u[kMaxPop];
+    __shared__ unsigned long long key[kMaxPop];
     const int t = threadIdx.x;
+    // the members' losses as unsigned keys in the same order as the FP64
+    // values (integer compares: FP64 compares are slow on this part); -0 is
+    // taken as +0, and a NaN loss ranks after every number
+    if (t < P) {
+        const double l = loss[(size_t)t * 6];
+        const long long b = isnan(l) ? 0x7FF8000000000000LL : __double_as_longlong(l + 0.0);
+        key[t] = b < 0 ? ~(unsigned long long)b : ((unsigned long long)b | 0x8000000000000000ull);
+    }
+    __syncthreads();
     if (blockIdx.x == 0) {
         const unsigned g = *d_gen;
         double* hist = ctl ? ctl->hist : nullptr;
@@ -1227,11 +1304,11 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
         if (t == 0) *d_gen = g + 1;
     }
     if (t < P) {
-        const double lk = loss[(size_t)t * 6];
+        const unsigned long long kk = key[t];
         int rank = 0;
         for (int j = 0; j < P; ++j) {
-            const double lj = loss[(size_t)j * 6];
-            rank += (lj < lk || (lj == lk && j < t)) ? 1 : 0;
+            const unsigned long long kj = key[j];
+            rank += (kj < kk || (kj == kk && j < t)) ? 1 : 0;
         }
         order[rank] = t;
         u[t] = util[t];
@@ -1285,7 +1362,7 @@ bool valid_shape(const nep_dataset* ds, const EvalShape& h)
            (h.discard == 0 || h.discard == 1) && (h.mlp_threads == 128 || h.mlp_threads == 256) &&
            (h.recv_unroll == 1 || h.recv_unroll == 4 || h.recv_unroll == 8 || h.recv_unroll == 12 || h.recv_unroll == 16) &&
            (h.fused == 0 || ((h.fused == 4 || h.fused == 8 || h.fused == 16) && fused_fits(ds, h.fused))) &&
-           (h.owner_tc == 0 || h.owner_tc == 1);
+           (h.owner_tc == 0 || h.owner_tc == 1) && (h.pop_pipe == 0 || h.pop_pipe == 1);
 }
 
 }  // namespace
@@ -1358,6 +1435,8 @@ int ensure_pop(nep_dataset* ds, int P)
     dfree(ds->pbuf);
     dfree(ds->w6);
     dfree(ds->fown);
+    dfree(ds->loss_part);
+    dfree(ds->loss_count);
     ds->pop_cap = 0;
     const int nn = ds->m->hp.n_neu;
     int rc;
@@ -1369,8 +1448,13 @@ int ensure_pop(nep_dataset* ds, int P)
         (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)) ||
         (rc = dalloc(&ds->pbuf, (size_t)ds->n_pairs * 3 * member_stride(P), nullptr)) ||
         (rc = dalloc(&ds->w6, (size_t)ds->N * 6 * member_stride(P), nullptr)) ||
-        (rc = dalloc(&ds->fown, (size_t)ds->N * 3 * member_stride(P), nullptr)))
+        (rc = dalloc(&ds->fown, (size_t)ds->N * 3 * member_stride(P), nullptr)) ||
+        (rc = dalloc(&ds->loss_part, (size_t)P * kLossSplit * 5, nullptr)) ||
+        (rc = dalloc(&ds->loss_count, (size_t)P, nullptr)))
         return rc;
+    // the loss kernel's block counts start at zero (each evaluation clears them again)
+    rc = cuda_fail(cudaMemset(ds->loss_count, 0, sizeof(unsigned) * (size_t)P), "clear loss counts");
+    if (rc) return rc;
     // members past P in the last group of G are never written: keep them zero
     rc = cuda_fail(cudaMemset(ds->G, 0, sizeof(float) * (size_t)ds->N * kNdes * member_stride(P)), "clear G");
     if (rc) return rc;
@@ -1496,16 +1580,17 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
     }
     const int nn = m->hp.n_neu, n_par = m->n_par, Pst = member_stride(P);
     const EvalShape& sh = ds->shape;
-    k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t, ds->b2t);
     int rc;
     if (precision == NEP_PREC_BF16) {
         // G in FP16: the contraction reads half the bytes (the loss terms
         // average its rounding over all force components)
         const int layout = !sh.fused && sh.owner_tc ? kGTilesF16 : kGRowsF16;
-        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, ds->W1t, ds->b1t, ds->w2t, ds->b2t, ds->packed, ds->G,
-                                layout, ds->U, m->d_err, st)))
+        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, z_pop, ds->packed, ds->G, layout, ds->U, m->d_err,
+                                sh.pop_pipe != 0, st)))
             return rc;
     } else {
+        k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t,
+                                                                      ds->b2t);
         const long long pairs = (ds->N + 1) / 2;
         const int mt = sh.mlp_threads == 128 ? 128 : 256;
         k_mlp_f32<<<blocks_for(pairs * P, mt), mt, 0, st>>>(ds->N, P, Pst, nn, ds->q, ds->W1t, ds->b1t, ds->w2t,
@@ -1521,8 +1606,10 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         fused_kernel(gm, gh)<<<ds->S * groups, kFusedThreads, smem, st>>>(
             P, Pst, groups, ds->s_order, ds->sstart, ds->G, ds->U, ds->B, ds->pstart, ds->pj, ds->rec, ds->astart,
             ds->ang, ds->f_tar, ds->partials, m->d_err);
-        k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, nullptr, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
-                                  z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
+        k_loss<<<dim3(P, kLossSplit), kLossThreads, 0, st>>>(P, ds->S, n_par, ds->N, nullptr, ds->s_inv_na,
+                                                             ds->partials, ds->e_tar, ds->w_tar, z_pop, lam[0], lam[1],
+                                                             lam[2], lam[3], lam[4], loss_inv(ds->S, ds->N, n_par),
+                                                             ds->loss_part, ds->loss_count, loss);
         return cuda_fail(cudaGetLastError(), "population evaluation kernels");
     }
     const int C = ds->n_chunks;
@@ -1558,8 +1645,10 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         cudaEventRecord(ds->ev_join, ds->aux);
         cudaStreamWaitEvent(st, ds->ev_join, 0);
     }
-    k_loss<<<P, 256, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_inv_na, ds->partials, ds->e_tar, ds->w_tar,
-                              z_pop, lam[0], lam[1], lam[2], lam[3], lam[4], loss);
+    k_loss<<<dim3(P, kLossSplit), kLossThreads, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_inv_na,
+                                                         ds->partials, ds->e_tar, ds->w_tar, z_pop, lam[0], lam[1],
+                                                         lam[2], lam[3], lam[4], loss_inv(ds->S, ds->N, n_par),
+                                                         ds->loss_part, ds->loss_count, loss);
     return cuda_fail(cudaGetLastError(), "population evaluation kernels");
 }
 
@@ -1877,6 +1966,8 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->pbuf);
     dfree(ds->w6);
     dfree(ds->fown);
+    dfree(ds->loss_part);
+    dfree(ds->loss_count);
     dfree(ds->tiles);
     dfree(ds->apack);
     dfree(ds->rowscale);
@@ -2088,10 +2179,11 @@ int nep_dataset_set_shape(nep_dataset* ds, const int* shape)
     h.recv_unroll = shape[4];
     h.fused = shape[5];
     h.owner_tc = shape[6];
+    h.pop_pipe = shape[7];
     if (!valid_shape(ds, h)) {
         set_error("nep_dataset_set_shape: waves 1..%d, owner warps 4 or 8, discard 0 or 1, network threads 128 or 256, "
                   "receiver unroll 4, 8, 12, 16 (staged) or 1 (bulk copies), fused 0, 4, 8 or 16 members per block (%d atoms x members x "
-                  "48 bytes of shared memory at most %zu), owner_tc 0 or 1",
+                  "48 bytes of shared memory at most %zu), owner_tc 0 or 1, pop_pipe 0 or 1",
                   kMaxWaves, ds->amax, kFusedSmemMax);
         return NEP_ERR_ARG;
     }
@@ -2113,6 +2205,7 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape)
     shape[4] = ds->shape.recv_unroll;
     shape[5] = ds->shape.fused;
     shape[6] = ds->shape.owner_tc;
+    shape[7] = ds->shape.pop_pipe;
     return NEP_OK;
 }
 
@@ -2141,11 +2234,16 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
                         h.discard = dc;
                         h.mlp_threads = mt;
                         h.recv_unroll = ru;
-                        cand.push_back(h);
-                        // BF16: the owner pass on the tensor cores (owner warps do not apply)
-                        if (precision == NEP_PREC_BF16 && ow == 4) {
-                            h.owner_tc = 1;
+                        // BF16: the network as the pipelined persistent kernel or not,
+                        // and the owner pass on the tensor cores (owner warps do not apply)
+                        for (int pp = 0; pp <= (precision == NEP_PREC_BF16 ? 1 : 0); ++pp) {
+                            h.pop_pipe = pp;
+                            h.owner_tc = 0;
                             cand.push_back(h);
+                            if (precision == NEP_PREC_BF16 && ow == 4) {
+                                h.owner_tc = 1;
+                                cand.push_back(h);
+                            }
                         }
                     }
     // the fused contraction: members per block (the atoms per warp follow:
@@ -2156,7 +2254,10 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
             EvalShape h;
             h.mlp_threads = mt;
             h.fused = gm;
-            cand.push_back(h);
+            for (int pp = 0; pp <= (precision == NEP_PREC_BF16 ? 1 : 0); ++pp) {
+                h.pop_pipe = pp;
+                cand.push_back(h);
+            }
         }
     const long long tot = (long long)n_pop * m->n_par;
     float* z = nullptr;

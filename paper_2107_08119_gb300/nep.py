@@ -448,7 +448,7 @@ class Dataset:
         _check(_lib.nep_dataset_descriptors(self._h, _ptr(q), _stream(stream)), "nep_dataset_descriptors")
         return q
 
-    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll", "fused", "owner_tc")
+    SHAPE_KEYS = ("waves", "owner_warps", "discard", "mlp_threads", "recv_unroll", "fused", "owner_tc", "pop_pipe")
 
     def shape(self):
         """Launch shape of the population evaluation (nep_dataset_get_shape)."""

@@ -60,20 +60,22 @@ def _two_pass_shapes(precision, N):
             for dc in ((0, 1) if w > 1 else (0,)):
                 for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
                     for ru in (1, 4, 8, 12, 16):
-                        out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru,
-                                        fused=0, owner_tc=0))
+                        for pp in ((0, 1) if precision == N.PREC_BF16 else (0,)):
+                            out.append(dict(waves=w, owner_warps=ow, discard=dc, mlp_threads=mt, recv_unroll=ru,
+                                            fused=0, owner_tc=0, pop_pipe=pp))
     return out
 
 
 def _tc_shapes():
     """Two-pass shapes with the first pass on the tensor cores (BF16)."""
-    return [dict(waves=w, owner_warps=4, discard=dc, mlp_threads=256, recv_unroll=ru, fused=0, owner_tc=1)
-            for w in (1, 2, 4) for dc in ((0, 1) if w > 1 else (0,)) for ru in (1, 4, 8, 12, 16)]
+    return [dict(waves=w, owner_warps=4, discard=dc, mlp_threads=256, recv_unroll=ru, fused=0, owner_tc=1, pop_pipe=pp)
+            for w in (1, 2, 4) for dc in ((0, 1) if w > 1 else (0,)) for ru in (1, 4, 8, 12, 16) for pp in (0, 1)]
 
 
 def _fused_shapes(precision, N):
-    return [dict(waves=1, owner_warps=4, discard=0, mlp_threads=mt, recv_unroll=4, fused=gm, owner_tc=0)
-            for gm in (4, 8, 16) for mt in ((128, 256) if precision == N.PREC_FP32 else (256,))]
+    return [dict(waves=1, owner_warps=4, discard=0, mlp_threads=mt, recv_unroll=4, fused=gm, owner_tc=0, pop_pipe=pp)
+            for gm in (4, 8, 16) for mt in ((128, 256) if precision == N.PREC_FP32 else (256,))
+            for pp in ((0, 1) if precision == N.PREC_BF16 else (0,))]
 
 
 def _all_shapes(precision, N):
@@ -91,12 +93,14 @@ def test_every_shape_gives_identical_losses(N, full_set, prec):
     model, ds, pop = full_set
     zp = torch.tensor(pop, dtype=torch.float32, device="cuda")
     refs = {}
-    extra = [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8, fused=0, owner_tc=0)]
+    extra = [dict(waves=16, owner_warps=8, discard=1, mlp_threads=128, recv_unroll=8, fused=0, owner_tc=0,
+                  pop_pipe=0)]
     forms = [("fused", _fused_shapes(prec, N))]
     if prec == N.PREC_FP32:
         # owner_tc does not apply in FP32: the same form, the same bits
         forms.append(("two-pass", _two_pass_shapes(prec, N) + extra +
-                      [dict(sh, mlp_threads=256) for sh in _tc_shapes()]))
+                      [dict(sh, mlp_threads=256) for sh in _tc_shapes()] +
+                      [dict(extra[0], pop_pipe=1)]))
     else:
         forms.append(("two-pass", _two_pass_shapes(prec, N) + extra))
         forms.append(("two-pass-tc", _tc_shapes() + [dict(extra[0], owner_tc=1)]))
@@ -144,10 +148,10 @@ def test_autotuner_picks_a_candidate(N, full_set):
 def test_shape_validation(N, full_set):
     model, ds, pop = full_set
     assert ds.default_shape() == dict(waves=1, owner_warps=4, discard=0, mlp_threads=256, recv_unroll=4, fused=8,
-                                      owner_tc=0)
+                                      owner_tc=0, pop_pipe=0)
     for bad in (dict(waves=0), dict(waves=17), dict(owner_warps=6), dict(discard=2), dict(mlp_threads=64),
                 dict(recv_unroll=0), dict(recv_unroll=2), dict(recv_unroll=6), dict(fused=2), dict(fused=32), dict(fused=-4),
-                dict(owner_tc=2), dict(owner_tc=-1)):
+                dict(owner_tc=2), dict(owner_tc=-1), dict(pop_pipe=2), dict(pop_pipe=-1)):
         with pytest.raises(N.NepError) as e:
             ds.set_shape(**bad)
         assert e.value.code == -1  # NEP_ERR_ARG

@@ -59,14 +59,14 @@ def test_bf16_population_losses_track_fp32(N, orc):
     model = N.NEP(teacher.astype(np.float32))
     ds = N.Dataset(model, structures, E, F, W)
     zp = torch.tensor(f32_exact(pop), dtype=torch.float32, device="cuda")
-    for fused, otc in ((8, 0), (0, 0), (0, 1)):
-        ds.set_shape(fused=fused, owner_tc=otc)
+    for fused, otc, pp in ((8, 0, 0), (0, 0, 0), (0, 1, 0), (0, 1, 1)):
+        ds.set_shape(fused=fused, owner_tc=otc, pop_pipe=pp)
         l32 = ds.evaluate(zp, N.PREC_FP32).cpu().numpy()
         l16 = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
         model.sync_status()
         rel = np.abs(l16 - l32) / np.abs(l32)
         for col in range(4):
-            assert rel[:, col].max() <= 1e-3, (fused, otc, col, rel[:, col].max())
+            assert rel[:, col].max() <= 1e-3, (fused, otc, pp, col, rel[:, col].max())
         assert np.array_equal(l16[:, 4:6], l32[:, 4:6])
         assert list(np.argsort(l16[:, 0], kind="stable")) == list(np.argsort(l32[:, 0], kind="stable"))
         # deterministic
