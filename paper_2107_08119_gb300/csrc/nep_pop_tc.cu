@@ -20,6 +20,7 @@
 
 #include "nep_dataset.cuh"
 #include "nep_internal.cuh"
+#include "nep_recv.cuh"
 #include "nep_tc.cuh"
 
 namespace nep {

@@ -38,6 +38,7 @@
 #include <cuda_fp16.h>
 
 #include "nep_dataset.cuh"
+#include "nep_recv.cuh"
 #include "nep_tc.cuh"
 
 namespace nep {
@@ -46,7 +47,6 @@ namespace {
 constexpr int kDsCap = 192;      // neighbour capacity per atom while building (within r_c)
 constexpr int kChunkAtoms = 32;       // atoms per contraction block (chunks never span structures)
 constexpr int kOwnerMaxThreads = 256;  // owner pass: 4 or 8 warps per block, one atom per warp at a time
-constexpr int kMaxPop = 64;
 
 inline int blocks_for(long long n, int t) { return (int)((n + t - 1) / t); }
 
@@ -414,11 +414,6 @@ __device__ __forceinline__ void pb_store2(__half* o, float2 v)
 {
     *reinterpret_cast<__half2*>(o) = __floats2half2_rn(v.x, v.y);
 }
-__device__ __forceinline__ float2 pb_load2(const float* o) { return *reinterpret_cast<const float2*>(o); }
-__device__ __forceinline__ float2 pb_load2(const __half* o)
-{
-    return __half22float2(*reinterpret_cast<const __half2*>(o));
-}
 
 constexpr int kOwnerChunk = 32;                                     // pairs staged per round
 constexpr int kRecFloats = (int)(sizeof(PairRec) / sizeof(float));  // 12
@@ -560,107 +555,6 @@ __global__ void __launch_bounds__(kOwnerMaxThreads) k_contract_owner(
 // L2 lines lying wholly inside them (discard.global.L2: no write-back of data
 // that is dead until the next evaluation rewrites every slot); lines shared
 // with a neighbouring atom's slots are left alone.
-constexpr int kReceiverThreads = 256;
-
-__device__ __forceinline__ void discard_l2_lines(const void* lo, const void* hi, int lane)
-{
-    const uintptr_t a = ((uintptr_t)lo + 127) & ~(uintptr_t)127, b = (uintptr_t)hi & ~(uintptr_t)127;
-    for (uintptr_t l = a + (uintptr_t)lane * 128; l < b; l += 32 * 128)
-        asm volatile("discard.global.L2 [%0], 128;" ::"l"(l) : "memory");
-}
-
-// Per-atom operands of the receiver pass, loaded one atom ahead.
-struct RecvAtom {
-    float2 fo[3];         // G_i . B_i of the lane's two members
-    float2 w6[6];         // owner virial terms
-    double u0, u1;        // site energies
-    float t[3];           // F_tar
-    long long ps, pe;     // slot range
-};
-
-__device__ __forceinline__ void recv_load(RecvAtom& a, int i, int P, int Pst, int k0, bool ld, bool on0, bool on1,
-                                          const double* __restrict__ U, const long long* __restrict__ pstart,
-                                          const float* __restrict__ fown, const float* __restrict__ w6in,
-                                          const float* __restrict__ f_tar)
-{
-    const float* o = fown + (size_t)i * 3 * Pst + k0;
-    const float* w = w6in + (size_t)i * 6 * Pst + k0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a.fo[c] = ld ? *reinterpret_cast<const float2*>(o + (size_t)c * Pst) : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) a.w6[c] = ld ? *reinterpret_cast<const float2*>(w + (size_t)c * Pst) : make_float2(0.f, 0.f);
-    a.u0 = on0 ? U[(size_t)i * P + k0] : 0.0;
-    a.u1 = on1 ? U[(size_t)i * P + k0 + 1] : 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a.t[c] = f_tar[(size_t)i * 3 + c];
-    a.ps = pstart[i];
-    a.pe = pstart[i + 1];
-}
-
-// A warp's running sums over its atoms of one chunk, for the lane's two
-// members: U in FP64 (site energies come as FP64), the squared force
-// residuals and the owner virial terms in FP32 (a warp takes at most
-// kChunkAtoms / 8 = 4 atoms of a chunk; the FP64 pipe is slow on this part, so
-// the per-atom terms stay off it), converted once per chunk to FP64.
-struct RecvAcc {
-    double u[2] = {0.0, 0.0};
-    float f[2] = {0.f, 0.f};
-    float w[2][6] = {{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}};
-    __device__ __forceinline__ void add(const RecvAtom& a, const float (&F)[2][3])
-    {
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            const float dx = F[m][0] - a.t[0], dy = F[m][1] - a.t[1], dz = F[m][2] - a.t[2];
-            u[m] += m == 0 ? a.u0 : a.u1;
-            f[m] += fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-#pragma unroll
-            for (int c = 0; c < 6; ++c) w[m][c] += m == 0 ? a.w6[c].x : a.w6[c].y;
-        }
-    }
-    // the lane's rows of the warp's slice (members past kMaxPop have none)
-    __device__ __forceinline__ void store(double* ru, float (*rf)[7], int k0) const
-    {
-#pragma unroll
-        for (int m = 0; m < 2; ++m) {
-            if (k0 + m >= kMaxPop) continue;
-            ru[k0 + m] = u[m];
-            rf[k0 + m][0] = f[m];
-#pragma unroll
-            for (int c = 0; c < 6; ++c) rf[k0 + m][1 + c] = w[m][c];
-        }
-    }
-};
-
-// Per-warp sums of a receiver block: U in FP64, the other seven terms in FP32.
-template <int W>
-struct RecvRed {
-    double u[W][kMaxPop];
-    float f[W][kMaxPop][7];
-};
-
-// The chunk's partials in a fixed order (warps 0..W-1): U summed in FP64,
-// the squared force residuals and virial terms in FP32 and converted once.
-template <int W>
-__device__ __forceinline__ void recv_chunk_store(const RecvRed<W>& red, int P, double* __restrict__ out)
-{
-    for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
-        const int k = e / 8, w = e % 8;
-        double t;
-        if (w == 0) {
-            double a = 0.0;
-#pragma unroll
-            for (int q = 0; q < W; ++q) a += red.u[q][k];
-            t = a;
-        } else {
-            float a = 0.f;
-#pragma unroll
-            for (int q = 0; q < W; ++q) a += red.f[q][k][w - 1];
-            t = (double)a;
-        }
-        out[(size_t)k * 8 + w] = t;
-    }
-}
-
 template <int UNROLL, class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
     int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
@@ -789,10 +683,6 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
 // copy that does not land latches NEP_ERR_TIMEOUT and the warp stops summing;
 // it then waits (bounded) for its copies still in flight before the block
 // exits, so no copy writes into shared memory another block owns.
-constexpr int kBulkStage = 4096;           // payload bytes of one piece
-constexpr int kBulkBuf = kBulkStage + 32;  // + the rounding at both ends (16-byte multiple)
-constexpr int kBulkSmem = (kReceiverThreads / 32) * 2 * kBulkBuf;
-constexpr uint32_t kBulkPolls = 1u << 22;
 
 template <class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
@@ -801,106 +691,13 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
     const PT* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
     double* __restrict__ partials, unsigned* __restrict__ err)
 {
-    constexpr int kWarps = kReceiverThreads / 32;
-    __shared__ RecvRed<kWarps> red;
-    __shared__ __align__(8) uint64_t bar[kWarps][2];
-    extern __shared__ __align__(128) unsigned char s_bulk[];  // [warps][2][kBulkBuf]
-    const int c = c0 + blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int k0 = 2 * lane;
-    const bool on0 = k0 < P, on1 = k0 + 1 < P;
-    const bool ld = k0 < Pst;
-    const long long slot_bytes = 3LL * Pst * (long long)sizeof(PT);
-    const long long per_piece = kBulkStage / slot_bytes;  // >= 5 slots (Pst <= 64)
-    unsigned char* buf = s_bulk + (size_t)warp * 2 * kBulkBuf;
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(pbuf);
-    RecvAcc acc;
-    if (lane == 0) {
-        tc::mbar_init(&bar[warp][0], 1);
-        tc::mbar_init(&bar[warp][1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    const int end = chunk_end[c];
-    // producer cursor: atom pa, its next slot pp and its slot end pend
-    int pa = chunk_begin[c] + warp;
-    long long pp = 0, pend = 0;
-    if (pa < end) {
-        pp = pstart[pa];
-        pend = pstart[pa + 1];
-    }
-    unsigned n_issued = 0, n_waited = 0;  // piece n: buffer n & 1, barrier phase parity (n >> 1) & 1
-    // requests the next piece of this warp's atoms, if any
-    auto issue = [&]() {
-        while (pa < end && pp >= pend) {
-            pa += kWarps;
-            if (pa < end) {
-                pp = pstart[pa];
-                pend = pstart[pa + 1];
-            }
-        }
-        if (pa >= end) return;
-        const long long q1 = min(pend, pp + per_piece);
-        const size_t b0 = (size_t)(pp * slot_bytes), b1 = (size_t)(q1 * slot_bytes);
-        const size_t a0 = b0 & ~(size_t)15, a1 = (b1 + 15) & ~(size_t)15;
-        const int s = (int)(n_issued & 1u);
-        if (lane == 0) {
-            const uint32_t bb = tc::smem_u32(&bar[warp][s]);
-            // the buffer's previous piece was read by ordinary loads (ordered by the __syncwarp before this call)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"((uint32_t)(a1 - a0))
-                         : "memory");
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                             tc::smem_u32(buf + s * kBulkBuf)),
-                         "l"(src + a0), "r"((uint32_t)(a1 - a0)), "r"(bb)
-                         : "memory");
-        }
-        pp = q1;
-        ++n_issued;
-    };
-    issue();
-    issue();
-    bool ok = true;
-    int i = chunk_begin[c] + warp;
-    RecvAtom cur, nxt;
-    if (i < end) recv_load(cur, i, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
-    for (; ok && i < end; i += kWarps) {
-        if (i + kWarps < end) recv_load(nxt, i + kWarps, P, Pst, k0, ld, on0, on1, U, pstart, fown, w6in, f_tar);
-        float F[2][3] = {{cur.fo[0].x, cur.fo[1].x, cur.fo[2].x}, {cur.fo[0].y, cur.fo[1].y, cur.fo[2].y}};
-        for (long long q0 = cur.ps; q0 < cur.pe; q0 += per_piece) {
-            const long long q1 = min(cur.pe, q0 + per_piece);
-            const int s = (int)(n_waited & 1u);
-            ok = __all_sync(0xffffffffu, tc::mbar_wait(&bar[warp][s], (n_waited >> 1) & 1u, kBulkPolls));
-            if (!ok) break;
-            ++n_waited;
-            const size_t b0 = (size_t)(q0 * slot_bytes);
-            const unsigned char* base = buf + s * kBulkBuf + (b0 - (b0 & ~(size_t)15));
-            if (ld)
-                for (long long q = q0; q < q1; ++q) {
-                    const PT* o = reinterpret_cast<const PT*>(base + (size_t)((q - q0) * slot_bytes)) + k0;
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        const float2 x = pb_load2(o + (size_t)cc * Pst);
-                        F[0][cc] -= x.x;
-                        F[1][cc] -= x.y;
-                    }
-                }
-            __syncwarp();  // every lane has read the buffer before it is refilled
-            issue();
-        }
-        if (!ok) break;
-        acc.add(cur, F);
-        cur = nxt;
-    }
-    if (!ok) {
-        if (lane == 0) atomicOr(err, kErrTimeout);
-        // the copies still in flight land before the block's shared memory goes (bounded)
-        for (; n_waited < n_issued; ++n_waited)
-            tc::mbar_wait(&bar[warp][n_waited & 1u], (n_waited >> 1) & 1u, kBulkPolls);
-    }
-    acc.store(red.u[warp], red.f[warp], k0);
-    __syncthreads();
-    recv_chunk_store(red, P, partials + (size_t)c * P * 8);
+    extern __shared__ __align__(128) unsigned char s_bulk[];
+    BulkSmem& S = *reinterpret_cast<BulkSmem*>(s_bulk);
+    bulk_init(S);
+    BulkWarp bw;
+    if (!bulk_receive_chunk<PT>(c0 + (int)blockIdx.x, P, Pst, chunk_begin, chunk_end, U, pstart, fown, pbuf, w6in,
+                                f_tar, partials, err, false, S, bw))
+        bulk_drain(S, bw);
 }
 
 // Fused contraction: one block per (structure s, group of GM members), the
@@ -1491,9 +1288,9 @@ int prepare_evaluation(nep_dataset* ds, int P)
         (rc = cuda_fail(cudaFuncSetAttribute(k_contract_staged<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              rstage / 2), "contraction shared memory")) ||
         (rc = cuda_fail(cudaFuncSetAttribute(k_contract_bulk<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kBulkSmem), "contraction shared memory")) ||
+                                             (int)sizeof(BulkSmem)), "contraction shared memory")) ||
         (rc = cuda_fail(cudaFuncSetAttribute(k_contract_bulk<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kBulkSmem), "contraction shared memory")))
+                                             (int)sizeof(BulkSmem)), "contraction shared memory")))
         return rc;
     for (int gm = 4; gm <= 16; gm *= 2) {
         if (!fused_fits(ds, gm)) continue;
@@ -1534,7 +1331,7 @@ void launch_contraction_t(const nep_dataset* ds, int P, int Pst, int c_lo, int c
         cudaStreamWaitEvent(p2, ev, 0);
     }
     if (sh.recv_unroll == 1) {
-        k_contract_bulk<PT><<<c_hi - c_lo, kReceiverThreads, kBulkSmem, p2>>>(c_lo, P, Pst, ds->chunk_begin,
+        k_contract_bulk<PT><<<c_hi - c_lo, kReceiverThreads, sizeof(BulkSmem), p2>>>(c_lo, P, Pst, ds->chunk_begin,
                                                                               ds->chunk_end, ds->U, ds->pstart,
                                                                               ds->fown, pbuf, ds->w6, ds->f_tar,
                                                                               ds->partials, ds->m->d_err);

@@ -159,7 +159,8 @@ def test_shape_validation(N, full_set):
 
 
 @pytest.mark.parametrize("shape", [dict(), dict(fused=0, waves=1), dict(fused=0, waves=4, discard=1),
-                                   dict(fused=0, owner_tc=1), dict(fused=0, waves=4, owner_tc=1)])
+                                   dict(fused=0, owner_tc=1), dict(fused=0, waves=4, owner_tc=1),
+                                   dict(fused=0, owner_tc=1, recv_unroll=1, pop_pipe=1)])
 def test_run_equals_steps(N, full_set, shape):
     """Generations from the replayed graph equal eager snes_step calls bit
     for bit, the loss history included, and the two interleave (the fused
