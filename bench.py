@@ -740,16 +740,21 @@ def adjoint_gradients(N, reps: int = 20, warm: int = 3):
             "gradients_timed": reps}
 
 
-def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
+def snes_generations(N, precision: int, gens: int = 20, warm: int = 3, shape=None):
     """SNES on the 200-structure training workload, population 50: one
     generation = draws + population evaluation + update, on the device.  The
-    launch shape is picked by the library's autotuner; the timed loop is
-    snes_run (one captured generation replayed), with the eager snes_step
-    loop timed beside it."""
+    launch shape is picked by the library's autotuner, or given (`shape`, a
+    dict of Dataset.SHAPE_KEYS: profiler captures use a fixed one); the timed
+    loop is snes_run (one captured generation replayed), with the eager
+    snes_step loop timed beside it."""
     import torch
     model, ds, structures, pop = training_set(N)
     info = ds.info()
-    shape, tune_ms = ds.tune(50, precision, reps=3)
+    if shape is None:
+        shape, tune_ms = ds.tune(50, precision, reps=3)
+    else:
+        ds.set_shape(**shape)
+        shape, tune_ms = ds.shape(), None
     snes = N.SNES(model, 50, np.zeros(model.hyper.n_par), np.full(model.hyper.n_par, 0.1), seed=2107081194)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -785,7 +790,7 @@ def snes_generations(N, precision: int, gens: int = 20, warm: int = 3):
 
 SNES_SOURCES = ("paper_2107_08119_gb300/csrc/nep_train.cu", "paper_2107_08119_gb300/csrc/nep_pop_tc.cu",
                 "paper_2107_08119_gb300/csrc/nep_tc.cuh", "paper_2107_08119_gb300/csrc/nep_dataset.cuh",
-                "paper_2107_08119_gb300/csrc/nep_internal.cuh")
+                "paper_2107_08119_gb300/csrc/nep_internal.cuh", "paper_2107_08119_gb300/csrc/nep_recv.cuh")
 SNES_PROFILE = os.path.join(ROOT, "profiles", "snes_generation_dram_200structs.json")
 
 
@@ -857,6 +862,9 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "md", "snes"],
                     help="md: the timed MD steps alone (no e2e, SNES or CPU legs); snes: the SNES legs alone. "
                          "Small single-purpose runs for profiler captures.")
+    ap.add_argument("--snes-shape", default=None,
+                    help="with --only snes: a fixed launch shape as JSON (Dataset.SHAPE_KEYS) instead of the "
+                         "autotuner's, so that profiler captures run one known shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -864,16 +872,16 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.only == "snes":
-        return run_snes_only()
+        return run_snes_only(json.loads(args.snes_shape) if args.snes_shape else None)
     return run_gpu(args, rank, world, local)
 
 
-def run_snes_only():
+def run_snes_only(shape=None):
     import torch  # noqa: F401
     from paper_2107_08119_gb300 import build
     build.build()
     from paper_2107_08119_gb300 import nep as N
-    out = {"fp32": snes_generations(N, N.PREC_FP32), "bf16": snes_generations(N, N.PREC_BF16)}
+    out = {"fp32": snes_generations(N, N.PREC_FP32, shape=shape), "bf16": snes_generations(N, N.PREC_BF16, shape=shape)}
     adj = adjoint_gradients(N)
     print(json.dumps({"snes": out, "adjoint": adj}), flush=True)
     return 0
