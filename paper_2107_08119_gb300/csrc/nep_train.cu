@@ -917,38 +917,59 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(int P, int S, int n_par, 
     const int stride = nq * blockDim.x;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // se, sf, sv, l1, l2
     {
-        // this thread's parameters (a few per member): FP32 sums, one conversion
+        // this thread's parameters (a few per member): loaded together, summed
+        // in order in FP32, one conversion
+        constexpr int kZ = 4;
         float a1 = 0.f, a2 = 0.f;
-        for (int p = q + nq * threadIdx.x; p < n_par; p += stride) {
-            const float zz = z[(size_t)k * n_par + p];
-            a1 += fabsf(zz);
-            a2 = fmaf(zz, zz, a2);
+        for (int p0 = q + nq * threadIdx.x; p0 < n_par; p0 += kZ * stride) {
+            float zz[kZ];
+#pragma unroll
+            for (int u = 0; u < kZ; ++u) {
+                const int p = p0 + u * stride;
+                zz[u] = p < n_par ? z[(size_t)k * n_par + p] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < kZ; ++u) {
+                a1 += fabsf(zz[u]);
+                a2 = fmaf(zz[u], zz[u], a2);
+            }
         }
         acc[3] = (double)a1;
         acc[4] = (double)a2;
     }
     for (int s = q + nq * threadIdx.x; s < S; s += stride) {
-        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        // per-chunk partials, or (s_chunk0 NULL) one partial per structure
+        // the structure's targets and chunk range first (independent loads)
+        const double ia = s_inv_na[s];  // per-atom energies and virials (FP64 division is slow here)
+        const double et = e_tar[s];
+        double wt[6];
+#pragma unroll
+        for (int w = 0; w < 6; ++w) wt[w] = w_tar[(size_t)s * 6 + w];
         const int c1 = s_chunk0 ? s_chunk0[s + 1] : s + 1;
+        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        // per-chunk partials, or (s_chunk0 NULL) one partial per structure:
+        // a record of 8 FP64 values as four 16-byte loads
         for (int c0 = s_chunk0 ? s_chunk0[s] : s; c0 < c1; c0 += kBatch) {
-            double b[kBatch][8];
+            double2 b[kBatch][4];
 #pragma unroll
-            for (int r = 0; r < kBatch; ++r)
+            for (int r = 0; r < kBatch; ++r) {
+                const double2* src = reinterpret_cast<const double2*>(partials + ((size_t)(c0 + r) * P + k) * 8);
 #pragma unroll
-                for (int w = 0; w < 8; ++w) b[r][w] = c0 + r < c1 ? partials[((size_t)(c0 + r) * P + k) * 8 + w] : 0.0;
+                for (int w = 0; w < 4; ++w) b[r][w] = c0 + r < c1 ? src[w] : make_double2(0.0, 0.0);
+            }
 #pragma unroll
             for (int r = 0; r < kBatch; ++r)
                 if (c0 + r < c1)
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) v[w] += b[r][w];
+                    for (int w = 0; w < 4; ++w) {
+                        v[2 * w] += b[r][w].x;
+                        v[2 * w + 1] += b[r][w].y;
+                    }
         }
-        const double inv = s_inv_na[s];  // per-atom energies and virials (FP64 division is slow here)
-        const double de = (v[0] - e_tar[s]) * inv;
+        const double de = (v[0] - et) * ia;
         acc[0] += de * de;
         acc[1] += v[1];
         for (int w = 0; w < 6; ++w) {
-            const double dv = (v[2 + w] - w_tar[(size_t)s * 6 + w]) * inv;
+            const double dv = (v[2 + w] - wt[w]) * ia;
             acc[2] += dv * dv;
         }
     }
@@ -1081,6 +1102,7 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
     __shared__ float u[kMaxPop];
     __shared__ unsigned long long key[kMaxPop];
     const int t = threadIdx.x;
+
     // the members' losses as unsigned keys in the same order as the FP64
     // values (integer compares: FP64 compares are slow on this part); -0 is
     // taken as +0, and a NaN loss ranks after every number
