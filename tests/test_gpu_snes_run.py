@@ -229,3 +229,33 @@ def test_fused_shape_follows_the_largest_structure(N):
     model.sync_status()
     ds.close()
     model.close()
+
+
+@pytest.mark.parametrize("n_pop", [1, 5, 64])
+def test_population_sizes_at_the_edges(N, full_set, n_pop):
+    """One member, a ragged last member group (5 = 4 + 1) and the largest
+    population (64, a full last group and the widest owner-pass MMA): in BF16
+    the pipelined and the one-CTA-per-tile network give the same bits, with
+    the tensor-core owner pass and the bulk receiver too; FP32 and BF16 agree
+    to 1e-3 on every loss term and rank the members alike."""
+    import torch
+    model, ds, pop = full_set
+    z = np.random.default_rng(31 + n_pop).normal(0.0, 0.1, size=(n_pop, 1021))
+    zp = torch.tensor(f32_exact(z), dtype=torch.float32, device="cuda")
+    got = {}
+    for pp in (0, 1):
+        for otc, ru in ((0, 4), (1, 1)):
+            ds.set_shape(fused=0, owner_tc=otc, recv_unroll=ru, pop_pipe=pp)
+            got[(pp, otc)] = ds.evaluate(zp, N.PREC_BF16).cpu().numpy()
+    for otc in (0, 1):
+        assert np.array_equal(got[(0, otc)], got[(1, otc)]), otc
+    ds.set_shape(fused=0)
+    l32 = ds.evaluate(zp, N.PREC_FP32).cpu().numpy()
+    for otc in (0, 1):
+        l16 = got[(1, otc)]
+        assert np.isfinite(l16).all()
+        rel = np.abs(l16[:, :4] - l32[:, :4]) / np.abs(l32[:, :4])
+        assert rel.max() <= 1e-3, (otc, rel.max(axis=0))
+        assert list(np.argsort(l16[:, 0], kind="stable")) == list(np.argsort(l32[:, 0], kind="stable"))
+    ds.set_shape()
+    model.sync_status()
