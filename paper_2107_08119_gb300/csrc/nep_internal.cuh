@@ -2,9 +2,11 @@
 //
 // Data layout in device memory (n atoms, M = neighbour capacity per atom):
 //   positions        FP64 [3][n] (caller) + FP32 hi/lo split xh, xl [n] float4
-//   neighbour list   int32 nbr[M][n] = j | image_code << 24, count[n], and
-//                    an atom-major copy vala[n][M] of the same values
+//   neighbour list   int32 nbr[M][n] = j | image_code << 24, count[n]
 //                    int32 rev[M][n] = slot of i in j's list (reverse pair)
+//                    int32 vala[n][M]: scratch of the list build (the rank of
+//                    each unsorted slot; the values atom-major in the brute
+//                    search)
 //   partial forces   FP32 pf[M][n] float4 (x, y, z, unused) = dU_i/dr_ij
 //                    (Eq. 23), slot-major: one 16-byte gather per reverse pair
 //   forces           FP32 [3][n], per-atom virials FP32 [9][n]
@@ -277,7 +279,7 @@ struct NeighborList {
     int* count = nullptr;
     int* nbr = nullptr;
     int* rev = nullptr;
-    int* vala = nullptr;     // atom-major copy of the list values [n][m_cap]
+    int* vala = nullptr;     // list-build scratch [n][m_cap] (slot ranks, or values atom-major)
     float* pf = nullptr;
     float* xh = nullptr;
     float* xl = nullptr;

@@ -7,16 +7,16 @@
 //   2. exclusive scan of the cell counts and scatter (the order of atoms
 //      within a cell is whatever the atomics give: the list order below
 //      depends only on the sort keys, so it stays deterministic);
-//   3. one warp per atom scans the 27 neighbouring cells and keeps every
-//      (j, image) with |r_ij| below the list radius (full list, both
-//      directions), then orders its slots by increasing distance (the
-//      partial-force buffer is free at this point and holds the sort keys,
-//      atom-major: key[i * m_cap + k]; the values are also kept atom-major
-//      in vala[i * m_cap + k] for the reverse search and the site pass);
-//   4. the reverse-pair index: for slot k of atom i, the slot of i in j's
-//      list, by binary search over j's contiguous keys.
+//   3. every pair within the list radius is tested once, by the atom whose
+//      half shell of cells holds the other, and goes into both atoms' rows
+//      (full list, both directions), unsorted; each row is then ordered by
+//      increasing distance, and the reverse-pair index (for slot k of atom
+//      i, the slot of i in j's list) follows from the partners' ranks
+//      (k_half_cells, k_sort_rows, k_rev_perm below);
 // Boxes with fewer than 3 cells in a direction (small training cells) use a
-// brute-force scan over all atoms and images instead of cells.
+// brute-force scan over all atoms and images, the rows sorted in place
+// (keys atom-major in the partial-force buffer, the values in vala), and
+// the reverse index by binary search over j's keys (k_reverse).
 // Every kernel takes an optional device gate word: when it is zero the kernel
 // returns at once, which lets the MD step skip the rebuild without a host
 // round trip.
@@ -38,12 +38,13 @@ __device__ __forceinline__ bool gated_off(const unsigned* gate)
 // otherwise be binned into a clamped cell and simply see no neighbours.
 __global__ void k_bin(int n, double* __restrict__ pos, const float* __restrict__ zatom, int wrap_in_place,
                       double* __restrict__ x_ref, float* __restrict__ xh, float* __restrict__ xl,
-                      int* __restrict__ atom_cell, int* __restrict__ cell_count, Box b, const unsigned* gate,
-                      unsigned* __restrict__ err)
+                      int* __restrict__ atom_cell, int* __restrict__ cell_count, int* __restrict__ count, Box b,
+                      const unsigned* gate, unsigned* __restrict__ err)
 {
     if (gated_off(gate)) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    count[i] = 0;  // the half-shell search counts each row's entries with atomics
     int c[3];
     double wx[3];
 #pragma unroll
@@ -200,15 +201,8 @@ __device__ void sort_near_first(int i, int n, int m_cap, int cnt, int* __restric
     }
 }
 
-// One warp per atom.  The candidates of the 27 neighbouring cells are
-// numbered consecutively (cell by cell) and the lanes take them 32 at a time
-// (a lane finds its cell by stepping from the round's first cell); a quick
-// test on the hi parts compacts the survivors with a ballot, the exact test
-// then runs on them with every lane busy, and the accepted pairs are sorted
-// by (squared distance, packed index) by ranking and written out.
-// Sorting on the pair of keys makes the order unique, hence deterministic.
+// Warps per block of the warp-per-atom list kernels.
 constexpr int kVerletWarps = 4;
-constexpr int kVerletCellWords = 192;  // per-warp cell tables: prefix, start, code, 3 shifts (32 words each)
 
 // (squared distance, packed index) as one unsigned 64-bit sort key: d2 >= 0,
 // so its IEEE bits order like its value, and the packed index is below 2^31.
@@ -217,15 +211,166 @@ __device__ __forceinline__ unsigned long long sort_key(float d2, int v)
     return ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)v;
 }
 
-// Sorts the warp's accepted entries by their keys and writes the first m of
-// them: lane l ranks the entries c0 + l + 32 t against all ns entries
-// (broadcast shared-memory reads, one 64-bit compare each) and stores each
-// at its rank, slot-major in nbr and atom-major in key / vala.  The pairs are
-// distinct, so the ranks are a permutation.
+// The list in three steps, each pair's distance tested once (the cells path):
+//   k_half_cells  one warp per atom i scans the 14 cells of its half shell
+//                 (cell offsets after (0, 0, 0) in x-slowest order, and its
+//                 own cell for j > i), so that every pair within the list
+//                 radius is met by exactly one of its two atoms; the
+//                 quick hi-part test and the exact hi/lo test as before, and
+//                 each accepted pair goes into both rows unsorted at slots
+//                 taken with atomics: (value, distance word, the partner
+//                 entry's slot).  The rows live in the partial-force buffer,
+//                 four words per slot.
+//   k_sort_rows   one warp per atom ranks its row by (squared distance,
+//                 value), which is unique, and writes the sorted values
+//                 (slot-major nbr), the rank of every unsorted slot (vala),
+//                 and into the fourth word of each partner entry the rank it
+//                 got here: the partner's reverse index.
+//   k_rev_perm    rev[rank of slot s][i] = the fourth word of i's slot s,
+//                 within each row.
+// The pair vector is computed once per pair in the canonical orientation, so
+// the rows and the reverse index are the same as those of the full-shell
+// search (the order of the unsorted slots, which the atomics decide, does
+// not reach the results).  The counts are cleared by k_bin.
+constexpr int kHalfCells = 14;
+
+__global__ void __launch_bounds__(32 * kVerletWarps) k_half_cells(int n, int m_cap, float rv2,
+                                                                 const float* __restrict__ xh,
+                                                                 const float* __restrict__ xl,
+                                                                 const int* __restrict__ atom_cell,
+                                                                 const int* __restrict__ cell_start,
+                                                                 const int* __restrict__ cell_atoms,
+                                                                 int* __restrict__ count, int* __restrict__ rows,
+                                                                 int lcap, unsigned* err, Box b, const unsigned* gate)
+{
+    if (gated_off(gate)) return;
+    extern __shared__ int s_half[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // per warp: lcap quick-test survivors, 15 prefix sums, 14 starts, codes, shifts
+    int* sq = s_half + (size_t)warp * (lcap + 6 * 32);
+    int* pre = sq + lcap;
+    int* cst = pre + 32;
+    int* ccode = cst + 32;
+    float* csh = reinterpret_cast<float*>(ccode + 32);
+    const float rq = sqrtf(rv2) + 1e-3f, rq2 = rq * rq;
+    for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += gridDim.x * kVerletWarps) {
+        float hi[3], li[3];
+        load_pos(xh, xl, n, i, hi, li);
+        const int cid = atom_cell[i];
+        const int cz = cid % b.nc[2];
+        const int cy = (cid / b.nc[2]) % b.nc[1];
+        const int cx = cid / (b.nc[2] * b.nc[1]);
+        // lane c < 14 describes half-shell cell c: offset index 13 + c of the
+        // 27 in x-slowest order (13 is the atom's own cell)
+        int ccount = 0;
+        if (lane < kHalfCells) {
+            const int o = 13 + lane;
+            int x2 = cx + o / 9 - 1, y2 = cy + (o / 3) % 3 - 1, z2 = cz + o % 3 - 1;
+            int sx = 0, sy = 0, sz = 0;
+            if (x2 < 0) { x2 += b.nc[0]; sx = -1; } else if (x2 >= b.nc[0]) { x2 -= b.nc[0]; sx = 1; }
+            if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
+            if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
+            const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
+            const int c2s = cell_start[c2];
+            ccount = cell_start[c2 + 1] - c2s;
+            cst[lane] = c2s;
+            ccode[lane] = image_code(sx, sy, sz);
+            csh[lane] = (float)sx * b.Lh[0];  // exact: s in {-1, 0, 1}
+            csh[32 + lane] = (float)sy * b.Lh[1];
+            csh[64 + lane] = (float)sz * b.Lh[2];
+        }
+        int incl = ccount;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane <= kHalfCells) pre[lane] = incl - ccount;
+        if (lane < kHalfCells) cst[lane] -= incl - ccount;
+        __syncwarp();
+        const int total = pre[kHalfCells];
+        // pass 1, quick rejection with the hi parts only: their pair vector is
+        // within 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a
+        // pair that the exact test keeps; survivors are compacted into sq
+        int nq = 0, c0 = 0;
+        for (int base = 0; base < total; base += 32) {
+            const int idx = base + lane;
+            bool pass = false;
+            int value = 0;
+            int c = c0;
+            if (idx < total) {
+                while (pre[c + 1] <= idx) ++c;
+                const int j = cell_atoms[cst[c] + idx];
+                // own cell (c == 0): the pairs with j > i only
+                if (c != 0 || j > i) {
+                    const float4 a = NEP_LDG(reinterpret_cast<const float4*>(xh) + j);
+                    const float qx = (a.x - hi[0]) + csh[c];
+                    const float qy = (a.y - hi[1]) + csh[32 + c];
+                    const float qz = (a.z - hi[2]) + csh[64 + c];
+                    pass = j != i && fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2;
+                    value = j | (ccode[c] << 24);
+                }
+            }
+            c0 = __shfl_sync(0xffffffffu, c, 31);
+            const unsigned mask = __ballot_sync(0xffffffffu, pass);
+            const int pos = nq + __popc(mask & ((1u << lane) - 1u));
+            if (pass && pos < lcap) sq[pos] = value;
+            nq += __popc(mask);
+        }
+        __syncwarp();
+        if (nq > lcap && lane == 0) atomicOr(err, kErrOverflow);
+        // pass 2: the exact test; an accepted pair takes a slot in i's row
+        // (one atomic per warp round) and one in j's row
+        const int nqs = nq < lcap ? nq : lcap;
+        for (int base = 0; base < nqs; base += 32) {
+            const int e = base + lane;
+            bool accept = false;
+            int value = 0, j = 0;
+            float d2 = 0.f;
+            if (e < nqs) {
+                value = sq[e];
+                j = value & 0xFFFFFF;
+                float hj[3], lj[3];
+                load_pos(xh, xl, n, j, hj, lj);
+                float rx, ry, rz;
+                pair_vector(i, j, value >> 24, hi, li, hj, lj, b, rx, ry, rz);
+                d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                accept = d2 < rv2;
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, accept);
+            int si0 = 0;
+            if (lane == 0 && mask) si0 = atomicAdd(count + i, __popc(mask));
+            si0 = __shfl_sync(0xffffffffu, si0, 0);
+            if (accept) {
+                const int si = si0 + __popc(mask & ((1u << lane) - 1u));
+                const int sj = atomicAdd(count + j, 1);
+                const int vj = i | ((124 - (value >> 24)) << 24);  // the reverse image
+                if (si < m_cap) {
+                    int* ri = rows + ((size_t)i * m_cap + si) * 4;
+                    ri[0] = value;
+                    ri[1] = (int)__float_as_uint(d2);
+                    ri[2] = sj;
+                }
+                if (sj < m_cap) {
+                    int* rj = rows + ((size_t)j * m_cap + sj) * 4;
+                    rj[0] = vj;
+                    rj[1] = (int)__float_as_uint(d2);
+                    rj[2] = si;
+                }
+            }
+        }
+        __syncwarp();  // the warp's buffers are reused by its next atom
+    }
+}
+
+// Ranks a warp's row entries c0 + lane + 32 t against all ns (keys in sk)
+// and writes each at its rank: the value to nbr (slot-major), the rank to
+// inv[i][unsorted slot] and to the fourth word of the partner entry (the
+// partner's reverse index; j's slot sp[e] of the atom in the value).
 template <int EPL>
-__device__ __forceinline__ void rank_sort_write(int c0, int ns, int m, int lane, const unsigned long long* sk, int i,
-                                                int n, int m_cap, int* __restrict__ nbr, float* __restrict__ key,
-                                                int* __restrict__ vala)
+__device__ __forceinline__ void rank_rows_write(int c0, int ns, int m, int lane, const unsigned long long* sk,
+                                                const int* sp, int i, int n, int m_cap, int* __restrict__ nbr,
+                                                int* __restrict__ rows, int* __restrict__ inv)
 {
     unsigned long long ke[EPL];
     int rk[EPL];
@@ -243,140 +388,69 @@ __device__ __forceinline__ void rank_sort_write(int c0, int ns, int m, int lane,
 #pragma unroll
     for (int t = 0; t < EPL; ++t) {
         const int e = c0 + lane + 32 * t;
-        if (e < ns && rk[t] < m) {
+        if (e < ns) {
             const int v = (int)(unsigned)ke[t];
+            inv[(size_t)i * m_cap + e] = rk[t];
             nbr[(size_t)rk[t] * n + i] = v;
-            key[(size_t)i * m_cap + rk[t]] = __uint_as_float((unsigned)(ke[t] >> 32));
-            vala[(size_t)i * m_cap + rk[t]] = v;
+            const int ps = sp[e];
+            if (ps < m_cap) rows[((size_t)(v & 0xFFFFFF) * m_cap + ps) * 4 + 3] = rk[t];
         }
     }
 }
 
-__global__ void __launch_bounds__(32 * kVerletWarps) k_verlet_cells(int n, int m_cap, int lcap, float rv2,
-                                                                   const float* __restrict__ xh,
-                                                                   const float* __restrict__ xl,
-                                                                   const int* __restrict__ atom_cell,
-                                                                   const int* __restrict__ cell_start,
-                                                                   const int* __restrict__ cell_atoms,
-                                                                   int* __restrict__ count, int* __restrict__ nbr,
-                                                                   float* __restrict__ key, int* __restrict__ vala,
-                                                                   unsigned* err, Box b, const unsigned* gate)
+__global__ void __launch_bounds__(32 * kVerletWarps) k_sort_rows(int n, int m_cap, int lcap, int* __restrict__ rows,
+                                                                const int* __restrict__ count, int* __restrict__ nbr,
+                                                                int* __restrict__ inv, unsigned* err,
+                                                                const unsigned* gate)
 {
     if (gated_off(gate)) return;
-    extern __shared__ float s_raw[];
+    extern __shared__ unsigned long long s_sort[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per warp: lcap sort keys, lcap quick-test survivors, 28 prefix sums,
-    // 27 starts, 27 codes, 27 image shifts (x, y, z)
-    unsigned long long* sk = reinterpret_cast<unsigned long long*>(s_raw + (size_t)warp * (3 * lcap + kVerletCellWords));
-    int* sq = reinterpret_cast<int*>(sk + lcap);
-    int* pre = sq + lcap;
-    int* cst = pre + 32;
-    int* ccode = cst + 32;
-    float* csh = reinterpret_cast<float*>(ccode + 32);
-    // a bounded grid strides over the atoms, so a gated-off launch is cheap
+    unsigned long long* sk = s_sort + (size_t)warp * lcap * 3 / 2;  // lcap keys, then lcap partner slots
+    int* sp = reinterpret_cast<int*>(sk + lcap);
     for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += gridDim.x * kVerletWarps) {
-        float hi[3], li[3];
-        load_pos(xh, xl, n, i, hi, li);
-        const int cid = atom_cell[i];
-        const int cz = cid % b.nc[2];
-        const int cy = (cid / b.nc[2]) % b.nc[1];
-        const int cx = cid / (b.nc[2] * b.nc[1]);
-        // lane c < 27 describes neighbouring cell c (x slowest, z fastest)
-        int ccount = 0;
-        if (lane < 27) {
-            int x2 = cx + lane / 9 - 1, y2 = cy + (lane / 3) % 3 - 1, z2 = cz + lane % 3 - 1;
-            int sx = 0, sy = 0, sz = 0;
-            if (x2 < 0) { x2 += b.nc[0]; sx = -1; } else if (x2 >= b.nc[0]) { x2 -= b.nc[0]; sx = 1; }
-            if (y2 < 0) { y2 += b.nc[1]; sy = -1; } else if (y2 >= b.nc[1]) { y2 -= b.nc[1]; sy = 1; }
-            if (z2 < 0) { z2 += b.nc[2]; sz = -1; } else if (z2 >= b.nc[2]) { z2 -= b.nc[2]; sz = 1; }
-            const int c2 = (x2 * b.nc[1] + y2) * b.nc[2] + z2;
-            const int c2s = cell_start[c2];
-            ccount = cell_start[c2 + 1] - c2s;
-            cst[lane] = c2s;
-            ccode[lane] = image_code(sx, sy, sz);
-            csh[lane] = (float)sx * b.Lh[0];  // exact: s in {-1, 0, 1}
-            csh[32 + lane] = (float)sy * b.Lh[1];
-            csh[64 + lane] = (float)sz * b.Lh[2];
-        }
-        // exclusive prefix of the cell sizes
-        int incl = ccount;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane < 28) pre[lane] = incl - ccount;
-        if (lane < 27) cst[lane] -= incl - ccount;  // candidate idx of cell c sits at cell_atoms[cst[c] + idx]
-        __syncwarp();
-        const int total = pre[27];
-        // Pass 1, quick rejection with the hi parts only: their pair vector is
-        // within 1e-4 A of the hi/lo one, so the 1e-3 A margin never drops a
-        // pair that the exact test keeps.  Survivors are compacted into sq.
-        const float rq = sqrtf(rv2) + 1e-3f, rq2 = rq * rq;
-        int nq = 0;
-        int c0 = 0;  // cell of this round's first candidate (warp-uniform)
-        for (int base = 0; base < total; base += 32) {
-            const int idx = base + lane;
-            bool pass = false;
-            int value = 0;
-            int c = c0;
-            if (idx < total) {
-                while (pre[c + 1] <= idx) ++c;  // a cell holds ~12 atoms: 0-3 steps
-                const int j = cell_atoms[cst[c] + idx];
-                const int code = ccode[c];
-                if (!(j == i && code == kImgCenter)) {
-                    const float4 a = NEP_LDG(reinterpret_cast<const float4*>(xh) + j);
-                    const float qx = (a.x - hi[0]) + csh[c];
-                    const float qy = (a.y - hi[1]) + csh[32 + c];
-                    const float qz = (a.z - hi[2]) + csh[64 + c];
-                    pass = fmaf(qx, qx, fmaf(qy, qy, qz * qz)) < rq2;
-                    value = j | (code << 24);
-                }
-            }
-            c0 = __shfl_sync(0xffffffffu, c, 31);
-            const unsigned mask = __ballot_sync(0xffffffffu, pass);
-            const int pos = nq + __popc(mask & ((1u << lane) - 1u));
-            if (pass && pos < lcap) sq[pos] = value;
-            nq += __popc(mask);
-        }
-        __syncwarp();
-        if (nq > lcap && lane == 0) atomicOr(err, kErrOverflow);
-        // Pass 2, the exact (canonical hi/lo) test on the survivors, every
-        // lane busy; accepted pairs are compacted into sk as sort keys.
-        const int nqs = nq < lcap ? nq : lcap;
-        int cnt = 0;
-        for (int base = 0; base < nqs; base += 32) {
-            const int e = base + lane;
-            bool accept = false;
-            int value = 0;
-            float d2 = 0.f;
-            if (e < nqs) {
-                value = sq[e];
-                const int j = value & 0xFFFFFF;
-                float hj[3], lj[3];
-                load_pos(xh, xl, n, j, hj, lj);
-                float rx, ry, rz;
-                pair_vector(i, j, value >> 24, hi, li, hj, lj, b, rx, ry, rz);
-                d2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                accept = d2 < rv2;
-            }
-            const unsigned mask = __ballot_sync(0xffffffffu, accept);
-            const int pos = cnt + __popc(mask & ((1u << lane) - 1u));
-            if (accept) sk[pos] = sort_key(d2, value);  // pos < nqs <= lcap
-            cnt += __popc(mask);
-        }
-        __syncwarp();
-        if (lane == 0) count[i] = cnt;
+        const int cnt = count[i];
         if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
         const int m = cnt < m_cap ? cnt : m_cap;
-        const int ns = cnt < lcap ? cnt : lcap;
+        const int ns = m < lcap ? m : lcap;
+        for (int e = lane; e < ns; e += 32) {
+            const int4 r = *reinterpret_cast<const int4*>(rows + ((size_t)i * m_cap + e) * 4);
+            sk[e] = sort_key(__int_as_float(r.y), r.x);
+            sp[e] = r.z;
+        }
+        __syncwarp();
         if (ns <= 32)
-            rank_sort_write<1>(0, ns, m, lane, sk, i, n, m_cap, nbr, key, vala);
+            rank_rows_write<1>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
         else if (ns <= 64)
-            rank_sort_write<2>(0, ns, m, lane, sk, i, n, m_cap, nbr, key, vala);
+            rank_rows_write<2>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
         else
-            for (int c0 = 0; c0 < ns; c0 += 128) rank_sort_write<4>(c0, ns, m, lane, sk, i, n, m_cap, nbr, key, vala);
-        __syncwarp();  // the warp's buffers are reused by its next atom
+            for (int c0 = 0; c0 < ns; c0 += 128)
+                rank_rows_write<4>(c0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
+        __syncwarp();
+    }
+}
+
+// rev[inv[i][s]][i] = the reverse index left in the fourth word of i's
+// unsorted slot s by the partner's sort; one warp per atom.  A value outside
+// the partner's kept entries (only after an overflow, already latched) is
+// latched again and replaced by the slot's own rank.
+__global__ void k_rev_perm(int n, int m_cap, const int* __restrict__ count, const int* __restrict__ rows,
+                           const int* __restrict__ inv, int* __restrict__ rev, unsigned* err, const unsigned* gate)
+{
+    if (gated_off(gate)) return;
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)(((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < n; i += warps) {
+        const int ci = min(count[i], m_cap);
+        for (int s = lane; s < ci; s += 32) {
+            const int r = inv[(size_t)i * m_cap + s];
+            int v = rows[((size_t)i * m_cap + s) * 4 + 3];
+            if (v < 0 || v >= m_cap) {
+                atomicOr(err, kErrReverse);
+                v = r;
+            }
+            rev[(size_t)r * n + i] = v;
+        }
     }
 }
 
@@ -473,18 +547,24 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, cons
     const bool cells = b.nc[0] > 0;
     const int ncell = cells ? b.nc[0] * b.nc[1] * b.nc[2] : 0;
     k_bin<<<blocks_for(n, T), T, 0, st>>>(n, pos, zatom, wrap_in_place ? 1 : 0, x_ref, nl.xh, nl.xl, nl.atom_cell,
-                                          nl.cell_count, b, d_gate, d_err);
+                                          nl.cell_count, nl.count, b, d_gate, d_err);
     if (cells) {
         k_scan<<<1, kScanThreads, 0, st>>>(ncell, nl.cell_count, nl.cell_start, nl.cell_fill, d_gate);
         k_scatter<<<blocks_for(n, T), T, 0, st>>>(n, nl.atom_cell, nl.cell_start, nl.cell_fill, nl.cell_atoms,
                                                   d_gate);
-        // per-warp list buffer: a power of two >= m_cap entries of (key, value)
+        // per-warp buffers: a power of two >= m_cap entries
         int lcap = 32;
         while (lcap < nl.m_cap) lcap <<= 1;
-        const size_t smem = (size_t)kVerletWarps * (3 * lcap + kVerletCellWords) * sizeof(float);
-        k_verlet_cells<<<std::min(blocks_for(n, kVerletWarps), kListGridCap), 32 * kVerletWarps, smem, st>>>(
-            n, nl.m_cap, lcap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, nl.nbr, nl.pf,
-            nl.vala, d_err, b, d_gate);
+        const int grid = std::min(blocks_for(n, kVerletWarps), kListGridCap);
+        int* rows = reinterpret_cast<int*>(nl.pf);  // four words per slot, free until the site pass
+        k_half_cells<<<grid, 32 * kVerletWarps, (size_t)kVerletWarps * (lcap + 6 * 32) * sizeof(int), st>>>(
+            n, nl.m_cap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, rows, lcap, d_err, b,
+            d_gate);
+        k_sort_rows<<<grid, 32 * kVerletWarps, (size_t)kVerletWarps * lcap * 12, st>>>(
+            n, nl.m_cap, lcap, rows, nl.count, nl.nbr, nl.vala, d_err, d_gate);
+        k_rev_perm<<<std::min(blocks_for(n, 4), kListGridCap), 128, 0, st>>>(n, nl.m_cap, nl.count, rows, nl.vala,
+                                                                              nl.rev, d_err, d_gate);
+        return cuda_fail(cudaGetLastError(), "neighbour-list kernels");
     } else {
         k_verlet_brute<<<blocks_for(n, 128), 128, 0, st>>>(n, nl.m_cap, rv2, nl.xh, nl.xl, nl.count, nl.nbr, nl.pf,
                                                            nl.vala, d_err, b, d_gate);
