@@ -408,17 +408,42 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_sort_rows(int n, int m_ca
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* sk = s_sort + (size_t)warp * lcap * 3 / 2;  // lcap keys, then lcap partner slots
     int* sp = reinterpret_cast<int*>(sk + lcap);
-    for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += gridDim.x * kVerletWarps) {
-        const int cnt = count[i];
+    // a lane's entries of the next atom's row (e = lane + 32 t), loaded while
+    // the current row is sorted
+    constexpr int kPre = 4;  // 128 entries per row at most
+    int4 pre[kPre];
+    int pre_cnt = 0;
+    const int stride = gridDim.x * kVerletWarps;
+    auto fetch = [&](int a) {
+        pre_cnt = a < n ? count[a] : 0;
+        const int ns_a = min(min(pre_cnt, m_cap), lcap);
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) {
+            const int e = lane + 32 * t;
+            if (e < ns_a) pre[t] = *reinterpret_cast<const int4*>(rows + ((size_t)a * m_cap + e) * 4);
+        }
+    };
+    fetch(blockIdx.x * kVerletWarps + warp);
+    for (int i = blockIdx.x * kVerletWarps + warp; i < n; i += stride) {
+        const int cnt = pre_cnt;
         if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
         const int m = cnt < m_cap ? cnt : m_cap;
         const int ns = m < lcap ? m : lcap;
-        for (int e = lane; e < ns; e += 32) {
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) {
+            const int e = lane + 32 * t;
+            if (e < ns) {
+                sk[e] = sort_key(__int_as_float(pre[t].y), pre[t].x);
+                sp[e] = pre[t].z;
+            }
+        }
+        for (int e = 32 * kPre + lane; e < ns; e += 32) {  // rows longer than the prefetch (m_cap > 128)
             const int4 r = *reinterpret_cast<const int4*>(rows + ((size_t)i * m_cap + e) * 4);
             sk[e] = sort_key(__int_as_float(r.y), r.x);
             sp[e] = r.z;
         }
         __syncwarp();
+        fetch(i + stride);
         if (ns <= 32)
             rank_rows_write<1>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
         else if (ns <= 64)
