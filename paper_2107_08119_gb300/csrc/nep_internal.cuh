@@ -394,11 +394,18 @@ int launch_pack_q_tc(int N, const float* q, unsigned char* qpack, cudaStream_t s
 //              as rows of a K-major [8 ceil(Pst / 8)] x 32 FP16 tile
 //              (owner_tc_g_bytes(Pst) bytes per atom, nep_tc.cuh layout).
 enum GLayout { kGRowsF32 = 0, kGRowsF16 = 1, kGTilesF16 = 2 };
-// z: the population [P][n_par] (packed into the group records by the launch)
+// z: the population [P][n_par] (packed into the group records by the launch),
+// or NULL when `packed` already holds it (launch_pack_tc_draw)
 // pipelined: the persistent warp-specialised kernel (same bits), else one CTA
 // per (member group, 128-atom tile)
 int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, const float* z, unsigned char* packed,
                   void* G, int g_layout, double* U, unsigned* err, bool pipelined, cudaStream_t st);
+// An SNES generation's draws and population packed in one launch: r [P][n_par]
+// the standard normals of generation *d_gen (the stream of nep_philox.cuh),
+// z = m + s (.) r, and the group records of z, with the same bits as the draw
+// kernel followed by the packing of launch_pop_tc.
+int launch_pack_tc_draw(int P, int n_neu, unsigned long long seed, const unsigned* d_gen, const float* m,
+                        const float* s, float* r, float* z, unsigned char* packed, cudaStream_t st);
 
 // The first contraction pass on the tensor cores (BF16 precision mode).  A
 // tile is up to 128 rows of one owner atom j: three per pair (the Jacobian

@@ -20,6 +20,7 @@
 
 #include "nep_dataset.cuh"
 #include "nep_internal.cuh"
+#include "nep_philox.cuh"
 #include "nep_recv.cuh"
 #include "nep_tc.cuh"
 
@@ -182,21 +183,40 @@ __global__ void k_pack_q_tc(int N, int tiles, const float* __restrict__ q, unsig
 }
 
 // One thread per (group, element) of the packed records, read straight from
-// the population z [P][n_par] (layout w1 [n_neu][32], b1, w2, b2 per member).
-__global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigned char* __restrict__ packed)
+// the population z [P][n_par] (layout w1 [n_neu][32], b1, w2, b2 per member),
+// or (kDraw, an SNES generation) drawn while packing: element e = k n_par + p
+// of the generation's normals r (nep_philox.cuh), z = m + s r, each stored by
+// the one thread whose record entry owns the element (a W1 weight appears in
+// both GEMM operands and is drawn twice, with the same bits).
+template <bool kDraw>
+__global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigned char* __restrict__ packed,
+                          unsigned long long seed, const unsigned* __restrict__ d_gen, const float* __restrict__ mv,
+                          const float* __restrict__ sv, float* __restrict__ r_out, float* __restrict__ z_out)
 {
     const int n_par = (kNdes + 2) * n_neu + 1;
     const int groups = (P + kTcGroup - 1) / kTcGroup;
     const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;  // w1 elems, w1t elems, bias rows
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= groups * per) return;
+    const unsigned gen = kDraw ? *d_gen : 0u;
+    auto val = [&](int k, int p, bool own) -> float {
+        const long long el = (long long)k * n_par + p;
+        if (!kDraw) return z[el];
+        const float g = normal_at(el, gen, seed);
+        const float v = fmaf(sv[p], g, mv[p]);
+        if (own) {
+            r_out[el] = g;
+            z_out[el] = v;
+        }
+        return v;
+    };
     const int g = e / per, r = e % per, k0 = g * kTcGroup;
     const int mg = min(kTcGroup, P - k0);
     unsigned char* rec = packed + (size_t)g * kGroupBytes;
     if (r < kTile * 32) {  // GEMM-1 B row = 32 m + mu, column nu
         const int row = r / 32, nu = r % 32, m = row / 32, mu = row % 32;
         const bool on = m < mg && mu < n_neu;
-        put_split(rec, rec + kW1Bytes, row, nu, on ? z[(size_t)(k0 + m) * n_par + mu * kNdes + nu] : 0.f);
+        put_split(rec, rec + kW1Bytes, row, nu, on ? val(k0 + m, mu * kNdes + nu, true) : 0.f);
         return;
     }
     int t = r - kTile * 32;
@@ -204,17 +224,16 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigne
         const int m = t / 1024, nu = (t / 32) % 32, mu = t % 32;
         const bool on = m < mg && mu < n_neu;
         unsigned char* hi = rec + 2 * kW1Bytes + m * kW1tBytes;
-        put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, on ? z[(size_t)(k0 + m) * n_par + mu * kNdes + nu] : 0.f);
+        put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, on ? val(k0 + m, mu * kNdes + nu, false) : 0.f);
         return;
     }
     t -= kTcGroup * 32 * 32;
     float* fb = reinterpret_cast<float*>(rec + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
     const int m = t / 32, mu = t % 32;
     const bool on = m < mg && mu < n_neu;
-    const float* zk = z + (size_t)(k0 + m) * n_par;
-    fb[m * 32 + mu] = on ? zk[n_neu * kNdes + mu] : 0.f;
-    fb[kTcGroup * 32 + m * 32 + mu] = on ? zk[n_neu * kNdes + n_neu + mu] : 0.f;
-    if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? zk[n_neu * (kNdes + 2)] : 0.f;
+    fb[m * 32 + mu] = on ? val(k0 + m, n_neu * kNdes + mu, true) : 0.f;
+    fb[kTcGroup * 32 + m * 32 + mu] = on ? val(k0 + m, n_neu * kNdes + n_neu + mu, true) : 0.f;
+    if (mu == 0) fb[2 * kTcGroup * 32 + m] = m < mg ? val(k0 + m, n_neu * (kNdes + 2), true) : 0.f;
 }
 
 // Issue the split-BF16 products of one K = 32 tile pair into d_tmem:
@@ -998,8 +1017,11 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, 
         return NEP_ERR_UNSUPPORTED;
     }
     const int groups = (P + kTcGroup - 1) / kTcGroup;
-    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
-    k_pack_tc<<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, z, packed);
+    if (z) {
+        const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
+        k_pack_tc<false><<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, z, packed, 0ull, nullptr, nullptr,
+                                                                     nullptr, nullptr, nullptr);
+    }
     const int tiles = (N + kTile - 1) / kTile;
     if (pipelined && g_layout != kGRowsF32) {
         // one CTA per SM, each keeping one member group's record: as many
@@ -1017,6 +1039,19 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, 
                                        : (g_layout == kGRowsF16 ? k_pop_tc<kGRowsF16> : k_pop_tc<kGRowsF32>);
     kern<<<dim3(groups, tiles), kPopThreads, smem, st>>>(N, P, Pst, qpack, packed, G, U, err);
     return cuda_fail(cudaGetLastError(), "population tensor-core kernel");
+}
+
+int launch_pack_tc_draw(int P, int n_neu, unsigned long long seed, const unsigned* d_gen, const float* m,
+                        const float* s, float* r, float* z, unsigned char* packed, cudaStream_t st)
+{
+    if (n_neu > 32) {
+        set_error("tensor-core population path needs n_neu <= 32");
+        return NEP_ERR_UNSUPPORTED;
+    }
+    const int groups = (P + kTcGroup - 1) / kTcGroup;
+    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
+    k_pack_tc<true><<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, nullptr, packed, seed, d_gen, m, s, r, z);
+    return cuda_fail(cudaGetLastError(), "draw and pack the population");
 }
 
 int launch_pack_owner_tc(int n_tiles, const OwnerTile* tiles, const PairRec* rec, const long long* aidx,

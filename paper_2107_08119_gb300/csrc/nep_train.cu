@@ -27,7 +27,8 @@
 //               U and W summed per chunk of 32 atoms (k_contract_bulk: the
 //               same, the slot rows arriving by bulk copies)
 //   k_loss      per member: per-structure sums in a fixed order, RMSEs
-// SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r), k_snes_update.
+// SNES (Eqs. 35-39): k_gauss (Philox4x32-10 normals, z = m + s r; in BF16
+// mode the packing kernel draws them itself), k_snes_update.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -38,6 +39,7 @@
 #include <cuda_fp16.h>
 
 #include "nep_dataset.cuh"
+#include "nep_philox.cuh"
 #include "nep_recv.cuh"
 #include "nep_tc.cuh"
 
@@ -1004,27 +1006,6 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(int P, int S, int n_par, 
 }
 
 // ------------------------------------------------------------------ SNES
-// Philox4x32-10 (Salmon et al., SC'11) from its published definition.
-__device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1,
-                                       uint32_t (&o)[4])
-{
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-        c0 = n0;
-        c1 = lo1;
-        c2 = n2;
-        c3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = c0;
-    o[1] = c1;
-    o[2] = c2;
-    o[3] = c3;
-}
-
 // Standard normals for elements e = 0..count-1 of stream (seed, gen): block
 // e/4 uses counter {e/4, 0, gen, 0x4E4550} and key {seed lo, seed hi};
 // u = (w + 1/2) 2^-32; lanes 0/1 (2/3) are the Box-Muller pair of (u0, u1)
@@ -1035,24 +1016,11 @@ __global__ void k_gauss(long long count, int n_par, unsigned long long seed, con
 {
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (4 * b >= count) return;
-    const unsigned gen = *d_gen;
     uint32_t w[4];
-    philox((uint32_t)b, 0u, gen, 0x4E4550u, (uint32_t)seed, (uint32_t)(seed >> 32), w);
+    philox_block(b, *d_gen, seed, w);
     float g[4];
-    for (int pr = 0; pr < 2; ++pr) {
-        // u = (w + 1/2) 2^-32 and 1 - u are exact in FP64; Box-Muller in FP32
-        // (FP64 transcendentals are slow on this part) with ln u taken as
-        // log1p(-(1 - u)) when u is near 1, so that the radius keeps full
-        // relative precision where ln u is tiny
-        const double u0 = ((double)w[2 * pr] + 0.5) * (1.0 / 4294967296.0);
-        const double u1 = ((double)w[2 * pr + 1] + 0.5) * (1.0 / 4294967296.0);
-        const float lu = u0 < 0.5 ? logf((float)u0) : log1pf(-(float)(1.0 - u0));
-        const float rad = sqrtf(-2.f * lu);
-        float sn, cs;
-        sincospif(2.f * (float)u1, &sn, &cs);
-        g[2 * pr] = rad * cs;
-        g[2 * pr + 1] = rad * sn;
-    }
+    box_muller(w[0], w[1], g[0], g[1]);
+    box_muller(w[2], w[3], g[2], g[3]);
     for (int l = 0; l < 4; ++l) {
         const long long e = 4 * b + l;
         if (e < count) {
@@ -1075,6 +1043,9 @@ __global__ void k_make_pop(long long count, int n_par, const float* __restrict__
     z[e] = fmaf(s[p], r[e], m[p]);
 }
 
+constexpr int kUpdateThreads = 128;  // parameters per update block (at least kMaxPop)
+static_assert(kUpdateThreads >= kMaxPop, "one thread per member in the ranking");
+
 // Where a run of generations keeps its loss history: row (generation - base).
 struct SnesCtl {
     double* hist;   // dev [n_gen][P][6] or NULL
@@ -1090,18 +1061,30 @@ __global__ void k_set_ctl(SnesCtl* ctl, double* hist, unsigned base)
 // Rank the members by (loss, index), then the natural gradients (Eqs. 36-37)
 // with the rank utilities `util` and the update of m with the pre-update s
 // (Eq. 38), then s (Eq. 39).  Every block ranks the (few) members itself and
-// updates its own slice of parameters.  Block 0 also appends the losses to
-// the run's history (ctl, may be NULL) and advances the device generation
+// updates its own slice of parameters; a thread's draws of every member and
+// its m and s do not depend on the ranking and are loaded before it, and the
+// gradient sums run over the members in index order, each draw weighted by
+// the utility of its member's rank.  Block 0 also appends the losses to the
+// run's history (ctl, may be NULL) and advances the device generation
 // counter that the next generation's draws read.
-__global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss, const float* __restrict__ util,
-                              const float* __restrict__ r, float* __restrict__ m, float* __restrict__ s, float eta_m,
-                              float eta_s, int* __restrict__ order_out, unsigned* __restrict__ d_gen,
-                              const SnesCtl* __restrict__ ctl)
+__global__ void __launch_bounds__(kUpdateThreads) k_snes_update(int P, int n_par, const double* __restrict__ loss,
+                                                               const float* __restrict__ util,
+                                                               const float* __restrict__ r, float* __restrict__ m,
+                                                               float* __restrict__ s, float eta_m, float eta_s,
+                                                               int* __restrict__ order_out,
+                                                               unsigned* __restrict__ d_gen,
+                                                               const SnesCtl* __restrict__ ctl)
 {
-    __shared__ int order[kMaxPop];
-    __shared__ float u[kMaxPop];
+    __shared__ float ut[kMaxPop];  // utility of rank j
+    __shared__ float uk[kMaxPop];  // utility of member k's rank (0 past P)
     __shared__ unsigned long long key[kMaxPop];
     const int t = threadIdx.x;
+    const int p = blockIdx.x * blockDim.x + t;
+    const bool live = p < n_par;
+    float rv[kMaxPop];
+#pragma unroll
+    for (int k = 0; k < kMaxPop; ++k) rv[k] = live && k < P ? r[(size_t)k * n_par + p] : 0.f;
+    const float mp = live ? m[p] : 0.f, sp = live ? s[p] : 0.f;
 
     // the members' losses as unsigned keys in the same order as the FP64
     // values (integer compares: FP64 compares are slow on this part); -0 is
@@ -1110,6 +1093,7 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
         const double l = loss[(size_t)t * 6];
         const long long b = isnan(l) ? 0x7FF8000000000000LL : __double_as_longlong(l + 0.0);
         key[t] = b < 0 ? ~(unsigned long long)b : ((unsigned long long)b | 0x8000000000000000ull);
+        ut[t] = util[t];
     }
     __syncthreads();
     if (blockIdx.x == 0) {
@@ -1122,35 +1106,29 @@ __global__ void k_snes_update(int P, int n_par, const double* __restrict__ loss,
         __syncthreads();
         if (t == 0) *d_gen = g + 1;
     }
-    if (t < P) {
-        const unsigned long long kk = key[t];
-        int rank = 0;
-        for (int j = 0; j < P; ++j) {
-            const unsigned long long kj = key[j];
-            rank += (kj < kk || (kj == kk && j < t)) ? 1 : 0;
+    if (t < kMaxPop) {
+        float w = 0.f;
+        if (t < P) {
+            const unsigned long long kk = key[t];
+            int rank = 0;
+            for (int j = 0; j < P; ++j) {
+                const unsigned long long kj = key[j];
+                rank += (kj < kk || (kj == kk && j < t)) ? 1 : 0;
+            }
+            w = ut[rank];
+            if (order_out && blockIdx.x == 0) order_out[rank] = t;
         }
-        order[rank] = t;
-        u[t] = util[t];
+        uk[t] = w;
     }
     __syncthreads();
-    if (order_out && blockIdx.x == 0 && t < P) order_out[t] = order[t];
-    const int p = blockIdx.x * blockDim.x + t;
-    if (p >= n_par) return;
+    if (!live) return;
     float gm = 0.f, gs = 0.f;
-    constexpr int kBatch = 25;  // draws loaded together (two rounds for 50 members), then summed in rank order
-    for (int q0 = 0; q0 < P; q0 += kBatch) {
-        float rv[kBatch];
 #pragma unroll
-        for (int b = 0; b < kBatch; ++b) rv[b] = q0 + b < P ? r[(size_t)order[q0 + b] * n_par + p] : 0.f;
-#pragma unroll
-        for (int b = 0; b < kBatch; ++b)
-            if (q0 + b < P) {
-                gm = fmaf(u[q0 + b], rv[b], gm);
-                gs = fmaf(u[q0 + b], fmaf(rv[b], rv[b], -1.f), gs);
-            }
+    for (int k = 0; k < kMaxPop; ++k) {
+        gm = fmaf(uk[k], rv[k], gm);
+        gs = fmaf(uk[k], fmaf(rv[k], rv[k], -1.f), gs);
     }
-    const float sp = s[p];
-    m[p] = fmaf(eta_m * sp, gm, m[p]);
+    m[p] = fmaf(eta_m * sp, gm, mp);
     s[p] = sp * expf(0.5f * eta_s * gs);
 }
 
@@ -1390,8 +1368,10 @@ void launch_contraction(const nep_dataset* ds, int P, int Pst, int c_lo, int c_h
 // stream) overlaps pass 1 of range w + 1, and a range's partial forces are
 // read back while they are still in L2.  A range never splits a structure:
 // pass 1 of a structure's owners writes into the slots of all its atoms.
+// prepacked: (BF16) the tensor-core records already hold z_pop (an SNES
+// generation that drew and packed in one launch)
 int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P, int precision,
-                       const double* lambdas, double* loss, cudaStream_t st)
+                       const double* lambdas, double* loss, cudaStream_t st, bool prepacked = false)
 {
     if (precision != NEP_PREC_FP32 && precision != NEP_PREC_BF16) {
         set_error("snes_evaluate_population: unknown precision %d", precision);
@@ -1404,8 +1384,8 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         // G in FP16: the contraction reads half the bytes (the loss terms
         // average its rounding over all force components)
         const int layout = !sh.fused && sh.owner_tc ? kGTilesF16 : kGRowsF16;
-        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, z_pop, ds->packed, ds->G, layout, ds->U, m->d_err,
-                                sh.pop_pipe != 0, st)))
+        if ((rc = launch_pop_tc(ds->N, P, Pst, nn, ds->qpack, prepacked ? nullptr : z_pop, ds->packed, ds->G, layout,
+                                ds->U, m->d_err, sh.pop_pipe != 0, st)))
             return rc;
     } else {
         k_pack<<<blocks_for((long long)P * n_par, 256), 256, 0, st>>>(P, nn, z_pop, ds->W1t, ds->b1t, ds->w2t,
@@ -1490,15 +1470,21 @@ int enqueue_generation(snes_state* st, nep_dataset* ds, int precision, const dou
         int rc = cuda_fail(cudaMemcpyAsync(st->r, r_in, sizeof(float) * tot, cudaMemcpyDeviceToDevice, cs), "copy r");
         if (rc) return rc;
         k_make_pop<<<blocks_for(tot, 256), 256, 0, cs>>>(tot, st->n_par, st->mean, st->sigma, st->r, st->z);
+    } else if (precision == NEP_PREC_BF16) {
+        // the draws, z and the tensor-core records in one launch
+        int rc = launch_pack_tc_draw(st->P, st->m->hp.n_neu, st->seed, st->d_gen, st->mean, st->sigma, st->r, st->z,
+                                     ds->packed, cs);
+        if (rc) return rc;
     } else {
         k_gauss<<<blocks_for((tot + 3) / 4, 256), 256, 0, cs>>>(tot, st->n_par, st->seed, st->d_gen, st->mean,
                                                                 st->sigma, st->r, st->z);
     }
-    int rc = enqueue_evaluation(st->m, ds, st->z, st->P, precision, lambdas, st->loss, cs);
+    const bool prepacked = !r_in && precision == NEP_PREC_BF16;
+    int rc = enqueue_evaluation(st->m, ds, st->z, st->P, precision, lambdas, st->loss, cs, prepacked);
     if (rc) return rc;
     const float eta_s = (float)((3.0 + std::log((double)st->n_par)) / (5.0 * std::sqrt((double)st->n_par)));
-    k_snes_update<<<blocks_for(st->n_par, 128), 128, 0, cs>>>(st->P, st->n_par, st->loss, st->util, st->r, st->mean,
-                                                               st->sigma, 1.f, eta_s, st->order, st->d_gen, ctl);
+    k_snes_update<<<blocks_for(st->n_par, kUpdateThreads), kUpdateThreads, 0, cs>>>(
+        st->P, st->n_par, st->loss, st->util, st->r, st->mean, st->sigma, 1.f, eta_s, st->order, st->d_gen, ctl);
     return cuda_fail(cudaGetLastError(), "snes generation kernels");
 }
 

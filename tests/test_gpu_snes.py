@@ -129,6 +129,42 @@ def test_philox_draws_match_oracle(N, orc, small_set):
     model.close()
 
 
+def test_bf16_generation_draws_while_packing(N, orc, small_set):
+    """In BF16 mode a generation draws r, forms z = m + s r and packs the
+    tensor-core records in one kernel: the draws are the FP32 generation's
+    bits (the same Philox stream), and with m = 0 (z = s r exactly) the
+    generation's losses are the bits of snes_evaluate_population on that z."""
+    import torch
+    structures, teacher, E, F, W, pop = small_set
+    model = N.NEP(teacher.astype(np.float32))
+    ds = N.Dataset(model, structures, E, F, W)
+    s0 = np.full(1021, 0.1)
+    a = N.SNES(model, 6, np.zeros(1021), s0, seed=2107081194)
+    b = N.SNES(model, 6, np.zeros(1021), s0, seed=2107081194)
+    la = torch.empty(6, N.LOSS_COLS, dtype=torch.float64, device="cuda")
+    lb = torch.empty(6, N.LOSS_COLS, dtype=torch.float64, device="cuda")
+    a.step(ds, N.PREC_FP32, loss=la)
+    b.step(ds, N.PREC_BF16, loss=lb)
+    ra = a.state()[2]
+    rb = b.state()[2]
+    assert torch.equal(ra, rb)
+    z = (torch.tensor(s0, dtype=torch.float32, device="cuda")[None, :] * rb).contiguous()
+    want = ds.evaluate(z, N.PREC_BF16)
+    torch.cuda.synchronize()
+    assert torch.equal(lb, want)
+    assert torch.equal(la[:, 4:6], lb[:, 4:6])   # L_1, L_2: functions of z alone
+    # the next generation's draws too (they do not depend on m and s)
+    a.step(ds, N.PREC_FP32)
+    b.step(ds, N.PREC_BF16)
+    assert torch.equal(a.state()[2], b.state()[2])
+    assert np.allclose(b.state()[2].cpu().numpy(), orc.gaussian(2107081194, 1, 6 * 1021).reshape(6, 1021),
+                       rtol=2e-5, atol=2e-5)
+    a.close()
+    b.close()
+    ds.close()
+    model.close()
+
+
 def test_config4_training_set_full_size(N, orc):
     """All 200 structures (uneven 32-256 atoms); four members, oracle losses."""
     import torch
