@@ -791,7 +791,8 @@ def snes_generations(N, precision: int, gens: int = 20, warm: int = 3, shape=Non
 
 SNES_SOURCES = ("paper_2107_08119_gb300/csrc/nep_train.cu", "paper_2107_08119_gb300/csrc/nep_pop_tc.cu",
                 "paper_2107_08119_gb300/csrc/nep_tc.cuh", "paper_2107_08119_gb300/csrc/nep_dataset.cuh",
-                "paper_2107_08119_gb300/csrc/nep_internal.cuh", "paper_2107_08119_gb300/csrc/nep_recv.cuh")
+                "paper_2107_08119_gb300/csrc/nep_internal.cuh", "paper_2107_08119_gb300/csrc/nep_recv.cuh",
+                "paper_2107_08119_gb300/csrc/nep_philox.cuh")
 SNES_PROFILE = os.path.join(ROOT, "profiles", "snes_generation_dram_200structs.json")
 
 
