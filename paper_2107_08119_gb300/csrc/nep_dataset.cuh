@@ -63,6 +63,7 @@ struct nep_dataset {
     int* sstart = nullptr;
     int* s_natoms = nullptr;
     double* s_inv_na = nullptr;  // 1 / atoms of each structure
+    float* s_vtar = nullptr;     // [S][8]: virial targets, 1 / atoms (FP32), 0
     int typed = 0;               // species numbers given (multicomponent weighting)
     int* s_chunk0 = nullptr;
     int* s_order = nullptr;      // structures by decreasing atom count (fused contraction blocks)
@@ -91,9 +92,7 @@ struct nep_dataset {
     float* b2t = nullptr;
     float* G = nullptr;
     double* U = nullptr;
-    double* partials = nullptr;
-    double* loss_part = nullptr;     // [P][kLossSplit][5] block sums of the loss kernel
-    unsigned* loss_count = nullptr;  // [P] blocks of the loss kernel done (zero between evaluations)
+    double* partials = nullptr;  // loss records (ChunkRec, 64 B) [chunk][member]
     unsigned char* packed = nullptr;  // tensor-core operand records
     unsigned char* qpack = nullptr;   // descriptors as split-BF16 A tiles (tensor cores)
     float* pbuf = nullptr;            // [n_pairs][3][Pst] partial forces p_kji at the receiver's slot

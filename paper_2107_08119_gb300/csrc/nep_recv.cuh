@@ -99,6 +99,17 @@ struct RecvAcc {
     }
 };
 
+// The loss partials of one chunk and member (64 bytes): the sum of U in
+// FP64, then the squared force residuals and the six owner virial sums in
+// FP32, as the receiver forms them (the loss kernel adds them in FP32 too:
+// the FP64 pipe is slow on this part).
+struct ChunkRec {
+    double u;
+    float fw[7];  // |F - F_tar|^2, W_xx, W_yy, W_zz, W_xy, W_yz, W_zx
+    float pad[7];
+};
+static_assert(sizeof(ChunkRec) == 64, "one record is eight FP64 slots of the partials buffer");
+
 // Per-warp sums of a receiver block: U in FP64, the other seven terms in FP32.
 template <int W>
 struct RecvRed {
@@ -107,25 +118,25 @@ struct RecvRed {
 };
 
 // The chunk's partials in a fixed order (warps 0..W-1): U summed in FP64,
-// the squared force residuals and virial terms in FP32 and converted once.
+// the squared force residuals and virial terms in FP32.  partials: the
+// buffer of ChunkRec records [chunk][member], this chunk's P records.
 template <int W>
-__device__ __forceinline__ void recv_chunk_store(const RecvRed<W>& red, int P, double* __restrict__ out)
+__device__ __forceinline__ void recv_chunk_store(const RecvRed<W>& red, int P, double* __restrict__ partials)
 {
+    ChunkRec* out = reinterpret_cast<ChunkRec*>(partials);
     for (int e = threadIdx.x; e < P * 8; e += blockDim.x) {
         const int k = e / 8, w = e % 8;
-        double t;
         if (w == 0) {
             double a = 0.0;
 #pragma unroll
             for (int q = 0; q < W; ++q) a += red.u[q][k];
-            t = a;
+            out[k].u = a;
         } else {
             float a = 0.f;
 #pragma unroll
             for (int q = 0; q < W; ++q) a += red.f[q][k][w - 1];
-            t = (double)a;
+            out[k].fw[w - 1] = a;
         }
-        out[(size_t)k * 8 + w] = t;
     }
 }
 

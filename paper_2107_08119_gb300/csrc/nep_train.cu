@@ -36,6 +36,7 @@
 #include <type_traits>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
 #include "nep_dataset.cuh"
@@ -45,6 +46,8 @@
 
 namespace nep {
 namespace {
+
+namespace cg = cooperative_groups;
 
 constexpr int kDsCap = 192;      // neighbour capacity per atom while building (within r_c)
 constexpr int kChunkAtoms = 32;       // atoms per contraction block (chunks never span structures)
@@ -855,7 +858,13 @@ __global__ void __launch_bounds__(kFusedThreads) k_contract_fused(
 #pragma unroll
             for (int w = 0; w < 6; ++w) v[2 + w] += (double)W6[(il * 6 + w) * GM + kk];
         }
-        block_sum_store<8>(v, partials + ((size_t)s * P + kg) * 8);
+        // the structure's record (U in FP64, the other terms in FP32)
+        __shared__ double tot[8];
+        block_sum_store<8>(v, tot);
+        __syncthreads();
+        ChunkRec* out = reinterpret_cast<ChunkRec*>(partials) + (size_t)s * P + kg;
+        if (threadIdx.x == 0) out->u = tot[0];
+        if (threadIdx.x >= 1 && threadIdx.x < 8) out->fw[threadIdx.x - 1] = (float)tot[threadIdx.x];
         __syncthreads();  // the block sum's shared scratch serves the next member
     }
 }
@@ -871,15 +880,17 @@ FusedKernel fused_kernel(int gm, bool gh)
     return gh ? k_contract_fused<16, __half> : k_contract_fused<16, float>;
 }
 
-// kLossSplit blocks per member (grid P x kLossSplit), block q taking the
-// structures s = q, q + kLossSplit, ...: per structure, the chunk sums (fixed
-// order) or the structure's own sum (fused contraction: s_chunk0 NULL), then
-// the squared per-atom energy and virial errors; with its share of the
-// parameters for L1, L2.  The member's last block adds the blocks' sums in
-// order and forms the RMSEs of Eqs. 30-32 and L1, L2 (Eqs. 33-34).  FP64
-// arithmetic is slow on this part, so the work is spread over four times as
-// many SMs as members and the parameter sums run in FP32 (four values per
-// thread) before their conversion.
+// kLossSplit blocks per member (grid P x kLossSplit, one thread-block
+// cluster per member), block q taking the structures s = q, q + kLossSplit,
+// ...: per structure, the chunk records in order (fixed order; with the fused
+// contraction, s_chunk0 NULL, the structure's own record): U in FP64, the
+// squared force residuals and the virial sums in FP32; then the squared
+// per-atom energy error in FP64 and the per-atom virial errors in FP32; with
+// its share of the parameters for L1, L2.  Rank 0 of the member's cluster
+// adds the blocks' sums in order, read from their shared memory, and forms
+// the RMSEs of Eqs. 30-32 and L1, L2 (Eqs. 33-34).  FP64 arithmetic is slow on
+// this part: the work is spread over four times as many SMs as members, and
+// every term that comes from FP32 values stays in FP32 until the block sums.
 constexpr int kLossSplit = 4;     // blocks per member, each over every fourth structure
 constexpr int kLossThreads = 64;
 
@@ -906,13 +917,11 @@ __device__ __forceinline__ double sqrt_refined(double x)
     return fma(fma(-y, y, x), (double)(0.5f / yf), y);
 }
 
-__global__ void __launch_bounds__(kLossThreads) k_loss(int P, int S, int n_par, int N, const int* __restrict__ s_chunk0,
-                                                       const double* __restrict__ s_inv_na,
-                                                       const double* __restrict__ partials,
-                                                       const double* __restrict__ e_tar, const double* __restrict__ w_tar,
-                                                       const float* __restrict__ z, double l_e, double l_f, double l_v,
-                                                       double l_1, double l_2, LossInv inv, double* __restrict__ part,
-                                                       unsigned* __restrict__ count, double* __restrict__ loss)
+__global__ void __cluster_dims__(1, kLossSplit, 1) __launch_bounds__(kLossThreads)
+    k_loss(int P, int S, int n_par, const int* __restrict__ s_chunk0, const double* __restrict__ s_inv_na,
+           const float* __restrict__ s_vtar, const double* __restrict__ partials, const double* __restrict__ e_tar,
+           const float* __restrict__ z, double l_e, double l_f, double l_v, double l_1, double l_2, LossInv inv,
+           double* __restrict__ loss)
 {
     constexpr int kBatch = 4;  // chunks whose loads are issued together (summed in order)
     const int k = blockIdx.x, q = blockIdx.y, nq = gridDim.y;
@@ -939,70 +948,80 @@ __global__ void __launch_bounds__(kLossThreads) k_loss(int P, int S, int n_par, 
         acc[3] = (double)a1;
         acc[4] = (double)a2;
     }
+    const ChunkRec* rec = reinterpret_cast<const ChunkRec*>(partials);
+    double se = 0.0;
+    float sf = 0.f, sv = 0.f;
     for (int s = q + nq * threadIdx.x; s < S; s += stride) {
-        // the structure's targets and chunk range first (independent loads)
-        const double ia = s_inv_na[s];  // per-atom energies and virials (FP64 division is slow here)
+        // the structure's targets and chunk range first (independent loads):
+        // 1 / atoms in FP64 for the energy, the virial targets and 1 / atoms
+        // in FP32 for the virial
+        const double ia = s_inv_na[s];
         const double et = e_tar[s];
-        double wt[6];
-#pragma unroll
-        for (int w = 0; w < 6; ++w) wt[w] = w_tar[(size_t)s * 6 + w];
+        const float4 t0 = reinterpret_cast<const float4*>(s_vtar)[2 * s];
+        const float4 t1 = reinterpret_cast<const float4*>(s_vtar)[2 * s + 1];
+        const float wt[6] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y};
+        const float iaf = t1.z;
         const int c1 = s_chunk0 ? s_chunk0[s + 1] : s + 1;
-        double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        // per-chunk partials, or (s_chunk0 NULL) one partial per structure:
-        // a record of 8 FP64 values as four 16-byte loads
+        double u = 0.0;
+        float fw[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // per-chunk records, or (s_chunk0 NULL) one record per structure: the
+        // first 36 bytes of each as three 16-byte loads
         for (int c0 = s_chunk0 ? s_chunk0[s] : s; c0 < c1; c0 += kBatch) {
-            double2 b[kBatch][4];
+            uint4 b[kBatch][3];
 #pragma unroll
             for (int r = 0; r < kBatch; ++r) {
-                const double2* src = reinterpret_cast<const double2*>(partials + ((size_t)(c0 + r) * P + k) * 8);
+                const uint4* src = reinterpret_cast<const uint4*>(rec + (size_t)(c0 + r) * P + k);
 #pragma unroll
-                for (int w = 0; w < 4; ++w) b[r][w] = c0 + r < c1 ? src[w] : make_double2(0.0, 0.0);
+                for (int w = 0; w < 3; ++w) b[r][w] = c0 + r < c1 ? src[w] : make_uint4(0u, 0u, 0u, 0u);
             }
 #pragma unroll
             for (int r = 0; r < kBatch; ++r)
-                if (c0 + r < c1)
+                if (c0 + r < c1) {
+                    u += __hiloint2double((int)b[r][0].y, (int)b[r][0].x);
+                    const uint32_t f7[7] = {b[r][0].z, b[r][0].w, b[r][1].x, b[r][1].y, b[r][1].z, b[r][1].w,
+                                            b[r][2].x};
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        v[2 * w] += b[r][w].x;
-                        v[2 * w + 1] += b[r][w].y;
-                    }
+                    for (int w = 0; w < 7; ++w) fw[w] += __uint_as_float(f7[w]);
+                }
         }
-        const double de = (v[0] - et) * ia;
-        acc[0] += de * de;
-        acc[1] += v[1];
+        const double de = (u - et) * ia;
+        se = fma(de, de, se);
+        sf += fw[0];
+#pragma unroll
         for (int w = 0; w < 6; ++w) {
-            const double dv = (v[2 + w] - wt[w]) * ia;
-            acc[2] += dv * dv;
+            const float dv = (fw[1 + w] - wt[w]) * iaf;
+            sv = fmaf(dv, dv, sv);
         }
     }
-    // the block's five sums; the last of the member's nq blocks (counted)
-    // adds the nq rows in order and forms the losses, then clears the count
-    // for the next evaluation
-    double* row = part + ((size_t)k * nq + q) * 5;
-    block_sum_store<5>(acc, row);
-    __shared__ int last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(&count[k], 1u) == (unsigned)(nq - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // thread c forms term c: the mean over its count (reciprocals from the
-    // host: FP64 division is a long serial sequence here), then the root
+    acc[0] = se;
+    acc[1] = (double)sf;
+    acc[2] = (double)sv;
+    // the block's five sums into its shared memory; rank 0 of the cluster
+    // (the member's four blocks) reads the four rows in order and forms the
+    // losses; the second cluster barrier keeps every row alive until then
+    __shared__ double part[5];
     __shared__ double L[5];
-    if (threadIdx.x < 5) {
-        const int c = threadIdx.x;
-        double t = 0.0;
-        for (int r = 0; r < nq; ++r) t += __ldcg(part + ((size_t)k * nq + r) * 5 + c);
-        const double mean = t * (c == 0 ? inv.S : c == 1 ? inv.F : c == 2 ? inv.V : inv.P);
-        L[c] = c == 3 ? mean : sqrt_refined(mean);
+    block_sum_store<5>(acc, part);
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (cl.block_rank() == 0) {
+        // thread c forms term c: the mean over its count (reciprocals from the
+        // host: FP64 division is a long serial sequence here), then the root
+        if (threadIdx.x < 5) {
+            const int c = threadIdx.x;
+            double t = 0.0;
+            for (int r = 0; r < nq; ++r) t += *cl.map_shared_rank(&part[c], r);
+            const double mean = t * (c == 0 ? inv.S : c == 1 ? inv.F : c == 2 ? inv.V : inv.P);
+            L[c] = c == 3 ? mean : sqrt_refined(mean);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double* out = loss + (size_t)k * 6;
+            out[0] = l_e * L[0] + l_f * L[1] + l_v * L[2] + l_1 * L[3] + l_2 * L[4];
+            for (int c = 0; c < 5; ++c) out[1 + c] = L[c];
+        }
     }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    count[k] = 0u;
-    double* out = loss + (size_t)k * 6;
-    out[0] = l_e * L[0] + l_f * L[1] + l_v * L[2] + l_1 * L[3] + l_2 * L[4];
-    for (int c = 0; c < 5; ++c) out[1 + c] = L[c];
+    cl.sync();
 }
 
 // ------------------------------------------------------------------ SNES
@@ -1232,8 +1251,6 @@ int ensure_pop(nep_dataset* ds, int P)
     dfree(ds->pbuf);
     dfree(ds->w6);
     dfree(ds->fown);
-    dfree(ds->loss_part);
-    dfree(ds->loss_count);
     ds->pop_cap = 0;
     const int nn = ds->m->hp.n_neu;
     int rc;
@@ -1245,13 +1262,8 @@ int ensure_pop(nep_dataset* ds, int P)
         (rc = dalloc(&ds->packed, pop_tc_packed_bytes(P), nullptr)) ||
         (rc = dalloc(&ds->pbuf, (size_t)ds->n_pairs * 3 * member_stride(P), nullptr)) ||
         (rc = dalloc(&ds->w6, (size_t)ds->N * 6 * member_stride(P), nullptr)) ||
-        (rc = dalloc(&ds->fown, (size_t)ds->N * 3 * member_stride(P), nullptr)) ||
-        (rc = dalloc(&ds->loss_part, (size_t)P * kLossSplit * 5, nullptr)) ||
-        (rc = dalloc(&ds->loss_count, (size_t)P, nullptr)))
+        (rc = dalloc(&ds->fown, (size_t)ds->N * 3 * member_stride(P), nullptr)))
         return rc;
-    // the loss kernel's block counts start at zero (each evaluation clears them again)
-    rc = cuda_fail(cudaMemset(ds->loss_count, 0, sizeof(unsigned) * (size_t)P), "clear loss counts");
-    if (rc) return rc;
     // members past P in the last group of G are never written: keep them zero
     rc = cuda_fail(cudaMemset(ds->G, 0, sizeof(float) * (size_t)ds->N * kNdes * member_stride(P)), "clear G");
     if (rc) return rc;
@@ -1405,10 +1417,9 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         fused_kernel(gm, gh)<<<ds->S * groups, kFusedThreads, smem, st>>>(
             P, Pst, groups, ds->s_order, ds->sstart, ds->G, ds->U, ds->B, ds->pstart, ds->pj, ds->rec, ds->astart,
             ds->ang, ds->f_tar, ds->partials, m->d_err);
-        k_loss<<<dim3(P, kLossSplit), kLossThreads, 0, st>>>(P, ds->S, n_par, ds->N, nullptr, ds->s_inv_na,
-                                                             ds->partials, ds->e_tar, ds->w_tar, z_pop, lam[0], lam[1],
-                                                             lam[2], lam[3], lam[4], loss_inv(ds->S, ds->N, n_par),
-                                                             ds->loss_part, ds->loss_count, loss);
+        k_loss<<<dim3(P, kLossSplit), kLossThreads, 0, st>>>(P, ds->S, n_par, nullptr, ds->s_inv_na, ds->s_vtar,
+                                                             ds->partials, ds->e_tar, z_pop, lam[0], lam[1], lam[2],
+                                                             lam[3], lam[4], loss_inv(ds->S, ds->N, n_par), loss);
         return cuda_fail(cudaGetLastError(), "population evaluation kernels");
     }
     const int C = ds->n_chunks;
@@ -1444,10 +1455,9 @@ int enqueue_evaluation(nep_model* m, nep_dataset* ds, const float* z_pop, int P,
         cudaEventRecord(ds->ev_join, ds->aux);
         cudaStreamWaitEvent(st, ds->ev_join, 0);
     }
-    k_loss<<<dim3(P, kLossSplit), kLossThreads, 0, st>>>(P, ds->S, n_par, ds->N, ds->s_chunk0, ds->s_inv_na,
-                                                         ds->partials, ds->e_tar, ds->w_tar, z_pop, lam[0], lam[1],
-                                                         lam[2], lam[3], lam[4], loss_inv(ds->S, ds->N, n_par),
-                                                         ds->loss_part, ds->loss_count, loss);
+    k_loss<<<dim3(P, kLossSplit), kLossThreads, 0, st>>>(P, ds->S, n_par, ds->s_chunk0, ds->s_inv_na, ds->s_vtar,
+                                                         ds->partials, ds->e_tar, z_pop, lam[0], lam[1], lam[2], lam[3],
+                                                         lam[4], loss_inv(ds->S, ds->N, n_par), loss);
     return cuda_fail(cudaGetLastError(), "population evaluation kernels");
 }
 
@@ -1591,7 +1601,7 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     };
     if ((rc = dalloc(&ds->boxes, S, bytes)) || (rc = dalloc(&ds->sid, N, bytes)) ||
         (rc = dalloc(&ds->sstart, S + 1, bytes)) || (rc = dalloc(&ds->s_natoms, S, bytes)) ||
-        (rc = dalloc(&ds->s_inv_na, S, bytes)) ||
+        (rc = dalloc(&ds->s_inv_na, S, bytes)) || (rc = dalloc(&ds->s_vtar, (size_t)8 * S, bytes)) ||
         (rc = dalloc(&ds->s_chunk0, S + 1, bytes)) || (rc = dalloc(&ds->s_order, S, bytes)) ||
         (rc = dalloc(&ds->chunk_begin, ds->n_chunks, bytes)) ||
         (rc = dalloc(&ds->chunk_end, ds->n_chunks, bytes)) || (rc = dalloc(&ds->q, (size_t)N * kNdes, bytes)) ||
@@ -1613,6 +1623,14 @@ int nep_dataset_create_species(nep_model* m, int n_struct, const int* n_atoms, c
     std::vector<double> hinv(S);
     for (int t = 0; t < S; ++t) hinv[t] = 1.0 / hnat[t];
     up(ds->s_inv_na, hinv.data(), sizeof(double) * S);
+    // the virial targets and 1 / atoms in FP32 for the loss kernel's FP32
+    // virial residuals: [S][8] = W_tar (6), 1 / atoms, 0
+    std::vector<float> hvt((size_t)8 * S, 0.f);
+    for (int t = 0; t < S; ++t) {
+        for (int w = 0; w < 6; ++w) hvt[(size_t)8 * t + w] = (float)w_tar[(size_t)6 * t + w];
+        hvt[(size_t)8 * t + 6] = (float)hinv[t];
+    }
+    up(ds->s_vtar, hvt.data(), sizeof(float) * hvt.size());
     up(ds->s_chunk0, hchunk0.data(), sizeof(int) * (S + 1));
     // fused contraction: blocks of the largest structures first (they take
     // longest), and the shared memory its largest structure needs
@@ -1741,6 +1759,7 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->sstart);
     dfree(ds->s_natoms);
     dfree(ds->s_inv_na);
+    dfree(ds->s_vtar);
     dfree(ds->s_chunk0);
     dfree(ds->s_order);
     dfree(ds->astart);
@@ -1771,8 +1790,6 @@ int nep_dataset_destroy(nep_dataset* ds)
     dfree(ds->pbuf);
     dfree(ds->w6);
     dfree(ds->fown);
-    dfree(ds->loss_part);
-    dfree(ds->loss_count);
     dfree(ds->tiles);
     dfree(ds->apack);
     dfree(ds->rowscale);
