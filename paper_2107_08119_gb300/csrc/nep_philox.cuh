@@ -33,18 +33,30 @@ __device__ __forceinline__ void philox(uint32_t c0, uint32_t c1, uint32_t c2, ui
     o[3] = c3;
 }
 
-// The Box-Muller pair of two 32-bit words: u = (w + 1/2) 2^-32 and 1 - u are
-// exact in FP64; the transform runs in FP32 (FP64 transcendentals are slow on
-// this part) with ln u taken as log1p(-(1 - u)) when u is near 1, so that the
-// radius keeps full relative precision where ln u is tiny.
+// u = (w + 1/2) 2^-32 rounded once to FP32 (round to nearest), from 32-bit
+// integer conversions (the FP64 pipe is slow on this part).  Below 2^31,
+// 2 w + 1 fits 32 bits and converts exactly-rounded.  From 2^31 on, FP32
+// values are 256 apart there and w + 1/2 is never halfway between two of
+// them, so its rounding is that of w except where w itself is halfway
+// (w = 128 mod 256), where ties-to-even may round w down but w + 1/2 rounds
+// up.
+__device__ __forceinline__ float unit_from_word(uint32_t w)
+{
+    if (w < 0x80000000u) return __uint2float_rn(2u * w + 1u) * 0x1p-33f;
+    const float a = (w & 255u) == 128u ? __uint2float_ru(w) : __uint2float_rn(w);
+    return a * 0x1p-32f;
+}
+
+// The Box-Muller pair of two 32-bit words, u = (w + 1/2) 2^-32: the transform
+// runs in FP32 with ln u0 taken as log1p(-(1 - u0)) when u0 >= 1/2 (1 - u0 =
+// (~w0 + 1/2) 2^-32 exactly), so that the radius keeps full relative
+// precision where ln u0 is tiny.
 __device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& g0, float& g1)
 {
-    const double u0 = ((double)w0 + 0.5) * (1.0 / 4294967296.0);
-    const double u1 = ((double)w1 + 0.5) * (1.0 / 4294967296.0);
-    const float lu = u0 < 0.5 ? logf((float)u0) : log1pf(-(float)(1.0 - u0));
+    const float lu = w0 < 0x80000000u ? logf(unit_from_word(w0)) : log1pf(-unit_from_word(~w0));
     const float rad = sqrtf(-2.f * lu);
     float sn, cs;
-    sincospif(2.f * (float)u1, &sn, &cs);
+    sincospif(2.f * unit_from_word(w1), &sn, &cs);
     g0 = rad * cs;
     g1 = rad * sn;
 }

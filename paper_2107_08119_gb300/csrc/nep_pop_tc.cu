@@ -186,8 +186,14 @@ __global__ void k_pack_q_tc(int N, int tiles, const float* __restrict__ q, unsig
 // the population z [P][n_par] (layout w1 [n_neu][32], b1, w2, b2 per member),
 // or (kDraw, an SNES generation) drawn while packing: element e = k n_par + p
 // of the generation's normals r (nep_philox.cuh), z = m + s r, each stored by
-// the one thread whose record entry owns the element (a W1 weight appears in
-// both GEMM operands and is drawn twice, with the same bits).
+// the one thread whose record entry owns the element; with draws, the thread
+// of a W1 weight's GEMM-1 entry also writes its GEMM-2 entry (the same
+// element), and the GEMM-2 range is not launched.
+__host__ __device__ constexpr int pack_tc_threads_per_group(bool draw)
+{
+    return kTile * 32 + (draw ? 0 : kTcGroup * 32 * 32) + kTcGroup * 32;
+}
+
 template <bool kDraw>
 __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigned char* __restrict__ packed,
                           unsigned long long seed, const unsigned* __restrict__ d_gen, const float* __restrict__ mv,
@@ -195,7 +201,7 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigne
 {
     const int n_par = (kNdes + 2) * n_neu + 1;
     const int groups = (P + kTcGroup - 1) / kTcGroup;
-    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;  // w1 elems, w1t elems, bias rows
+    const int per = pack_tc_threads_per_group(kDraw);  // w1 elems, (w1t elems,) bias rows
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= groups * per) return;
     const unsigned gen = kDraw ? *d_gen : 0u;
@@ -216,18 +222,23 @@ __global__ void k_pack_tc(int P, int n_neu, const float* __restrict__ z, unsigne
     if (r < kTile * 32) {  // GEMM-1 B row = 32 m + mu, column nu
         const int row = r / 32, nu = r % 32, m = row / 32, mu = row % 32;
         const bool on = m < mg && mu < n_neu;
-        put_split(rec, rec + kW1Bytes, row, nu, on ? val(k0 + m, mu * kNdes + nu, true) : 0.f);
+        const float v = on ? val(k0 + m, mu * kNdes + nu, true) : 0.f;
+        put_split(rec, rec + kW1Bytes, row, nu, v);
+        if (kDraw) {  // GEMM-2 B of member m: row nu, column mu
+            unsigned char* hi = rec + 2 * kW1Bytes + m * kW1tBytes;
+            put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, v);
+        }
         return;
     }
     int t = r - kTile * 32;
-    if (t < kTcGroup * 32 * 32) {  // GEMM-2 B of member m: row nu, column mu
+    if (!kDraw && t < kTcGroup * 32 * 32) {  // GEMM-2 B of member m: row nu, column mu
         const int m = t / 1024, nu = (t / 32) % 32, mu = t % 32;
         const bool on = m < mg && mu < n_neu;
         unsigned char* hi = rec + 2 * kW1Bytes + m * kW1tBytes;
         put_split(hi, hi + kTcGroup * kW1tBytes, nu, mu, on ? val(k0 + m, mu * kNdes + nu, false) : 0.f);
         return;
     }
-    t -= kTcGroup * 32 * 32;
+    if (!kDraw) t -= kTcGroup * 32 * 32;
     float* fb = reinterpret_cast<float*>(rec + 2 * kW1Bytes + 2 * kTcGroup * kW1tBytes);
     const int m = t / 32, mu = t % 32;
     const bool on = m < mg && mu < n_neu;
@@ -1018,7 +1029,7 @@ int launch_pop_tc(int N, int P, int Pst, int n_neu, const unsigned char* qpack, 
     }
     const int groups = (P + kTcGroup - 1) / kTcGroup;
     if (z) {
-        const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
+        const int per = pack_tc_threads_per_group(false);
         k_pack_tc<false><<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, z, packed, 0ull, nullptr, nullptr,
                                                                      nullptr, nullptr, nullptr);
     }
@@ -1049,7 +1060,7 @@ int launch_pack_tc_draw(int P, int n_neu, unsigned long long seed, const unsigne
         return NEP_ERR_UNSUPPORTED;
     }
     const int groups = (P + kTcGroup - 1) / kTcGroup;
-    const int per = kTile * 32 + kTcGroup * 32 * 32 + kTcGroup * 32;
+    const int per = pack_tc_threads_per_group(true);
     k_pack_tc<true><<<(groups * per + 255) / 256, 256, 0, st>>>(P, n_neu, nullptr, packed, seed, d_gen, m, s, r, z);
     return cuda_fail(cudaGetLastError(), "draw and pack the population");
 }
