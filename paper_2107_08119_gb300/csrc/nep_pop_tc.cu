@@ -127,13 +127,45 @@ __device__ __forceinline__ unsigned char* d_tile(PopSmem& S, int m)
     return m < 2 ? S.a + m * kTileBytes : S.grp + (m - 2) * kTileBytes;
 }
 
-// tanh(a) = 1 - 2 / (1 + e^(2a)) with the hardware exponential (__expf) and a
-// fast division: absolute error of order 1e-7 for small |a| (the subtraction
-// from 1), saturating to +-1 where e^(2a) over- or underflows.  The BF16
-// mode's network only: D = w2 (1 - x^2) is rounded to BF16 for GEMM 2 and the
-// losses are held to 1e-3 of the FP32 path, against an error of about 1e-6 eV
-// per atom that this gives U.
-__device__ __forceinline__ float tanh_fast(float a) { return 1.f - __fdividef(2.f, 1.f + __expf(2.f * a)); }
+// tanh(a) is taken as 1 - 2 / (1 + e^(2a)) with the hardware exponential
+// (__expf) and a fast division: absolute error of order 1e-7 for small |a|
+// (the subtraction from 1), saturating to +-1 where e^(2a) over- or
+// underflows.  The BF16 mode's network only: D = w2 (1 - x^2) is rounded to
+// BF16 for GEMM 2 and the losses are held to 1e-3 of the FP32 path, against an
+// error of about 1e-6 eV per atom that this gives U.
+
+// Epilogue-1 arithmetic of eight neurons mu = 8c .. 8c + 7 of one (atom,
+// member): x = tanh(h - b1) as above, the running sums of w2 x (even and odd
+// neurons apart, u2.x and u2.y), and D = w2 (1 - x^2) rounded to BF16, as
+// four words of BF16 pairs.  The FP32 arithmetic runs on packed pairs (f32x2:
+// two IEEE round-to-nearest results per instruction, the same as two scalar
+// operations): h - b1 = fma(b1, -1, h), 1 - q = fma(q, -1, 1), and
+// w2 (1 - x^2) as -(w2 (x^2 - 1)) (rounding is symmetric in sign, the sign
+// restored on the BF16 bits).  fb14 / fw24: this member's b1 and w2 rows from
+// neuron 8c on, as float4.
+__device__ __forceinline__ void epi1_eight(const uint32_t (&h)[8], const float4* fb14, const float4* fw24, float2& u2,
+                                           uint32_t (&d)[4])
+{
+    const float2 one2 = make_float2(1.f, 1.f), mone2 = make_float2(-1.f, -1.f), two2 = make_float2(2.f, 2.f);
+    const float4 ba = fb14[0], bb = fb14[1], wa = fw24[0], wb = fw24[1];
+    const float2 b1p[4] = {make_float2(ba.x, ba.y), make_float2(ba.z, ba.w), make_float2(bb.x, bb.y),
+                           make_float2(bb.z, bb.w)};
+    const float2 w2p[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                           make_float2(wb.z, wb.w)};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float2 hv = make_float2(__uint_as_float(h[2 * e]), __uint_as_float(h[2 * e + 1]));
+        const float2 a = __ffma2_rn(b1p[e], mone2, hv);  // h - b1
+        const float2 t = __fmul2_rn(a, two2);
+        const float2 den = __fadd2_rn(one2, make_float2(__expf(t.x), __expf(t.y)));
+        const float2 q = make_float2(__fdividef(2.f, den.x), __fdividef(2.f, den.y));
+        const float2 x = __ffma2_rn(q, mone2, one2);  // 1 - 2 / (1 + e^(2a))
+        u2 = __ffma2_rn(w2p[e], x, u2);
+        const float2 dn = __fmul2_rn(w2p[e], __ffma2_rn(x, x, mone2));  // -w2 (1 - x^2)
+        const __nv_bfloat162 b = __float22bfloat162_rn(dn);
+        d[e] = *reinterpret_cast<const uint32_t*>(&b) ^ 0x80008000u;
+    }
+}
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo)
 {
@@ -347,7 +379,7 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
 #pragma unroll
             for (int c = 0; c < 4; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(32 * m + 8 * c), r[c]);
             tc::tmem_ld_wait();
-            float u = 0.f;
+            float2 u2 = make_float2(0.f, 0.f);
             unsigned char* D = d_tile(S, m);
             // b1 and w2 of the member's 32 neurons: 16-byte broadcast loads
             const float4* b14 = reinterpret_cast<const float4*>(fb + m * 32);
@@ -355,24 +387,10 @@ __global__ void __launch_bounds__(kPopThreads) k_pop_tc(int N, int P, int Pst, c
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 uint32_t d[4];
-                const float4 ba = b14[2 * c], bb = b14[2 * c + 1], wa = w24[2 * c], wb = w24[2 * c + 1];
-                const float b1v[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                const float w2v[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    __nv_bfloat16 dd[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int mu = 2 * e + h;
-                        const float x = tanh_fast(__uint_as_float(r[c][mu]) - b1v[mu]);
-                        const float w2 = w2v[mu];
-                        u = fmaf(w2, x, u);
-                        dd[h] = __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
-                    }
-                    d[e] = pack2(dd[0], dd[1]);
-                }
+                epi1_eight(r[c], b14 + 2 * c, w24 + 2 * c, u2, d);
                 *reinterpret_cast<uint4*>(D + tc::kmajor_offset(row, 8 * c)) = make_uint4(d[0], d[1], d[2], d[3]);
             }
+            const float u = u2.x + u2.y;
             if (valid && k0 + m < P) U[(size_t)i * P + k0 + m] = (double)u - (double)fb[2 * kTcGroup * 32 + m];
         }
     }
@@ -629,31 +647,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1) k_pop_tc_pipe(int N, int P, i
 #pragma unroll
             for (int c = 0; c < 4; ++c) tc::tmem_ld8(tb + lane_base + (uint32_t)(b * kTmemCols + 32 * m + 8 * c), r[c]);
             tc::tmem_ld_wait();
-            float u = 0.f;
+            float2 u2 = make_float2(0.f, 0.f);
             unsigned char* D = S.d[db][m];
             const float4* b14 = reinterpret_cast<const float4*>(fb + m * 32);
             const float4* w24 = reinterpret_cast<const float4*>(fb + kTcGroup * 32 + m * 32);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 uint32_t d[4];
-                const float4 ba = b14[2 * c], bb = b14[2 * c + 1], wa = w24[2 * c], wb = w24[2 * c + 1];
-                const float b1v[8] = {ba.x, ba.y, ba.z, ba.w, bb.x, bb.y, bb.z, bb.w};
-                const float w2v[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    __nv_bfloat16 dd[2];
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int mu = 2 * e + h;
-                        const float x = tanh_fast(__uint_as_float(r[c][mu]) - b1v[mu]);
-                        const float w2 = w2v[mu];
-                        u = fmaf(w2, x, u);
-                        dd[h] = __float2bfloat16_rn(w2 * fmaf(-x, x, 1.f));
-                    }
-                    d[e] = pack2(dd[0], dd[1]);
-                }
+                epi1_eight(r[c], b14 + 2 * c, w24 + 2 * c, u2, d);
                 *reinterpret_cast<uint4*>(D + tc::kmajor_offset(row, 8 * c)) = make_uint4(d[0], d[1], d[2], d[3]);
             }
+            const float u = u2.x + u2.y;
             // D is visible to the tensor core, and this warp's TMEM reads are done
             tc::fence_proxy_async_smem();
             tc::fence_before_sync();
