@@ -402,10 +402,11 @@ def run_gpu(args, rank, world, local):
                     "h2d_bytes_per_step": int(state.numel() * 8),
                     "d2h_bytes_per_step": int(state.numel() * 8 + N.THERMO_COLS * 8),
                     "steps": Ke},
-            # per replayed step: kick-drift, decide, site, assembly, finish; per
-            # rebuild the six list kernels of the conditional body (bin, scan,
-            # scatter, half-shell search, row sort, reverse index)
-            "gpu_launches": 5 * K + 6 * rebuilds,
+            # per replayed step: kick-drift (with the rebuild decision), site,
+            # assembly, finish; per rebuild the six list kernels of the
+            # conditional body (bin, scan, scatter, half-shell search, row
+            # sort, reverse index)
+            "gpu_launches": 4 * K + 6 * rebuilds,
             "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         }
         line["force_eval_vs_plain_fp32"] = force_eval_comparison(N, model, p0, box)

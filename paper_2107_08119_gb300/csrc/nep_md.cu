@@ -3,15 +3,16 @@
 // One step is a fixed sequence of kernels on the caller's stream, with no
 // host round trip:
 //   k_kick_drift   v += dt/2 F/m; x += dt v (FP64); FP32 hi/lo split of x;
-//                  largest squared displacement since the last list build
-//   k_decide       gate = (max displacement > skin/2) or a pending rebuild
+//                  largest squared displacement since the last list build;
+//                  its last block sets the gate = (max displacement >
+//                  skin/2) or a pending rebuild
 //   list build     wrap, bin, Verlet list, reverse index (gated: the kernels
 //                  return at once when the gate is zero)
 //   k_site         site energies and partial forces
 //   k_assemble     forces, second half kick, E_kin, virial and heat current
 //                  J = sum_i W_i . v_i (Eq. 7), per-block FP64 sums
-//   k_md_finish    block sums in a fixed order, thermo row and J of this
-//                  step, Berendsen factor
+//   k_md_finish    block sums in a fixed order (one block per sum), thermo
+//                  row and J of this step, Berendsen factor
 // Optional extensions (nep_md_set_thermostat, nep_md_set_hnemd):
 //   HNEMD          the assembly writes F and W_i; after the virial sum,
 //                  k_hnemd_kick adds F_i^ext = F_e . W_i - F_e . W / N
@@ -45,11 +46,28 @@ namespace nep {
 namespace {
 
 // control words on the device
-enum { kCtlDisp = 0, kCtlGate = 1, kCtlPending = 2, kCtlStep = 3, kCtlWords = 4 };
+enum { kCtlDisp = 0, kCtlGate = 1, kCtlPending = 2, kCtlStep = 3, kCtlFinish = 4, kCtlKick = 5, kCtlWords = 6 };
+
+// The rebuild decision: gate = a pending rebuild or the largest squared
+// displacement since the last build above thresh2; the displacement and the
+// pending flag are cleared.  use_cond: the step runs from a CUDA graph whose
+// list rebuild sits behind the conditional node `cond`, which this sets.
+__device__ void decide(unsigned* ctl, float thresh2, unsigned long long* rebuilds, cudaGraphConditionalHandle cond,
+                       int use_cond)
+{
+    const unsigned disp = __ldcg(ctl + kCtlDisp);
+    const bool go = __ldcg(ctl + kCtlPending) != 0u || __uint_as_float(disp) > thresh2;
+    ctl[kCtlGate] = go ? 1u : 0u;
+    ctl[kCtlDisp] = 0u;
+    ctl[kCtlPending] = 0u;
+    if (go) *rebuilds += 1ull;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
 
 __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__ v, const float* __restrict__ F,
                              double hdtm, double dt, float* __restrict__ xh, float* __restrict__ xl,
-                             const double* __restrict__ x_ref, unsigned* __restrict__ ctl)
+                             const double* __restrict__ x_ref, unsigned* __restrict__ ctl, float thresh2,
+                             unsigned long long* __restrict__ rebuilds, cudaGraphConditionalHandle cond, int use_cond)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float d2 = 0.f;
@@ -83,19 +101,18 @@ __global__ void k_kick_drift(int n, double* __restrict__ x, double* __restrict__
         // non-negative floats order like their bit patterns
         if (threadIdx.x == 0 && d2 > 0.f) atomicMax(ctl + kCtlDisp, __float_as_uint(d2));
     }
-}
-
-// use_cond: the step runs from a CUDA graph whose list rebuild sits behind
-// the conditional node `cond`, which this sets.
-__global__ void k_decide(unsigned* __restrict__ ctl, float thresh2, unsigned long long* __restrict__ rebuilds,
-                         cudaGraphConditionalHandle cond, int use_cond)
-{
-    const bool go = ctl[kCtlPending] != 0u || __uint_as_float(ctl[kCtlDisp]) > thresh2;
-    ctl[kCtlGate] = go ? 1u : 0u;
-    ctl[kCtlDisp] = 0u;
-    ctl[kCtlPending] = 0u;
-    if (go) *rebuilds += 1ull;
-    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+    // the last block to finish (a count in ctl, which it clears) takes the
+    // rebuild decision
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's maximum before the count
+        last = atomicAdd(ctl + kCtlKick, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    ctl[kCtlKick] = 0u;
+    decide(ctl, thresh2, rebuilds, cond, use_cond);
 }
 
 // Second half kick with the HNEMD driving force, E_kin and J per block.
@@ -284,57 +301,75 @@ __global__ void k_scale_v(int n, double* __restrict__ vel, const double* __restr
     for (int c = 0; c < 3; ++c) vel[(size_t)c * n + i] *= lam;
 }
 
-// The step's last kernel: warp 0 sums the site-energy block partials into
-// red[0], warp 1 + c sums component c of the other block partials into
-// red[off_x + c] (fixed order, like k_reduce), then thread 0 writes the thermo
-// row and J and the Berendsen factor.
-__global__ void k_md_finish(const double* __restrict__ part_e, int nb_e, const double* __restrict__ part_x, int nb_x,
-                            int ncomp_x, int off_x, double* __restrict__ red, double* __restrict__ thermo,
-                            double* __restrict__ heat, unsigned* __restrict__ ctl, double t0, double tau, double dt,
-                            double dof_kb)
+// The step's last kernel, one block per sum: block 0 adds the site-energy
+// block partials into red[0], block 1 + c component c of the other block
+// partials into red[off_x + c] (each thread a fixed stride of the partials in
+// order, then a fixed tree: deterministic).  Several SMs share the FP64 adds
+// (slow on this part).  The last block to finish (a count in ctl, which it
+// clears) writes the thermo row and J and the Berendsen factor.
+constexpr int kFinishThreads = 128;
+
+__global__ void __launch_bounds__(kFinishThreads) k_md_finish(const double* __restrict__ part_e, int nb_e,
+                                                              const double* __restrict__ part_x, int nb_x,
+                                                              int ncomp_x, int off_x, double* __restrict__ red,
+                                                              double* __restrict__ thermo, double* __restrict__ heat,
+                                                              unsigned* __restrict__ ctl, double t0, double tau,
+                                                              double dt, double dof_kb)
 {
     // red: [0] E_pot, [1..9] W (row-major), [10] E_kin, [11..13] J, [14] lambda
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w <= ncomp_x) {
-        const double* src = w == 0 ? part_e : part_x + (w - 1);
-        const int nb = w == 0 ? nb_e : nb_x;
-        const int stride = w == 0 ? 1 : ncomp_x;
-        double v = 0.0;
-        // unrolled so that eight loads are in flight ahead of the (ordered) adds
+    const int w = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double* src = w == 0 ? part_e : part_x + (w - 1);
+    const int nb = w == 0 ? nb_e : nb_x;
+    const int stride = w == 0 ? 1 : ncomp_x;
+    double v = 0.0;
+    // unrolled so that eight loads are in flight ahead of the (ordered) adds
 #pragma unroll 8
-        for (int b = lane; b < nb; b += 32) v += src[(size_t)b * stride];
+    for (int b = threadIdx.x; b < nb; b += kFinishThreads) v += src[(size_t)b * stride];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[w == 0 ? 0 : off_x + w - 1] = v;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __shared__ double wsum[kFinishThreads / 32];
+    __shared__ int last;
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < kFinishThreads / 32; ++q) t += wsum[q];
+        red[w == 0 ? 0 : off_x + w - 1] = t;
+        __threadfence();  // this sum before the count
+        last = atomicAdd(ctl + kCtlFinish, 1u) == gridDim.x - 1;
     }
     __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    ctl[kCtlFinish] = 0u;
+    // the other blocks' sums, read from L2
+    auto rd = [&](int k) { return __ldcg(red + k); };
     const unsigned s = ctl[kCtlStep];
-    if (threadIdx.x == 0) {
-        double ek = red[10];
-        if (tau > 0.0) {
-            const double T = 2.0 * ek / dof_kb;
-            const double lam = T > 0.0 ? sqrt(1.0 + dt / tau * (t0 / T - 1.0)) : 1.0;
-            red[14] = lam;
-            ek *= lam * lam;
-        }
-        if (thermo) {
-            double* t = thermo + (size_t)s * NEP_THERMO_COLS;
-            t[0] = red[0];
-            t[1] = ek;
-            t[2] = red[1];  // xx
-            t[3] = red[5];  // yy
-            t[4] = red[9];  // zz
-            t[5] = red[2];  // xy
-            t[6] = red[6];  // yz
-            t[7] = red[7];  // zx
-        }
-        if (heat) {
-            heat[(size_t)s * 3 + 0] = red[11];
-            heat[(size_t)s * 3 + 1] = red[12];
-            heat[(size_t)s * 3 + 2] = red[13];
-        }
-        ctl[kCtlStep] = s + 1u;
+    double ek = rd(10);
+    if (tau > 0.0) {
+        const double T = 2.0 * ek / dof_kb;
+        const double lam = T > 0.0 ? sqrt(1.0 + dt / tau * (t0 / T - 1.0)) : 1.0;
+        red[14] = lam;
+        ek *= lam * lam;
     }
+    if (thermo) {
+        double* t = thermo + (size_t)s * NEP_THERMO_COLS;
+        t[0] = rd(0);
+        t[1] = ek;
+        t[2] = rd(1);  // xx
+        t[3] = rd(5);  // yy
+        t[4] = rd(9);  // zz
+        t[5] = rd(2);  // xy
+        t[6] = rd(6);  // yz
+        t[7] = rd(7);  // zx
+    }
+    if (heat) {
+        heat[(size_t)s * 3 + 0] = rd(11);
+        heat[(size_t)s * 3 + 1] = rd(12);
+        heat[(size_t)s * 3 + 2] = rd(13);
+    }
+    ctl[kCtlStep] = s + 1u;
 }
 
 inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
@@ -749,8 +784,8 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
     auto head = [&](cudaStream_t q, bool use_cond, cudaGraphConditionalHandle cond) {
         Profiler::Slot* pk = m->prof.begin(NEP_PROFILE_STEP, q);
         k_kick_drift<<<blocks_for(n, 256), 256, 0, q>>>(n, pos, vel, md->ws.force, hdtm, dt, nl.xh, nl.xl, md->x_ref,
-                                                        md->ctl);
-        k_decide<<<1, 1, 0, q>>>(md->ctl, thresh * thresh, md->rebuilds, cond, use_cond ? 1 : 0);
+                                                        md->ctl, thresh * thresh, md->rebuilds, cond,
+                                                        use_cond ? 1 : 0);
         m->prof.end(pk, q);
     };
     auto rebuild = [&](cudaStream_t q, const unsigned* g) {
@@ -784,11 +819,11 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
             if ((r = launch_reduce(part_a, b2, c2, md->red + 1, q))) return r;
             k_hnemd_kick<<<nbk, 256, 0, q>>>(n, md->ws.force, w_out, vel, md->fe[0], md->fe[1], md->fe[2],
                                              md->red + 1, 1.0 / n, hdtm, kef, part_h, m->d_err);
-            k_md_finish<<<1, 32 * 5, 0, q>>>(part_e, b1, part_h, nbk, 4, 10, md->red, thermo, heat, md->ctl, md->t0,
-                                             md->tau, dt, dof_kb);
+            k_md_finish<<<5, kFinishThreads, 0, q>>>(part_e, b1, part_h, nbk, 4, 10, md->red, thermo, heat, md->ctl,
+                                                     md->t0, md->tau, dt, dof_kb);
         } else {
-            k_md_finish<<<1, 32 * (1 + c2), 0, q>>>(part_e, b1, part_a, b2, c2, 1, md->red, thermo, heat, md->ctl,
-                                                    md->t0, md->tau, dt, dof_kb);
+            k_md_finish<<<1 + c2, kFinishThreads, 0, q>>>(part_e, b1, part_a, b2, c2, 1, md->red, thermo, heat,
+                                                          md->ctl, md->t0, md->tau, dt, dof_kb);
         }
         if (sample) {  // v is that of J: after the second half kick, before the thermostat
             const int avail = (int)(md->shc_samples + 1 < md->shc_lags ? md->shc_samples + 1 : md->shc_lags);
@@ -807,7 +842,8 @@ int nep_md_step(nep_md* md, double* pos, double* vel, int n_steps, double dt, do
 
     // Without phase timing and without the per-step host logic of the
     // spectral heat current, a step runs from a CUDA graph captured once: the
-    // list rebuild is the body of a conditional node that k_decide switches,
+    // list rebuild is the body of a conditional node that the last block of
+    // k_kick_drift switches,
     // so a step without a rebuild launches none of the list kernels.
     if (!m->prof.on && md->shc_lags == 0) {
         nep_md::GraphKey key{pos, vel, thermo, heat, dt, md->t0, md->tau, {md->fe[0], md->fe[1], md->fe[2]}, drive,
