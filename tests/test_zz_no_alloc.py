@@ -72,6 +72,49 @@ def test_static_entry_point_matches_compute_efv(N):
             assert (out["virial_total"] - ref["virial_total"]).abs().max().item() <= TOL_W * n
 
 
+def _outs(n):
+    import torch
+    return {"e_total": torch.empty(1, dtype=torch.float64, device="cuda"),
+            "e_atom": torch.empty(n, dtype=torch.float64, device="cuda"),
+            "force": torch.empty(3, n, dtype=torch.float32, device="cuda"),
+            "virial_atom": torch.empty(9, n, dtype=torch.float32, device="cuda"),
+            "virial_total": torch.empty(9, dtype=torch.float64, device="cuda"),
+            "err": torch.full((1,), -1, dtype=torch.int32, device="cuda")}
+
+
+def test_static_entry_point_in_a_cuda_graph(N):
+    """The call allocates and synchronises nothing, so after a first eager
+    call in the context it can be captured into a CUDA graph: each replay
+    reads the positions as they are at replay time and gives the bits of an
+    eager call on them."""
+    import torch
+    h = N.Hyper(max_neighbors=N.STATIC_MAX_NEIGHBORS)
+    pos, box, z = inputs.config1()
+    n = len(pos)
+    z_dev = torch.tensor(np.asarray(z, np.float32), device="cuda")
+    ps = soa(pos)
+    eager, graphed = _outs(n), _outs(n)
+    assert _call_static(N, h, z_dev, ps, box, eager) == 0, N._lib.nep_last_error()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        assert _call_static(N, h, z_dev, ps, box, graphed) == 0, N._lib.nep_last_error()
+    rng = np.random.default_rng(11)
+    for step in range(3):
+        if step:
+            # move the atoms a little: the replay must see the new positions
+            ps += torch.tensor(rng.normal(scale=0.02, size=ps.shape), dtype=torch.float64, device="cuda")
+            assert _call_static(N, h, z_dev, ps, box, eager) == 0, N._lib.nep_last_error()
+        for t in graphed.values():
+            t.fill_(float("nan") if t.is_floating_point() else -1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(graphed["err"].item()) == 0
+        for k in eager:
+            assert torch.equal(graphed[k], eager[k]), (step, k)
+    del g
+
+
 def test_static_entry_point_rejects_oversize_inputs(N):
     """Sizes beyond the fixed scratch are refused before any launch."""
     import torch
