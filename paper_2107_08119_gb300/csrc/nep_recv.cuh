@@ -1,7 +1,7 @@
 // nep_recv.cuh -- device helpers of the SNES receiver pass (the second
 // contraction pass: F_i = G_i . B_i - sum_j p_kji, and the per-chunk loss sums
-// of Eqs. 30-32), shared by the receiver kernels of nep_train.cu and the
-// combined owner-receiver kernel of nep_pop_tc.cu.
+// of Eqs. 30-32), used by the receiver kernels of nep_train.cu; nep_pop_tc.cu
+// takes the population bound kMaxPop from here.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -41,9 +41,8 @@ struct RecvAtom {
     long long ps, pe;     // slot range
 };
 
-// The own and virial terms are read from L2 (ld.global.cg): in the combined
-// owner-receiver kernel they were written by other blocks of the same launch,
-// and a line cached in L1 earlier could hold stale parts.
+// The own and virial terms are read through L2 (ld.global.cg, no L1
+// allocation): each is read once.
 __device__ __forceinline__ void recv_load(RecvAtom& a, int i, int P, int Pst, int k0, bool ld, bool on0, bool on1,
                                           const double* __restrict__ U, const long long* __restrict__ pstart,
                                           const float* __restrict__ fown, const float* __restrict__ w6in,

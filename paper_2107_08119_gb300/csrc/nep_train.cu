@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract(
 {
     constexpr int kWarps = kReceiverThreads / 32;
     __shared__ RecvRed<kWarps> red;
-    const int c = c0 + blockIdx.x;
+    const int c = c0 + (int)(gridDim.x - 1 - blockIdx.x);  // last chunk first (as k_contract_bulk)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = 2 * lane;
     const bool on0 = k0 < P, on1 = k0 + 1 < P;
@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
     constexpr int kPair = 2 * (int)sizeof(PT);  // bytes of one lane's two members
     __shared__ RecvRed<kWarps> red;
     extern __shared__ __align__(16) unsigned char s_slots_raw[];  // [warps][kRecvStage][3][Pst / 2] member pairs
-    const int c = c0 + blockIdx.x;
+    const int c = c0 + (int)(gridDim.x - 1 - blockIdx.x);  // last chunk first (as k_contract_bulk)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k0 = 2 * lane;
     const bool on0 = k0 < P, on1 = k0 + 1 < P;
@@ -700,8 +700,12 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
     BulkSmem& S = *reinterpret_cast<BulkSmem*>(s_bulk);
     bulk_init(S);
     BulkWarp bw;
-    if (!bulk_receive_chunk<PT>(c0 + (int)blockIdx.x, P, Pst, chunk_begin, chunk_end, U, pstart, fown, pbuf, w6in,
-                                f_tar, partials, err, false, S, bw))
+    // the range's chunks from the last: the owner pass wrote the partial
+    // forces in owner order, so the last chunks' rows are the ones most
+    // likely still in L2
+    const int c = c0 + (int)(gridDim.x - 1 - blockIdx.x);
+    if (!bulk_receive_chunk<PT>(c, P, Pst, chunk_begin, chunk_end, U, pstart, fown, pbuf, w6in, f_tar, partials, err,
+                                false, S, bw))
         bulk_drain(S, bw);
 }
 
