@@ -439,7 +439,7 @@ int nep_dataset_get_shape(const nep_dataset* ds, int* shape);
  * the fastest on the dataset.  Candidates: the fused contraction with 4, 8
  * or 16 members per block (where the shared memory fits; the owner atoms per
  * warp are 32 / members), and the two passes with waves 1, 2, 4 x owner
- * warps 4, 8 x discard 0, 1 when waves > 1 x unroll 1, 4, 8, 12, 16; each
+ * warps 4, 8 x discard 0, 1 x unroll 1, 4, 8, 12, 16; each
  * with network threads 128, 256 in FP32 mode; in BF16 mode also every
  * two-pass candidate with owner_tc 1, and every candidate with pop_pipe 0
  * and 1.  Synchronises the stream.

@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_staged(
 
 template <class PT>
 __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
-    int c0, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
+    int c0, int discard, int P, int Pst, const int* __restrict__ chunk_begin, const int* __restrict__ chunk_end,
     const double* __restrict__ U, const long long* __restrict__ pstart, const float* __restrict__ fown,
     const PT* __restrict__ pbuf, const float* __restrict__ w6in, const float* __restrict__ f_tar,
     double* __restrict__ partials, unsigned* __restrict__ err)
@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(kReceiverThreads, 2) k_contract_bulk(
     // likely still in L2
     const int c = c0 + (int)(gridDim.x - 1 - blockIdx.x);
     if (!bulk_receive_chunk<PT>(c, P, Pst, chunk_begin, chunk_end, U, pstart, fown, pbuf, w6in, f_tar, partials, err,
-                                false, S, bw))
+                                discard != 0, S, bw))
         bulk_drain(S, bw);
 }
 
@@ -1347,10 +1347,9 @@ void launch_contraction_t(const nep_dataset* ds, int P, int Pst, int c_lo, int c
         cudaStreamWaitEvent(p2, ev, 0);
     }
     if (sh.recv_unroll == 1) {
-        k_contract_bulk<PT><<<c_hi - c_lo, kReceiverThreads, sizeof(BulkSmem), p2>>>(c_lo, P, Pst, ds->chunk_begin,
-                                                                              ds->chunk_end, ds->U, ds->pstart,
-                                                                              ds->fown, pbuf, ds->w6, ds->f_tar,
-                                                                              ds->partials, ds->m->d_err);
+        k_contract_bulk<PT><<<c_hi - c_lo, kReceiverThreads, sizeof(BulkSmem), p2>>>(
+            c_lo, sh.discard, P, Pst, ds->chunk_begin, ds->chunk_end, ds->U, ds->pstart, ds->fown, pbuf, ds->w6,
+            ds->f_tar, ds->partials, ds->m->d_err);
     } else if (sh.recv_unroll == 16) {
         const size_t smem = (size_t)(kReceiverThreads / 32) * kRecvStage * 3 * Pst * sizeof(PT);
         k_contract_staged<PT><<<c_hi - c_lo, kReceiverThreads, smem, p2>>>(c_lo, sh.discard, P, Pst, ds->chunk_begin,
@@ -2050,7 +2049,7 @@ int nep_dataset_tune(nep_model* m, nep_dataset* ds, int n_pop, int precision, in
     const int wv[] = {1, 2, 4};
     for (int w : wv)
         for (int ow = 4; ow <= 8; ow += 4)
-            for (int dc = 0; dc <= (w > 1 ? 1 : 0); ++dc)
+            for (int dc = 0; dc <= 1; ++dc)
                 for (int mt = 128; mt <= 256; mt += 128)
                     for (int ru : {1, 4, 8, 12, 16}) {
                         if (precision == NEP_PREC_BF16 && mt == 128) continue;  // the FP32 network is not launched

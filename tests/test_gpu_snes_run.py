@@ -57,7 +57,7 @@ def _two_pass_shapes(precision, N):
     out = []
     for w in (1, 2, 4):
         for ow in (4, 8):
-            for dc in ((0, 1) if w > 1 else (0,)):
+            for dc in (0, 1):
                 for mt in ((128, 256) if precision == N.PREC_FP32 else (256,)):
                     for ru in (1, 4, 8, 12, 16):
                         for pp in ((0, 1) if precision == N.PREC_BF16 else (0,)):
@@ -69,7 +69,7 @@ def _two_pass_shapes(precision, N):
 def _tc_shapes():
     """Two-pass shapes with the first pass on the tensor cores (BF16)."""
     return [dict(waves=w, owner_warps=4, discard=dc, mlp_threads=256, recv_unroll=ru, fused=0, owner_tc=1, pop_pipe=pp)
-            for w in (1, 2, 4) for dc in ((0, 1) if w > 1 else (0,)) for ru in (1, 4, 8, 12, 16) for pp in (0, 1)]
+            for w in (1, 2, 4) for dc in (0, 1) for ru in (1, 4, 8, 12, 16) for pp in (0, 1)]
 
 
 def _fused_shapes(precision, N):
