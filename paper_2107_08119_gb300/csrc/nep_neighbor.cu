@@ -12,7 +12,7 @@
 //      (full list, both directions), unsorted; each row is then ordered by
 //      increasing distance, and the reverse-pair index (for slot k of atom
 //      i, the slot of i in j's list) follows from the partners' ranks
-//      (k_half_cells, k_sort_rows, k_rev_perm below);
+//      (k_half_cells, k_sort_rows, k_rev_tile below);
 // Boxes with fewer than 3 cells in a direction (small training cells) use a
 // brute-force scan over all atoms and images, the rows sorted in place
 // (keys atom-major in the partial-force buffer, the values in vala), and
@@ -226,8 +226,10 @@ __device__ __forceinline__ unsigned long long sort_key(float d2, int v)
 //                 (slot-major nbr), the rank of every unsorted slot (vala),
 //                 and into the fourth word of each partner entry the rank it
 //                 got here: the partner's reverse index.
-//   k_rev_perm    rev[rank of slot s][i] = the fourth word of i's slot s,
-//                 within each row.
+//   k_rev_tile    rev[rank of slot s][i] = the fourth word of i's slot s,
+//                 within each row, 32 atoms per block transposed through
+//                 shared memory into whole-row stores (k_rev_perm, a warp
+//                 per atom, above 352 slots).
 // The pair vector is computed once per pair in the canonical orientation, so
 // the rows and the reverse index are the same as those of the full-shell
 // search (the order of the unsorted slots, which the atomics decide, does
@@ -479,6 +481,56 @@ __global__ void k_rev_perm(int n, int m_cap, const int* __restrict__ count, cons
     }
 }
 
+// The same reverse index with the slot-major stores made whole: a block of
+// eight warps takes tiles of 32 consecutive atoms in turn; each warp fills the shared tile
+// columns of its atoms (rev value of sorted slot r of atom a at tile[r][a],
+// reading the rows as k_rev_perm does), then each warp stores tile rows, 32
+// consecutive atoms per 128-byte store.  Slots at or past an atom's count are
+// not stored.  Shared memory: m_cap x 33 ints.
+constexpr int kRevAtoms = 32;
+constexpr int kRevThreads = 256;
+constexpr int kRevTileMaxSlots = 352;  // 352 x 33 x 4 bytes stay under 48 KB
+constexpr int kRevGridCap = 152 * 8;   // blocks walk the 32-atom tiles; a gated-off launch retires fast
+
+__global__ void __launch_bounds__(kRevThreads) k_rev_tile(int n, int m_cap, const int* __restrict__ count,
+                                                          const int* __restrict__ rows, const int* __restrict__ inv,
+                                                          int* __restrict__ rev, unsigned* err, const unsigned* gate)
+{
+    if (gated_off(gate)) return;
+    extern __shared__ int s_tile[];  // [m_cap][kRevAtoms + 1]
+    __shared__ int s_cnt[kRevAtoms];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = (n + kRevAtoms - 1) / kRevAtoms;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int i0 = tile * kRevAtoms;
+        if (threadIdx.x < kRevAtoms) {
+            const int i = i0 + threadIdx.x;
+            s_cnt[threadIdx.x] = i < n ? min(count[i], m_cap) : 0;
+        }
+        __syncthreads();
+        for (int a = warp; a < kRevAtoms; a += kRevThreads / 32) {
+            const int i = i0 + a, ci = s_cnt[a];
+            for (int s = lane; s < ci; s += 32) {
+                const int r = inv[(size_t)i * m_cap + s];
+                int v = rows[((size_t)i * m_cap + s) * 4 + 3];
+                if (v < 0 || v >= m_cap) {
+                    atomicOr(err, kErrReverse);
+                    v = r;
+                }
+                if (r >= 0 && r < ci)
+                    s_tile[r * (kRevAtoms + 1) + a] = v;
+                else
+                    atomicOr(err, kErrReverse);
+            }
+        }
+        __syncthreads();
+        const int ca = s_cnt[lane];
+        for (int r = warp; r < m_cap; r += kRevThreads / 32)
+            if (r < ca) rev[(size_t)r * n + i0 + lane] = s_tile[r * (kRevAtoms + 1) + lane];
+        __syncthreads();  // the tile and the counts are read before the next tile writes them
+    }
+}
+
 __global__ void k_verlet_brute(int n, int m_cap, float rv2, const float* __restrict__ xh,
                                const float* __restrict__ xl, int* __restrict__ count, int* __restrict__ nbr,
                                float* __restrict__ key, int* __restrict__ vala, unsigned* err, Box b,
@@ -587,8 +639,13 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, cons
             d_gate);
         k_sort_rows<<<grid, 32 * kVerletWarps, (size_t)kVerletWarps * lcap * 12, st>>>(
             n, nl.m_cap, lcap, rows, nl.count, nl.nbr, nl.vala, d_err, d_gate);
-        k_rev_perm<<<std::min(blocks_for(n, 4), kListGridCap), 128, 0, st>>>(n, nl.m_cap, nl.count, rows, nl.vala,
-                                                                              nl.rev, d_err, d_gate);
+        if (nl.m_cap <= kRevTileMaxSlots)
+            k_rev_tile<<<std::min(blocks_for(n, kRevAtoms), kRevGridCap), kRevThreads,
+                         (size_t)nl.m_cap * (kRevAtoms + 1) * sizeof(int), st>>>(n, nl.m_cap, nl.count, rows,
+                                                                                  nl.vala, nl.rev, d_err, d_gate);
+        else
+            k_rev_perm<<<std::min(blocks_for(n, 4), kListGridCap), 128, 0, st>>>(n, nl.m_cap, nl.count, rows,
+                                                                                  nl.vala, nl.rev, d_err, d_gate);
         return cuda_fail(cudaGetLastError(), "neighbour-list kernels");
     } else {
         k_verlet_brute<<<blocks_for(n, 128), 128, 0, st>>>(n, nl.m_cap, rv2, nl.xh, nl.xl, nl.count, nl.nbr, nl.pf,
