@@ -12,7 +12,7 @@
 //      (full list, both directions), unsorted; each row is then ordered by
 //      increasing distance, and the reverse-pair index (for slot k of atom
 //      i, the slot of i in j's list) follows from the partners' ranks
-//      (k_half_cells, k_sort_rows, k_rev_tile below);
+//      (k_half_cells, k_sort_tile, k_rev_tile below);
 // Boxes with fewer than 3 cells in a direction (small training cells) use a
 // brute-force scan over all atoms and images, the rows sorted in place
 // (keys atom-major in the partial-force buffer, the values in vala), and
@@ -221,11 +221,14 @@ __device__ __forceinline__ unsigned long long sort_key(float d2, int v)
 //                 taken with atomics: (value, distance word, the partner
 //                 entry's slot).  The rows live in the partial-force buffer,
 //                 four words per slot.
-//   k_sort_rows   one warp per atom ranks its row by (squared distance,
+//   k_sort_tile   one warp per atom ranks its row by (squared distance,
 //                 value), which is unique, and writes the sorted values
-//                 (slot-major nbr), the rank of every unsorted slot (vala),
-//                 and into the fourth word of each partner entry the rank it
-//                 got here: the partner's reverse index.
+//                 (slot-major nbr, through a shared tile of 32 atoms so that
+//                 the stores are whole rows), the rank of every unsorted
+//                 slot (vala), and into the fourth word of each partner
+//                 entry the rank it got here: the partner's reverse index
+//                 (k_sort_rows, a warp per atom storing nbr directly, above
+//                 128 slots).
 //   k_rev_tile    rev[rank of slot s][i] = the fourth word of i's slot s,
 //                 within each row, 32 atoms per block transposed through
 //                 shared memory into whole-row stores (k_rev_perm, a warp
@@ -366,12 +369,13 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_half_cells(int n, int m_c
 }
 
 // Ranks a warp's row entries c0 + lane + 32 t against all ns (keys in sk)
-// and writes each at its rank: the value to nbr (slot-major), the rank to
-// inv[i][unsorted slot] and to the fourth word of the partner entry (the
+// and writes each at its rank: the value to out[rank * out_stride] (the
+// atom's column of the slot-major nbr, or of a shared-memory tile), the rank
+// to inv[i][unsorted slot] and to the fourth word of the partner entry (the
 // partner's reverse index; j's slot sp[e] of the atom in the value).
 template <int EPL>
 __device__ __forceinline__ void rank_rows_write(int c0, int ns, int m, int lane, const unsigned long long* sk,
-                                                const int* sp, int i, int n, int m_cap, int* __restrict__ nbr,
+                                                const int* sp, int i, int out_stride, int m_cap, int* out,
                                                 int* __restrict__ rows, int* __restrict__ inv)
 {
     unsigned long long ke[EPL];
@@ -393,7 +397,7 @@ __device__ __forceinline__ void rank_rows_write(int c0, int ns, int m, int lane,
         if (e < ns) {
             const int v = (int)(unsigned)ke[t];
             inv[(size_t)i * m_cap + e] = rk[t];
-            nbr[(size_t)rk[t] * n + i] = v;
+            out[(size_t)rk[t] * out_stride] = v;
             const int ps = sp[e];
             if (ps < m_cap) rows[((size_t)(v & 0xFFFFFF) * m_cap + ps) * 4 + 3] = rk[t];
         }
@@ -447,13 +451,107 @@ __global__ void __launch_bounds__(32 * kVerletWarps) k_sort_rows(int n, int m_ca
         __syncwarp();
         fetch(i + stride);
         if (ns <= 32)
-            rank_rows_write<1>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
+            rank_rows_write<1>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr + i, rows, inv);
         else if (ns <= 64)
-            rank_rows_write<2>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
+            rank_rows_write<2>(0, ns, m, lane, sk, sp, i, n, m_cap, nbr + i, rows, inv);
         else
             for (int c0 = 0; c0 < ns; c0 += 128)
-                rank_rows_write<4>(c0, ns, m, lane, sk, sp, i, n, m_cap, nbr, rows, inv);
+                rank_rows_write<4>(c0, ns, m, lane, sk, sp, i, n, m_cap, nbr + i, rows, inv);
         __syncwarp();
+    }
+}
+
+// The same sort with the slot-major nbr stores made whole: a block of
+// kSortWarps warps takes tiles of 32 consecutive atoms in turn, warp w the
+// atoms w, w + 8, w + 16, w + 24 of each (the next one's row loaded into
+// registers while the current one sorts); the sorted values go to a shared
+// tile (atom a's column), stored after the block barrier as rows of 32
+// consecutive atoms (one 128-byte store each).  inv and the partner words are
+// written as in k_sort_rows.  Shared memory: the warps' key buffers (lcap x
+// 12 bytes each), then the m_cap x 33-int tile.
+constexpr int kSortWarps = 8;
+constexpr int kSortAtoms = 32;
+constexpr int kSortGridCap = 152 * 8;
+constexpr size_t kSortTileMaxSmem = 48 * 1024;  // up to 128 slots per atom (the warp-per-atom sort beyond)
+
+__global__ void __launch_bounds__(32 * kSortWarps) k_sort_tile(int n, int m_cap, int lcap, int* __restrict__ rows,
+                                                              const int* __restrict__ count, int* __restrict__ nbr,
+                                                              int* __restrict__ inv, unsigned* err,
+                                                              const unsigned* gate)
+{
+    if (gated_off(gate)) return;
+    extern __shared__ unsigned long long s_sort[];
+    __shared__ int s_cnt[kSortAtoms];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long* sk = s_sort + (size_t)warp * lcap * 3 / 2;  // lcap keys, then lcap partner slots
+    int* sp = reinterpret_cast<int*>(sk + lcap);
+    int* s_tile = reinterpret_cast<int*>(s_sort + (size_t)kSortWarps * lcap * 3 / 2);  // [m_cap][33]
+    constexpr int kPer = kSortAtoms / kSortWarps;  // atoms per warp and tile
+    const int tiles = (n + kSortAtoms - 1) / kSortAtoms;
+    // this warp's k-th atom: tile blockIdx.x + (k / kPer) gridDim.x, column warp + kSortWarps (k % kPer)
+    auto atom_of = [&](int k, int& tile, int& a) {
+        tile = blockIdx.x + (k / kPer) * gridDim.x;
+        a = warp + kSortWarps * (k % kPer);
+        return tile * kSortAtoms + a;
+    };
+    constexpr int kPre = 4;  // 128 entries per row at most
+    int4 pre[kPre];
+    int pre_cnt = 0;
+    auto fetch = [&](int k) {
+        int tile, a;
+        const int at = atom_of(k, tile, a);
+        pre_cnt = tile < tiles && at < n ? count[at] : 0;
+        const int ns_a = min(min(pre_cnt, m_cap), lcap);
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) {
+            const int e = lane + 32 * t;
+            if (e < ns_a) pre[t] = *reinterpret_cast<const int4*>(rows + ((size_t)at * m_cap + e) * 4);
+        }
+    };
+    fetch(0);
+    for (int k = 0;; ++k) {
+        int tile, a;
+        const int i = atom_of(k, tile, a);
+        if (tile >= tiles) break;
+        const int cnt = pre_cnt;  // 0 past the last atom
+        if (cnt > m_cap && lane == 0) atomicOr(err, kErrOverflow);
+        const int m = cnt < m_cap ? cnt : m_cap;
+        const int ns = m < lcap ? m : lcap;
+        if (lane == 0) s_cnt[a] = ns;
+#pragma unroll
+        for (int t = 0; t < kPre; ++t) {
+            const int e = lane + 32 * t;
+            if (e < ns) {
+                sk[e] = sort_key(__int_as_float(pre[t].y), pre[t].x);
+                sp[e] = pre[t].z;
+            }
+        }
+        for (int e = 32 * kPre + lane; e < ns; e += 32) {  // rows longer than the prefetch (m_cap > 128)
+            const int4 r = *reinterpret_cast<const int4*>(rows + ((size_t)i * m_cap + e) * 4);
+            sk[e] = sort_key(__int_as_float(r.y), r.x);
+            sp[e] = r.z;
+        }
+        __syncwarp();
+        fetch(k + 1);
+        int* col = s_tile + a;
+        if (ns == 0) {
+        } else if (ns <= 32)
+            rank_rows_write<1>(0, ns, m, lane, sk, sp, i, kSortAtoms + 1, m_cap, col, rows, inv);
+        else if (ns <= 64)
+            rank_rows_write<2>(0, ns, m, lane, sk, sp, i, kSortAtoms + 1, m_cap, col, rows, inv);
+        else
+            for (int c0 = 0; c0 < ns; c0 += 128)
+                rank_rows_write<4>(c0, ns, m, lane, sk, sp, i, kSortAtoms + 1, m_cap, col, rows, inv);
+        __syncwarp();
+        if (k % kPer == kPer - 1) {
+            // the tile is complete: its rows to nbr, 32 consecutive atoms each
+            __syncthreads();
+            const int i0 = tile * kSortAtoms;
+            const int ca = s_cnt[lane];
+            for (int r = warp; r < m_cap; r += kSortWarps)
+                if (r < ca) nbr[(size_t)r * n + i0 + lane] = s_tile[r * (kSortAtoms + 1) + lane];
+            __syncthreads();  // the tile and the counts are read before the next tile writes them
+        }
     }
 }
 
@@ -637,8 +735,13 @@ int build_neighbor_list(NeighborList& nl, const Box& b, int n, double* pos, cons
         k_half_cells<<<grid, 32 * kVerletWarps, (size_t)kVerletWarps * (lcap + 6 * 32) * sizeof(int), st>>>(
             n, nl.m_cap, rv2, nl.xh, nl.xl, nl.atom_cell, nl.cell_start, nl.cell_atoms, nl.count, rows, lcap, d_err, b,
             d_gate);
-        k_sort_rows<<<grid, 32 * kVerletWarps, (size_t)kVerletWarps * lcap * 12, st>>>(
-            n, nl.m_cap, lcap, rows, nl.count, nl.nbr, nl.vala, d_err, d_gate);
+        const size_t sort_smem = (size_t)kSortWarps * lcap * 12 + (size_t)nl.m_cap * (kSortAtoms + 1) * sizeof(int);
+        if (sort_smem <= kSortTileMaxSmem)
+            k_sort_tile<<<std::min(blocks_for(n, kSortAtoms), kSortGridCap), 32 * kSortWarps, sort_smem, st>>>(
+                n, nl.m_cap, lcap, rows, nl.count, nl.nbr, nl.vala, d_err, d_gate);
+        else
+            k_sort_rows<<<grid, 32 * kVerletWarps, (size_t)kVerletWarps * lcap * 12, st>>>(
+                n, nl.m_cap, lcap, rows, nl.count, nl.nbr, nl.vala, d_err, d_gate);
         if (nl.m_cap <= kRevTileMaxSlots)
             k_rev_tile<<<std::min(blocks_for(n, kRevAtoms), kRevGridCap), kRevThreads,
                          (size_t)nl.m_cap * (kRevAtoms + 1) * sizeof(int), st>>>(n, nl.m_cap, nl.count, rows,
