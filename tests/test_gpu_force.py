@@ -76,6 +76,33 @@ def test_degenerate_inputs(N, orc):
     _compare(N, orc, np.array([[1.0, 1.5, 2.0]]), np.diag([3.1, 3.3, 3.6]), z)
 
 
+def test_list_kernels_at_large_capacities(N):
+    """Up to 128 slots per atom the row sort, and up to 352 the reverse index,
+    go through 32-atom shared-memory tiles; above, their warp-per-atom forms
+    run.  Every capacity gives the same distance-sorted lists, and forces
+    and energies within FP32 rounding of the default capacity's."""
+    pos, box, z = inputs.config1()
+    n = len(pos)
+    ref = None
+    for mn in (96, 160, 200, 384):
+        model = N.NEP(np.asarray(z, np.float32), N.Hyper(max_neighbors=mn))
+        out = model.compute(soa(pos), box)
+        cnt, nbr = model.neighbors(n)
+        cnt = cnt.cpu().numpy()
+        nbr = nbr.cpu().numpy()
+        rec = (cnt, [nbr[:cnt[i], i].copy() for i in range(n)], out["e_atom"].cpu().numpy(),
+               out["force"].cpu().numpy())
+        model.close()
+        assert cnt.max() <= 96
+        if ref is None:
+            ref = rec
+            continue
+        assert np.array_equal(rec[0], ref[0]), mn
+        assert all(np.array_equal(a, b) for a, b in zip(rec[1], ref[1])), mn
+        assert np.abs(rec[2] - ref[2]).max() <= 1e-6, mn
+        assert np.abs(rec[3] - ref[3]).max() <= 1e-5, mn
+
+
 def test_neighbor_list_matches_oracle(N, orc):
     """Integer work is exact: the GPU list holds the same (j, image) pairs as
     the oracle's brute force, away from the cutoff where FP32 and FP64 may
