@@ -831,15 +831,16 @@ constexpr int kOtcThreads = 128;
 constexpr int kOtcATile = 128 * 64;  // 128 rows x 32 FP16
 constexpr int kOtcBTile = 64 * 64;   // up to 64 members x 32 FP16
 constexpr int kOtcCols = 64;         // TMEM columns (members)
-// epilogue staging of the FP16 pair rows: 64 halves per row at a stride of
-// 36 words (16-byte row writes by one thread each take the minimum four
-// wavefronts), and each row's destination
-constexpr int kOtcRowWords = 36;
+// epilogue staging of the FP16 pair rows, one half of the member columns at a
+// time: 32 halves per row at a stride of 20 words (16-byte row writes by one
+// thread each take the minimum four wavefronts), and each row's destination
+constexpr int kOtcRowWords = 20;
 constexpr int kOtcStageH = 128 * kOtcRowWords * 4;
 constexpr int kOtcBars = 64;
 constexpr int kOtcSmem = 2 * (kOtcATile + kOtcBTile) + kOtcBars + kOtcStageH + 128 * 8;
+constexpr int kOtcPerSm = 6;  // CTAs per SM (35 KB of shared memory and 64 TMEM columns each)
 
-__global__ void __launch_bounds__(kOtcThreads) k_owner_tc(int t0, int t1, const OwnerTile* __restrict__ tiles,
+__global__ void __launch_bounds__(kOtcThreads, kOtcPerSm) k_owner_tc(int t0, int t1, const OwnerTile* __restrict__ tiles,
                                                           const unsigned char* __restrict__ apack,
                                                           const float* __restrict__ rowscale,
                                                           const unsigned char* __restrict__ Gt, int Pst,
@@ -932,54 +933,63 @@ __global__ void __launch_bounds__(kOtcThreads) k_owner_tc(int t0, int t1, const 
         if (!ok) break;
         ++mma_waited;
         tc::fence_after_sync();
-        // ---- epilogue, 1: thread t takes tile row t (TMEM lane t): a pair row
-        // to shared memory as FP16, an own-term or virial row straight to its
-        // FP32 destination (columns past Pst are staged but never stored)
-        uint32_t d[8][8];
+        // ---- epilogue, in two halves of the member columns (32 each; the
+        // second only when Pst > 32), so that a thread holds 32 TMEM values
+        // and the staging takes half the shared memory.  1: thread t takes
+        // tile row t (TMEM lane t): a pair row half to shared memory as FP16,
+        // an own-term or virial row half straight to its FP32 destination
+        // (columns past Pst are staged but never stored)
+        if (t < np) dst[t] = pbuf + ((size_t)rq * 3 + t % 3) * Pst;
+        const int halves = c8 > 4 ? 2 : 1;
+        for (int hh = 0; hh < halves; ++hh) {
+            uint32_t d[4][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            if (c < c8) tc::tmem_ld8(tb + lane_base + (uint32_t)(8 * c), d[c]);
-        tc::tmem_ld_wait();
-        if (t < np) {
-            dst[t] = pbuf + ((size_t)rq * 3 + t % 3) * Pst;
-            uint4* row = reinterpret_cast<uint4*>(stage_h + t * kOtcRowWords);
+            for (int c = 0; c < 4; ++c)
+                if (4 * hh + c < c8) tc::tmem_ld8(tb + lane_base + (uint32_t)(8 * (4 * hh + c)), d[c]);
+            tc::tmem_ld_wait();
+            if (t < np) {
+                uint4* row = reinterpret_cast<uint4*>(stage_h + t * kOtcRowWords);
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                if (c < c8) {
-                    uint32_t h[4];
+                for (int c = 0; c < 4; ++c)
+                    if (4 * hh + c < c8) {
+                        uint32_t h[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const __half2 v = __floats2half2_rn(__uint_as_float(d[c][2 * u]) * sc,
-                                                            __uint_as_float(d[c][2 * u + 1]) * sc);
-                        h[u] = *reinterpret_cast<const uint32_t*>(&v);
+                        for (int u = 0; u < 4; ++u) {
+                            const __half2 v = __floats2half2_rn(__uint_as_float(d[c][2 * u]) * sc,
+                                                                __uint_as_float(d[c][2 * u + 1]) * sc);
+                            h[u] = *reinterpret_cast<const uint32_t*>(&v);
+                        }
+                        row[c] = make_uint4(h[0], h[1], h[2], h[3]);
                     }
-                    row[c] = make_uint4(h[0], h[1], h[2], h[3]);
-                }
-        } else if (t < rows) {
-            const int e = t - np;
-            float* o = e < 3 ? fown + ((size_t)T.j * 3 + e) * Pst : w6 + ((size_t)T.j * 6 + (e - 3)) * Pst;
+            } else if (t < rows) {
+                const int e = t - np;
+                float* o = e < 3 ? fown + ((size_t)T.j * 3 + e) * Pst : w6 + ((size_t)T.j * 6 + (e - 3)) * Pst;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
+                for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (8 * c + 4 * h < Pst)  // Pst is a multiple of 4
-                        *reinterpret_cast<float4*>(o + 8 * c + 4 * h) =
-                            make_float4(__uint_as_float(d[c][4 * h]) * sc, __uint_as_float(d[c][4 * h + 1]) * sc,
-                                        __uint_as_float(d[c][4 * h + 2]) * sc, __uint_as_float(d[c][4 * h + 3]) * sc);
+                    for (int h = 0; h < 2; ++h) {
+                        const int m0 = 8 * (4 * hh + c) + 4 * h;
+                        if (m0 < Pst)  // Pst is a multiple of 4
+                            *reinterpret_cast<float4*>(o + m0) =
+                                make_float4(__uint_as_float(d[c][4 * h]) * sc, __uint_as_float(d[c][4 * h + 1]) * sc,
+                                            __uint_as_float(d[c][4 * h + 2]) * sc,
+                                            __uint_as_float(d[c][4 * h + 3]) * sc);
+                    }
+            }
+            // this half's TMEM reads are done (the last half's before the next MMA)
+            tc::fence_before_sync();
+            __syncthreads();
+            // ---- 2: the pair row halves, four per warp step: quarter-warp q
+            // stores row r + q's half as 8 pieces of 8 bytes (64 contiguous bytes)
+            {
+                const int lane = t & 31, q = lane >> 3, piece = lane & 7;
+                for (int r = 4 * warp + q; r - q < np; r += 4 * (kOtcThreads / 32))
+                    if (r < np && 4 * (8 * hh + piece) < Pst)
+                        reinterpret_cast<uint2*>(dst[r])[8 * hh + piece] =
+                            reinterpret_cast<const uint2*>(stage_h + r * kOtcRowWords)[piece];
+            }
+            __syncthreads();  // the staging is read before the next half or tile writes it
         }
-        __syncthreads();
-        // ---- 2: the pair rows, two per warp step: half-warp h stores row
-        // r + h as Pst / 4 pieces of 8 bytes (one coalesced row)
-        {
-            const int lane = t & 31, hw = lane >> 4, piece = lane & 15;
-            for (int r = 2 * warp + hw; r - hw < np; r += 2 * (kOtcThreads / 32))
-                if (r < np && 4 * piece < Pst)
-                    reinterpret_cast<uint2*>(dst[r])[piece] =
-                        reinterpret_cast<const uint2*>(stage_h + r * kOtcRowWords)[piece];
-        }
-        // every lane has read TMEM before the next MMA overwrites it
-        tc::fence_before_sync();
-        __syncthreads();
     }
     if (!ok) {
         if (t == 0) atomicOr(err, kErrTimeout);
@@ -1080,8 +1090,14 @@ int launch_pack_owner_tc(int n_tiles, const OwnerTile* tiles, const PairRec* rec
 
 int prepare_owner_tc()
 {
-    return cuda_fail(cudaFuncSetAttribute(k_owner_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kOtcSmem),
-                     "owner-pass shared memory");
+    // kOtcPerSm CTAs per SM need nearly all of the SM's shared memory: ask
+    // for the largest carveout
+    int rc = cuda_fail(cudaFuncSetAttribute(k_owner_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kOtcSmem),
+                       "owner-pass shared memory");
+    if (rc) return rc;
+    return cuda_fail(cudaFuncSetAttribute(k_owner_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                          (int)cudaSharedmemCarveoutMaxShared),
+                     "owner-pass shared-memory carveout");
 }
 
 int launch_owner_tc(int t0, int t1, const OwnerTile* tiles, const unsigned char* apack, const float* rowscale,
@@ -1093,7 +1109,7 @@ int launch_owner_tc(int t0, int t1, const OwnerTile* tiles, const unsigned char*
         return NEP_ERR_UNSUPPORTED;
     }
     if (t1 <= t0) return NEP_OK;
-    const int grid = std::min(t1 - t0, 152 * 5);  // five CTAs per SM (registers and shared memory)
+    const int grid = std::min(t1 - t0, 152 * kOtcPerSm);  // persistent: kOtcPerSm CTAs per SM
     k_owner_tc<<<grid, kOtcThreads, kOtcSmem, st>>>(t0, t1, tiles, apack, rowscale,
                                                     static_cast<const unsigned char*>(G), Pst, rev,
                                                     static_cast<__half*>(pbuf), fown, w6, err);
